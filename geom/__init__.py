@@ -1,0 +1,363 @@
+"""Seeded synthetic inputs for the diffusion-MRI finite-element solve.
+
+This module builds the *inputs* of the method only: node coordinates, tetrahedra,
+the compartment label of each tetrahedron, per-compartment diffusivity and
+membrane permeability, the PGSE timing and the gradient directions and b-values.
+It holds none of the method's arithmetic (no interface doubling, no element
+matrices, no time stepping); both the CPU oracle and the GPU library consume
+these arrays independently.
+
+Units follow the paper's own convention (Section 4 uses micrometres and
+microseconds): lengths in um, times in us.  With these units D in mm^2/s,
+b in s/mm^2 and kappa in m/s keep their numerical values.
+
+Workloads (synthetic stand-ins for the paper's neuron / extracellular meshes,
+Section 5, which are not available):
+  cfg1  40 um cube, 24^3 Kuhn grid, one compartment, Neumann, 1 RHS
+  cfg2  20 um cube, 48^3, centred sphere r = 5 um (two compartments), 5 b-values
+  cfg3  30 um periodic box, 64^3, 40 z-cylinders (lognormal radii), 64 dirs x 8 b
+  cfg4  40 um cube, 96^3, packed spheres + finite cylinders, 32 dirs x 4 b
+  cfg5  32 packings of uneven size (50k .. 2M nodes), 16 dirs x 4 b each
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Background compartment: no membrane of its own.  The permeability of the
+# interface between compartments a and b is the series value
+# 1 / (1/kappa_a + 1/kappa_b); an infinite entry contributes nothing.
+NO_MEMBRANE = math.inf
+
+
+# --------------------------------------------------------------------------
+# Structured Kuhn grid
+# --------------------------------------------------------------------------
+def kuhn_grid(nx: int, ny: int, nz: int, lo, hi):
+    """Nodes and positively oriented tetrahedra of an nx*ny*nz Kuhn grid.
+
+    Node (i, j, k) has index i + (nx+1)*(j + (ny+1)*k) (x fastest).  Each cell
+    is split into the six tetrahedra that share its (0,0,0)-(1,1,1) diagonal,
+    one per axis permutation, identical in every cell.
+    """
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    xs = np.linspace(lo[0], hi[0], nx + 1)
+    ys = np.linspace(lo[1], hi[1], ny + 1)
+    zs = np.linspace(lo[2], hi[2], nz + 1)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+    sx, sy, sz = 1, nx + 1, (nx + 1) * (ny + 1)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    base = (i * sx + j * sy + k * sz).ravel().astype(np.int64)
+    step = np.array([sx, sy, sz], dtype=np.int64)
+    perms = [(0, 1, 2), (1, 2, 0), (2, 0, 1), (0, 2, 1), (2, 1, 0), (1, 0, 2)]
+    tets = []
+    for p in perms:
+        even = p in [(0, 1, 2), (1, 2, 0), (2, 0, 1)]
+        v0 = base
+        v1 = v0 + step[p[0]]
+        v2 = v1 + step[p[1]]
+        v3 = v2 + step[p[2]]
+        tets.append(np.stack([v0, v1, v2, v3] if even else [v0, v1, v3, v2], axis=1))
+    # cell-major order: the six tetrahedra of a cell are consecutive
+    tets = np.stack(tets, axis=1).reshape(-1, 4)
+    return xyz, tets.astype(np.int32)
+
+
+def tet_centroids(xyz, tets):
+    return xyz[tets].mean(axis=1)
+
+
+# --------------------------------------------------------------------------
+# Compartment labelling (centroid rule)
+# --------------------------------------------------------------------------
+def label_sphere(xyz, tets, center, radius):
+    c = tet_centroids(xyz, tets)
+    inside = ((c - np.asarray(center)) ** 2).sum(axis=1) < radius * radius
+    return inside.astype(np.int32)
+
+
+def place_cylinders_periodic(n: int, L: float, mean_r: float, sigma: float, seed: int,
+                             max_trials: int = 100_000):
+    """Non-overlapping z-parallel cylinders in a periodic L x L square.
+
+    Radii are lognormal with log-space sd `sigma` and arithmetic mean `mean_r`
+    (mu = ln(mean_r) - sigma^2/2).  Cylinders are placed largest first at
+    uniform random centres; a centre is accepted when its periodic
+    minimum-image distance to every placed centre is at least r_i + r_j.
+    If one cylinder cannot be placed in `max_trials` draws the whole packing
+    is redrawn with seed + 1.  Returns (centres [n,2], radii [n], seed used).
+    """
+    s = seed
+    while True:
+        rng = np.random.default_rng(s)
+        mu = math.log(mean_r) - 0.5 * sigma * sigma
+        r = np.sort(rng.lognormal(mu, sigma, n))[::-1].copy()
+        cen = np.zeros((0, 2))
+        ok = True
+        for ri in r:
+            placed = False
+            tried = 0
+            while tried < max_trials:
+                b = min(4096, max_trials - tried)
+                cand = rng.uniform(0.0, L, size=(b, 2))
+                tried += b
+                if len(cen) == 0:
+                    cen = cand[:1]
+                    placed = True
+                    break
+                d = cand[:, None, :] - cen[None, :, :]
+                d -= L * np.round(d / L)
+                dist = np.sqrt((d ** 2).sum(-1))
+                good = np.all(dist >= ri + r[: len(cen)][None, :], axis=1)
+                idx = np.flatnonzero(good)
+                if idx.size:
+                    cen = np.vstack([cen, cand[idx[0]]])
+                    placed = True
+                    break
+            if not placed:
+                ok = False
+                break
+        if ok:
+            return cen, r, s
+        s += 1
+
+
+def label_cylinders_periodic(xyz, tets, centres, radii, L):
+    c = tet_centroids(xyz, tets)[:, :2]
+    lab = np.zeros(len(tets), dtype=np.int32)
+    for m, (cc, r) in enumerate(zip(centres, radii)):
+        d = c - cc
+        d -= L * np.round(d / L)
+        inside = (d ** 2).sum(1) < r * r
+        lab[inside & (lab == 0)] = m + 1
+    return lab
+
+
+def place_objects(n: int, L: float, rmin: float, rmax: float, gap: float, seed: int,
+                  max_trials: int = 10_000):
+    """Random non-overlapping spheres and finite cylinders in an L-cube.
+
+    Each object draws its radius r ~ U(rmin, rmax) and its kind (sphere or
+    cylinder, 50/50).  A cylinder has length 2r and a random unit axis.  The
+    overlap test uses bounding spheres (radius r for a sphere, r*sqrt(2) for a
+    cylinder) separated by at least `gap`.  Objects are placed largest first at
+    uniform random centres inside the cube; an object that cannot be placed in
+    `max_trials` draws is dropped.  Returns a list of dicts.
+    """
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(rmin, rmax, n)
+    kind = rng.integers(0, 2, n)  # 0 sphere, 1 cylinder
+    ax = rng.normal(size=(n, 3))
+    ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    rb = np.where(kind == 1, r * math.sqrt(2.0), r)
+    order = np.argsort(-rb, kind="stable")
+    placed = []
+    cen = np.zeros((0, 3))
+    rbp = np.zeros(0)
+    for o in order:
+        tried = 0
+        while tried < max_trials:
+            b = min(2048, max_trials - tried)
+            cand = rng.uniform(0.0, L, size=(b, 3))
+            tried += b
+            if len(cen):
+                dist = np.sqrt(((cand[:, None, :] - cen[None]) ** 2).sum(-1))
+                good = np.all(dist >= rb[o] + rbp[None, :] + gap, axis=1)
+                idx = np.flatnonzero(good)
+            else:
+                idx = np.array([0])
+            if idx.size:
+                c = cand[idx[0]]
+                cen = np.vstack([cen, c])
+                rbp = np.append(rbp, rb[o])
+                placed.append({"kind": int(kind[o]), "r": float(r[o]), "c": c.copy(),
+                               "axis": ax[o].copy()})
+                break
+    return placed
+
+
+def label_objects(xyz, tets, objects, h: float, n_cells: int, lo):
+    """Centroid rule: a tetrahedron belongs to object m+1 when its centroid is
+    inside object m (spheres: |x-c| < r; cylinders: radial distance < r and
+    |axial| < r).  Objects do not overlap, so the label is unique."""
+    c = tet_centroids(xyz, tets)
+    lab = np.zeros(len(tets), dtype=np.int32)
+    lo = np.asarray(lo, dtype=np.float64)
+    # tetrahedra are cell-major (6 per cell), cells x-fastest
+    for m, ob in enumerate(objects):
+        rb = ob["r"] * (math.sqrt(2.0) if ob["kind"] == 1 else 1.0)
+        i0 = np.clip(np.floor((ob["c"] - rb - lo) / h).astype(int), 0, n_cells - 1)
+        i1 = np.clip(np.floor((ob["c"] + rb - lo) / h).astype(int), 0, n_cells - 1)
+        kk, jj, ii = np.meshgrid(np.arange(i0[2], i1[2] + 1), np.arange(i0[1], i1[1] + 1),
+                                 np.arange(i0[0], i1[0] + 1), indexing="ij")
+        cells = (ii + n_cells * (jj + n_cells * kk)).ravel()
+        t = (cells[:, None] * 6 + np.arange(6)[None, :]).ravel()
+        d = c[t] - ob["c"]
+        if ob["kind"] == 0:
+            inside = (d ** 2).sum(1) < ob["r"] ** 2
+        else:
+            a = d @ ob["axis"]
+            rad2 = (d ** 2).sum(1) - a * a
+            inside = (rad2 < ob["r"] ** 2) & (np.abs(a) < ob["r"])
+        sel = t[inside & (lab[t] == 0)]
+        lab[sel] = m + 1
+    return lab
+
+
+# --------------------------------------------------------------------------
+# Gradient directions and sequences
+# --------------------------------------------------------------------------
+def fibonacci_dirs(n: int):
+    """Golden-angle spiral on the unit sphere: z_i = 1 - (2i+1)/n."""
+    i = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / n
+    rho = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * math.pi * (3.0 - math.sqrt(5.0))
+    d = np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+@dataclass
+class Problem:
+    """One geometry with its sequence, directions and b-values.
+
+    RHS r = d * n_b + j uses direction dirs[d] and b-value bvals[j]."""
+    name: str
+    xyz: np.ndarray            # [n_nodes, 3] float64, um
+    tets: np.ndarray           # [n_tets, 4] int32, positive orientation
+    tet_cmpt: np.ndarray       # [n_tets] int32 in [0, n_cmpt)
+    D_cmpt: np.ndarray         # [n_cmpt] float64, um^2/us (= mm^2/s)
+    kappa_cmpt: np.ndarray     # [n_cmpt] float64, um/us (= m/s); inf = no membrane
+    periodic_mask: int         # bit k: axis k periodic
+    box_lo: np.ndarray
+    box_hi: np.ndarray
+    dt: float                  # us
+    delta: float               # us
+    Delta: float               # us
+    TE: float                  # us
+    dirs: np.ndarray           # [n_dir, 3] unit vectors
+    bvals: np.ndarray          # [n_b] s/mm^2 (= us/um^2)
+    theta: float = 0.5
+    transformed: bool = False  # True: gauge-transformed frame (needed when periodic)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_cmpt(self):
+        return len(self.D_cmpt)
+
+    @property
+    def n_rhs(self):
+        return len(self.dirs) * len(self.bvals)
+
+    @property
+    def n_steps(self):
+        return int(round(self.TE / self.dt))
+
+
+def cfg1(n: int = 24, dt: float = 50.0):
+    L = 40.0
+    lo, hi = np.full(3, -L / 2), np.full(3, L / 2)
+    xyz, tets = kuhn_grid(n, n, n, lo, hi)
+    return Problem("cfg1", xyz, tets, np.zeros(len(tets), np.int32), np.array([2e-3]),
+                   np.array([NO_MEMBRANE]), 0, lo, hi, dt, 2500.0, 5000.0, 7500.0,
+                   np.array([[1.0, 0.0, 0.0]]), np.array([1000.0]))
+
+
+def cfg2(n: int = 48, dt: float = 50.0, bvals=(0.0, 500.0, 1000.0, 2000.0, 3000.0),
+         kappa: float = 1e-5):
+    L = 20.0
+    lo, hi = np.full(3, -L / 2), np.full(3, L / 2)
+    xyz, tets = kuhn_grid(n, n, n, lo, hi)
+    lab = label_sphere(xyz, tets, np.zeros(3), 5.0)
+    return Problem("cfg2", xyz, tets, lab, np.array([2e-3, 2e-3]),
+                   np.array([NO_MEMBRANE, kappa]), 0, lo, hi, dt, 2500.0, 5000.0, 7500.0,
+                   np.array([[1.0, 0.0, 0.0]]), np.asarray(bvals, dtype=np.float64))
+
+
+def cfg3(n: int = 64, dt: float = 50.0, n_dir: int = 64, n_b: int = 8, seed: int = 0):
+    L = 30.0
+    lo, hi = np.zeros(3), np.full(3, L)
+    cen, rad, used = place_cylinders_periodic(40, L, 2.0, 0.3, seed)
+    xyz, tets = kuhn_grid(n, n, n, lo, hi)
+    lab = label_cylinders_periodic(xyz, tets, cen, rad, L)
+    nc = len(rad) + 1
+    D = np.full(nc, 2e-3)
+    kap = np.full(nc, 5e-5)
+    kap[0] = NO_MEMBRANE
+    return Problem("cfg3", xyz, tets, lab, D, kap, 7, lo, hi, dt, 2500.0, 5000.0, 7500.0,
+                   fibonacci_dirs(n_dir), np.linspace(0.0, 3000.0, n_b), transformed=True,
+                   meta={"cyl_centres": cen, "cyl_radii": rad, "seed_used": used})
+
+
+def cfg4(n: int = 96, dt: float = 50.0, n_dir: int = 32, bvals=(500.0, 1000.0, 2000.0, 3000.0),
+         seed: int = 0, n_obj: int = 200):
+    L = 40.0
+    lo, hi = np.zeros(3), np.full(3, L)
+    h_ref = L / 96.0
+    objs = place_objects(n_obj, L, 1.0, 4.0, h_ref, seed)
+    xyz, tets = kuhn_grid(n, n, n, lo, hi)
+    lab = label_objects(xyz, tets, objs, L / n, n, lo)
+    rng = np.random.default_rng(seed + 1)
+    nc = len(objs) + 1
+    kap = np.concatenate([[NO_MEMBRANE], rng.uniform(1e-5, 1e-4, nc - 1)])
+    D = np.full(nc, 2e-3)
+    return Problem("cfg4", xyz, tets, lab, D, kap, 0, lo, hi, dt, 2500.0, 5000.0, 7500.0,
+                   fibonacci_dirs(n_dir), np.asarray(bvals, dtype=np.float64),
+                   meta={"objects": objs, "n_placed": len(objs)})
+
+
+def cfg5_geometry(g: int, dt: float = 50.0, n_dir: int = 16,
+                  bvals=(500.0, 1000.0, 2000.0, 3000.0), scale: float = 1.0):
+    """Geometry g (0..31) of the uneven batch.  Node count n ~ log-uniform
+    [50k, 2M]; grid N = round(n^(1/3)) - 1 (times `scale` for reduced copies);
+    box side N * 40/96 um (the cfg4 cell size); objects as in cfg4 with a count
+    proportional to the box volume; PGSE delta ~ U(2, 10) ms,
+    Delta ~ U(max(delta, 5), 40) ms, both rounded to dt."""
+    rng = np.random.default_rng(5000 + g)
+    nn = math.exp(rng.uniform(math.log(5e4), math.log(2e6)))
+    N = int(round(nn ** (1.0 / 3.0))) - 1
+    L = N * 40.0 / 96.0
+    n_obj = max(1, int(round(200 * (L / 40.0) ** 3)))
+    objs = place_objects(n_obj, L, 1.0, 4.0, 40.0 / 96.0, 5000 + g)
+    delta = rng.uniform(2000.0, 10000.0)
+    Delta = rng.uniform(max(delta, 5000.0), 40000.0)
+    delta = max(dt, round(delta / dt) * dt)
+    Delta = max(delta, round(Delta / dt) * dt)
+    Ng = max(2, int(round(N * scale)))
+    lo, hi = np.zeros(3), np.full(3, L)
+    xyz, tets = kuhn_grid(Ng, Ng, Ng, lo, hi)
+    lab = label_objects(xyz, tets, objs, L / Ng, Ng, lo)
+    nc = len(objs) + 1
+    kap = np.concatenate([[NO_MEMBRANE], rng.uniform(1e-5, 1e-4, nc - 1)])
+    D = np.full(nc, 2e-3)
+    return Problem(f"cfg5_g{g}", xyz, tets, lab, D, kap, 0, lo, hi, dt, delta, Delta,
+                   Delta + delta, fibonacci_dirs(n_dir), np.asarray(bvals, dtype=np.float64),
+                   meta={"N": N, "n_placed": len(objs)})
+
+
+def free_periodic_box(n: int = 8, L: float = 10.0, dt: float = 50.0, D: float = 2e-3,
+                      dirs=((1.0, 0.0, 0.0),), bvals=(1000.0,)):
+    """Periodic box without compartments (free diffusion)."""
+    lo, hi = np.zeros(3), np.full(3, L)
+    xyz, tets = kuhn_grid(n, n, n, lo, hi)
+    return Problem("free_periodic", xyz, tets, np.zeros(len(tets), np.int32), np.array([D]),
+                   np.array([NO_MEMBRANE]), 7, lo, hi, dt, 2500.0, 5000.0, 7500.0,
+                   np.asarray(dirs, dtype=np.float64), np.asarray(bvals, dtype=np.float64),
+                   transformed=True)
+
+
+def slab_1d(nx: int, L: float = 40.0, w: float = 1.0, dt: float = 50.0, D: float = 2e-3,
+            b: float = 1000.0, delta: float = 2500.0, Delta: float = 5000.0):
+    """[-L/2, L/2] x [0, w] x [0, w] Neumann box with nx x 1 x 1 Kuhn cells and
+    the gradient along x: the continuum signal equals that of the 1-D interval."""
+    lo = np.array([-L / 2, 0.0, 0.0])
+    hi = np.array([L / 2, w, w])
+    xyz, tets = kuhn_grid(nx, 1, 1, lo, hi)
+    return Problem("slab1d", xyz, tets, np.zeros(len(tets), np.int32), np.array([D]),
+                   np.array([NO_MEMBRANE]), 0, lo, hi, dt, delta, Delta, Delta + delta,
+                   np.array([[1.0, 0.0, 0.0]]), np.array([b]))

@@ -1,0 +1,326 @@
+"""Plain, slow FP64 CPU finite-element solve of the multi-compartment
+Bloch-Torrey equation (test infrastructure only; see the package docstring).
+
+What it follows (section / equation of arXiv 1908.01719):
+  * model: Bloch-Torrey PDE (Eq. strong_BT, Section 2) with T2 = infinity, the
+    permeable interface conditions (Eq. btpde_ic), PGSE profile (Eq. pgse),
+    signal S = integral of U at TE (Eq. signal), b-value (Eq. b_value);
+  * PUFEM interface treatment (Appendix A): one nodal copy per compartment on
+    interface nodes, with the jump term kappa <[u], [v]> on interface faces;
+  * theta-method in time and the matrix form A U^n = F (Appendix B,
+    Eqs. theta_discretization2, linear_billinear2, matrix_form);
+  * strong pseudo-periodic conditions through the gauge transform
+    u = U exp(i gamma F(t) g.x) (Appendix A, Eqs. trBlo, Periodic,
+    Binterface2 and the weak form F(u, v, t)).
+
+Readings where the paper leaves a choice (each is also listed in the design
+notes of the repository):
+  * f(t) enters each theta step as its average over the step, f_bar_n, on both
+    sides of the step (the paper evaluates f at t^n and t^{n-1}, which is
+    ambiguous where the PGSE profile jumps exactly at a grid time);
+  * the first-moment matrices use coordinates relative to the box centre;
+  * a face between compartments a and b has permeability
+    1/(1/kappa_a + 1/kappa_b) (an infinite kappa means "no membrane");
+  * consistent mass, exact integration;
+  * in the transformed frame the interface and Neumann terms combine with the
+    volume term into E_k = C_k - C_k^T, C_k[i, j] = D * integral(phi_i d_k phi_j),
+    so the step operator is K + J + D q^2 F^2 M + i q F sum_k qhat_k E_k.
+
+Every linear solve is a sparse direct LU (scipy.sparse.linalg.splu), one
+factorisation per distinct step matrix.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+# --------------------------------------------------------------------------
+# Periodic identification and interface-node doubling (PUFEM, Appendix A)
+# --------------------------------------------------------------------------
+def periodic_master(xyz, periodic_mask, lo, hi):
+    """Map every node to its master node: on a periodic axis k, a node with
+    x_k = hi_k is the same unknown as the node with x_k = lo_k and equal other
+    coordinates (master-slave periodicity, Section 2, Eq. btpde_bc)."""
+    n = len(xyz)
+    if periodic_mask == 0:
+        return np.arange(n)
+    lo = np.asarray(lo, float)
+    hi = np.asarray(hi, float)
+    tol = 1e-9 * float(np.max(hi - lo))
+    canon = xyz.copy()
+    for k in range(3):
+        if periodic_mask >> k & 1:
+            on_hi = np.abs(canon[:, k] - hi[k]) < tol
+            canon[on_hi, k] = lo[k]
+    key = np.round(canon / tol).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    # master = smallest node index among identified nodes
+    grp_min = np.full(len(first), n, dtype=np.int64)
+    np.minimum.at(grp_min, inv.ravel(), np.arange(n))
+    return grp_min[inv.ravel()]
+
+
+def doubling(master, tets, tet_cmpt, n_cmpt):
+    """One degree of freedom per (master node, compartment) pair that occurs in
+    some tetrahedron of that compartment.  Dofs are numbered in increasing
+    (node, compartment) order."""
+    keys = master[tets].astype(np.int64) * n_cmpt + tet_cmpt[:, None].astype(np.int64)
+    uniq, inv = np.unique(keys.ravel(), return_inverse=True)
+    tet_dof = inv.reshape(-1, 4)
+    return tet_dof, uniq // n_cmpt, uniq % n_cmpt
+
+
+def interface_faces(master, tets, tet_cmpt):
+    """Faces shared by two tetrahedra of different compartments.
+
+    Returns (tet_a, tet_b, verts [nf,3] master ids, local vertex indices of the
+    face in tet_a [nf,3]).  Face keys use master ids, so faces identified by
+    periodicity are found too."""
+    loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    mt = master[tets]
+    fv = mt[:, loc]                                # [nt, 4, 3]
+    fv_sorted = np.sort(fv, axis=2).reshape(-1, 3)
+    owner = np.repeat(np.arange(len(tets)), 4)
+    lface = np.tile(np.arange(4), len(tets))
+    order = np.lexsort((fv_sorted[:, 2], fv_sorted[:, 1], fv_sorted[:, 0]))
+    fs = fv_sorted[order]
+    same = np.all(fs[1:] == fs[:-1], axis=1)
+    i0 = np.flatnonzero(same)
+    ta, tb = owner[order][i0], owner[order][i0 + 1]
+    la = lface[order][i0]
+    diff = tet_cmpt[ta] != tet_cmpt[tb]
+    ta, tb, la = ta[diff], tb[diff], la[diff]
+    return ta, tb, loc[la]
+
+
+# --------------------------------------------------------------------------
+# Element matrices (P1 tetrahedra, exact integration)
+# --------------------------------------------------------------------------
+def _cubic_moments():
+    """c[i,j,l] = (1/|T|) * integral over T of lambda_i lambda_j lambda_l, from
+    the barycentric integration formula alpha! 3! / (|alpha| + 3)!."""
+    c = np.empty((4, 4, 4))
+    for i in range(4):
+        for j in range(4):
+            for l in range(4):
+                a = np.bincount([i, j, l], minlength=4)
+                num = np.prod([math.factorial(x) for x in a]) * math.factorial(3)
+                c[i, j, l] = num / math.factorial(3 + 3)
+    return c
+
+
+def tet_geometry(X):
+    """Volumes [nt] and barycentric gradients [nt, 4, 3] of tetrahedra X [nt,4,3]."""
+    E = X[:, 1:, :] - X[:, :1, :]                 # rows: edge vectors
+    vol = np.linalg.det(E) / 6.0
+    Ginv = np.linalg.inv(E)                        # columns: grad lambda_{1..3}
+    G = np.empty((len(X), 4, 3))
+    G[:, 1:, :] = np.transpose(Ginv, (0, 2, 1))
+    G[:, 0, :] = -G[:, 1:, :].sum(axis=1)
+    return vol, G
+
+
+def _coo(rows, cols, vals, n):
+    return sp.coo_matrix((vals.ravel(), (rows.ravel(), cols.ravel())), shape=(n, n)).tocsr()
+
+
+def assemble(p):
+    """Assemble every matrix of the method for problem `p` (a geom.Problem).
+
+    Returns a dict with the dof map and the CSR matrices
+      M   mass                              (Appendix B, matrix M)
+      K   stiffness, D-weighted             (Appendix B, matrix S)
+      J   interface jump, kappa-weighted    (Appendix B, matrix I)
+      Mx, My, Mz  first-moment mass         (Appendix B, matrix J = sum g_k M_k)
+      MD  D-weighted mass                   (transformed frame, Appendix A)
+      Ex, Ey, Ez  skew transport matrices   (transformed frame, Appendix A)
+    """
+    master = periodic_master(p.xyz, p.periodic_mask, p.box_lo, p.box_hi)
+    tet_dof, dof_node, dof_cmpt = doubling(master, p.tets, p.tet_cmpt, p.n_cmpt)
+    n = len(dof_node)
+    X = p.xyz[p.tets]                              # unwrapped element coordinates
+    vol, G = tet_geometry(X)
+    Dt = p.D_cmpt[p.tet_cmpt]
+    rows = np.repeat(tet_dof[:, :, None], 4, axis=2)
+    cols = np.repeat(tet_dof[:, None, :], 4, axis=1)
+
+    eye = np.eye(4)
+    Me = vol[:, None, None] / 20.0 * (1.0 + eye)[None]
+    Ke = (Dt * vol)[:, None, None] * np.einsum("tik,tjk->tij", G, G)
+    centre = 0.5 * (np.asarray(p.box_lo, float) + np.asarray(p.box_hi, float))
+    Xc = X - centre
+    c3 = _cubic_moments()
+    out = {"n": n, "tet_dof": tet_dof, "dof_node": dof_node, "dof_cmpt": dof_cmpt,
+           "master": master}
+    out["M"] = _coo(rows, cols, Me, n)
+    out["K"] = _coo(rows, cols, Ke, n)
+    out["MD"] = _coo(rows, cols, Dt[:, None, None] * Me, n)
+    for k, nm in enumerate("xyz"):
+        Mk = vol[:, None, None] * np.einsum("ijl,tl->tij", c3, Xc[:, :, k])
+        out["M" + nm] = _coo(rows, cols, Mk, n)
+        Ck = (Dt * vol / 4.0)[:, None, None] * np.broadcast_to(G[:, None, :, k], (len(vol), 4, 4))
+        out["E" + nm] = _coo(rows, cols, Ck - np.transpose(Ck, (0, 2, 1)), n)
+
+    # interface jump term kappa <[u], [v]> on faces between compartments
+    ta, tb, lv = interface_faces(master, p.tets, p.tet_cmpt)
+    nf = len(ta)
+    if nf:
+        va = p.tets[ta[:, None], lv]                    # global vertices of face (tet a)
+        Xa = p.xyz[va]
+        area = 0.5 * np.linalg.norm(np.cross(Xa[:, 1] - Xa[:, 0], Xa[:, 2] - Xa[:, 0]), axis=1)
+        ka = p.kappa_cmpt[p.tet_cmpt[ta]]
+        kb = p.kappa_cmpt[p.tet_cmpt[tb]]
+        with np.errstate(divide="ignore"):
+            kap = 1.0 / (1.0 / ka + 1.0 / kb)
+        dof_a = tet_dof[ta[:, None], lv]
+        # matching vertex on side b, by master id
+        mb = master[p.tets[tb]]
+        ma = master[va]
+        lb = np.argmax(mb[:, None, :] == ma[:, :, None], axis=2)
+        dof_b = tet_dof[tb[:, None], lb]
+        Fm = (area * kap)[:, None, None] / 12.0 * (1.0 + np.eye(3))[None]
+        d6 = np.concatenate([dof_a, dof_b], axis=1)
+        blk = np.block([[np.ones((3, 3)), -np.ones((3, 3))], [-np.ones((3, 3)), np.ones((3, 3))]])
+        F6 = np.tile(Fm, (1, 2, 2)) * blk[None]
+        r6 = np.repeat(d6[:, :, None], 6, axis=2)
+        c6 = np.repeat(d6[:, None, :], 6, axis=1)
+        out["J"] = _coo(r6, c6, F6, n)
+    else:
+        out["J"] = sp.csr_matrix((n, n))
+    out["n_iface"] = nf
+    out["volume"] = float(vol.sum())
+    return out
+
+
+def signal_weights(asm):
+    """w = M 1: the exact integral of each P1 basis function (Eq. signal)."""
+    return asm["M"] @ np.ones(asm["n"])
+
+
+# --------------------------------------------------------------------------
+# Sequence (Eq. pgse, Eq. b_value)
+# --------------------------------------------------------------------------
+def pgse_f(t, delta, Delta):
+    t = np.asarray(t, float)
+    return np.where((t >= 0) & (t <= delta), 1.0, np.where((t > Delta) & (t <= Delta + delta), -1.0, 0.0))
+
+
+def pgse_F(t, delta, Delta):
+    """F(t) = integral_0^t f(s) ds for the PGSE profile."""
+    t = np.asarray(t, float)
+    return np.clip(t, 0.0, delta) - np.clip(t - Delta, 0.0, delta)
+
+
+def pgse_tables(delta, Delta, dt, n_steps):
+    """f_bar[n] (n = 1..N, index n-1) = step average of f over (t_{n-1}, t_n];
+    F[n] (n = 0..N) = F(t_n)."""
+    t = dt * np.arange(n_steps + 1)
+    F = pgse_F(t, delta, Delta)
+    fbar = np.diff(F) / dt
+    return fbar, F
+
+
+def q_from_b(b, delta, Delta):
+    """q = gamma |g| from b = q^2 delta^2 (Delta - delta/3) (Eq. b_value with the
+    PGSE F(t))."""
+    return np.sqrt(np.asarray(b, float) / (delta * delta * (Delta - delta / 3.0)))
+
+
+# --------------------------------------------------------------------------
+# Time stepping (theta-method, Appendix B matrix form)
+# --------------------------------------------------------------------------
+class _LUCache:
+    def __init__(self):
+        self.cache = {}
+
+    def get(self, key, build):
+        lu = self.cache.get(key)
+        if lu is None:
+            lu = spla.splu(build().tocsc())
+            self.cache[key] = lu
+        return lu
+
+
+def run_lab(p, asm=None, rhs=None, return_history=False):
+    """Lab frame (Neumann outer boundary):
+        L_n = M + theta dt (K + J + i q f_bar_n Mq)
+        R_n = M - (1 - theta) dt (K + J + i q f_bar_n Mq),  Mq = sum_k qhat_k M_k
+        L_n u^n = R_n u^{n-1},  u^0 = 1,  S = (M 1)^T u^N."""
+    if asm is None:
+        asm = assemble(p)
+    if p.periodic_mask:
+        raise ValueError("periodic boxes need the transformed frame")
+    M, KJ = asm["M"], asm["K"] + asm["J"]
+    w = signal_weights(asm)
+    N = p.n_steps
+    fbar, _ = pgse_tables(p.delta, p.Delta, p.dt, N)
+    nb = len(p.bvals)
+    rhs = range(p.n_rhs) if rhs is None else rhs
+    th, dt = p.theta, p.dt
+    out, hist = [], []
+    for r in rhs:
+        qh = p.dirs[r // nb]
+        q = float(q_from_b(p.bvals[r % nb], p.delta, p.Delta))
+        Mq = qh[0] * asm["Mx"] + qh[1] * asm["My"] + qh[2] * asm["Mz"]
+        lus = _LUCache()
+        u = np.ones(asm["n"], dtype=np.complex128)
+        h = [w @ u]
+        for n in range(1, N + 1):
+            fb = fbar[n - 1]
+            A = KJ + (1j * q * fb) * Mq
+            lu = lus.get(fb, lambda: (M + th * dt * A).astype(np.complex128))
+            u = lu.solve((M - (1.0 - th) * dt * A) @ u)
+            h.append(w @ u)
+        out.append(w @ u)
+        hist.append(h)
+    out = np.array(out)
+    return (out, np.array(hist)) if return_history else out
+
+
+def run_transformed(p, asm=None, rhs=None, return_history=False):
+    """Gauge-transformed frame u = U exp(i q F(t) qhat.x) (Appendix A), valid
+    for periodic and Neumann outer boundaries:
+        A(F) = K + J + q^2 F^2 MD + i q F Eq,  Eq = sum_k qhat_k E_k
+        L_n = M + theta dt A(F_n),  R_n = M - (1 - theta) dt A(F_{n-1})
+        S = (M 1)^T u^N  (F(TE) = 0 for PGSE, so U = u at TE)."""
+    if asm is None:
+        asm = assemble(p)
+    M, KJ, MD = asm["M"], asm["K"] + asm["J"], asm["MD"]
+    w = signal_weights(asm)
+    N = p.n_steps
+    _, F = pgse_tables(p.delta, p.Delta, p.dt, N)
+    if abs(F[-1]) > 1e-12 * max(1.0, p.delta):
+        raise ValueError("F(TE) != 0: the signal needs the phase factor")
+    nb = len(p.bvals)
+    rhs = range(p.n_rhs) if rhs is None else rhs
+    th, dt = p.theta, p.dt
+    out, hist = [], []
+    for r in rhs:
+        qh = p.dirs[r // nb]
+        q = float(q_from_b(p.bvals[r % nb], p.delta, p.Delta))
+        Eq = qh[0] * asm["Ex"] + qh[1] * asm["Ey"] + qh[2] * asm["Ez"]
+
+        def A(Fv):
+            return KJ + (q * q * Fv * Fv) * MD + (1j * q * Fv) * Eq
+
+        lus = _LUCache()
+        u = np.ones(asm["n"], dtype=np.complex128)
+        h = [w @ u]
+        for n in range(1, N + 1):
+            Fn, Fp = F[n], F[n - 1]
+            lu = lus.get(Fn, lambda: (M + th * dt * A(Fn)).astype(np.complex128))
+            u = lu.solve((M - (1.0 - th) * dt * A(Fp)) @ u)
+            h.append(w @ u)
+        out.append(w @ u)
+        hist.append(h)
+    out = np.array(out)
+    return (out, np.array(hist)) if return_history else out
+
+
+def run(p, asm=None, rhs=None, return_history=False):
+    f = run_transformed if (p.transformed or p.periodic_mask) else run_lab
+    return f(p, asm, rhs, return_history)

@@ -1,0 +1,326 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics,
+not by the oracle itself: exact integrals, conservation, symmetries, exact
+discrete closed forms, brute force on tiny meshes, limits and convergence
+orders.  (CPU only.)"""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+import geom
+import oracle
+from oracle import btoracle as bo
+from oracle import mf1d
+
+
+# ---------------------------------------------------------------- elements
+def test_cubic_moments_exact_rationals():
+    """integral over the reference tetrahedron of lambda_i lambda_j lambda_l,
+    integrated symbolically, equals |T| * c[i,j,l]."""
+    sympy = pytest.importorskip("sympy")
+    x, y, z = sympy.symbols("x y z")
+    lam = [1 - x - y - z, x, y, z]
+    c = bo._cubic_moments()
+    for i, j, l in [(0, 0, 0), (1, 1, 2), (0, 2, 3), (3, 3, 1), (2, 2, 2)]:
+        e = lam[i] * lam[j] * lam[l]
+        val = sympy.integrate(e, (z, 0, 1 - x - y), (y, 0, 1 - x), (x, 0, 1))
+        assert abs(float(val) - c[i, j, l] / 6.0) < 1e-15
+
+
+def test_tet_geometry_reproduces_linear_functions():
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(20, 4, 3))
+    X[:, 3] += 3.0
+    vol, G = bo.tet_geometry(X)
+    # volume by the scalar triple product
+    e = X[:, 1:] - X[:, :1]
+    v2 = np.einsum("ti,ti->t", np.cross(e[:, 0], e[:, 1]), e[:, 2]) / 6.0
+    assert np.allclose(vol, v2, rtol=1e-13)
+    # gradient of the P1 interpolant of a linear function is exact
+    a = rng.normal(size=3)
+    f = X @ a + 0.7
+    grad = np.einsum("ti,tik->tk", f, G)
+    assert np.allclose(grad, a[None, :], atol=1e-12)
+
+
+def _quad4():
+    a, b = 0.5854101966249685, 0.1381966011250105
+    return np.array([[a, b, b, b], [b, a, b, b], [b, b, a, b], [b, b, b, a]])
+
+
+def test_transformed_form_equals_gauge_energy():
+    """u^H (K + q^2F^2 MD + i q F Eq) u = sum_T D_T int_T |grad u - i qF qhat u|^2,
+    evaluated with a 4-point rule that is exact for quadratics."""
+    p = geom.cfg2(n=4)
+    p.D_cmpt = np.array([2e-3, 1.3e-3])
+    a = bo.assemble(p)
+    rng = np.random.default_rng(1)
+    u = rng.normal(size=a["n"]) + 1j * rng.normal(size=a["n"])
+    qh = np.array([0.3, -0.5, 0.81]); qh /= np.linalg.norm(qh)
+    qF = 0.37
+    Eq = qh[0] * a["Ex"] + qh[1] * a["Ey"] + qh[2] * a["Ez"]
+    A = a["K"] + qF * qF * a["MD"] + 1j * qF * Eq
+    lhs = np.vdot(u, A @ u)
+    X = p.xyz[p.tets]
+    vol, G = bo.tet_geometry(X)
+    ue = u[a["tet_dof"]]                       # [nt, 4]
+    g = np.einsum("ti,tik->tk", ue, G)         # constant gradient per tet
+    B = _quad4()
+    uq = ue @ B.T                              # values at the 4 points
+    Dt = p.D_cmpt[p.tet_cmpt]
+    v = g[:, None, :] - 1j * qF * qh[None, None, :] * uq[:, :, None]
+    rhs = np.sum(Dt * vol * 0.25 * np.sum(np.abs(v) ** 2, axis=(1, 2)))
+    assert abs(lhs.imag) < 1e-12 * abs(rhs)
+    assert abs(lhs.real - rhs) < 1e-12 * abs(rhs)
+
+
+# ---------------------------------------------------------------- assembly
+@pytest.fixture(scope="module")
+def sphere_small():
+    p = geom.cfg2(n=8, kappa=3e-3)
+    return p, bo.assemble(p)
+
+
+def test_assembly_identities(sphere_small):
+    p, a = sphere_small
+    one = np.ones(a["n"])
+    L = 20.0
+    assert abs(one @ a["M"] @ one - L ** 3) < 1e-12 * L ** 3
+    assert abs(oracle.signal_weights(a).sum() - L ** 3) < 1e-12 * L ** 3
+    for nm in ["K", "J"]:
+        assert np.abs(a[nm] @ one).max() < 1e-14 * abs(a[nm]).max() * 20
+    for nm in ["M", "K", "J", "Mx", "My", "Mz", "MD"]:
+        d = a[nm] - a[nm].T
+        assert abs(d).max() <= 1e-15 * max(1.0, abs(a[nm]).max())
+    for nm in ["Ex", "Ey", "Ez"]:
+        d = a[nm] + a[nm].T
+        assert abs(d).max() <= 1e-15 * max(1.0, abs(a[nm]).max())
+    # first moments: 1^T M_k 1 = integral of (x_k - centre_k) = 0 for the centred cube
+    X = p.xyz[p.tets]
+    vol, _ = bo.tet_geometry(X)
+    for k, nm in enumerate("xyz"):
+        exact = np.sum(vol * (X[:, :, k].mean(axis=1) - 0.0))
+        assert abs(one @ a["M" + nm] @ one - exact) < 1e-11
+    # D-weighted mass: 1^T MD 1 = sum_c D_c |Omega_c|
+    Dv = np.sum(p.D_cmpt[p.tet_cmpt] * vol)
+    assert abs(one @ a["MD"] @ one - Dv) < 1e-12 * Dv
+
+
+def test_first_moment_off_centre():
+    """Mesh shifted by s inside a box centred at 0: 1^T M_k 1 = |Omega| s_k."""
+    p = geom.cfg1(n=3)
+    s = np.array([5.0, -2.0, 1.0])
+    p.xyz = p.xyz + s
+    a = bo.assemble(p)
+    one = np.ones(a["n"])
+    for k, nm in enumerate("xyz"):
+        assert abs(one @ a["M" + nm] @ one - 64000.0 * s[k]) < 1e-9 * 64000.0
+
+
+def test_interface_area_brute_force():
+    """1_0^T J 1_0 = sum over interface faces of kappa |F|; the faces are found
+    here by brute force over all tetrahedron pairs of a tiny mesh."""
+    p = geom.cfg2(n=4, kappa=2e-3)
+    a = bo.assemble(p)
+    side0 = (a["dof_cmpt"] == 0).astype(float)
+    lhs = side0 @ a["J"] @ side0
+    faces = {}
+    for t, tet in enumerate(p.tets):
+        for drop in range(4):
+            key = tuple(sorted(np.delete(tet, drop)))
+            faces.setdefault(key, []).append(t)
+    area = 0.0
+    for key, ts in faces.items():
+        if len(ts) == 2 and p.tet_cmpt[ts[0]] != p.tet_cmpt[ts[1]]:
+            X = p.xyz[list(key)]
+            area += 0.5 * np.linalg.norm(np.cross(X[1] - X[0], X[2] - X[0]))
+    kap = 1.0 / (1.0 / math.inf + 1.0 / 2e-3)
+    assert area > 0
+    assert abs(lhs - kap * area) < 1e-13 * kap * area
+
+
+def test_periodic_identification_and_skew_annihilates_constants():
+    p = geom.free_periodic_box(n=4, L=6.0)
+    a = bo.assemble(p)
+    assert a["n"] == 4 ** 3
+    one = np.ones(a["n"])
+    for nm in ["Ex", "Ey", "Ez", "K"]:
+        assert np.abs(a[nm] @ one).max() < 1e-15
+    assert abs(one @ a["M"] @ one - 216.0) < 1e-12
+
+
+# ---------------------------------------------------------------- sequence
+def test_pgse_tables_and_b_value():
+    delta, Delta, dt = 2500.0, 5000.0, 50.0
+    N = 150
+    fbar, F = oracle.pgse_tables(delta, Delta, dt, N)
+    assert set(np.unique(fbar)) == {-1.0, 0.0, 1.0}
+    assert np.sum(fbar == 1) == 50 and np.sum(fbar == -1) == 50
+    assert abs(F[-1]) < 1e-12 and abs(F[50] - delta) < 1e-12
+    # b = q^2 int_0^TE F^2 by fine quadrature of the profile (Eq. b_value)
+    t = np.linspace(0, 7500.0, 750001)
+    Ft = bo.pgse_F(t, delta, Delta)
+    intF2 = np.trapezoid(Ft ** 2, t)
+    q = oracle.q_from_b(1000.0, delta, Delta)
+    assert abs(q * q * intF2 - 1000.0) < 1e-6 * 1000.0
+    assert abs(q - 1.95959e-4) < 1e-9
+
+
+# ---------------------------------------------------------------- matrix formalism
+def test_mf_moment_matrix_closed_form():
+    L = 7.0
+    X = mf1d.moment_matrix(L, 12)
+    xg, wg = np.polynomial.legendre.leggauss(200)
+    x = xg * L / 2
+    wx = wg * L / 2
+    m = np.arange(12)
+    phi = np.where(m[:, None] == 0, 1 / np.sqrt(L), np.sqrt(2 / L) * np.cos(m[:, None] * np.pi * (x[None] + L / 2) / L))
+    Xq = (phi * x[None] * wx[None]) @ phi.T
+    assert np.abs(X - Xq).max() < 1e-12
+
+
+def test_mf_limits():
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+    # no diffusion: the phase refocuses at TE
+    assert abs(oracle.mf_interval_signal(40.0, 0.0, q, 2500.0, 5000.0, 200) - 1.0) < 1e-10
+    # no gradient
+    assert abs(oracle.mf_interval_signal(40.0, 2e-3, 0.0, 2500.0, 5000.0, 50) - 1.0) < 1e-12
+    # the published worked value and the approach to exp(-bD) in wide intervals:
+    s40 = oracle.mf_interval_signal(40.0, 2e-3, q, 2500.0, 5000.0, 400).real
+    assert abs(s40 - 0.1997576) < 2e-7
+    gaps = []
+    for L in [80.0, 160.0, 320.0]:
+        s = oracle.mf_interval_signal(L, 2e-3, q, 2500.0, 5000.0, int(L * 6)).real
+        gaps.append(s / math.exp(-2.0) - 1.0)
+    assert 0.45 < gaps[1] / gaps[0] < 0.55 and 0.45 < gaps[2] / gaps[1] < 0.55
+
+
+# ---------------------------------------------------------------- stepping pins
+def test_conservation_without_gradient():
+    """g = 0, Neumann, permeable interface: 1^T M u^n = |Omega| for all n (P-2)."""
+    p = geom.cfg2(n=6, kappa=1e-3, bvals=(0.0,))
+    p.TE = 1000.0
+    S, h = oracle.run(p, return_history=True)
+    assert np.abs(h - 8000.0).max() < 1e-11 * 8000.0
+
+
+def test_conjugate_symmetry_and_real_echo():
+    """S(t_n; -g) = conj(S(t_n; g)) at every step (real data), and for the
+    symmetric PGSE pair the echo signal at TE is real: the product of the
+    complex-symmetric step operators is palindromic up to conjugation (P-3)."""
+    p = geom.cfg2(n=5, kappa=1e-4, bvals=(3000.0,))
+    p.D_cmpt = np.array([2e-3, 1e-3])
+    p.dirs = np.array([[0.6, 0.8, 0.0], [-0.6, -0.8, 0.0]])
+    p.tet_cmpt = geom.label_sphere(p.xyz, p.tets, np.array([2.0, -1.0, 0.5]), 5.0)
+    S, h = oracle.run(p, return_history=True)
+    assert np.abs(h[0] - np.conj(h[1])).max() < 1e-12 * abs(h[0, 0])
+    assert np.abs(h[0].imag).max() > 1e-4 * abs(h[0, 0])     # genuinely complex midway
+    assert abs(S[0].imag) < 1e-12 * abs(S[0])
+
+
+def test_phase_sign_without_diffusion():
+    """D = 0: U(x, t) = exp(-i q F(t) qhat.x) (Eq. strong_BT).  The discrete
+    solution refocuses exactly at TE, and at t = delta the nodal phase follows
+    -q F x."""
+    p = geom.cfg1(n=12)
+    p.D_cmpt = np.array([0.0])
+    p.bvals = np.array([50.0])
+    a = bo.assemble(p)
+    S, h = oracle.run_lab(p, a, return_history=True)
+    assert abs(h[0, -1] - 64000.0) < 1e-10 * 64000.0
+    import scipy.sparse.linalg as spla
+    q = float(oracle.q_from_b(50.0, p.delta, p.Delta))
+    _, F = oracle.pgse_tables(p.delta, p.Delta, p.dt, p.n_steps)
+    L = (a["M"] + 0.5 * p.dt * 1j * q * a["Mx"]).tocsc()
+    R = a["M"] - 0.5 * p.dt * 1j * q * a["Mx"]
+    lu = spla.splu(L)
+    u = np.ones(a["n"], complex)
+    for n in range(50):
+        u = lu.solve(R @ u)
+    x = p.xyz[a["dof_node"], 0]
+    err = np.abs(np.angle(u * np.exp(1j * q * F[50] * x)))
+    assert q * F[50] * 20.0 > 1.0 and err.max() < 0.05, err.max()
+
+
+def test_free_periodic_exact_discrete_closed_form():
+    """Periodic box, no compartments, transformed frame: u stays spatially
+    constant and S/|Omega| = prod_n (1 - (1-th) dt D q^2 F_{n-1}^2) /
+    (1 + th dt D q^2 F_n^2) exactly, which tends to exp(-bD) (P-5)."""
+    p = geom.free_periodic_box(n=5, L=8.0, dirs=((0.3, 0.4, np.sqrt(0.75)),), bvals=(2000.0,))
+    S = oracle.run(p)[0] / 512.0
+    q = float(oracle.q_from_b(2000.0, p.delta, p.Delta))
+    _, F = oracle.pgse_tables(p.delta, p.Delta, p.dt, p.n_steps)
+    D, th, dt = 2e-3, 0.5, p.dt
+    prod = np.prod((1 - (1 - th) * dt * D * q * q * F[:-1] ** 2) / (1 + th * dt * D * q * q * F[1:] ** 2))
+    assert abs(S - prod) < 1e-13
+    assert abs(prod - math.exp(-2000.0 * D)) < 2e-3 * math.exp(-4.0)
+
+
+def test_kappa_zero_separates():
+    """kappa = 0: the two-compartment signal is the sum of separate runs on the
+    inside-only and outside-only meshes (P-6)."""
+    p = geom.cfg2(n=6, kappa=0.0, bvals=(1500.0,))
+    p.kappa_cmpt = np.array([math.inf, 0.0])
+    S = oracle.run(p)[0]
+    parts = 0.0
+    for c in (0, 1):
+        q = copy.copy(p)
+        keep = p.tet_cmpt == c
+        q.tets = p.tets[keep]
+        q.tet_cmpt = p.tet_cmpt[keep]
+        parts += oracle.run(q)[0]
+    assert abs(S - parts) < 1e-12 * abs(S)
+
+
+def test_large_kappa_limit_is_first_order():
+    """Large kappa: difference from the undoubled single-compartment run on the
+    same mesh decays like 1/kappa (P-7)."""
+    base = geom.cfg2(n=6, bvals=(2000.0,))
+    one = copy.copy(base)
+    one.tet_cmpt = np.zeros_like(base.tet_cmpt)
+    one.D_cmpt = base.D_cmpt[:1]
+    one.kappa_cmpt = base.kappa_cmpt[:1]
+    S1 = oracle.run(one)[0]
+    errs = []
+    for k in [1e-2, 1e-1, 1.0]:
+        q = copy.copy(base)
+        q.kappa_cmpt = np.array([math.inf, k])
+        errs.append(abs(oracle.run(q)[0] - S1))
+    slopes = np.diff(np.log10(errs))
+    assert np.all(np.abs(slopes + 1.0) < 0.1), slopes
+
+
+def test_axis_permutation_symmetry():
+    """A centred sphere on the Kuhn grid: S(x) = S(y) = S(z) (P-8)."""
+    p = geom.cfg2(n=6, kappa=1e-4, bvals=(2500.0,))
+    p.dirs = np.eye(3)
+    S = oracle.run(p)
+    assert np.abs(S - S[0]).max() < 1e-12 * abs(S[0])
+
+
+def test_lab_converges_to_matrix_formalism_second_order():
+    """Slab with the 1-D matrix-formalism limit; h and dt halved together:
+    errors shrink by about 4 per halving (P-4, P-9)."""
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+    ref = oracle.mf_interval_signal(40.0, 2e-3, q, 2500.0, 5000.0, 400).real
+    errs = []
+    for nx, dt in [(48, 50.0), (96, 25.0), (192, 12.5)]:
+        p = geom.slab_1d(nx, dt=dt)
+        S = oracle.run(p)[0] / 40.0
+        errs.append(abs(S.real - ref))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.3 < r1 < 4.7 and 3.3 < r2 < 4.7, errs
+
+
+def test_transformed_frame_agrees_with_lab_in_neumann_box():
+    """Both frames discretise the same PDE; on a Neumann box with a permeable
+    sphere they agree to discretisation error, which shrinks with h and dt."""
+    diffs = []
+    for n, dt in [(6, 100.0), (12, 50.0)]:
+        p = geom.cfg2(n=n, dt=dt, kappa=1e-4, bvals=(2000.0,))
+        a = bo.assemble(p)
+        Sl = oracle.run_lab(p, a)[0]
+        St = oracle.run_transformed(p, a)[0]
+        diffs.append(abs(Sl - St) / abs(Sl))
+    assert diffs[1] < 0.15 and diffs[1] < diffs[0] / 2.0, diffs
