@@ -1,0 +1,169 @@
+/*
+ * bt.h -- C ABI of libbtgpu: GB300 (sm_103a) finite-element solver for the
+ * multi-compartment Bloch-Torrey equation of diffusion MRI
+ * (Nguyen, Li, Grebenkov, Hoffman et al., "Portable simulation framework for
+ * diffusion MRI", arXiv 1908.01719).
+ *
+ * Method (paper section / equation):
+ *   PDE      dU/dt = -i gamma f(t) g.x U + div(D grad U)        (Section 2, Eq. strong_BT)
+ *   membrane flux continuity, mean flux = -kappa [U]            (Section 2, Eq. btpde_ic)
+ *   outer    homogeneous Neumann, or pseudo-periodic             (Section 2, Eq. btpde_bc)
+ *   profile  PGSE f(t)                                           (Section 2, Eq. pgse)
+ *   signal   S = integral of U(x, TE) dx                         (Section 2, Eq. signal)
+ *   b-value  b = gamma^2 |g|^2 int_0^TE F(s)^2 ds                (Section 2, Eq. b_value)
+ *   space    P1 tetrahedra, one nodal copy per compartment on interface nodes (PUFEM,
+ *            Appendix A, Eq. phase_func)
+ *   time     theta-method, matrix form A U^n = F                 (Appendix B, Eq. matrix_form)
+ *   periodic gauge transform u = U exp(i gamma F(t) g.x)         (Appendix A, Eq. trBlo)
+ *
+ * Units: lengths in um, times in us (the paper's own convention).  With these
+ * units D in mm^2/s, b in s/mm^2 and kappa in m/s keep their numerical values.
+ *
+ * Conventions for every entry point:
+ *   - Return value: BT_OK (0) or a positive error code.  No C++ exception ever
+ *     crosses the ABI.  After an error, bt_last_error(ctx) describes it.
+ *   - Host pointers: read (or written) during the call only; the caller keeps
+ *     ownership.  No entry point takes a device pointer unless it says so.
+ *   - Device memory belongs to the context and is released by bt_destroy.
+ *   - All device work is issued on the context's stream (default stream unless
+ *     bt_set_stream was called); entry points that return results to host
+ *     memory synchronise that stream before returning.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef BT_H
+#define BT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int bt_status;
+enum {
+  BT_OK = 0,
+  BT_EINVAL = 1,    /* invalid argument or mesh                              */
+  BT_ENOMEM = 2,    /* host or device allocation failed                       */
+  BT_ECUDA = 3,     /* CUDA runtime error (message in bt_last_error)          */
+  BT_ENOCONV = 4,   /* a Krylov or refinement loop hit its iteration cap      */
+  BT_ENAN = 5,      /* NaN/Inf met in a right-hand side or a Krylov scalar    */
+  BT_ETIMEOUT = 6,  /* a bounded device loop gave up                          */
+  BT_ESTATE = 7,    /* call out of order (e.g. bt_run before bt_assemble)     */
+  BT_ENODEV = 8     /* GPU call on a host-only context                        */
+};
+
+typedef struct bt_ctx bt_ctx;
+
+/* Create a context on CUDA device `device`.  device < 0 creates a host-only
+ * context: mesh upload, interface doubling, periodic identification and the
+ * CSR pattern work (they run on the host), every GPU entry point returns
+ * BT_ENODEV.  *out is set to NULL on failure. */
+bt_status bt_create(bt_ctx** out, int device);
+bt_status bt_destroy(bt_ctx* ctx);
+/* Issue all device work on `cuda_stream` (a cudaStream_t; NULL = default). */
+bt_status bt_set_stream(bt_ctx* ctx, void* cuda_stream);
+const char* bt_last_error(const bt_ctx* ctx);
+
+/* ---------------------------------------------------------------- mesh
+ * Upload one geometry (copied).  xyz [3*n_nodes] (x,y,z per node, um);
+ * tet4 [4*n_tets] node ids, positively oriented (signed volume > 0, else
+ * BT_EINVAL); tet_cmpt [n_tets] compartment id in [0, n_cmpt);
+ * D_cmpt [n_cmpt] diffusivity (um^2/us); kappa_cmpt [n_cmpt] membrane
+ * permeability (um/us), +inf for "no membrane".  The face between
+ * compartments a != b gets kappa = 1/(1/kappa_a + 1/kappa_b) (Eq. btpde_ic).
+ * periodic_mask bit k: axis k periodic on [box_lo[k], box_hi[k]] (nodes on
+ * the high face are identified with those on the low face, master-slave,
+ * Eq. btpde_bc).  box_lo/box_hi also fix the origin of g.x: the box centre.
+ * Builds, on the host: periodic identification, one dof per (node,
+ * compartment) pair in increasing (master node, compartment) order,
+ * interface faces and the shared CSR pattern of every matrix. */
+bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_tets,
+                         const int32_t* tet4, const int32_t* tet_cmpt, int32_t n_cmpt,
+                         const double* D_cmpt, const double* kappa_cmpt, uint32_t periodic_mask,
+                         const double* box_lo, const double* box_hi);
+/* Sizes after bt_upload_mesh.  Any output pointer may be NULL. */
+bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t* n_iface);
+/* dof_node [n_dof] master node of each dof; dof_cmpt [n_dof] its compartment. */
+bt_status bt_get_dofmap(const bt_ctx* ctx, int32_t* dof_node, int32_t* dof_cmpt);
+/* CSR pattern: row_ptr [n_dof+1], col [nnz], columns ascending in each row. */
+bt_status bt_get_pattern(const bt_ctx* ctx, int64_t* row_ptr, int32_t* col);
+
+/* ---------------------------------------------------------------- assembly
+ * Element-by-element, deterministic assembly on the GPU of every matrix over
+ * the shared pattern (Appendix B, Eq. matrix_form; Appendix A weak form):
+ *   M mass, K stiffness (D-weighted), J interface (kappa-weighted),
+ *   MD D-weighted mass, Mx My Mz first-moment mass (x relative to the box
+ *   centre), Ex Ey Ez = C_k - C_k^T with C_k[i,j] = D int phi_i d_k phi_j,
+ * then the step planes for time step dt_us and theta (0 < theta <= 1):
+ *   A0 = M + theta dt (K + J), in FP64, FP32 and double-float (hi+lo FP32).
+ * flags: BT_FRAME_LAB (Neumann only) or BT_FRAME_TRANSFORMED (required when
+ * periodic_mask != 0). */
+enum { BT_FRAME_LAB = 0, BT_FRAME_TRANSFORMED = 1 };
+bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags);
+/* Copy one assembled FP64 value plane [nnz] to host memory. */
+enum { BT_PLANE_M = 0, BT_PLANE_K = 1, BT_PLANE_J = 2, BT_PLANE_MD = 3, BT_PLANE_MX = 4,
+       BT_PLANE_MY = 5, BT_PLANE_MZ = 6, BT_PLANE_EX = 7, BT_PLANE_EY = 8, BT_PLANE_EZ = 9,
+       BT_PLANE_A0 = 10, BT_N_PLANES = 11 };
+bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals);
+
+/* ---------------------------------------------------------------- sequence
+ * PGSE (Eq. pgse): f = 1 on [0, delta], -1 on (Delta, Delta + delta], 0
+ * otherwise; TE >= Delta + delta, TE/dt must be an integer (to 1e-9).  Each
+ * theta step uses the step average of f on both sides (design reading of the
+ * paper's f(t^n), f(t^{n-1})); F(t_n) is exact.  Needs bt_assemble first. */
+enum { BT_PGSE = 0 };
+bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta_us, double Delta_us, double TE_us);
+/* Directions dirs [3*n_dir] (normalised here) and b-values bvals [n_b]
+ * (s/mm^2).  Right-hand side r = d*n_b + j uses dirs[d], bvals[j];
+ * q = gamma |g| = sqrt(b / (delta^2 (Delta - delta/3))) (Eq. b_value, PGSE). */
+bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32_t n_b,
+                           const double* bvals);
+
+/* ---------------------------------------------------------------- solve
+ * Modes:
+ *   BT_MODE_PLAIN_FP64  FP64 vectors and Krylov (COCG in the lab frame, CG in
+ *                       the transformed frame), Jacobi; stop at
+ *                       |r| <= tol_fp64 * |r_0| per step.
+ *   BT_MODE_MIXED       FP32 complex SpMM and Krylov vectors inside
+ *                       iterative refinement; refinement residuals in
+ *                       double-float (or native FP64 with BT_OPT_RESID_FP64);
+ *                       stop at |r| <= tol_ref * |r_0|.
+ *   BT_MODE_LEARNED     as MIXED, with the learned polynomial preconditioner
+ *                       (bt_load_precond) in the inner Krylov; Jacobi fallback.
+ * Each step solves L_n d = r_0 = (R_n - L_n) u^{n-1}, u^n = u^{n-1} + d, with
+ * L_n = M + theta dt A_n, R_n = M - (1-theta) dt A_{n-1} (Appendix B). */
+enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
+enum { BT_OPT_RESID_FP64 = 1u, BT_OPT_PROFILE = 2u, BT_OPT_NO_GRAPH = 4u };
+typedef struct bt_solver_opts {
+  double tol_fp64;      /* plain FP64 stopping tolerance (default 1e-12)          */
+  double tol_inner;     /* inner FP32 Krylov tolerance (default 1e-5)             */
+  double tol_ref;       /* refinement tolerance (default 1e-9)                    */
+  int32_t max_iter;     /* Krylov iteration cap per solve (default 1000)          */
+  int32_t max_refine;   /* refinement passes per step (default 6)                 */
+  int32_t check_every;  /* host polls convergence every k iterations (default 4)  */
+  uint32_t flags;       /* BT_OPT_*                                               */
+  int32_t rhs_begin;    /* solve RHS [rhs_begin, rhs_end); both 0 = all           */
+  int32_t rhs_end;
+} bt_solver_opts;
+/* Fill `o` with the defaults above. */
+bt_status bt_default_opts(bt_solver_opts* o);
+/* Run the whole time loop from u^0 = 1 to TE for the selected RHS. */
+bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts);
+/* Results of the last bt_run.  S_re_im [2R] (re, im per RHS, um^3);
+ * err_est [R] sum over steps of the final relative refinement residual
+ * |r|/|r_0| (an upper proxy of the relative signal error); status [R]
+ * BT_OK / BT_ENOCONV / BT_ENAN per RHS.  Any pointer may be NULL. */
+bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t* status);
+/* Counters of the last bt_run (any pointer may be NULL): time steps, total
+ * Krylov iterations (summed over solves, not RHS), refinement passes, fused
+ * SpMM launches, with BT_OPT_PROFILE the summed device time (ms) of the
+ * FP32/FP64 fused SpMM launches and of the refinement-residual launches, the
+ * number of refinement-residual launches and of all kernel launches. */
+bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters,
+                       int64_t* refine_passes, int64_t* spmm_launches, double* spmm_ms,
+                       double* resid_ms, int64_t* resid_launches, int64_t* kernel_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BT_H */

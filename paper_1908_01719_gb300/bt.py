@@ -1,0 +1,196 @@
+"""Thin Python binding of libbtgpu (include/bt.h), argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Arrays are NumPy
+arrays on the host; the library copies what it needs.  A non-zero status
+raises BtError with the library's message.  The library must have been built
+(``paper_1908_01719_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbtgpu.so")
+
+BT_OK, BT_EINVAL, BT_ENOMEM, BT_ECUDA, BT_ENOCONV, BT_ENAN, BT_ETIMEOUT, BT_ESTATE, BT_ENODEV = range(9)
+BT_FRAME_LAB, BT_FRAME_TRANSFORMED = 0, 1
+BT_PGSE = 0
+BT_MODE_PLAIN_FP64, BT_MODE_MIXED, BT_MODE_LEARNED = 0, 1, 2
+BT_OPT_RESID_FP64, BT_OPT_PROFILE, BT_OPT_NO_GRAPH = 1, 2, 4
+PLANES = {"M": 0, "K": 1, "J": 2, "MD": 3, "Mx": 4, "My": 5, "Mz": 6, "Ex": 7, "Ey": 8, "Ez": 9, "A0": 10}
+
+# every symbol include/bt.h declares
+EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_upload_mesh", "bt_get_sizes",
+           "bt_get_dofmap", "bt_get_pattern", "bt_assemble", "bt_get_plane", "bt_set_sequence",
+           "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats"]
+
+
+class BtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[bt status {code}] {msg}")
+        self.code = code
+
+
+class bt_solver_opts(C.Structure):
+    _fields_ = [("tol_fp64", C.c_double), ("tol_inner", C.c_double), ("tol_ref", C.c_double),
+                ("max_iter", C.c_int32), ("max_refine", C.c_int32), ("check_every", C.c_int32),
+                ("flags", C.c_uint32), ("rhs_begin", C.c_int32), ("rhs_end", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1908_01719_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64, U32, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
+        sig = {
+            "bt_create": [C.POINTER(P), C.c_int],
+            "bt_destroy": [P],
+            "bt_set_stream": [P, P],
+            "bt_upload_mesh": [P, I64, P, I64, P, P, I32, P, P, U32, P, P],
+            "bt_get_sizes": [P, P, P, P],
+            "bt_get_dofmap": [P, P, P],
+            "bt_get_pattern": [P, P, P],
+            "bt_assemble": [P, D, D, U32],
+            "bt_get_plane": [P, C.c_int, P],
+            "bt_set_sequence": [P, C.c_int, D, D, D],
+            "bt_set_gradients": [P, I32, P, I32, P],
+            "bt_default_opts": [C.POINTER(bt_solver_opts)],
+            "bt_run": [P, C.c_int, C.POINTER(bt_solver_opts)],
+            "bt_get_signals": [P, P, P, P],
+            "bt_get_stats": [P, P, P, P, P, P, P, P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.bt_last_error.argtypes = [P]
+        L.bt_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, st):
+    if st != BT_OK:
+        msg = lib().bt_last_error(ctx).decode() if ctx else ""
+        raise BtError(st, msg)
+
+
+def bt_create(device: int):
+    h = C.c_void_p()
+    st = lib().bt_create(C.byref(h), device)
+    if st != BT_OK:
+        raise BtError(st, f"bt_create(device={device}) failed")
+    return h
+
+
+def bt_destroy(ctx):
+    lib().bt_destroy(ctx)
+
+
+def bt_set_stream(ctx, stream_handle: int):
+    _check(ctx, lib().bt_set_stream(ctx, C.c_void_p(stream_handle)))
+
+
+def bt_last_error(ctx) -> str:
+    return lib().bt_last_error(ctx).decode()
+
+
+def bt_upload_mesh(ctx, xyz, tets, tet_cmpt, D_cmpt, kappa_cmpt, periodic_mask, box_lo, box_hi):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    tc = np.ascontiguousarray(tet_cmpt, dtype=np.int32)
+    D = np.ascontiguousarray(D_cmpt, dtype=np.float64)
+    K = np.ascontiguousarray(kappa_cmpt, dtype=np.float64)
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(box_hi, dtype=np.float64)
+    _check(ctx, lib().bt_upload_mesh(ctx, len(xyz), _ptr(xyz), len(tets), _ptr(tets), _ptr(tc), len(D), _ptr(D),
+                                     _ptr(K), int(periodic_mask), _ptr(lo), _ptr(hi)))
+
+
+def bt_get_sizes(ctx):
+    a = (C.c_int64 * 3)()
+    _check(ctx, lib().bt_get_sizes(ctx, C.byref(a, 0), C.byref(a, 8), C.byref(a, 16)))
+    return int(a[0]), int(a[1]), int(a[2])
+
+
+def bt_get_dofmap(ctx):
+    n, _, _ = bt_get_sizes(ctx)
+    dn = np.empty(n, np.int32)
+    dc = np.empty(n, np.int32)
+    _check(ctx, lib().bt_get_dofmap(ctx, _ptr(dn), _ptr(dc)))
+    return dn, dc
+
+
+def bt_get_pattern(ctx):
+    n, nnz, _ = bt_get_sizes(ctx)
+    rp = np.empty(n + 1, np.int64)
+    col = np.empty(nnz, np.int32)
+    _check(ctx, lib().bt_get_pattern(ctx, _ptr(rp), _ptr(col)))
+    return rp, col
+
+
+def bt_assemble(ctx, dt_us: float, theta: float, frame: int):
+    _check(ctx, lib().bt_assemble(ctx, float(dt_us), float(theta), int(frame)))
+
+
+def bt_get_plane(ctx, which):
+    _, nnz, _ = bt_get_sizes(ctx)
+    v = np.empty(nnz, np.float64)
+    idx = PLANES[which] if isinstance(which, str) else int(which)
+    _check(ctx, lib().bt_get_plane(ctx, idx, _ptr(v)))
+    return v
+
+
+def bt_set_sequence(ctx, kind, delta, Delta, TE):
+    _check(ctx, lib().bt_set_sequence(ctx, int(kind), float(delta), float(Delta), float(TE)))
+
+
+def bt_set_gradients(ctx, dirs, bvals):
+    d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    b = np.ascontiguousarray(bvals, dtype=np.float64).ravel()
+    _check(ctx, lib().bt_set_gradients(ctx, len(d), _ptr(d), len(b), _ptr(b)))
+
+
+def bt_default_opts(**kw):
+    o = bt_solver_opts()
+    lib().bt_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def bt_run(ctx, mode, opts=None, raise_on_status=True):
+    o = opts if opts is not None else bt_default_opts()
+    st = lib().bt_run(ctx, int(mode), C.byref(o))
+    if st != BT_OK and (raise_on_status or st not in (BT_ENOCONV, BT_ENAN)):
+        _check(ctx, st)
+    return st
+
+
+def bt_get_signals(ctx, R):
+    S = np.empty(2 * R, np.float64)
+    err = np.empty(R, np.float64)
+    stat = np.empty(R, np.int32)
+    _check(ctx, lib().bt_get_signals(ctx, _ptr(S), _ptr(err), _ptr(stat)))
+    return S[0::2] + 1j * S[1::2], err, stat
+
+
+def bt_get_stats(ctx):
+    i = (C.c_int64 * 6)()
+    d = (C.c_double * 2)()
+    _check(ctx, lib().bt_get_stats(ctx, C.byref(i, 0), C.byref(i, 8), C.byref(i, 16), C.byref(i, 24),
+                                   C.byref(d, 0), C.byref(d, 8), C.byref(i, 32), C.byref(i, 40)))
+    return {"steps": i[0], "krylov_iters": i[1], "refine_passes": i[2], "spmm_launches": i[3],
+            "spmm_ms": d[0], "resid_ms": d[1], "resid_launches": i[4], "kernel_launches": i[5]}

@@ -1,0 +1,735 @@
+// C ABI of libbtgpu (declared in include/bt.h): context, mesh upload,
+// assembly, sequence, gradients, the time loop with iterative refinement, and
+// result read-back.  All arithmetic of the method runs in the CUDA kernels of
+// this library; this file only moves data and sequences launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bt_kernels.cuh"
+
+using namespace bt;
+
+namespace {
+
+constexpr int N_COUNTERS = 16;
+
+struct EventPair {
+  cudaEvent_t a, b;
+  int kind;  // 0 fused Krylov SpMM, 1 refinement residual
+};
+
+}  // namespace
+
+struct bt_ctx {
+  int device = -1;
+  bool host_only = true;
+  cudaStream_t stream = nullptr;
+  int sms = 152;
+  std::string err;
+
+  HostMesh mesh;
+  bool have_mesh = false;
+
+  // device copies of the mesh and the contribution lists
+  DBuf<double> d_xyz, d_D, d_face_kappa, d_geo, d_fcoef;
+  DBuf<int32_t> d_tets, d_cmpt, d_face_ta, d_tc, d_fc, d_rp, d_col;
+  DBuf<int8_t> d_face_lv;
+  DBuf<int64_t> d_tc_ptr, d_fc_ptr;
+  // assembled planes
+  DBuf<double> d_planes, d_A0, d_KJ, d_w, d_diag_md64;
+  DBuf<double4> d_pk64, d_diag64;
+  DBuf<float4> d_pk32, d_pkhi, d_pklo, d_diag32;
+  DBuf<float> d_md32, d_diag_md32;
+  DBuf<float2> d_kjmd_hi, d_kjmd_lo;
+  bool assembled = false;
+  double dt = 0, theta = 0.5, wmax = 0;
+  int transformed = 0;
+
+  // sequence
+  bool have_seq = false;
+  double delta = 0, Delta = 0, TE = 0;
+  int n_steps = 0;
+  std::vector<double> fbar, F;  // fbar[n-1], n = 1..N; F[n], n = 0..N
+
+  // gradients
+  int n_dir = 0, n_b = 0, R = 0;
+  std::vector<double> qhat_rhs, q_rhs;  // [3R], [R]
+
+  // run buffers
+  DBuf<double> d_q, d_qhat;
+  DBuf<OpCoef> d_coef;
+  DBuf<double2> u64, r64, x64, rk64, p64, q64;
+  DBuf<float4> udf, rdf;
+  DBuf<float2> x32, r32, p32, q32;
+  DBuf<double> ks_rho, ks_alpha, ks_beta, ks_rr0, ks_rr, ks_tol2;
+  DBuf<int> ks_iter, ks_active, ks_status, n_active, ks_it_best;
+  DBuf<double> ks_rr_best;
+  DBuf<double> rf_r0n2, rf_rk2, rf_scale, rf_err;
+  DBuf<int> rf_active;
+  DBuf<double> red_part, d_S;
+  DBuf<unsigned int> red_counter;
+  int* h_flags = nullptr;  // pinned: [0] Krylov n_active, [1] refinement n_active
+
+  // results
+  std::vector<double> S, err_est;
+  std::vector<int> status;
+  int64_t st_steps = 0, st_iters = 0, st_refine = 0, st_spmm = 0, st_resid = 0, st_launches = 0;
+  double st_spmm_ms = 0, st_resid_ms = 0;
+  std::vector<EventPair> ev_pool;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+bt_status fail(bt_ctx* c, bt_status code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? BT_ENOMEM : BT_ECUDA,                   \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+  } while (0)
+
+#define CKL()                                                                                    \
+  do {                                                                                           \
+    cudaError_t e_ = cudaGetLastError();                                                         \
+    if (e_ != cudaSuccess) return fail(ctx, BT_ECUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+cudaError_t upload(DBuf<T>& b, const std::vector<T>& h, cudaStream_t st) {
+  cudaError_t e = b.alloc(h.size());
+  if (e != cudaSuccess || h.empty()) return e;
+  return cudaMemcpyAsync(b.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+bool need_gpu(bt_ctx* ctx) { return ctx && !ctx->host_only; }
+
+EventPair* ev_next(bt_ctx* ctx, int kind) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    EventPair e;
+    if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return nullptr;
+    ctx->ev_pool.push_back(e);
+  }
+  EventPair* e = &ctx->ev_pool[ctx->ev_used++];
+  e->kind = kind;
+  return e;
+}
+
+void ev_harvest(bt_ctx* ctx) {
+  for (size_t i = 0; i < ctx->ev_used; ++i) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, ctx->ev_pool[i].a, ctx->ev_pool[i].b) == cudaSuccess) {
+      if (ctx->ev_pool[i].kind == 0) ctx->st_spmm_ms += ms;
+      else ctx->st_resid_ms += ms;
+    }
+  }
+  ctx->ev_used = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+bt_status bt_create(bt_ctx** out, int device) {
+  if (!out) return BT_EINVAL;
+  *out = nullptr;
+  bt_ctx* c = new (std::nothrow) bt_ctx();
+  if (!c) return BT_ENOMEM;
+  c->device = device;
+  c->host_only = device < 0;
+  if (!c->host_only) {
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->h_flags, 4 * sizeof(int), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = c->red_counter.alloc(N_COUNTERS);
+    if (e == cudaSuccess) e = cudaMemset(c->red_counter.p, 0, N_COUNTERS * sizeof(unsigned int));
+    if (e != cudaSuccess) {
+      delete c;
+      return BT_ECUDA;
+    }
+  }
+  *out = c;
+  return BT_OK;
+}
+
+bt_status bt_destroy(bt_ctx* ctx) {
+  if (!ctx) return BT_OK;
+  if (!ctx->host_only) {
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& e : ctx->ev_pool) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+  }
+  delete ctx;
+  return BT_OK;
+}
+
+bt_status bt_set_stream(bt_ctx* ctx, void* s) {
+  if (!ctx) return BT_EINVAL;
+  ctx->stream = (cudaStream_t)s;
+  return BT_OK;
+}
+
+const char* bt_last_error(const bt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_tets, const int32_t* tet4,
+                         const int32_t* tet_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* kappa_cmpt,
+                         uint32_t periodic_mask, const double* box_lo, const double* box_hi) {
+  if (!ctx) return BT_EINVAL;
+  if (!xyz || !tet4 || !tet_cmpt || !D_cmpt || !kappa_cmpt || !box_lo || !box_hi || n_nodes <= 0 || n_tets <= 0 ||
+      n_cmpt <= 0 || periodic_mask > 7)
+    return fail(ctx, BT_EINVAL, "bt_upload_mesh: invalid argument");
+  HostMesh& m = ctx->mesh;
+  m = HostMesh();
+  ctx->have_mesh = ctx->assembled = ctx->have_seq = false;
+  try {
+    m.n_nodes = n_nodes;
+    m.n_tets = n_tets;
+    m.n_cmpt = n_cmpt;
+    m.xyz.assign(xyz, xyz + 3 * n_nodes);
+    m.tets.assign(tet4, tet4 + 4 * n_tets);
+    m.tet_cmpt.assign(tet_cmpt, tet_cmpt + n_tets);
+    m.D.assign(D_cmpt, D_cmpt + n_cmpt);
+    m.kappa.assign(kappa_cmpt, kappa_cmpt + n_cmpt);
+    m.pmask = periodic_mask;
+    for (int k = 0; k < 3; ++k) {
+      m.lo[k] = box_lo[k];
+      m.hi[k] = box_hi[k];
+    }
+    std::string msg;
+    int st = build_host_mesh(m, msg);
+    if (st) return fail(ctx, st, "bt_upload_mesh: " + msg);
+    for (double kf : m.face_kappa)
+      if (!std::isfinite(kf))
+        return fail(ctx, BT_EINVAL, "bt_upload_mesh: two compartments without membrane (kappa = inf) touch");
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, BT_ENOMEM, "bt_upload_mesh: host allocation failed");
+  }
+  ctx->have_mesh = true;
+  if (ctx->host_only) return BT_OK;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  CK(upload(ctx->d_xyz, m.xyz, st));
+  CK(upload(ctx->d_tets, m.tets, st));
+  CK(upload(ctx->d_cmpt, m.tet_cmpt, st));
+  CK(upload(ctx->d_D, m.D, st));
+  CK(upload(ctx->d_face_ta, m.face_ta, st));
+  CK(upload(ctx->d_face_lv, m.face_lv, st));
+  CK(upload(ctx->d_face_kappa, m.face_kappa, st));
+  CK(upload(ctx->d_tc_ptr, m.tc_ptr, st));
+  CK(upload(ctx->d_tc, m.tc, st));
+  CK(upload(ctx->d_fc_ptr, m.fc_ptr, st));
+  CK(upload(ctx->d_fc, m.fc, st));
+  std::vector<int32_t> rp32(m.row_ptr.begin(), m.row_ptr.end());
+  CK(upload(ctx->d_rp, rp32, st));
+  CK(upload(ctx->d_col, m.col, st));
+  CK(cudaStreamSynchronize(st));
+  return BT_OK;
+}
+
+bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t* n_iface) {
+  if (!ctx || !ctx->have_mesh) return BT_ESTATE;
+  if (n_dof) *n_dof = ctx->mesh.n_dof;
+  if (nnz) *nnz = ctx->mesh.nnz;
+  if (n_iface) *n_iface = ctx->mesh.n_face;
+  return BT_OK;
+}
+
+bt_status bt_get_dofmap(const bt_ctx* ctx, int32_t* dof_node, int32_t* dof_cmpt) {
+  if (!ctx || !ctx->have_mesh) return BT_ESTATE;
+  if (dof_node) std::memcpy(dof_node, ctx->mesh.dof_node.data(), ctx->mesh.n_dof * sizeof(int32_t));
+  if (dof_cmpt) std::memcpy(dof_cmpt, ctx->mesh.dof_cmpt.data(), ctx->mesh.n_dof * sizeof(int32_t));
+  return BT_OK;
+}
+
+bt_status bt_get_pattern(const bt_ctx* ctx, int64_t* row_ptr, int32_t* col) {
+  if (!ctx || !ctx->have_mesh) return BT_ESTATE;
+  if (row_ptr) std::memcpy(row_ptr, ctx->mesh.row_ptr.data(), (ctx->mesh.n_dof + 1) * sizeof(int64_t));
+  if (col) std::memcpy(col, ctx->mesh.col.data(), ctx->mesh.nnz * sizeof(int32_t));
+  return BT_OK;
+}
+
+bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
+  if (!ctx) return BT_EINVAL;
+  if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_assemble: no mesh");
+  if (!need_gpu(ctx)) return fail(ctx, BT_ENODEV, "bt_assemble: host-only context");
+  if (!(dt_us > 0) || !std::isfinite(dt_us) || !(theta > 0) || theta > 1 || flags > 1)
+    return fail(ctx, BT_EINVAL, "bt_assemble: need dt > 0, 0 < theta <= 1, flags in {LAB, TRANSFORMED}");
+  if (ctx->mesh.pmask && flags != BT_FRAME_TRANSFORMED)
+    return fail(ctx, BT_EINVAL, "bt_assemble: periodic boxes need BT_FRAME_TRANSFORMED");
+  CK(cudaSetDevice(ctx->device));
+  const HostMesh& m = ctx->mesh;
+  const int64_t nnz = m.nnz, n = m.n_dof;
+  cudaStream_t st = ctx->stream;
+  CK(ctx->d_geo.alloc(26 * (size_t)m.n_tets));
+  CK(ctx->d_fcoef.alloc(std::max<int64_t>(1, m.n_face)));
+  CK(ctx->d_planes.alloc(10 * (size_t)nnz));
+  AsmArgs a;
+  a.xyz = ctx->d_xyz.p;
+  a.tets = ctx->d_tets.p;
+  a.cmpt = ctx->d_cmpt.p;
+  a.Dc = ctx->d_D.p;
+  for (int k = 0; k < 3; ++k) a.centre[k] = 0.5 * (m.lo[k] + m.hi[k]);
+  a.nt = m.n_tets;
+  a.nf = m.n_face;
+  a.nnz = nnz;
+  a.face_ta = ctx->d_face_ta.p;
+  a.face_lv = ctx->d_face_lv.p;
+  a.face_kappa = ctx->d_face_kappa.p;
+  a.tc_ptr = ctx->d_tc_ptr.p;
+  a.tc = ctx->d_tc.p;
+  a.fc_ptr = ctx->d_fc_ptr.p;
+  a.fc = ctx->d_fc.p;
+  a.geo = ctx->d_geo.p;
+  a.fcoef = ctx->d_fcoef.p;
+  a.planes = ctx->d_planes.p;
+  launch_assembly(a, st);
+  CKL();
+  CK(ctx->d_A0.alloc(nnz));
+  CK(ctx->d_KJ.alloc(nnz));
+  CK(ctx->d_pk64.alloc(nnz));
+  CK(ctx->d_pk32.alloc(nnz));
+  CK(ctx->d_md32.alloc(nnz));
+  CK(ctx->d_pkhi.alloc(nnz));
+  CK(ctx->d_pklo.alloc(nnz));
+  CK(ctx->d_kjmd_hi.alloc(nnz));
+  CK(ctx->d_kjmd_lo.alloc(nnz));
+  CK(ctx->d_w.alloc(n));
+  CK(ctx->d_diag64.alloc(n));
+  CK(ctx->d_diag_md64.alloc(n));
+  CK(ctx->d_diag32.alloc(n));
+  CK(ctx->d_diag_md32.alloc(n));
+  DeriveArgs d;
+  d.planes = ctx->d_planes.p;
+  d.nnz = nnz;
+  d.n = n;
+  d.thdt = theta * dt_us;
+  d.transformed = (int)flags;
+  d.rp = ctx->d_rp.p;
+  d.col = ctx->d_col.p;
+  d.A0 = ctx->d_A0.p;
+  d.KJ = ctx->d_KJ.p;
+  d.pk64 = ctx->d_pk64.p;
+  d.pk32 = ctx->d_pk32.p;
+  d.md32 = ctx->d_md32.p;
+  d.pkhi = ctx->d_pkhi.p;
+  d.pklo = ctx->d_pklo.p;
+  d.kjmd_hi = ctx->d_kjmd_hi.p;
+  d.kjmd_lo = ctx->d_kjmd_lo.p;
+  d.w = ctx->d_w.p;
+  d.diag64 = ctx->d_diag64.p;
+  d.diag_md64 = ctx->d_diag_md64.p;
+  d.diag32 = ctx->d_diag32.p;
+  d.diag_md32 = ctx->d_diag_md32.p;
+  launch_derive(d, st);
+  CKL();
+  std::vector<double> w(n);
+  CK(cudaMemcpyAsync(w.data(), ctx->d_w.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->wmax = 0;
+  for (double x : w) ctx->wmax = std::max(ctx->wmax, std::fabs(x));
+  ctx->dt = dt_us;
+  ctx->theta = theta;
+  ctx->transformed = (int)flags;
+  ctx->assembled = true;
+  ctx->have_seq = false;
+  return BT_OK;
+}
+
+bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals) {
+  if (!ctx || !vals || which < 0 || which >= BT_N_PLANES) return fail(ctx, BT_EINVAL, "bt_get_plane: bad argument");
+  if (!need_gpu(ctx)) return fail(ctx, BT_ENODEV, "bt_get_plane: host-only context");
+  if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_get_plane: not assembled");
+  CK(cudaSetDevice(ctx->device));
+  const double* src = which == BT_PLANE_A0 ? ctx->d_A0.p : ctx->d_planes.p + (size_t)which * ctx->mesh.nnz;
+  CK(cudaMemcpyAsync(vals, src, ctx->mesh.nnz * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return BT_OK;
+}
+
+bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta, double Delta, double TE) {
+  if (!ctx) return BT_EINVAL;
+  if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_set_sequence: assemble first (dt is needed)");
+  if (kind != BT_PGSE) return fail(ctx, BT_EINVAL, "bt_set_sequence: only BT_PGSE");
+  if (!(delta > 0) || !(Delta >= delta) || !(TE >= Delta + delta - 1e-9 * TE))
+    return fail(ctx, BT_EINVAL, "bt_set_sequence: need 0 < delta <= Delta and TE >= Delta + delta");
+  double ns = TE / ctx->dt;
+  int N = (int)std::llround(ns);
+  if (std::fabs(ns - N) > 1e-9 * std::max(1.0, ns) || N < 1)
+    return fail(ctx, BT_EINVAL, "bt_set_sequence: TE must be an integer multiple of dt");
+  ctx->delta = delta;
+  ctx->Delta = Delta;
+  ctx->TE = TE;
+  ctx->n_steps = N;
+  // F(t) = int_0^t f for PGSE; f_bar_n = (F(t_n) - F(t_{n-1})) / dt (step average)
+  auto Ft = [&](double t) {
+    double a = std::min(std::max(t, 0.0), delta);
+    double b = std::min(std::max(t - Delta, 0.0), delta);
+    return a - b;
+  };
+  ctx->F.resize(N + 1);
+  ctx->fbar.resize(N);
+  for (int n = 0; n <= N; ++n) ctx->F[n] = Ft(n * ctx->dt);
+  for (int n = 1; n <= N; ++n) ctx->fbar[n - 1] = (ctx->F[n] - ctx->F[n - 1]) / ctx->dt;
+  if (ctx->transformed && std::fabs(ctx->F[N]) > 1e-12 * delta)
+    return fail(ctx, BT_EINVAL, "bt_set_sequence: F(TE) != 0 in the transformed frame");
+  ctx->have_seq = true;
+  return BT_OK;
+}
+
+bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32_t n_b, const double* bvals) {
+  if (!ctx) return BT_EINVAL;
+  if (!ctx->have_seq) return fail(ctx, BT_ESTATE, "bt_set_gradients: set the sequence first");
+  if (n_dir <= 0 || n_b <= 0 || !dirs || !bvals || (int64_t)n_dir * n_b > 1024)
+    return fail(ctx, BT_EINVAL, "bt_set_gradients: need 1 <= n_dir * n_b <= 1024");
+  ctx->n_dir = n_dir;
+  ctx->n_b = n_b;
+  ctx->R = n_dir * n_b;
+  ctx->qhat_rhs.resize(3 * ctx->R);
+  ctx->q_rhs.resize(ctx->R);
+  const double d = ctx->delta, D = ctx->Delta;
+  const double intF2 = d * d * (D - d / 3.0);  // int_0^TE F^2 for PGSE
+  for (int i = 0; i < n_dir; ++i) {
+    double nx = dirs[3 * i], ny = dirs[3 * i + 1], nz = dirs[3 * i + 2];
+    double nr = std::sqrt(nx * nx + ny * ny + nz * nz);
+    if (!(nr > 0) || !std::isfinite(nr)) return fail(ctx, BT_EINVAL, "bt_set_gradients: zero direction");
+    for (int j = 0; j < n_b; ++j) {
+      if (!(bvals[j] >= 0) || !std::isfinite(bvals[j])) return fail(ctx, BT_EINVAL, "bt_set_gradients: b < 0");
+      int r = i * n_b + j;
+      ctx->qhat_rhs[3 * r] = nx / nr;
+      ctx->qhat_rhs[3 * r + 1] = ny / nr;
+      ctx->qhat_rhs[3 * r + 2] = nz / nr;
+      ctx->q_rhs[r] = std::sqrt(bvals[j] / intF2);  // b = q^2 int F^2 (Eq. b_value)
+    }
+  }
+  ctx->S.assign(2 * ctx->R, 0.0);
+  ctx->err_est.assign(ctx->R, 0.0);
+  ctx->status.assign(ctx->R, BT_OK);
+  return BT_OK;
+}
+
+bt_status bt_default_opts(bt_solver_opts* o) {
+  if (!o) return BT_EINVAL;
+  o->tol_fp64 = 1e-12;
+  o->tol_inner = 1e-5;
+  o->tol_ref = 1e-9;
+  o->max_iter = 1000;
+  o->max_refine = 6;
+  o->check_every = 4;
+  o->flags = 0;
+  o->rhs_begin = 0;
+  o->rhs_end = 0;
+  return BT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// RHS per lane: the NB right-hand sides of a lane must share one direction
+// NB consecutive systems of one lane must share a direction, and with NB > 1
+// the RHS count must fill whole tiles of 32 NB columns
+int pick_nb(const bt_ctx* ctx, int rb, int Rs) {
+  for (int nb : {4, 2}) {
+    if (ctx->n_b % nb == 0 && rb % nb == 0 && Rs % (32 * nb) == 0) return nb;
+  }
+  return 1;
+}
+
+template <class T>
+cudaError_t ensure(DBuf<T>& b, size_t n) {
+  if (b.n >= n && b.p) return cudaSuccess;
+  return b.alloc(n);
+}
+
+}  // namespace
+
+extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in) {
+  if (!ctx) return BT_EINVAL;
+  if (!need_gpu(ctx)) return fail(ctx, BT_ENODEV, "bt_run: host-only context");
+  if (!ctx->assembled || !ctx->have_seq || ctx->R == 0)
+    return fail(ctx, BT_ESTATE, "bt_run: need mesh, assembly, sequence and gradients");
+  if (mode != BT_MODE_PLAIN_FP64 && mode != BT_MODE_MIXED)
+    return fail(ctx, BT_EINVAL, "bt_run: mode not available");
+  bt_solver_opts o;
+  bt_default_opts(&o);
+  if (opts_in) o = *opts_in;
+  int rb = o.rhs_begin, re = o.rhs_end;
+  if (rb == 0 && re == 0) re = ctx->R;
+  if (rb < 0 || re > ctx->R || rb >= re) return fail(ctx, BT_EINVAL, "bt_run: bad RHS range");
+  if (o.max_iter < 1 || o.max_refine < 1 || o.check_every < 1 || !(o.tol_fp64 > 0) || !(o.tol_inner > 0) ||
+      !(o.tol_ref > 0))
+    return fail(ctx, BT_EINVAL, "bt_run: bad solver options");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const int Rs = re - rb;
+  const int nb = pick_nb(ctx, rb, Rs);
+  const int Rp = ((Rs + nb - 1) / nb) * nb;
+  const int64_t n = ctx->mesh.n_dof;
+  const size_t NE = (size_t)n * Rp;
+  const bool plain = mode == BT_MODE_PLAIN_FP64;
+  const bool df = !plain && !(o.flags & BT_OPT_RESID_FP64);
+  const bool prof = (o.flags & BT_OPT_PROFILE) != 0;
+  const bool narrow = plain && Rs <= 4;  // lanes over nonzeros for the per-direction FP64 solve
+  const int conj = ctx->transformed ? 1 : 0;  // CG (Hermitian) vs COCG (complex symmetric)
+
+  // per-run device buffers
+  CK(ensure(ctx->d_q, Rs));
+  CK(ensure(ctx->d_qhat, 3 * (size_t)Rs));
+  CK(cudaMemcpyAsync(ctx->d_q.p, ctx->q_rhs.data() + rb, Rs * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_qhat.p, ctx->qhat_rhs.data() + 3 * rb, 3 * Rs * sizeof(double), cudaMemcpyHostToDevice,
+                     st));
+  if (plain) {
+    CK(ensure(ctx->u64, NE));
+    CK(ensure(ctx->r64, NE));
+    CK(ensure(ctx->x64, NE));
+    CK(ensure(ctx->rk64, NE));
+    CK(ensure(ctx->p64, NE));
+    CK(ensure(ctx->q64, NE));
+  } else {
+    if (df) {
+      CK(ensure(ctx->udf, NE));
+      CK(ensure(ctx->rdf, NE));
+    } else {
+      CK(ensure(ctx->u64, NE));
+      CK(ensure(ctx->r64, NE));
+    }
+    CK(ensure(ctx->x32, NE));
+    CK(ensure(ctx->r32, NE));
+    CK(ensure(ctx->p32, NE));
+    CK(ensure(ctx->q32, NE));
+  }
+  CK(ensure(ctx->ks_rho, 2 * (size_t)Rs));
+  CK(ensure(ctx->ks_alpha, 2 * (size_t)Rs));
+  CK(ensure(ctx->ks_beta, 2 * (size_t)Rs));
+  CK(ensure(ctx->ks_rr0, Rs));
+  CK(ensure(ctx->ks_rr, Rs));
+  CK(ensure(ctx->ks_tol2, Rs));
+  CK(ensure(ctx->ks_iter, Rs));
+  CK(ensure(ctx->ks_active, Rs));
+  CK(ensure(ctx->ks_status, Rs));
+  CK(ensure(ctx->ks_rr_best, Rs));
+  CK(ensure(ctx->ks_it_best, Rs));
+  CK(ensure(ctx->n_active, 4));
+  CK(ensure(ctx->rf_r0n2, Rs));
+  CK(ensure(ctx->rf_rk2, Rs));
+  CK(ensure(ctx->rf_scale, Rs));
+  CK(ensure(ctx->rf_err, Rs));
+  CK(ensure(ctx->rf_active, Rs));
+  CK(ensure(ctx->d_S, 2 * (size_t)Rs));
+  const size_t max_blocks = (size_t)ctx->sms * REDUCE_BLOCKS_PER_SM + 64;
+  CK(ensure(ctx->red_part, max_blocks * Rp * 4));  // up to two complex partials per (block, RHS)
+  // coefficient table: per step, [0] = r_0 operator (R_n - L_n), [1] = L_n
+  const int N = ctx->n_steps;
+  std::vector<OpCoef> coefs(2 * (size_t)N);
+  const double dt = ctx->dt, th = ctx->theta;
+  for (int s = 1; s <= N; ++s) {
+    OpCoef c0, c1;
+    if (!ctx->transformed) {
+      double fb = ctx->fbar[s - 1];
+      c0 = {-dt, 0.0, -dt * fb};
+      c1 = {1.0, 0.0, th * dt * fb};
+    } else {
+      double Fn = ctx->F[s], Fp = ctx->F[s - 1];
+      c0 = {-dt, -dt * ((1 - th) * Fp * Fp + th * Fn * Fn), -dt * ((1 - th) * Fp + th * Fn)};
+      c1 = {1.0, th * dt * Fn * Fn, th * dt * Fn};
+    }
+    coefs[2 * (s - 1)] = c0;
+    coefs[2 * (s - 1) + 1] = c1;
+  }
+  CK(ensure(ctx->d_coef, coefs.size()));
+  CK(cudaMemcpyAsync(ctx->d_coef.p, coefs.data(), coefs.size() * sizeof(OpCoef), cudaMemcpyHostToDevice, st));
+
+  OpArgs op{};
+  op.rp = ctx->d_rp.p;
+  op.col = ctx->d_col.p;
+  op.n = n;
+  op.pk64 = ctx->d_pk64.p;
+  op.p0_64 = ctx->d_KJ.p;
+  op.p1_64 = ctx->d_planes.p + 3 * (size_t)ctx->mesh.nnz;  // MD plane
+  op.pk32 = ctx->d_pk32.p;
+  op.p1_32 = ctx->d_md32.p;
+  op.pkhi = ctx->d_pkhi.p;
+  op.pklo = ctx->d_pklo.p;
+  op.kjmd_hi = ctx->d_kjmd_hi.p;
+  op.kjmd_lo = ctx->d_kjmd_lo.p;
+  op.q = ctx->d_q.p;
+  op.qhat = ctx->d_qhat.p;
+  op.R = Rs;
+  op.Rp = Rp;
+  op.transformed = ctx->transformed;
+  VecArgs va{n, Rs, Rp, nb, ctx->d_diag64.p, ctx->d_diag_md64.p, ctx->d_diag32.p, ctx->d_diag_md32.p};
+  KrylovState ks{ctx->ks_rho.p, ctx->ks_alpha.p, ctx->ks_beta.p, ctx->ks_rr0.p, ctx->ks_rr.p, ctx->ks_tol2.p,
+                 ctx->ks_iter.p, ctx->ks_active.p, ctx->n_active.p, ctx->ks_status.p, ctx->ks_rr_best.p,
+                 ctx->ks_it_best.p, o.max_iter, plain ? 0 : 30};
+  RefineState rf{ctx->rf_r0n2.p, ctx->rf_rk2.p, ctx->rf_scale.p, ctx->rf_err.p, ctx->rf_active.p,
+                 ctx->n_active.p + 1, o.tol_ref * o.tol_ref, 0.0};
+  const double feps = 1e-14 * ctx->wmax;
+  rf.floor_c2 = feps * feps;
+  auto rs_at = [&](int c) { return RedScratch{ctx->red_part.p, ctx->red_counter.p + c}; };
+
+  ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
+  ctx->st_spmm_ms = ctx->st_resid_ms = 0;
+  ctx->ev_used = 0;
+  CK(cudaMemsetAsync(ctx->rf_err.p, 0, Rs * sizeof(double), st));
+  CK(cudaMemsetAsync(ctx->ks_status.p, 0, Rs * sizeof(int), st));
+  if (df) launch_fill_u_df(va, ctx->udf.p, st);
+  else launch_fill_u(va, ctx->u64.p, st);
+  CKL();
+  int64_t& L = ctx->st_launches;
+  L = 1;
+
+  auto read_flag = [&](const int* dptr, int& out) -> bt_status {
+    CK(cudaMemcpyAsync(ctx->h_flags, dptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out = ctx->h_flags[0];
+    return BT_OK;
+  };
+  auto timed = [&](int kind, auto&& launch) {
+    EventPair* e = prof ? ev_next(ctx, kind) : nullptr;
+    if (e) cudaEventRecord(e->a, st);
+    launch();
+    if (e) cudaEventRecord(e->b, st);
+  };
+
+  for (int step = 1; step <= N; ++step) {
+    const OpCoef* c_r0 = ctx->d_coef.p + 2 * (step - 1);
+    const OpCoef* c_L = c_r0 + 1;
+    launch_set_int(ctx->rf_active.p, 1, Rs, st);
+    launch_set_int(rf.n_active, Rs, 1, st);
+    L += 3;  // two set kernels and the step-start residual
+    op.coef = c_r0;
+    timed(1, [&] {
+      if (df) launch_resid0_df(op, ctx->udf.p, ctx->rdf.p, rf, rs_at(0), nb, ctx->sms, st);
+      else if (narrow) launch_resid0_narrow(op, ctx->u64.p, ctx->r64.p, rf, rs_at(0), ctx->sms, st);
+      else launch_resid0(op, ctx->u64.p, ctx->r64.p, rf, rs_at(0), nb, ctx->sms, st);
+    });
+    CKL();
+    ctx->st_resid++;
+    op.coef = c_L;
+    for (int pass = 0; pass < (plain ? 1 : o.max_refine); ++pass) {
+      int nref = 0;
+      if (bt_status e = read_flag(rf.n_active, nref)) return e;
+      if (nref == 0) break;
+      ctx->st_refine++;
+      L += 2;  // Krylov init and the closing residual / update
+      if (plain) {
+        launch_krylov_init_f64(op, va, ctx->r64.p, ctx->rf_active.p, ctx->x64.p, ctx->rk64.p, ctx->p64.p, ks,
+                               o.tol_fp64, rs_at(1), conj, ctx->sms, st);
+      } else if (df) {
+        launch_krylov_init_f32_df(op, va, ctx->rdf.p, ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p,
+                                  ctx->p32.p, ks, o.tol_inner, rs_at(1), conj, ctx->sms, st);
+      } else {
+        launch_krylov_init_f32(op, va, ctx->r64.p, ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p,
+                               ctx->p32.p, ks, o.tol_inner, rs_at(1), conj, ctx->sms, st);
+      }
+      CKL();
+      for (int it = 0; it < o.max_iter; ++it) {
+        if (plain) {
+          timed(0, [&] {
+            if (narrow) launch_spmm_krylov_f64_narrow(op, ctx->p64.p, ctx->q64.p, ks, rs_at(2), conj, ctx->sms, st);
+            else launch_spmm_krylov_f64(op, ctx->p64.p, ctx->q64.p, ks, rs_at(2), conj, nb, ctx->sms, st);
+          });
+          launch_krylov_update_f64(op, va, ctx->x64.p, ctx->rk64.p, ctx->p64.p, ctx->q64.p, ks, rs_at(3), conj,
+                                   ctx->sms, st);
+          launch_krylov_p_f64(op, va, ctx->rk64.p, ctx->p64.p, ks, ctx->sms, st);
+        } else {
+          timed(0, [&] { launch_spmm_krylov_f32(op, ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb, ctx->sms, st); });
+          launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs_at(3), conj,
+                                   ctx->sms, st);
+          launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st);
+        }
+        CKL();
+        ctx->st_iters++;
+        ctx->st_spmm++;
+        L += 3;
+        if ((it + 1) % o.check_every == 0) {
+          int na = 0;
+          if (bt_status e = read_flag(ks.n_active, na)) return e;
+          if (na == 0) break;
+        }
+      }
+      if (plain) {
+        launch_axpy_u(va, ctx->x64.p, ctx->u64.p, ks, rf, ctx->sms, st);
+        launch_finish_step(rf, ks, Rs, st);
+        L += 1;
+      } else {
+        timed(1, [&] {
+          if (df) launch_resid_sub_df(op, ctx->x32.p, ctx->udf.p, ctx->rdf.p, rf, rs_at(4), nb, ctx->sms, st);
+          else launch_resid_sub(op, ctx->x32.p, ctx->u64.p, ctx->r64.p, rf, rs_at(4), nb, ctx->sms, st);
+        });
+        ctx->st_resid++;
+      }
+      CKL();
+    }
+    if (!plain) {
+      launch_mark_ref_left(rf, ks, Rs, st);
+      L += 1;
+    }
+    ctx->st_steps++;
+  }
+  op.coef = ctx->d_coef.p;
+  if (df) launch_signal_df(va, ctx->d_w.p, ctx->udf.p, ctx->d_S.p, rs_at(5), ctx->sms, st);
+  else launch_signal(va, ctx->d_w.p, ctx->u64.p, ctx->d_S.p, rs_at(5), ctx->sms, st);
+  CKL();
+  L += 1;
+  std::vector<double> S(2 * Rs), err(Rs);
+  std::vector<int> stat(Rs), ref_left(Rs);
+  CK(cudaMemcpyAsync(S.data(), ctx->d_S.p, 2 * Rs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(err.data(), ctx->rf_err.p, Rs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(stat.data(), ctx->ks_status.p, Rs * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ref_left.data(), ctx->rf_active.p, Rs * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (prof) ev_harvest(ctx);
+  bt_status ret = BT_OK;
+  for (int s = 0; s < Rs; ++s) {
+    ctx->S[2 * (rb + s)] = S[2 * s];
+    ctx->S[2 * (rb + s) + 1] = S[2 * s + 1];
+    ctx->err_est[rb + s] = err[s];
+    int stt = stat[s];
+    if (!plain && ref_left[s] && stt == BT_OK) stt = BT_ENOCONV;  // refinement cap hit in the last step
+    ctx->status[rb + s] = stt;
+    if (stt != BT_OK && ret == BT_OK) ret = stt;
+  }
+  if (ret != BT_OK) ctx->err = "bt_run: some right-hand sides did not converge (see status)";
+  return ret;
+}
+
+extern "C" bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t* status) {
+  if (!ctx) return BT_EINVAL;
+  if (ctx->R == 0) return fail(ctx, BT_ESTATE, "bt_get_signals: nothing run");
+  if (S_re_im) std::memcpy(S_re_im, ctx->S.data(), 2 * ctx->R * sizeof(double));
+  if (err_est) std::memcpy(err_est, ctx->err_est.data(), ctx->R * sizeof(double));
+  if (status)
+    for (int i = 0; i < ctx->R; ++i) status[i] = ctx->status[i];
+  return BT_OK;
+}
+
+extern "C" bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters, int64_t* refine_passes,
+                                  int64_t* spmm_launches, double* spmm_ms, double* resid_ms,
+                                  int64_t* resid_launches, int64_t* kernel_launches) {
+  if (!ctx) return BT_EINVAL;
+  if (steps) *steps = ctx->st_steps;
+  if (krylov_iters) *krylov_iters = ctx->st_iters;
+  if (refine_passes) *refine_passes = ctx->st_refine;
+  if (spmm_launches) *spmm_launches = ctx->st_spmm;
+  if (spmm_ms) *spmm_ms = ctx->st_spmm_ms;
+  if (resid_ms) *resid_ms = ctx->st_resid_ms;
+  if (resid_launches) *resid_launches = ctx->st_resid;
+  if (kernel_launches) *kernel_launches = ctx->st_launches;
+  return BT_OK;
+}

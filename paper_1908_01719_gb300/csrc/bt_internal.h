@@ -1,0 +1,86 @@
+// Internal declarations of libbtgpu (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bt.h"
+
+namespace bt {
+
+// ---------------------------------------------------------------- host mesh
+struct HostMesh {
+  // input (copied)
+  int64_t n_nodes = 0, n_tets = 0;
+  int32_t n_cmpt = 0;
+  std::vector<double> xyz;          // 3 n_nodes
+  std::vector<int32_t> tets;        // 4 n_tets
+  std::vector<int32_t> tet_cmpt;    // n_tets
+  std::vector<double> D, kappa;     // n_cmpt
+  uint32_t pmask = 0;
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  // derived on the host
+  std::vector<int32_t> master;      // n_nodes -> master node
+  std::vector<int32_t> tet_dof;     // 4 n_tets
+  std::vector<int32_t> dof_node, dof_cmpt;
+  int64_t n_dof = 0;
+  // interface faces: tet a / tet b, local vertex ids of the face in tet a,
+  // the 6 dofs (3 of side a, then the matching 3 of side b), kappa
+  std::vector<int32_t> face_ta, face_tb;
+  std::vector<int8_t> face_lv;      // 3 nf
+  std::vector<int32_t> face_dof;    // 6 nf
+  std::vector<double> face_kappa;
+  int64_t n_face = 0;
+  // CSR pattern shared by every matrix
+  std::vector<int64_t> row_ptr;     // n_dof + 1
+  std::vector<int32_t> col;         // nnz
+  int64_t nnz = 0;
+  // slot-sorted element contributions: tet entries (t*16 + i*4 + j) and face
+  // entries (f*36 + a*6 + b), each in increasing element order per slot
+  std::vector<int64_t> tc_ptr, fc_ptr;  // nnz + 1
+  std::vector<int32_t> tc, fc;
+};
+
+// Validates and builds everything above; returns BT_OK or BT_EINVAL with msg.
+int build_host_mesh(HostMesh& m, std::string& msg);
+
+// ---------------------------------------------------------------- device helpers
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t alloc(size_t count) {
+    free();
+    n = count;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void**)&p, count * sizeof(T));
+  }
+  void free() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DBuf() { free(); }
+};
+
+// Step coefficients of the generic operator
+//   y_r = a * (P0 x_r) + bq2 * q_r^2 * (P1 x_r) + i * cq * q_r * (sum_k qhat_k P_{2+k}) x_r
+// where P0 is A0 or K+J, P1 the D-weighted mass (transformed frame only) and
+// P2..P4 the direction planes (Mx,My,Mz in the lab frame, Ex,Ey,Ez in the
+// transformed frame).
+struct OpCoef {
+  double a;
+  double bq2;
+  double cq;
+};
+
+// Double-float plane: value = hi + lo, both FP32.
+struct DFPlanes {
+  float* hi = nullptr;
+  float* lo = nullptr;
+};
+
+}  // namespace bt

@@ -1,0 +1,341 @@
+// Kernel argument structures, device helpers and launch wrappers of libbtgpu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bt_internal.h"
+
+namespace bt {
+
+// ---------------------------------------------------------------- assembly
+struct AsmArgs {
+  const double* xyz;
+  const int32_t* tets;
+  const int32_t* cmpt;
+  const double* Dc;
+  double centre[3];
+  int64_t nt, nf, nnz;
+  const int32_t* face_ta;
+  const int8_t* face_lv;
+  const double* face_kappa;
+  const int64_t* tc_ptr;
+  const int32_t* tc;
+  const int64_t* fc_ptr;
+  const int32_t* fc;
+  double* geo;     // 26 nt
+  double* fcoef;   // nf
+  double* planes;  // 10 nnz
+};
+void launch_assembly(const AsmArgs& a, cudaStream_t st);
+
+struct DeriveArgs {
+  const double* planes;
+  int64_t nnz, n;
+  double thdt;
+  int transformed;
+  const int32_t* rp;
+  const int32_t* col;
+  double* A0;
+  double* KJ;
+  double4* pk64;
+  float4* pk32;
+  float* md32;
+  float4* pkhi;
+  float4* pklo;
+  float2* kjmd_hi;
+  float2* kjmd_lo;
+  double* w;
+  double4* diag64;
+  double* diag_md64;
+  float4* diag32;
+  float* diag_md32;
+};
+void launch_derive(const DeriveArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------- solver state
+// Per-system (right-hand side) Krylov scalars, FP64.
+struct KrylovState {
+  double* rho;       // complex rho: [2 * n_sys] (COCG scalars are complex)
+  double* alpha;     // complex alpha: [2 * n_sys]
+  double* beta;      // complex beta:  [2 * n_sys]
+  double* rr0;       // |r_0|^2 of the current solve
+  double* rr;        // |r|^2
+  double* tol2;      // stop when rr <= tol2
+  int* iter;
+  int* active;
+  int* n_active;     // device counter of active systems
+  int* status;       // BT_OK / BT_ENOCONV / BT_ENAN per system
+  double* rr_best;   // smallest |r|^2 seen in the current solve
+  int* it_best;      // iteration at which it was seen
+  int max_iter;
+  int stall;         // > 0: stop a solve after `stall` iterations without a new best
+};
+
+// Per-system refinement scalars.
+struct RefineState {
+  double* r0n2;      // |r_0|^2 of the step
+  double* rk2;       // |r_k|^2
+  double* scale;     // |r_k| used to normalise the inner right-hand side
+  double* err;       // accumulated |r_final| / |r_0|
+  int* active;
+  int* n_active;
+  double tol2;       // tol_ref^2
+  double floor_c2;   // (eps * max w)^2: |r_0|^2 below floor_c2 |u|^2 counts as zero
+};
+
+// Operator description shared by all fused SpMM kernels.
+//   y_r = a (P0 x_r) + bq2 q_r^2 (P1 x_r) + i cq q_r (qhat_d . Pd) x_r
+struct OpArgs {
+  const int32_t* rp;
+  const int32_t* col;
+  int64_t n;
+  const double4* pk64;   // {A0, d0, d1, d2}
+  const double* p0_64;   // P0 override (K + J), or null: P0 = A0
+  const double* p1_64;   // D-weighted mass (transformed frame) or null
+  const float4* pk32;
+  const float* p1_32;
+  const float4* pkhi;    // double-float split of pk64
+  const float4* pklo;
+  const float2* kjmd_hi; // double-float split of (K + J, MD)
+  const float2* kjmd_lo;
+  const OpCoef* coef;    // device, one per segment
+  const double* q;       // [R]
+  const double* qhat;    // [3 R] unit direction of each RHS
+  int R, Rp;
+  int transformed;
+};
+
+struct VecArgs {
+  int64_t n;
+  int R, Rp, nb;
+  const double4* diag64;
+  const double* diag_md64;
+  const float4* diag32;
+  const float* diag_md32;
+};
+
+// partial-sum scratch for the deterministic last-block reductions
+struct RedScratch {
+  double* part;          // [max_blocks * Rp * 4]
+  unsigned int* counter; // one per reduction site
+};
+
+// launch wrappers (k_spmm.cu / k_krylov.cu)
+enum { REDUCE_BLOCKS_PER_SM = 4 };
+int spmm_grid_rows(int64_t n, int sms);
+
+void launch_spmm_krylov_f32(const OpArgs& op, const float2* p, float2* q, const KrylovState& ks,
+                            RedScratch rs, int conj, int nb, int sms, cudaStream_t st);
+void launch_spmm_krylov_f64(const OpArgs& op, const double2* p, double2* q, const KrylovState& ks,
+                            RedScratch rs, int conj, int nb, int sms, cudaStream_t st);
+// r = op_{P0=K+J}(u) with |r|^2, |u|^2 partials; sets refinement state
+void launch_resid0(const OpArgs& op, const double2* u, double2* r, const RefineState& rf, RedScratch rs,
+                   int nb, int sms, cudaStream_t st);
+// u += s d; r -= s op_{P0=A0}(d) with |r|^2 partials; updates refinement state
+void launch_resid_sub(const OpArgs& op, const float2* d, double2* u, double2* r, const RefineState& rf,
+                      RedScratch rs, int nb, int sms, cudaStream_t st);
+// the same two residual kernels in double-float arithmetic (u, r stored as
+// {re_hi, im_hi, re_lo, im_lo} FP32 quadruples)
+void launch_resid0_df(const OpArgs& op, const float4* u, float4* r, const RefineState& rf, RedScratch rs,
+                      int nb, int sms, cudaStream_t st);
+void launch_resid_sub_df(const OpArgs& op, const float2* d, float4* u, float4* r, const RefineState& rf,
+                         RedScratch rs, int nb, int sms, cudaStream_t st);
+void launch_krylov_init_f32_df(const OpArgs& op, const VecArgs& va, const float4* rdf, const double* scale,
+                               const int* ref_active, float2* x, float2* r, float2* p, const KrylovState& ks,
+                               double tol, RedScratch rs, int conj, int sms, cudaStream_t st);
+void launch_signal_df(const VecArgs& va, const double* w, const float4* u, double* S, RedScratch rs, int sms,
+                      cudaStream_t st);
+void launch_fill_u_df(const VecArgs& va, float4* u, cudaStream_t st);
+
+void launch_spmm_krylov_f64_narrow(const OpArgs& op, const double2* p, double2* q, const KrylovState& ks,
+                                   RedScratch rs, int conj, int sms, cudaStream_t st);
+void launch_resid0_narrow(const OpArgs& op, const double2* u, double2* r, const RefineState& rf, RedScratch rs,
+                          int sms, cudaStream_t st);
+void launch_krylov_init_f32(const OpArgs& op, const VecArgs& va, const double2* r64, const double* scale,
+                            const int* ref_active, float2* x, float2* r, float2* p, const KrylovState& ks,
+                            double tol, RedScratch rs, int conj, int sms, cudaStream_t st);
+void launch_krylov_update_f32(const OpArgs& op, const VecArgs& va, float2* x, float2* r, const float2* p,
+                              const float2* q, const KrylovState& ks, RedScratch rs, int conj, int sms,
+                              cudaStream_t st);
+void launch_krylov_p_f32(const OpArgs& op, const VecArgs& va, const float2* r, float2* p, const KrylovState& ks,
+                         int sms, cudaStream_t st);
+
+void launch_krylov_init_f64(const OpArgs& op, const VecArgs& va, const double2* r64, const int* ref_active,
+                            double2* x, double2* r, double2* p, const KrylovState& ks, double tol, RedScratch rs,
+                            int conj, int sms, cudaStream_t st);
+void launch_krylov_update_f64(const OpArgs& op, const VecArgs& va, double2* x, double2* r, const double2* p,
+                              const double2* q, const KrylovState& ks, RedScratch rs, int conj, int sms,
+                              cudaStream_t st);
+void launch_krylov_p_f64(const OpArgs& op, const VecArgs& va, const double2* r, double2* p,
+                         const KrylovState& ks, int sms, cudaStream_t st);
+
+void launch_axpy_u(const VecArgs& va, const double2* d, double2* u, const KrylovState& ks,
+                   const RefineState& rf, int sms, cudaStream_t st);
+void launch_fill_u(const VecArgs& va, double2* u, cudaStream_t st);
+void launch_signal(const VecArgs& va, const double* w, const double2* u, double* S, RedScratch rs, int sms,
+                   cudaStream_t st);
+void launch_set_int(int* p, int v, int n, cudaStream_t st);
+void launch_finish_step(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st);
+void launch_mark_ref_left(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st);
+
+// ---------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// 1/(a + ib)
+__device__ __forceinline__ double2 crcp(double a, double b) {
+  double d = 1.0 / (a * a + b * b);
+  return make_double2(a * d, -b * d);
+}
+__device__ __forceinline__ float2 crcpf(float a, float b) {
+  float d = 1.0f / (a * a + b * b);
+  return make_float2(a * d, -b * d);
+}
+
+// Vector layout.  X is [n][Rp] complex; within each tile of 32*NB columns the
+// column of system (RHS) s = tile*32*NB + l*NB + b is tile*32*NB + b*32 + l, so
+// that lane l of a warp owns the NB consecutive systems of one direction and
+// each of its NB loads is one contiguous 32-lane access.  NB = 1 is the
+// identity.
+__host__ __device__ __forceinline__ int sys_of_col(int c, int nb) {
+  if (nb == 1) return c;
+  const int t = c / (32 * nb), w = c - t * 32 * nb;
+  return t * 32 * nb + (w & 31) * nb + (w >> 5);
+}
+__host__ __device__ __forceinline__ int col_of_sys(int s, int nb) {
+  if (nb == 1) return s;
+  const int t = s / (32 * nb), w = s - t * 32 * nb;
+  return t * 32 * nb + (w % nb) * 32 + w / nb;
+}
+
+// read-only 32-byte / 16-byte plane loads
+__device__ __forceinline__ double4 ldg4(const double4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+
+// Last-block-done: every block stores its partials, then the block that
+// arrives last (atomic ticket, no waiting) reduces them in a fixed order.
+__device__ __forceinline__ bool last_block(unsigned int* counter, unsigned int nblocks) {
+  __shared__ unsigned int s_ticket;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  bool last = (s_ticket == nblocks - 1);
+  if (last) {
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;  // ready for the next launch
+  }
+  return last;
+}
+// the NB values of one lane: base points at column tile*32*NB + lane
+template <int NB, class T2>
+__device__ __forceinline__ void load_x(const T2* __restrict__ p, T2 (&x)[NB]) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b) x[b] = __ldg(p + 32 * b);
+}
+
+// per-lane constants of the operator
+template <int NB>
+struct LaneCoef {
+  double qx, qy, qz;
+  double b[NB], c[NB];
+  double a;
+  int act[NB];
+};
+
+template <int NB>
+__device__ __forceinline__ void lane_coef(const OpArgs& op, int r0, const int* active, LaneCoef<NB>& lc) {
+  const OpCoef cf = op.coef[0];
+  lc.a = cf.a;
+  // the NB RHS of a lane share one direction (the host picks NB accordingly)
+  const int d = r0 < op.R ? r0 : 0;
+  lc.qx = op.qhat[3 * d];
+  lc.qy = op.qhat[3 * d + 1];
+  lc.qz = op.qhat[3 * d + 2];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    int r = r0 + b;
+    double q = r < op.R ? op.q[r] : 0.0;
+    lc.b[b] = cf.bq2 * q * q;
+    lc.c[b] = cf.cq * q;
+    lc.act[b] = (r < op.R) && (active == nullptr || active[r]);
+  }
+}
+
+// Reduce per-lane complex partials of NB RHS over the warps of the block and
+// write them to part[blockIdx.x][r] (2 doubles per r).
+template <int NB>
+__device__ __forceinline__ void block_partials(double2 (&acc)[NB], int r0, int Rp, double* part) {
+  __shared__ double2 sm[8][32][NB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) sm[warp][lane][b] = acc[b];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      double2 s = make_double2(0, 0);
+      for (int w = 0; w < W; ++w) {
+        s.x += sm[w][lane][b].x;
+        s.y += sm[w][lane][b].y;
+      }
+      int r = r0 + b;
+      if (r < Rp) reinterpret_cast<double2*>(part)[(size_t)blockIdx.x * Rp + r] = s;
+    }
+  }
+}
+
+// Sum part[0..nbx)[s] for s < R in a fixed order; callback per s.
+template <class F>
+__device__ __forceinline__ void reduce_partials(const double* part, int nbx, int Rp, int R, F&& fn) {
+  for (int s = threadIdx.x; s < R; s += blockDim.x) {
+    double2 t = make_double2(0, 0);
+    for (int b = 0; b < nbx; ++b) {
+      double2 v = __ldcg(reinterpret_cast<const double2*>(part) + (size_t)b * Rp + s);
+      t.x += v.x;
+      t.y += v.y;
+    }
+    fn(s, t);
+  }
+}
+
+
+// Refinement bookkeeping of system s after a residual launch (last block).
+// mode 0: step start, t = (|r_0|^2, |u|^2); mode 1: after a correction, t.x = |r|^2.
+__device__ __forceinline__ void refine_finish(int mode, const RefineState& rf, int s, double2 t) {
+  if (!rf.active[s]) return;
+  if (mode == 0) {
+    rf.r0n2[s] = t.x;
+    rf.rk2[s] = t.x;
+    rf.scale[s] = (double)(float)sqrt(t.x);  // FP32-exact: the same number scales and unscales
+    if (!isfinite(t.x) || !(t.x > rf.floor_c2 * t.y)) {
+      // nothing to solve: the increment is zero to FP64 rounding (or not finite)
+      rf.active[s] = 0;
+      atomicSub(rf.n_active, 1);
+    }
+  } else {
+    const double prev = rf.rk2[s];
+    rf.rk2[s] = t.x;
+    rf.scale[s] = (double)(float)sqrt(t.x);
+    // converged, or stagnated: a pass that no longer halves the residual has
+    // reached the rounding floor of the residual arithmetic; the achieved
+    // relative residual is what err_est reports
+    if (!(t.x > rf.tol2 * rf.r0n2[s]) || t.x > 0.25 * prev) {
+      rf.err[s] += sqrt(t.x / rf.r0n2[s]);
+      rf.active[s] = 0;
+      atomicSub(rf.n_active, 1);
+    }
+  }
+}
+#endif
+
+}  // namespace bt

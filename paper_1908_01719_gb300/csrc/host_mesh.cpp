@@ -1,0 +1,366 @@
+// Host-side mesh pipeline: validation, periodic identification, interface-node
+// doubling, interface faces, the shared CSR pattern and the slot-sorted
+// element-contribution lists used by the deterministic assembly kernels.
+//
+// Paper: PUFEM with one nodal copy per compartment (Appendix A, Eq. phase_func
+// and the broken inner product (.,.)_{Omega_0 u Omega_1}); interface jump term
+// kappa <[U],[v]> (Appendix B, Eq. loadvec); master-slave periodicity
+// (Section 2, Eq. btpde_bc).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+
+#include "bt_internal.h"
+
+namespace bt {
+namespace {
+
+template <class F>
+void parallel_for(int64_t n, F&& fn) {
+  unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  int64_t nt = std::min<int64_t>(hw, std::max<int64_t>(1, n / 4096));
+  if (nt <= 1) {
+    fn(int64_t(0), n);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (n + nt - 1) / nt;
+  for (int64_t t = 0; t < nt; ++t) {
+    int64_t b = t * chunk, e = std::min(n, b + chunk);
+    if (b >= e) break;
+    th.emplace_back([&fn, b, e] { fn(b, e); });
+  }
+  for (auto& x : th) x.join();
+}
+
+double signed_volume(const double* a, const double* b, const double* c, const double* d) {
+  double e1[3], e2[3], e3[3];
+  for (int k = 0; k < 3; ++k) {
+    e1[k] = b[k] - a[k];
+    e2[k] = c[k] - a[k];
+    e3[k] = d[k] - a[k];
+  }
+  double cx = e1[1] * e2[2] - e1[2] * e2[1];
+  double cy = e1[2] * e2[0] - e1[0] * e2[2];
+  double cz = e1[0] * e2[1] - e1[1] * e2[0];
+  return (cx * e3[0] + cy * e3[1] + cz * e3[2]) / 6.0;
+}
+
+int validate(const HostMesh& m, std::string& msg) {
+  if (m.n_nodes <= 0 || m.n_tets <= 0 || m.n_cmpt <= 0) {
+    msg = "empty mesh";
+    return BT_EINVAL;
+  }
+  if (m.n_nodes >= (int64_t(1) << 31) || m.n_tets * 16 >= (int64_t(1) << 31)) {
+    msg = "mesh too large for 32-bit element indexing";
+    return BT_EINVAL;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (!(m.hi[k] > m.lo[k]) || !std::isfinite(m.lo[k]) || !std::isfinite(m.hi[k])) {
+      msg = "box_hi must exceed box_lo";
+      return BT_EINVAL;
+    }
+  for (int32_t c = 0; c < m.n_cmpt; ++c) {
+    if (!(m.D[c] >= 0.0) || !std::isfinite(m.D[c])) {
+      msg = "D_cmpt must be finite and >= 0";
+      return BT_EINVAL;
+    }
+    if (!(m.kappa[c] >= 0.0)) {  // +inf allowed, NaN rejected
+      msg = "kappa_cmpt must be >= 0 (inf = no membrane)";
+      return BT_EINVAL;
+    }
+  }
+  for (int64_t i = 0; i < 3 * m.n_nodes; ++i)
+    if (!std::isfinite(m.xyz[i])) {
+      msg = "non-finite node coordinate";
+      return BT_EINVAL;
+    }
+  for (int64_t t = 0; t < m.n_tets; ++t) {
+    const int32_t* v = &m.tets[4 * t];
+    for (int a = 0; a < 4; ++a)
+      if (v[a] < 0 || v[a] >= m.n_nodes) {
+        msg = "tetrahedron " + std::to_string(t) + " has a node id out of range";
+        return BT_EINVAL;
+      }
+    if (m.tet_cmpt[t] < 0 || m.tet_cmpt[t] >= m.n_cmpt) {
+      msg = "tetrahedron " + std::to_string(t) + " has a compartment id out of range";
+      return BT_EINVAL;
+    }
+    double vol = signed_volume(&m.xyz[3 * v[0]], &m.xyz[3 * v[1]], &m.xyz[3 * v[2]], &m.xyz[3 * v[3]]);
+    if (!(vol > 0.0)) {
+      msg = "tetrahedron " + std::to_string(t) + " is degenerate or inverted (signed volume " +
+            std::to_string(vol) + ")";
+      return BT_EINVAL;
+    }
+  }
+  return BT_OK;
+}
+
+// Master node of every node: on a periodic axis, a node on the high face is
+// the node on the low face with equal other coordinates; the master of a
+// group of identified nodes is its smallest index.
+int periodic_identify(HostMesh& m, std::string& msg) {
+  const int64_t n = m.n_nodes;
+  m.master.resize(n);
+  std::iota(m.master.begin(), m.master.end(), 0);
+  if (m.pmask == 0) return BT_OK;
+  double ext = 0;
+  for (int k = 0; k < 3; ++k) ext = std::max(ext, m.hi[k] - m.lo[k]);
+  const double tol = 1e-9 * ext;
+  std::vector<std::array<int64_t, 3>> key(n);
+  int64_t n_hi = 0, n_lo = 0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      double x = m.xyz[3 * i + k];
+      if ((m.pmask >> k) & 1u) {
+        if (std::fabs(x - m.hi[k]) < tol) {
+          x = m.lo[k];
+          ++n_hi;
+        } else if (std::fabs(x - m.lo[k]) < tol) {
+          ++n_lo;
+        }
+      }
+      key[i][k] = (int64_t)std::llround(x / tol);
+    }
+  if (n_hi != n_lo) {
+    msg = "periodic faces do not match (different node counts on the low and high faces)";
+    return BT_EINVAL;
+  }
+  std::vector<int32_t> ord(n);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+    return key[a] != key[b] ? key[a] < key[b] : a < b;
+  });
+  int64_t i = 0;
+  while (i < n) {
+    int64_t j = i + 1;
+    while (j < n && key[ord[j]] == key[ord[i]]) ++j;
+    for (int64_t k = i; k < j; ++k) m.master[ord[k]] = ord[i];  // ord[i] is the smallest index
+    i = j;
+  }
+  return BT_OK;
+}
+
+// One dof per (master node, compartment) pair present in some tetrahedron of
+// that compartment, numbered in increasing (node, compartment) order.
+void double_interface_nodes(HostMesh& m) {
+  const int64_t n = m.n_nodes;
+  std::vector<int32_t> first(n, -1);
+  std::vector<std::pair<int32_t, int32_t>> extra;
+  for (int64_t t = 0; t < m.n_tets; ++t) {
+    int32_t c = m.tet_cmpt[t];
+    for (int a = 0; a < 4; ++a) {
+      int32_t v = m.master[m.tets[4 * t + a]];
+      if (first[v] < 0)
+        first[v] = c;
+      else if (first[v] != c)
+        extra.emplace_back(v, c);
+    }
+  }
+  std::sort(extra.begin(), extra.end());
+  extra.erase(std::unique(extra.begin(), extra.end()), extra.end());
+  // per node: sorted list of its compartments
+  std::vector<int64_t> base(n + 1, 0);
+  std::vector<int32_t> cnt(n, 0);
+  for (int64_t v = 0; v < n; ++v) cnt[v] = first[v] >= 0 ? 1 : 0;
+  for (auto& e : extra) cnt[e.first]++;
+  for (int64_t v = 0; v < n; ++v) base[v + 1] = base[v] + cnt[v];
+  m.n_dof = base[n];
+  m.dof_node.resize(m.n_dof);
+  m.dof_cmpt.resize(m.n_dof);
+  size_t ei = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    if (cnt[v] == 0) continue;
+    int32_t* cl = &m.dof_cmpt[base[v]];
+    int k = 0;
+    cl[k++] = first[v];
+    while (ei < extra.size() && extra[ei].first == v) cl[k++] = extra[ei++].second;
+    std::sort(cl, cl + k);
+    for (int j = 0; j < k; ++j) m.dof_node[base[v] + j] = (int32_t)v;
+  }
+  m.tet_dof.resize(4 * m.n_tets);
+  parallel_for(m.n_tets, [&](int64_t b, int64_t e) {
+    for (int64_t t = b; t < e; ++t) {
+      int32_t c = m.tet_cmpt[t];
+      for (int a = 0; a < 4; ++a) {
+        int32_t v = m.master[m.tets[4 * t + a]];
+        int64_t d = base[v];
+        while (m.dof_cmpt[d] != c) ++d;
+        m.tet_dof[4 * t + a] = (int32_t)d;
+      }
+    }
+  });
+}
+
+// Faces shared by two tetrahedra of different compartments.  Only faces whose
+// three (master) vertices all carry more than one dof can be interface faces.
+void find_interface_faces(HostMesh& m) {
+  std::vector<uint8_t> multi(m.n_nodes, 0);
+  for (int64_t d = 1; d < m.n_dof; ++d)
+    if (m.dof_node[d] == m.dof_node[d - 1]) multi[m.dof_node[d]] = 1;
+  static const int LOC[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  struct Cand {
+    std::array<int32_t, 3> key;
+    int32_t tet;
+    int8_t lf;
+  };
+  std::vector<Cand> cand;
+  for (int64_t t = 0; t < m.n_tets; ++t) {
+    for (int f = 0; f < 4; ++f) {
+      std::array<int32_t, 3> k;
+      bool ok = true;
+      for (int a = 0; a < 3; ++a) {
+        k[a] = m.master[m.tets[4 * t + LOC[f][a]]];
+        ok = ok && multi[k[a]];
+      }
+      if (!ok) continue;
+      std::sort(k.begin(), k.end());
+      cand.push_back({k, (int32_t)t, (int8_t)f});
+    }
+  }
+  std::sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+    return a.key != b.key ? a.key < b.key : a.tet < b.tet;
+  });
+  m.face_ta.clear();
+  m.face_tb.clear();
+  m.face_lv.clear();
+  m.face_dof.clear();
+  m.face_kappa.clear();
+  for (size_t i = 0; i + 1 < cand.size(); ++i) {
+    if (cand[i].key != cand[i + 1].key) continue;
+    int32_t ta = cand[i].tet, tb = cand[i + 1].tet;
+    int32_t ca = m.tet_cmpt[ta], cb = m.tet_cmpt[tb];
+    if (ca == cb) continue;
+    m.face_ta.push_back(ta);
+    m.face_tb.push_back(tb);
+    int32_t dofs[6];
+    for (int a = 0; a < 3; ++a) {
+      int la = LOC[cand[i].lf][a];
+      m.face_lv.push_back((int8_t)la);
+      dofs[a] = m.tet_dof[4 * ta + la];
+      int32_t v = m.master[m.tets[4 * ta + la]];
+      int lb = 0;
+      while (m.master[m.tets[4 * tb + lb]] != v) ++lb;
+      dofs[3 + a] = m.tet_dof[4 * tb + lb];
+    }
+    for (int a = 0; a < 6; ++a) m.face_dof.push_back(dofs[a]);
+    double inv = 1.0 / m.kappa[ca] + 1.0 / m.kappa[cb];  // 1/inf = 0
+    m.face_kappa.push_back(inv > 0 ? 1.0 / inv : INFINITY);
+  }
+  m.n_face = (int64_t)m.face_ta.size();
+}
+
+void build_pattern(HostMesh& m) {
+  const int64_t nd = m.n_dof, nt = m.n_tets, nf = m.n_face;
+  // dof -> elements incidence (tets, then faces)
+  std::vector<int64_t> tp(nd + 1, 0), fp(nd + 1, 0);
+  for (int64_t i = 0; i < 4 * nt; ++i) tp[m.tet_dof[i] + 1]++;
+  for (int64_t i = 0; i < 6 * nf; ++i) fp[m.face_dof[i] + 1]++;
+  for (int64_t d = 0; d < nd; ++d) {
+    tp[d + 1] += tp[d];
+    fp[d + 1] += fp[d];
+  }
+  std::vector<int32_t> ti(4 * nt), fi(6 * nf);
+  {
+    std::vector<int64_t> pos(tp.begin(), tp.end() - 1);
+    for (int64_t t = 0; t < nt; ++t)
+      for (int a = 0; a < 4; ++a) ti[pos[m.tet_dof[4 * t + a]]++] = (int32_t)t;
+    std::vector<int64_t> pf(fp.begin(), fp.end() - 1);
+    for (int64_t f = 0; f < nf; ++f)
+      for (int a = 0; a < 6; ++a) fi[pf[m.face_dof[6 * f + a]]++] = (int32_t)f;
+  }
+  auto row_cols = [&](int64_t d, std::vector<int32_t>& buf) {
+    buf.clear();
+    for (int64_t k = tp[d]; k < tp[d + 1]; ++k)
+      for (int a = 0; a < 4; ++a) buf.push_back(m.tet_dof[4 * (int64_t)ti[k] + a]);
+    for (int64_t k = fp[d]; k < fp[d + 1]; ++k)
+      for (int a = 0; a < 6; ++a) buf.push_back(m.face_dof[6 * (int64_t)fi[k] + a]);
+    std::sort(buf.begin(), buf.end());
+    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+  };
+  std::vector<int64_t> len(nd);
+  parallel_for(nd, [&](int64_t b, int64_t e) {
+    std::vector<int32_t> buf;
+    for (int64_t d = b; d < e; ++d) {
+      row_cols(d, buf);
+      len[d] = (int64_t)buf.size();
+    }
+  });
+  m.row_ptr.assign(nd + 1, 0);
+  for (int64_t d = 0; d < nd; ++d) m.row_ptr[d + 1] = m.row_ptr[d] + len[d];
+  m.nnz = m.row_ptr[nd];
+  m.col.resize(m.nnz);
+  parallel_for(nd, [&](int64_t b, int64_t e) {
+    std::vector<int32_t> buf;
+    for (int64_t d = b; d < e; ++d) {
+      row_cols(d, buf);
+      std::copy(buf.begin(), buf.end(), m.col.begin() + m.row_ptr[d]);
+    }
+  });
+}
+
+inline int64_t slot_of(const HostMesh& m, int32_t r, int32_t c) {
+  const int32_t* b = m.col.data() + m.row_ptr[r];
+  const int32_t* e = m.col.data() + m.row_ptr[r + 1];
+  return m.row_ptr[r] + (std::lower_bound(b, e, c) - b);
+}
+
+// Counting sort of element entries by slot; within a slot the entries keep
+// increasing element order, so the per-slot sums are deterministic.
+void build_contributions(HostMesh& m) {
+  const int64_t nt = m.n_tets, nf = m.n_face, nnz = m.nnz;
+  std::vector<int64_t> tslot(16 * nt);
+  parallel_for(nt, [&](int64_t b, int64_t e) {
+    for (int64_t t = b; t < e; ++t)
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+          tslot[16 * t + 4 * i + j] = slot_of(m, m.tet_dof[4 * t + i], m.tet_dof[4 * t + j]);
+  });
+  m.tc_ptr.assign(nnz + 1, 0);
+  for (int64_t k = 0; k < 16 * nt; ++k) m.tc_ptr[tslot[k] + 1]++;
+  for (int64_t s = 0; s < nnz; ++s) m.tc_ptr[s + 1] += m.tc_ptr[s];
+  m.tc.resize(16 * nt);
+  {
+    std::vector<int64_t> pos(m.tc_ptr.begin(), m.tc_ptr.end() - 1);
+    for (int64_t k = 0; k < 16 * nt; ++k) m.tc[pos[tslot[k]]++] = (int32_t)k;
+  }
+  std::vector<int64_t>().swap(tslot);
+  m.fc_ptr.assign(nnz + 1, 0);
+  std::vector<int64_t> fslot(36 * nf);
+  for (int64_t f = 0; f < nf; ++f)
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b)
+        fslot[36 * f + 6 * a + b] = slot_of(m, m.face_dof[6 * f + a], m.face_dof[6 * f + b]);
+  for (int64_t k = 0; k < 36 * nf; ++k) m.fc_ptr[fslot[k] + 1]++;
+  for (int64_t s = 0; s < nnz; ++s) m.fc_ptr[s + 1] += m.fc_ptr[s];
+  m.fc.resize(36 * nf);
+  std::vector<int64_t> pos(m.fc_ptr.begin(), m.fc_ptr.end() - 1);
+  for (int64_t k = 0; k < 36 * nf; ++k) m.fc[pos[fslot[k]]++] = (int32_t)k;
+}
+
+}  // namespace
+
+int build_host_mesh(HostMesh& m, std::string& msg) {
+  int st = validate(m, msg);
+  if (st) return st;
+  st = periodic_identify(m, msg);
+  if (st) return st;
+  double_interface_nodes(m);
+  find_interface_faces(m);
+  if (m.nnz >= (int64_t(1) << 31)) {
+    msg = "pattern too large";
+    return BT_EINVAL;
+  }
+  build_pattern(m);
+  if (m.nnz >= (int64_t(1) << 31) || 36 * m.n_face >= (int64_t(1) << 31)) {
+    msg = "pattern too large for 32-bit indexing";
+    return BT_EINVAL;
+  }
+  build_contributions(m);
+  return BT_OK;
+}
+
+}  // namespace bt

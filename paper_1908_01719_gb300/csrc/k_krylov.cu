@@ -1,0 +1,513 @@
+// Batched Krylov vector kernels: every right-hand side (system) has its own
+// scalars, convergence test and freeze mask.  Lab frame: COCG (the step matrix
+// is complex symmetric, unconjugated inner products); transformed frame: CG
+// (the step matrix is Hermitian positive definite).  Jacobi preconditioner
+// z = diag(L_n)^-1 r with diag(L_n) = A0_ii + b_s MD_ii + i c_s (qhat.Pd)_ii
+// formed on the fly.  Inner products: FP32 products summed over at most 32
+// rows per thread, all further accumulation in FP64, and the block partials
+// reduced by the last block in a fixed order (deterministic).
+#include "bt_kernels.cuh"
+
+namespace bt {
+
+// thread -> fixed set of RHS columns, rows strided by rows_per_pass
+struct ElemMap {
+  int RS, rpp, NK;
+  __device__ ElemMap(int Rp) {
+    RS = Rp < 256 ? Rp : 256;
+    rpp = 256 / RS;
+    NK = (Rp + 255) / 256;
+  }
+};
+constexpr int EM_NK = 4;  // Rp <= 1024
+
+// diag(L) for system s at row i (FP32 / FP64)
+__device__ __forceinline__ float2 diag_f32(const VecArgs& va, const OpArgs& op, int64_t i, float b, float c,
+                                           float qx, float qy, float qz) {
+  float4 d = va.diag32[i];
+  float re = d.x;
+  if (op.transformed) re = fmaf(b, va.diag_md32[i], re);
+  float im = c * (qx * d.y + qy * d.z + qz * d.w);
+  return make_float2(re, im);
+}
+__device__ __forceinline__ double2 diag_f64(const VecArgs& va, const OpArgs& op, int64_t i, double b, double c,
+                                            double qx, double qy, double qz) {
+  double4 d = va.diag64[i];
+  double re = d.x;
+  if (op.transformed) re = fma(b, va.diag_md64[i], re);
+  double im = c * (qx * d.y + qy * d.z + qz * d.w);
+  return make_double2(re, im);
+}
+
+struct SysCoef {
+  double b, c, qx, qy, qz;
+};
+__device__ __forceinline__ SysCoef sys_coef(const OpArgs& op, int s) {
+  const OpCoef cf = op.coef[0];
+  double q = op.q[s];
+  SysCoef sc;
+  sc.b = cf.bq2 * q * q;
+  sc.c = cf.cq * q;
+  sc.qx = op.qhat[3 * s];
+  sc.qy = op.qhat[3 * s + 1];
+  sc.qz = op.qhat[3 * s + 2];
+  return sc;
+}
+
+// Reduce per-thread partials (NC complex pairs per RHS column) to
+// part[blockIdx.x][r][NC] and return whether this block is the last one.
+template <int NC>
+__device__ bool elem_block_reduce(double2 (&acc)[EM_NK][NC], const ElemMap& em, int Rp, int nb, double* part,
+                                  unsigned int* counter) {
+  __shared__ double2 sm[256][NC];
+  const int t = threadIdx.x;
+  if (em.NK == 1) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sm[t][c] = acc[0][c];
+    __syncthreads();
+    if (t < em.RS) {
+      for (int c = 0; c < NC; ++c) {
+        double2 s = make_double2(0, 0);
+        for (int o = 0; o < em.rpp; ++o) {
+          s.x += sm[o * em.RS + t][c].x;
+          s.y += sm[o * em.RS + t][c].y;
+        }
+        reinterpret_cast<double2*>(part)[((size_t)blockIdx.x * Rp + sys_of_col(t, nb)) * NC + c] = s;
+      }
+    }
+  } else {
+    for (int k = 0; k < em.NK; ++k) {
+      int r = t + 256 * k;
+      if (r < Rp)
+        for (int c = 0; c < NC; ++c)
+          reinterpret_cast<double2*>(part)[((size_t)blockIdx.x * Rp + sys_of_col(r, nb)) * NC + c] = acc[k][c];
+    }
+  }
+  return last_block(counter, gridDim.x);
+}
+
+template <int NC>
+__device__ __forceinline__ void sum_part(const double* part, int nbx, int Rp, int s, double2 (&out)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c] = make_double2(0, 0);
+  for (int b = 0; b < nbx; ++b)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double2 v = __ldcg(reinterpret_cast<const double2*>(part) + ((size_t)b * Rp + s) * NC + c);
+      out[c].x += v.x;
+      out[c].y += v.y;
+    }
+}
+
+static int elem_grid(int64_t n, int sms) {
+  int64_t g = (int64_t)sms * REDUCE_BLOCKS_PER_SM;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, n));
+}
+
+// load the refinement residual (FP64 or double-float) of one element
+__device__ __forceinline__ double2 load_res(const double2* p, size_t e) { return p[e]; }
+__device__ __forceinline__ double2 load_res(const float4* p, size_t e) {
+  float4 v = p[e];
+  return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+
+// ---------------------------------------------------------------- init
+// r = r_res / scale_s, x = 0, z = r / diag, p = z; rho = <r, z>, |r|^2.
+template <class T, class T2, class TR, bool CONJ>
+__global__ void __launch_bounds__(256) k_krylov_init(OpArgs op, VecArgs va, const TR* __restrict__ rres,
+                                                     const double* __restrict__ scale, const int* __restrict__ ref_active,
+                                                     T2* __restrict__ x, T2* __restrict__ r, T2* __restrict__ p,
+                                                     KrylovState ks, double tol, RedScratch rs) {
+  ElemMap em(va.Rp);
+  const int t = threadIdx.x;
+  const bool live = t < em.rpp * em.RS;
+  const int rr = t % em.RS, ro = t / em.RS;
+  double2 acc[EM_NK][2];
+  for (int k = 0; k < EM_NK; ++k) acc[k][0] = acc[k][1] = make_double2(0, 0);
+  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
+  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  if (live) {
+    for (int k = 0; k < em.NK; ++k) {
+      const int col = rr + 256 * k;
+      if (col >= va.Rp) continue;
+      const int s = sys_of_col(col, va.nb);
+      if (s >= va.R) continue;
+      const bool act = ref_active[s] != 0;
+      const SysCoef sc = sys_coef(op, s);
+      const double inv = (scale && act && scale[s] > 0) ? 1.0 / scale[s] : 1.0;
+      T2 ar = {0, 0}, an = {0, 0};
+      int cnt = 0;
+      for (int64_t i = rb + ro; i < re; i += em.rpp) {
+        const size_t e = (size_t)i * va.Rp + col;
+        T2 rv = {0, 0};
+        if (act) {
+          double2 v = load_res(rres, e);
+          rv.x = (T)(v.x * inv);
+          rv.y = (T)(v.y * inv);
+        }
+        T2 z = {0, 0};
+        if (act) {
+          T2 d;
+          if constexpr (sizeof(T) == 4) {
+            float2 df = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
+            d.x = df.x; d.y = df.y;
+          } else {
+            double2 dd = diag_f64(va, op, i, sc.b, sc.c, sc.qx, sc.qy, sc.qz);
+            d.x = dd.x; d.y = dd.y;
+          }
+          T den = (T)1 / (d.x * d.x + d.y * d.y);
+          z.x = (rv.x * d.x + rv.y * d.y) * den;
+          z.y = (rv.y * d.x - rv.x * d.y) * den;
+        }
+        r[e] = rv;
+        p[e] = z;
+        x[e] = T2{0, 0};
+        T2 rc = rv;
+        if constexpr (CONJ) rc.y = -rc.y;
+        ar.x += rc.x * z.x - rc.y * z.y;
+        ar.y += rc.x * z.y + rc.y * z.x;
+        an.x += rv.x * rv.x + rv.y * rv.y;
+        if (++cnt == 32) {
+          cnt = 0;
+          acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
+          ar = T2{0, 0}; an = T2{0, 0};
+        }
+      }
+      acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
+    }
+  }
+  if (!elem_block_reduce<2>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
+  __shared__ int s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < va.R; s += blockDim.x) {
+    double2 o[2];
+    sum_part<2>(rs.part, gridDim.x, va.Rp, s, o);
+    ks.rho[2 * s] = o[0].x;
+    ks.rho[2 * s + 1] = o[0].y;
+    ks.rr0[s] = o[1].x;
+    ks.rr[s] = o[1].x;
+    ks.tol2[s] = tol * tol * o[1].x;
+    ks.iter[s] = 0;
+    ks.rr_best[s] = o[1].x;
+    ks.it_best[s] = 0;
+    int a = ref_active[s] && o[1].x > 0;
+    if (ref_active[s] && !isfinite(o[1].x)) {
+      a = 0;
+      ks.status[s] = BT_ENAN;
+    }
+    ks.active[s] = a;
+    if (a) atomicAdd(&s_cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ks.n_active = s_cnt;
+}
+
+// ---------------------------------------------------------------- update
+// x += alpha p; r -= alpha q; z = r / diag; rho' = <r, z>, |r|^2; the last
+// block applies the convergence test and forms beta = rho'/rho.
+template <class T, class T2, bool CONJ>
+__global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2* __restrict__ x,
+                                                       T2* __restrict__ r, const T2* __restrict__ p,
+                                                       const T2* __restrict__ q, KrylovState ks, RedScratch rs) {
+  if (*ks.n_active == 0) return;
+  ElemMap em(va.Rp);
+  const int t = threadIdx.x;
+  const bool live = t < em.rpp * em.RS;
+  const int rr = t % em.RS, ro = t / em.RS;
+  double2 acc[EM_NK][2];
+  for (int k = 0; k < EM_NK; ++k) acc[k][0] = acc[k][1] = make_double2(0, 0);
+  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
+  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  if (live) {
+    for (int k = 0; k < em.NK; ++k) {
+      const int col = rr + 256 * k;
+      if (col >= va.Rp) continue;
+      const int s = sys_of_col(col, va.nb);
+      if (s >= va.R || !ks.active[s]) continue;
+      const SysCoef sc = sys_coef(op, s);
+      const T axr = (T)ks.alpha[2 * s], axi = (T)ks.alpha[2 * s + 1];
+      T2 ar = {0, 0}, an = {0, 0};
+      int cnt = 0;
+      for (int64_t i = rb + ro; i < re; i += em.rpp) {
+        const size_t e = (size_t)i * va.Rp + col;
+        T2 pv = p[e], qv = q[e], xv = x[e], rv = r[e];
+        xv.x += axr * pv.x - axi * pv.y;
+        xv.y += axr * pv.y + axi * pv.x;
+        rv.x -= axr * qv.x - axi * qv.y;
+        rv.y -= axr * qv.y + axi * qv.x;
+        x[e] = xv;
+        r[e] = rv;
+        T2 d;
+        if constexpr (sizeof(T) == 4) {
+          float2 df = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
+          d.x = df.x; d.y = df.y;
+        } else {
+          double2 dd = diag_f64(va, op, i, sc.b, sc.c, sc.qx, sc.qy, sc.qz);
+          d.x = dd.x; d.y = dd.y;
+        }
+        T den = (T)1 / (d.x * d.x + d.y * d.y);
+        T2 z;
+        z.x = (rv.x * d.x + rv.y * d.y) * den;
+        z.y = (rv.y * d.x - rv.x * d.y) * den;
+        T2 rc = rv;
+        if constexpr (CONJ) rc.y = -rc.y;
+        ar.x += rc.x * z.x - rc.y * z.y;
+        ar.y += rc.x * z.y + rc.y * z.x;
+        an.x += rv.x * rv.x + rv.y * rv.y;
+        if (++cnt == 32) {
+          cnt = 0;
+          acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
+          ar = T2{0, 0}; an = T2{0, 0};
+        }
+      }
+      acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
+    }
+  }
+  if (!elem_block_reduce<2>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
+  __shared__ int s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < va.R; s += blockDim.x) {
+    if (!ks.active[s]) continue;
+    double2 o[2];
+    sum_part<2>(rs.part, gridDim.x, va.Rp, s, o);
+    ks.rr[s] = o[1].x;
+    int it = ++ks.iter[s];
+    if (!isfinite(o[1].x) || !isfinite(o[0].x) || !isfinite(o[0].y)) {
+      ks.active[s] = 0;
+      ks.status[s] = BT_ENAN;
+      continue;
+    }
+    if (o[1].x <= ks.tol2[s]) {
+      ks.active[s] = 0;
+      continue;
+    }
+    if (o[1].x < ks.rr_best[s]) {
+      ks.rr_best[s] = o[1].x;
+      ks.it_best[s] = it;
+    } else if (ks.stall > 0 && it - ks.it_best[s] >= ks.stall) {
+      // the FP32 recurrence has stagnated: hand back to the refinement loop
+      ks.active[s] = 0;
+      continue;
+    }
+    if (it >= ks.max_iter) {
+      ks.active[s] = 0;
+      ks.status[s] = BT_ENOCONV;
+      continue;
+    }
+    // beta = rho' / rho (complex)
+    double2 rho = make_double2(ks.rho[2 * s], ks.rho[2 * s + 1]);
+    double den = rho.x * rho.x + rho.y * rho.y;
+    if (!(den > 0)) {
+      ks.active[s] = 0;
+      ks.status[s] = BT_ENOCONV;
+      continue;
+    }
+    ks.beta[2 * s] = (o[0].x * rho.x + o[0].y * rho.y) / den;
+    ks.beta[2 * s + 1] = (o[0].y * rho.x - o[0].x * rho.y) / den;
+    ks.rho[2 * s] = o[0].x;
+    ks.rho[2 * s + 1] = o[0].y;
+    atomicAdd(&s_cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ks.n_active = s_cnt;
+}
+
+// p = z + beta p for active systems (z recomputed from r)
+template <class T, class T2>
+__global__ void __launch_bounds__(256) k_krylov_p(OpArgs op, VecArgs va, const T2* __restrict__ r,
+                                                  T2* __restrict__ p, KrylovState ks) {
+  if (*ks.n_active == 0) return;
+  ElemMap em(va.Rp);
+  const int t = threadIdx.x;
+  if (t >= em.rpp * em.RS) return;
+  const int rr = t % em.RS, ro = t / em.RS;
+  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
+  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  for (int k = 0; k < em.NK; ++k) {
+    const int col = rr + 256 * k;
+    if (col >= va.Rp) continue;
+    const int s = sys_of_col(col, va.nb);
+    if (s >= va.R || !ks.active[s]) continue;
+    const SysCoef sc = sys_coef(op, s);
+    const T br = (T)ks.beta[2 * s], bi = (T)ks.beta[2 * s + 1];
+    for (int64_t i = rb + ro; i < re; i += em.rpp) {
+      const size_t e = (size_t)i * va.Rp + col;
+      T2 rv = r[e], pv = p[e];
+      T2 d;
+      if constexpr (sizeof(T) == 4) {
+        float2 df = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
+        d.x = df.x; d.y = df.y;
+      } else {
+        double2 dd = diag_f64(va, op, i, sc.b, sc.c, sc.qx, sc.qy, sc.qz);
+        d.x = dd.x; d.y = dd.y;
+      }
+      T den = (T)1 / (d.x * d.x + d.y * d.y);
+      T2 z;
+      z.x = (rv.x * d.x + rv.y * d.y) * den;
+      z.y = (rv.y * d.x - rv.x * d.y) * den;
+      T2 np;
+      np.x = z.x + br * pv.x - bi * pv.y;
+      np.y = z.y + br * pv.y + bi * pv.x;
+      p[e] = np;
+    }
+  }
+}
+
+// u += d (plain FP64 path); accumulates the final relative residual of the solve
+__global__ void k_axpy_u(VecArgs va, const double2* __restrict__ d, double2* __restrict__ u, KrylovState ks,
+                         RefineState rf) {
+  ElemMap em(va.Rp);
+  const int t = threadIdx.x;
+  if (t >= em.rpp * em.RS) return;
+  const int rr = t % em.RS, ro = t / em.RS;
+  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
+  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  for (int k = 0; k < em.NK; ++k) {
+    const int col = rr + 256 * k;
+    if (col >= va.Rp) continue;
+    const int s = sys_of_col(col, va.nb);
+    if (s >= va.R || !rf.active[s]) continue;
+    for (int64_t i = rb + ro; i < re; i += em.rpp) {
+      const size_t e = (size_t)i * va.Rp + col;
+      double2 uv = u[e], dv = d[e];
+      uv.x += dv.x;
+      uv.y += dv.y;
+      u[e] = uv;
+    }
+  }
+}
+
+// end of a plain-FP64 step: accumulate |r|/|r_0| of the solve into err
+__global__ void k_finish_step(RefineState rf, KrylovState ks, int R) {
+  for (int s = threadIdx.x; s < R; s += blockDim.x) {
+    if (rf.active[s] && ks.rr0[s] > 0) rf.err[s] += sqrt(ks.rr[s] / ks.rr0[s]);
+  }
+}
+
+__global__ void k_fill_u(VecArgs va, double2* __restrict__ u) {
+  size_t N = (size_t)va.n * va.Rp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+    int s = sys_of_col((int)(e % va.Rp), va.nb);
+    u[e] = s < va.R ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void k_set_int(int* p, int v, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+// S_s = sum_i w_i u_i (Eq. signal) in FP64
+template <class TU>
+__global__ void __launch_bounds__(256) k_signal(VecArgs va, const double* __restrict__ w, const TU* __restrict__ u,
+                                                double* __restrict__ S, RedScratch rs) {
+  ElemMap em(va.Rp);
+  const int t = threadIdx.x;
+  const bool live = t < em.rpp * em.RS;
+  const int rr = t % em.RS, ro = t / em.RS;
+  double2 acc[EM_NK][1];
+  for (int k = 0; k < EM_NK; ++k) acc[k][0] = make_double2(0, 0);
+  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
+  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  if (live) {
+    for (int k = 0; k < em.NK; ++k) {
+      const int col = rr + 256 * k;
+      if (col >= va.Rp) continue;
+      const int s = sys_of_col(col, va.nb);
+      if (s >= va.R) continue;
+      for (int64_t i = rb + ro; i < re; i += em.rpp) {
+        double2 v = load_res(u, (size_t)i * va.Rp + col);
+        double wi = w[i];
+        acc[k][0].x = fma(wi, v.x, acc[k][0].x);
+        acc[k][0].y = fma(wi, v.y, acc[k][0].y);
+      }
+    }
+  }
+  if (!elem_block_reduce<1>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
+  for (int s = threadIdx.x; s < va.R; s += blockDim.x) {
+    double2 o[1];
+    sum_part<1>(rs.part, gridDim.x, va.Rp, s, o);
+    S[2 * s] = o[0].x;
+    S[2 * s + 1] = o[0].y;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_krylov_init_f32(const OpArgs& op, const VecArgs& va, const double2* r64, const double* scale,
+                            const int* ref_active, float2* x, float2* r, float2* p, const KrylovState& ks,
+                            double tol, RedScratch rs, int conj, int sms, cudaStream_t st) {
+  int g = elem_grid(va.n, sms);
+  if (conj) k_krylov_init<float, float2, double2, true><<<g, 256, 0, st>>>(op, va, r64, scale, ref_active, x, r, p, ks, tol, rs);
+  else k_krylov_init<float, float2, double2, false><<<g, 256, 0, st>>>(op, va, r64, scale, ref_active, x, r, p, ks, tol, rs);
+}
+void launch_krylov_init_f32_df(const OpArgs& op, const VecArgs& va, const float4* rdf, const double* scale,
+                               const int* ref_active, float2* x, float2* r, float2* p, const KrylovState& ks,
+                               double tol, RedScratch rs, int conj, int sms, cudaStream_t st) {
+  int g = elem_grid(va.n, sms);
+  if (conj) k_krylov_init<float, float2, float4, true><<<g, 256, 0, st>>>(op, va, rdf, scale, ref_active, x, r, p, ks, tol, rs);
+  else k_krylov_init<float, float2, float4, false><<<g, 256, 0, st>>>(op, va, rdf, scale, ref_active, x, r, p, ks, tol, rs);
+}
+void launch_krylov_update_f32(const OpArgs& op, const VecArgs& va, float2* x, float2* r, const float2* p,
+                              const float2* q, const KrylovState& ks, RedScratch rs, int conj, int sms,
+                              cudaStream_t st) {
+  int g = elem_grid(va.n, sms);
+  if (conj) k_krylov_update<float, float2, true><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs);
+  else k_krylov_update<float, float2, false><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs);
+}
+void launch_krylov_p_f32(const OpArgs& op, const VecArgs& va, const float2* r, float2* p, const KrylovState& ks,
+                         int sms, cudaStream_t st) {
+  k_krylov_p<float, float2><<<elem_grid(va.n, sms), 256, 0, st>>>(op, va, r, p, ks);
+}
+void launch_krylov_init_f64(const OpArgs& op, const VecArgs& va, const double2* r64, const int* ref_active,
+                            double2* x, double2* r, double2* p, const KrylovState& ks, double tol, RedScratch rs,
+                            int conj, int sms, cudaStream_t st) {
+  int g = elem_grid(va.n, sms);
+  if (conj) k_krylov_init<double, double2, double2, true><<<g, 256, 0, st>>>(op, va, r64, nullptr, ref_active, x, r, p, ks, tol, rs);
+  else k_krylov_init<double, double2, double2, false><<<g, 256, 0, st>>>(op, va, r64, nullptr, ref_active, x, r, p, ks, tol, rs);
+}
+void launch_krylov_update_f64(const OpArgs& op, const VecArgs& va, double2* x, double2* r, const double2* p,
+                              const double2* q, const KrylovState& ks, RedScratch rs, int conj, int sms,
+                              cudaStream_t st) {
+  int g = elem_grid(va.n, sms);
+  if (conj) k_krylov_update<double, double2, true><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs);
+  else k_krylov_update<double, double2, false><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs);
+}
+void launch_krylov_p_f64(const OpArgs& op, const VecArgs& va, const double2* r, double2* p,
+                         const KrylovState& ks, int sms, cudaStream_t st) {
+  k_krylov_p<double, double2><<<elem_grid(va.n, sms), 256, 0, st>>>(op, va, r, p, ks);
+}
+void launch_axpy_u(const VecArgs& va, const double2* d, double2* u, const KrylovState& ks, const RefineState& rf,
+                   int sms, cudaStream_t st) {
+  k_axpy_u<<<elem_grid(va.n, sms), 256, 0, st>>>(va, d, u, ks, rf);
+}
+void launch_finish_step(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st) {
+  k_finish_step<<<1, 256, 0, st>>>(rf, ks, R);
+}
+void launch_fill_u(const VecArgs& va, double2* u, cudaStream_t st) {
+  k_fill_u<<<1024, 256, 0, st>>>(va, u);
+}
+void launch_set_int(int* p, int v, int n, cudaStream_t st) {
+  k_set_int<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, st>>>(p, v, n);
+}
+void launch_signal(const VecArgs& va, const double* w, const double2* u, double* S, RedScratch rs, int sms,
+                   cudaStream_t st) {
+  k_signal<double2><<<elem_grid(va.n, sms), 256, 0, st>>>(va, w, u, S, rs);
+}
+void launch_signal_df(const VecArgs& va, const double* w, const float4* u, double* S, RedScratch rs, int sms,
+                      cudaStream_t st) {
+  k_signal<float4><<<elem_grid(va.n, sms), 256, 0, st>>>(va, w, u, S, rs);
+}
+
+}  // namespace bt
+
+namespace bt {
+// mixed mode: RHS still refining after the last pass of a step did not reach tol_ref
+__global__ void k_mark_ref_left(RefineState rf, KrylovState ks, int R) {
+  for (int s = threadIdx.x; s < R; s += blockDim.x)
+    if (rf.active[s] && ks.status[s] == BT_OK) ks.status[s] = BT_ENOCONV;
+}
+void launch_mark_ref_left(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st) {
+  k_mark_ref_left<<<1, 256, 0, st>>>(rf, ks, R);
+}
+}  // namespace bt

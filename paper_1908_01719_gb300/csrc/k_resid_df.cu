@@ -1,0 +1,274 @@
+// Refinement residuals in double-float arithmetic.
+//
+// GB300 executes FP64 at about 1/58 of its FP32 rate, so the FP64-grade
+// residuals of the iterative refinement are carried out on the FP32 pipes with
+// error-free transformations: a value is an unevaluated sum hi + lo of two
+// FP32 numbers (about 48 significand bits).  Primitives (Dekker 1971; Knuth,
+// TAOCP vol. 2, 4.2.2):
+//   two_sum(a, b)  = (s, e) with s = fl(a + b), s + e = a + b exactly;
+//   two_prod(a, b) = (p, e) with p = fl(a b), e = fma(a, b, -p), p + e = a b.
+// A dot product keeps its leading part in `hi` with two_sum and gathers every
+// rounding error (and the lo x hi cross terms) in an FP32 `lo` accumulator;
+// its error is about (terms) * 2^-46 of the magnitude of the terms, far below
+// the refinement tolerance.
+//
+// The operators are those of k_spmm.cu:
+//   mode 0 (step start): r = (R_n - L_n) u^{n-1} = op_{P0 = K+J}(u)
+//   mode 1 (correction):  u += s d;  r -= s op_{P0 = A0}(d)
+// with u and r stored as {re_hi, im_hi, re_lo, im_lo} and d the FP32 solution
+// of the inner solve for the right-hand side r / s.
+#include "bt_kernels.cuh"
+
+namespace bt {
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+// (sh, sl) += (ah + al) * (xh + xl)
+__device__ __forceinline__ void dd_acc(float& sh, float& sl, float ah, float al, float xh, float xl) {
+  float p = ah * xh;
+  float e = fmaf(ah, xh, -p);
+  e = fmaf(ah, xl, fmaf(al, xh, e));
+  float s, t;
+  two_sum(sh, p, s, t);
+  sh = s;
+  sl += t + e;
+}
+// (sh, sl) += (ah + al) * x, x an exact FP32 number
+__device__ __forceinline__ void dd_acc1(float& sh, float& sl, float ah, float al, float x) {
+  float p = ah * x;
+  float e = fmaf(ah, x, -p);
+  e = fmaf(al, x, e);
+  float s, t;
+  two_sum(sh, p, s, t);
+  sh = s;
+  sl += t + e;
+}
+struct dd {
+  float h, l;
+};
+__device__ __forceinline__ dd dd_norm(float h, float l) {
+  dd r;
+  fast_two_sum(h, l, r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ dd dd_split(double v) {
+  dd r;
+  r.h = (float)v;
+  r.l = (float)(v - (double)r.h);
+  return r;
+}
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  return dd_norm(p, e);
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e += a.l + b.l;
+  return dd_norm(s, e);
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.h, -a.l}; }
+
+template <int NB, bool TRANSF, int MODE, class TX>
+__global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restrict__ x, float4* __restrict__ u,
+                                                  float4* __restrict__ r, RefineState rf, RedScratch rs) {
+  if (*rf.n_active == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int r0 = (blockIdx.y * 32 + lane) * NB;
+  const int c0 = blockIdx.y * 32 * NB + lane;
+  const bool on = r0 < op.R;
+  LaneCoef<NB> lc;
+  lane_coef<NB>(op, on ? r0 : 0, rf.active, lc);
+  bool any = false;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) any |= (on && lc.act[b]);
+  const bool warp_any = __any_sync(0xffffffffu, any);
+  const dd qx = dd_split(lc.qx), qy = dd_split(lc.qy), qz = dd_split(lc.qz);
+  const dd ca = dd_split(lc.a);
+  dd cb[NB], cc[NB];
+  float sc[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    cb[b] = dd_split(lc.b[b]);
+    cc[b] = dd_split(lc.c[b]);
+    sc[b] = (MODE == 1 && on && r0 + b < op.R) ? (float)rf.scale[r0 + b] : 1.0f;
+  }
+  const int64_t per = (op.n + gridDim.x - 1) / gridDim.x;
+  const int64_t rb = (int64_t)blockIdx.x * per, re = min(op.n, rb + per);
+  double2 acc[NB];
+  float2 accf[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    acc[b] = make_double2(0, 0);
+    accf[b] = make_float2(0, 0);
+  }
+  int cnt = 0;
+  if (warp_any) {
+    for (int64_t row = rb + warp; row < re; row += W) {
+      const int k0 = op.rp[row], k1 = op.rp[row + 1];
+      // accumulators: P (P0 x), Q (m x), Z (MD x); re/im, hi/lo
+      float Ph[NB][2], Pl[NB][2], Qh[NB][2], Ql[NB][2], Zh[NB][2], Zl[NB][2];
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) Ph[b][c] = Pl[b][c] = Qh[b][c] = Ql[b][c] = Zh[b][c] = Zl[b][c] = 0.f;
+      for (int k = k0; k < k1; ++k) {
+        const int j = __ldg(op.col + k);
+        const float4 vh = __ldg(op.pkhi + k), vl = __ldg(op.pklo + k);
+        float p0h, p0l;
+        float mdh = 0.f, mdl = 0.f;
+        if (MODE == 0 || TRANSF) {
+          const float2 kh = __ldg(op.kjmd_hi + k), kl = __ldg(op.kjmd_lo + k);
+          mdh = kh.y;
+          mdl = kl.y;
+          if (MODE == 0) {
+            p0h = kh.x;
+            p0l = kl.x;
+          } else {
+            p0h = vh.x;
+            p0l = vl.x;
+          }
+        } else {
+          p0h = vh.x;
+          p0l = vl.x;
+        }
+        // m = qhat . Pd in double-float
+        float mh = 0.f, ml = 0.f;
+        dd_acc(mh, ml, qx.h, qx.l, vh.y, vl.y);
+        dd_acc(mh, ml, qy.h, qy.l, vh.z, vl.z);
+        dd_acc(mh, ml, qz.h, qz.l, vh.w, vl.w);
+        const dd m = dd_norm(mh, ml);
+        if (!on) continue;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const size_t e = (size_t)j * op.Rp + c0 + 32 * b;
+          float xr, xi, xrl = 0.f, xil = 0.f;
+          if constexpr (MODE == 0) {
+            const float4 xv = __ldg(reinterpret_cast<const float4*>(x) + e);
+            xr = xv.x; xi = xv.y; xrl = xv.z; xil = xv.w;
+            dd_acc(Ph[b][0], Pl[b][0], p0h, p0l, xr, xrl);
+            dd_acc(Ph[b][1], Pl[b][1], p0h, p0l, xi, xil);
+            dd_acc(Qh[b][0], Ql[b][0], m.h, m.l, xr, xrl);
+            dd_acc(Qh[b][1], Ql[b][1], m.h, m.l, xi, xil);
+            if constexpr (TRANSF) {
+              dd_acc(Zh[b][0], Zl[b][0], mdh, mdl, xr, xrl);
+              dd_acc(Zh[b][1], Zl[b][1], mdh, mdl, xi, xil);
+            }
+          } else {
+            const float2 xv = __ldg(reinterpret_cast<const float2*>(x) + e);
+            xr = xv.x; xi = xv.y;
+            dd_acc1(Ph[b][0], Pl[b][0], p0h, p0l, xr);
+            dd_acc1(Ph[b][1], Pl[b][1], p0h, p0l, xi);
+            dd_acc1(Qh[b][0], Ql[b][0], m.h, m.l, xr);
+            dd_acc1(Qh[b][1], Ql[b][1], m.h, m.l, xi);
+            if constexpr (TRANSF) {
+              dd_acc1(Zh[b][0], Zl[b][0], mdh, mdl, xr);
+              dd_acc1(Zh[b][1], Zl[b][1], mdh, mdl, xi);
+            }
+          }
+        }
+      }
+      if (on) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          if (!lc.act[b]) continue;
+          const size_t e = (size_t)row * op.Rp + c0 + 32 * b;
+          // y = a P + b Z + i c Q
+          dd Pr = dd_norm(Ph[b][0], Pl[b][0]), Pi = dd_norm(Ph[b][1], Pl[b][1]);
+          dd Qr = dd_norm(Qh[b][0], Ql[b][0]), Qi = dd_norm(Qh[b][1], Ql[b][1]);
+          dd yr = dd_add(dd_mul(ca, Pr), dd_neg(dd_mul(cc[b], Qi)));
+          dd yi = dd_add(dd_mul(ca, Pi), dd_mul(cc[b], Qr));
+          if constexpr (TRANSF) {
+            dd Zr = dd_norm(Zh[b][0], Zl[b][0]), Zi = dd_norm(Zh[b][1], Zl[b][1]);
+            yr = dd_add(yr, dd_mul(cb[b], Zr));
+            yi = dd_add(yi, dd_mul(cb[b], Zi));
+          }
+          if constexpr (MODE == 0) {
+            r[e] = make_float4(yr.h, yi.h, yr.l, yi.l);
+            const float4 uv = u[e];
+            accf[b].x += yr.h * yr.h + yi.h * yi.h;
+            accf[b].y += uv.x * uv.x + uv.y * uv.y;
+          } else {
+            // u += s d (exact product, double-float sum)
+            const float2 dv = reinterpret_cast<const float2*>(x)[e];
+            const float4 uv = u[e];
+            dd s = dd{sc[b], 0.f};
+            dd ur = dd_add(dd{uv.x, uv.z}, dd_mul(s, dd{dv.x, 0.f}));
+            dd ui = dd_add(dd{uv.y, uv.w}, dd_mul(s, dd{dv.y, 0.f}));
+            u[e] = make_float4(ur.h, ui.h, ur.l, ui.l);
+            // r -= s y
+            const float4 rv = r[e];
+            dd rr = dd_add(dd{rv.x, rv.z}, dd_neg(dd_mul(s, yr)));
+            dd ri = dd_add(dd{rv.y, rv.w}, dd_neg(dd_mul(s, yi)));
+            r[e] = make_float4(rr.h, ri.h, rr.l, ri.l);
+            accf[b].x += rr.h * rr.h + ri.h * ri.h;
+          }
+        }
+      }
+      if (++cnt == 32) {
+        cnt = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          acc[b].x += (double)accf[b].x;
+          acc[b].y += (double)accf[b].y;
+          accf[b] = make_float2(0, 0);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    acc[b].x += (double)accf[b].x;
+    acc[b].y += (double)accf[b].y;
+  }
+  block_partials<NB>(acc, on ? r0 : op.Rp, op.Rp, rs.part);
+  if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
+  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 t) { refine_finish(MODE, rf, s, t); });
+}
+
+#define BT_DISPATCH_NB(nb, ...)                                 \
+  switch (nb) {                                                 \
+    case 4: { constexpr int NB_ = 4; __VA_ARGS__; } break;      \
+    case 2: { constexpr int NB_ = 2; __VA_ARGS__; } break;      \
+    default: { constexpr int NB_ = 1; __VA_ARGS__; } break;     \
+  }
+
+void launch_resid0_df(const OpArgs& op, const float4* u, float4* r, const RefineState& rf, RedScratch rs, int nb,
+                      int sms, cudaStream_t st) {
+  BT_DISPATCH_NB(nb, {
+    dim3 grid(spmm_grid_rows(op.n, sms), (op.R + 32 * NB_ - 1) / (32 * NB_));
+    if (op.transformed)
+      k_resid_df<NB_, true, 0, float4><<<grid, 256, 0, st>>>(op, u, const_cast<float4*>(u), r, rf, rs);
+    else
+      k_resid_df<NB_, false, 0, float4><<<grid, 256, 0, st>>>(op, u, const_cast<float4*>(u), r, rf, rs);
+  })
+}
+
+void launch_resid_sub_df(const OpArgs& op, const float2* d, float4* u, float4* r, const RefineState& rf,
+                         RedScratch rs, int nb, int sms, cudaStream_t st) {
+  BT_DISPATCH_NB(nb, {
+    dim3 grid(spmm_grid_rows(op.n, sms), (op.R + 32 * NB_ - 1) / (32 * NB_));
+    if (op.transformed) k_resid_df<NB_, true, 1, float2><<<grid, 256, 0, st>>>(op, d, u, r, rf, rs);
+    else k_resid_df<NB_, false, 1, float2><<<grid, 256, 0, st>>>(op, d, u, r, rf, rs);
+  })
+}
+
+__global__ void k_fill_u_df(VecArgs va, float4* __restrict__ u) {
+  size_t N = (size_t)va.n * va.Rp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+    int s = sys_of_col((int)(e % va.Rp), va.nb);
+    u[e] = s < va.R ? make_float4(1.f, 0.f, 0.f, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+void launch_fill_u_df(const VecArgs& va, float4* u, cudaStream_t st) { k_fill_u_df<<<1024, 256, 0, st>>>(va, u); }
+
+}  // namespace bt

@@ -1,0 +1,58 @@
+"""Convenience driver over the C ABI: upload a geometry, assemble, set the
+sequence and gradients, run, read the signals.  Marshalling only; every step of
+the method runs inside libbtgpu."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import bt
+
+
+class Simulation:
+    """One context holding one geometry.  `geom` is any object with the fields
+    xyz, tets, tet_cmpt, D_cmpt, kappa_cmpt, periodic_mask, box_lo, box_hi,
+    dt, theta, delta, Delta, TE, dirs, bvals, transformed."""
+
+    def __init__(self, geom, device: int = 0, stream: int | None = None):
+        self.g = geom
+        self.ctx = bt.bt_create(device)
+        if stream is not None:
+            bt.bt_set_stream(self.ctx, stream)
+        bt.bt_upload_mesh(self.ctx, geom.xyz, geom.tets, geom.tet_cmpt, geom.D_cmpt, geom.kappa_cmpt,
+                          geom.periodic_mask, geom.box_lo, geom.box_hi)
+        self.n_dof, self.nnz, self.n_iface = bt.bt_get_sizes(self.ctx)
+        self.frame = bt.BT_FRAME_TRANSFORMED if (geom.transformed or geom.periodic_mask) else bt.BT_FRAME_LAB
+        if device >= 0:
+            bt.bt_assemble(self.ctx, geom.dt, geom.theta, self.frame)
+            bt.bt_set_sequence(self.ctx, bt.BT_PGSE, geom.delta, geom.Delta, geom.TE)
+            bt.bt_set_gradients(self.ctx, geom.dirs, geom.bvals)
+        self.R = len(geom.dirs) * len(geom.bvals)
+
+    def run(self, mode=bt.BT_MODE_MIXED, raise_on_status=True, **opts):
+        o = bt.bt_default_opts(**opts)
+        st = bt.bt_run(self.ctx, mode, o, raise_on_status=raise_on_status)
+        S, err, stat = bt.bt_get_signals(self.ctx, self.R)
+        return S, err, stat, st
+
+    def stats(self):
+        return bt.bt_get_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            bt.bt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simulate(geom, mode=bt.BT_MODE_MIXED, device: int = 0, **opts):
+    sim = Simulation(geom, device)
+    try:
+        S, err, stat, _ = sim.run(mode, **opts)
+        return S, err, stat
+    finally:
+        sim.close()

@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU FP64 oracle on
+the same seeded inputs.  Tolerances (relative, |S_gpu - S_oracle| / |S_oracle|):
+  plain FP64 mode   1e-10
+  mixed mode        1e-6   (FP32 Krylov inside double-float refinement)
+  assembled planes  1e-13 of the plane's largest entry."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import geom
+import oracle
+from oracle import btoracle as bo
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+TOL_FP64 = 1e-10
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_1908_01719_gb300 import build, bt as btmod
+    build.build()
+    return btmod
+
+
+@pytest.fixture(scope="module")
+def sim_cls(bt):
+    from paper_1908_01719_gb300.simulate import Simulation
+    return Simulation
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+# ---------------------------------------------------------------- assembly
+@pytest.mark.parametrize("maker", [lambda: geom.cfg2(n=8, kappa=1e-3),
+                                   lambda: geom.cfg3(n=8, n_dir=2, n_b=1),
+                                   lambda: geom.cfg4(n=10, n_dir=1, bvals=(1000.0,))])
+def test_assembled_planes_match_oracle(sim_cls, bt, maker):
+    p = maker()
+    a = bo.assemble(p)
+    sim = sim_cls(p)
+    try:
+        rp, col = bt.bt_get_pattern(sim.ctx)
+        for nm in ["M", "K", "J", "MD", "Mx", "My", "Mz", "Ex", "Ey", "Ez"]:
+            v = bt.bt_get_plane(sim.ctx, nm)
+            ref = a[nm].tocsr()
+            # oracle value at every slot of the shared pattern (0 where absent)
+            dense = np.zeros_like(v)
+            for i in range(len(rp) - 1):
+                cols = col[rp[i]:rp[i + 1]]
+                row = ref.getrow(i)
+                m = dict(zip(row.indices, row.data))
+                dense[rp[i]:rp[i + 1]] = [m.get(c, 0.0) for c in cols]
+            scale = max(np.abs(dense).max(), 1e-300)
+            assert np.abs(v - dense).max() <= 1e-13 * scale, nm
+        A0 = bt.bt_get_plane(sim.ctx, "A0")
+        M = bt.bt_get_plane(sim.ctx, "M")
+        KJ = bt.bt_get_plane(sim.ctx, "K") + bt.bt_get_plane(sim.ctx, "J")
+        assert np.abs(A0 - (M + 0.5 * p.dt * KJ)).max() <= 1e-14 * np.abs(A0).max()
+    finally:
+        sim.close()
+
+
+# ---------------------------------------------------------------- small live parity
+CASES = {
+    "cfg1_n8": lambda: geom.cfg1(n=8),
+    "cfg2_n8": lambda: geom.cfg2(n=8, kappa=1e-4),
+    "cfg2_n8_dirs": lambda: _dirs(geom.cfg2(n=8, kappa=1e-4, bvals=(1000.0, 3000.0))),
+    "cfg3_n8": lambda: geom.cfg3(n=8, n_dir=3, n_b=2),
+    "cfg4_n10": lambda: geom.cfg4(n=10, n_dir=2, bvals=(500.0, 3000.0)),
+}
+
+
+def _dirs(p):
+    d = np.array([[1.0, 0.0, 0.0], [0.2, -0.5, 0.7], [0.0, 0.0, 1.0]])
+    p.dirs = d / np.linalg.norm(d, axis=1, keepdims=True)
+    return p
+
+
+@pytest.fixture(scope="module")
+def live_ref():
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            p = CASES[name]()
+            cache[name] = (p, oracle.run(p))
+        return cache[name]
+    return get
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_plain_fp64_matches_oracle(sim_cls, bt, live_ref, name):
+    p, ref = live_ref(name)
+    sim = sim_cls(p)
+    try:
+        S, err, stat, st = sim.run(bt.BT_MODE_PLAIN_FP64)
+        assert np.all(stat == 0)
+        assert rel(S, ref).max() < TOL_FP64, (S, ref)
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("resid", ["df", "fp64"])
+def test_mixed_matches_oracle(sim_cls, bt, live_ref, name, resid):
+    p, ref = live_ref(name)
+    sim = sim_cls(p)
+    try:
+        flags = bt.BT_OPT_RESID_FP64 if resid == "fp64" else 0
+        S, err, stat, st = sim.run(bt.BT_MODE_MIXED, flags=flags)
+        assert np.all(stat == 0)
+        e = rel(S, ref)
+        assert e.max() < TOL_MIXED, (e, err)
+        # the stated error proxy bounds the observed error
+        assert np.all(e <= np.maximum(err, 1e-15) * 10 + 1e-12)
+    finally:
+        sim.close()
+
+
+def test_free_periodic_exact_closed_form_gpu(sim_cls, bt):
+    """Periodic box without compartments: the exact discrete product (P-5)."""
+    p = geom.free_periodic_box(n=10, L=10.0, dirs=((0.3, 0.4, math.sqrt(0.75)), (1.0, 0.0, 0.0)),
+                               bvals=(1000.0, 3000.0))
+    sim = sim_cls(p)
+    try:
+        for mode, tol in [(bt.BT_MODE_PLAIN_FP64, 1e-11), (bt.BT_MODE_MIXED, 1e-8)]:
+            S, err, stat, st = sim.run(mode)
+            _, F = oracle.pgse_tables(p.delta, p.Delta, p.dt, p.n_steps)
+            for r in range(p.n_rhs):
+                q = float(oracle.q_from_b(p.bvals[r % 2], p.delta, p.Delta))
+                prod = np.prod((1 - 0.5 * p.dt * 2e-3 * q * q * F[:-1] ** 2) /
+                               (1 + 0.5 * p.dt * 2e-3 * q * q * F[1:] ** 2))
+                assert abs(S[r] / 1000.0 - prod) < tol
+    finally:
+        sim.close()
+
+
+# ---------------------------------------------------------------- stored oracle signals (full sizes)
+def _golden(name):
+    path = os.path.join(GOLDEN, name + ".json")
+    if not os.path.exists(path):
+        pytest.skip(f"golden file {name} not generated")
+    with open(path) as f:
+        g = json.load(f)
+    p = getattr(geom, g["builder"])(**g["kwargs"])
+    cnt = np.bincount(p.tet_cmpt, minlength=p.n_cmpt)
+    fp = g["fingerprint"]
+    assert int(np.sum(np.arange(len(cnt)) * cnt)) == fp["cmpt_weighted_sum"], "seeded geometry differs"
+    return p, g
+
+
+@pytest.mark.parametrize("name", ["cfg1_full", "cfg2_full", "cfg3_n20", "cfg4_n24", "cfg2_n12_dt100"])
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_golden_signals(sim_cls, bt, name, mode):
+    p, g = _golden(name)
+    ref = np.array(g["S_re"]) + 1j * np.array(g["S_im"])
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S = np.zeros(len(g["rhs"]), complex)
+        for k, r in enumerate(g["rhs"]):
+            Sk, err, stat, st = sim.run(m, rhs_begin=r, rhs_end=r + 1)
+            assert stat[r] == 0
+            S[k] = Sk[r]
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()

@@ -1,0 +1,142 @@
+"""CPU tests of the C ABI: the library loads, exports every declared entry
+point, and its host pipeline (validation, periodic identification, interface
+doubling, interface faces, CSR pattern) agrees with the oracle's own
+construction.  Host-only contexts (device = -1) make no GPU call."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import geom
+from oracle import btoracle as bo
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_1908_01719_gb300 import build, bt as btmod
+    build.build()
+    return btmod
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "bt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bt_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(bt):
+    L = bt.lib()
+    syms = header_symbols()
+    assert len(syms) >= 16
+    for s in syms:
+        assert hasattr(L, s), s
+    assert sorted(bt.EXPORTS) == syms
+
+
+def test_gpu_calls_refused_on_host_only_context(bt):
+    p = geom.cfg1(n=2)
+    ctx = bt.bt_create(-1)
+    try:
+        bt.bt_upload_mesh(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, 0, p.box_lo, p.box_hi)
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_assemble(ctx, 50.0, 0.5, bt.BT_FRAME_LAB)
+        assert e.value.code == bt.BT_ENODEV
+    finally:
+        bt.bt_destroy(ctx)
+
+
+def _host(bt, p):
+    ctx = bt.bt_create(-1)
+    bt.bt_upload_mesh(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, p.periodic_mask, p.box_lo, p.box_hi)
+    return ctx
+
+
+def _oracle_pattern(a):
+    S = (abs(a["M"]) + abs(a["J"]) + abs(a["Mx"])).tocsr()
+    S.sort_indices()
+    # structural union of the tet pattern and the face pattern
+    Mst = a["M"].copy(); Mst.data[:] = 1
+    Jst = a["J"].copy(); Jst.data[:] = 1
+    U = (Mst + Jst).tocsr()
+    U.sort_indices()
+    return U.indptr, U.indices
+
+
+@pytest.mark.parametrize("maker", [lambda: geom.cfg2(n=6, kappa=1e-4),
+                                   lambda: geom.cfg3(n=8, n_dir=2, n_b=1),
+                                   lambda: geom.cfg4(n=8, n_dir=1, bvals=(1000.0,))])
+def test_doubling_faces_and_pattern_match_oracle(bt, maker):
+    p = maker()
+    a = bo.assemble(p)
+    ctx = _host(bt, p)
+    try:
+        n, nnz, nf = bt.bt_get_sizes(ctx)
+        assert n == a["n"]
+        assert nf == a["n_iface"]
+        dn, dc = bt.bt_get_dofmap(ctx)
+        assert np.array_equal(dn, a["dof_node"]) and np.array_equal(dc, a["dof_cmpt"])
+        rp, col = bt.bt_get_pattern(ctx)
+        orp, ocol = _oracle_pattern(a)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    finally:
+        bt.bt_destroy(ctx)
+
+
+def test_periodic_identification_counts(bt):
+    p = geom.free_periodic_box(n=5, L=7.0)
+    ctx = _host(bt, p)
+    try:
+        n, nnz, nf = bt.bt_get_sizes(ctx)
+        assert n == 125 and nf == 0
+        rp, col = bt.bt_get_pattern(ctx)
+        assert np.all(np.diff(rp) == 15)    # Kuhn stencil, every node interior when periodic
+    finally:
+        bt.bt_destroy(ctx)
+
+
+@pytest.mark.parametrize("defect", ["inverted", "node_range", "cmpt_range", "nan_kappa", "bad_box",
+                                    "touching_free_cmpts", "neg_D"])
+def test_mesh_validation_errors(bt, defect):
+    p = geom.cfg2(n=3, kappa=1e-4)
+    xyz, tets, tc = p.xyz.copy(), p.tets.copy(), p.tet_cmpt.copy()
+    D, K, lo, hi = p.D_cmpt.copy(), p.kappa_cmpt.copy(), p.box_lo.copy(), p.box_hi.copy()
+    if defect == "inverted":
+        tets[5, [2, 3]] = tets[5, [3, 2]]
+    elif defect == "node_range":
+        tets[3, 1] = len(xyz)
+    elif defect == "cmpt_range":
+        tc[7] = 2
+    elif defect == "nan_kappa":
+        K[1] = math.nan
+    elif defect == "bad_box":
+        hi[0] = lo[0]
+    elif defect == "touching_free_cmpts":
+        tc = geom.label_sphere(xyz, tets, np.zeros(3), 5.0)
+        K = np.array([math.inf, math.inf])
+    elif defect == "neg_D":
+        D[0] = -1.0
+    ctx = bt.bt_create(-1)
+    try:
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_upload_mesh(ctx, xyz, tets, tc, D, K, 0, lo, hi)
+        assert e.value.code == bt.BT_EINVAL
+        assert len(bt.bt_last_error(ctx)) > 0
+    finally:
+        bt.bt_destroy(ctx)
+
+
+def test_state_errors(bt):
+    ctx = bt.bt_create(-1)
+    try:
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_get_sizes(ctx)
+        assert e.value.code == bt.BT_ESTATE
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_run(ctx, bt.BT_MODE_MIXED)
+        assert e.value.code == bt.BT_ENODEV
+    finally:
+        bt.bt_destroy(ctx)

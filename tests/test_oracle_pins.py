@@ -324,3 +324,18 @@ def test_transformed_frame_agrees_with_lab_in_neumann_box():
         St = oracle.run_transformed(p, a)[0]
         diffs.append(abs(Sl - St) / abs(Sl))
     assert diffs[1] < 0.15 and diffs[1] < diffs[0] / 2.0, diffs
+
+
+def test_direct_and_iterative_routes_agree():
+    """The ILU-preconditioned Krylov route (used above a few thousand unknowns)
+    reproduces the sparse-LU route to rounding, in both frames."""
+    p = geom.cfg2(n=6, kappa=1e-4, bvals=(1000.0, 3000.0))
+    a = bo.assemble(p)
+    S1 = oracle.run(p, a, route="lu")
+    S2 = oracle.run(p, a, route="iter")
+    assert np.abs(S1 - S2).max() < 1e-12 * np.abs(S1).max()
+    p = geom.cfg3(n=6, n_dir=1, n_b=2)
+    a = bo.assemble(p)
+    S1 = oracle.run(p, a, route="lu")
+    S2 = oracle.run(p, a, route="iter")
+    assert np.abs(S1 - S2).max() < 1e-12 * np.abs(S1).max()
