@@ -136,8 +136,8 @@ enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
 enum { BT_OPT_RESID_FP64 = 1u, BT_OPT_PROFILE = 2u, BT_OPT_NO_GRAPH = 4u };
 typedef struct bt_solver_opts {
   double tol_fp64;      /* plain FP64 stopping tolerance (default 1e-12)          */
-  double tol_inner;     /* inner FP32 Krylov tolerance (default 1e-5)             */
-  double tol_ref;       /* refinement tolerance (default 1e-9)                    */
+  double tol_inner;     /* inner FP32 Krylov tolerance (default 1e-4)             */
+  double tol_ref;       /* refinement tolerance (default 1e-8)                    */
   int32_t max_iter;     /* Krylov iteration cap per solve (default 1000)          */
   int32_t max_refine;   /* refinement passes per step (default 6)                 */
   int32_t check_every;  /* host polls convergence every k iterations (default 4)  */
@@ -162,6 +162,59 @@ bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t*
 bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters,
                        int64_t* refine_passes, int64_t* spmm_launches, double* spmm_ms,
                        double* resid_ms, int64_t* resid_launches, int64_t* kernel_launches);
+
+/* ---------------------------------------------------------------- learned preconditioner
+ * A small network (5 -> 64 -> 64 -> 9, ReLU, bfloat16 weights, FP32
+ * accumulation) maps the features of one step solve
+ *   (dt [us], q|f_bar| [rad/(um us)] in the lab frame or q|F| [rad/um] in the
+ *    transformed frame, D [um^2/us], kappa [um/us], h [um])
+ * (each normalised as (log(x + eps) - mu)/sd with fixed constants) to the
+ * coefficients c_0..c_8 of the polynomial preconditioner
+ *   P_c = sum_j c_j (D^-1 L)^j D^-1,  D = diag(L), L the step matrix,
+ * applied by Horner (8 fused SpMMs) inside the inner Krylov solve.  A system
+ * falls back to Jacobi when the polynomial breaks down (rho = 0, or a
+ * non-positive <r, z> for the Hermitian transformed systems), stagnates, or
+ * has not converged within max_iter / 2; the refinement tolerance judges the
+ * result, so signals match the Jacobi path to that tolerance.  (The paper's
+ * solver is unnamed, Appendix B; this preconditioner has no counterpart
+ * there.)  Parameters: BT_PRECOND_NPARAM floats in the order W1 (64x5,
+ * row-major), b1, W2 (64x64), b2, W3 (9x64), b3. */
+enum { BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9 };
+enum { BT_TRAIN_CONTINUE = 1u };
+typedef struct bt_train_opts {
+  int32_t epochs;   /* default 300  */
+  int32_t batch;    /* default 512  */
+  double lr;        /* Adam step (default 2e-3; betas 0.9, 0.999)       */
+  uint64_t seed;    /* initialisation and shuffling (default 1)         */
+  uint32_t flags;   /* BT_TRAIN_CONTINUE: start from the current weights */
+} bt_train_opts;
+bt_status bt_train_default_opts(bt_train_opts* o);
+/* Geometry features of the assembled mesh: volume-weighted mean D,
+ * area-weighted mean interface kappa (0 without interfaces), and
+ * h = (6 * mean tetrahedron volume)^(1/3). */
+bt_status bt_precond_features(const bt_ctx* ctx, double* D, double* kappa, double* h);
+/* Training samples from the method's own step solves: runs the mixed-mode time
+ * loop (opts as bt_run) and, at each listed step (1-based), takes every RHS's
+ * normalised step residual r and the Krylov basis y_j = L (D^-1 L)^j D^-1 r,
+ * j = 0..8, returning per sample (sample = step-major, then RHS):
+ * feat [5], G = Re(Y^H Y)/|r|^2 [81], h = Re(Y^H r)/|r|^2 [9].
+ * Output arrays hold n_steps * R samples. */
+bt_status bt_collect_precond_data(bt_ctx* ctx, const bt_solver_opts* opts, int32_t n_steps, const int32_t* steps,
+                                  float* feat, double* G, double* h);
+/* Train on n samples (feat [n][5], G [n][81], h [n][9]) with minibatch Adam on
+ * the mean loss |r - L P_c r|^2/|r|^2 = 1 - 2 c.h + c.G c; loss_hist[epoch]
+ * (may be NULL) receives the mean training loss of each epoch.  The network
+ * stays in the context for BT_MODE_LEARNED. */
+bt_status bt_train_precond(bt_ctx* ctx, int64_t n, const float* feat, const double* G, const double* h,
+                           const bt_train_opts* opts, double* loss_hist);
+/* Coefficients [n][9], mean loss and its gradient [BT_PRECOND_NPARAM] of the
+ * current network on n samples (any output may be NULL; G, h needed for loss
+ * and gradient). */
+bt_status bt_precond_eval(bt_ctx* ctx, int64_t n, const float* feat, const double* G, const double* h,
+                          double* coef, double* loss, double* grad);
+/* Copy the FP32 master weights out / in (BT_PRECOND_NPARAM floats). */
+bt_status bt_save_precond(const bt_ctx* ctx, float* w);
+bt_status bt_load_precond(bt_ctx* ctx, const float* w);
 
 #ifdef __cplusplus
 }

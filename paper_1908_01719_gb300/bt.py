@@ -25,7 +25,11 @@ PLANES = {"M": 0, "K": 1, "J": 2, "MD": 3, "Mx": 4, "My": 5, "Mz": 6, "Ex": 7, "
 # every symbol include/bt.h declares
 EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_upload_mesh", "bt_get_sizes",
            "bt_get_dofmap", "bt_get_pattern", "bt_assemble", "bt_get_plane", "bt_set_sequence",
-           "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats"]
+           "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats",
+           "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
+           "bt_precond_eval", "bt_save_precond", "bt_load_precond"]
+BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
+BT_TRAIN_CONTINUE = 1
 
 
 class BtError(RuntimeError):
@@ -38,6 +42,11 @@ class bt_solver_opts(C.Structure):
     _fields_ = [("tol_fp64", C.c_double), ("tol_inner", C.c_double), ("tol_ref", C.c_double),
                 ("max_iter", C.c_int32), ("max_refine", C.c_int32), ("check_every", C.c_int32),
                 ("flags", C.c_uint32), ("rhs_begin", C.c_int32), ("rhs_end", C.c_int32)]
+
+
+class bt_train_opts(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
+                ("flags", C.c_uint32)]
 
 
 _lib = None
@@ -66,6 +75,13 @@ def lib():
             "bt_run": [P, C.c_int, C.POINTER(bt_solver_opts)],
             "bt_get_signals": [P, P, P, P],
             "bt_get_stats": [P, P, P, P, P, P, P, P, P],
+            "bt_train_default_opts": [C.POINTER(bt_train_opts)],
+            "bt_precond_features": [P, P, P, P],
+            "bt_collect_precond_data": [P, C.POINTER(bt_solver_opts), I32, P, P, P, P],
+            "bt_train_precond": [P, I64, P, P, P, C.POINTER(bt_train_opts), P],
+            "bt_precond_eval": [P, I64, P, P, P, P, P, P],
+            "bt_save_precond": [P, P],
+            "bt_load_precond": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -194,3 +210,66 @@ def bt_get_stats(ctx):
                                    C.byref(d, 0), C.byref(d, 8), C.byref(i, 32), C.byref(i, 40)))
     return {"steps": i[0], "krylov_iters": i[1], "refine_passes": i[2], "spmm_launches": i[3],
             "spmm_ms": d[0], "resid_ms": d[1], "resid_launches": i[4], "kernel_launches": i[5]}
+
+
+def bt_train_default_opts(**kw):
+    o = bt_train_opts()
+    lib().bt_train_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def bt_precond_features(ctx):
+    a = (C.c_double * 3)()
+    _check(ctx, lib().bt_precond_features(ctx, C.byref(a, 0), C.byref(a, 8), C.byref(a, 16)))
+    return float(a[0]), float(a[1]), float(a[2])
+
+
+def bt_collect_precond_data(ctx, steps, R, opts=None):
+    steps = np.ascontiguousarray(steps, dtype=np.int32)
+    ns = len(steps) * R
+    feat = np.zeros((ns, 5), np.float32)
+    G = np.zeros((ns, 81), np.float64)
+    h = np.zeros((ns, 9), np.float64)
+    o = opts if opts is not None else bt_default_opts()
+    _check(ctx, lib().bt_collect_precond_data(ctx, C.byref(o), len(steps), _ptr(steps), _ptr(feat), _ptr(G),
+                                              _ptr(h)))
+    return feat, G.reshape(ns, 9, 9), h
+
+
+def bt_train_precond(ctx, feat, G, h, opts=None):
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    G = np.ascontiguousarray(G, dtype=np.float64).reshape(len(feat), 81)
+    h = np.ascontiguousarray(h, dtype=np.float64).reshape(len(feat), 9)
+    o = opts if opts is not None else bt_train_default_opts()
+    hist = np.zeros(o.epochs, np.float64)
+    _check(ctx, lib().bt_train_precond(ctx, len(feat), _ptr(feat), _ptr(G), _ptr(h), C.byref(o), _ptr(hist)))
+    return hist
+
+
+def bt_precond_eval(ctx, feat, G=None, h=None):
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    n = len(feat)
+    coef = np.zeros((n, 9), np.float64)
+    loss = np.zeros(1, np.float64)
+    grad = np.zeros(BT_PRECOND_NPARAM, np.float64)
+    if G is None:
+        _check(ctx, lib().bt_precond_eval(ctx, n, _ptr(feat), None, None, _ptr(coef), None, None))
+        return coef, None, None
+    Gc = np.ascontiguousarray(G, dtype=np.float64).reshape(n, 81)
+    hc = np.ascontiguousarray(h, dtype=np.float64).reshape(n, 9)
+    _check(ctx, lib().bt_precond_eval(ctx, n, _ptr(feat), _ptr(Gc), _ptr(hc), _ptr(coef), _ptr(loss), _ptr(grad)))
+    return coef, float(loss[0]), grad
+
+
+def bt_save_precond(ctx):
+    w = np.zeros(BT_PRECOND_NPARAM, np.float32)
+    _check(ctx, lib().bt_save_precond(ctx, _ptr(w)))
+    return w
+
+
+def bt_load_precond(ctx, w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    assert len(w) == BT_PRECOND_NPARAM
+    _check(ctx, lib().bt_load_precond(ctx, _ptr(w)))

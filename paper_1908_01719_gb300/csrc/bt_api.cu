@@ -11,100 +11,16 @@
 #include <string>
 #include <vector>
 
-#include "bt_kernels.cuh"
+#include "bt_ctx.h"
 
 using namespace bt;
 
-namespace {
-
-constexpr int N_COUNTERS = 16;
-
-struct EventPair {
-  cudaEvent_t a, b;
-  int kind;  // 0 fused Krylov SpMM, 1 refinement residual
-};
-
-}  // namespace
-
-struct bt_ctx {
-  int device = -1;
-  bool host_only = true;
-  cudaStream_t stream = nullptr;
-  int sms = 152;
-  std::string err;
-
-  HostMesh mesh;
-  bool have_mesh = false;
-
-  // device copies of the mesh and the contribution lists
-  DBuf<double> d_xyz, d_D, d_face_kappa, d_geo, d_fcoef;
-  DBuf<int32_t> d_tets, d_cmpt, d_face_ta, d_tc, d_fc, d_rp, d_col;
-  DBuf<int8_t> d_face_lv;
-  DBuf<int64_t> d_tc_ptr, d_fc_ptr;
-  // assembled planes
-  DBuf<double> d_planes, d_A0, d_KJ, d_w, d_diag_md64;
-  DBuf<double4> d_pk64, d_diag64;
-  DBuf<float4> d_pk32, d_pkhi, d_pklo, d_diag32;
-  DBuf<float> d_md32, d_diag_md32;
-  DBuf<float2> d_kjmd_hi, d_kjmd_lo;
-  bool assembled = false;
-  double dt = 0, theta = 0.5, wmax = 0;
-  int transformed = 0;
-
-  // sequence
-  bool have_seq = false;
-  double delta = 0, Delta = 0, TE = 0;
-  int n_steps = 0;
-  std::vector<double> fbar, F;  // fbar[n-1], n = 1..N; F[n], n = 0..N
-
-  // gradients
-  int n_dir = 0, n_b = 0, R = 0;
-  std::vector<double> qhat_rhs, q_rhs;  // [3R], [R]
-
-  // run buffers
-  DBuf<double> d_q, d_qhat;
-  DBuf<OpCoef> d_coef;
-  DBuf<double2> u64, r64, x64, rk64, p64, q64;
-  DBuf<float4> udf, rdf;
-  DBuf<float2> x32, r32, p32, q32;
-  DBuf<double> ks_rho, ks_alpha, ks_beta, ks_rr0, ks_rr, ks_tol2;
-  DBuf<int> ks_iter, ks_active, ks_status, n_active, ks_it_best;
-  DBuf<double> ks_rr_best;
-  DBuf<double> rf_r0n2, rf_rk2, rf_scale, rf_err;
-  DBuf<int> rf_active;
-  DBuf<double> red_part, d_S;
-  DBuf<unsigned int> red_counter;
-  int* h_flags = nullptr;  // pinned: [0] Krylov n_active, [1] refinement n_active
-
-  // results
-  std::vector<double> S, err_est;
-  std::vector<int> status;
-  int64_t st_steps = 0, st_iters = 0, st_refine = 0, st_spmm = 0, st_resid = 0, st_launches = 0;
-  double st_spmm_ms = 0, st_resid_ms = 0;
-  std::vector<EventPair> ev_pool;
-  size_t ev_used = 0;
-};
-
-namespace {
-
-bt_status fail(bt_ctx* c, bt_status code, const std::string& msg) {
-  if (c) c->err = msg;
-  return code;
+namespace bt {
+void compute_geom_features(bt_ctx* ctx);
 }
 
-#define CK(call)                                                                                 \
-  do {                                                                                           \
-    cudaError_t e_ = (call);                                                                     \
-    if (e_ != cudaSuccess)                                                                       \
-      return fail(ctx, e_ == cudaErrorMemoryAllocation ? BT_ENOMEM : BT_ECUDA,                   \
-                  std::string(#call) + ": " + cudaGetErrorString(e_));                           \
-  } while (0)
 
-#define CKL()                                                                                    \
-  do {                                                                                           \
-    cudaError_t e_ = cudaGetLastError();                                                         \
-    if (e_ != cudaSuccess) return fail(ctx, BT_ECUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
-  } while (0)
+namespace {
 
 template <class T>
 cudaError_t upload(DBuf<T>& b, const std::vector<T>& h, cudaStream_t st) {
@@ -345,6 +261,7 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   ctx->dt = dt_us;
   ctx->theta = theta;
   ctx->transformed = (int)flags;
+  compute_geom_features(ctx);
   ctx->assembled = true;
   ctx->have_seq = false;
   return BT_OK;
@@ -425,8 +342,8 @@ bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32
 bt_status bt_default_opts(bt_solver_opts* o) {
   if (!o) return BT_EINVAL;
   o->tol_fp64 = 1e-12;
-  o->tol_inner = 1e-5;
-  o->tol_ref = 1e-9;
+  o->tol_inner = 1e-4;
+  o->tol_ref = 1e-8;
   o->max_iter = 1000;
   o->max_refine = 6;
   o->check_every = 4;
@@ -450,21 +367,83 @@ int pick_nb(const bt_ctx* ctx, int rb, int Rs) {
   return 1;
 }
 
-template <class T>
-cudaError_t ensure(DBuf<T>& b, size_t n) {
-  if (b.n >= n && b.p) return cudaSuccess;
-  return b.alloc(n);
-}
-
 }  // namespace
 
-extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in) {
+namespace {
+// z = P_c r for the polynomial systems of the current inner solve (Horner,
+// ping-pong zA/zB, ending in zA), z = D^-1 r for Jacobi systems
+bt_status apply_poly(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const KrylovState& ks, cudaStream_t st) {
+  float2* bufs[2] = {ctx->zA.p, ctx->zB.p};
+  for (int j = MLP_OUT - 1, w = 0; j >= 0; --j, w ^= 1) {
+    launch_horner(op, va, bufs[w ^ 1], ctx->r32.p, bufs[w], ctx->d_coef9.p, j, ks.active, ctx->pmode.p,
+                  ks.n_active, ctx->sms, st);
+  }
+  CKL();
+  return BT_OK;
+}
+}  // namespace
+
+namespace {
+// training-data collection during a run (bt_collect_precond_data)
+struct CollectSpec {
+  std::vector<int> steps;  // 1-based, ascending
+  float* feat;
+  double* G;
+  double* h;
+};
+}  // namespace
+
+// At a sampled step: v_0 = D^-1 r (the p of the fresh Krylov init),
+// v_{j+1} = D^-1 L v_j (Horner kernel with zero coefficients), then the Gram
+// data of every RHS; samples without a step residual get zero G.
+static bt_status collect_samples(bt_ctx* ctx, OpArgs op, const VecArgs& va, const KrylovState& ks, int Rs, int Rp,
+                                 size_t NE, double fq, const CollectSpec* col, size_t k) {
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(ctx->d_coef9.p, 0, 9 * (size_t)Rs * sizeof(double), st));
+  launch_set_int(ctx->pmode.p, 1, Rs, st);
+  CK(cudaMemcpyAsync(ctx->Vbuf.p, ctx->p32.p, NE * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  for (int j = 0; j < 9; ++j)
+    launch_horner(op, va, ctx->Vbuf.p + (size_t)j * NE, ctx->r32.p, ctx->Vbuf.p + (size_t)(j + 1) * NE,
+                  ctx->d_coef9.p, 0, ks.active, ctx->pmode.p, ks.n_active, ctx->sms, st);
+  launch_gram(op, va, ctx->r32.p, ctx->Vbuf.p, NE, ctx->gram_part.p, ctx->red_counter.p + 7, ctx->gram_out.p,
+              ctx->sms, st);
+  CKL();
+  std::vector<double> g((size_t)Rs * 55);
+  std::vector<int> act(Rs);
+  CK(cudaMemcpyAsync(g.data(), ctx->gram_out.p, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(act.data(), ks.active, Rs * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int s = 0; s < Rs; ++s) {
+    const size_t o = k * Rs + s;
+    float* f = col->feat + 5 * o;
+    f[0] = (float)ctx->dt;
+    f[1] = (float)(ctx->q_rhs[s] * std::fabs(fq));
+    f[2] = (float)ctx->feat_D;
+    f[3] = (float)ctx->feat_kappa;
+    f[4] = (float)ctx->feat_h;
+    double* G = col->G + 81 * o;
+    double* h = col->h + 9 * o;
+    const double* gs = &g[(size_t)s * 55];
+    const double rr = gs[54];
+    const bool ok = act[s] && rr > 0;
+    int q = 0;
+    for (int a2 = 0; a2 < 9; ++a2)
+      for (int b2 = a2; b2 < 9; ++b2, ++q) G[9 * a2 + b2] = G[9 * b2 + a2] = ok ? gs[q] / rr : 0.0;
+    for (int a2 = 0; a2 < 9; ++a2) h[a2] = ok ? gs[45 + a2] / rr : 0.0;
+  }
+  return BT_OK;
+}
+
+static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, const CollectSpec* col) {
   if (!ctx) return BT_EINVAL;
   if (!need_gpu(ctx)) return fail(ctx, BT_ENODEV, "bt_run: host-only context");
   if (!ctx->assembled || !ctx->have_seq || ctx->R == 0)
     return fail(ctx, BT_ESTATE, "bt_run: need mesh, assembly, sequence and gradients");
-  if (mode != BT_MODE_PLAIN_FP64 && mode != BT_MODE_MIXED)
-    return fail(ctx, BT_EINVAL, "bt_run: mode not available");
+  if (mode != BT_MODE_PLAIN_FP64 && mode != BT_MODE_MIXED && mode != BT_MODE_LEARNED)
+    return fail(ctx, BT_EINVAL, "bt_run: unknown mode");
+  if (mode == BT_MODE_LEARNED && !ctx->have_precond)
+    return fail(ctx, BT_ESTATE, "bt_run: BT_MODE_LEARNED needs a trained or loaded preconditioner");
+  const bool learned = mode == BT_MODE_LEARNED;
   bt_solver_opts o;
   bt_default_opts(&o);
   if (opts_in) o = *opts_in;
@@ -531,6 +510,18 @@ extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in
   CK(ensure(ctx->rf_err, Rs));
   CK(ensure(ctx->rf_active, Rs));
   CK(ensure(ctx->d_S, 2 * (size_t)Rs));
+  if (learned || col) {
+    CK(ensure(ctx->zA, NE));
+    CK(ensure(ctx->zB, NE));
+    CK(ensure(ctx->pmode, Rs));
+    CK(ensure(ctx->d_feat, 5 * (size_t)Rs));
+    CK(ensure(ctx->d_coef9, 9 * (size_t)Rs));
+  }
+  if (col) {
+    CK(ensure(ctx->Vbuf, 10 * NE));
+    CK(ensure(ctx->gram_part, (size_t)(2 * ctx->sms + 8) * Rp * 55));
+    CK(ensure(ctx->gram_out, (size_t)Rs * 55));
+  }
   const size_t max_blocks = (size_t)ctx->sms * REDUCE_BLOCKS_PER_SM + 64;
   CK(ensure(ctx->red_part, max_blocks * Rp * 4));  // up to two complex partials per (block, RHS)
   // coefficient table: per step, [0] = r_0 operator (R_n - L_n), [1] = L_n
@@ -606,9 +597,24 @@ extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in
     if (e) cudaEventRecord(e->b, st);
   };
 
+  double last_fq = NAN;
+  size_t col_next = 0;
   for (int step = 1; step <= N; ++step) {
     const OpCoef* c_r0 = ctx->d_coef.p + 2 * (step - 1);
     const OpCoef* c_L = c_r0 + 1;
+    // f_bar_n (lab) or F_n (transformed) of this step: the preconditioner feature
+    const double fq = ctx->transformed ? ctx->F[step] : ctx->fbar[step - 1];
+    const bool collect_now = col && col_next < col->steps.size() && col->steps[col_next] == step;
+    if (learned) {
+      if (!(fq == last_fq)) {
+        launch_features(ctx->d_q.p, Rs, ctx->dt, fq, ctx->feat_D, ctx->feat_kappa, ctx->feat_h, ctx->d_feat.p, st);
+        launch_mlp_forward(ctx->pw16.p, ctx->d_feat.p, Rs, ctx->d_coef9.p, st);
+        L += 2;
+        last_fq = fq;
+      }
+      launch_set_int(ctx->pmode.p, 1, Rs, st);
+      L += 1;
+    }
     launch_set_int(ctx->rf_active.p, 1, Rs, st);
     launch_set_int(rf.n_active, Rs, 1, st);
     L += 3;  // two set kernels and the step-start residual
@@ -638,6 +644,18 @@ extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in
                                ctx->p32.p, ks, o.tol_inner, rs_at(1), conj, ctx->sms, st);
       }
       CKL();
+      if (collect_now && pass == 0) {
+        if (bt_status e = collect_samples(ctx, op, va, ks, Rs, Rp, NE, fq, col, col_next)) return e;
+        ++col_next;
+      }
+      if (learned) {
+        // z = P_c r (Horner), then rho = <r, z>, p = z for polynomial systems
+        if (bt_status e = apply_poly(ctx, op, va, ks, st)) return e;
+        launch_precond_dot(va, ctx->r32.p, ctx->zA.p, ks, rs_at(6), ctx->pmode.p, conj, 1, ctx->sms, st);
+        launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st, ctx->zA.p, ctx->pmode.p);
+        CKL();
+        L += 11;
+      }
       for (int it = 0; it < o.max_iter; ++it) {
         if (plain) {
           timed(0, [&] {
@@ -650,8 +668,15 @@ extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in
         } else {
           timed(0, [&] { launch_spmm_krylov_f32(op, ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb, ctx->sms, st); });
           launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs_at(3), conj,
-                                   ctx->sms, st);
-          launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st);
+                                   ctx->sms, st, learned ? ctx->pmode.p : nullptr);
+          if (learned) {
+            if (bt_status e = apply_poly(ctx, op, va, ks, st)) return e;
+            launch_precond_dot(va, ctx->r32.p, ctx->zA.p, ks, rs_at(6), ctx->pmode.p, conj, 0, ctx->sms, st);
+            launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st, ctx->zA.p, ctx->pmode.p);
+            L += 10;
+          } else {
+            launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st);
+          }
         }
         CKL();
         ctx->st_iters++;
@@ -707,6 +732,29 @@ extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in
   }
   if (ret != BT_OK) ctx->err = "bt_run: some right-hand sides did not converge (see status)";
   return ret;
+}
+
+extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts) {
+  return run_impl(ctx, mode, opts, nullptr);
+}
+
+extern "C" bt_status bt_collect_precond_data(bt_ctx* ctx, const bt_solver_opts* opts, int32_t n_steps,
+                                             const int32_t* steps, float* feat, double* G, double* h) {
+  if (!ctx || n_steps < 1 || !steps || !feat || !G || !h) return fail(ctx, BT_EINVAL, "bt_collect_precond_data: bad arguments");
+  if (!ctx->have_seq) return fail(ctx, BT_ESTATE, "bt_collect_precond_data: set sequence and gradients first");
+  CollectSpec c;
+  c.steps.assign(steps, steps + n_steps);
+  for (int i = 0; i < n_steps; ++i)
+    if (c.steps[i] < 1 || c.steps[i] > ctx->n_steps || (i && c.steps[i] <= c.steps[i - 1]))
+      return fail(ctx, BT_EINVAL, "bt_collect_precond_data: steps must be ascending in [1, n_steps]");
+  bt_solver_opts o;
+  bt_default_opts(&o);
+  if (opts) o = *opts;
+  o.rhs_begin = o.rhs_end = 0;
+  c.feat = feat;
+  c.G = G;
+  c.h = h;
+  return run_impl(ctx, BT_MODE_MIXED, &o, &c);
 }
 
 extern "C" bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t* status) {

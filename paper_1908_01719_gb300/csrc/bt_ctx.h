@@ -1,0 +1,113 @@
+// Context of libbtgpu (internal; the ABI sees only an opaque pointer).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "bt_kernels.cuh"
+
+namespace bt {
+constexpr int N_COUNTERS = 16;
+struct EventPair {
+  cudaEvent_t a, b;
+  int kind;  // 0 fused Krylov SpMM, 1 refinement residual
+};
+}  // namespace bt
+
+struct bt_ctx {
+  int device = -1;
+  bool host_only = true;
+  cudaStream_t stream = nullptr;
+  int sms = 152;
+  std::string err;
+
+  bt::HostMesh mesh;
+  bool have_mesh = false;
+
+  // device copies of the mesh and the contribution lists
+  bt::DBuf<double> d_xyz, d_D, d_face_kappa, d_geo, d_fcoef;
+  bt::DBuf<int32_t> d_tets, d_cmpt, d_face_ta, d_tc, d_fc, d_rp, d_col;
+  bt::DBuf<int8_t> d_face_lv;
+  bt::DBuf<int64_t> d_tc_ptr, d_fc_ptr;
+  // assembled planes
+  bt::DBuf<double> d_planes, d_A0, d_KJ, d_w, d_diag_md64;
+  bt::DBuf<double4> d_pk64, d_diag64;
+  bt::DBuf<float4> d_pk32, d_pkhi, d_pklo, d_diag32;
+  bt::DBuf<float> d_md32, d_diag_md32;
+  bt::DBuf<float2> d_kjmd_hi, d_kjmd_lo;
+  bool assembled = false;
+  double dt = 0, theta = 0.5, wmax = 0;
+  int transformed = 0;
+
+  // sequence
+  bool have_seq = false;
+  double delta = 0, Delta = 0, TE = 0;
+  int n_steps = 0;
+  std::vector<double> fbar, F;  // fbar[n-1], n = 1..N; F[n], n = 0..N
+
+  // gradients
+  int n_dir = 0, n_b = 0, R = 0;
+  std::vector<double> qhat_rhs, q_rhs;  // [3R], [R]
+
+  // run buffers
+  bt::DBuf<double> d_q, d_qhat;
+  bt::DBuf<bt::OpCoef> d_coef;
+  bt::DBuf<double2> u64, r64, x64, rk64, p64, q64;
+  bt::DBuf<float4> udf, rdf;
+  bt::DBuf<float2> x32, r32, p32, q32;
+  bt::DBuf<double> ks_rho, ks_alpha, ks_beta, ks_rr0, ks_rr, ks_tol2;
+  bt::DBuf<int> ks_iter, ks_active, ks_status, n_active, ks_it_best;
+  bt::DBuf<double> ks_rr_best;
+  bt::DBuf<double> rf_r0n2, rf_rk2, rf_scale, rf_err;
+  bt::DBuf<int> rf_active;
+  bt::DBuf<double> red_part, d_S;
+  bt::DBuf<unsigned int> red_counter;
+  int* h_flags = nullptr;  // pinned: [0] Krylov n_active, [1] refinement n_active
+
+  // results
+  std::vector<double> S, err_est;
+  std::vector<int> status;
+  int64_t st_steps = 0, st_iters = 0, st_refine = 0, st_spmm = 0, st_resid = 0, st_launches = 0;
+  double st_spmm_ms = 0, st_resid_ms = 0;
+  std::vector<bt::EventPair> ev_pool;
+  size_t ev_used = 0;
+
+  // learned polynomial preconditioner
+  bool have_precond = false;
+  bt::DBuf<float> pw32, pm, pv, d_feat;
+  bt::DBuf<__nv_bfloat16> pw16;
+  bt::DBuf<double> d_coef9;
+  bt::DBuf<float2> zA, zB, Vbuf;
+  bt::DBuf<int> pmode;
+  bt::DBuf<double> gram_part, gram_out;
+  double feat_D = 0, feat_kappa = 0, feat_h = 0;  // geometry features (bt_assemble)
+};
+
+namespace bt {
+inline bt_status fail(bt_ctx* c, bt_status code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+template <class T>
+cudaError_t ensure(DBuf<T>& b, size_t n) {
+  if (b.n >= n && b.p) return cudaSuccess;
+  return b.alloc(n);
+}
+}  // namespace bt
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return bt::fail(ctx, e_ == cudaErrorMemoryAllocation ? BT_ENOMEM : BT_ECUDA,               \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+  } while (0)
+
+#define CKL()                                                                                    \
+  do {                                                                                           \
+    cudaError_t e_ = cudaGetLastError();                                                         \
+    if (e_ != cudaSuccess) return bt::fail(ctx, BT_ECUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+  } while (0)

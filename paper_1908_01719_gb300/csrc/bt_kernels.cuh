@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "bt_internal.h"
 
 namespace bt {
@@ -121,6 +123,27 @@ struct RedScratch {
   unsigned int* counter; // one per reduction site
 };
 
+// learned polynomial preconditioner (k_precond.cu)
+constexpr int MLP_IN = 5, MLP_H = 64, MLP_OUT = 9;
+constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT;
+struct MlpTrainArgs {
+  float* w32;
+  __nv_bfloat16* w16;
+  float *m, *v;
+  const float *feat, *G, *h;
+  const int* idx;
+  int B;
+  float *sx, *sa1, *sa2, *sd1, *sd2, *sdc, *loss;
+  double* grad_out;
+  int apply, t;
+  float lr, beta1, beta2, eps;
+};
+void launch_mlp_forward(const __nv_bfloat16* w, const float* feat, int S, double* coef, cudaStream_t st);
+void launch_mlp_train(const MlpTrainArgs& a, cudaStream_t st);
+void launch_to_bf16(const float* a, __nv_bfloat16* b, int n, cudaStream_t st);
+void launch_features(const double* q, int R, double dt, double fq, double D, double kap, double hh, float* feat,
+                     cudaStream_t st);
+
 // launch wrappers (k_spmm.cu / k_krylov.cu)
 enum { REDUCE_BLOCKS_PER_SM = 4 };
 int spmm_grid_rows(int64_t n, int sms);
@@ -157,9 +180,17 @@ void launch_krylov_init_f32(const OpArgs& op, const VecArgs& va, const double2* 
                             double tol, RedScratch rs, int conj, int sms, cudaStream_t st);
 void launch_krylov_update_f32(const OpArgs& op, const VecArgs& va, float2* x, float2* r, const float2* p,
                               const float2* q, const KrylovState& ks, RedScratch rs, int conj, int sms,
-                              cudaStream_t st);
+                              cudaStream_t st, int* pmode = nullptr);
 void launch_krylov_p_f32(const OpArgs& op, const VecArgs& va, const float2* r, float2* p, const KrylovState& ks,
-                         int sms, cudaStream_t st);
+                         int sms, cudaStream_t st, const float2* zbuf = nullptr, const int* pmode = nullptr);
+// polynomial preconditioner application and its inner product
+void launch_horner(const OpArgs& op, const VecArgs& va, const float2* zin, const float2* r, float2* zout,
+                   const double* coef, int j, const int* active, const int* pmode, const int* n_active, int sms,
+                   cudaStream_t st);
+void launch_precond_dot(const VecArgs& va, const float2* r, const float2* z, const KrylovState& ks, RedScratch rs,
+                        int* pmode, int conj, int init, int sms, cudaStream_t st);
+void launch_gram(const OpArgs& op, const VecArgs& va, const float2* r, const float2* V, size_t vstride,
+                 double* part, unsigned int* counter, double* out, int sms, cudaStream_t st);
 
 void launch_krylov_init_f64(const OpArgs& op, const VecArgs& va, const double2* r64, const int* ref_active,
                             double2* x, double2* r, double2* p, const KrylovState& ks, double tol, RedScratch rs,
@@ -212,6 +243,16 @@ __host__ __device__ __forceinline__ int col_of_sys(int s, int nb) {
   const int t = s / (32 * nb), w = s - t * 32 * nb;
   return t * 32 * nb + (w % nb) * 32 + w / nb;
 }
+
+// Row order of the gathering kernels: blocks take 32-row chunks round-robin,
+// so at any moment all blocks work inside one window of about
+// gridDim.x * 32 rows; the +-1 z-plane neighbours of that window stay
+// resident in L2 and each row of X is fetched from HBM about once.
+constexpr int ROW_CHUNK = 32;
+#define BT_FOR_CHUNKED_ROWS(row, n, first, stride)                                               \
+  for (int64_t ch_ = blockIdx.x; ch_ * ROW_CHUNK < (int64_t)(n); ch_ += gridDim.x)                \
+    for (int64_t row = ch_ * ROW_CHUNK + (first), re_ = min((int64_t)(n), (ch_ + 1) * ROW_CHUNK); \
+         row < re_; row += (stride))
 
 // read-only 32-byte / 16-byte plane loads
 __device__ __forceinline__ double4 ldg4(const double4* p) {
@@ -308,6 +349,28 @@ __device__ __forceinline__ void reduce_partials(const double* part, int nbx, int
   }
 }
 
+
+// alpha = rho / <p, q> for system s (last block of a Krylov SpMM); a zero or
+// non-finite <p, q> is a breakdown and freezes the system.
+__device__ __forceinline__ void krylov_alpha(const KrylovState& ks, int s, double2 pq) {
+  if (!ks.active[s]) {
+    ks.alpha[2 * s] = 0;
+    ks.alpha[2 * s + 1] = 0;
+    return;
+  }
+  const double2 rho = make_double2(ks.rho[2 * s], ks.rho[2 * s + 1]);
+  const double den = pq.x * pq.x + pq.y * pq.y;
+  if (!(den > 0) || !isfinite(den)) {
+    ks.alpha[2 * s] = 0;
+    ks.alpha[2 * s + 1] = 0;
+    ks.active[s] = 0;
+    ks.status[s] = isfinite(den) ? BT_ENOCONV : BT_ENAN;
+    atomicSub(ks.n_active, 1);
+    return;
+  }
+  ks.alpha[2 * s] = (rho.x * pq.x + rho.y * pq.y) / den;
+  ks.alpha[2 * s + 1] = (rho.y * pq.x - rho.x * pq.y) / den;
+}
 
 // Refinement bookkeeping of system s after a residual launch (last block).
 // mode 0: step start, t = (|r_0|^2, |u|^2); mode 1: after a correction, t.x = |r|^2.

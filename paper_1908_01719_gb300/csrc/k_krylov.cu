@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(256) k_krylov_init(OpArgs op, VecArgs va, cons
 template <class T, class T2, bool CONJ>
 __global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2* __restrict__ x,
                                                        T2* __restrict__ r, const T2* __restrict__ p,
-                                                       const T2* __restrict__ q, KrylovState ks, RedScratch rs) {
+                                                       const T2* __restrict__ q, KrylovState ks, RedScratch rs,
+                                                       int* __restrict__ pmode) {
   if (*ks.n_active == 0) return;
   ElemMap em(va.Rp);
   const int t = threadIdx.x;
@@ -229,33 +230,46 @@ __global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2
       const T axr = (T)ks.alpha[2 * s], axi = (T)ks.alpha[2 * s + 1];
       T2 ar = {0, 0}, an = {0, 0};
       int cnt = 0;
-      for (int64_t i = rb + ro; i < re; i += em.rpp) {
-        const size_t e = (size_t)i * va.Rp + col;
-        T2 pv = p[e], qv = q[e], xv = x[e], rv = r[e];
-        xv.x += axr * pv.x - axi * pv.y;
-        xv.y += axr * pv.y + axi * pv.x;
-        rv.x -= axr * qv.x - axi * qv.y;
-        rv.y -= axr * qv.y + axi * qv.x;
-        x[e] = xv;
-        r[e] = rv;
-        T2 d;
-        if constexpr (sizeof(T) == 4) {
-          float2 df = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
-          d.x = df.x; d.y = df.y;
-        } else {
-          double2 dd = diag_f64(va, op, i, sc.b, sc.c, sc.qx, sc.qy, sc.qz);
-          d.x = dd.x; d.y = dd.y;
+      // four rows per trip, all loads issued before the arithmetic
+      for (int64_t i0 = rb + ro; i0 < re; i0 += 4 * em.rpp) {
+        T2 pv[4], qv[4], xv[4], rv[4], d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + (int64_t)u * em.rpp;
+          if (i < re) {
+            const size_t e = (size_t)i * va.Rp + col;
+            pv[u] = p[e]; qv[u] = q[e]; xv[u] = x[e]; rv[u] = r[e];
+            if constexpr (sizeof(T) == 4) {
+              float2 df = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
+              d[u].x = df.x; d[u].y = df.y;
+            } else {
+              double2 dd = diag_f64(va, op, i, sc.b, sc.c, sc.qx, sc.qy, sc.qz);
+              d[u].x = dd.x; d[u].y = dd.y;
+            }
+          }
         }
-        T den = (T)1 / (d.x * d.x + d.y * d.y);
-        T2 z;
-        z.x = (rv.x * d.x + rv.y * d.y) * den;
-        z.y = (rv.y * d.x - rv.x * d.y) * den;
-        T2 rc = rv;
-        if constexpr (CONJ) rc.y = -rc.y;
-        ar.x += rc.x * z.x - rc.y * z.y;
-        ar.y += rc.x * z.y + rc.y * z.x;
-        an.x += rv.x * rv.x + rv.y * rv.y;
-        if (++cnt == 32) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + (int64_t)u * em.rpp;
+          if (i >= re) break;
+          const size_t e = (size_t)i * va.Rp + col;
+          xv[u].x += axr * pv[u].x - axi * pv[u].y;
+          xv[u].y += axr * pv[u].y + axi * pv[u].x;
+          rv[u].x -= axr * qv[u].x - axi * qv[u].y;
+          rv[u].y -= axr * qv[u].y + axi * qv[u].x;
+          x[e] = xv[u];
+          r[e] = rv[u];
+          T den = (T)1 / (d[u].x * d[u].x + d[u].y * d[u].y);
+          T2 z;
+          z.x = (rv[u].x * d[u].x + rv[u].y * d[u].y) * den;
+          z.y = (rv[u].y * d[u].x - rv[u].x * d[u].y) * den;
+          T2 rc = rv[u];
+          if constexpr (CONJ) rc.y = -rc.y;
+          ar.x += rc.x * z.x - rc.y * z.y;
+          ar.y += rc.x * z.y + rc.y * z.x;
+          an.x += rv[u].x * rv[u].x + rv[u].y * rv[u].y;
+        }
+        if (++cnt == 8) {
           cnt = 0;
           acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
           ar = T2{0, 0}; an = T2{0, 0};
@@ -289,11 +303,24 @@ __global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2
     } else if (ks.stall > 0 && it - ks.it_best[s] >= ks.stall) {
       // the FP32 recurrence has stagnated: hand back to the refinement loop
       ks.active[s] = 0;
+      if (pmode) pmode[s] = 0;
       continue;
     }
     if (it >= ks.max_iter) {
       ks.active[s] = 0;
       ks.status[s] = BT_ENOCONV;
+      continue;
+    }
+    if (pmode && pmode[s]) {
+      // polynomial-preconditioned system: rho and beta come from z = P_c r
+      // (k_precond_dot); fall back to Jacobi when it is not converged by
+      // max_iter / 2
+      if (it >= ks.max_iter / 2) {
+        ks.active[s] = 0;
+        pmode[s] = 0;
+        continue;
+      }
+      atomicAdd(&s_cnt, 1);
       continue;
     }
     // beta = rho' / rho (complex)
@@ -317,7 +344,8 @@ __global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2
 // p = z + beta p for active systems (z recomputed from r)
 template <class T, class T2>
 __global__ void __launch_bounds__(256) k_krylov_p(OpArgs op, VecArgs va, const T2* __restrict__ r,
-                                                  T2* __restrict__ p, KrylovState ks) {
+                                                  T2* __restrict__ p, KrylovState ks, const T2* __restrict__ zbuf,
+                                                  const int* __restrict__ pmode) {
   if (*ks.n_active == 0) return;
   ElemMap em(va.Rp);
   const int t = threadIdx.x;
@@ -332,25 +360,42 @@ __global__ void __launch_bounds__(256) k_krylov_p(OpArgs op, VecArgs va, const T
     if (s >= va.R || !ks.active[s]) continue;
     const SysCoef sc = sys_coef(op, s);
     const T br = (T)ks.beta[2 * s], bi = (T)ks.beta[2 * s + 1];
-    for (int64_t i = rb + ro; i < re; i += em.rpp) {
-      const size_t e = (size_t)i * va.Rp + col;
-      T2 rv = r[e], pv = p[e];
-      T2 d;
-      if constexpr (sizeof(T) == 4) {
-        float2 df = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
-        d.x = df.x; d.y = df.y;
-      } else {
-        double2 dd = diag_f64(va, op, i, sc.b, sc.c, sc.qx, sc.qy, sc.qz);
-        d.x = dd.x; d.y = dd.y;
+    const bool usez = zbuf && pmode && pmode[s];
+    for (int64_t i0 = rb + ro; i0 < re; i0 += 4 * em.rpp) {
+      T2 rv[4], pv[4], d[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + (int64_t)u * em.rpp;
+        if (i < re) {
+          const size_t e = (size_t)i * va.Rp + col;
+          rv[u] = r[e];
+          pv[u] = p[e];
+          if constexpr (sizeof(T) == 4) {
+            float2 df = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
+            d[u].x = df.x; d[u].y = df.y;
+          } else {
+            double2 dd = diag_f64(va, op, i, sc.b, sc.c, sc.qx, sc.qy, sc.qz);
+            d[u].x = dd.x; d[u].y = dd.y;
+          }
+        }
       }
-      T den = (T)1 / (d.x * d.x + d.y * d.y);
-      T2 z;
-      z.x = (rv.x * d.x + rv.y * d.y) * den;
-      z.y = (rv.y * d.x - rv.x * d.y) * den;
-      T2 np;
-      np.x = z.x + br * pv.x - bi * pv.y;
-      np.y = z.y + br * pv.y + bi * pv.x;
-      p[e] = np;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + (int64_t)u * em.rpp;
+        if (i >= re) break;
+        T2 z;
+        if (usez) {
+          z = zbuf[(size_t)i * va.Rp + col];
+        } else {
+          T den = (T)1 / (d[u].x * d[u].x + d[u].y * d[u].y);
+          z.x = (rv[u].x * d[u].x + rv[u].y * d[u].y) * den;
+          z.y = (rv[u].y * d[u].x - rv[u].x * d[u].y) * den;
+        }
+        T2 np;
+        np.x = z.x + br * pv[u].x - bi * pv[u].y;
+        np.y = z.y + br * pv[u].y + bi * pv[u].x;
+        p[(size_t)i * va.Rp + col] = np;
+      }
     }
   }
 }
@@ -450,14 +495,14 @@ void launch_krylov_init_f32_df(const OpArgs& op, const VecArgs& va, const float4
 }
 void launch_krylov_update_f32(const OpArgs& op, const VecArgs& va, float2* x, float2* r, const float2* p,
                               const float2* q, const KrylovState& ks, RedScratch rs, int conj, int sms,
-                              cudaStream_t st) {
+                              cudaStream_t st, int* pmode) {
   int g = elem_grid(va.n, sms);
-  if (conj) k_krylov_update<float, float2, true><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs);
-  else k_krylov_update<float, float2, false><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs);
+  if (conj) k_krylov_update<float, float2, true><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs, pmode);
+  else k_krylov_update<float, float2, false><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs, pmode);
 }
 void launch_krylov_p_f32(const OpArgs& op, const VecArgs& va, const float2* r, float2* p, const KrylovState& ks,
-                         int sms, cudaStream_t st) {
-  k_krylov_p<float, float2><<<elem_grid(va.n, sms), 256, 0, st>>>(op, va, r, p, ks);
+                         int sms, cudaStream_t st, const float2* zbuf, const int* pmode) {
+  k_krylov_p<float, float2><<<elem_grid(va.n, sms), 256, 0, st>>>(op, va, r, p, ks, zbuf, pmode);
 }
 void launch_krylov_init_f64(const OpArgs& op, const VecArgs& va, const double2* r64, const int* ref_active,
                             double2* x, double2* r, double2* p, const KrylovState& ks, double tol, RedScratch rs,
@@ -470,12 +515,12 @@ void launch_krylov_update_f64(const OpArgs& op, const VecArgs& va, double2* x, d
                               const double2* q, const KrylovState& ks, RedScratch rs, int conj, int sms,
                               cudaStream_t st) {
   int g = elem_grid(va.n, sms);
-  if (conj) k_krylov_update<double, double2, true><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs);
-  else k_krylov_update<double, double2, false><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs);
+  if (conj) k_krylov_update<double, double2, true><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs, nullptr);
+  else k_krylov_update<double, double2, false><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs, nullptr);
 }
 void launch_krylov_p_f64(const OpArgs& op, const VecArgs& va, const double2* r, double2* p,
                          const KrylovState& ks, int sms, cudaStream_t st) {
-  k_krylov_p<double, double2><<<elem_grid(va.n, sms), 256, 0, st>>>(op, va, r, p, ks);
+  k_krylov_p<double, double2><<<elem_grid(va.n, sms), 256, 0, st>>>(op, va, r, p, ks, nullptr, nullptr);
 }
 void launch_axpy_u(const VecArgs& va, const double2* d, double2* u, const KrylovState& ks, const RefineState& rf,
                    int sms, cudaStream_t st) {

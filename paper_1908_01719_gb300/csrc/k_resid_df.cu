@@ -78,13 +78,18 @@ __device__ __forceinline__ dd dd_add(dd a, dd b) {
 }
 __device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.h, -a.l}; }
 
-template <int NB, bool TRANSF, int MODE, class TX>
+// NBL: columns of the layout tile per lane; NB (<= NBL): the share of them one
+// thread computes (the residual's register budget keeps NB at 2 so that two
+// blocks fit per SM); blockIdx.y = tile * (NBL / NB) + part.
+template <int NBL, int NB, bool TRANSF, int MODE, class TX>
 __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restrict__ x, float4* __restrict__ u,
                                                   float4* __restrict__ r, RefineState rf, RedScratch rs) {
   if (*rf.n_active == 0) return;
+  constexpr int NSPLIT = NBL / NB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const int r0 = (blockIdx.y * 32 + lane) * NB;
-  const int c0 = blockIdx.y * 32 * NB + lane;
+  const int tile = blockIdx.y / NSPLIT, part = blockIdx.y % NSPLIT;
+  const int r0 = (tile * 32 + lane) * NBL + part * NB;
+  const int c0 = tile * 32 * NBL + lane + 32 * part * NB;
   const bool on = r0 < op.R;
   LaneCoef<NB> lc;
   lane_coef<NB>(op, on ? r0 : 0, rf.active, lc);
@@ -102,8 +107,6 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
     cc[b] = dd_split(lc.c[b]);
     sc[b] = (MODE == 1 && on && r0 + b < op.R) ? (float)rf.scale[r0 + b] : 1.0f;
   }
-  const int64_t per = (op.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(op.n, rb + per);
   double2 acc[NB];
   float2 accf[NB];
 #pragma unroll
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
   }
   int cnt = 0;
   if (warp_any) {
-    for (int64_t row = rb + warp; row < re; row += W) {
+    BT_FOR_CHUNKED_ROWS(row, op.n, warp, W) {
       const int k0 = op.rp[row], k1 = op.rp[row + 1];
       // accumulators: P (P0 x), Q (m x), Z (MD x); re/im, hi/lo
       float Ph[NB][2], Pl[NB][2], Qh[NB][2], Ql[NB][2], Zh[NB][2], Zl[NB][2];
@@ -121,58 +124,74 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
       for (int b = 0; b < NB; ++b)
 #pragma unroll
         for (int c = 0; c < 2; ++c) Ph[b][c] = Pl[b][c] = Qh[b][c] = Ql[b][c] = Zh[b][c] = Zl[b][c] = 0.f;
-      for (int k = k0; k < k1; ++k) {
-        const int j = __ldg(op.col + k);
-        const float4 vh = __ldg(op.pkhi + k), vl = __ldg(op.pklo + k);
-        float p0h, p0l;
-        float mdh = 0.f, mdl = 0.f;
-        if (MODE == 0 || TRANSF) {
-          const float2 kh = __ldg(op.kjmd_hi + k), kl = __ldg(op.kjmd_lo + k);
-          mdh = kh.y;
-          mdl = kl.y;
-          if (MODE == 0) {
-            p0h = kh.x;
-            p0l = kl.x;
-          } else {
-            p0h = vh.x;
-            p0l = vl.x;
-          }
-        } else {
-          p0h = vh.x;
-          p0l = vl.x;
-        }
-        // m = qhat . Pd in double-float
-        float mh = 0.f, ml = 0.f;
-        dd_acc(mh, ml, qx.h, qx.l, vh.y, vl.y);
-        dd_acc(mh, ml, qy.h, qy.l, vh.z, vl.z);
-        dd_acc(mh, ml, qz.h, qz.l, vh.w, vl.w);
-        const dd m = dd_norm(mh, ml);
-        if (!on) continue;
+      // column indices fetched lane-parallel, then DU gathers in flight
+      constexpr int DU = 2;
+      for (int kb = k0; kb < k1; kb += 32) {
+        const int n_in = min(32, k1 - kb);
+        const int jl = lane < n_in ? __ldg(op.col + kb + lane) : 0;
+        for (int t = 0; t < n_in; t += DU) {
+          TX xs[DU][NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          const size_t e = (size_t)j * op.Rp + c0 + 32 * b;
-          float xr, xi, xrl = 0.f, xil = 0.f;
-          if constexpr (MODE == 0) {
-            const float4 xv = __ldg(reinterpret_cast<const float4*>(x) + e);
-            xr = xv.x; xi = xv.y; xrl = xv.z; xil = xv.w;
-            dd_acc(Ph[b][0], Pl[b][0], p0h, p0l, xr, xrl);
-            dd_acc(Ph[b][1], Pl[b][1], p0h, p0l, xi, xil);
-            dd_acc(Qh[b][0], Ql[b][0], m.h, m.l, xr, xrl);
-            dd_acc(Qh[b][1], Ql[b][1], m.h, m.l, xi, xil);
-            if constexpr (TRANSF) {
-              dd_acc(Zh[b][0], Zl[b][0], mdh, mdl, xr, xrl);
-              dd_acc(Zh[b][1], Zl[b][1], mdh, mdl, xi, xil);
+          for (int u = 0; u < DU; ++u) {
+            const int tt = t + u;
+            const int j = __shfl_sync(0xffffffffu, jl, tt & 31);
+            if (tt < n_in && on) {
+#pragma unroll
+              for (int b = 0; b < NB; ++b) xs[u][b] = __ldg(x + (size_t)j * op.Rp + c0 + 32 * b);
             }
-          } else {
-            const float2 xv = __ldg(reinterpret_cast<const float2*>(x) + e);
-            xr = xv.x; xi = xv.y;
-            dd_acc1(Ph[b][0], Pl[b][0], p0h, p0l, xr);
-            dd_acc1(Ph[b][1], Pl[b][1], p0h, p0l, xi);
-            dd_acc1(Qh[b][0], Ql[b][0], m.h, m.l, xr);
-            dd_acc1(Qh[b][1], Ql[b][1], m.h, m.l, xi);
-            if constexpr (TRANSF) {
-              dd_acc1(Zh[b][0], Zl[b][0], mdh, mdl, xr);
-              dd_acc1(Zh[b][1], Zl[b][1], mdh, mdl, xi);
+          }
+#pragma unroll
+          for (int u = 0; u < DU; ++u) {
+            const int k = kb + t + u;
+            if (t + u >= n_in) break;
+            const float4 vh = __ldg(op.pkhi + k), vl = __ldg(op.pklo + k);
+            float p0h, p0l;
+            float mdh = 0.f, mdl = 0.f;
+            if (MODE == 0 || TRANSF) {
+              const float2 kh = __ldg(op.kjmd_hi + k), kl = __ldg(op.kjmd_lo + k);
+              mdh = kh.y;
+              mdl = kl.y;
+              if (MODE == 0) {
+                p0h = kh.x;
+                p0l = kl.x;
+              } else {
+                p0h = vh.x;
+                p0l = vl.x;
+              }
+            } else {
+              p0h = vh.x;
+              p0l = vl.x;
+            }
+            // m = qhat . Pd in double-float
+            float mh = 0.f, ml = 0.f;
+            dd_acc(mh, ml, qx.h, qx.l, vh.y, vl.y);
+            dd_acc(mh, ml, qy.h, qy.l, vh.z, vl.z);
+            dd_acc(mh, ml, qz.h, qz.l, vh.w, vl.w);
+            const dd m = dd_norm(mh, ml);
+            if (!on) continue;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              if constexpr (MODE == 0) {
+                const float4 xv = xs[u][b];
+                dd_acc(Ph[b][0], Pl[b][0], p0h, p0l, xv.x, xv.z);
+                dd_acc(Ph[b][1], Pl[b][1], p0h, p0l, xv.y, xv.w);
+                dd_acc(Qh[b][0], Ql[b][0], m.h, m.l, xv.x, xv.z);
+                dd_acc(Qh[b][1], Ql[b][1], m.h, m.l, xv.y, xv.w);
+                if constexpr (TRANSF) {
+                  dd_acc(Zh[b][0], Zl[b][0], mdh, mdl, xv.x, xv.z);
+                  dd_acc(Zh[b][1], Zl[b][1], mdh, mdl, xv.y, xv.w);
+                }
+              } else {
+                const float2 xv = xs[u][b];
+                dd_acc1(Ph[b][0], Pl[b][0], p0h, p0l, xv.x);
+                dd_acc1(Ph[b][1], Pl[b][1], p0h, p0l, xv.y);
+                dd_acc1(Qh[b][0], Ql[b][0], m.h, m.l, xv.x);
+                dd_acc1(Qh[b][1], Ql[b][1], m.h, m.l, xv.y);
+                if constexpr (TRANSF) {
+                  dd_acc1(Zh[b][0], Zl[b][0], mdh, mdl, xv.x);
+                  dd_acc1(Zh[b][1], Zl[b][1], mdh, mdl, xv.y);
+                }
+              }
             }
           }
         }
@@ -242,24 +261,23 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
     default: { constexpr int NB_ = 1; __VA_ARGS__; } break;     \
   }
 
+template <int NBL, int MODE, class TX>
+static void resid_df_t(const OpArgs& op, const TX* x, float4* u, float4* r, const RefineState& rf, RedScratch rs,
+                       int sms, cudaStream_t st) {
+  constexpr int NB = NBL < 2 ? NBL : 2;
+  dim3 grid(spmm_grid_rows(op.n, sms), ((op.R + 32 * NBL - 1) / (32 * NBL)) * (NBL / NB));
+  if (op.transformed) k_resid_df<NBL, NB, true, MODE, TX><<<grid, 256, 0, st>>>(op, x, u, r, rf, rs);
+  else k_resid_df<NBL, NB, false, MODE, TX><<<grid, 256, 0, st>>>(op, x, u, r, rf, rs);
+}
+
 void launch_resid0_df(const OpArgs& op, const float4* u, float4* r, const RefineState& rf, RedScratch rs, int nb,
                       int sms, cudaStream_t st) {
-  BT_DISPATCH_NB(nb, {
-    dim3 grid(spmm_grid_rows(op.n, sms), (op.R + 32 * NB_ - 1) / (32 * NB_));
-    if (op.transformed)
-      k_resid_df<NB_, true, 0, float4><<<grid, 256, 0, st>>>(op, u, const_cast<float4*>(u), r, rf, rs);
-    else
-      k_resid_df<NB_, false, 0, float4><<<grid, 256, 0, st>>>(op, u, const_cast<float4*>(u), r, rf, rs);
-  })
+  BT_DISPATCH_NB(nb, { resid_df_t<NB_, 0, float4>(op, u, const_cast<float4*>(u), r, rf, rs, sms, st); })
 }
 
 void launch_resid_sub_df(const OpArgs& op, const float2* d, float4* u, float4* r, const RefineState& rf,
                          RedScratch rs, int nb, int sms, cudaStream_t st) {
-  BT_DISPATCH_NB(nb, {
-    dim3 grid(spmm_grid_rows(op.n, sms), (op.R + 32 * NB_ - 1) / (32 * NB_));
-    if (op.transformed) k_resid_df<NB_, true, 1, float2><<<grid, 256, 0, st>>>(op, d, u, r, rf, rs);
-    else k_resid_df<NB_, false, 1, float2><<<grid, 256, 0, st>>>(op, d, u, r, rf, rs);
-  })
+  BT_DISPATCH_NB(nb, { resid_df_t<NB_, 1, float2>(op, d, u, r, rf, rs, sms, st); })
 }
 
 __global__ void k_fill_u_df(VecArgs va, float4* __restrict__ u) {

@@ -22,9 +22,8 @@ constexpr int KU = 4;  // gathers in flight per warp
 
 int spmm_grid_rows(int64_t n, int sms) {
   int64_t g = (int64_t)sms * REDUCE_BLOCKS_PER_SM;
-  int64_t per = (n + g - 1) / g;
-  if (per < 8) per = 8;
-  return (int)((n + per - 1) / per);
+  int64_t chunks = (n + ROW_CHUNK - 1) / ROW_CHUNK;
+  return (int)std::max<int64_t>(1, std::min(g, chunks));
 }
 
 // ---------------------------------------------------------------- Krylov apply
@@ -53,8 +52,6 @@ __global__ void __launch_bounds__(256) k_spmm_krylov(OpArgs op, const T2* __rest
     cb[b] = (T)lc.b[b];
     cc[b] = (T)lc.c[b];
   }
-  const int64_t per = (op.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(op.n, rb + per);
   double2 acc[NB];
   T2 accf[NB];
 #pragma unroll
@@ -64,7 +61,7 @@ __global__ void __launch_bounds__(256) k_spmm_krylov(OpArgs op, const T2* __rest
   }
   int cnt = 0;
   if (warp_any) {
-    for (int64_t row = rb + warp; row < re; row += W) {
+    BT_FOR_CHUNKED_ROWS(row, op.n, warp, W) {
       const int k0 = op.rp[row], k1 = op.rp[row + 1];
       T2 P[NB], Q[NB];
 #pragma unroll
@@ -142,24 +139,7 @@ __global__ void __launch_bounds__(256) k_spmm_krylov(OpArgs op, const T2* __rest
   }
   block_partials<NB>(acc, on ? r0 : op.Rp, op.Rp, rs.part);
   if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
-  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 pq) {
-    if (!ks.active[s]) {
-      ks.alpha[2 * s] = 0; ks.alpha[2 * s + 1] = 0;
-      return;
-    }
-    double2 rho = make_double2(ks.rho[2 * s], ks.rho[2 * s + 1]);
-    double den = pq.x * pq.x + pq.y * pq.y;
-    if (!(den > 0) || !isfinite(den)) {
-      ks.alpha[2 * s] = 0; ks.alpha[2 * s + 1] = 0;
-      ks.active[s] = 0;
-      ks.status[s] = (isfinite(den) ? BT_ENOCONV : BT_ENAN);
-      atomicSub(ks.n_active, 1);
-      return;
-    }
-    // alpha = rho / pq
-    ks.alpha[2 * s] = (rho.x * pq.x + rho.y * pq.y) / den;
-    ks.alpha[2 * s + 1] = (rho.y * pq.x - rho.x * pq.y) / den;
-  });
+  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
 }
 
 template <int NB, bool TRANSF, bool CONJ>
@@ -229,13 +209,11 @@ __global__ void __launch_bounds__(256) k_resid64(OpArgs op, const TX2* __restric
   double sc[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) sc[b] = (MODE == 1 && on) ? rf.scale[r0 + b] : 1.0;
-  const int64_t per = (op.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(op.n, rb + per);
   double2 acc[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) acc[b] = make_double2(0, 0);
   if (warp_any) {
-    for (int64_t row = rb + warp; row < re; row += W) {
+    BT_FOR_CHUNKED_ROWS(row, op.n, warp, W) {
       const int k0 = op.rp[row], k1 = op.rp[row + 1];
       double2 P[NB], Q[NB];
 #pragma unroll

@@ -91,15 +91,16 @@ __global__ void __launch_bounds__(256) k_spmm_krylov_narrow(OpArgs op, const dou
     cb[b] = cf.bq2 * qq * qq;
     cc[b] = cf.cq * qq;
   }
-  const int64_t per = (op.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(op.n, rb + per);
   double2 acc[RM];
 #pragma unroll
   for (int b = 0; b < RM; ++b) acc[b] = make_double2(0, 0);
   // all lanes of a warp run the same number of row iterations (shuffles)
-  for (int64_t base = rb; base < re; base += ngrp) {
-    const int64_t row = base + grp;
-    const bool ok = row < re;
+  // round-robin chunks of ngrp rows (one per 8-lane group); the loop trip
+  // count is uniform over the block so the shuffles stay converged
+  for (int64_t ch = blockIdx.x; ch * ngrp < op.n; ch += gridDim.x) {
+    const int64_t row = ch * ngrp + grp;
+    const bool ok = row < op.n;
+    const int64_t rb = ch * ngrp;
     double2 P[RM], Q[RM], Z[RM];
     narrow_row<RM, TRANSF>(op, ok ? row : rb, ok ? g : (1 << 30), qx, qy, qz, nullptr, p, P, Q, Z);
     if (ok && g == 0) {
@@ -122,23 +123,7 @@ __global__ void __launch_bounds__(256) k_spmm_krylov_narrow(OpArgs op, const dou
   }
   narrow_partials<RM>(acc, g, op.Rp, rs.part);
   if (!last_block(rs.counter, gridDim.x)) return;
-  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 pq) {
-    if (!ks.active[s]) {
-      ks.alpha[2 * s] = 0; ks.alpha[2 * s + 1] = 0;
-      return;
-    }
-    double2 rho = make_double2(ks.rho[2 * s], ks.rho[2 * s + 1]);
-    double den = pq.x * pq.x + pq.y * pq.y;
-    if (!(den > 0) || !isfinite(den)) {
-      ks.alpha[2 * s] = 0; ks.alpha[2 * s + 1] = 0;
-      ks.active[s] = 0;
-      ks.status[s] = (isfinite(den) ? BT_ENOCONV : BT_ENAN);
-      atomicSub(ks.n_active, 1);
-      return;
-    }
-    ks.alpha[2 * s] = (rho.x * pq.x + rho.y * pq.y) / den;
-    ks.alpha[2 * s + 1] = (rho.y * pq.x - rho.x * pq.y) / den;
-  });
+  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
 }
 
 // r = op_{P0 = K+J}(u) (mode 0 of the refinement residual), FP64, R <= 4
@@ -159,14 +144,15 @@ __global__ void __launch_bounds__(256) k_resid0_narrow(OpArgs op, const double2*
     cb[b] = cf.bq2 * qq * qq;
     cc[b] = cf.cq * qq;
   }
-  const int64_t per = (op.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(op.n, rb + per);
   double2 acc[RM];
 #pragma unroll
   for (int b = 0; b < RM; ++b) acc[b] = make_double2(0, 0);
-  for (int64_t base = rb; base < re; base += ngrp) {
-    const int64_t row = base + grp;
-    const bool ok = row < re;
+  // round-robin chunks of ngrp rows (one per 8-lane group); the loop trip
+  // count is uniform over the block so the shuffles stay converged
+  for (int64_t ch = blockIdx.x; ch * ngrp < op.n; ch += gridDim.x) {
+    const int64_t row = ch * ngrp + grp;
+    const bool ok = row < op.n;
+    const int64_t rb = ch * ngrp;
     double2 P[RM], Q[RM], Z[RM];
     narrow_row<RM, TRANSF>(op, ok ? row : rb, ok ? g : (1 << 30), qx, qy, qz, op.p0_64, u, P, Q, Z);
     if (ok && g == 0) {
