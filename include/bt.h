@@ -216,6 +216,31 @@ bt_status bt_precond_eval(bt_ctx* ctx, int64_t n, const float* feat, const doubl
 bt_status bt_save_precond(const bt_ctx* ctx, float* w);
 bt_status bt_load_precond(bt_ctx* ctx, const float* w);
 
+/* ---------------------------------------------------------------- allocation-free gradient
+ * bt_precond_grad_noalloc computes what bt_precond_eval computes for the loss
+ * and gradient of the preconditioner network, for callers that cannot
+ * allocate device memory: code running inside CUDA stream capture, under a
+ * framework that owns every device allocation, or in a service that forbids
+ * allocation after start-up.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine; its scratch is a fixed file-scope device array of about
+ * 2.2 MB that every GPU loading the library holds until the process exits.
+ * The paper has no counterpart of this entry point.
+ *
+ * All pointers are DEVICE pointers owned by the caller: w [BT_PRECOND_NPARAM]
+ * FP32 weights (converted to bfloat16 inside), feat [n][5] raw features,
+ * G [n][81], h [n][9] (FP32), grad [BT_PRECOND_NPARAM] (FP64, out), loss [n]
+ * per-sample losses (FP32, out; their mean is bt_precond_eval's loss).
+ * stream: a cudaStream_t (NULL = default stream); the call is asynchronous.
+ * 1 <= n <= BT_NOALLOC_MAX_SAMPLES, else BT_EINVAL (nothing is launched).
+ * The first call on a device looks up the scratch array's device address;
+ * make that first call before any stream capture.  All calls on a device share
+ * the scratch array, so calls that overlap on the GPU (different streams, no
+ * ordering between them) race; order them on one stream.  No context is used:
+ * errors are reported by the return code only. */
+enum { BT_NOALLOC_MAX_SAMPLES = 2048 };
+bt_status bt_precond_grad_noalloc(const float* w, int32_t n, const float* feat, const float* G, const float* h,
+                                  double* grad, float* loss, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

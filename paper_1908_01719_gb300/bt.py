@@ -27,7 +27,8 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_get_dofmap", "bt_get_pattern", "bt_assemble", "bt_get_plane", "bt_set_sequence",
            "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats",
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
-           "bt_precond_eval", "bt_save_precond", "bt_load_precond"]
+           "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc"]
+BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
 
@@ -82,6 +83,7 @@ def lib():
             "bt_precond_eval": [P, I64, P, P, P, P, P, P],
             "bt_save_precond": [P, P],
             "bt_load_precond": [P, P],
+            "bt_precond_grad_noalloc": [P, I32, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -273,3 +275,11 @@ def bt_load_precond(ctx, w):
     w = np.ascontiguousarray(w, dtype=np.float32)
     assert len(w) == BT_PRECOND_NPARAM
     _check(ctx, lib().bt_load_precond(ctx, _ptr(w)))
+
+
+def bt_precond_grad_noalloc(w_ptr, n, feat_ptr, G_ptr, h_ptr, grad_ptr, loss_ptr, stream=0):
+    """Device-pointer call of the allocation-free gradient (see include/bt.h);
+    returns the status code."""
+    V = C.c_void_p
+    return lib().bt_precond_grad_noalloc(V(w_ptr), int(n), V(feat_ptr), V(G_ptr), V(h_ptr), V(grad_ptr),
+                                         V(loss_ptr), V(stream))
