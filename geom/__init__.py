@@ -361,3 +361,40 @@ def slab_1d(nx: int, L: float = 40.0, w: float = 1.0, dt: float = 50.0, D: float
     return Problem("slab1d", xyz, tets, np.zeros(len(tets), np.int32), np.array([D]),
                    np.array([NO_MEMBRANE]), 0, lo, hi, dt, delta, Delta, Delta + delta,
                    np.array([[1.0, 0.0, 0.0]]), np.array([b]))
+
+
+def union(problems, name="batch"):
+    """Disjoint union of several geometries as one input mesh (the uneven
+    batch): each geometry is translated so that its box centre sits at the
+    origin (the origin of g.x is then each geometry's own centre), node and
+    compartment ids are offset, and the PGSE timing of each geometry is kept
+    in `segments`.  All geometries must share dt and the directions/b-values
+    (the first problem's are used)."""
+    xyz, tets, cmpt, D, kap = [], [], [], [], []
+    node_off, c_off = [0], 0
+    half = 0.0
+    for p in problems:
+        c = 0.5 * (np.asarray(p.box_lo) + np.asarray(p.box_hi))
+        xyz.append(p.xyz - c)
+        tets.append(p.tets + node_off[-1])
+        cmpt.append(p.tet_cmpt + c_off)
+        D.append(p.D_cmpt)
+        kap.append(p.kappa_cmpt)
+        node_off.append(node_off[-1] + len(p.xyz))
+        c_off += p.n_cmpt
+        half = max(half, float(np.max(np.asarray(p.box_hi) - c)))
+    p0 = problems[0]
+    out = Problem(name, np.concatenate(xyz), np.concatenate(tets).astype(np.int32),
+                  np.concatenate(cmpt).astype(np.int32), np.concatenate(D), np.concatenate(kap), 0,
+                  np.full(3, -half), np.full(3, half), p0.dt, p0.delta, p0.Delta, p0.TE, p0.dirs, p0.bvals)
+    out.segments = {"node_off": np.array(node_off, dtype=np.int64),
+                    "delta": np.array([p.delta for p in problems]),
+                    "Delta": np.array([p.Delta for p in problems]),
+                    "TE": np.array([p.TE for p in problems])}
+    return out
+
+
+def cfg5(n_geom: int = 32, scale: float = 1.0, dt: float = 50.0):
+    """The uneven batch: geometries 0..n_geom-1 of cfg5_geometry (grids scaled
+    by `scale` for reduced copies) as one union mesh."""
+    return union([cfg5_geometry(g, dt=dt, scale=scale) for g in range(n_geom)], name="cfg5")

@@ -113,6 +113,17 @@ bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals);
  * paper's f(t^n), f(t^{n-1})); F(t_n) is exact.  Needs bt_assemble first. */
 enum { BT_PGSE = 0 };
 bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta_us, double Delta_us, double TE_us);
+/* Several geometries of uneven size in one context (the uneven batch): after
+ * uploading their disjoint union as one mesh (nodes of geometry g =
+ * [node_off[g], node_off[g+1]), every tetrahedron inside one geometry, each
+ * geometry centred on the box centre so that g.x uses its own origin) and
+ * assembling, give each geometry its PGSE timing.  The time loop then runs all
+ * geometries together, each right-hand side set repeated per geometry, and
+ * freezes a geometry after its own TE.  System (signal) index s = g R + r.
+ * Replaces bt_set_sequence; call bt_set_gradients afterwards.  Lab frame or
+ * Neumann transformed frame only (no periodic box). */
+bt_status bt_set_segments(bt_ctx* ctx, int32_t G, const int64_t* node_off, const double* delta_us,
+                          const double* Delta_us, const double* TE_us);
 /* Directions dirs [3*n_dir] (normalised here) and b-values bvals [n_b]
  * (s/mm^2).  Right-hand side r = d*n_b + j uses dirs[d], bvals[j];
  * q = gamma |g| = sqrt(b / (delta^2 (Delta - delta/3))) (Eq. b_value, PGSE). */
@@ -149,10 +160,11 @@ typedef struct bt_solver_opts {
 bt_status bt_default_opts(bt_solver_opts* o);
 /* Run the whole time loop from u^0 = 1 to TE for the selected RHS. */
 bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts);
-/* Results of the last bt_run.  S_re_im [2R] (re, im per RHS, um^3);
- * err_est [R] sum over steps of the final relative refinement residual
- * |r|/|r_0| (an upper proxy of the relative signal error); status [R]
- * BT_OK / BT_ENOCONV / BT_ENAN per RHS.  Any pointer may be NULL. */
+/* Results of the last bt_run, per system s = g R + r (G = 1 without
+ * segments).  S_re_im [2 G R] (re, im, um^3); err_est [G R] sum over steps
+ * of the final relative refinement residual |r|/|r_0| (an upper proxy of the
+ * relative signal error); status [G R] BT_OK / BT_ENOCONV / BT_ENAN.  Any
+ * pointer may be NULL. */
 bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t* status);
 /* Counters of the last bt_run (any pointer may be NULL): time steps, total
  * Krylov iterations (summed over solves, not RHS), refinement passes, fused

@@ -27,7 +27,8 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_get_dofmap", "bt_get_pattern", "bt_assemble", "bt_get_plane", "bt_set_sequence",
            "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats",
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
-           "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc"]
+           "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
+           "bt_set_segments"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -72,6 +73,7 @@ def lib():
             "bt_get_plane": [P, C.c_int, P],
             "bt_set_sequence": [P, C.c_int, D, D, D],
             "bt_set_gradients": [P, I32, P, I32, P],
+            "bt_set_segments": [P, I32, P, P, P, P],
             "bt_default_opts": [C.POINTER(bt_solver_opts)],
             "bt_run": [P, C.c_int, C.POINTER(bt_solver_opts)],
             "bt_get_signals": [P, P, P, P],
@@ -173,6 +175,14 @@ def bt_get_plane(ctx, which):
 
 def bt_set_sequence(ctx, kind, delta, Delta, TE):
     _check(ctx, lib().bt_set_sequence(ctx, int(kind), float(delta), float(Delta), float(TE)))
+
+
+def bt_set_segments(ctx, node_off, delta, Delta, TE):
+    no = np.ascontiguousarray(node_off, dtype=np.int64)
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    D = np.ascontiguousarray(Delta, dtype=np.float64)
+    T = np.ascontiguousarray(TE, dtype=np.float64)
+    _check(ctx, lib().bt_set_segments(ctx, len(no) - 1, _ptr(no), _ptr(d), _ptr(D), _ptr(T)))
 
 
 def bt_set_gradients(ctx, dirs, bvals):

@@ -304,7 +304,16 @@ bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta, double Delta, dou
   for (int n = 1; n <= N; ++n) ctx->fbar[n - 1] = (ctx->F[n] - ctx->F[n - 1]) / ctx->dt;
   if (ctx->transformed && std::fabs(ctx->F[N]) > 1e-12 * delta)
     return fail(ctx, BT_EINVAL, "bt_set_sequence: F(TE) != 0 in the transformed frame");
+  ctx->G = 1;
+  ctx->seg_row0 = {0, ctx->mesh.n_dof};
+  ctx->seg_delta = {delta};
+  ctx->seg_Delta = {Delta};
+  ctx->seg_TE = {TE};
+  ctx->seg_N = {N};
+  ctx->seg_fbar = {ctx->fbar};
+  ctx->seg_F = {ctx->F};
   ctx->have_seq = true;
+  ctx->R = 0;
   return BT_OK;
 }
 
@@ -313,29 +322,100 @@ bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32
   if (!ctx->have_seq) return fail(ctx, BT_ESTATE, "bt_set_gradients: set the sequence first");
   if (n_dir <= 0 || n_b <= 0 || !dirs || !bvals || (int64_t)n_dir * n_b > 1024)
     return fail(ctx, BT_EINVAL, "bt_set_gradients: need 1 <= n_dir * n_b <= 1024");
-  ctx->n_dir = n_dir;
-  ctx->n_b = n_b;
-  ctx->R = n_dir * n_b;
-  ctx->qhat_rhs.resize(3 * ctx->R);
-  ctx->q_rhs.resize(ctx->R);
-  const double d = ctx->delta, D = ctx->Delta;
-  const double intF2 = d * d * (D - d / 3.0);  // int_0^TE F^2 for PGSE
-  for (int i = 0; i < n_dir; ++i) {
-    double nx = dirs[3 * i], ny = dirs[3 * i + 1], nz = dirs[3 * i + 2];
-    double nr = std::sqrt(nx * nx + ny * ny + nz * nz);
-    if (!(nr > 0) || !std::isfinite(nr)) return fail(ctx, BT_EINVAL, "bt_set_gradients: zero direction");
-    for (int j = 0; j < n_b; ++j) {
-      if (!(bvals[j] >= 0) || !std::isfinite(bvals[j])) return fail(ctx, BT_EINVAL, "bt_set_gradients: b < 0");
-      int r = i * n_b + j;
-      ctx->qhat_rhs[3 * r] = nx / nr;
-      ctx->qhat_rhs[3 * r + 1] = ny / nr;
-      ctx->qhat_rhs[3 * r + 2] = nz / nr;
-      ctx->q_rhs[r] = std::sqrt(bvals[j] / intF2);  // b = q^2 int F^2 (Eq. b_value)
+  const int R = n_dir * n_b, G = ctx->G;
+  std::vector<double> qh(3 * (size_t)G * R), qv((size_t)G * R);
+  for (int g = 0; g < G; ++g) {
+    const double d = ctx->seg_delta[g], D = ctx->seg_Delta[g];
+    const double intF2 = d * d * (D - d / 3.0);  // int_0^TE F^2 for PGSE
+    for (int i = 0; i < n_dir; ++i) {
+      double nx = dirs[3 * i], ny = dirs[3 * i + 1], nz = dirs[3 * i + 2];
+      double nr = std::sqrt(nx * nx + ny * ny + nz * nz);
+      if (!(nr > 0) || !std::isfinite(nr)) return fail(ctx, BT_EINVAL, "bt_set_gradients: zero direction");
+      for (int j = 0; j < n_b; ++j) {
+        if (!(bvals[j] >= 0) || !std::isfinite(bvals[j])) return fail(ctx, BT_EINVAL, "bt_set_gradients: b < 0");
+        const size_t s = (size_t)g * R + i * n_b + j;
+        qh[3 * s] = nx / nr;
+        qh[3 * s + 1] = ny / nr;
+        qh[3 * s + 2] = nz / nr;
+        qv[s] = std::sqrt(bvals[j] / intF2);  // b = q^2 int F^2 (Eq. b_value)
+      }
     }
   }
-  ctx->S.assign(2 * ctx->R, 0.0);
-  ctx->err_est.assign(ctx->R, 0.0);
-  ctx->status.assign(ctx->R, BT_OK);
+  ctx->n_dir = n_dir;
+  ctx->n_b = n_b;
+  ctx->R = R;
+  ctx->qhat_rhs = qh;
+  ctx->q_rhs = qv;
+  ctx->S.assign(2 * (size_t)G * R, 0.0);
+  ctx->err_est.assign((size_t)G * R, 0.0);
+  ctx->status.assign((size_t)G * R, BT_OK);
+  return BT_OK;
+}
+
+// Several geometries in one context: segment g = nodes [node_off[g],
+// node_off[g+1]) with its own PGSE timing; the time loop runs to the largest
+// TE and freezes each segment after its own last step.
+bt_status bt_set_segments(bt_ctx* ctx, int32_t G, const int64_t* node_off, const double* delta,
+                          const double* Delta, const double* TE) {
+  if (!ctx) return BT_EINVAL;
+  if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_set_segments: assemble first");
+  if (G < 1 || !node_off || !delta || !Delta || !TE) return fail(ctx, BT_EINVAL, "bt_set_segments: bad arguments");
+  const HostMesh& m = ctx->mesh;
+  if (m.pmask) return fail(ctx, BT_EINVAL, "bt_set_segments: periodic boxes hold one geometry");
+  if (node_off[0] != 0 || node_off[G] != m.n_nodes) return fail(ctx, BT_EINVAL, "bt_set_segments: node offsets must cover the mesh");
+  for (int g = 0; g < G; ++g)
+    if (node_off[g + 1] <= node_off[g]) return fail(ctx, BT_EINVAL, "bt_set_segments: empty segment");
+  // every tetrahedron inside one segment
+  for (int64_t t = 0; t < m.n_tets; ++t) {
+    const int32_t v0 = m.tets[4 * t];
+    const int g = (int)(std::upper_bound(node_off, node_off + G + 1, (int64_t)v0) - node_off) - 1;
+    for (int a2 = 1; a2 < 4; ++a2)
+      if (m.tets[4 * t + a2] < node_off[g] || m.tets[4 * t + a2] >= node_off[g + 1])
+        return fail(ctx, BT_EINVAL, "bt_set_segments: a tetrahedron spans two segments");
+  }
+  std::vector<int64_t> row0(G + 1);
+  for (int g = 0; g <= G; ++g)
+    row0[g] = std::lower_bound(m.dof_node.begin(), m.dof_node.end(), (int32_t)std::min<int64_t>(node_off[g], INT32_MAX)) -
+              m.dof_node.begin();
+  row0[G] = m.n_dof;
+  for (int g = 0; g < G; ++g)
+    if (row0[g + 1] <= row0[g]) return fail(ctx, BT_EINVAL, "bt_set_segments: segment without dofs");
+  std::vector<int> N(G);
+  std::vector<std::vector<double>> fb(G), FF(G);
+  for (int g = 0; g < G; ++g) {
+    const double d = delta[g], D = Delta[g], T = TE[g];
+    if (!(d > 0) || !(D >= d) || !(T >= D + d - 1e-9 * T))
+      return fail(ctx, BT_EINVAL, "bt_set_segments: need 0 < delta <= Delta and TE >= Delta + delta");
+    const double ns = T / ctx->dt;
+    N[g] = (int)std::llround(ns);
+    if (std::fabs(ns - N[g]) > 1e-9 * std::max(1.0, ns) || N[g] < 1)
+      return fail(ctx, BT_EINVAL, "bt_set_segments: TE must be an integer multiple of dt");
+    auto Ft = [&](double t) {
+      double a3 = std::min(std::max(t, 0.0), d);
+      double b3 = std::min(std::max(t - D, 0.0), d);
+      return a3 - b3;
+    };
+    FF[g].resize(N[g] + 1);
+    fb[g].resize(N[g]);
+    for (int n = 0; n <= N[g]; ++n) FF[g][n] = Ft(n * ctx->dt);
+    for (int n = 1; n <= N[g]; ++n) fb[g][n - 1] = (FF[g][n] - FF[g][n - 1]) / ctx->dt;
+  }
+  ctx->G = G;
+  ctx->seg_row0 = row0;
+  ctx->seg_delta.assign(delta, delta + G);
+  ctx->seg_Delta.assign(Delta, Delta + G);
+  ctx->seg_TE.assign(TE, TE + G);
+  ctx->seg_N = N;
+  ctx->seg_fbar = fb;
+  ctx->seg_F = FF;
+  ctx->delta = delta[0];
+  ctx->Delta = Delta[0];
+  ctx->TE = TE[0];
+  ctx->n_steps = *std::max_element(N.begin(), N.end());
+  ctx->fbar = fb[0];
+  ctx->F = FF[0];
+  ctx->have_seq = true;
+  ctx->R = 0;
   return BT_OK;
 }
 
@@ -450,6 +530,9 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   int rb = o.rhs_begin, re = o.rhs_end;
   if (rb == 0 && re == 0) re = ctx->R;
   if (rb < 0 || re > ctx->R || rb >= re) return fail(ctx, BT_EINVAL, "bt_run: bad RHS range");
+  const int G = ctx->G;
+  if (G > 1 && (rb != 0 || re != ctx->R)) return fail(ctx, BT_EINVAL, "bt_run: RHS ranges need a single segment");
+  if (G > 1 && (learned || col)) return fail(ctx, BT_EINVAL, "bt_run: learned mode and data collection need a single segment");
   if (o.max_iter < 1 || o.max_refine < 1 || o.check_every < 1 || !(o.tol_fp64 > 0) || !(o.tol_inner > 0) ||
       !(o.tol_ref > 0))
     return fail(ctx, BT_EINVAL, "bt_run: bad solver options");
@@ -463,15 +546,35 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   const bool plain = mode == BT_MODE_PLAIN_FP64;
   const bool df = !plain && !(o.flags & BT_OPT_RESID_FP64);
   const bool prof = (o.flags & BT_OPT_PROFILE) != 0;
-  const bool narrow = plain && Rs <= 4;  // lanes over nonzeros for the per-direction FP64 solve
+  const bool narrow = plain && Rs <= 4 && G == 1;  // lanes over nonzeros for the per-direction FP64 solve
+  const int SY = G * Rs;                            // systems: G segments x Rs right-hand sides
   const int conj = ctx->transformed ? 1 : 0;  // CG (Hermitian) vs COCG (complex symmetric)
 
   // per-run device buffers
-  CK(ensure(ctx->d_q, Rs));
-  CK(ensure(ctx->d_qhat, 3 * (size_t)Rs));
-  CK(cudaMemcpyAsync(ctx->d_q.p, ctx->q_rhs.data() + rb, Rs * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->d_qhat.p, ctx->qhat_rhs.data() + 3 * rb, 3 * Rs * sizeof(double), cudaMemcpyHostToDevice,
+  CK(ensure(ctx->d_q, SY));
+  CK(ensure(ctx->d_qhat, 3 * (size_t)SY));
+  CK(cudaMemcpyAsync(ctx->d_q.p, ctx->q_rhs.data() + rb, SY * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_qhat.p, ctx->qhat_rhs.data() + 3 * rb, 3 * SY * sizeof(double), cudaMemcpyHostToDevice,
                      st));
+  // block plan: blocks in proportion to segment rows, each block in one segment
+  {
+    const int target = ctx->sms * REDUCE_BLOCKS_PER_SM;
+    std::vector<int> blk_seg, blk0(G + 1, 0);
+    for (int g = 0; g < G; ++g) {
+      const int64_t rows = ctx->seg_row0[g + 1] - ctx->seg_row0[g];
+      const int64_t chunks = (rows + ROW_CHUNK - 1) / ROW_CHUNK;
+      int64_t nbg = (int64_t)std::llround((double)target * rows / (double)n);
+      nbg = std::max<int64_t>(1, std::min(nbg, chunks));
+      blk0[g + 1] = blk0[g] + (int)nbg;
+      for (int64_t k = 0; k < nbg; ++k) blk_seg.push_back(g);
+    }
+    ctx->nblk = blk0[G];
+    CK(upload(ctx->d_blk_seg, blk_seg, st));
+    CK(upload(ctx->d_blk0, blk0, st));
+    CK(upload(ctx->d_row0, ctx->seg_row0, st));
+    CK(upload(ctx->d_seg_N, ctx->seg_N, st));
+  }
+  const SegPlan sp{ctx->d_blk_seg.p, ctx->d_blk0.p, ctx->d_row0.p, G, ctx->nblk};
   if (plain) {
     CK(ensure(ctx->u64, NE));
     CK(ensure(ctx->r64, NE));
@@ -492,28 +595,28 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     CK(ensure(ctx->p32, NE));
     CK(ensure(ctx->q32, NE));
   }
-  CK(ensure(ctx->ks_rho, 2 * (size_t)Rs));
-  CK(ensure(ctx->ks_alpha, 2 * (size_t)Rs));
-  CK(ensure(ctx->ks_beta, 2 * (size_t)Rs));
-  CK(ensure(ctx->ks_rr0, Rs));
-  CK(ensure(ctx->ks_rr, Rs));
-  CK(ensure(ctx->ks_tol2, Rs));
-  CK(ensure(ctx->ks_iter, Rs));
-  CK(ensure(ctx->ks_active, Rs));
-  CK(ensure(ctx->ks_status, Rs));
-  CK(ensure(ctx->ks_rr_best, Rs));
-  CK(ensure(ctx->ks_it_best, Rs));
+  CK(ensure(ctx->ks_rho, 2 * (size_t)SY));
+  CK(ensure(ctx->ks_alpha, 2 * (size_t)SY));
+  CK(ensure(ctx->ks_beta, 2 * (size_t)SY));
+  CK(ensure(ctx->ks_rr0, SY));
+  CK(ensure(ctx->ks_rr, SY));
+  CK(ensure(ctx->ks_tol2, SY));
+  CK(ensure(ctx->ks_iter, SY));
+  CK(ensure(ctx->ks_active, SY));
+  CK(ensure(ctx->ks_status, SY));
+  CK(ensure(ctx->ks_rr_best, SY));
+  CK(ensure(ctx->ks_it_best, SY));
   CK(ensure(ctx->n_active, 4));
-  CK(ensure(ctx->rf_r0n2, Rs));
-  CK(ensure(ctx->rf_rk2, Rs));
-  CK(ensure(ctx->rf_scale, Rs));
-  CK(ensure(ctx->rf_err, Rs));
-  CK(ensure(ctx->rf_active, Rs));
-  CK(ensure(ctx->d_S, 2 * (size_t)Rs));
+  CK(ensure(ctx->rf_r0n2, SY));
+  CK(ensure(ctx->rf_rk2, SY));
+  CK(ensure(ctx->rf_scale, SY));
+  CK(ensure(ctx->rf_err, SY));
+  CK(ensure(ctx->rf_active, SY));
+  CK(ensure(ctx->d_S, 2 * (size_t)SY));
   if (learned || col) {
     CK(ensure(ctx->zA, NE));
     CK(ensure(ctx->zB, NE));
-    CK(ensure(ctx->pmode, Rs));
+    CK(ensure(ctx->pmode, SY));
     CK(ensure(ctx->d_feat, 5 * (size_t)Rs));
     CK(ensure(ctx->d_coef9, 9 * (size_t)Rs));
   }
@@ -522,26 +625,29 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     CK(ensure(ctx->gram_part, (size_t)(2 * ctx->sms + 8) * Rp * 55));
     CK(ensure(ctx->gram_out, (size_t)Rs * 55));
   }
-  const size_t max_blocks = (size_t)ctx->sms * REDUCE_BLOCKS_PER_SM + 64;
+  const size_t max_blocks = (size_t)std::max(ctx->sms * REDUCE_BLOCKS_PER_SM, ctx->nblk) + 64;
   CK(ensure(ctx->red_part, max_blocks * Rp * 4));  // up to two complex partials per (block, RHS)
   // coefficient table: per step, [0] = r_0 operator (R_n - L_n), [1] = L_n
+  // coefficient table [step][0 = r_0 operator (R_n - L_n), 1 = L_n][segment]
   const int N = ctx->n_steps;
-  std::vector<OpCoef> coefs(2 * (size_t)N);
+  std::vector<OpCoef> coefs(2 * (size_t)N * G, OpCoef{0.0, 0.0, 0.0});
   const double dt = ctx->dt, th = ctx->theta;
-  for (int s = 1; s <= N; ++s) {
-    OpCoef c0, c1;
-    if (!ctx->transformed) {
-      double fb = ctx->fbar[s - 1];
-      c0 = {-dt, 0.0, -dt * fb};
-      c1 = {1.0, 0.0, th * dt * fb};
-    } else {
-      double Fn = ctx->F[s], Fp = ctx->F[s - 1];
-      c0 = {-dt, -dt * ((1 - th) * Fp * Fp + th * Fn * Fn), -dt * ((1 - th) * Fp + th * Fn)};
-      c1 = {1.0, th * dt * Fn * Fn, th * dt * Fn};
+  for (int s = 1; s <= N; ++s)
+    for (int g = 0; g < G; ++g) {
+      if (s > ctx->seg_N[g]) continue;  // segment finished: frozen
+      OpCoef c0, c1;
+      if (!ctx->transformed) {
+        const double fb = ctx->seg_fbar[g][s - 1];
+        c0 = {-dt, 0.0, -dt * fb};
+        c1 = {1.0, 0.0, th * dt * fb};
+      } else {
+        const double Fn = ctx->seg_F[g][s], Fp = ctx->seg_F[g][s - 1];
+        c0 = {-dt, -dt * ((1 - th) * Fp * Fp + th * Fn * Fn), -dt * ((1 - th) * Fp + th * Fn)};
+        c1 = {1.0, th * dt * Fn * Fn, th * dt * Fn};
+      }
+      coefs[(2 * (size_t)(s - 1)) * G + g] = c0;
+      coefs[(2 * (size_t)(s - 1) + 1) * G + g] = c1;
     }
-    coefs[2 * (s - 1)] = c0;
-    coefs[2 * (s - 1) + 1] = c1;
-  }
   CK(ensure(ctx->d_coef, coefs.size()));
   CK(cudaMemcpyAsync(ctx->d_coef.p, coefs.data(), coefs.size() * sizeof(OpCoef), cudaMemcpyHostToDevice, st));
 
@@ -563,7 +669,8 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   op.R = Rs;
   op.Rp = Rp;
   op.transformed = ctx->transformed;
-  VecArgs va{n, Rs, Rp, nb, ctx->d_diag64.p, ctx->d_diag_md64.p, ctx->d_diag32.p, ctx->d_diag_md32.p};
+  op.sp = sp;
+  VecArgs va{n, Rs, Rp, nb, sp, ctx->d_diag64.p, ctx->d_diag_md64.p, ctx->d_diag32.p, ctx->d_diag_md32.p};
   KrylovState ks{ctx->ks_rho.p, ctx->ks_alpha.p, ctx->ks_beta.p, ctx->ks_rr0.p, ctx->ks_rr.p, ctx->ks_tol2.p,
                  ctx->ks_iter.p, ctx->ks_active.p, ctx->n_active.p, ctx->ks_status.p, ctx->ks_rr_best.p,
                  ctx->ks_it_best.p, o.max_iter, plain ? 0 : 30};
@@ -576,8 +683,8 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
   ctx->st_spmm_ms = ctx->st_resid_ms = 0;
   ctx->ev_used = 0;
-  CK(cudaMemsetAsync(ctx->rf_err.p, 0, Rs * sizeof(double), st));
-  CK(cudaMemsetAsync(ctx->ks_status.p, 0, Rs * sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->rf_err.p, 0, SY * sizeof(double), st));
+  CK(cudaMemsetAsync(ctx->ks_status.p, 0, SY * sizeof(int), st));
   if (df) launch_fill_u_df(va, ctx->udf.p, st);
   else launch_fill_u(va, ctx->u64.p, st);
   CKL();
@@ -600,8 +707,8 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   double last_fq = NAN;
   size_t col_next = 0;
   for (int step = 1; step <= N; ++step) {
-    const OpCoef* c_r0 = ctx->d_coef.p + 2 * (step - 1);
-    const OpCoef* c_L = c_r0 + 1;
+    const OpCoef* c_r0 = ctx->d_coef.p + 2 * (size_t)(step - 1) * G;
+    const OpCoef* c_L = c_r0 + G;
     // f_bar_n (lab) or F_n (transformed) of this step: the preconditioner feature
     const double fq = ctx->transformed ? ctx->F[step] : ctx->fbar[step - 1];
     const bool collect_now = col && col_next < col->steps.size() && col->steps[col_next] == step;
@@ -615,8 +722,10 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       launch_set_int(ctx->pmode.p, 1, Rs, st);
       L += 1;
     }
-    launch_set_int(ctx->rf_active.p, 1, Rs, st);
-    launch_set_int(rf.n_active, Rs, 1, st);
+    int live = 0;  // systems of segments that have not finished
+    for (int g = 0; g < G; ++g) live += step <= ctx->seg_N[g] ? Rs : 0;
+    launch_seg_active(ctx->rf_active.p, Rs, G, step, ctx->d_seg_N.p, st);
+    launch_set_int(rf.n_active, live, 1, st);
     L += 3;  // two set kernels and the step-start residual
     op.coef = c_r0;
     timed(1, [&] {
@@ -690,7 +799,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       }
       if (plain) {
         launch_axpy_u(va, ctx->x64.p, ctx->u64.p, ks, rf, ctx->sms, st);
-        launch_finish_step(rf, ks, Rs, st);
+        launch_finish_step(rf, ks, SY, st);
         L += 1;
       } else {
         timed(1, [&] {
@@ -702,7 +811,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       CKL();
     }
     if (!plain) {
-      launch_mark_ref_left(rf, ks, Rs, st);
+      launch_mark_ref_left(rf, ks, SY, st);
       L += 1;
     }
     ctx->st_steps++;
@@ -712,16 +821,16 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   else launch_signal(va, ctx->d_w.p, ctx->u64.p, ctx->d_S.p, rs_at(5), ctx->sms, st);
   CKL();
   L += 1;
-  std::vector<double> S(2 * Rs), err(Rs);
-  std::vector<int> stat(Rs), ref_left(Rs);
-  CK(cudaMemcpyAsync(S.data(), ctx->d_S.p, 2 * Rs * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(err.data(), ctx->rf_err.p, Rs * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(stat.data(), ctx->ks_status.p, Rs * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(ref_left.data(), ctx->rf_active.p, Rs * sizeof(int), cudaMemcpyDeviceToHost, st));
+  std::vector<double> S(2 * (size_t)SY), err(SY);
+  std::vector<int> stat(SY), ref_left(SY);
+  CK(cudaMemcpyAsync(S.data(), ctx->d_S.p, 2 * SY * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(err.data(), ctx->rf_err.p, SY * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(stat.data(), ctx->ks_status.p, SY * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ref_left.data(), ctx->rf_active.p, SY * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (prof) ev_harvest(ctx);
   bt_status ret = BT_OK;
-  for (int s = 0; s < Rs; ++s) {
+  for (int s = 0; s < SY; ++s) {
     ctx->S[2 * (rb + s)] = S[2 * s];
     ctx->S[2 * (rb + s) + 1] = S[2 * s + 1];
     ctx->err_est[rb + s] = err[s];
@@ -760,10 +869,11 @@ extern "C" bt_status bt_collect_precond_data(bt_ctx* ctx, const bt_solver_opts* 
 extern "C" bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t* status) {
   if (!ctx) return BT_EINVAL;
   if (ctx->R == 0) return fail(ctx, BT_ESTATE, "bt_get_signals: nothing run");
-  if (S_re_im) std::memcpy(S_re_im, ctx->S.data(), 2 * ctx->R * sizeof(double));
-  if (err_est) std::memcpy(err_est, ctx->err_est.data(), ctx->R * sizeof(double));
+  const size_t SYt = (size_t)ctx->G * ctx->R;
+  if (S_re_im) std::memcpy(S_re_im, ctx->S.data(), 2 * SYt * sizeof(double));
+  if (err_est) std::memcpy(err_est, ctx->err_est.data(), SYt * sizeof(double));
   if (status)
-    for (int i = 0; i < ctx->R; ++i) status[i] = ctx->status[i];
+    for (size_t i = 0; i < SYt; ++i) status[i] = ctx->status[i];
   return BT_OK;
 }
 

@@ -42,15 +42,24 @@ struct bt_ctx {
   double dt = 0, theta = 0.5, wmax = 0;
   int transformed = 0;
 
-  // sequence
+  // sequence (segment 0 when the context holds several geometries)
   bool have_seq = false;
   double delta = 0, Delta = 0, TE = 0;
   int n_steps = 0;
   std::vector<double> fbar, F;  // fbar[n-1], n = 1..N; F[n], n = 0..N
+  // segments: G geometries of one block-diagonal system (G = 1: the whole mesh)
+  int G = 1;
+  std::vector<int64_t> seg_row0{0, 0};          // [G+1] dof offsets
+  std::vector<double> seg_delta, seg_Delta, seg_TE;
+  std::vector<int> seg_N;                        // steps per segment
+  std::vector<std::vector<double>> seg_fbar, seg_F;
+  bt::DBuf<int> d_blk_seg, d_blk0, d_seg_N;
+  bt::DBuf<int64_t> d_row0;
+  int nblk = 0;
 
   // gradients
   int n_dir = 0, n_b = 0, R = 0;
-  std::vector<double> qhat_rhs, q_rhs;  // [3R], [R]
+  std::vector<double> qhat_rhs, q_rhs;  // [3 G R], [G R]
 
   // run buffers
   bt::DBuf<double> d_q, d_qhat;

@@ -86,6 +86,19 @@ struct RefineState {
   double floor_c2;   // (eps * max w)^2: |r_0|^2 below floor_c2 |u|^2 counts as zero
 };
 
+// Segment plan: the solve may hold several geometries ("segments") of uneven
+// size as one block-diagonal system.  Segment g owns rows [row0[g], row0[g+1])
+// and systems [g R, (g+1) R); every block of a launch works inside one
+// segment (blocks blk0[g] .. blk0[g+1]-1), so block partial sums never mix
+// geometries.
+struct SegPlan {
+  const int* blk_seg;   // [nblk] segment of each block
+  const int* blk0;      // [G+1] first block of each segment
+  const int64_t* row0;  // [G+1] first row of each segment
+  int G;
+  int nblk;
+};
+
 // Operator description shared by all fused SpMM kernels.
 //   y_r = a (P0 x_r) + bq2 q_r^2 (P1 x_r) + i cq q_r (qhat_d . Pd) x_r
 struct OpArgs {
@@ -101,16 +114,18 @@ struct OpArgs {
   const float4* pklo;
   const float2* kjmd_hi; // double-float split of (K + J, MD)
   const float2* kjmd_lo;
-  const OpCoef* coef;    // device, one per segment
-  const double* q;       // [R]
-  const double* qhat;    // [3 R] unit direction of each RHS
-  int R, Rp;
+  const OpCoef* coef;    // device, one per segment (current step)
+  const double* q;       // [G R]
+  const double* qhat;    // [3 G R] unit direction of each system
+  int R, Rp;             // systems per segment, padded vector width
   int transformed;
+  SegPlan sp;
 };
 
 struct VecArgs {
   int64_t n;
   int R, Rp, nb;
+  SegPlan sp;
   const double4* diag64;
   const double* diag_md64;
   const float4* diag32;
@@ -209,6 +224,7 @@ void launch_signal(const VecArgs& va, const double* w, const double2* u, double*
 void launch_set_int(int* p, int v, int n, cudaStream_t st);
 void launch_finish_step(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st);
 void launch_mark_ref_left(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st);
+void launch_seg_active(int* act, int R, int G, int step, const int* segN, cudaStream_t st);
 
 // ---------------------------------------------------------------- device helpers
 #ifdef __CUDACC__
@@ -253,6 +269,15 @@ constexpr int ROW_CHUNK = 32;
   for (int64_t ch_ = blockIdx.x; ch_ * ROW_CHUNK < (int64_t)(n); ch_ += gridDim.x)                \
     for (int64_t row = ch_ * ROW_CHUNK + (first), re_ = min((int64_t)(n), (ch_ + 1) * ROW_CHUNK); \
          row < re_; row += (stride))
+// the same inside the block's segment (sg_ = segment, rows [sr0_, sr1_))
+#define BT_SEG_BEGIN(sp)                                                                          \
+  const int sg_ = (sp).blk_seg[blockIdx.x];                                                       \
+  const int sk_ = blockIdx.x - (sp).blk0[sg_], snb_ = (sp).blk0[sg_ + 1] - (sp).blk0[sg_];        \
+  const int64_t sr0_ = (sp).row0[sg_], sr1_ = (sp).row0[sg_ + 1];
+#define BT_FOR_SEG_CHUNKED_ROWS(row, first, stride)                                               \
+  for (int64_t ch_ = sk_; sr0_ + ch_ * ROW_CHUNK < sr1_; ch_ += snb_)                             \
+    for (int64_t row = sr0_ + ch_ * ROW_CHUNK + (first), re_ = min(sr1_, sr0_ + (ch_ + 1) * ROW_CHUNK); \
+         row < re_; row += (stride))
 
 // read-only 32-byte / 16-byte plane loads
 __device__ __forceinline__ double4 ldg4(const double4* p) {
@@ -293,22 +318,24 @@ struct LaneCoef {
   int act[NB];
 };
 
+// r0: first local system of the lane in segment g (global system g R + r)
 template <int NB>
-__device__ __forceinline__ void lane_coef(const OpArgs& op, int r0, const int* active, LaneCoef<NB>& lc) {
-  const OpCoef cf = op.coef[0];
+__device__ __forceinline__ void lane_coef(const OpArgs& op, int g, int r0, const int* active, LaneCoef<NB>& lc) {
+  const OpCoef cf = op.coef[g];
+  const int base = g * op.R;
   lc.a = cf.a;
   // the NB RHS of a lane share one direction (the host picks NB accordingly)
-  const int d = r0 < op.R ? r0 : 0;
+  const int d = base + (r0 < op.R ? r0 : 0);
   lc.qx = op.qhat[3 * d];
   lc.qy = op.qhat[3 * d + 1];
   lc.qz = op.qhat[3 * d + 2];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     int r = r0 + b;
-    double q = r < op.R ? op.q[r] : 0.0;
+    double q = r < op.R ? op.q[base + r] : 0.0;
     lc.b[b] = cf.bq2 * q * q;
     lc.c[b] = cf.cq * q;
-    lc.act[b] = (r < op.R) && (active == nullptr || active[r]);
+    lc.act[b] = (r < op.R) && (active == nullptr || active[base + r]);
   }
 }
 
@@ -335,13 +362,29 @@ __device__ __forceinline__ void block_partials(double2 (&acc)[NB], int r0, int R
   }
 }
 
-// Sum part[0..nbx)[s] for s < R in a fixed order; callback per s.
+// Single-segment variant over nbx blocks (kernels with their own grid).
 template <class F>
-__device__ __forceinline__ void reduce_partials(const double* part, int nbx, int Rp, int R, F&& fn) {
+__device__ __forceinline__ void reduce_partials_flat(const double* part, int nbx, int Rp, int R, F&& fn) {
   for (int s = threadIdx.x; s < R; s += blockDim.x) {
     double2 t = make_double2(0, 0);
     for (int b = 0; b < nbx; ++b) {
       double2 v = __ldcg(reinterpret_cast<const double2*>(part) + (size_t)b * Rp + s);
+      t.x += v.x;
+      t.y += v.y;
+    }
+    fn(s, t);
+  }
+}
+
+// For every global system s = g R + r: sum part[b][r] over the blocks b of
+// segment g in a fixed order; callback fn(s, sum).
+template <class F>
+__device__ __forceinline__ void reduce_partials(const double* part, const SegPlan& sp, int Rp, int R, F&& fn) {
+  for (int s = threadIdx.x; s < sp.G * R; s += blockDim.x) {
+    const int g = s / R, r = s - g * R;
+    double2 t = make_double2(0, 0);
+    for (int b = sp.blk0[g]; b < sp.blk0[g + 1]; ++b) {
+      double2 v = __ldcg(reinterpret_cast<const double2*>(part) + (size_t)b * Rp + r);
       t.x += v.x;
       t.y += v.y;
     }

@@ -43,7 +43,7 @@ struct SysCoef {
   double b, c, qx, qy, qz;
 };
 __device__ __forceinline__ SysCoef sys_coef(const OpArgs& op, int s) {
-  const OpCoef cf = op.coef[0];
+  const OpCoef cf = op.coef[s / op.R];
   double q = op.q[s];
   SysCoef sc;
   sc.b = cf.bq2 * q * q;
@@ -86,11 +86,15 @@ __device__ bool elem_block_reduce(double2 (&acc)[EM_NK][NC], const ElemMap& em, 
   return last_block(counter, gridDim.x);
 }
 
+// sum of the partials of global system s = g R + r over the blocks of segment g
 template <int NC>
-__device__ __forceinline__ void sum_part(const double* part, int nbx, int Rp, int s, double2 (&out)[NC]) {
+__device__ __forceinline__ void sum_part(const double* part, const SegPlan& sp, int R, int Rp, int s,
+                                         double2 (&out)[NC]) {
 #pragma unroll
   for (int c = 0; c < NC; ++c) out[c] = make_double2(0, 0);
-  for (int b = 0; b < nbx; ++b)
+  const int g = s / R, r = s - g * R;
+  s = r;
+  for (int b = sp.blk0[g]; b < sp.blk0[g + 1]; ++b)
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       double2 v = __ldcg(reinterpret_cast<const double2*>(part) + ((size_t)b * Rp + s) * NC + c);
@@ -99,10 +103,13 @@ __device__ __forceinline__ void sum_part(const double* part, int nbx, int Rp, in
     }
 }
 
-static int elem_grid(int64_t n, int sms) {
-  int64_t g = (int64_t)sms * REDUCE_BLOCKS_PER_SM;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, n));
-}
+static int elem_grid(const VecArgs& va) { return va.sp.nblk; }
+
+// rows of this block: a contiguous share of its segment
+#define BT_SEG_ROWS(va)                                                   \
+  BT_SEG_BEGIN((va).sp);                                                  \
+  const int64_t per = (sr1_ - sr0_ + snb_ - 1) / snb_;                    \
+  const int64_t rb = sr0_ + (int64_t)sk_ * per, re = min(sr1_, rb + per);
 
 // load the refinement residual (FP64 or double-float) of one element
 __device__ __forceinline__ double2 load_res(const double2* p, size_t e) { return p[e]; }
@@ -124,14 +131,14 @@ __global__ void __launch_bounds__(256) k_krylov_init(OpArgs op, VecArgs va, cons
   const int rr = t % em.RS, ro = t / em.RS;
   double2 acc[EM_NK][2];
   for (int k = 0; k < EM_NK; ++k) acc[k][0] = acc[k][1] = make_double2(0, 0);
-  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  BT_SEG_ROWS(va);
   if (live) {
     for (int k = 0; k < em.NK; ++k) {
       const int col = rr + 256 * k;
       if (col >= va.Rp) continue;
-      const int s = sys_of_col(col, va.nb);
-      if (s >= va.R) continue;
+      const int rl = sys_of_col(col, va.nb);
+      if (rl >= va.R) continue;
+      const int s = sg_ * va.R + rl;
       const bool act = ref_active[s] != 0;
       const SysCoef sc = sys_coef(op, s);
       const double inv = (scale && act && scale[s] > 0) ? 1.0 / scale[s] : 1.0;
@@ -180,9 +187,9 @@ __global__ void __launch_bounds__(256) k_krylov_init(OpArgs op, VecArgs va, cons
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < va.R; s += blockDim.x) {
+  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
     double2 o[2];
-    sum_part<2>(rs.part, gridDim.x, va.Rp, s, o);
+    sum_part<2>(rs.part, va.sp, va.R, va.Rp, s, o);
     ks.rho[2 * s] = o[0].x;
     ks.rho[2 * s + 1] = o[0].y;
     ks.rr0[s] = o[1].x;
@@ -218,14 +225,15 @@ __global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2
   const int rr = t % em.RS, ro = t / em.RS;
   double2 acc[EM_NK][2];
   for (int k = 0; k < EM_NK; ++k) acc[k][0] = acc[k][1] = make_double2(0, 0);
-  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  BT_SEG_ROWS(va);
   if (live) {
     for (int k = 0; k < em.NK; ++k) {
       const int col = rr + 256 * k;
       if (col >= va.Rp) continue;
-      const int s = sys_of_col(col, va.nb);
-      if (s >= va.R || !ks.active[s]) continue;
+      const int rl = sys_of_col(col, va.nb);
+      if (rl >= va.R) continue;
+      const int s = sg_ * va.R + rl;
+      if (!ks.active[s]) continue;
       const SysCoef sc = sys_coef(op, s);
       const T axr = (T)ks.alpha[2 * s], axi = (T)ks.alpha[2 * s + 1];
       T2 ar = {0, 0}, an = {0, 0};
@@ -282,10 +290,10 @@ __global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < va.R; s += blockDim.x) {
+  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
     if (!ks.active[s]) continue;
     double2 o[2];
-    sum_part<2>(rs.part, gridDim.x, va.Rp, s, o);
+    sum_part<2>(rs.part, va.sp, va.R, va.Rp, s, o);
     ks.rr[s] = o[1].x;
     int it = ++ks.iter[s];
     if (!isfinite(o[1].x) || !isfinite(o[0].x) || !isfinite(o[0].y)) {
@@ -351,13 +359,14 @@ __global__ void __launch_bounds__(256) k_krylov_p(OpArgs op, VecArgs va, const T
   const int t = threadIdx.x;
   if (t >= em.rpp * em.RS) return;
   const int rr = t % em.RS, ro = t / em.RS;
-  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  BT_SEG_ROWS(va);
   for (int k = 0; k < em.NK; ++k) {
     const int col = rr + 256 * k;
     if (col >= va.Rp) continue;
-    const int s = sys_of_col(col, va.nb);
-    if (s >= va.R || !ks.active[s]) continue;
+    const int rl = sys_of_col(col, va.nb);
+    if (rl >= va.R) continue;
+    const int s = sg_ * va.R + rl;
+    if (!ks.active[s]) continue;
     const SysCoef sc = sys_coef(op, s);
     const T br = (T)ks.beta[2 * s], bi = (T)ks.beta[2 * s + 1];
     const bool usez = zbuf && pmode && pmode[s];
@@ -407,13 +416,14 @@ __global__ void k_axpy_u(VecArgs va, const double2* __restrict__ d, double2* __r
   const int t = threadIdx.x;
   if (t >= em.rpp * em.RS) return;
   const int rr = t % em.RS, ro = t / em.RS;
-  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  BT_SEG_ROWS(va);
   for (int k = 0; k < em.NK; ++k) {
     const int col = rr + 256 * k;
     if (col >= va.Rp) continue;
-    const int s = sys_of_col(col, va.nb);
-    if (s >= va.R || !rf.active[s]) continue;
+    const int rl = sys_of_col(col, va.nb);
+    if (rl >= va.R) continue;
+    const int s = sg_ * va.R + rl;
+    if (!rf.active[s]) continue;
     for (int64_t i = rb + ro; i < re; i += em.rpp) {
       const size_t e = (size_t)i * va.Rp + col;
       double2 uv = u[e], dv = d[e];
@@ -453,14 +463,13 @@ __global__ void __launch_bounds__(256) k_signal(VecArgs va, const double* __rest
   const int rr = t % em.RS, ro = t / em.RS;
   double2 acc[EM_NK][1];
   for (int k = 0; k < EM_NK; ++k) acc[k][0] = make_double2(0, 0);
-  const int64_t per = (va.n + gridDim.x - 1) / gridDim.x;
-  const int64_t rb = (int64_t)blockIdx.x * per, re = min(va.n, rb + per);
+  BT_SEG_ROWS(va);
   if (live) {
     for (int k = 0; k < em.NK; ++k) {
       const int col = rr + 256 * k;
       if (col >= va.Rp) continue;
-      const int s = sys_of_col(col, va.nb);
-      if (s >= va.R) continue;
+      const int rl = sys_of_col(col, va.nb);
+      if (rl >= va.R) continue;
       for (int64_t i = rb + ro; i < re; i += em.rpp) {
         double2 v = load_res(u, (size_t)i * va.Rp + col);
         double wi = w[i];
@@ -470,9 +479,9 @@ __global__ void __launch_bounds__(256) k_signal(VecArgs va, const double* __rest
     }
   }
   if (!elem_block_reduce<1>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
-  for (int s = threadIdx.x; s < va.R; s += blockDim.x) {
+  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
     double2 o[1];
-    sum_part<1>(rs.part, gridDim.x, va.Rp, s, o);
+    sum_part<1>(rs.part, va.sp, va.R, va.Rp, s, o);
     S[2 * s] = o[0].x;
     S[2 * s + 1] = o[0].y;
   }
@@ -482,49 +491,49 @@ __global__ void __launch_bounds__(256) k_signal(VecArgs va, const double* __rest
 void launch_krylov_init_f32(const OpArgs& op, const VecArgs& va, const double2* r64, const double* scale,
                             const int* ref_active, float2* x, float2* r, float2* p, const KrylovState& ks,
                             double tol, RedScratch rs, int conj, int sms, cudaStream_t st) {
-  int g = elem_grid(va.n, sms);
+  int g = elem_grid(va);
   if (conj) k_krylov_init<float, float2, double2, true><<<g, 256, 0, st>>>(op, va, r64, scale, ref_active, x, r, p, ks, tol, rs);
   else k_krylov_init<float, float2, double2, false><<<g, 256, 0, st>>>(op, va, r64, scale, ref_active, x, r, p, ks, tol, rs);
 }
 void launch_krylov_init_f32_df(const OpArgs& op, const VecArgs& va, const float4* rdf, const double* scale,
                                const int* ref_active, float2* x, float2* r, float2* p, const KrylovState& ks,
                                double tol, RedScratch rs, int conj, int sms, cudaStream_t st) {
-  int g = elem_grid(va.n, sms);
+  int g = elem_grid(va);
   if (conj) k_krylov_init<float, float2, float4, true><<<g, 256, 0, st>>>(op, va, rdf, scale, ref_active, x, r, p, ks, tol, rs);
   else k_krylov_init<float, float2, float4, false><<<g, 256, 0, st>>>(op, va, rdf, scale, ref_active, x, r, p, ks, tol, rs);
 }
 void launch_krylov_update_f32(const OpArgs& op, const VecArgs& va, float2* x, float2* r, const float2* p,
                               const float2* q, const KrylovState& ks, RedScratch rs, int conj, int sms,
                               cudaStream_t st, int* pmode) {
-  int g = elem_grid(va.n, sms);
+  int g = elem_grid(va);
   if (conj) k_krylov_update<float, float2, true><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs, pmode);
   else k_krylov_update<float, float2, false><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs, pmode);
 }
 void launch_krylov_p_f32(const OpArgs& op, const VecArgs& va, const float2* r, float2* p, const KrylovState& ks,
                          int sms, cudaStream_t st, const float2* zbuf, const int* pmode) {
-  k_krylov_p<float, float2><<<elem_grid(va.n, sms), 256, 0, st>>>(op, va, r, p, ks, zbuf, pmode);
+  k_krylov_p<float, float2><<<elem_grid(va), 256, 0, st>>>(op, va, r, p, ks, zbuf, pmode);
 }
 void launch_krylov_init_f64(const OpArgs& op, const VecArgs& va, const double2* r64, const int* ref_active,
                             double2* x, double2* r, double2* p, const KrylovState& ks, double tol, RedScratch rs,
                             int conj, int sms, cudaStream_t st) {
-  int g = elem_grid(va.n, sms);
+  int g = elem_grid(va);
   if (conj) k_krylov_init<double, double2, double2, true><<<g, 256, 0, st>>>(op, va, r64, nullptr, ref_active, x, r, p, ks, tol, rs);
   else k_krylov_init<double, double2, double2, false><<<g, 256, 0, st>>>(op, va, r64, nullptr, ref_active, x, r, p, ks, tol, rs);
 }
 void launch_krylov_update_f64(const OpArgs& op, const VecArgs& va, double2* x, double2* r, const double2* p,
                               const double2* q, const KrylovState& ks, RedScratch rs, int conj, int sms,
                               cudaStream_t st) {
-  int g = elem_grid(va.n, sms);
+  int g = elem_grid(va);
   if (conj) k_krylov_update<double, double2, true><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs, nullptr);
   else k_krylov_update<double, double2, false><<<g, 256, 0, st>>>(op, va, x, r, p, q, ks, rs, nullptr);
 }
 void launch_krylov_p_f64(const OpArgs& op, const VecArgs& va, const double2* r, double2* p,
                          const KrylovState& ks, int sms, cudaStream_t st) {
-  k_krylov_p<double, double2><<<elem_grid(va.n, sms), 256, 0, st>>>(op, va, r, p, ks, nullptr, nullptr);
+  k_krylov_p<double, double2><<<elem_grid(va), 256, 0, st>>>(op, va, r, p, ks, nullptr, nullptr);
 }
 void launch_axpy_u(const VecArgs& va, const double2* d, double2* u, const KrylovState& ks, const RefineState& rf,
                    int sms, cudaStream_t st) {
-  k_axpy_u<<<elem_grid(va.n, sms), 256, 0, st>>>(va, d, u, ks, rf);
+  k_axpy_u<<<elem_grid(va), 256, 0, st>>>(va, d, u, ks, rf);
 }
 void launch_finish_step(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st) {
   k_finish_step<<<1, 256, 0, st>>>(rf, ks, R);
@@ -537,11 +546,11 @@ void launch_set_int(int* p, int v, int n, cudaStream_t st) {
 }
 void launch_signal(const VecArgs& va, const double* w, const double2* u, double* S, RedScratch rs, int sms,
                    cudaStream_t st) {
-  k_signal<double2><<<elem_grid(va.n, sms), 256, 0, st>>>(va, w, u, S, rs);
+  k_signal<double2><<<elem_grid(va), 256, 0, st>>>(va, w, u, S, rs);
 }
 void launch_signal_df(const VecArgs& va, const double* w, const float4* u, double* S, RedScratch rs, int sms,
                       cudaStream_t st) {
-  k_signal<float4><<<elem_grid(va.n, sms), 256, 0, st>>>(va, w, u, S, rs);
+  k_signal<float4><<<elem_grid(va), 256, 0, st>>>(va, w, u, S, rs);
 }
 
 }  // namespace bt
@@ -554,5 +563,16 @@ __global__ void k_mark_ref_left(RefineState rf, KrylovState ks, int R) {
 }
 void launch_mark_ref_left(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st) {
   k_mark_ref_left<<<1, 256, 0, st>>>(rf, ks, R);
+}
+}  // namespace bt
+
+namespace bt {
+// rf_active[g R + r] = (step <= N_g): segments past their echo time stay frozen
+__global__ void k_seg_active(int* act, int R, int G, int step, const int* segN) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < G * R; s += gridDim.x * blockDim.x)
+    act[s] = step <= segN[s / R] ? 1 : 0;
+}
+void launch_seg_active(int* act, int R, int G, int step, const int* segN, cudaStream_t st) {
+  k_seg_active<<<(G * R + 255) / 256, 256, 0, st>>>(act, R, G, step, segN);
 }
 }  // namespace bt

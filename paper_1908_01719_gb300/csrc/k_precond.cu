@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) k_spmm_horner(OpArgs op, VecArgs va, cons
   const int c0 = blockIdx.y * 32 * NB + lane;
   const bool on = r0 < op.R;
   LaneCoef<NB> lc;
-  lane_coef<NB>(op, on ? r0 : 0, active, lc);
+  lane_coef<NB>(op, 0, on ? r0 : 0, active, lc);
   bool any = false;
   float cj[NB];
 #pragma unroll

@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
   const int c0 = tile * 32 * NBL + lane + 32 * part * NB;
   const bool on = r0 < op.R;
   LaneCoef<NB> lc;
-  lane_coef<NB>(op, on ? r0 : 0, rf.active, lc);
+  BT_SEG_BEGIN(op.sp);
+  lane_coef<NB>(op, sg_, on ? r0 : 0, rf.active, lc);
   bool any = false;
 #pragma unroll
   for (int b = 0; b < NB; ++b) any |= (on && lc.act[b]);
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
   for (int b = 0; b < NB; ++b) {
     cb[b] = dd_split(lc.b[b]);
     cc[b] = dd_split(lc.c[b]);
-    sc[b] = (MODE == 1 && on && r0 + b < op.R) ? (float)rf.scale[r0 + b] : 1.0f;
+    sc[b] = (MODE == 1 && on && r0 + b < op.R) ? (float)rf.scale[sg_ * op.R + r0 + b] : 1.0f;
   }
   double2 acc[NB];
   float2 accf[NB];
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
   }
   int cnt = 0;
   if (warp_any) {
-    BT_FOR_CHUNKED_ROWS(row, op.n, warp, W) {
+    BT_FOR_SEG_CHUNKED_ROWS(row, warp, W) {
       const int k0 = op.rp[row], k1 = op.rp[row + 1];
       // accumulators: P (P0 x), Q (m x), Z (MD x); re/im, hi/lo
       float Ph[NB][2], Pl[NB][2], Qh[NB][2], Ql[NB][2], Zh[NB][2], Zl[NB][2];
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
   }
   block_partials<NB>(acc, on ? r0 : op.Rp, op.Rp, rs.part);
   if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
-  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 t) { refine_finish(MODE, rf, s, t); });
+  reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 t) { refine_finish(MODE, rf, s, t); });
 }
 
 #define BT_DISPATCH_NB(nb, ...)                                 \
@@ -265,7 +266,7 @@ template <int NBL, int MODE, class TX>
 static void resid_df_t(const OpArgs& op, const TX* x, float4* u, float4* r, const RefineState& rf, RedScratch rs,
                        int sms, cudaStream_t st) {
   constexpr int NB = NBL < 2 ? NBL : 2;
-  dim3 grid(spmm_grid_rows(op.n, sms), ((op.R + 32 * NBL - 1) / (32 * NBL)) * (NBL / NB));
+  dim3 grid(op.sp.nblk, ((op.R + 32 * NBL - 1) / (32 * NBL)) * (NBL / NB));
   if (op.transformed) k_resid_df<NBL, NB, true, MODE, TX><<<grid, 256, 0, st>>>(op, x, u, r, rf, rs);
   else k_resid_df<NBL, NB, false, MODE, TX><<<grid, 256, 0, st>>>(op, x, u, r, rf, rs);
 }

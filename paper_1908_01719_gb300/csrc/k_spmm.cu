@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256) k_spmm_krylov(OpArgs op, const T2* __rest
   const int c0 = blockIdx.y * 32 * NB + lane;        // its first column (stride 32)
   const bool on = r0 < op.R;
   LaneCoef<NB> lc;
-  lane_coef<NB>(op, on ? r0 : 0, ks.active, lc);
+  BT_SEG_BEGIN(op.sp);
+  lane_coef<NB>(op, sg_, on ? r0 : 0, ks.active, lc);
   bool any = false;
 #pragma unroll
   for (int b = 0; b < NB; ++b) any |= (on && lc.act[b]);
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) k_spmm_krylov(OpArgs op, const T2* __rest
   }
   int cnt = 0;
   if (warp_any) {
-    BT_FOR_CHUNKED_ROWS(row, op.n, warp, W) {
+    BT_FOR_SEG_CHUNKED_ROWS(row, warp, W) {
       const int k0 = op.rp[row], k1 = op.rp[row + 1];
       T2 P[NB], Q[NB];
 #pragma unroll
@@ -139,19 +140,19 @@ __global__ void __launch_bounds__(256) k_spmm_krylov(OpArgs op, const T2* __rest
   }
   block_partials<NB>(acc, on ? r0 : op.Rp, op.Rp, rs.part);
   if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
-  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
+  reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
 }
 
 template <int NB, bool TRANSF, bool CONJ>
 static void spmm_krylov_f32_t(const OpArgs& op, const float2* p, float2* q, const KrylovState& ks, RedScratch rs,
                               int sms, cudaStream_t st) {
-  dim3 grid(spmm_grid_rows(op.n, sms), (op.R + 32 * NB - 1) / (32 * NB));
+  dim3 grid(op.sp.nblk, (op.R + 32 * NB - 1) / (32 * NB));
   k_spmm_krylov<NB, TRANSF, CONJ, float, float2, float4><<<grid, 256, 0, st>>>(op, p, q, ks, rs, op.pk32, op.p1_32);
 }
 template <int NB, bool TRANSF, bool CONJ>
 static void spmm_krylov_f64_t(const OpArgs& op, const double2* p, double2* q, const KrylovState& ks,
                               RedScratch rs, int sms, cudaStream_t st) {
-  dim3 grid(spmm_grid_rows(op.n, sms), (op.R + 32 * NB - 1) / (32 * NB));
+  dim3 grid(op.sp.nblk, (op.R + 32 * NB - 1) / (32 * NB));
   k_spmm_krylov<NB, TRANSF, CONJ, double, double2, double4><<<grid, 256, 0, st>>>(op, p, q, ks, rs, op.pk64,
                                                                                    op.p1_64);
 }
@@ -201,19 +202,20 @@ __global__ void __launch_bounds__(256) k_resid64(OpArgs op, const TX2* __restric
   const int c0 = blockIdx.y * 32 * NB + lane;
   const bool on = r0 < op.R;
   LaneCoef<NB> lc;
-  lane_coef<NB>(op, on ? r0 : 0, rf.active, lc);
+  BT_SEG_BEGIN(op.sp);
+  lane_coef<NB>(op, sg_, on ? r0 : 0, rf.active, lc);
   bool any = false;
 #pragma unroll
   for (int b = 0; b < NB; ++b) any |= (on && lc.act[b]);
   const bool warp_any = __any_sync(0xffffffffu, any);
   double sc[NB];
 #pragma unroll
-  for (int b = 0; b < NB; ++b) sc[b] = (MODE == 1 && on) ? rf.scale[r0 + b] : 1.0;
+  for (int b = 0; b < NB; ++b) sc[b] = (MODE == 1 && on) ? rf.scale[sg_ * op.R + r0 + b] : 1.0;
   double2 acc[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) acc[b] = make_double2(0, 0);
   if (warp_any) {
-    BT_FOR_CHUNKED_ROWS(row, op.n, warp, W) {
+    BT_FOR_SEG_CHUNKED_ROWS(row, warp, W) {
       const int k0 = op.rp[row], k1 = op.rp[row + 1];
       double2 P[NB], Q[NB];
 #pragma unroll
@@ -271,19 +273,19 @@ __global__ void __launch_bounds__(256) k_resid64(OpArgs op, const TX2* __restric
   }
   block_partials<NB>(acc, on ? r0 : op.Rp, op.Rp, rs.part);
   if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
-  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 t) { refine_finish(MODE, rf, s, t); });
+  reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 t) { refine_finish(MODE, rf, s, t); });
 }
 
 template <int NB, bool TRANSF>
 static void resid0_t(const OpArgs& op, const double2* u, double2* r, const RefineState& rf, RedScratch rs, int sms,
                      cudaStream_t st) {
-  dim3 grid(spmm_grid_rows(op.n, sms), (op.R + 32 * NB - 1) / (32 * NB));
+  dim3 grid(op.sp.nblk, (op.R + 32 * NB - 1) / (32 * NB));
   k_resid64<NB, TRANSF, 0, double2><<<grid, 256, 0, st>>>(op, u, const_cast<double2*>(u), r, rf, rs);
 }
 template <int NB, bool TRANSF>
 static void resid_sub_t(const OpArgs& op, const float2* d, double2* u, double2* r, const RefineState& rf,
                         RedScratch rs, int sms, cudaStream_t st) {
-  dim3 grid(spmm_grid_rows(op.n, sms), (op.R + 32 * NB - 1) / (32 * NB));
+  dim3 grid(op.sp.nblk, (op.R + 32 * NB - 1) / (32 * NB));
   k_resid64<NB, TRANSF, 1, float2><<<grid, 256, 0, st>>>(op, d, u, r, rf, rs);
 }
 

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) k_spmm_krylov_narrow(OpArgs op, const dou
   }
   narrow_partials<RM>(acc, g, op.Rp, rs.part);
   if (!last_block(rs.counter, gridDim.x)) return;
-  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
+  reduce_partials_flat(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
 }
 
 // r = op_{P0 = K+J}(u) (mode 0 of the refinement residual), FP64, R <= 4
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_resid0_narrow(OpArgs op, const double2*
   }
   narrow_partials<RM>(acc, g, op.Rp, rs.part);
   if (!last_block(rs.counter, gridDim.x)) return;
-  reduce_partials(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 t) { refine_finish(0, rf, s, t); });
+  reduce_partials_flat(rs.part, gridDim.x, op.Rp, op.R, [&](int s, double2 t) { refine_finish(0, rf, s, t); });
 }
 
 static int narrow_grid(int64_t n, int sms) {

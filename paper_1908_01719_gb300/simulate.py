@@ -22,16 +22,21 @@ class Simulation:
                           geom.periodic_mask, geom.box_lo, geom.box_hi)
         self.n_dof, self.nnz, self.n_iface = bt.bt_get_sizes(self.ctx)
         self.frame = bt.BT_FRAME_TRANSFORMED if (geom.transformed or geom.periodic_mask) else bt.BT_FRAME_LAB
+        seg = getattr(geom, "segments", None)
+        self.G = 1 if seg is None else len(seg["node_off"]) - 1
         if device >= 0:
             bt.bt_assemble(self.ctx, geom.dt, geom.theta, self.frame)
-            bt.bt_set_sequence(self.ctx, bt.BT_PGSE, geom.delta, geom.Delta, geom.TE)
+            if seg is None:
+                bt.bt_set_sequence(self.ctx, bt.BT_PGSE, geom.delta, geom.Delta, geom.TE)
+            else:
+                bt.bt_set_segments(self.ctx, seg["node_off"], seg["delta"], seg["Delta"], seg["TE"])
             bt.bt_set_gradients(self.ctx, geom.dirs, geom.bvals)
         self.R = len(geom.dirs) * len(geom.bvals)
 
     def run(self, mode=bt.BT_MODE_MIXED, raise_on_status=True, **opts):
         o = bt.bt_default_opts(**opts)
         st = bt.bt_run(self.ctx, mode, o, raise_on_status=raise_on_status)
-        S, err, stat = bt.bt_get_signals(self.ctx, self.R)
+        S, err, stat = bt.bt_get_signals(self.ctx, self.G * self.R)
         return S, err, stat, st
 
     def stats(self):
