@@ -171,6 +171,11 @@ bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t*
  * SpMM launches, with BT_OPT_PROFILE the summed device time (ms) of the
  * FP32/FP64 fused SpMM launches and of the refinement-residual launches, the
  * number of refinement-residual launches and of all kernel launches. */
+/* The SpMM autotuner's last choice (tuned at the first FP32 run of a given
+ * RHS count, RHS-per-lane and segmentation, by timing both kernels on the real
+ * pattern): variant 0 = row kernel, 1 = row-tile kernel sharing gathered rows;
+ * and the measured ms per launch of each.  BT_ESTATE before any tuning. */
+bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_row, double* ms_tiled);
 bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters,
                        int64_t* refine_passes, int64_t* spmm_launches, double* spmm_ms,
                        double* resid_ms, int64_t* resid_launches, int64_t* kernel_launches);

@@ -28,7 +28,7 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats",
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
-           "bt_set_segments"]
+           "bt_set_segments", "bt_get_tuning"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -74,6 +74,7 @@ def lib():
             "bt_set_sequence": [P, C.c_int, D, D, D],
             "bt_set_gradients": [P, I32, P, I32, P],
             "bt_set_segments": [P, I32, P, P, P, P],
+            "bt_get_tuning": [P, P, P, P],
             "bt_default_opts": [C.POINTER(bt_solver_opts)],
             "bt_run": [P, C.c_int, C.POINTER(bt_solver_opts)],
             "bt_get_signals": [P, P, P, P],
@@ -293,3 +294,10 @@ def bt_precond_grad_noalloc(w_ptr, n, feat_ptr, G_ptr, h_ptr, grad_ptr, loss_ptr
     V = C.c_void_p
     return lib().bt_precond_grad_noalloc(V(w_ptr), int(n), V(feat_ptr), V(G_ptr), V(h_ptr), V(grad_ptr),
                                          V(loss_ptr), V(stream))
+
+
+def bt_get_tuning(ctx):
+    v = C.c_int32()
+    d = (C.c_double * 2)()
+    _check(ctx, lib().bt_get_tuning(ctx, C.byref(v), C.byref(d, 0), C.byref(d, 8)))
+    return {"variant": ["row", "tiled"][v.value], "ms_row": d[0], "ms_tiled": d[1]}

@@ -89,6 +89,8 @@ bt_status bt_destroy(bt_ctx* ctx) {
       cudaEventDestroy(e.b);
     }
     if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+    for (auto& s : ctx->cap_stream)
+      if (s) cudaStreamDestroy(s);
   }
   delete ctx;
   return BT_OK;
@@ -262,6 +264,7 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   ctx->theta = theta;
   ctx->transformed = (int)flags;
   compute_geom_features(ctx);
+  ++ctx->planes_version;
   ctx->assembled = true;
   ctx->have_seq = false;
   return BT_OK;
@@ -450,6 +453,78 @@ int pick_nb(const bt_ctx* ctx, int rb, int Rs) {
 }  // namespace
 
 namespace {
+// Row tiles of the register-reuse SpMM for the current segmentation, and the
+// plane values in tile-entry order for the current assembly.
+bt_status ensure_tiles(bt_ctx* ctx, cudaStream_t st) {
+  if (ctx->tiles_for != ctx->seg_row0) {
+    RowTiles t;
+    build_row_tiles(ctx->mesh, ctx->seg_row0, t);
+    CK(upload(ctx->t_row0, t.row0, st));
+    CK(upload(ctx->t_u0, t.u0, st));
+    CK(upload(ctx->t_s0, t.s0, st));
+    CK(upload(ctx->t_seg0, t.seg_tile0, st));
+    CK(upload(ctx->t_slot, t.slot, st));
+    std::vector<uint32_t> uc(t.ucol.begin(), t.ucol.end());
+    CK(upload(ctx->t_ucol, uc, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->tiles_for = ctx->seg_row0;
+    ctx->tiles_planes_version = -1;
+  }
+  if (ctx->tiles_planes_version != ctx->planes_version) {
+    CK(ensure(ctx->pkt, ctx->mesh.nnz));
+    CK(ensure(ctx->mdt, ctx->mesh.nnz));
+    launch_gather_tile_planes(ctx->t_slot.p, ctx->mesh.nnz, ctx->d_pk32.p, ctx->d_md32.p, ctx->pkt.p, ctx->mdt.p, st);
+    CKL();
+    ctx->tiles_planes_version = ctx->planes_version;
+  }
+  return BT_OK;
+}
+
+void spmm_f32(int variant, const OpArgs& op, const float2* p, float2* q, const KrylovState& ks, RedScratch rs,
+              int conj, int nb, int sms, cudaStream_t st) {
+  if (variant == 1) launch_spmm_krylov_f32_tiled(op, p, q, ks, rs, conj, nb, sms, st);
+  else launch_spmm_krylov_f32(op, p, q, ks, rs, conj, nb, sms, st);
+}
+
+// Autotuner: time the row kernel and the tiled kernel on the real pattern and
+// RHS count (3 launches each, CUDA events) and keep the faster, cached per
+// (RHS, RHS per lane, segments).  State touched here is re-initialised by the
+// Krylov init of the first solve.
+bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const KrylovState& ks, RedScratch rs, int conj, int nb,
+                        int SY, int Rs, int G, int* variant) {
+  for (auto& t : ctx->tuned)
+    if (t.R == Rs && t.nb == nb && t.G == G) {
+      *variant = t.variant;
+      return BT_OK;
+    }
+  cudaStream_t st = ctx->stream;
+  launch_set_int(ks.active, 1, SY, st);
+  launch_set_int(ks.n_active, SY, 1, st);
+  CK(cudaMemsetAsync(ctx->p32.p, 0x3f, (size_t)op.n * op.Rp * sizeof(float2), st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0}};
+  for (int v = 0; v < 2; ++v) {
+    spmm_f32(v, op, ctx->p32.p, ctx->q32.p, ks, rs, conj, nb, ctx->sms, st);  // warm-up
+    CK(cudaEventRecord(e0, st));
+    for (int k = 0; k < 3; ++k) spmm_f32(v, op, ctx->p32.p, ctx->q32.p, ks, rs, conj, nb, ctx->sms, st);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    tu.ms[v] = ms / 3;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CKL();
+  CK(cudaMemsetAsync(ctx->ks_status.p, 0, SY * sizeof(int), st));
+  tu.variant = tu.ms[1] < tu.ms[0] ? 1 : 0;
+  ctx->tuned.push_back(tu);
+  *variant = tu.variant;
+  return BT_OK;
+}
+
 // z = P_c r for the polynomial systems of the current inner solve (Horner,
 // ping-pong zA/zB, ending in zA), z = D^-1 r for Jacobi systems
 bt_status apply_poly(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const KrylovState& ks, cudaStream_t st) {
@@ -511,6 +586,144 @@ static bt_status collect_samples(bt_ctx* ctx, OpArgs op, const VecArgs& va, cons
       for (int b2 = a2; b2 < 9; ++b2, ++q) G[9 * a2 + b2] = G[9 * b2 + a2] = ok ? gs[q] / rr : 0.0;
     for (int a2 = 0; a2 < 9; ++a2) h[a2] = ok ? gs[45 + a2] / rr : 0.0;
   }
+  return BT_OK;
+}
+
+// Mixed mode with the time step captured once as a CUDA graph: refinement
+// loop and inner Krylov loop are nested WHILE conditional nodes whose
+// conditions device kernels set from the convergence counters, the step and
+// its coefficients come from a device counter, so the host only launches the
+// graph once per step.  Returns BT_ECUDA (and leaves the state untouched, as
+// nothing ran) when the graph cannot be built; the caller then drives the same
+// kernels from the host.
+struct GraphRun {
+  int variant;
+  OpArgs op;
+  VecArgs va;
+  KrylovState ks;
+  RefineState rf;
+  bool df;
+  int conj, nb, N;
+  double tol_inner;
+};
+
+static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts& o, int Rs, int G,
+                           int64_t* iters, int64_t* passes) {
+  // the graph is captured on private streams (capture runs nothing, and the
+  // legacy default stream cannot be captured) and launched on the context's stream
+  cudaStream_t run_st = ctx->stream;
+  for (auto& s : ctx->cap_stream)
+    if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return BT_ECUDA;
+  cudaStream_t cs = ctx->cap_stream[2], c2 = ctx->cap_stream[0], c3 = ctx->cap_stream[1];
+  if (ensure(ctx->d_ctl, 8) != cudaSuccess) return BT_ECUDA;
+  const int h0[8] = {1, 0, 0, 0, 0, 0, 0, 0};
+  if (cudaMemcpyAsync(ctx->d_ctl.p, h0, sizeof(h0), cudaMemcpyHostToDevice, run_st) != cudaSuccess) return BT_ECUDA;
+  if (cudaStreamSynchronize(run_st) != cudaSuccess) return BT_ECUDA;
+  GraphCtl gc{ctx->d_ctl.p, g.ks.n_active, ctx->d_seg_N.p, Rs, G, o.max_iter, o.max_refine};
+  OpArgs op0 = g.op, opL = g.op;
+  op0.coef = opL.coef = ctx->d_coef.p;
+  op0.step = opL.step = ctx->d_ctl.p;
+  op0.sel = 0;
+  opL.sel = 1;
+  auto rs_at = [&](int c) { return RedScratch{ctx->red_part.p, ctx->red_counter.p + c}; };
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = true;
+  std::string why;
+  int site = 0;
+  auto E = [&](cudaError_t e) {
+    ++site;
+    if (e != cudaSuccess && ok) why = "site " + std::to_string(site) + ": " + cudaGetErrorString(e);
+    if (e != cudaSuccess) ok = false;
+    return e == cudaSuccess;
+  };
+  auto while_node = [&](cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t capg;
+    const cudaGraphNode_t* deps;
+    size_t nd = 0;
+    if (!E(cudaStreamGetCaptureInfo(s, &cst, nullptr, &capg, &deps, nullptr, &nd))) return;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (!E(cudaGraphAddNode(&node, capg, deps, nullptr, nd, &p))) return;
+    *body = p.conditional.phGraph_out[0];
+    E(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  };
+  auto capg_of = [&](cudaStream_t s) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t capg = nullptr;
+    E(cudaStreamGetCaptureInfo(s, &cst, nullptr, &capg, nullptr, nullptr, nullptr));
+    return capg;
+  };
+  if (E(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) {
+    launch_graph_step_begin(gc, ctx->rf_active.p, cs);
+    if (g.df) launch_resid0_df(op0, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(0), g.nb, ctx->sms, cs);
+    else launch_resid0(op0, ctx->u64.p, ctx->r64.p, g.rf, rs_at(0), g.nb, ctx->sms, cs);
+    cudaGraphConditionalHandle hR{}, hI{};
+    cudaGraph_t bodyR = nullptr, bodyI = nullptr;
+    cudaGraph_t top = capg_of(cs);
+    if (ok) E(cudaGraphConditionalHandleCreate(&hR, top, 0, 0));
+    if (ok) launch_graph_cond(gc, 0, hR, cs);
+    if (ok) while_node(cs, hR, &bodyR);
+    if (ok && E(cudaStreamBeginCaptureToGraph(c2, bodyR, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
+      if (g.df)
+        launch_krylov_init_f32_df(opL, g.va, ctx->rdf.p, ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p,
+                                  ctx->p32.p, g.ks, g.tol_inner, rs_at(1), g.conj, ctx->sms, c2);
+      else
+        launch_krylov_init_f32(opL, g.va, ctx->r64.p, ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p,
+                               ctx->p32.p, g.ks, g.tol_inner, rs_at(1), g.conj, ctx->sms, c2);
+      if (E(cudaGraphConditionalHandleCreate(&hI, bodyR, 0, 0))) {
+        launch_graph_cond(gc, 2, hI, c2);
+        while_node(c2, hI, &bodyI);
+        if (ok && E(cudaStreamBeginCaptureToGraph(c3, bodyI, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
+          spmm_f32(g.variant, opL, ctx->p32.p, ctx->q32.p, g.ks, rs_at(2), g.conj, g.nb, ctx->sms, c3);
+          launch_krylov_update_f32(opL, g.va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, g.ks, rs_at(3), g.conj,
+                                   ctx->sms, c3);
+          launch_krylov_p_f32(opL, g.va, ctx->r32.p, ctx->p32.p, g.ks, ctx->sms, c3);
+          launch_graph_cond(gc, 3, hI, c3);
+          E(cudaGetLastError());
+          cudaGraph_t tmp;
+          E(cudaStreamEndCapture(c3, &tmp));
+        }
+      }
+      if (g.df) launch_resid_sub_df(opL, ctx->x32.p, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(4), g.nb, ctx->sms, c2);
+      else launch_resid_sub(opL, ctx->x32.p, ctx->u64.p, ctx->r64.p, g.rf, rs_at(4), g.nb, ctx->sms, c2);
+      launch_graph_cond(gc, 1, hR, c2);
+      E(cudaGetLastError());
+      cudaGraph_t tmp;
+      E(cudaStreamEndCapture(c2, &tmp));
+    }
+    launch_mark_ref_left(g.rf, g.ks, Rs * G, cs);
+    launch_graph_step_end(gc, cs);
+    E(cudaGetLastError());
+    cudaGraph_t tmp = nullptr;
+    const bool was_ok = ok;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &tmp);
+    if (ee != cudaSuccess && was_ok) why = std::string("end capture: ") + cudaGetErrorString(ee);
+    if (ee != cudaSuccess) ok = false;
+    graph = tmp;
+  }
+  if (ok && graph) E(cudaGraphInstantiate(&exec, graph, 0));
+  if (!ok || !graph) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    // not an error of the run: the caller drives the same kernels from the host
+    ctx->err = "step graph unavailable (" + why + "); host-driven launches used";
+    return BT_ECUDA;
+  }
+  for (int s = 0; s < g.N && ok; ++s) ok = cudaGraphLaunch(exec, run_st) == cudaSuccess;
+  int hc[8] = {0};
+  if (ok) ok = cudaMemcpyAsync(hc, ctx->d_ctl.p, sizeof(hc), cudaMemcpyDeviceToHost, run_st) == cudaSuccess;
+  if (ok) ok = cudaStreamSynchronize(run_st) == cudaSuccess;
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (!ok) return fail(ctx, BT_ECUDA, std::string("bt_run: graph launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+  *iters = hc[3];
+  *passes = hc[4] + 0;
   return BT_OK;
 }
 
@@ -675,11 +888,26 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
                  ctx->ks_iter.p, ctx->ks_active.p, ctx->n_active.p, ctx->ks_status.p, ctx->ks_rr_best.p,
                  ctx->ks_it_best.p, o.max_iter, plain ? 0 : 30};
   RefineState rf{ctx->rf_r0n2.p, ctx->rf_rk2.p, ctx->rf_scale.p, ctx->rf_err.p, ctx->rf_active.p,
-                 ctx->n_active.p + 1, o.tol_ref * o.tol_ref, 0.0};
+                 ctx->n_active.p + 1, o.tol_ref * o.tol_ref, 0.0, ctx->ks_status.p};
   const double feps = 1e-14 * ctx->wmax;
   rf.floor_c2 = feps * feps;
   auto rs_at = [&](int c) { return RedScratch{ctx->red_part.p, ctx->red_counter.p + c}; };
 
+  // register-reuse tiles and the tuned SpMM variant for the FP32 inner solves
+  int variant = 0;
+  if (!plain) {
+    if (bt_status e = ensure_tiles(ctx, st)) return e;
+    op.t_row0 = ctx->t_row0.p;
+    op.t_u0 = ctx->t_u0.p;
+    op.t_s0 = ctx->t_s0.p;
+    op.t_ucol = ctx->t_ucol.p;
+    op.t_seg0 = ctx->t_seg0.p;
+    op.pkt = ctx->pkt.p;
+    op.mdt = ctx->mdt.p;
+    OpArgs opt = op;
+    opt.coef = ctx->d_coef.p + G;  // step 1, L operator
+    if (bt_status e = autotune_spmm(ctx, opt, ks, rs_at(2), conj, nb, SY, Rs, G, &variant)) return e;
+  }
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
   ctx->st_spmm_ms = ctx->st_resid_ms = 0;
   ctx->ev_used = 0;
@@ -704,9 +932,23 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     if (e) cudaEventRecord(e->b, st);
   };
 
+  // production path: the captured time step (mixed mode)
+  bool graph_done = false;
+  if (!plain && !learned && !col && !prof && !(o.flags & BT_OPT_NO_GRAPH)) {
+    GraphRun gr{variant, op, va, ks, rf, df, conj, nb, N, o.tol_inner};
+    int64_t gi = 0, gp = 0;
+    if (run_graph(ctx, gr, o, Rs, G, &gi, &gp) == BT_OK) {
+      graph_done = true;
+      ctx->st_steps = N;
+      ctx->st_iters = ctx->st_spmm = gi;
+      ctx->st_refine = gp;
+      ctx->st_resid = N + gp;
+      L += 5 * (int64_t)N + 4 * gp + 4 * gi;
+    }
+  }
   double last_fq = NAN;
   size_t col_next = 0;
-  for (int step = 1; step <= N; ++step) {
+  for (int step = 1; step <= N && !graph_done; ++step) {
     const OpCoef* c_r0 = ctx->d_coef.p + 2 * (size_t)(step - 1) * G;
     const OpCoef* c_L = c_r0 + G;
     // f_bar_n (lab) or F_n (transformed) of this step: the preconditioner feature
@@ -775,7 +1017,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
                                    ctx->sms, st);
           launch_krylov_p_f64(op, va, ctx->rk64.p, ctx->p64.p, ks, ctx->sms, st);
         } else {
-          timed(0, [&] { launch_spmm_krylov_f32(op, ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb, ctx->sms, st); });
+          timed(0, [&] { spmm_f32(variant, op, ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb, ctx->sms, st); });
           launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs_at(3), conj,
                                    ctx->sms, st, learned ? ctx->pmode.p : nullptr);
           if (learned) {
@@ -874,6 +1116,16 @@ extern "C" bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_es
   if (err_est) std::memcpy(err_est, ctx->err_est.data(), SYt * sizeof(double));
   if (status)
     for (size_t i = 0; i < SYt; ++i) status[i] = ctx->status[i];
+  return BT_OK;
+}
+
+extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_row, double* ms_tiled) {
+  if (!ctx) return BT_EINVAL;
+  if (ctx->tuned.empty()) return BT_ESTATE;
+  const auto& t = ctx->tuned.back();
+  if (variant) *variant = t.variant;
+  if (ms_row) *ms_row = t.ms[0];
+  if (ms_tiled) *ms_tiled = t.ms[1];
   return BT_OK;
 }
 

@@ -53,9 +53,23 @@ struct bt_ctx {
   std::vector<double> seg_delta, seg_Delta, seg_TE;
   std::vector<int> seg_N;                        // steps per segment
   std::vector<std::vector<double>> seg_fbar, seg_F;
-  bt::DBuf<int> d_blk_seg, d_blk0, d_seg_N;
+  bt::DBuf<int> d_blk_seg, d_blk0, d_seg_N, d_ctl;
+  cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};  // captures of the step graph
   bt::DBuf<int64_t> d_row0;
   int nblk = 0;
+  // register-reuse SpMM tiles (built for one segmentation) and the autotuner's choice
+  bt::DBuf<int32_t> t_row0, t_u0, t_s0, t_seg0, t_slot;
+  bt::DBuf<uint32_t> t_ucol;
+  bt::DBuf<float4> pkt;
+  bt::DBuf<float> mdt;
+  std::vector<int64_t> tiles_for;   // seg_row0 the tiles were built for
+  int64_t planes_version = 0, tiles_planes_version = -1;
+  struct Tuned {
+    int R, nb, G;
+    int variant;   // 0 row kernel, 1 tiled kernel
+    double ms[2];
+  };
+  std::vector<Tuned> tuned;
 
   // gradients
   int n_dir = 0, n_b = 0, R = 0;

@@ -84,6 +84,7 @@ struct RefineState {
   int* n_active;
   double tol2;       // tol_ref^2
   double floor_c2;   // (eps * max w)^2: |r_0|^2 below floor_c2 |u|^2 counts as zero
+  int* status;       // per-system status (shared with the Krylov state)
 };
 
 // Segment plan: the solve may hold several geometries ("segments") of uneven
@@ -114,12 +115,23 @@ struct OpArgs {
   const float4* pklo;
   const float2* kjmd_hi; // double-float split of (K + J, MD)
   const float2* kjmd_lo;
-  const OpCoef* coef;    // device, one per segment (current step)
+  const OpCoef* coef;    // device: one per segment for the current step, or (step != null)
+                         // the whole table [step][2][segment]
+  const int* step;       // device step counter (captured time step) or null
+  int sel;               // with step: 0 = r_0 operator, 1 = L_n
   const double* q;       // [G R]
   const double* qhat;    // [3 G R] unit direction of each system
   int R, Rp;             // systems per segment, padded vector width
   int transformed;
   SegPlan sp;
+  // row tiles of the register-reuse SpMM (null when not built)
+  const int32_t* t_row0;
+  const int32_t* t_u0;
+  const int32_t* t_s0;
+  const uint32_t* t_ucol;
+  const int32_t* t_seg0;   // [G + 1] first tile of each segment
+  const float4* pkt;       // pk32 in tile-entry order
+  const float* mdt;        // md32 in tile-entry order
 };
 
 struct VecArgs {
@@ -165,6 +177,11 @@ int spmm_grid_rows(int64_t n, int sms);
 
 void launch_spmm_krylov_f32(const OpArgs& op, const float2* p, float2* q, const KrylovState& ks,
                             RedScratch rs, int conj, int nb, int sms, cudaStream_t st);
+// the same operator with row tiles sharing gathered rows (register reuse)
+void launch_spmm_krylov_f32_tiled(const OpArgs& op, const float2* p, float2* q, const KrylovState& ks,
+                                  RedScratch rs, int conj, int nb, int sms, cudaStream_t st);
+void launch_gather_tile_planes(const int32_t* slot, int64_t nnz, const float4* pk32, const float* md32, float4* pkt,
+                               float* mdt, cudaStream_t st);
 void launch_spmm_krylov_f64(const OpArgs& op, const double2* p, double2* q, const KrylovState& ks,
                             RedScratch rs, int conj, int nb, int sms, cudaStream_t st);
 // r = op_{P0=K+J}(u) with |r|^2, |u|^2 partials; sets refinement state
@@ -225,6 +242,16 @@ void launch_set_int(int* p, int v, int n, cudaStream_t st);
 void launch_finish_step(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st);
 void launch_mark_ref_left(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st);
 void launch_seg_active(int* act, int R, int G, int step, const int* segN, cudaStream_t st);
+// captured time step (k_graph.cu)
+struct GraphCtl {
+  int* ctl;        // [0] step, [1] refinement pass, [2] inner iteration, [3] total iterations, [4] total passes
+  int* n_active;   // [0] Krylov, [1] refinement
+  const int* segN;
+  int R, G, max_iter, max_refine;
+};
+void launch_graph_step_begin(const GraphCtl& c, int* rf_active, cudaStream_t st);
+void launch_graph_cond(const GraphCtl& c, int which, cudaGraphConditionalHandle h, cudaStream_t st);
+void launch_graph_step_end(const GraphCtl& c, cudaStream_t st);
 
 // ---------------------------------------------------------------- device helpers
 #ifdef __CUDACC__
@@ -318,10 +345,16 @@ struct LaneCoef {
   int act[NB];
 };
 
+// coefficients of segment g for the current step
+__device__ __forceinline__ OpCoef op_coef(const OpArgs& op, int g) {
+  if (op.step) return op.coef[((size_t)(*op.step - 1) * 2 + op.sel) * op.sp.G + g];
+  return op.coef[g];
+}
+
 // r0: first local system of the lane in segment g (global system g R + r)
 template <int NB>
 __device__ __forceinline__ void lane_coef(const OpArgs& op, int g, int r0, const int* active, LaneCoef<NB>& lc) {
-  const OpCoef cf = op.coef[g];
+  const OpCoef cf = op_coef(op, g);
   const int base = g * op.R;
   lc.a = cf.a;
   // the NB RHS of a lane share one direction (the host picks NB accordingly)
@@ -423,13 +456,24 @@ __device__ __forceinline__ void refine_finish(int mode, const RefineState& rf, i
     rf.r0n2[s] = t.x;
     rf.rk2[s] = t.x;
     rf.scale[s] = (double)(float)sqrt(t.x);  // FP32-exact: the same number scales and unscales
-    if (!isfinite(t.x) || !(t.x > rf.floor_c2 * t.y)) {
-      // nothing to solve: the increment is zero to FP64 rounding (or not finite)
+    if (!isfinite(t.x) || !isfinite(t.y)) {
+      // a non-finite step residual: this system stops, the others go on
+      rf.status[s] = BT_ENAN;
+      rf.active[s] = 0;
+      atomicSub(rf.n_active, 1);
+    } else if (!(t.x > rf.floor_c2 * t.y)) {
+      // nothing to solve: the increment is zero to FP64 rounding
       rf.active[s] = 0;
       atomicSub(rf.n_active, 1);
     }
   } else {
     const double prev = rf.rk2[s];
+    if (!isfinite(t.x)) {
+      rf.status[s] = BT_ENAN;
+      rf.active[s] = 0;
+      atomicSub(rf.n_active, 1);
+      return;
+    }
     rf.rk2[s] = t.x;
     rf.scale[s] = (double)(float)sqrt(t.x);
     // converged, or stagnated: a pass that no longer halves the residual has

@@ -43,7 +43,7 @@ struct SysCoef {
   double b, c, qx, qy, qz;
 };
 __device__ __forceinline__ SysCoef sys_coef(const OpArgs& op, int s) {
-  const OpCoef cf = op.coef[s / op.R];
+  const OpCoef cf = op_coef(op, s / op.R);
   double q = op.q[s];
   SysCoef sc;
   sc.b = cf.bq2 * q * q;

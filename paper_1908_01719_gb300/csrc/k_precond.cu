@@ -312,7 +312,7 @@ __global__ void k_horner_first(OpArgs op, VecArgs va, const float2* __restrict__
     const int s = sys_of_col(col, va.nb);
     if (s >= va.R || !active[s]) continue;
     const int64_t i = (int64_t)(e / va.Rp);
-    const OpCoef cf = op.coef[0];
+    const OpCoef cf = op_coef(op, 0);
     const double q = op.q[s];
     const float bb = (float)(cf.bq2 * q * q), cc = (float)(cf.cq * q);
     const float4 dg = va.diag32[i];
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(256) k_gram(OpArgs op, VecArgs va, const float
   const bool live = t < rpp * RS && col < va.Rp;
   const int s = live ? sys_of_col(col, va.nb) : 0;
   if (live && s < va.R) {
-    const OpCoef cf = op.coef[0];
+    const OpCoef cf = op_coef(op, 0);
     const double q = op.q[s];
     const float bb = (float)(cf.bq2 * q * q), cc = (float)(cf.cq * q);
     const float qx = (float)op.qhat[3 * s], qy = (float)op.qhat[3 * s + 1], qz = (float)op.qhat[3 * s + 2];

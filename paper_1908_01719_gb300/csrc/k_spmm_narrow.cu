@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_spmm_krylov_narrow(OpArgs op, const dou
                                                             double2* __restrict__ q, KrylovState ks, RedScratch rs) {
   if (*ks.n_active == 0) return;
   const int g = threadIdx.x % NG, grp = threadIdx.x / NG, ngrp = blockDim.x / NG;
-  const OpCoef cf = op.coef[0];
+  const OpCoef cf = op_coef(op, 0);
   double qx[RM], qy[RM], qz[RM], cb[RM], cc[RM];
 #pragma unroll
   for (int b = 0; b < RM; ++b) {
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) k_resid0_narrow(OpArgs op, const double2*
                                                        double2* __restrict__ r, RefineState rf, RedScratch rs) {
   if (*rf.n_active == 0) return;
   const int g = threadIdx.x % NG, grp = threadIdx.x / NG, ngrp = blockDim.x / NG;
-  const OpCoef cf = op.coef[0];
+  const OpCoef cf = op_coef(op, 0);
   double qx[RM], qy[RM], qz[RM], cb[RM], cc[RM];
 #pragma unroll
   for (int b = 0; b < RM; ++b) {

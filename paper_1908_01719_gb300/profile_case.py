@@ -1,0 +1,45 @@
+"""One small, short run of a workload for profilers (ncu): the seeded geometry
+of a config on a chosen grid, a shortened PGSE sequence (a few time steps),
+mixed precision.  It prints the sizes and the counters of the run.
+
+  python -m paper_1908_01719_gb300.profile_case --config cfg4 --grid 64 --steps 2
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    import geom
+    from paper_1908_01719_gb300 import bt
+    from paper_1908_01719_gb300.build import build
+    from paper_1908_01719_gb300.simulate import Simulation
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--grid", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=2, help="time steps (pulse on throughout)")
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "plain"])
+    a = ap.parse_args()
+    build()
+    p = getattr(geom, a.config)(n=a.grid)
+    # a sequence of `steps` steps: first pulse for half, second for the rest
+    half = max(1, a.steps // 2)
+    p.delta = half * p.dt
+    p.Delta = half * p.dt
+    p.TE = 2 * half * p.dt
+    sim = Simulation(p)
+    mode = bt.BT_MODE_MIXED if a.mode == "mixed" else bt.BT_MODE_PLAIN_FP64
+    S, err, stat, _ = sim.run(mode, flags=bt.BT_OPT_NO_GRAPH)
+    print(f"{a.config} grid {a.grid}: n_dof {sim.n_dof}, nnz {sim.nnz}, RHS {sim.R}, stats {sim.stats()}")
+    sim.close()
+
+
+if __name__ == "__main__":
+    main()
