@@ -87,6 +87,20 @@ bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t*
 bt_status bt_get_dofmap(const bt_ctx* ctx, int32_t* dof_node, int32_t* dof_cmpt);
 /* CSR pattern: row_ptr [n_dof+1], col [nnz], columns ascending in each row. */
 bt_status bt_get_pattern(const bt_ctx* ctx, int64_t* row_ptr, int32_t* col);
+/* The halo tiles the shared-memory Krylov apply uses (host-side build, no GPU
+ * needed): rows in Morton order of their node coordinates, cut into tiles of
+ * at most 128 rows whose columns span at most `umax` distinct rows.  With all
+ * array pointers NULL only the sizes are returned (n_tiles, n_halo = total
+ * halo entries).  Otherwise (caller-allocated): r0 [n_tiles+1] offsets into
+ * rows; rows [n_dof] owned rows tile by tile; rowe [n_dof+1] first entry of
+ * each owned row; rowl [n_dof] local halo index of each owned row; u0
+ * [n_tiles+1] offsets into ucol; ucol [n_halo] halo rows ascending, bit 31 set
+ * on the rows the tile owns; lidx [nnz] local column index of each entry in
+ * tile order.  Tiles respect the current segments.  BT_EINVAL if umax is
+ * outside [16, 65535] or a row has more than umax columns. */
+bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t* n_halo, int32_t* r0,
+                            int32_t* rows, int32_t* rowe, uint16_t* rowl, int32_t* u0, uint32_t* ucol,
+                            uint16_t* lidx);
 
 /* ---------------------------------------------------------------- assembly
  * Element-by-element, deterministic assembly on the GPU of every matrix over
@@ -144,7 +158,20 @@ bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32
  * Each step solves L_n d = r_0 = (R_n - L_n) u^{n-1}, u^n = u^{n-1} + d, with
  * L_n = M + theta dt A_n, R_n = M - (1-theta) dt A_{n-1} (Appendix B). */
 enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
-enum { BT_OPT_RESID_FP64 = 1u, BT_OPT_PROFILE = 2u, BT_OPT_NO_GRAPH = 4u };
+/* Option flags: BT_OPT_RESID_FP64 native-FP64 refinement residuals;
+ * BT_OPT_PROFILE CUDA events around every fused SpMM and residual launch
+ * (host-driven loop); BT_OPT_NO_GRAPH host-driven loop instead of the
+ * captured step graph; BT_OPT_VARIANT_ROW / _TILED / _HALO bypass the
+ * autotuner and use that Krylov variant (bt_get_tuning; _HALO falls back to
+ * the tuned choice where the halo tiles are not available). */
+enum {
+  BT_OPT_RESID_FP64 = 1u,
+  BT_OPT_PROFILE = 2u,
+  BT_OPT_NO_GRAPH = 4u,
+  BT_OPT_VARIANT_ROW = 8u,
+  BT_OPT_VARIANT_TILED = 16u,
+  BT_OPT_VARIANT_HALO = 32u
+};
 typedef struct bt_solver_opts {
   double tol_fp64;      /* plain FP64 stopping tolerance (default 1e-12)          */
   double tol_inner;     /* inner FP32 Krylov tolerance (default 1e-4)             */
@@ -166,19 +193,40 @@ bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts);
  * relative signal error); status [G R] BT_OK / BT_ENOCONV / BT_ENAN.  Any
  * pointer may be NULL. */
 bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t* status);
+/* The field u^N at TE of one system of the last bt_run (the discrete
+ * magnetization of Appendix B's time loop, lab or transformed frame as
+ * assembled), as FP64 complex values in the context's dof numbering
+ * (bt_get_dofmap).  system = g R + r; with G = 1 it must lie in the RHS range
+ * of the last run.  u_re_im [2 n_g] (re, im per dof) receives the dofs of
+ * geometry g, n_g = node_off-derived dof count of that segment (n_dof when
+ * G = 1); n_rows (may be NULL) receives n_g.  Mixed runs return hi + lo of the
+ * double-float state rounded to FP64.  BT_ESTATE if no run left a state (any
+ * call that changes the mesh, assembly, sequence, segments or gradients
+ * discards it), BT_EINVAL for a system outside the last run. */
+bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_rows);
+/* The Krylov autotuner's last choice, made at the first FP32 run of a given
+ * RHS count, RHS-per-lane and segmentation by timing one inner iteration of
+ * each variant on the real pattern:
+ *   0  row SpMM (one warp per row, X gathered per nonzero) + vector updates
+ *   1  4-row register-reuse SpMM + vector updates
+ *   2  halo-staged apply (Morton-ordered row tiles, their halo rows of X staged
+ *      in shared memory, search-direction and solution updates fused in) +
+ *      z update; offered in BT_MODE_MIXED only
+ * ms_iter [3] (may be NULL) receives the measured ms per iteration of each
+ * (0 = not timed).  BT_ESTATE before any tuning. */
+bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter);
 /* Counters of the last bt_run (any pointer may be NULL): time steps, total
  * Krylov iterations (summed over solves, not RHS), refinement passes, fused
  * SpMM launches, with BT_OPT_PROFILE the summed device time (ms) of the
- * FP32/FP64 fused SpMM launches and of the refinement-residual launches, the
- * number of refinement-residual launches and of all kernel launches. */
-/* The SpMM autotuner's last choice (tuned at the first FP32 run of a given
- * RHS count, RHS-per-lane and segmentation, by timing both kernels on the real
- * pattern): variant 0 = row kernel, 1 = row-tile kernel sharing gathered rows;
- * and the measured ms per launch of each.  BT_ESTATE before any tuning. */
-bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_row, double* ms_tiled);
+ * FP32/FP64 fused SpMM launches (for variant 2 the halo-staged apply) and of
+ * the refinement-residual launches, the number of refinement-residual
+ * launches and of all kernel launches, and the number of active systems
+ * summed over the fused SpMM launches (the right-hand sides each launch
+ * actually processed). */
 bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters,
                        int64_t* refine_passes, int64_t* spmm_launches, double* spmm_ms,
-                       double* resid_ms, int64_t* resid_launches, int64_t* kernel_launches);
+                       double* resid_ms, int64_t* resid_launches, int64_t* kernel_launches,
+                       int64_t* sys_iters);
 
 /* ---------------------------------------------------------------- learned preconditioner
  * A small network (5 -> 64 -> 64 -> 9, ReLU, bfloat16 weights, FP32

@@ -280,7 +280,7 @@ class _Solver:
         return x
 
 
-def run_lab(p, asm=None, rhs=None, return_history=False, route=None):
+def run_lab(p, asm=None, rhs=None, return_history=False, route=None, return_field=False):
     """Lab frame (Neumann outer boundary):
         L_n = M + theta dt (K + J + i q f_bar_n Mq)
         R_n = M - (1 - theta) dt (K + J + i q f_bar_n Mq),  Mq = sum_k qhat_k M_k
@@ -296,7 +296,7 @@ def run_lab(p, asm=None, rhs=None, return_history=False, route=None):
     nb = len(p.bvals)
     rhs = range(p.n_rhs) if rhs is None else rhs
     th, dt = p.theta, p.dt
-    out, hist = [], []
+    out, hist, fields = [], [], []
     for r in rhs:
         qh = p.dirs[r // nb]
         q = float(q_from_b(p.bvals[r % nb], p.delta, p.Delta))
@@ -311,11 +311,11 @@ def run_lab(p, asm=None, rhs=None, return_history=False, route=None):
             h.append(w @ u)
         out.append(w @ u)
         hist.append(h)
-    out = np.array(out)
-    return (out, np.array(hist)) if return_history else out
+        fields.append(u)
+    return _result(np.array(out), hist, fields, return_history, return_field)
 
 
-def run_transformed(p, asm=None, rhs=None, return_history=False, route=None):
+def run_transformed(p, asm=None, rhs=None, return_history=False, route=None, return_field=False):
     """Gauge-transformed frame u = U exp(i q F(t) qhat.x) (Appendix A), valid
     for periodic and Neumann outer boundaries:
         A(F) = K + J + q^2 F^2 MD + i q F Eq,  Eq = sum_k qhat_k E_k
@@ -332,7 +332,7 @@ def run_transformed(p, asm=None, rhs=None, return_history=False, route=None):
     nb = len(p.bvals)
     rhs = range(p.n_rhs) if rhs is None else rhs
     th, dt = p.theta, p.dt
-    out, hist = [], []
+    out, hist, fields = [], [], []
     for r in rhs:
         qh = p.dirs[r // nb]
         q = float(q_from_b(p.bvals[r % nb], p.delta, p.Delta))
@@ -350,10 +350,21 @@ def run_transformed(p, asm=None, rhs=None, return_history=False, route=None):
             h.append(w @ u)
         out.append(w @ u)
         hist.append(h)
-    out = np.array(out)
-    return (out, np.array(hist)) if return_history else out
+        fields.append(u)
+    return _result(np.array(out), hist, fields, return_history, return_field)
 
 
-def run(p, asm=None, rhs=None, return_history=False, route=None):
+def _result(out, hist, fields, return_history, return_field):
+    """The signals; with return_history also S(t_n) per RHS, with return_field
+    also u^N per RHS (rows in the dof numbering of `assemble`)."""
+    res = (out,)
+    if return_history:
+        res += (np.array(hist),)
+    if return_field:
+        res += (np.array(fields),)
+    return res[0] if len(res) == 1 else res
+
+
+def run(p, asm=None, rhs=None, return_history=False, route=None, return_field=False):
     f = run_transformed if (p.transformed or p.periodic_mask) else run_lab
-    return f(p, asm, rhs, return_history, route)
+    return f(p, asm, rhs, return_history, route, return_field)

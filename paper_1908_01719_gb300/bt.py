@@ -20,6 +20,7 @@ BT_FRAME_LAB, BT_FRAME_TRANSFORMED = 0, 1
 BT_PGSE = 0
 BT_MODE_PLAIN_FP64, BT_MODE_MIXED, BT_MODE_LEARNED = 0, 1, 2
 BT_OPT_RESID_FP64, BT_OPT_PROFILE, BT_OPT_NO_GRAPH = 1, 2, 4
+BT_OPT_VARIANT_ROW, BT_OPT_VARIANT_TILED, BT_OPT_VARIANT_HALO = 8, 16, 32
 PLANES = {"M": 0, "K": 1, "J": 2, "MD": 3, "Mx": 4, "My": 5, "Mz": 6, "Ex": 7, "Ey": 8, "Ez": 9, "A0": 10}
 
 # every symbol include/bt.h declares
@@ -28,7 +29,7 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats",
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
-           "bt_set_segments", "bt_get_tuning"]
+           "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -74,11 +75,13 @@ def lib():
             "bt_set_sequence": [P, C.c_int, D, D, D],
             "bt_set_gradients": [P, I32, P, I32, P],
             "bt_set_segments": [P, I32, P, P, P, P],
-            "bt_get_tuning": [P, P, P, P],
+            "bt_get_tuning": [P, P, P],
             "bt_default_opts": [C.POINTER(bt_solver_opts)],
             "bt_run": [P, C.c_int, C.POINTER(bt_solver_opts)],
             "bt_get_signals": [P, P, P, P],
-            "bt_get_stats": [P, P, P, P, P, P, P, P, P],
+            "bt_get_state": [P, I32, P, P],
+            "bt_get_halo_tiles": [P, I32, P, P, P, P, P, P, P, P, P],
+            "bt_get_stats": [P, P, P, P, P, P, P, P, P, P],
             "bt_train_default_opts": [C.POINTER(bt_train_opts)],
             "bt_precond_features": [P, P, P, P],
             "bt_collect_precond_data": [P, C.POINTER(bt_solver_opts), I32, P, P, P, P],
@@ -216,13 +219,38 @@ def bt_get_signals(ctx, R):
     return S[0::2] + 1j * S[1::2], err, stat
 
 
+def bt_get_state(ctx, system):
+    """u^N of one system of the last run, complex FP64, in dof order."""
+    n = C.c_int64(0)
+    _check(ctx, lib().bt_get_state(ctx, int(system), None, C.byref(n)))
+    u = np.empty(2 * n.value, np.float64)
+    _check(ctx, lib().bt_get_state(ctx, int(system), _ptr(u), C.byref(n)))
+    return u[0::2] + 1j * u[1::2]
+
+
+def bt_get_halo_tiles(ctx, umax):
+    """The halo tiles of the shared-memory Krylov apply, as numpy arrays."""
+    nt, nh = C.c_int64(0), C.c_int64(0)
+    _check(ctx, lib().bt_get_halo_tiles(ctx, int(umax), C.byref(nt), C.byref(nh), *([None] * 7)))
+    n_dof, nnz, _ = bt_get_sizes(ctx)
+    out = {"r0": np.empty(nt.value + 1, np.int32), "rows": np.empty(n_dof, np.int32),
+           "rowe": np.empty(n_dof + 1, np.int32), "rowl": np.empty(n_dof, np.uint16),
+           "u0": np.empty(nt.value + 1, np.int32), "ucol": np.empty(nh.value, np.uint32),
+           "lidx": np.empty(nnz, np.uint16)}
+    _check(ctx, lib().bt_get_halo_tiles(ctx, int(umax), C.byref(nt), C.byref(nh),
+                                        *[_ptr(out[k]) for k in ("r0", "rows", "rowe", "rowl", "u0", "ucol",
+                                                                 "lidx")]))
+    return out
+
+
 def bt_get_stats(ctx):
-    i = (C.c_int64 * 6)()
+    i = (C.c_int64 * 7)()
     d = (C.c_double * 2)()
     _check(ctx, lib().bt_get_stats(ctx, C.byref(i, 0), C.byref(i, 8), C.byref(i, 16), C.byref(i, 24),
-                                   C.byref(d, 0), C.byref(d, 8), C.byref(i, 32), C.byref(i, 40)))
+                                   C.byref(d, 0), C.byref(d, 8), C.byref(i, 32), C.byref(i, 40), C.byref(i, 48)))
     return {"steps": i[0], "krylov_iters": i[1], "refine_passes": i[2], "spmm_launches": i[3],
-            "spmm_ms": d[0], "resid_ms": d[1], "resid_launches": i[4], "kernel_launches": i[5]}
+            "spmm_ms": d[0], "resid_ms": d[1], "resid_launches": i[4], "kernel_launches": i[5],
+            "sys_iters": i[6]}
 
 
 def bt_train_default_opts(**kw):
@@ -298,6 +326,7 @@ def bt_precond_grad_noalloc(w_ptr, n, feat_ptr, G_ptr, h_ptr, grad_ptr, loss_ptr
 
 def bt_get_tuning(ctx):
     v = C.c_int32()
-    d = (C.c_double * 2)()
-    _check(ctx, lib().bt_get_tuning(ctx, C.byref(v), C.byref(d, 0), C.byref(d, 8)))
-    return {"variant": ["row", "tiled"][v.value], "ms_row": d[0], "ms_tiled": d[1]}
+    d = (C.c_double * 3)()
+    _check(ctx, lib().bt_get_tuning(ctx, C.byref(v), d))
+    return {"variant": ["row", "tiled", "halo"][v.value], "ms_iter_row": d[0], "ms_iter_tiled": d[1],
+            "ms_iter_halo": d[2]}

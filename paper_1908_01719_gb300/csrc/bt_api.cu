@@ -108,6 +108,7 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
                          const int32_t* tet_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* kappa_cmpt,
                          uint32_t periodic_mask, const double* box_lo, const double* box_hi) {
   if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
   if (!xyz || !tet4 || !tet_cmpt || !D_cmpt || !kappa_cmpt || !box_lo || !box_hi || n_nodes <= 0 || n_tets <= 0 ||
       n_cmpt <= 0 || periodic_mask > 7)
     return fail(ctx, BT_EINVAL, "bt_upload_mesh: invalid argument");
@@ -138,6 +139,8 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
     return fail(ctx, BT_ENOMEM, "bt_upload_mesh: host allocation failed");
   }
   ctx->have_mesh = true;
+  ctx->G = 1;
+  ctx->seg_row0 = {0, ctx->mesh.n_dof};
   if (ctx->host_only) return BT_OK;
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -181,8 +184,33 @@ bt_status bt_get_pattern(const bt_ctx* ctx, int64_t* row_ptr, int32_t* col) {
   return BT_OK;
 }
 
+bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t* n_halo, int32_t* r0,
+                            int32_t* rows, int32_t* rowe, uint16_t* rowl, int32_t* u0, uint32_t* ucol,
+                            uint16_t* lidx) {
+  if (!ctx) return BT_EINVAL;
+  if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_get_halo_tiles: no mesh");
+  if (umax < 16 || umax > 65535) return fail(ctx, BT_EINVAL, "bt_get_halo_tiles: umax outside [16, 65535]");
+  HaloTiles t;
+  build_halo_tiles(ctx->mesh, ctx->seg_row0, umax, 128, t);
+  if (t.too_wide) return fail(ctx, BT_EINVAL, "bt_get_halo_tiles: a row has more than umax columns");
+  if (n_tiles) *n_tiles = (int64_t)t.r0.size() - 1;
+  if (n_halo) *n_halo = (int64_t)t.ucol.size();
+  auto put = [](auto* dst, const auto& v) {
+    if (dst) std::memcpy(dst, v.data(), v.size() * sizeof(v[0]));
+  };
+  put(r0, t.r0);
+  put(rows, t.rows);
+  put(rowe, t.rowe);
+  put(rowl, t.rowl);
+  put(u0, t.u0);
+  put(ucol, t.ucol);
+  put(lidx, t.lidx);
+  return BT_OK;
+}
+
 bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
   if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_assemble: no mesh");
   if (!need_gpu(ctx)) return fail(ctx, BT_ENODEV, "bt_assemble: host-only context");
   if (!(dt_us > 0) || !std::isfinite(dt_us) || !(theta > 0) || theta > 1 || flags > 1)
@@ -283,6 +311,7 @@ bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals) {
 
 bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta, double Delta, double TE) {
   if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
   if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_set_sequence: assemble first (dt is needed)");
   if (kind != BT_PGSE) return fail(ctx, BT_EINVAL, "bt_set_sequence: only BT_PGSE");
   if (!(delta > 0) || !(Delta >= delta) || !(TE >= Delta + delta - 1e-9 * TE))
@@ -322,6 +351,7 @@ bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta, double Delta, dou
 
 bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32_t n_b, const double* bvals) {
   if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
   if (!ctx->have_seq) return fail(ctx, BT_ESTATE, "bt_set_gradients: set the sequence first");
   if (n_dir <= 0 || n_b <= 0 || !dirs || !bvals || (int64_t)n_dir * n_b > 1024)
     return fail(ctx, BT_EINVAL, "bt_set_gradients: need 1 <= n_dir * n_b <= 1024");
@@ -361,6 +391,7 @@ bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32
 bt_status bt_set_segments(bt_ctx* ctx, int32_t G, const int64_t* node_off, const double* delta,
                           const double* Delta, const double* TE) {
   if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
   if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_set_segments: assemble first");
   if (G < 1 || !node_off || !delta || !Delta || !TE) return fail(ctx, BT_EINVAL, "bt_set_segments: bad arguments");
   const HostMesh& m = ctx->mesh;
@@ -480,48 +511,134 @@ bt_status ensure_tiles(bt_ctx* ctx, cudaStream_t st) {
   return BT_OK;
 }
 
+// Halo tiles for RHS-per-lane nb (umax from the shared-memory budget) and the
+// plane values in halo-entry order.  Sets ctx->halo_ok = false when a row is
+// wider than umax (the halo iteration is then not offered).
+bt_status ensure_halo(bt_ctx* ctx, int nb, cudaStream_t st) {
+  const int umax = (int)std::min<size_t>(65535, (96 * 1024) / halo_smem_bytes(nb, 1));
+  if (!ctx->halo_attr) {
+    halo_prepare();
+    CKL();
+    ctx->halo_attr = true;
+  }
+  if (ctx->halo_for != ctx->seg_row0 || ctx->halo_umax != umax) {
+    HaloTiles t;
+    build_halo_tiles(ctx->mesh, ctx->seg_row0, umax, 128, t);
+    ctx->halo_for = ctx->seg_row0;
+    ctx->halo_umax = umax;
+    ctx->halo_ok = !t.too_wide;
+    ctx->halo_planes_version = -1;
+    if (!ctx->halo_ok) return BT_OK;
+    CK(upload(ctx->h_r0, t.r0, st));
+    CK(upload(ctx->h_rows, t.rows, st));
+    CK(upload(ctx->h_rowe, t.rowe, st));
+    CK(upload(ctx->h_rowl, t.rowl, st));
+    CK(upload(ctx->h_u0, t.u0, st));
+    CK(upload(ctx->h_ucol, t.ucol, st));
+    CK(upload(ctx->h_lidx, t.lidx, st));
+    CK(upload(ctx->h_slot, t.slot, st));
+    CK(upload(ctx->h_seg0, t.seg_tile0, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (ctx->halo_ok && ctx->halo_planes_version != ctx->planes_version) {
+    CK(ensure(ctx->h_pkt, ctx->mesh.nnz));
+    CK(ensure(ctx->h_mdt, ctx->mesh.nnz));
+    launch_gather_tile_planes(ctx->h_slot.p, ctx->mesh.nnz, ctx->d_pk32.p, ctx->d_md32.p, ctx->h_pkt.p,
+                              ctx->h_mdt.p, st);
+    CKL();
+    ctx->halo_planes_version = ctx->planes_version;
+  }
+  return BT_OK;
+}
+
+HaloArgs halo_args(const bt_ctx* ctx) {
+  return HaloArgs{ctx->h_r0.p,  ctx->h_rows.p, ctx->h_rowe.p, ctx->h_rowl.p, ctx->h_u0.p, ctx->h_ucol.p,
+                  ctx->h_lidx.p, ctx->h_pkt.p, ctx->h_mdt.p, ctx->h_seg0.p, ctx->halo_umax};
+}
+
 void spmm_f32(int variant, const OpArgs& op, const float2* p, float2* q, const KrylovState& ks, RedScratch rs,
               int conj, int nb, int sms, cudaStream_t st) {
   if (variant == 1) launch_spmm_krylov_f32_tiled(op, p, q, ks, rs, conj, nb, sms, st);
   else launch_spmm_krylov_f32(op, p, q, ks, rs, conj, nb, sms, st);
 }
 
-// Autotuner: time the row kernel and the tiled kernel on the real pattern and
-// RHS count (3 launches each, CUDA events) and keep the faster, cached per
-// (RHS, RHS per lane, segments).  State touched here is re-initialised by the
-// Krylov init of the first solve.
-bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const KrylovState& ks, RedScratch rs, int conj, int nb,
-                        int SY, int Rs, int G, int* variant) {
+// Autotuner: time one Krylov iteration of each variant on the real pattern
+// and RHS count (CUDA events, 3 iterations after a warm-up) and keep the
+// fastest, cached per (RHS, RHS per lane, segments):
+//   0: row SpMM + vector update + p update
+//   1: 4-row register-reuse SpMM + vector update + p update
+//   2: halo-staged apply + z update (when the halo tiles exist and allow_halo)
+// The Krylov state is primed with benign scalars (nothing converges while
+// timing); the Krylov init of the first solve re-initialises all of it.
+bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const KrylovState& ks, RedScratch rs,
+                        RedScratch rs2, int conj, int nb, int SY, int Rs, int G, bool allow_halo, int* variant) {
+  bt_ctx::Tuned* hit = nullptr;
   for (auto& t : ctx->tuned)
-    if (t.R == Rs && t.nb == nb && t.G == G) {
-      *variant = t.variant;
-      return BT_OK;
+    if (t.R == Rs && t.nb == nb && t.G == G) hit = &t;
+  const bool halo = allow_halo && ctx->halo_ok;
+  if (!hit || (halo && hit->ms[2] == 0)) {
+    cudaStream_t st = ctx->stream;
+    const size_t NE = (size_t)op.n * op.Rp;
+    std::vector<double> one(2 * (size_t)SY), small(2 * (size_t)SY), half(2 * (size_t)SY), big(SY, 1e300);
+    for (int s2 = 0; s2 < SY; ++s2) {
+      one[2 * s2] = 1.0;
+      small[2 * s2] = 0.1;
+      half[2 * s2] = 0.5;
     }
-  cudaStream_t st = ctx->stream;
-  launch_set_int(ks.active, 1, SY, st);
-  launch_set_int(ks.n_active, SY, 1, st);
-  CK(cudaMemsetAsync(ctx->p32.p, 0x3f, (size_t)op.n * op.Rp * sizeof(float2), st));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0}};
-  for (int v = 0; v < 2; ++v) {
-    spmm_f32(v, op, ctx->p32.p, ctx->q32.p, ks, rs, conj, nb, ctx->sms, st);  // warm-up
-    CK(cudaEventRecord(e0, st));
-    for (int k = 0; k < 3; ++k) spmm_f32(v, op, ctx->p32.p, ctx->q32.p, ks, rs, conj, nb, ctx->sms, st);
-    CK(cudaEventRecord(e1, st));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    tu.ms[v] = ms / 3;
+    auto prime = [&]() -> bt_status {
+      launch_set_int(ks.active, 1, SY, st);
+      launch_set_int(ks.n_active, SY, 1, st);
+      launch_set_int(ks.iter, 0, SY, st);
+      launch_set_int(ks.it_best, 0, SY, st);
+      if (ks.pend) launch_set_int(ks.pend, 1, SY, st);
+      if (ks.par) launch_set_int(ks.par, 0, 1, st);
+      CK(cudaMemcpyAsync(ks.rho, one.data(), one.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(ks.alpha, small.data(), small.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(ks.beta, half.data(), half.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      CK(cudaMemsetAsync(ks.tol2, 0, SY * sizeof(double), st));
+      CK(cudaMemcpyAsync(ks.rr_best, big.data(), big.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      return BT_OK;
+    };
+    for (float2* b : {ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ctx->p32b.p})
+      if (b) CK(cudaMemsetAsync(b, 0x3e, NE * sizeof(float2), st));
+    auto iter = [&](int v) {
+      if (v == 2) {
+        launch_spmm_halo(op, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, ks, rs,
+                         conj, nb, st);
+        launch_krylov_update_z(op, va, ctx->r32.p, ctx->q32.p, ks, rs2, conj, st);
+      } else {
+        spmm_f32(v, op, ctx->p32.p, ctx->q32.p, ks, rs, conj, nb, ctx->sms, st);
+        launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs2, conj, ctx->sms,
+                                 st);
+        launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st);
+      }
+    };
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0, 0}};
+    for (int v = 0; v < (halo ? 3 : 2); ++v) {
+      if (bt_status e = prime()) return e;
+      iter(v);  // warm-up
+      CK(cudaEventRecord(e0, st));
+      for (int k = 0; k < 3; ++k) iter(v);
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      tu.ms[v] = ms / 3;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CKL();
+    CK(cudaMemsetAsync(ctx->ks_status.p, 0, SY * sizeof(int), st));
+    if (hit) *hit = tu;
+    else ctx->tuned.push_back(tu);
+    hit = hit ? hit : &ctx->tuned.back();
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  CKL();
-  CK(cudaMemsetAsync(ctx->ks_status.p, 0, SY * sizeof(int), st));
-  tu.variant = tu.ms[1] < tu.ms[0] ? 1 : 0;
-  ctx->tuned.push_back(tu);
-  *variant = tu.variant;
+  int best = hit->ms[1] < hit->ms[0] ? 1 : 0;
+  if (halo && hit->ms[2] > 0 && hit->ms[2] < hit->ms[best]) best = 2;
+  *variant = best;
   return BT_OK;
 }
 
@@ -670,7 +787,11 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
     if (ok) launch_graph_cond(gc, 0, hR, cs);
     if (ok) while_node(cs, hR, &bodyR);
     if (ok && E(cudaStreamBeginCaptureToGraph(c2, bodyR, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
-      if (g.df)
+      if (g.variant == 2)
+        launch_krylov_init_z(opL, g.va, g.df ? (const void*)ctx->rdf.p : (const void*)ctx->r64.p, g.df,
+                             ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p, g.ks, g.tol_inner, rs_at(1),
+                             g.conj, c2);
+      else if (g.df)
         launch_krylov_init_f32_df(opL, g.va, ctx->rdf.p, ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p,
                                   ctx->p32.p, g.ks, g.tol_inner, rs_at(1), g.conj, ctx->sms, c2);
       else
@@ -680,16 +801,23 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
         launch_graph_cond(gc, 2, hI, c2);
         while_node(c2, hI, &bodyI);
         if (ok && E(cudaStreamBeginCaptureToGraph(c3, bodyI, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
-          spmm_f32(g.variant, opL, ctx->p32.p, ctx->q32.p, g.ks, rs_at(2), g.conj, g.nb, ctx->sms, c3);
-          launch_krylov_update_f32(opL, g.va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, g.ks, rs_at(3), g.conj,
-                                   ctx->sms, c3);
-          launch_krylov_p_f32(opL, g.va, ctx->r32.p, ctx->p32.p, g.ks, ctx->sms, c3);
+          if (g.variant == 2) {
+            launch_spmm_halo(opL, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, g.ks,
+                             rs_at(2), g.conj, g.nb, c3);
+            launch_krylov_update_z(opL, g.va, ctx->r32.p, ctx->q32.p, g.ks, rs_at(3), g.conj, c3);
+          } else {
+            spmm_f32(g.variant, opL, ctx->p32.p, ctx->q32.p, g.ks, rs_at(2), g.conj, g.nb, ctx->sms, c3);
+            launch_krylov_update_f32(opL, g.va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, g.ks, rs_at(3),
+                                     g.conj, ctx->sms, c3);
+            launch_krylov_p_f32(opL, g.va, ctx->r32.p, ctx->p32.p, g.ks, ctx->sms, c3);
+          }
           launch_graph_cond(gc, 3, hI, c3);
           E(cudaGetLastError());
           cudaGraph_t tmp;
           E(cudaStreamEndCapture(c3, &tmp));
         }
       }
+      if (g.variant == 2) launch_flush_x(g.va, ctx->x32.p, ctx->p32.p, ctx->p32b.p, g.ks, c2);
       if (g.df) launch_resid_sub_df(opL, ctx->x32.p, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(4), g.nb, ctx->sms, c2);
       else launch_resid_sub(opL, ctx->x32.p, ctx->u64.p, ctx->r64.p, g.rf, rs_at(4), g.nb, ctx->sms, c2);
       launch_graph_cond(gc, 1, hR, c2);
@@ -751,6 +879,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     return fail(ctx, BT_EINVAL, "bt_run: bad solver options");
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
+  ctx->last_kind = 0;
   const int Rs = re - rb;
   const int nb = pick_nb(ctx, rb, Rs);
   const int Rp = ((Rs + nb - 1) / nb) * nb;
@@ -807,7 +936,11 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     CK(ensure(ctx->r32, NE));
     CK(ensure(ctx->p32, NE));
     CK(ensure(ctx->q32, NE));
+    if (!learned && !col) CK(ensure(ctx->p32b, NE));
   }
+  CK(ensure(ctx->ks_pend, SY));
+  CK(ensure(ctx->ks_par, 1));
+  CK(ensure(ctx->d_sys_iter, 1));
   CK(ensure(ctx->ks_rho, 2 * (size_t)SY));
   CK(ensure(ctx->ks_alpha, 2 * (size_t)SY));
   CK(ensure(ctx->ks_beta, 2 * (size_t)SY));
@@ -886,7 +1019,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   VecArgs va{n, Rs, Rp, nb, sp, ctx->d_diag64.p, ctx->d_diag_md64.p, ctx->d_diag32.p, ctx->d_diag_md32.p};
   KrylovState ks{ctx->ks_rho.p, ctx->ks_alpha.p, ctx->ks_beta.p, ctx->ks_rr0.p, ctx->ks_rr.p, ctx->ks_tol2.p,
                  ctx->ks_iter.p, ctx->ks_active.p, ctx->n_active.p, ctx->ks_status.p, ctx->ks_rr_best.p,
-                 ctx->ks_it_best.p, o.max_iter, plain ? 0 : 30};
+                 ctx->ks_it_best.p, o.max_iter, plain ? 0 : 30, ctx->ks_par.p, ctx->ks_pend.p, ctx->d_sys_iter.p};
   RefineState rf{ctx->rf_r0n2.p, ctx->rf_rk2.p, ctx->rf_scale.p, ctx->rf_err.p, ctx->rf_active.p,
                  ctx->n_active.p + 1, o.tol_ref * o.tol_ref, 0.0, ctx->ks_status.p};
   const double feps = 1e-14 * ctx->wmax;
@@ -904,15 +1037,23 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     op.t_seg0 = ctx->t_seg0.p;
     op.pkt = ctx->pkt.p;
     op.mdt = ctx->mdt.p;
+    const bool allow_halo = !learned && !col;
+    if (allow_halo)
+      if (bt_status e = ensure_halo(ctx, nb, st)) return e;
     OpArgs opt = op;
     opt.coef = ctx->d_coef.p + G;  // step 1, L operator
-    if (bt_status e = autotune_spmm(ctx, opt, ks, rs_at(2), conj, nb, SY, Rs, G, &variant)) return e;
+    if (bt_status e = autotune_spmm(ctx, opt, va, ks, rs_at(2), rs_at(3), conj, nb, SY, Rs, G, allow_halo, &variant))
+      return e;
+    if (o.flags & BT_OPT_VARIANT_ROW) variant = 0;
+    if (o.flags & BT_OPT_VARIANT_TILED) variant = 1;
+    if ((o.flags & BT_OPT_VARIANT_HALO) && allow_halo && ctx->halo_ok) variant = 2;
   }
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
   ctx->st_spmm_ms = ctx->st_resid_ms = 0;
   ctx->ev_used = 0;
   CK(cudaMemsetAsync(ctx->rf_err.p, 0, SY * sizeof(double), st));
   CK(cudaMemsetAsync(ctx->ks_status.p, 0, SY * sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_sys_iter.p, 0, sizeof(unsigned long long), st));
   if (df) launch_fill_u_df(va, ctx->udf.p, st);
   else launch_fill_u(va, ctx->u64.p, st);
   CKL();
@@ -943,7 +1084,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       ctx->st_iters = ctx->st_spmm = gi;
       ctx->st_refine = gp;
       ctx->st_resid = N + gp;
-      L += 5 * (int64_t)N + 4 * gp + 4 * gi;
+      L += variant == 2 ? 5 * (int64_t)N + 6 * gp + 3 * gi : 5 * (int64_t)N + 4 * gp + 4 * gi;
     }
   }
   double last_fq = NAN;
@@ -987,6 +1128,9 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       if (plain) {
         launch_krylov_init_f64(op, va, ctx->r64.p, ctx->rf_active.p, ctx->x64.p, ctx->rk64.p, ctx->p64.p, ks,
                                o.tol_fp64, rs_at(1), conj, ctx->sms, st);
+      } else if (variant == 2) {
+        launch_krylov_init_z(op, va, df ? (const void*)ctx->rdf.p : (const void*)ctx->r64.p, df, ctx->rf_scale.p,
+                             ctx->rf_active.p, ctx->x32.p, ctx->r32.p, ks, o.tol_inner, rs_at(1), conj, st);
       } else if (df) {
         launch_krylov_init_f32_df(op, va, ctx->rdf.p, ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p,
                                   ctx->p32.p, ks, o.tol_inner, rs_at(1), conj, ctx->sms, st);
@@ -1016,6 +1160,13 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
           launch_krylov_update_f64(op, va, ctx->x64.p, ctx->rk64.p, ctx->p64.p, ctx->q64.p, ks, rs_at(3), conj,
                                    ctx->sms, st);
           launch_krylov_p_f64(op, va, ctx->rk64.p, ctx->p64.p, ks, ctx->sms, st);
+        } else if (variant == 2) {
+          timed(0, [&] {
+            launch_spmm_halo(op, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, ks,
+                             rs_at(2), conj, nb, st);
+          });
+          launch_krylov_update_z(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
+          L -= 1;  // two launches per iteration
         } else {
           timed(0, [&] { spmm_f32(variant, op, ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb, ctx->sms, st); });
           launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs_at(3), conj,
@@ -1044,6 +1195,10 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
         launch_finish_step(rf, ks, SY, st);
         L += 1;
       } else {
+        if (variant == 2) {
+          launch_flush_x(va, ctx->x32.p, ctx->p32.p, ctx->p32b.p, ks, st);
+          L += 2;
+        }
         timed(1, [&] {
           if (df) launch_resid_sub_df(op, ctx->x32.p, ctx->udf.p, ctx->rdf.p, rf, rs_at(4), nb, ctx->sms, st);
           else launch_resid_sub(op, ctx->x32.p, ctx->u64.p, ctx->r64.p, rf, rs_at(4), nb, ctx->sms, st);
@@ -1069,8 +1224,11 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   CK(cudaMemcpyAsync(err.data(), ctx->rf_err.p, SY * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(stat.data(), ctx->ks_status.p, SY * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ref_left.data(), ctx->rf_active.p, SY * sizeof(int), cudaMemcpyDeviceToHost, st));
+  unsigned long long sys_iter = 0;
+  CK(cudaMemcpyAsync(&sys_iter, ctx->d_sys_iter.p, sizeof(sys_iter), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (prof) ev_harvest(ctx);
+  ctx->st_sys_iters = (int64_t)sys_iter;
   bt_status ret = BT_OK;
   for (int s = 0; s < SY; ++s) {
     ctx->S[2 * (rb + s)] = S[2 * s];
@@ -1081,6 +1239,11 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     ctx->status[rb + s] = stt;
     if (stt != BT_OK && ret == BT_OK) ret = stt;
   }
+  ctx->last_kind = df ? 2 : 1;
+  ctx->last_Rp = Rp;
+  ctx->last_nb = nb;
+  ctx->last_rb = rb;
+  ctx->last_Rs = Rs;
   if (ret != BT_OK) ctx->err = "bt_run: some right-hand sides did not converge (see status)";
   return ret;
 }
@@ -1119,19 +1282,49 @@ extern "C" bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_es
   return BT_OK;
 }
 
-extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_row, double* ms_tiled) {
+extern "C" bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_rows) {
+  if (!ctx) return BT_EINVAL;
+  if (!need_gpu(ctx)) return fail(ctx, BT_ENODEV, "bt_get_state: host-only context");
+  if (ctx->last_kind == 0) return fail(ctx, BT_ESTATE, "bt_get_state: no state (run first)");
+  const int G = ctx->G, R = ctx->R;
+  int g = 0, r = 0;
+  if (G > 1) {
+    if (system < 0 || system >= G * R) return fail(ctx, BT_EINVAL, "bt_get_state: system out of range");
+    g = system / R;
+    r = system % R;
+  } else {
+    if (system < ctx->last_rb || system >= ctx->last_rb + ctx->last_Rs)
+      return fail(ctx, BT_EINVAL, "bt_get_state: system not in the last run's RHS range");
+    r = system - ctx->last_rb;
+  }
+  const int64_t row0 = ctx->seg_row0[g], rows = ctx->seg_row0[g + 1] - row0;
+  if (n_rows) *n_rows = rows;
+  if (!u_re_im) return BT_OK;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  CK(ensure(ctx->d_state, (size_t)rows));
+  const void* u = ctx->last_kind == 2 ? (const void*)ctx->udf.p : (const void*)ctx->u64.p;
+  launch_extract_state(u, ctx->last_kind == 2, row0, rows, ctx->last_Rp, col_of_sys(r, ctx->last_nb),
+                       ctx->d_state.p, ctx->sms, st);
+  CKL();
+  CK(cudaMemcpyAsync(u_re_im, ctx->d_state.p, (size_t)rows * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return BT_OK;
+}
+
+extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter) {
   if (!ctx) return BT_EINVAL;
   if (ctx->tuned.empty()) return BT_ESTATE;
   const auto& t = ctx->tuned.back();
   if (variant) *variant = t.variant;
-  if (ms_row) *ms_row = t.ms[0];
-  if (ms_tiled) *ms_tiled = t.ms[1];
+  if (ms_iter)
+    for (int k = 0; k < 3; ++k) ms_iter[k] = t.ms[k];
   return BT_OK;
 }
 
 extern "C" bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters, int64_t* refine_passes,
                                   int64_t* spmm_launches, double* spmm_ms, double* resid_ms,
-                                  int64_t* resid_launches, int64_t* kernel_launches) {
+                                  int64_t* resid_launches, int64_t* kernel_launches, int64_t* sys_iters) {
   if (!ctx) return BT_EINVAL;
   if (steps) *steps = ctx->st_steps;
   if (krylov_iters) *krylov_iters = ctx->st_iters;
@@ -1141,5 +1334,6 @@ extern "C" bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* kr
   if (resid_ms) *resid_ms = ctx->st_resid_ms;
   if (resid_launches) *resid_launches = ctx->st_resid;
   if (kernel_launches) *kernel_launches = ctx->st_launches;
+  if (sys_iters) *sys_iters = ctx->st_sys_iters;
   return BT_OK;
 }

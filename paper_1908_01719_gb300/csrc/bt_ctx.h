@@ -64,10 +64,21 @@ struct bt_ctx {
   bt::DBuf<float> mdt;
   std::vector<int64_t> tiles_for;   // seg_row0 the tiles were built for
   int64_t planes_version = 0, tiles_planes_version = -1;
+  // halo tiles of the shared-memory Krylov apply (one segmentation, one umax)
+  bt::DBuf<int32_t> h_r0, h_rows, h_rowe, h_u0, h_seg0, h_slot;
+  bt::DBuf<uint16_t> h_rowl, h_lidx;
+  bt::DBuf<uint32_t> h_ucol;
+  bt::DBuf<float4> h_pkt;
+  bt::DBuf<float> h_mdt;
+  std::vector<int64_t> halo_for;
+  int halo_umax = 0;
+  bool halo_ok = false;             // every row fits a tile of umax halo rows
+  int64_t halo_planes_version = -1;
+  bool halo_attr = false;
   struct Tuned {
     int R, nb, G;
-    int variant;   // 0 row kernel, 1 tiled kernel
-    double ms[2];
+    int variant;   // 0 row kernel, 1 tiled kernel, 2 halo iteration
+    double ms[3];  // one Krylov iteration of each variant (ms; 0 = not timed)
   };
   std::vector<Tuned> tuned;
 
@@ -80,20 +91,26 @@ struct bt_ctx {
   bt::DBuf<bt::OpCoef> d_coef;
   bt::DBuf<double2> u64, r64, x64, rk64, p64, q64;
   bt::DBuf<float4> udf, rdf;
-  bt::DBuf<float2> x32, r32, p32, q32;
+  bt::DBuf<float2> x32, r32, p32, q32, p32b;  // p32b: second p buffer of the halo iteration
   bt::DBuf<double> ks_rho, ks_alpha, ks_beta, ks_rr0, ks_rr, ks_tol2;
   bt::DBuf<int> ks_iter, ks_active, ks_status, n_active, ks_it_best;
   bt::DBuf<double> ks_rr_best;
+  bt::DBuf<int> ks_pend, ks_par;
+  bt::DBuf<unsigned long long> d_sys_iter;
   bt::DBuf<double> rf_r0n2, rf_rk2, rf_scale, rf_err;
   bt::DBuf<int> rf_active;
   bt::DBuf<double> red_part, d_S;
   bt::DBuf<unsigned int> red_counter;
+  // u^N left by the last run: kind 0 none, 1 FP64 (u64), 2 double-float (udf);
+  // its padded width, RHS per lane and RHS range
+  int last_kind = 0, last_Rp = 0, last_nb = 1, last_rb = 0, last_Rs = 0;
+  bt::DBuf<double2> d_state;
   int* h_flags = nullptr;  // pinned: [0] Krylov n_active, [1] refinement n_active
 
   // results
   std::vector<double> S, err_est;
   std::vector<int> status;
-  int64_t st_steps = 0, st_iters = 0, st_refine = 0, st_spmm = 0, st_resid = 0, st_launches = 0;
+  int64_t st_steps = 0, st_iters = 0, st_refine = 0, st_spmm = 0, st_resid = 0, st_launches = 0, st_sys_iters = 0;
   double st_spmm_ms = 0, st_resid_ms = 0;
   std::vector<bt::EventPair> ev_pool;
   size_t ev_used = 0;

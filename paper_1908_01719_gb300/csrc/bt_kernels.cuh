@@ -72,6 +72,10 @@ struct KrylovState {
   int* it_best;      // iteration at which it was seen
   int max_iter;
   int stall;         // > 0: stop a solve after `stall` iterations without a new best
+  // halo-tile iteration only (null otherwise)
+  int* par;          // device: which of the two p buffers holds the current p
+  int* pend;         // per system: x += alpha p of the last apply still to do
+  unsigned long long* sys_iter;  // device: active systems summed over SpMM launches (or null)
 };
 
 // Per-system refinement scalars.
@@ -132,6 +136,21 @@ struct OpArgs {
   const int32_t* t_seg0;   // [G + 1] first tile of each segment
   const float4* pkt;       // pk32 in tile-entry order
   const float* mdt;        // md32 in tile-entry order
+};
+
+// Halo tiles of the shared-memory Krylov apply (HaloTiles on the device).
+struct HaloArgs {
+  const int32_t* t_r0;      // [ntiles + 1] offsets into rows
+  const int32_t* rows;      // owned rows, tile by tile
+  const int32_t* rowe;      // [n + 1] first entry of each owned row (tile order)
+  const uint16_t* rowl;     // local halo index of each owned row
+  const int32_t* u0;        // [ntiles + 1] offsets into ucol
+  const uint32_t* ucol;     // halo rows, bit 31 = owned
+  const uint16_t* lidx;     // [nnz] local column index of each entry
+  const float4* pkt;        // [nnz] {A0, d0, d1, d2} in tile-entry order
+  const float* mdt;         // [nnz] MD in tile-entry order
+  const int32_t* seg_tile0; // [G + 1]
+  int umax;
 };
 
 struct VecArgs {
@@ -224,6 +243,24 @@ void launch_precond_dot(const VecArgs& va, const float2* r, const float2* z, con
 void launch_gram(const OpArgs& op, const VecArgs& va, const float2* r, const float2* V, size_t vstride,
                  double* part, unsigned int* counter, double* out, int sms, cudaStream_t st);
 
+// Halo-tile Jacobi iteration (FP32): the Krylov state keeps z = D^-1 r
+// instead of r, and p in two buffers.  One iteration is
+//   apply:  p = z + beta p_prev (halo rows staged in shared memory), deferred
+//           x += alpha_prev p_prev, q = L p, alpha = rho / <p, q>
+//   update: r = D z - alpha q, z = D^-1 r, rho' = <r, z>, |r|^2, beta
+// and flush_x applies the last deferred x update after the loop.
+void halo_prepare();
+size_t halo_smem_bytes(int nb, int umax);
+void launch_spmm_halo(const OpArgs& op, const HaloArgs& h, const float2* z, float2* pA, float2* pB, float2* x,
+                      float2* q, const KrylovState& ks, RedScratch rs, int conj, int nb, cudaStream_t st);
+void launch_krylov_init_z(const OpArgs& op, const VecArgs& va, const void* rres, int df, const double* scale,
+                          const int* ref_active, float2* x, float2* z, const KrylovState& ks, double tol,
+                          RedScratch rs, int conj, cudaStream_t st);
+void launch_krylov_update_z(const OpArgs& op, const VecArgs& va, float2* z, const float2* q, const KrylovState& ks,
+                            RedScratch rs, int conj, cudaStream_t st);
+void launch_flush_x(const VecArgs& va, float2* x, const float2* pA, const float2* pB, const KrylovState& ks,
+                    cudaStream_t st);
+
 void launch_krylov_init_f64(const OpArgs& op, const VecArgs& va, const double2* r64, const int* ref_active,
                             double2* x, double2* r, double2* p, const KrylovState& ks, double tol, RedScratch rs,
                             int conj, int sms, cudaStream_t st);
@@ -236,6 +273,8 @@ void launch_krylov_p_f64(const OpArgs& op, const VecArgs& va, const double2* r, 
 void launch_axpy_u(const VecArgs& va, const double2* d, double2* u, const KrylovState& ks,
                    const RefineState& rf, int sms, cudaStream_t st);
 void launch_fill_u(const VecArgs& va, double2* u, cudaStream_t st);
+void launch_extract_state(const void* u, int df, int64_t row0, int64_t rows, int Rp, int col, double2* out,
+                          int sms, cudaStream_t st);
 void launch_signal(const VecArgs& va, const double* w, const double2* u, double* S, RedScratch rs, int sms,
                    cudaStream_t st);
 void launch_set_int(int* p, int v, int n, cudaStream_t st);
@@ -446,6 +485,62 @@ __device__ __forceinline__ void krylov_alpha(const KrylovState& ks, int s, doubl
   }
   ks.alpha[2 * s] = (rho.x * pq.x + rho.y * pq.y) / den;
   ks.alpha[2 * s + 1] = (rho.y * pq.x - rho.x * pq.y) / den;
+}
+
+// End of one Krylov update for system s (last block): o[0] = rho' (complex),
+// o[1].x = |r|^2.  Applies the convergence, stagnation and iteration-cap tests
+// and forms beta = rho' / rho; returns whether the system stays active.
+__device__ __forceinline__ bool krylov_step_finish(const KrylovState& ks, int s, const double2 (&o)[2],
+                                                   int* pmode) {
+  ks.rr[s] = o[1].x;
+  const int it = ++ks.iter[s];
+  if (!isfinite(o[1].x) || !isfinite(o[0].x) || !isfinite(o[0].y)) {
+    ks.active[s] = 0;
+    ks.status[s] = BT_ENAN;
+    return false;
+  }
+  if (o[1].x <= ks.tol2[s]) {
+    ks.active[s] = 0;
+    return false;
+  }
+  if (o[1].x < ks.rr_best[s]) {
+    ks.rr_best[s] = o[1].x;
+    ks.it_best[s] = it;
+  } else if (ks.stall > 0 && it - ks.it_best[s] >= ks.stall) {
+    // the FP32 recurrence has stagnated: hand back to the refinement loop
+    ks.active[s] = 0;
+    if (pmode) pmode[s] = 0;
+    return false;
+  }
+  if (it >= ks.max_iter) {
+    ks.active[s] = 0;
+    ks.status[s] = BT_ENOCONV;
+    return false;
+  }
+  if (pmode && pmode[s]) {
+    // polynomial-preconditioned system: rho and beta come from z = P_c r
+    // (k_precond_dot); fall back to Jacobi when it is not converged by
+    // max_iter / 2
+    if (it >= ks.max_iter / 2) {
+      ks.active[s] = 0;
+      pmode[s] = 0;
+      return false;
+    }
+    return true;
+  }
+  // beta = rho' / rho (complex)
+  const double2 rho = make_double2(ks.rho[2 * s], ks.rho[2 * s + 1]);
+  const double den = rho.x * rho.x + rho.y * rho.y;
+  if (!(den > 0)) {
+    ks.active[s] = 0;
+    ks.status[s] = BT_ENOCONV;
+    return false;
+  }
+  ks.beta[2 * s] = (o[0].x * rho.x + o[0].y * rho.y) / den;
+  ks.beta[2 * s + 1] = (o[0].y * rho.x - o[0].x * rho.y) / den;
+  ks.rho[2 * s] = o[0].x;
+  ks.rho[2 * s + 1] = o[0].y;
+  return true;
 }
 
 // Refinement bookkeeping of system s after a residual launch (last block).

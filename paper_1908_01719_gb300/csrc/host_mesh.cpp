@@ -382,6 +382,101 @@ void build_row_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, Ro
   t.s0.push_back((int32_t)t.slot.size());
 }
 
+// 16-bit spread for a 48-bit Morton code
+static uint64_t spread3(uint64_t v) {
+  v &= 0xFFFFull;
+  v = (v | (v << 16)) & 0x0000FF0000FFull;
+  v = (v | (v << 8)) & 0x00F00F00F00Full;
+  v = (v | (v << 4)) & 0x0C30C30C30C3ull;
+  v = (v | (v << 2)) & 0x249249249249ull;
+  return v;
+}
+
+void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, int umax, int tmax, HaloTiles& t) {
+  t = HaloTiles();
+  t.umax = umax;
+  const int G = (int)seg_row0.size() - 1;
+  const int64_t n = m.n_dof;
+  t.rows.reserve(n);
+  t.rowe.reserve(n + 1);
+  t.rowl.reserve(n);
+  t.lidx.reserve(m.nnz);
+  t.slot.reserve(m.nnz);
+  std::vector<int32_t> mark(n, -1), lpos(n, 0);
+  std::vector<std::pair<uint64_t, int32_t>> order;
+  std::vector<int32_t> cur, uc;
+  int32_t tid = 0;
+  for (int g = 0; g < G; ++g) {
+    t.seg_tile0.push_back((int32_t)t.r0.size());
+    const int64_t a = seg_row0[g], b = seg_row0[g + 1];
+    if (a == b) continue;
+    // Morton order of the rows' node coordinates over the segment's bounding box
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t r = a; r < b; ++r)
+      for (int k = 0; k < 3; ++k) {
+        const double x = m.xyz[3 * (size_t)m.dof_node[r] + k];
+        lo[k] = std::min(lo[k], x);
+        hi[k] = std::max(hi[k], x);
+      }
+    order.clear();
+    for (int64_t r = a; r < b; ++r) {
+      uint64_t code = 0;
+      for (int k = 0; k < 3; ++k) {
+        const double ext = hi[k] - lo[k];
+        const double f = ext > 0 ? (m.xyz[3 * (size_t)m.dof_node[r] + k] - lo[k]) / ext : 0.0;
+        code |= spread3((uint64_t)std::min(65535.0, std::floor(f * 65535.0 + 0.5))) << k;
+      }
+      order.emplace_back(code, (int32_t)r);
+    }
+    std::sort(order.begin(), order.end());
+    // greedy tiles along the curve: at most tmax rows and umax distinct columns
+    size_t i = 0;
+    while (i < order.size()) {
+      cur.clear();
+      uc.clear();
+      for (; i < order.size() && (int)cur.size() < tmax; ++i) {
+        const int32_t r = order[i].second;
+        int fresh = 0;
+        for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k) fresh += mark[m.col[k]] != tid;
+        if ((int)uc.size() + fresh > umax) {
+          if (cur.empty()) {
+            // a single row wider than umax cannot be staged
+            t.too_wide = true;
+            return;
+          }
+          break;
+        }
+        for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k)
+          if (mark[m.col[k]] != tid) {
+            mark[m.col[k]] = tid;
+            uc.push_back(m.col[k]);
+          }
+        cur.push_back(r);
+      }
+      std::sort(uc.begin(), uc.end());
+      for (size_t u = 0; u < uc.size(); ++u) lpos[uc[u]] = (int32_t)u;
+      t.r0.push_back((int32_t)t.rows.size());
+      t.u0.push_back((int32_t)t.ucol.size());
+      for (int32_t c : uc) t.ucol.push_back((uint32_t)c);
+      for (int32_t r : cur) {
+        t.ucol[t.u0.back() + lpos[r]] |= 0x80000000u;  // owned by this tile
+        t.rows.push_back(r);
+        t.rowe.push_back((int32_t)t.lidx.size());
+        t.rowl.push_back((uint16_t)lpos[r]);
+        for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k) {
+          t.lidx.push_back((uint16_t)lpos[m.col[k]]);
+          t.slot.push_back((int32_t)k);
+        }
+      }
+      ++tid;
+    }
+  }
+  t.seg_tile0.push_back((int32_t)t.r0.size());
+  t.r0.push_back((int32_t)t.rows.size());
+  t.u0.push_back((int32_t)t.ucol.size());
+  t.rowe.push_back((int32_t)t.lidx.size());
+}
+
 int build_host_mesh(HostMesh& m, std::string& msg) {
   int st = validate(m, msg);
   if (st) return st;

@@ -6,6 +6,7 @@
 // formed on the fly.  Inner products: FP32 products summed over at most 32
 // rows per thread, all further accumulation in FP64, and the block partials
 // reduced by the last block in a fixed order (deterministic).
+#include <algorithm>
 #include "bt_kernels.cuh"
 
 namespace bt {
@@ -294,56 +295,7 @@ __global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2
     if (!ks.active[s]) continue;
     double2 o[2];
     sum_part<2>(rs.part, va.sp, va.R, va.Rp, s, o);
-    ks.rr[s] = o[1].x;
-    int it = ++ks.iter[s];
-    if (!isfinite(o[1].x) || !isfinite(o[0].x) || !isfinite(o[0].y)) {
-      ks.active[s] = 0;
-      ks.status[s] = BT_ENAN;
-      continue;
-    }
-    if (o[1].x <= ks.tol2[s]) {
-      ks.active[s] = 0;
-      continue;
-    }
-    if (o[1].x < ks.rr_best[s]) {
-      ks.rr_best[s] = o[1].x;
-      ks.it_best[s] = it;
-    } else if (ks.stall > 0 && it - ks.it_best[s] >= ks.stall) {
-      // the FP32 recurrence has stagnated: hand back to the refinement loop
-      ks.active[s] = 0;
-      if (pmode) pmode[s] = 0;
-      continue;
-    }
-    if (it >= ks.max_iter) {
-      ks.active[s] = 0;
-      ks.status[s] = BT_ENOCONV;
-      continue;
-    }
-    if (pmode && pmode[s]) {
-      // polynomial-preconditioned system: rho and beta come from z = P_c r
-      // (k_precond_dot); fall back to Jacobi when it is not converged by
-      // max_iter / 2
-      if (it >= ks.max_iter / 2) {
-        ks.active[s] = 0;
-        pmode[s] = 0;
-        continue;
-      }
-      atomicAdd(&s_cnt, 1);
-      continue;
-    }
-    // beta = rho' / rho (complex)
-    double2 rho = make_double2(ks.rho[2 * s], ks.rho[2 * s + 1]);
-    double den = rho.x * rho.x + rho.y * rho.y;
-    if (!(den > 0)) {
-      ks.active[s] = 0;
-      ks.status[s] = BT_ENOCONV;
-      continue;
-    }
-    ks.beta[2 * s] = (o[0].x * rho.x + o[0].y * rho.y) / den;
-    ks.beta[2 * s + 1] = (o[0].y * rho.x - o[0].x * rho.y) / den;
-    ks.rho[2 * s] = o[0].x;
-    ks.rho[2 * s + 1] = o[0].y;
-    atomicAdd(&s_cnt, 1);
+    if (krylov_step_finish(ks, s, o, pmode)) atomicAdd(&s_cnt, 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) *ks.n_active = s_cnt;
@@ -556,6 +508,23 @@ void launch_signal_df(const VecArgs& va, const double* w, const float4* u, doubl
 }  // namespace bt
 
 namespace bt {
+// one column of the lane-interleaved state, rows [row0, row0 + rows), as FP64
+template <class TU>
+__global__ void k_extract_state(const TU* __restrict__ u, int64_t row0, int64_t rows, int Rp, int col,
+                                double2* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = load_res(u, (size_t)(row0 + i) * Rp + col);
+}
+void launch_extract_state(const void* u, int df, int64_t row0, int64_t rows, int Rp, int col, double2* out,
+                          int sms, cudaStream_t st) {
+  const int64_t want = (rows + 255) / 256;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+  if (df) k_extract_state<float4><<<g, 256, 0, st>>>((const float4*)u, row0, rows, Rp, col, out);
+  else k_extract_state<double2><<<g, 256, 0, st>>>((const double2*)u, row0, rows, Rp, col, out);
+}
+}  // namespace bt
+
+namespace bt {
 // mixed mode: RHS still refining after the last pass of a step did not reach tol_ref
 __global__ void k_mark_ref_left(RefineState rf, KrylovState ks, int R) {
   for (int s = threadIdx.x; s < R; s += blockDim.x)
@@ -574,5 +543,238 @@ __global__ void k_seg_active(int* act, int R, int G, int step, const int* segN) 
 }
 void launch_seg_active(int* act, int R, int G, int step, const int* segN, cudaStream_t st) {
   k_seg_active<<<(G * R + 255) / 256, 256, 0, st>>>(act, R, G, step, segN);
+}
+}  // namespace bt
+
+// ---------------------------------------------------------------- halo-tile iteration (FP32, Jacobi)
+namespace bt {
+// complex helpers: D z, r / D
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cdivf(float2 r, float2 d) {
+  const float den = 1.0f / (d.x * d.x + d.y * d.y);
+  return make_float2((r.x * d.x + r.y * d.y) * den, (r.y * d.x - r.x * d.y) * den);
+}
+
+// z = D^-1 (r_res / scale), x = 0; rho = <r, z>, |r|^2; beta = 0, no pending
+// x update, p buffer parity 0.  The p buffers are not touched: the first
+// apply takes p = z because beta = 0.
+template <class TR, bool CONJ>
+__global__ void __launch_bounds__(256) k_krylov_init_z(OpArgs op, VecArgs va, const TR* __restrict__ rres,
+                                                       const double* __restrict__ scale,
+                                                       const int* __restrict__ ref_active, float2* __restrict__ x,
+                                                       float2* __restrict__ z, KrylovState ks, double tol,
+                                                       RedScratch rs) {
+  ElemMap em(va.Rp);
+  const int t = threadIdx.x;
+  const bool live = t < em.rpp * em.RS;
+  const int rr = t % em.RS, ro = t / em.RS;
+  double2 acc[EM_NK][2];
+  for (int k = 0; k < EM_NK; ++k) acc[k][0] = acc[k][1] = make_double2(0, 0);
+  BT_SEG_ROWS(va);
+  if (live) {
+    for (int k = 0; k < em.NK; ++k) {
+      const int col = rr + 256 * k;
+      if (col >= va.Rp) continue;
+      const int rl = sys_of_col(col, va.nb);
+      if (rl >= va.R) continue;
+      const int s = sg_ * va.R + rl;
+      const bool act = ref_active[s] != 0;
+      const SysCoef sc = sys_coef(op, s);
+      const double inv = (scale && act && scale[s] > 0) ? 1.0 / scale[s] : 1.0;
+      float2 ar = {0, 0}, an = {0, 0};
+      int cnt = 0;
+      for (int64_t i = rb + ro; i < re; i += em.rpp) {
+        const size_t e = (size_t)i * va.Rp + col;
+        float2 rv = {0, 0}, zv = {0, 0};
+        if (act) {
+          const double2 v = load_res(rres, e);
+          rv = make_float2((float)(v.x * inv), (float)(v.y * inv));
+          zv = cdivf(rv, diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz));
+        }
+        z[e] = zv;
+        x[e] = make_float2(0.f, 0.f);
+        float2 rc = rv;
+        if constexpr (CONJ) rc.y = -rc.y;
+        ar.x += rc.x * zv.x - rc.y * zv.y;
+        ar.y += rc.x * zv.y + rc.y * zv.x;
+        an.x += rv.x * rv.x + rv.y * rv.y;
+        if (++cnt == 32) {
+          cnt = 0;
+          acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
+          ar = float2{0, 0}; an = float2{0, 0};
+        }
+      }
+      acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
+    }
+  }
+  if (!elem_block_reduce<2>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
+  __shared__ int s_cnt;
+  if (threadIdx.x == 0) {
+    s_cnt = 0;
+    *ks.par = 0;
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+    double2 o[2];
+    sum_part<2>(rs.part, va.sp, va.R, va.Rp, s, o);
+    ks.rho[2 * s] = o[0].x;
+    ks.rho[2 * s + 1] = o[0].y;
+    ks.beta[2 * s] = 0;
+    ks.beta[2 * s + 1] = 0;
+    ks.pend[s] = 0;
+    ks.rr0[s] = o[1].x;
+    ks.rr[s] = o[1].x;
+    ks.tol2[s] = tol * tol * o[1].x;
+    ks.iter[s] = 0;
+    ks.rr_best[s] = o[1].x;
+    ks.it_best[s] = 0;
+    int a = ref_active[s] && o[1].x > 0;
+    if (ref_active[s] && !isfinite(o[1].x)) {
+      a = 0;
+      ks.status[s] = BT_ENAN;
+    }
+    ks.active[s] = a;
+    if (a) atomicAdd(&s_cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ks.n_active = s_cnt;
+}
+
+// r = D z - alpha q; z = D^-1 r; rho' = <r, z>, |r|^2; the last block applies
+// the tests and forms beta (krylov_step_finish).
+template <bool CONJ>
+__global__ void __launch_bounds__(256) k_krylov_update_z(OpArgs op, VecArgs va, float2* __restrict__ z,
+                                                         const float2* __restrict__ q, KrylovState ks,
+                                                         RedScratch rs) {
+  if (*ks.n_active == 0) return;
+  ElemMap em(va.Rp);
+  const int t = threadIdx.x;
+  const bool live = t < em.rpp * em.RS;
+  const int rr = t % em.RS, ro = t / em.RS;
+  double2 acc[EM_NK][2];
+  for (int k = 0; k < EM_NK; ++k) acc[k][0] = acc[k][1] = make_double2(0, 0);
+  BT_SEG_ROWS(va);
+  if (live) {
+    for (int k = 0; k < em.NK; ++k) {
+      const int col = rr + 256 * k;
+      if (col >= va.Rp) continue;
+      const int rl = sys_of_col(col, va.nb);
+      if (rl >= va.R) continue;
+      const int s = sg_ * va.R + rl;
+      if (!ks.active[s]) continue;
+      const SysCoef sc = sys_coef(op, s);
+      const float2 al = make_float2((float)ks.alpha[2 * s], (float)ks.alpha[2 * s + 1]);
+      const float fb = (float)sc.b, fc = (float)sc.c, fx = (float)sc.qx, fy = (float)sc.qy, fz = (float)sc.qz;
+      float2 ar = {0, 0}, an = {0, 0};
+      int cnt = 0;
+      for (int64_t i0 = rb + ro; i0 < re; i0 += 4 * em.rpp) {
+        float2 zv[4], qv[4], d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + (int64_t)u * em.rpp;
+          if (i < re) {
+            const size_t e = (size_t)i * va.Rp + col;
+            zv[u] = z[e];
+            qv[u] = __ldg(q + e);
+            d[u] = diag_f32(va, op, i, fb, fc, fx, fy, fz);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + (int64_t)u * em.rpp;
+          if (i >= re) break;
+          float2 r = cmulf(d[u], zv[u]);
+          const float2 aq = cmulf(al, qv[u]);
+          r.x -= aq.x;
+          r.y -= aq.y;
+          const float2 zn = cdivf(r, d[u]);
+          z[(size_t)i * va.Rp + col] = zn;
+          float2 rc = r;
+          if constexpr (CONJ) rc.y = -rc.y;
+          ar.x += rc.x * zn.x - rc.y * zn.y;
+          ar.y += rc.x * zn.y + rc.y * zn.x;
+          an.x += r.x * r.x + r.y * r.y;
+        }
+        if (++cnt == 8) {
+          cnt = 0;
+          acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
+          ar = float2{0, 0}; an = float2{0, 0};
+        }
+      }
+      acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
+    }
+  }
+  if (!elem_block_reduce<2>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
+  __shared__ int s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+    if (!ks.active[s]) continue;
+    double2 o[2];
+    sum_part<2>(rs.part, va.sp, va.R, va.Rp, s, o);
+    if (krylov_step_finish(ks, s, o, nullptr)) atomicAdd(&s_cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ks.n_active = s_cnt;
+}
+
+// x += alpha p for systems whose last apply is still pending (after the loop);
+// p is the buffer the last apply wrote (the current parity's source).
+__global__ void __launch_bounds__(256) k_flush_x(VecArgs va, float2* __restrict__ x, const float2* __restrict__ pA,
+                                                 const float2* __restrict__ pB, KrylovState ks) {
+  ElemMap em(va.Rp);
+  const int t = threadIdx.x;
+  if (t >= em.rpp * em.RS) return;
+  const int rr = t % em.RS, ro = t / em.RS;
+  const float2* __restrict__ p = *ks.par ? pB : pA;
+  BT_SEG_ROWS(va);
+  for (int k = 0; k < em.NK; ++k) {
+    const int col = rr + 256 * k;
+    if (col >= va.Rp) continue;
+    const int rl = sys_of_col(col, va.nb);
+    if (rl >= va.R) continue;
+    const int s = sg_ * va.R + rl;
+    if (!ks.pend[s]) continue;
+    const float2 al = make_float2((float)ks.alpha[2 * s], (float)ks.alpha[2 * s + 1]);
+    for (int64_t i = rb + ro; i < re; i += em.rpp) {
+      const size_t e = (size_t)i * va.Rp + col;
+      const float2 pv = __ldg(p + e);
+      float2 xv = x[e];
+      xv.x += al.x * pv.x - al.y * pv.y;
+      xv.y += al.x * pv.y + al.y * pv.x;
+      x[e] = xv;
+    }
+  }
+}
+// clears the pending flags once every block has flushed (separate launch)
+__global__ void k_clear_pend(KrylovState ks, int n) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) ks.pend[s] = 0;
+}
+
+void launch_krylov_init_z(const OpArgs& op, const VecArgs& va, const void* rres, int df, const double* scale,
+                          const int* ref_active, float2* x, float2* z, const KrylovState& ks, double tol,
+                          RedScratch rs, int conj, cudaStream_t st) {
+  const int g = elem_grid(va);
+  if (df) {
+    if (conj) k_krylov_init_z<float4, true><<<g, 256, 0, st>>>(op, va, (const float4*)rres, scale, ref_active, x, z, ks, tol, rs);
+    else k_krylov_init_z<float4, false><<<g, 256, 0, st>>>(op, va, (const float4*)rres, scale, ref_active, x, z, ks, tol, rs);
+  } else {
+    if (conj) k_krylov_init_z<double2, true><<<g, 256, 0, st>>>(op, va, (const double2*)rres, scale, ref_active, x, z, ks, tol, rs);
+    else k_krylov_init_z<double2, false><<<g, 256, 0, st>>>(op, va, (const double2*)rres, scale, ref_active, x, z, ks, tol, rs);
+  }
+}
+void launch_krylov_update_z(const OpArgs& op, const VecArgs& va, float2* z, const float2* q, const KrylovState& ks,
+                            RedScratch rs, int conj, cudaStream_t st) {
+  const int g = elem_grid(va);
+  if (conj) k_krylov_update_z<true><<<g, 256, 0, st>>>(op, va, z, q, ks, rs);
+  else k_krylov_update_z<false><<<g, 256, 0, st>>>(op, va, z, q, ks, rs);
+}
+void launch_flush_x(const VecArgs& va, float2* x, const float2* pA, const float2* pB, const KrylovState& ks,
+                    cudaStream_t st) {
+  k_flush_x<<<elem_grid(va), 256, 0, st>>>(va, x, pA, pB, ks);
+  const int n = va.sp.G * va.R;
+  k_clear_pend<<<(n + 255) / 256, 256, 0, st>>>(ks, n);
 }
 }  // namespace bt

@@ -140,6 +140,8 @@ __global__ void __launch_bounds__(256) k_spmm_krylov(OpArgs op, const T2* __rest
   }
   block_partials<NB>(acc, on ? r0 : op.Rp, op.Rp, rs.part);
   if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
+  if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
+  __syncthreads();
   reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
 }
 
@@ -281,6 +283,8 @@ __global__ void __launch_bounds__(256) k_spmm_tiled(OpArgs op, const float2* __r
   }
   block_partials<NB>(acc, on ? r0 : op.Rp, op.Rp, rs.part);
   if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
+  if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
+  __syncthreads();
   reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
 }
 

@@ -37,7 +37,8 @@ def _small_union():
 def test_small_union_matches_oracle_per_geometry(sim_cls, bt, mode):
     parts = _small_union()
     u = geom.union(parts)
-    ref = np.concatenate([oracle.run(p) for p in parts])
+    runs = [oracle.run(p, return_field=True) for p in parts]
+    ref = np.concatenate([r[0] for r in runs])
     sim = sim_cls(u)
     try:
         m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
@@ -45,6 +46,12 @@ def test_small_union_matches_oracle_per_geometry(sim_cls, bt, mode):
         assert len(S) == 3 * 2 and np.all(stat == 0)
         tol = 1e-10 if mode == "plain" else 1e-6
         assert np.max(np.abs(S - ref) / np.abs(ref)) < tol, (S, ref)
+        # each segment's field at its own echo time, dof by dof
+        for g, (_, U) in enumerate(runs):
+            for r in range(2):
+                ug = bt.bt_get_state(sim.ctx, g * 2 + r)
+                assert ug.shape == U[r].shape
+                assert np.max(np.abs(ug - U[r])) / np.abs(U[r]).max() < tol, (g, r)
     finally:
         sim.close()
 

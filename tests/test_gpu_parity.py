@@ -127,6 +127,88 @@ def test_mixed_matches_oracle(sim_cls, bt, live_ref, name, resid):
         sim.close()
 
 
+@pytest.fixture(scope="module")
+def live_field():
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            p = CASES[name]()
+            cache[name] = (p,) + oracle.run(p, return_field=True)
+        return cache[name]
+    return get
+
+
+@pytest.mark.parametrize("name", ["cfg1_n8", "cfg2_n8_dirs", "cfg3_n8", "cfg4_n10"])
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_field_matches_oracle_elementwise(sim_cls, bt, live_field, name, mode):
+    """u^N at TE, every dof of every RHS, against the oracle's field (the two
+    number dofs the same way: sorted (master node, compartment) pairs).  The
+    bound is on |u - U| per entry relative to max |U| of that RHS."""
+    p, ref, U = live_field(name)
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S, err, stat, st = sim.run(m)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        for r in range(p.n_rhs):
+            u = bt.bt_get_state(sim.ctx, r)
+            assert u.shape == U[r].shape
+            e = np.abs(u - U[r]) / np.abs(U[r]).max()
+            assert e.max() < tol, (r, e.max(), int(e.argmax()))
+        with pytest.raises(bt.BtError):
+            bt.bt_get_state(sim.ctx, p.n_rhs)
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("name", ["cfg1_n8", "cfg2_n8_dirs", "cfg3_n8", "cfg4_n10"])
+@pytest.mark.parametrize("variant", ["row", "tiled", "halo"])
+@pytest.mark.parametrize("loop", ["graph", "host"])
+def test_krylov_variants_match_oracle(sim_cls, bt, live_field, name, variant, loop):
+    """Each inner-Krylov variant (row SpMM, 4-row register-reuse SpMM,
+    halo-staged apply with the fused direction and solution updates), driven by
+    the captured step graph or by the host loop: signals and fields against
+    the oracle at the mixed-mode bound."""
+    p, ref, U = live_field(name)
+    flags = {"row": bt.BT_OPT_VARIANT_ROW, "tiled": bt.BT_OPT_VARIANT_TILED,
+             "halo": bt.BT_OPT_VARIANT_HALO}[variant]
+    if loop == "host":
+        flags |= bt.BT_OPT_NO_GRAPH
+    sim = sim_cls(p)
+    try:
+        S, err, stat, st = sim.run(bt.BT_MODE_MIXED, flags=flags)
+        assert np.all(stat == 0)
+        assert rel(S, ref).max() < TOL_MIXED, rel(S, ref)
+        for r in range(p.n_rhs):
+            u = bt.bt_get_state(sim.ctx, r)
+            assert (np.abs(u - U[r]) / np.abs(U[r]).max()).max() < TOL_MIXED
+        st_ = sim.stats()
+        assert st_["sys_iters"] > 0 and st_["sys_iters"] <= st_["spmm_launches"] * p.n_rhs
+    finally:
+        sim.close()
+
+
+def test_field_of_rhs_range(sim_cls, bt, live_field):
+    """A run over an RHS sub-range returns the fields of exactly those RHS."""
+    p, ref, U = live_field("cfg2_n8_dirs")
+    sim = sim_cls(p)
+    try:
+        sim.run(bt.BT_MODE_PLAIN_FP64, rhs_begin=2, rhs_end=4)
+        for r in (2, 3):
+            u = bt.bt_get_state(sim.ctx, r)
+            assert (np.abs(u - U[r]) / np.abs(U[r]).max()).max() < TOL_FP64
+        for r in (1, 4):
+            with pytest.raises(bt.BtError):
+                bt.bt_get_state(sim.ctx, r)
+        bt.bt_set_gradients(sim.ctx, p.dirs, p.bvals)      # discards the state
+        with pytest.raises(bt.BtError):
+            bt.bt_get_state(sim.ctx, 2)
+    finally:
+        sim.close()
+
+
 def test_free_periodic_exact_closed_form_gpu(sim_cls, bt):
     """Periodic box without compartments: the exact discrete product (P-5)."""
     p = geom.free_periodic_box(n=10, L=10.0, dirs=((0.3, 0.4, math.sqrt(0.75)), (1.0, 0.0, 0.0)),

@@ -140,3 +140,45 @@ def test_state_errors(bt):
         assert e.value.code == bt.BT_ENODEV
     finally:
         bt.bt_destroy(ctx)
+
+
+@pytest.mark.parametrize("maker,umax", [(lambda: geom.cfg2(n=10, kappa=1e-4), 96),
+                                        (lambda: geom.cfg3(n=10, n_dir=1, n_b=1), 192),
+                                        (lambda: geom.cfg4(n=12, n_dir=1, bvals=(1000.0,)), 384)])
+def test_halo_tiles_cover_the_pattern(bt, maker, umax):
+    """Every row is owned by exactly one tile; each tile's halo is the sorted,
+    duplicate-free union of its rows' columns, within umax; the local indices
+    of every entry point back to the CSR column; the owned flags mark exactly
+    the tile's rows; and the halo is smaller than one gather per nonzero."""
+    p = maker()
+    ctx = _host(bt, p)
+    try:
+        rp, col = bt.bt_get_pattern(ctx)
+        n = len(rp) - 1
+        t = bt.bt_get_halo_tiles(ctx, umax)
+        assert np.array_equal(np.sort(t["rows"]), np.arange(n))
+        nt = len(t["r0"]) - 1
+        assert t["r0"][0] == 0 and t["r0"][-1] == n and t["u0"][-1] == len(t["ucol"])
+        for k in range(nt):
+            rows = t["rows"][t["r0"][k]:t["r0"][k + 1]]
+            assert 0 < len(rows) <= 128
+            uc = t["ucol"][t["u0"][k]:t["u0"][k + 1]]
+            ids = (uc & 0x7FFFFFFF).astype(np.int64)
+            own = (uc >> 31).astype(bool)
+            assert len(uc) <= umax
+            assert np.all(np.diff(ids) > 0)
+            want = np.unique(np.concatenate([col[rp[r]:rp[r + 1]] for r in rows]))
+            assert np.array_equal(ids, want)
+            assert np.array_equal(np.sort(ids[own]), np.sort(rows))
+            for j, r in enumerate(rows):
+                kk = t["r0"][k] + j
+                e0, e1 = t["rowe"][kk], t["rowe"][kk + 1]
+                assert e1 - e0 == rp[r + 1] - rp[r]
+                assert np.array_equal(ids[t["lidx"][e0:e1]], col[rp[r]:rp[r + 1]])
+                assert ids[t["rowl"][kk]] == r and own[t["rowl"][kk]]
+        assert t["rowe"][-1] == len(col)
+        assert len(t["ucol"]) < 0.5 * len(col)
+        with pytest.raises(bt.BtError):
+            bt.bt_get_halo_tiles(ctx, 8)
+    finally:
+        bt.bt_destroy(ctx)

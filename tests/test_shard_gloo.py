@@ -62,6 +62,8 @@ def test_two_gloo_ranks_gather_equals_unsharded():
     import geom
     import oracle
     ctx = mp.get_context("spawn")
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):    # one BLAS thread per rank
+        os.environ.setdefault(k, "1")
     q = ctx.Queue()
     port = _free_port()
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
