@@ -183,9 +183,9 @@ def run_reference(args):
 
 
 # vectors of n complex FP32 values (8 B) each active right-hand side moves per
-# launch of the dominant kernel: the row / tiled SpMM reads X and writes Y; the
+# launch of the dominant kernel: the row SpMM reads X and writes Y; the
 # halo-staged apply reads z, p_prev and x and writes x, p and q
-VECTORS_PER_SYSTEM = {"row": 2, "tiled": 2, "halo": 6}
+VECTORS_PER_SYSTEM = {"row": 2, "halo": 6}
 
 
 def spmm_bytes(n, nnz, transformed, launches, sys_iters, variant):
@@ -319,8 +319,7 @@ def run_ours(args):
                                              "speedup_of_value": value / ws / fp64_rate},
             "spmm_autotune": tuning,
             "roofline": {"bound": "hbm",
-                         "kernel": {"row": "k_spmm_krylov", "tiled": "k_spmm_tiled",
-                                    "halo": "k_spmm_halo"}[tuning["variant"]]
+                         "kernel": {"row": "k_spmm_krylov", "halo": "k_spmm_halo"}[tuning["variant"]]
                          + " (fused FP32 complex SpMM of the Krylov iteration, the autotuned variant)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "frac_of_nominal_7900_gbs": achieved / 7900.0,

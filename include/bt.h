@@ -161,16 +161,15 @@ enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
 /* Option flags: BT_OPT_RESID_FP64 native-FP64 refinement residuals;
  * BT_OPT_PROFILE CUDA events around every fused SpMM and residual launch
  * (host-driven loop); BT_OPT_NO_GRAPH host-driven loop instead of the
- * captured step graph; BT_OPT_VARIANT_ROW / _TILED / _HALO bypass the
- * autotuner and use that Krylov variant (bt_get_tuning; _HALO falls back to
- * the tuned choice where the halo tiles are not available). */
+ * captured step graph; BT_OPT_VARIANT_ROW / _HALO bypass the autotuner and
+ * use that Krylov variant (bt_get_tuning; _HALO falls back to the tuned
+ * choice where the halo tiles are not available). */
 enum {
   BT_OPT_RESID_FP64 = 1u,
   BT_OPT_PROFILE = 2u,
   BT_OPT_NO_GRAPH = 4u,
   BT_OPT_VARIANT_ROW = 8u,
-  BT_OPT_VARIANT_TILED = 16u,
-  BT_OPT_VARIANT_HALO = 32u
+  BT_OPT_VARIANT_HALO = 16u
 };
 typedef struct bt_solver_opts {
   double tol_fp64;      /* plain FP64 stopping tolerance (default 1e-12)          */
@@ -208,11 +207,11 @@ bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_
  * RHS count, RHS-per-lane and segmentation by timing one inner iteration of
  * each variant on the real pattern:
  *   0  row SpMM (one warp per row, X gathered per nonzero) + vector updates
- *   1  4-row register-reuse SpMM + vector updates
- *   2  halo-staged apply (Morton-ordered row tiles, their halo rows of X staged
+ *   1  halo-staged apply (Morton-ordered row tiles, their halo rows of X staged
  *      in shared memory, search-direction and solution updates fused in) +
- *      z update; offered in BT_MODE_MIXED only
- * ms_iter [3] (may be NULL) receives the measured ms per iteration of each
+ *      z update, and halo-staged double-float residuals; offered in
+ *      BT_MODE_MIXED only
+ * ms_iter [2] (may be NULL) receives the measured ms per iteration of each
  * (0 = not timed).  BT_ESTATE before any tuning. */
 bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter);
 /* Counters of the last bt_run (any pointer may be NULL): time steps, total

@@ -484,33 +484,6 @@ int pick_nb(const bt_ctx* ctx, int rb, int Rs) {
 }  // namespace
 
 namespace {
-// Row tiles of the register-reuse SpMM for the current segmentation, and the
-// plane values in tile-entry order for the current assembly.
-bt_status ensure_tiles(bt_ctx* ctx, cudaStream_t st) {
-  if (ctx->tiles_for != ctx->seg_row0) {
-    RowTiles t;
-    build_row_tiles(ctx->mesh, ctx->seg_row0, t);
-    CK(upload(ctx->t_row0, t.row0, st));
-    CK(upload(ctx->t_u0, t.u0, st));
-    CK(upload(ctx->t_s0, t.s0, st));
-    CK(upload(ctx->t_seg0, t.seg_tile0, st));
-    CK(upload(ctx->t_slot, t.slot, st));
-    std::vector<uint32_t> uc(t.ucol.begin(), t.ucol.end());
-    CK(upload(ctx->t_ucol, uc, st));
-    CK(cudaStreamSynchronize(st));
-    ctx->tiles_for = ctx->seg_row0;
-    ctx->tiles_planes_version = -1;
-  }
-  if (ctx->tiles_planes_version != ctx->planes_version) {
-    CK(ensure(ctx->pkt, ctx->mesh.nnz));
-    CK(ensure(ctx->mdt, ctx->mesh.nnz));
-    launch_gather_tile_planes(ctx->t_slot.p, ctx->mesh.nnz, ctx->d_pk32.p, ctx->d_md32.p, ctx->pkt.p, ctx->mdt.p, st);
-    CKL();
-    ctx->tiles_planes_version = ctx->planes_version;
-  }
-  return BT_OK;
-}
-
 // Halo tiles for RHS-per-lane nb (umax from the shared-memory budget) and the
 // plane values in halo-entry order.  Sets ctx->halo_ok = false when a row is
 // wider than umax (the halo iteration is then not offered).
@@ -518,6 +491,7 @@ bt_status ensure_halo(bt_ctx* ctx, int nb, cudaStream_t st) {
   const int umax = (int)std::min<size_t>(65535, (96 * 1024) / halo_smem_bytes(nb, 1));
   if (!ctx->halo_attr) {
     halo_prepare();
+    resid_df_halo_prepare();
     CKL();
     ctx->halo_attr = true;
   }
@@ -556,18 +530,11 @@ HaloArgs halo_args(const bt_ctx* ctx) {
                   ctx->h_lidx.p, ctx->h_pkt.p, ctx->h_mdt.p, ctx->h_seg0.p, ctx->halo_umax};
 }
 
-void spmm_f32(int variant, const OpArgs& op, const float2* p, float2* q, const KrylovState& ks, RedScratch rs,
-              int conj, int nb, int sms, cudaStream_t st) {
-  if (variant == 1) launch_spmm_krylov_f32_tiled(op, p, q, ks, rs, conj, nb, sms, st);
-  else launch_spmm_krylov_f32(op, p, q, ks, rs, conj, nb, sms, st);
-}
-
 // Autotuner: time one Krylov iteration of each variant on the real pattern
 // and RHS count (CUDA events, 3 iterations after a warm-up) and keep the
-// fastest, cached per (RHS, RHS per lane, segments):
+// faster, cached per (RHS, RHS per lane, segments):
 //   0: row SpMM + vector update + p update
-//   1: 4-row register-reuse SpMM + vector update + p update
-//   2: halo-staged apply + z update (when the halo tiles exist and allow_halo)
+//   1: halo-staged apply + z update (when the halo tiles exist and allow_halo)
 // The Krylov state is primed with benign scalars (nothing converges while
 // timing); the Krylov init of the first solve re-initialises all of it.
 bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const KrylovState& ks, RedScratch rs,
@@ -576,7 +543,7 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
   for (auto& t : ctx->tuned)
     if (t.R == Rs && t.nb == nb && t.G == G) hit = &t;
   const bool halo = allow_halo && ctx->halo_ok;
-  if (!hit || (halo && hit->ms[2] == 0)) {
+  if (!hit || (halo && hit->ms[1] == 0)) {
     cudaStream_t st = ctx->stream;
     const size_t NE = (size_t)op.n * op.Rp;
     std::vector<double> one(2 * (size_t)SY), small(2 * (size_t)SY), half(2 * (size_t)SY), big(SY, 1e300);
@@ -602,12 +569,12 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     for (float2* b : {ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ctx->p32b.p})
       if (b) CK(cudaMemsetAsync(b, 0x3e, NE * sizeof(float2), st));
     auto iter = [&](int v) {
-      if (v == 2) {
+      if (v == 1) {
         launch_spmm_halo(op, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, ks, rs,
                          conj, nb, st);
         launch_krylov_update_z(op, va, ctx->r32.p, ctx->q32.p, ks, rs2, conj, st);
       } else {
-        spmm_f32(v, op, ctx->p32.p, ctx->q32.p, ks, rs, conj, nb, ctx->sms, st);
+        launch_spmm_krylov_f32(op, ctx->p32.p, ctx->q32.p, ks, rs, conj, nb, ctx->sms, st);
         launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs2, conj, ctx->sms,
                                  st);
         launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st);
@@ -616,8 +583,8 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0, 0}};
-    for (int v = 0; v < (halo ? 3 : 2); ++v) {
+    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0}};
+    for (int v = 0; v < (halo ? 2 : 1); ++v) {
       if (bt_status e = prime()) return e;
       iter(v);  // warm-up
       CK(cudaEventRecord(e0, st));
@@ -636,9 +603,7 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     else ctx->tuned.push_back(tu);
     hit = hit ? hit : &ctx->tuned.back();
   }
-  int best = hit->ms[1] < hit->ms[0] ? 1 : 0;
-  if (halo && hit->ms[2] > 0 && hit->ms[2] < hit->ms[best]) best = 2;
-  *variant = best;
+  *variant = (halo && hit->ms[1] > 0 && hit->ms[1] < hit->ms[0]) ? 1 : 0;
   return BT_OK;
 }
 
@@ -778,7 +743,9 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
   };
   if (E(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) {
     launch_graph_step_begin(gc, ctx->rf_active.p, cs);
-    if (g.df) launch_resid0_df(op0, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(0), g.nb, ctx->sms, cs);
+    if (g.df && g.variant == 1 && resid_df_halo_available(g.nb, 0))
+      launch_resid0_df_halo(op0, halo_args(ctx), ctx->udf.p, ctx->rdf.p, g.rf, rs_at(0), g.nb, cs);
+    else if (g.df) launch_resid0_df(op0, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(0), g.nb, ctx->sms, cs);
     else launch_resid0(op0, ctx->u64.p, ctx->r64.p, g.rf, rs_at(0), g.nb, ctx->sms, cs);
     cudaGraphConditionalHandle hR{}, hI{};
     cudaGraph_t bodyR = nullptr, bodyI = nullptr;
@@ -787,7 +754,7 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
     if (ok) launch_graph_cond(gc, 0, hR, cs);
     if (ok) while_node(cs, hR, &bodyR);
     if (ok && E(cudaStreamBeginCaptureToGraph(c2, bodyR, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
-      if (g.variant == 2)
+      if (g.variant == 1)
         launch_krylov_init_z(opL, g.va, g.df ? (const void*)ctx->rdf.p : (const void*)ctx->r64.p, g.df,
                              ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p, g.ks, g.tol_inner, rs_at(1),
                              g.conj, c2);
@@ -801,12 +768,12 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
         launch_graph_cond(gc, 2, hI, c2);
         while_node(c2, hI, &bodyI);
         if (ok && E(cudaStreamBeginCaptureToGraph(c3, bodyI, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
-          if (g.variant == 2) {
+          if (g.variant == 1) {
             launch_spmm_halo(opL, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, g.ks,
                              rs_at(2), g.conj, g.nb, c3);
             launch_krylov_update_z(opL, g.va, ctx->r32.p, ctx->q32.p, g.ks, rs_at(3), g.conj, c3);
           } else {
-            spmm_f32(g.variant, opL, ctx->p32.p, ctx->q32.p, g.ks, rs_at(2), g.conj, g.nb, ctx->sms, c3);
+            launch_spmm_krylov_f32(opL, ctx->p32.p, ctx->q32.p, g.ks, rs_at(2), g.conj, g.nb, ctx->sms, c3);
             launch_krylov_update_f32(opL, g.va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, g.ks, rs_at(3),
                                      g.conj, ctx->sms, c3);
             launch_krylov_p_f32(opL, g.va, ctx->r32.p, ctx->p32.p, g.ks, ctx->sms, c3);
@@ -817,8 +784,10 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
           E(cudaStreamEndCapture(c3, &tmp));
         }
       }
-      if (g.variant == 2) launch_flush_x(g.va, ctx->x32.p, ctx->p32.p, ctx->p32b.p, g.ks, c2);
-      if (g.df) launch_resid_sub_df(opL, ctx->x32.p, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(4), g.nb, ctx->sms, c2);
+      if (g.variant == 1) launch_flush_x(g.va, ctx->x32.p, ctx->p32.p, ctx->p32b.p, g.ks, c2);
+      if (g.df && g.variant == 1)
+        launch_resid_sub_df_halo(opL, halo_args(ctx), ctx->x32.p, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(4), g.nb, c2);
+      else if (g.df) launch_resid_sub_df(opL, ctx->x32.p, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(4), g.nb, ctx->sms, c2);
       else launch_resid_sub(opL, ctx->x32.p, ctx->u64.p, ctx->r64.p, g.rf, rs_at(4), g.nb, ctx->sms, c2);
       launch_graph_cond(gc, 1, hR, c2);
       E(cudaGetLastError());
@@ -1026,17 +995,9 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   rf.floor_c2 = feps * feps;
   auto rs_at = [&](int c) { return RedScratch{ctx->red_part.p, ctx->red_counter.p + c}; };
 
-  // register-reuse tiles and the tuned SpMM variant for the FP32 inner solves
+  // halo tiles and the tuned Krylov variant for the FP32 inner solves
   int variant = 0;
   if (!plain) {
-    if (bt_status e = ensure_tiles(ctx, st)) return e;
-    op.t_row0 = ctx->t_row0.p;
-    op.t_u0 = ctx->t_u0.p;
-    op.t_s0 = ctx->t_s0.p;
-    op.t_ucol = ctx->t_ucol.p;
-    op.t_seg0 = ctx->t_seg0.p;
-    op.pkt = ctx->pkt.p;
-    op.mdt = ctx->mdt.p;
     const bool allow_halo = !learned && !col;
     if (allow_halo)
       if (bt_status e = ensure_halo(ctx, nb, st)) return e;
@@ -1045,8 +1006,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     if (bt_status e = autotune_spmm(ctx, opt, va, ks, rs_at(2), rs_at(3), conj, nb, SY, Rs, G, allow_halo, &variant))
       return e;
     if (o.flags & BT_OPT_VARIANT_ROW) variant = 0;
-    if (o.flags & BT_OPT_VARIANT_TILED) variant = 1;
-    if ((o.flags & BT_OPT_VARIANT_HALO) && allow_halo && ctx->halo_ok) variant = 2;
+    if ((o.flags & BT_OPT_VARIANT_HALO) && allow_halo && ctx->halo_ok) variant = 1;
   }
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
   ctx->st_spmm_ms = ctx->st_resid_ms = 0;
@@ -1084,7 +1044,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       ctx->st_iters = ctx->st_spmm = gi;
       ctx->st_refine = gp;
       ctx->st_resid = N + gp;
-      L += variant == 2 ? 5 * (int64_t)N + 6 * gp + 3 * gi : 5 * (int64_t)N + 4 * gp + 4 * gi;
+      L += variant == 1 ? 5 * (int64_t)N + 6 * gp + 3 * gi : 5 * (int64_t)N + 4 * gp + 4 * gi;
     }
   }
   double last_fq = NAN;
@@ -1112,7 +1072,9 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     L += 3;  // two set kernels and the step-start residual
     op.coef = c_r0;
     timed(1, [&] {
-      if (df) launch_resid0_df(op, ctx->udf.p, ctx->rdf.p, rf, rs_at(0), nb, ctx->sms, st);
+      if (df && variant == 1 && resid_df_halo_available(nb, 0))
+        launch_resid0_df_halo(op, halo_args(ctx), ctx->udf.p, ctx->rdf.p, rf, rs_at(0), nb, st);
+      else if (df) launch_resid0_df(op, ctx->udf.p, ctx->rdf.p, rf, rs_at(0), nb, ctx->sms, st);
       else if (narrow) launch_resid0_narrow(op, ctx->u64.p, ctx->r64.p, rf, rs_at(0), ctx->sms, st);
       else launch_resid0(op, ctx->u64.p, ctx->r64.p, rf, rs_at(0), nb, ctx->sms, st);
     });
@@ -1128,7 +1090,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       if (plain) {
         launch_krylov_init_f64(op, va, ctx->r64.p, ctx->rf_active.p, ctx->x64.p, ctx->rk64.p, ctx->p64.p, ks,
                                o.tol_fp64, rs_at(1), conj, ctx->sms, st);
-      } else if (variant == 2) {
+      } else if (variant == 1) {
         launch_krylov_init_z(op, va, df ? (const void*)ctx->rdf.p : (const void*)ctx->r64.p, df, ctx->rf_scale.p,
                              ctx->rf_active.p, ctx->x32.p, ctx->r32.p, ks, o.tol_inner, rs_at(1), conj, st);
       } else if (df) {
@@ -1160,7 +1122,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
           launch_krylov_update_f64(op, va, ctx->x64.p, ctx->rk64.p, ctx->p64.p, ctx->q64.p, ks, rs_at(3), conj,
                                    ctx->sms, st);
           launch_krylov_p_f64(op, va, ctx->rk64.p, ctx->p64.p, ks, ctx->sms, st);
-        } else if (variant == 2) {
+        } else if (variant == 1) {
           timed(0, [&] {
             launch_spmm_halo(op, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, ks,
                              rs_at(2), conj, nb, st);
@@ -1168,7 +1130,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
           launch_krylov_update_z(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
           L -= 1;  // two launches per iteration
         } else {
-          timed(0, [&] { spmm_f32(variant, op, ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb, ctx->sms, st); });
+          timed(0, [&] { launch_spmm_krylov_f32(op, ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb, ctx->sms, st); });
           launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs_at(3), conj,
                                    ctx->sms, st, learned ? ctx->pmode.p : nullptr);
           if (learned) {
@@ -1195,12 +1157,14 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
         launch_finish_step(rf, ks, SY, st);
         L += 1;
       } else {
-        if (variant == 2) {
+        if (variant == 1) {
           launch_flush_x(va, ctx->x32.p, ctx->p32.p, ctx->p32b.p, ks, st);
           L += 2;
         }
         timed(1, [&] {
-          if (df) launch_resid_sub_df(op, ctx->x32.p, ctx->udf.p, ctx->rdf.p, rf, rs_at(4), nb, ctx->sms, st);
+          if (df && variant == 1)
+            launch_resid_sub_df_halo(op, halo_args(ctx), ctx->x32.p, ctx->udf.p, ctx->rdf.p, rf, rs_at(4), nb, st);
+          else if (df) launch_resid_sub_df(op, ctx->x32.p, ctx->udf.p, ctx->rdf.p, rf, rs_at(4), nb, ctx->sms, st);
           else launch_resid_sub(op, ctx->x32.p, ctx->u64.p, ctx->r64.p, rf, rs_at(4), nb, ctx->sms, st);
         });
         ctx->st_resid++;
@@ -1318,7 +1282,7 @@ extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* 
   const auto& t = ctx->tuned.back();
   if (variant) *variant = t.variant;
   if (ms_iter)
-    for (int k = 0; k < 3; ++k) ms_iter[k] = t.ms[k];
+    for (int k = 0; k < 2; ++k) ms_iter[k] = t.ms[k];
   return BT_OK;
 }
 

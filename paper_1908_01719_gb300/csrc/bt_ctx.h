@@ -57,13 +57,7 @@ struct bt_ctx {
   cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};  // captures of the step graph
   bt::DBuf<int64_t> d_row0;
   int nblk = 0;
-  // register-reuse SpMM tiles (built for one segmentation) and the autotuner's choice
-  bt::DBuf<int32_t> t_row0, t_u0, t_s0, t_seg0, t_slot;
-  bt::DBuf<uint32_t> t_ucol;
-  bt::DBuf<float4> pkt;
-  bt::DBuf<float> mdt;
-  std::vector<int64_t> tiles_for;   // seg_row0 the tiles were built for
-  int64_t planes_version = 0, tiles_planes_version = -1;
+  int64_t planes_version = 0;  // bumped by every assembly
   // halo tiles of the shared-memory Krylov apply (one segmentation, one umax)
   bt::DBuf<int32_t> h_r0, h_rows, h_rowe, h_u0, h_seg0, h_slot;
   bt::DBuf<uint16_t> h_rowl, h_lidx;
@@ -77,8 +71,8 @@ struct bt_ctx {
   bool halo_attr = false;
   struct Tuned {
     int R, nb, G;
-    int variant;   // 0 row kernel, 1 tiled kernel, 2 halo iteration
-    double ms[3];  // one Krylov iteration of each variant (ms; 0 = not timed)
+    int variant;   // 0 row SpMM iteration, 1 halo iteration
+    double ms[2];  // one Krylov iteration of each variant (ms; 0 = not timed)
   };
   std::vector<Tuned> tuned;
 

@@ -47,19 +47,6 @@ struct HostMesh {
 // Validates and builds everything above; returns BT_OK or BT_EINVAL with msg.
 int build_host_mesh(HostMesh& m, std::string& msg);
 
-// Row tiles of 4 consecutive rows inside each segment, for the register-reuse
-// SpMM: per tile the merged, sorted union of its rows' columns, each unique
-// column packed with the 4-bit mask of the rows that contain it
-// (col | mask << 28), and the CSR slots of those entries in (column, row) order.
-struct RowTiles {
-  std::vector<int32_t> row0;   // [ntiles + 1] first row (sentinel n)
-  std::vector<int32_t> u0;     // [ntiles + 1] offsets into ucol
-  std::vector<int32_t> s0;     // [ntiles + 1] offsets into slot
-  std::vector<int32_t> ucol;   // unique columns with masks
-  std::vector<int32_t> slot;   // [nnz] CSR slot of each tile entry
-  std::vector<int32_t> seg_tile0;  // [G + 1]
-};
-void build_row_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, RowTiles& t);
 
 // Halo tiles for the shared-memory SpMM: rows of each segment in Morton order
 // of their node coordinates, cut greedily into tiles of at most `tmax` rows

@@ -128,14 +128,6 @@ struct OpArgs {
   int R, Rp;             // systems per segment, padded vector width
   int transformed;
   SegPlan sp;
-  // row tiles of the register-reuse SpMM (null when not built)
-  const int32_t* t_row0;
-  const int32_t* t_u0;
-  const int32_t* t_s0;
-  const uint32_t* t_ucol;
-  const int32_t* t_seg0;   // [G + 1] first tile of each segment
-  const float4* pkt;       // pk32 in tile-entry order
-  const float* mdt;        // md32 in tile-entry order
 };
 
 // Halo tiles of the shared-memory Krylov apply (HaloTiles on the device).
@@ -196,9 +188,6 @@ int spmm_grid_rows(int64_t n, int sms);
 
 void launch_spmm_krylov_f32(const OpArgs& op, const float2* p, float2* q, const KrylovState& ks,
                             RedScratch rs, int conj, int nb, int sms, cudaStream_t st);
-// the same operator with row tiles sharing gathered rows (register reuse)
-void launch_spmm_krylov_f32_tiled(const OpArgs& op, const float2* p, float2* q, const KrylovState& ks,
-                                  RedScratch rs, int conj, int nb, int sms, cudaStream_t st);
 void launch_gather_tile_planes(const int32_t* slot, int64_t nnz, const float4* pk32, const float* md32, float4* pkt,
                                float* mdt, cudaStream_t st);
 void launch_spmm_krylov_f64(const OpArgs& op, const double2* p, double2* q, const KrylovState& ks,
@@ -215,6 +204,13 @@ void launch_resid0_df(const OpArgs& op, const float4* u, float4* r, const Refine
                       int nb, int sms, cudaStream_t st);
 void launch_resid_sub_df(const OpArgs& op, const float2* d, float4* u, float4* r, const RefineState& rf,
                          RedScratch rs, int nb, int sms, cudaStream_t st);
+// the same over the halo tiles (the halo-staged variant): mode 0 needs nb >= 2
+void resid_df_halo_prepare();
+bool resid_df_halo_available(int nb, int mode);
+void launch_resid0_df_halo(const OpArgs& op, const HaloArgs& h, const float4* u, float4* r, const RefineState& rf,
+                           RedScratch rs, int nb, cudaStream_t st);
+void launch_resid_sub_df_halo(const OpArgs& op, const HaloArgs& h, const float2* d, float4* u, float4* r,
+                              const RefineState& rf, RedScratch rs, int nb, cudaStream_t st);
 void launch_krylov_init_f32_df(const OpArgs& op, const VecArgs& va, const float4* rdf, const double* scale,
                                const int* ref_active, float2* x, float2* r, float2* p, const KrylovState& ks,
                                double tol, RedScratch rs, int conj, int sms, cudaStream_t st);

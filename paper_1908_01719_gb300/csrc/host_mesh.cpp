@@ -344,44 +344,6 @@ void build_contributions(HostMesh& m) {
 
 }  // namespace
 
-void build_row_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, RowTiles& t) {
-  t = RowTiles();
-  const int G = (int)seg_row0.size() - 1;
-  t.slot.reserve(m.nnz);
-  for (int g = 0; g < G; ++g) {
-    t.seg_tile0.push_back((int32_t)t.row0.size());
-    for (int64_t r = seg_row0[g]; r < seg_row0[g + 1]; r += 4) {
-      const int nr = (int)std::min<int64_t>(4, seg_row0[g + 1] - r);
-      t.row0.push_back((int32_t)r);
-      t.u0.push_back((int32_t)t.ucol.size());
-      t.s0.push_back((int32_t)t.slot.size());
-      int64_t c[4], e[4];
-      for (int k = 0; k < 4; ++k) {
-        c[k] = k < nr ? m.row_ptr[r + k] : 0;
-        e[k] = k < nr ? m.row_ptr[r + k + 1] : 0;
-      }
-      for (;;) {
-        int32_t j = INT32_MAX;
-        for (int k = 0; k < nr; ++k)
-          if (c[k] < e[k]) j = std::min(j, m.col[c[k]]);
-        if (j == INT32_MAX) break;
-        int mask = 0;
-        for (int k = 0; k < nr; ++k)
-          if (c[k] < e[k] && m.col[c[k]] == j) {
-            mask |= 1 << k;
-            t.slot.push_back((int32_t)c[k]);
-            ++c[k];
-          }
-        t.ucol.push_back((int32_t)((uint32_t)j | ((uint32_t)mask << 28)));
-      }
-    }
-  }
-  t.seg_tile0.push_back((int32_t)t.row0.size());
-  t.row0.push_back((int32_t)m.n_dof);
-  t.u0.push_back((int32_t)t.ucol.size());
-  t.s0.push_back((int32_t)t.slot.size());
-}
-
 // 16-bit spread for a 48-bit Morton code
 static uint64_t spread3(uint64_t v) {
   v &= 0xFFFFull;

@@ -291,3 +291,248 @@ __global__ void k_fill_u_df(VecArgs va, float4* __restrict__ u) {
 void launch_fill_u_df(const VecArgs& va, float4* u, cudaStream_t st) { k_fill_u_df<<<1024, 256, 0, st>>>(va, u); }
 
 }  // namespace bt
+
+// ---------------------------------------------------------------- halo-staged variant
+// The same two residuals over the halo tiles of the Krylov apply: the gathered
+// vector (u in mode 0, d in mode 1) is staged in shared memory for the tile's
+// halo rows, then every owned row forms its double-float sums from shared
+// memory.  Each owned row's entries are its CSR entries in order, so the
+// double-float planes are read at their CSR slots.  Shared memory per halo
+// row: 32 NB sizeof(TX) bytes (NB columns per lane in this block).
+namespace bt {
+
+template <int NBL, int NB, bool TRANSF, int MODE, class TX>
+__global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h, const TX* __restrict__ x,
+                                                          float4* __restrict__ u, float4* __restrict__ r,
+                                                          RefineState rf, RedScratch rs) {
+  if (*rf.n_active == 0) return;
+  extern __shared__ float4 sdf_[];
+  TX* xs_ = reinterpret_cast<TX*>(sdf_);  // [umax][NB][32]
+  constexpr int NSPLIT = NBL / NB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tile = blockIdx.y / NSPLIT, part = blockIdx.y % NSPLIT;
+  const int r0 = (tile * 32 + lane) * NBL + part * NB;
+  const int c0 = tile * 32 * NBL + lane + 32 * part * NB;
+  const bool on = r0 < op.R;
+  LaneCoef<NB> lc;
+  BT_SEG_BEGIN(op.sp);
+  (void)sr0_;
+  (void)sr1_;
+  lane_coef<NB>(op, sg_, on ? r0 : 0, rf.active, lc);
+  bool act[NB];
+  bool any = false;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    act[b] = on && lc.act[b];
+    any |= act[b];
+  }
+  const dd qx = dd_split(lc.qx), qy = dd_split(lc.qy), qz = dd_split(lc.qz);
+  const dd ca = dd_split(lc.a);
+  dd cb[NB], cc[NB];
+  float sc[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    cb[b] = dd_split(lc.b[b]);
+    cc[b] = dd_split(lc.c[b]);
+    sc[b] = (MODE == 1 && on && r0 + b < op.R) ? (float)rf.scale[sg_ * op.R + r0 + b] : 1.0f;
+  }
+  double2 acc[NB];
+  float2 accf[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    acc[b] = make_double2(0, 0);
+    accf[b] = make_float2(0, 0);
+  }
+  int cnt = 0;
+  if (__syncthreads_or(any)) {
+    const int tb = h.seg_tile0[sg_], te = h.seg_tile0[sg_ + 1];
+    for (int tau = tb + sk_; tau < te; tau += snb_) {
+      // ---- stage the gathered vector for the halo rows
+      const int ub = h.u0[tau], nu = h.u0[tau + 1] - ub;
+      for (int uu0 = warp; uu0 < nu; uu0 += 16) {
+        TX v[2][NB];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int uu = uu0 + 8 * k;
+          const size_t e = uu < nu ? (size_t)(__ldg(h.ucol + ub + uu) & 0x7FFFFFFFu) * op.Rp + c0 : 0;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            if (uu < nu && act[b]) v[k][b] = __ldg(x + e + 32 * b);
+            else v[k][b] = TX{};
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int uu = uu0 + 8 * k;
+          if (uu >= nu) break;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) xs_[(uu * NB + b) * 32 + lane] = v[k][b];
+        }
+      }
+      __syncthreads();
+      // ---- double-float sums of the owned rows
+      const int ra = h.t_r0[tau], rz = h.t_r0[tau + 1];
+      for (int kk = ra + warp; kk < rz; kk += 8) {
+        const int row = __ldg(h.rows + kk);
+        const int e0 = __ldg(h.rowe + kk), e1 = __ldg(h.rowe + kk + 1);
+        const int k0 = op.rp[row];  // CSR slot of the row's first entry
+        float Ph[NB][2], Pl[NB][2], Qh[NB][2], Ql[NB][2], Zh[NB][2], Zl[NB][2];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) Ph[b][c] = Pl[b][c] = Qh[b][c] = Ql[b][c] = Zh[b][c] = Zl[b][c] = 0.f;
+        for (int e = e0; e < e1; ++e) {
+          const int k = k0 + (e - e0);
+          const int l = __ldg(h.lidx + e);
+          const float4 vh = __ldg(op.pkhi + k), vl = __ldg(op.pklo + k);
+          float p0h, p0l, mdh = 0.f, mdl = 0.f;
+          if (MODE == 0 || TRANSF) {
+            const float2 kh = __ldg(op.kjmd_hi + k), kl = __ldg(op.kjmd_lo + k);
+            mdh = kh.y;
+            mdl = kl.y;
+            p0h = MODE == 0 ? kh.x : vh.x;
+            p0l = MODE == 0 ? kl.x : vl.x;
+          } else {
+            p0h = vh.x;
+            p0l = vl.x;
+          }
+          float mh = 0.f, ml = 0.f;
+          dd_acc(mh, ml, qx.h, qx.l, vh.y, vl.y);
+          dd_acc(mh, ml, qy.h, qy.l, vh.z, vl.z);
+          dd_acc(mh, ml, qz.h, qz.l, vh.w, vl.w);
+          const dd m = dd_norm(mh, ml);
+          const TX* xp = xs_ + l * NB * 32 + lane;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            if constexpr (MODE == 0) {
+              const float4 xv = xp[32 * b];
+              dd_acc(Ph[b][0], Pl[b][0], p0h, p0l, xv.x, xv.z);
+              dd_acc(Ph[b][1], Pl[b][1], p0h, p0l, xv.y, xv.w);
+              dd_acc(Qh[b][0], Ql[b][0], m.h, m.l, xv.x, xv.z);
+              dd_acc(Qh[b][1], Ql[b][1], m.h, m.l, xv.y, xv.w);
+              if constexpr (TRANSF) {
+                dd_acc(Zh[b][0], Zl[b][0], mdh, mdl, xv.x, xv.z);
+                dd_acc(Zh[b][1], Zl[b][1], mdh, mdl, xv.y, xv.w);
+              }
+            } else {
+              const float2 xv = xp[32 * b];
+              dd_acc1(Ph[b][0], Pl[b][0], p0h, p0l, xv.x);
+              dd_acc1(Ph[b][1], Pl[b][1], p0h, p0l, xv.y);
+              dd_acc1(Qh[b][0], Ql[b][0], m.h, m.l, xv.x);
+              dd_acc1(Qh[b][1], Ql[b][1], m.h, m.l, xv.y);
+              if constexpr (TRANSF) {
+                dd_acc1(Zh[b][0], Zl[b][0], mdh, mdl, xv.x);
+                dd_acc1(Zh[b][1], Zl[b][1], mdh, mdl, xv.y);
+              }
+            }
+          }
+        }
+        const TX* xo = xs_ + (int)__ldg(h.rowl + kk) * NB * 32 + lane;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          if (!act[b]) continue;
+          const size_t e = (size_t)row * op.Rp + c0 + 32 * b;
+          dd Pr = dd_norm(Ph[b][0], Pl[b][0]), Pi = dd_norm(Ph[b][1], Pl[b][1]);
+          dd Qr = dd_norm(Qh[b][0], Ql[b][0]), Qi = dd_norm(Qh[b][1], Ql[b][1]);
+          dd yr = dd_add(dd_mul(ca, Pr), dd_neg(dd_mul(cc[b], Qi)));
+          dd yi = dd_add(dd_mul(ca, Pi), dd_mul(cc[b], Qr));
+          if constexpr (TRANSF) {
+            dd Zr = dd_norm(Zh[b][0], Zl[b][0]), Zi = dd_norm(Zh[b][1], Zl[b][1]);
+            yr = dd_add(yr, dd_mul(cb[b], Zr));
+            yi = dd_add(yi, dd_mul(cb[b], Zi));
+          }
+          if constexpr (MODE == 0) {
+            r[e] = make_float4(yr.h, yi.h, yr.l, yi.l);
+            const float4 uv = xo[32 * b];  // own row of u, staged
+            accf[b].x += yr.h * yr.h + yi.h * yi.h;
+            accf[b].y += uv.x * uv.x + uv.y * uv.y;
+          } else {
+            const float2 dv = xo[32 * b];  // own row of d, staged
+            const float4 uv = u[e];
+            dd s = dd{sc[b], 0.f};
+            dd ur = dd_add(dd{uv.x, uv.z}, dd_mul(s, dd{dv.x, 0.f}));
+            dd ui = dd_add(dd{uv.y, uv.w}, dd_mul(s, dd{dv.y, 0.f}));
+            u[e] = make_float4(ur.h, ui.h, ur.l, ui.l);
+            const float4 rv = r[e];
+            dd rr = dd_add(dd{rv.x, rv.z}, dd_neg(dd_mul(s, yr)));
+            dd ri = dd_add(dd{rv.y, rv.w}, dd_neg(dd_mul(s, yi)));
+            r[e] = make_float4(rr.h, ri.h, rr.l, ri.l);
+            accf[b].x += rr.h * rr.h + ri.h * ri.h;
+          }
+        }
+        if (++cnt == 16) {
+          cnt = 0;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            acc[b].x += (double)accf[b].x;
+            acc[b].y += (double)accf[b].y;
+            accf[b] = make_float2(0, 0);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    acc[b].x += (double)accf[b].x;
+    acc[b].y += (double)accf[b].y;
+  }
+  block_partials<NB>(acc, on ? r0 : op.Rp, op.Rp, rs.part);
+  if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
+  reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 t) { refine_finish(MODE, rf, s, t); });
+}
+
+// columns per lane one block of the halo residual handles: the staged halo
+// (umax rows of 32 NB sizeof(TX) bytes) must fit the Krylov apply's budget of
+// umax rows of 32 NBL float2
+template <int NBL, int MODE>
+constexpr int df_halo_nb() {
+  return MODE == 0 ? NBL / 2 : (NBL < 2 ? NBL : 2);
+}
+
+template <int NBL, int MODE, class TX>
+static void resid_df_halo_t(const OpArgs& op, const HaloArgs& h, const TX* x, float4* u, float4* r,
+                            const RefineState& rf, RedScratch rs, cudaStream_t st) {
+  constexpr int NB = df_halo_nb<NBL, MODE>();
+  static_assert(NB >= 1, "no halo residual for this width");
+  dim3 grid(op.sp.nblk, ((op.R + 32 * NBL - 1) / (32 * NBL)) * (NBL / NB));
+  const size_t smem = (size_t)h.umax * 32 * NB * sizeof(TX);
+  if (op.transformed)
+    k_resid_df_halo<NBL, NB, true, MODE, TX><<<grid, 256, smem, st>>>(op, h, x, u, r, rf, rs);
+  else
+    k_resid_df_halo<NBL, NB, false, MODE, TX><<<grid, 256, smem, st>>>(op, h, x, u, r, rf, rs);
+}
+
+template <int NBL, int MODE, class TX>
+static void df_halo_attr() {
+  constexpr int NB = df_halo_nb<NBL, MODE>();
+  cudaFuncSetAttribute(k_resid_df_halo<NBL, NB, true, MODE, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       96 * 1024);
+  cudaFuncSetAttribute(k_resid_df_halo<NBL, NB, false, MODE, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       96 * 1024);
+}
+void resid_df_halo_prepare() {
+  df_halo_attr<4, 0, float4>();
+  df_halo_attr<2, 0, float4>();
+  df_halo_attr<4, 1, float2>();
+  df_halo_attr<2, 1, float2>();
+  df_halo_attr<1, 1, float2>();
+}
+
+bool resid_df_halo_available(int nb, int mode) { return !(mode == 0 && nb == 1); }
+
+void launch_resid0_df_halo(const OpArgs& op, const HaloArgs& h, const float4* u, float4* r, const RefineState& rf,
+                           RedScratch rs, int nb, cudaStream_t st) {
+  if (nb == 4) resid_df_halo_t<4, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
+  else resid_df_halo_t<2, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
+}
+
+void launch_resid_sub_df_halo(const OpArgs& op, const HaloArgs& h, const float2* d, float4* u, float4* r,
+                              const RefineState& rf, RedScratch rs, int nb, cudaStream_t st) {
+  if (nb == 4) resid_df_halo_t<4, 1, float2>(op, h, d, u, r, rf, rs, st);
+  else if (nb == 2) resid_df_halo_t<2, 1, float2>(op, h, d, u, r, rf, rs, st);
+  else resid_df_halo_t<1, 1, float2>(op, h, d, u, r, rf, rs, st);
+}
+
+}  // namespace bt

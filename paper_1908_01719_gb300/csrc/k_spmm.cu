@@ -145,149 +145,8 @@ __global__ void __launch_bounds__(256) k_spmm_krylov(OpArgs op, const T2* __rest
   reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
 }
 
-// ---------------------------------------------------------------- register reuse
-// Warp per tile of 4 consecutive rows: the tile's unique columns are walked
-// in order, each column's NB values gathered once and applied to every row
-// of the tile that holds that column (warp-uniform 4-bit mask).  On the Kuhn
-// stencil a tile has about 36 unique columns for 60 nonzeros, so the gather
-// stream -- the kernel's limiter, about 7x the HBM bytes -- shrinks by ~40%.
-// Plane values are read in tile-entry order (pkt, mdt).  Tiles are taken in
-// 8-tile chunks, round-robin over the blocks of the segment (L2 locality as
-// in the row kernels).
-constexpr int TILE_CHUNK = 8;
-// NBL: layout columns per lane; NB (<= NBL): the share one thread computes
-// (blockIdx.y = tile * (NBL / NB) + part), keeping the kernel at 2 blocks/SM.
-template <int NBL, int NB, bool TRANSF, bool CONJ>
-__global__ void __launch_bounds__(256) k_spmm_tiled(OpArgs op, const float2* __restrict__ p, float2* __restrict__ q,
-                                                    KrylovState ks, RedScratch rs) {
-  if (*ks.n_active == 0) return;
-  constexpr int KT = 4;  // unique-column gathers in flight
-  constexpr int NSPLIT = NBL / NB;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ytile = blockIdx.y / NSPLIT, part = blockIdx.y % NSPLIT;
-  const int r0 = (ytile * 32 + lane) * NBL + part * NB;
-  const int c0 = ytile * 32 * NBL + lane + 32 * part * NB;
-  const bool on = r0 < op.R;
-  BT_SEG_BEGIN(op.sp);
-  (void)sr0_;
-  (void)sr1_;
-  LaneCoef<NB> lc;
-  lane_coef<NB>(op, sg_, on ? r0 : 0, ks.active, lc);
-  bool any = false;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) any |= (on && lc.act[b]);
-  const bool warp_any = __any_sync(0xffffffffu, any);
-  const float qx = (float)lc.qx, qy = (float)lc.qy, qz = (float)lc.qz, ca = (float)lc.a;
-  float cb[NB], cc[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    cb[b] = (float)lc.b[b];
-    cc[b] = (float)lc.c[b];
-  }
-  double2 acc[NB];
-  float2 accf[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    acc[b] = make_double2(0, 0);
-    accf[b] = make_float2(0.f, 0.f);
-  }
-  int cnt = 0;
-  const int tb = op.t_seg0[sg_], te = op.t_seg0[sg_ + 1];
-  const float2* pc = p + c0;
-  if (warp_any) {
-    for (int ch = sk_; tb + ch * TILE_CHUNK < te; ch += snb_) {
-      const int tau = tb + ch * TILE_CHUNK + warp;
-      if (warp >= TILE_CHUNK || tau >= te) continue;
-      const int row0 = op.t_row0[tau], nr = op.t_row0[tau + 1] - row0;
-      const int u0 = op.t_u0[tau], u1 = op.t_u0[tau + 1];
-      int sp = op.t_s0[tau];
-      float2 P[4][NB], Q[4][NB];
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int b = 0; b < NB; ++b) P[t][b] = Q[t][b] = make_float2(0.f, 0.f);
-      for (int ub = u0; ub < u1; ub += 32) {
-        const int n_in = min(32, u1 - ub);
-        const uint32_t wl = lane < n_in ? __ldg(op.t_ucol + ub + lane) : 0u;
-        for (int t = 0; t < n_in; t += KT) {
-          float2 x[KT][NB];
-          uint32_t wd[KT];
-#pragma unroll
-          for (int u = 0; u < KT; ++u) {
-            wd[u] = __shfl_sync(0xffffffffu, wl, (t + u) & 31);
-            if (t + u < n_in) {
-              const float2* xp = pc + (size_t)(wd[u] & 0x0FFFFFFFu) * op.Rp;
-#pragma unroll
-              for (int b = 0; b < NB; ++b) x[u][b] = on ? __ldg(xp + 32 * b) : make_float2(0.f, 0.f);
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < KT; ++u) {
-            if (t + u >= n_in) break;
-            const uint32_t mask = wd[u] >> 28;
-#pragma unroll
-            for (int rr = 0; rr < 4; ++rr) {
-              if (!(mask & (1u << rr))) continue;
-              const float4 v = __ldg(op.pkt + sp);
-              float z1 = 0.f;
-              if constexpr (TRANSF) z1 = __ldg(op.mdt + sp);
-              ++sp;
-              const float m = qx * v.y + qy * v.z + qz * v.w;
-              const float a0 = ca * v.x;
-#pragma unroll
-              for (int b = 0; b < NB; ++b) {
-                float c = a0;
-                if constexpr (TRANSF) c = fmaf(cb[b], z1, c);
-                P[rr][b].x = fmaf(c, x[u][b].x, P[rr][b].x);
-                P[rr][b].y = fmaf(c, x[u][b].y, P[rr][b].y);
-                Q[rr][b].x = fmaf(m, x[u][b].x, Q[rr][b].x);
-                Q[rr][b].y = fmaf(m, x[u][b].y, Q[rr][b].y);
-              }
-            }
-          }
-        }
-      }
-      if (on) {
-#pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          if (rr >= nr) break;
-          const size_t rowoff = (size_t)(row0 + rr) * op.Rp;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            float2 y;
-            y.x = P[rr][b].x - cc[b] * Q[rr][b].y;
-            y.y = P[rr][b].y + cc[b] * Q[rr][b].x;
-            q[rowoff + c0 + 32 * b] = y;
-            float2 pv = __ldg(p + rowoff + c0 + 32 * b);
-            if constexpr (CONJ) pv.y = -pv.y;
-            accf[b].x = fmaf(pv.x, y.x, fmaf(-pv.y, y.y, accf[b].x));
-            accf[b].y = fmaf(pv.x, y.y, fmaf(pv.y, y.x, accf[b].y));
-          }
-        }
-      }
-      if (++cnt == 8) {
-        cnt = 0;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          acc[b].x += (double)accf[b].x;
-          acc[b].y += (double)accf[b].y;
-          accf[b] = make_float2(0.f, 0.f);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    acc[b].x += (double)accf[b].x;
-    acc[b].y += (double)accf[b].y;
-  }
-  block_partials<NB>(acc, on ? r0 : op.Rp, op.Rp, rs.part);
-  if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
-  if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
-  __syncthreads();
-  reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
-}
-
+// ---------------------------------------------------------------- plane gather
+// The packed FP32 planes (and MD) in the entry order of a tiling: out[k] = in[slot[k]].
 __global__ void k_gather_tile_planes(const int32_t* __restrict__ slot, int64_t nnz, const float4* __restrict__ pk32,
                                      const float* __restrict__ md32, float4* __restrict__ pkt, float* __restrict__ mdt) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
@@ -464,27 +323,4 @@ void launch_resid_sub(const OpArgs& op, const float2* d, double2* u, double2* r,
   })
 }
 
-}  // namespace bt
-
-namespace bt {
-template <int NBL, bool TRANSF, bool CONJ>
-static void spmm_tiled_t(const OpArgs& op, const float2* p, float2* q, const KrylovState& ks, RedScratch rs,
-                         cudaStream_t st) {
-  constexpr int NB = NBL < 2 ? NBL : 2;
-  dim3 grid(op.sp.nblk, ((op.R + 32 * NBL - 1) / (32 * NBL)) * (NBL / NB));
-  k_spmm_tiled<NBL, NB, TRANSF, CONJ><<<grid, 256, 0, st>>>(op, p, q, ks, rs);
-}
-void launch_spmm_krylov_f32_tiled(const OpArgs& op, const float2* p, float2* q, const KrylovState& ks,
-                                  RedScratch rs, int conj, int nb, int sms, cudaStream_t st) {
-  (void)sms;
-  BT_DISPATCH_NB(nb, {
-    if (op.transformed) {
-      if (conj) spmm_tiled_t<NB_, true, true>(op, p, q, ks, rs, st);
-      else spmm_tiled_t<NB_, true, false>(op, p, q, ks, rs, st);
-    } else {
-      if (conj) spmm_tiled_t<NB_, false, true>(op, p, q, ks, rs, st);
-      else spmm_tiled_t<NB_, false, false>(op, p, q, ks, rs, st);
-    }
-  })
-}
 }  // namespace bt

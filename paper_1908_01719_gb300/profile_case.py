@@ -2,7 +2,7 @@
 of a config on a chosen grid, a shortened PGSE sequence (a few time steps),
 mixed precision.  It prints the sizes and the counters of the run.
 
-  python -m paper_1908_01719_gb300.profile_case --config cfg4 --grid 64 --steps 2
+  python -m paper_1908_01719_gb300.profile_case --config cfg4 --grid 64 --steps 2 [--variant halo]
 """
 from __future__ import annotations
 
@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--steps", type=int, default=2, help="time steps (pulse on throughout)")
     ap.add_argument("--mode", default="mixed", choices=["mixed", "plain"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "row", "halo"],
+                    help="inner Krylov variant (auto: the autotuner's choice)")
     a = ap.parse_args()
     build()
     p = getattr(geom, a.config)(n=a.grid)
@@ -36,8 +38,12 @@ def main():
     p.TE = 2 * half * p.dt
     sim = Simulation(p)
     mode = bt.BT_MODE_MIXED if a.mode == "mixed" else bt.BT_MODE_PLAIN_FP64
-    S, err, stat, _ = sim.run(mode, flags=bt.BT_OPT_NO_GRAPH)
-    print(f"{a.config} grid {a.grid}: n_dof {sim.n_dof}, nnz {sim.nnz}, RHS {sim.R}, stats {sim.stats()}")
+    flags = bt.BT_OPT_NO_GRAPH | {"auto": 0, "row": bt.BT_OPT_VARIANT_ROW,
+                                  "halo": bt.BT_OPT_VARIANT_HALO}[a.variant]
+    S, err, stat, _ = sim.run(mode, flags=flags)
+    tuning = bt.bt_get_tuning(sim.ctx) if mode != bt.BT_MODE_PLAIN_FP64 else None
+    print(f"{a.config} grid {a.grid}: n_dof {sim.n_dof}, nnz {sim.nnz}, RHS {sim.R}, stats {sim.stats()}, "
+          f"tuning {tuning}")
     sim.close()
 
 
