@@ -204,7 +204,7 @@ void launch_resid0_df(const OpArgs& op, const float4* u, float4* r, const Refine
                       int nb, int sms, cudaStream_t st);
 void launch_resid_sub_df(const OpArgs& op, const float2* d, float4* u, float4* r, const RefineState& rf,
                          RedScratch rs, int nb, int sms, cudaStream_t st);
-// the same over the halo tiles (the halo-staged variant): mode 0 needs nb >= 2
+// the same over the halo tiles (the halo-staged variant)
 void resid_df_halo_prepare();
 bool resid_df_halo_available(int nb, int mode);
 void launch_resid0_df_halo(const OpArgs& op, const HaloArgs& h, const float4* u, float4* r, const RefineState& rf,

@@ -301,6 +301,13 @@ void launch_fill_u_df(const VecArgs& va, float4* u, cudaStream_t st) { k_fill_u_
 // row: 32 NB sizeof(TX) bytes (NB columns per lane in this block).
 namespace bt {
 
+template <int BYTES>
+__device__ __forceinline__ void cp_async_tx(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (BYTES == 16) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+
 template <int NBL, int NB, bool TRANSF, int MODE, class TX>
 __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h, const TX* __restrict__ x,
                                                           float4* __restrict__ u, float4* __restrict__ r,
@@ -347,28 +354,21 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
   if (__syncthreads_or(any)) {
     const int tb = h.seg_tile0[sg_], te = h.seg_tile0[sg_ + 1];
     for (int tau = tb + sk_; tau < te; tau += snb_) {
-      // ---- stage the gathered vector for the halo rows
+      // ---- stage the gathered vector for the halo rows (asynchronous copies;
+      // entries of inactive lanes are left unset and never used)
       const int ub = h.u0[tau], nu = h.u0[tau + 1] - ub;
-      for (int uu0 = warp; uu0 < nu; uu0 += 16) {
-        TX v[2][NB];
+      const int myrows = nu > warp ? (nu - warp + 7) / 8 : 0;  // <= 32 since umax <= 256
+      const uint32_t wl = lane < myrows ? __ldg(h.ucol + ub + warp + 8 * lane) : 0u;
+      for (int k = 0; k < myrows; ++k) {
+        const uint32_t w = __shfl_sync(0xffffffffu, wl, k);
+        const int uu = warp + 8 * k;
+        const size_t e = (size_t)(w & 0x7FFFFFFFu) * op.Rp + c0;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int uu = uu0 + 8 * k;
-          const size_t e = uu < nu ? (size_t)(__ldg(h.ucol + ub + uu) & 0x7FFFFFFFu) * op.Rp + c0 : 0;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            if (uu < nu && act[b]) v[k][b] = __ldg(x + e + 32 * b);
-            else v[k][b] = TX{};
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int uu = uu0 + 8 * k;
-          if (uu >= nu) break;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) xs_[(uu * NB + b) * 32 + lane] = v[k][b];
-        }
+        for (int b = 0; b < NB; ++b)
+          if (act[b]) cp_async_tx<sizeof(TX)>(xs_ + (uu * NB + b) * 32 + lane, x + e + 32 * b);
       }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       __syncthreads();
       // ---- double-float sums of the owned rows
       const int ra = h.t_r0[tau], rz = h.t_r0[tau + 1];
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
 // umax rows of 32 NBL float2
 template <int NBL, int MODE>
 constexpr int df_halo_nb() {
-  return MODE == 0 ? NBL / 2 : (NBL < 2 ? NBL : 2);
+  return MODE == 0 ? (NBL < 2 ? 1 : NBL / 2) : (NBL < 2 ? NBL : 2);
 }
 
 template <int NBL, int MODE, class TX>
@@ -515,17 +515,23 @@ static void df_halo_attr() {
 void resid_df_halo_prepare() {
   df_halo_attr<4, 0, float4>();
   df_halo_attr<2, 0, float4>();
+  df_halo_attr<1, 0, float4>();
   df_halo_attr<4, 1, float2>();
   df_halo_attr<2, 1, float2>();
   df_halo_attr<1, 1, float2>();
 }
 
-bool resid_df_halo_available(int nb, int mode) { return !(mode == 0 && nb == 1); }
+bool resid_df_halo_available(int nb, int mode) {
+  (void)nb;
+  (void)mode;
+  return true;
+}
 
 void launch_resid0_df_halo(const OpArgs& op, const HaloArgs& h, const float4* u, float4* r, const RefineState& rf,
                            RedScratch rs, int nb, cudaStream_t st) {
   if (nb == 4) resid_df_halo_t<4, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
-  else resid_df_halo_t<2, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
+  else if (nb == 2) resid_df_halo_t<2, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
+  else resid_df_halo_t<1, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
 }
 
 void launch_resid_sub_df_halo(const OpArgs& op, const HaloArgs& h, const float2* d, float4* u, float4* r,

@@ -3,15 +3,19 @@
 //
 // Rows are grouped into tiles along a Morton curve of their node coordinates
 // (HaloTiles, built on the host).  A block takes one tile and one slice of
-// 32*NB right-hand sides:
+// 32*NB right-hand sides (NB <= 2 columns per lane; a wider vector layout is
+// split over blockIdx.y):
 //   1. stage: for every halo row j of the tile (the union of the tile rows'
-//      columns) form p_j = z_j + beta p_prev_j for the slice and keep it in
-//      shared memory; rows the tile owns also store p_j and apply the x update
-//      x_j += alpha_prev p_prev_j that the previous iteration left pending;
+//      columns) copy z_j and, where needed, p_prev_j of the slice into shared
+//      memory with asynchronous copies (cp.async: no register round trip, all
+//      of a tile's copies in flight at once), then form p_j = z_j + beta p_prev_j
+//      in place;
 //   2. apply: for every owned row, q_i = sum_j L_ij p_j from shared memory
 //      (L_ij = a A0_ij + bq2 q_r^2 MD_ij + i cq q_r (qhat . Pd)_ij, the step
-//      operator of Appendix B / Appendix A built on the fly), and the partial
-//      inner product <p, q>;
+//      operator of Appendix B / Appendix A built on the fly), the partial
+//      inner product <p, q>, the store of p_i and the x update
+//      x_i += alpha_prev p_prev_i that the previous iteration left pending
+//      (its load is issued before the row's sums, so its latency is hidden);
 //   3. the last block forms alpha = rho / <p, q>, marks the x update of every
 //      active system pending and flips the p-buffer parity.
 // On the Kuhn stencil a tile of ~20 rows has ~100 halo rows, so each X row is
@@ -23,20 +27,35 @@
 
 namespace bt {
 
-constexpr int HALO_SMEM_BUDGET = 96 * 1024;  // bytes of staged p per block (2 blocks / SM)
+constexpr int HALO_SMEM_BUDGET = 96 * 1024;  // staged z and p_prev per block (2 blocks / SM)
 
-size_t halo_smem_bytes(int nb, int umax) { return (size_t)umax * 32 * nb * sizeof(float2); }
+// columns per lane one block handles for a vector layout of nb columns per lane
+__host__ __device__ constexpr int halo_nb(int nb) { return nb < 2 ? nb : 2; }
+size_t halo_smem_bytes(int nb, int umax) { return (size_t)umax * 2 * 32 * halo_nb(nb) * sizeof(float2); }
 
-template <int NB, bool TRANSF, bool CONJ>
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int NBL, int NB, bool TRANSF, bool CONJ>
 __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, const float2* __restrict__ z,
                                                       float2* __restrict__ pA, float2* __restrict__ pB,
                                                       float2* __restrict__ x, float2* __restrict__ q,
                                                       KrylovState ks, RedScratch rs) {
   if (*ks.n_active == 0) return;
-  extern __shared__ float2 sp_[];  // [umax][NB][32]
+  extern __shared__ float2 sh_[];
+  float2* sz = sh_;                        // [umax][NB][32]: z, then p = z + beta p_prev
+  float2* spv = sh_ + h.umax * NB * 32;    // [umax][NB][32]: p_prev
+  constexpr int NSPLIT = NBL / NB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r0 = (blockIdx.y * 32 + lane) * NB;  // first system of this lane
-  const int c0 = blockIdx.y * 32 * NB + lane;     // its first column (stride 32)
+  const int tile = blockIdx.y / NSPLIT, part = blockIdx.y % NSPLIT;
+  const int r0 = (tile * 32 + lane) * NBL + part * NB;  // first system of this lane
+  const int c0 = tile * 32 * NBL + lane + 32 * part * NB;  // its first column (stride 32)
   const bool on = r0 < op.R;
   const int par = *ks.par;
   const float2* __restrict__ src = par ? pB : pA;
@@ -77,46 +96,35 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
   if (__syncthreads_or(any)) {
     const int tb = h.seg_tile0[sg_], te = h.seg_tile0[sg_ + 1];
     for (int tau = tb + sk_; tau < te; tau += snb_) {
-      // ---- 1. stage p = z + beta p_prev for the halo rows of the slice
+      // ---- 1. stage z and p_prev of the halo rows (warp w takes rows w, w + 8, ...)
       const int ub = h.u0[tau], nu = h.u0[tau + 1] - ub;
-      constexpr int US = 2;  // halo rows per warp trip (loads in flight: 2 US NB)
-      for (int u = warp; u < nu; u += 8 * US) {
-        uint32_t w[US];
-        float2 zv[US][NB], pv[US][NB];
+      const int myrows = nu > warp ? (nu - warp + 7) / 8 : 0;  // <= 32 since umax <= 256
+      const uint32_t wl = lane < myrows ? __ldg(h.ucol + ub + warp + 8 * lane) : 0u;
+      for (int k = 0; k < myrows; ++k) {
+        const uint32_t w = __shfl_sync(0xffffffffu, wl, k);
+        const int uu = warp + 8 * k;
+        const size_t e = (size_t)(w & 0x7FFFFFFFu) * op.Rp + c0;
+        const bool own = (w >> 31) != 0;
 #pragma unroll
-        for (int k = 0; k < US; ++k) {
-          const int uu = u + 8 * k;
-          w[k] = uu < nu ? __ldg(h.ucol + ub + uu) : 0u;
-          const size_t e = (size_t)(w[k] & 0x7FFFFFFFu) * op.Rp + c0;
-          const bool own = (w[k] >> 31) != 0;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            zv[k][b] = (uu < nu && act[b]) ? __ldg(z + e + 32 * b) : make_float2(0.f, 0.f);
-            pv[k][b] = (uu < nu && (usep[b] || (own && pend[b]))) ? __ldg(src + e + 32 * b) : make_float2(0.f, 0.f);
-          }
+        for (int b = 0; b < NB; ++b) {
+          if (act[b]) cp_async8(sz + (uu * NB + b) * 32 + lane, z + e + 32 * b);
+          if (usep[b] || (own && pend[b])) cp_async8(spv + (uu * NB + b) * 32 + lane, src + e + 32 * b);
         }
+      }
+      cp_async_wait_all();
+      // each thread converts exactly the entries it copied: no barrier needed in between
+      for (int k = 0; k < myrows; ++k) {
+        const int uu = warp + 8 * k;
 #pragma unroll
-        for (int k = 0; k < US; ++k) {
-          const int uu = u + 8 * k;
-          if (uu >= nu) break;
-          const size_t e = (size_t)(w[k] & 0x7FFFFFFFu) * op.Rp + c0;
-          const bool own = (w[k] >> 31) != 0;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            float2 pn = zv[k][b];
-            pn.x = fmaf(beta[b].x, pv[k][b].x, fmaf(-beta[b].y, pv[k][b].y, pn.x));
-            pn.y = fmaf(beta[b].x, pv[k][b].y, fmaf(beta[b].y, pv[k][b].x, pn.y));
-            sp_[(uu * NB + b) * 32 + lane] = pn;
-            if (own) {
-              if (act[b]) dst[e + 32 * b] = pn;
-              if (pend[b]) {
-                float2 xv = x[e + 32 * b];
-                xv.x = fmaf(alp[b].x, pv[k][b].x, fmaf(-alp[b].y, pv[k][b].y, xv.x));
-                xv.y = fmaf(alp[b].x, pv[k][b].y, fmaf(alp[b].y, pv[k][b].x, xv.y));
-                x[e + 32 * b] = xv;
-              }
-            }
+        for (int b = 0; b < NB; ++b) {
+          const int ix = (uu * NB + b) * 32 + lane;
+          float2 pn = act[b] ? sz[ix] : make_float2(0.f, 0.f);
+          if (usep[b]) {
+            const float2 pv = spv[ix];
+            pn.x = fmaf(beta[b].x, pv.x, fmaf(-beta[b].y, pv.y, pn.x));
+            pn.y = fmaf(beta[b].x, pv.y, fmaf(beta[b].y, pv.x, pn.y));
           }
+          sz[ix] = pn;
         }
       }
       __syncthreads();
@@ -125,6 +133,11 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
       for (int k = ra + warp; k < rz; k += 8) {
         const int row = __ldg(h.rows + k);
         const int e0 = __ldg(h.rowe + k), e1 = __ldg(h.rowe + k + 1);
+        const int lo = __ldg(h.rowl + k);
+        const size_t erow = (size_t)row * op.Rp + c0;
+        float2 xv[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) xv[b] = pend[b] ? x[erow + 32 * b] : make_float2(0.f, 0.f);
         float2 P[NB], Q[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) P[b] = Q[b] = make_float2(0.f, 0.f);
@@ -145,31 +158,39 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
             if (e + u >= e1) break;
             const float m = qx * v[u].y + qy * v[u].z + qz * v[u].w;
             const float a0 = ca * v[u].x;
-            const float2* xs = sp_ + l[u] * NB * 32 + lane;
+            const float2* xs = sz + l[u] * NB * 32 + lane;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-              const float2 xv = xs[32 * b];
+              const float2 xx = xs[32 * b];
               float c = a0;
               if constexpr (TRANSF) c = fmaf(cb[b], z1[u], c);
-              P[b].x = fmaf(c, xv.x, P[b].x);
-              P[b].y = fmaf(c, xv.y, P[b].y);
-              Q[b].x = fmaf(m, xv.x, Q[b].x);
-              Q[b].y = fmaf(m, xv.y, Q[b].y);
+              P[b].x = fmaf(c, xx.x, P[b].x);
+              P[b].y = fmaf(c, xx.y, P[b].y);
+              Q[b].x = fmaf(m, xx.x, Q[b].x);
+              Q[b].y = fmaf(m, xx.y, Q[b].y);
             }
           }
         }
-        const float2* ps = sp_ + (int)__ldg(h.rowl + k) * NB * 32 + lane;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          if (!act[b]) continue;
-          float2 y;
-          y.x = P[b].x - cc[b] * Q[b].y;
-          y.y = P[b].y + cc[b] * Q[b].x;
-          q[(size_t)row * op.Rp + c0 + 32 * b] = y;
-          float2 pv = ps[32 * b];
-          if constexpr (CONJ) pv.y = -pv.y;
-          accf[b].x = fmaf(pv.x, y.x, fmaf(-pv.y, y.y, accf[b].x));
-          accf[b].y = fmaf(pv.x, y.y, fmaf(pv.y, y.x, accf[b].y));
+          const int ix = (lo * NB + b) * 32 + lane;
+          if (act[b]) {
+            float2 y;
+            y.x = P[b].x - cc[b] * Q[b].y;
+            y.y = P[b].y + cc[b] * Q[b].x;
+            q[erow + 32 * b] = y;
+            float2 pv = sz[ix];
+            dst[erow + 32 * b] = pv;
+            if constexpr (CONJ) pv.y = -pv.y;
+            accf[b].x = fmaf(pv.x, y.x, fmaf(-pv.y, y.y, accf[b].x));
+            accf[b].y = fmaf(pv.x, y.y, fmaf(pv.y, y.x, accf[b].y));
+          }
+          if (pend[b]) {
+            const float2 pp = spv[ix];
+            xv[b].x = fmaf(alp[b].x, pp.x, fmaf(-alp[b].y, pp.y, xv[b].x));
+            xv[b].y = fmaf(alp[b].x, pp.y, fmaf(alp[b].y, pp.x, xv[b].y));
+            x[erow + 32 * b] = xv[b];
+          }
         }
         if (++cnt == 16) {
           cnt = 0;
@@ -200,9 +221,9 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
   if (threadIdx.x == 0) *ks.par = par ^ 1;
 }
 
-template <int NB, bool TRANSF, bool CONJ>
+template <int NBL, bool TRANSF, bool CONJ>
 static void halo_attr() {
-  cudaFuncSetAttribute(k_spmm_halo<NB, TRANSF, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_spmm_halo<NBL, halo_nb(NBL), TRANSF, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        HALO_SMEM_BUDGET);
 }
 // raise the dynamic shared memory limit of every instance (outside any capture)
@@ -212,11 +233,13 @@ void halo_prepare() {
   halo_attr<4, false, false>(); halo_attr<4, false, true>(); halo_attr<4, true, false>(); halo_attr<4, true, true>();
 }
 
-template <int NB, bool TRANSF, bool CONJ>
+template <int NBL, bool TRANSF, bool CONJ>
 static void halo_t(const OpArgs& op, const HaloArgs& h, const float2* z, float2* pA, float2* pB, float2* x,
                    float2* q, const KrylovState& ks, RedScratch rs, cudaStream_t st) {
-  dim3 grid(op.sp.nblk, (op.R + 32 * NB - 1) / (32 * NB));
-  k_spmm_halo<NB, TRANSF, CONJ><<<grid, 256, halo_smem_bytes(NB, h.umax), st>>>(op, h, z, pA, pB, x, q, ks, rs);
+  constexpr int NB = halo_nb(NBL);
+  dim3 grid(op.sp.nblk, ((op.R + 32 * NBL - 1) / (32 * NBL)) * (NBL / NB));
+  k_spmm_halo<NBL, NB, TRANSF, CONJ><<<grid, 256, halo_smem_bytes(NBL, h.umax), st>>>(op, h, z, pA, pB, x, q, ks,
+                                                                                       rs);
 }
 
 void launch_spmm_halo(const OpArgs& op, const HaloArgs& h, const float2* z, float2* pA, float2* pB, float2* x,
