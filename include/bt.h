@@ -89,7 +89,8 @@ bt_status bt_get_dofmap(const bt_ctx* ctx, int32_t* dof_node, int32_t* dof_cmpt)
 bt_status bt_get_pattern(const bt_ctx* ctx, int64_t* row_ptr, int32_t* col);
 /* The halo tiles the shared-memory Krylov apply uses (host-side build, no GPU
  * needed): rows in Morton order of their node coordinates, cut into tiles of
- * at most 128 rows whose columns span at most `umax` distinct rows.  With all
+ * at most 128 rows and 448 entries whose columns span at most `umax`
+ * distinct rows.  With all
  * array pointers NULL only the sizes are returned (n_tiles, n_halo = total
  * halo entries).  Otherwise (caller-allocated): r0 [n_tiles+1] offsets into
  * rows; rows [n_dof] owned rows tile by tile; rowe [n_dof+1] first entry of

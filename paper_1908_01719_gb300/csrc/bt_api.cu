@@ -191,7 +191,7 @@ bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t
   if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_get_halo_tiles: no mesh");
   if (umax < 16 || umax > 65535) return fail(ctx, BT_EINVAL, "bt_get_halo_tiles: umax outside [16, 65535]");
   HaloTiles t;
-  build_halo_tiles(ctx->mesh, ctx->seg_row0, umax, 128, t);
+  build_halo_tiles(ctx->mesh, ctx->seg_row0, umax, HALO_TMAX, HALO_EMAX, t);
   if (t.too_wide) return fail(ctx, BT_EINVAL, "bt_get_halo_tiles: a row has more than umax columns");
   if (n_tiles) *n_tiles = (int64_t)t.r0.size() - 1;
   if (n_halo) *n_halo = (int64_t)t.ucol.size();
@@ -488,7 +488,7 @@ namespace {
 // plane values in halo-entry order.  Sets ctx->halo_ok = false when a row is
 // wider than umax (the halo iteration is then not offered).
 bt_status ensure_halo(bt_ctx* ctx, int nb, cudaStream_t st) {
-  const int umax = (int)std::min<size_t>(65535, (96 * 1024) / halo_smem_bytes(nb, 1));
+  const int umax = halo_umax(nb);
   if (!ctx->halo_attr) {
     halo_prepare();
     resid_df_halo_prepare();
@@ -497,7 +497,7 @@ bt_status ensure_halo(bt_ctx* ctx, int nb, cudaStream_t st) {
   }
   if (ctx->halo_for != ctx->seg_row0 || ctx->halo_umax != umax) {
     HaloTiles t;
-    build_halo_tiles(ctx->mesh, ctx->seg_row0, umax, 128, t);
+    build_halo_tiles(ctx->mesh, ctx->seg_row0, umax, HALO_TMAX, HALO_EMAX, t);
     ctx->halo_for = ctx->seg_row0;
     ctx->halo_umax = umax;
     ctx->halo_ok = !t.too_wide;
@@ -508,7 +508,10 @@ bt_status ensure_halo(bt_ctx* ctx, int nb, cudaStream_t st) {
     CK(upload(ctx->h_rowe, t.rowe, st));
     CK(upload(ctx->h_rowl, t.rowl, st));
     CK(upload(ctx->h_u0, t.u0, st));
+    CK(upload(ctx->h_e0, t.e0, st));
     CK(upload(ctx->h_ucol, t.ucol, st));
+    t.lidx.push_back(0);  // padding: the kernels copy local indices in 4-byte words
+    t.lidx.push_back(0);
     CK(upload(ctx->h_lidx, t.lidx, st));
     CK(upload(ctx->h_slot, t.slot, st));
     CK(upload(ctx->h_seg0, t.seg_tile0, st));
@@ -526,8 +529,8 @@ bt_status ensure_halo(bt_ctx* ctx, int nb, cudaStream_t st) {
 }
 
 HaloArgs halo_args(const bt_ctx* ctx) {
-  return HaloArgs{ctx->h_r0.p,  ctx->h_rows.p, ctx->h_rowe.p, ctx->h_rowl.p, ctx->h_u0.p, ctx->h_ucol.p,
-                  ctx->h_lidx.p, ctx->h_pkt.p, ctx->h_mdt.p, ctx->h_seg0.p, ctx->halo_umax};
+  return HaloArgs{ctx->h_r0.p,   ctx->h_rows.p, ctx->h_rowe.p, ctx->h_rowl.p, ctx->h_u0.p,  ctx->h_e0.p,
+                  ctx->h_ucol.p, ctx->h_lidx.p, ctx->h_pkt.p,  ctx->h_mdt.p,  ctx->h_seg0.p, ctx->halo_umax};
 }
 
 // Autotuner: time one Krylov iteration of each variant on the real pattern

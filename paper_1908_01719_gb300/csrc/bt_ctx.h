@@ -59,7 +59,7 @@ struct bt_ctx {
   int nblk = 0;
   int64_t planes_version = 0;  // bumped by every assembly
   // halo tiles of the shared-memory Krylov apply (one segmentation, one umax)
-  bt::DBuf<int32_t> h_r0, h_rows, h_rowe, h_u0, h_seg0, h_slot;
+  bt::DBuf<int32_t> h_r0, h_rows, h_rowe, h_u0, h_e0, h_seg0, h_slot;
   bt::DBuf<uint16_t> h_rowl, h_lidx;
   bt::DBuf<uint32_t> h_ucol;
   bt::DBuf<float4> h_pkt;

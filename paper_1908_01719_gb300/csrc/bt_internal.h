@@ -50,13 +50,15 @@ int build_host_mesh(HostMesh& m, std::string& msg);
 
 // Halo tiles for the shared-memory SpMM: rows of each segment in Morton order
 // of their node coordinates, cut greedily into tiles of at most `tmax` rows
-// whose columns span at most `umax` distinct rows of X (the tile's halo).
+// and `emax` entries whose columns span at most `umax` distinct rows of X
+// (the tile's halo).
 struct HaloTiles {
   int umax = 0;
   bool too_wide = false;          // some row has more than umax columns
   std::vector<int32_t> r0;        // [ntiles + 1] offsets into rows
   std::vector<int32_t> rows;      // [n] owned rows, tile by tile
   std::vector<int32_t> rowe;      // [n + 1] first entry of each owned row
+  std::vector<int32_t> e0;        // [ntiles + 1] first entry of each tile
   std::vector<uint16_t> rowl;     // [n] local index of each owned row in its halo
   std::vector<int32_t> u0;        // [ntiles + 1] offsets into ucol
   std::vector<uint32_t> ucol;     // halo rows, ascending; bit 31: owned by the tile
@@ -64,7 +66,14 @@ struct HaloTiles {
   std::vector<int32_t> slot;      // [nnz] CSR slot of each entry
   std::vector<int32_t> seg_tile0; // [G + 1]
 };
-void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, int umax, int tmax, HaloTiles& t);
+void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, int umax, int tmax, int emax,
+                      HaloTiles& t);
+// tile limits of the halo kernels: rows and entries per tile, and the shared
+// memory (bytes) one block of the halo apply may use for its staged rows and
+// entries
+constexpr int HALO_TMAX = 128;
+constexpr int HALO_EMAX = 448;
+constexpr int HALO_SMEM_BUDGET = 96 * 1024;
 
 // ---------------------------------------------------------------- device helpers
 template <class T>

@@ -137,6 +137,7 @@ struct HaloArgs {
   const int32_t* rowe;      // [n + 1] first entry of each owned row (tile order)
   const uint16_t* rowl;     // local halo index of each owned row
   const int32_t* u0;        // [ntiles + 1] offsets into ucol
+  const int32_t* e0;        // [ntiles + 1] first entry of each tile
   const uint32_t* ucol;     // halo rows, bit 31 = owned
   const uint16_t* lidx;     // [nnz] local column index of each entry
   const float4* pkt;        // [nnz] {A0, d0, d1, d2} in tile-entry order
@@ -247,6 +248,7 @@ void launch_gram(const OpArgs& op, const VecArgs& va, const float2* r, const flo
 // and flush_x applies the last deferred x update after the loop.
 void halo_prepare();
 size_t halo_smem_bytes(int nb, int umax);
+int halo_umax(int nb);  // halo rows per tile for a vector layout of nb columns per lane
 void launch_spmm_halo(const OpArgs& op, const HaloArgs& h, const float2* z, float2* pA, float2* pB, float2* x,
                       float2* q, const KrylovState& ks, RedScratch rs, int conj, int nb, cudaStream_t st);
 void launch_krylov_init_z(const OpArgs& op, const VecArgs& va, const void* rres, int df, const double* scale,

@@ -354,7 +354,8 @@ static uint64_t spread3(uint64_t v) {
   return v;
 }
 
-void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, int umax, int tmax, HaloTiles& t) {
+void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, int umax, int tmax, int emax,
+                      HaloTiles& t) {
   t = HaloTiles();
   t.umax = umax;
   const int G = (int)seg_row0.size() - 1;
@@ -391,23 +392,27 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
       order.emplace_back(code, (int32_t)r);
     }
     std::sort(order.begin(), order.end());
-    // greedy tiles along the curve: at most tmax rows and umax distinct columns
+    // greedy tiles along the curve: at most tmax rows, umax distinct columns
+    // and emax entries
     size_t i = 0;
     while (i < order.size()) {
       cur.clear();
       uc.clear();
+      int64_t ne = 0;
       for (; i < order.size() && (int)cur.size() < tmax; ++i) {
         const int32_t r = order[i].second;
+        const int64_t rn = m.row_ptr[r + 1] - m.row_ptr[r];
         int fresh = 0;
         for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k) fresh += mark[m.col[k]] != tid;
-        if ((int)uc.size() + fresh > umax) {
+        if ((int)uc.size() + fresh > umax || ne + rn > emax) {
           if (cur.empty()) {
-            // a single row wider than umax cannot be staged
+            // a single row wider than umax (or emax) cannot be staged
             t.too_wide = true;
             return;
           }
           break;
         }
+        ne += rn;
         for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k)
           if (mark[m.col[k]] != tid) {
             mark[m.col[k]] = tid;
@@ -419,6 +424,7 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
       for (size_t u = 0; u < uc.size(); ++u) lpos[uc[u]] = (int32_t)u;
       t.r0.push_back((int32_t)t.rows.size());
       t.u0.push_back((int32_t)t.ucol.size());
+      t.e0.push_back((int32_t)t.lidx.size());
       for (int32_t c : uc) t.ucol.push_back((uint32_t)c);
       for (int32_t r : cur) {
         t.ucol[t.u0.back() + lpos[r]] |= 0x80000000u;  // owned by this tile
@@ -436,6 +442,7 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
   t.seg_tile0.push_back((int32_t)t.r0.size());
   t.r0.push_back((int32_t)t.rows.size());
   t.u0.push_back((int32_t)t.ucol.size());
+  t.e0.push_back((int32_t)t.lidx.size());
   t.rowe.push_back((int32_t)t.lidx.size());
 }
 

@@ -27,19 +27,36 @@
 
 namespace bt {
 
-constexpr int HALO_SMEM_BUDGET = 96 * 1024;  // staged z and p_prev per block (2 blocks / SM)
-
 // columns per lane one block handles for a vector layout of nb columns per lane
 __host__ __device__ constexpr int halo_nb(int nb) { return nb < 2 ? nb : 2; }
-size_t halo_smem_bytes(int nb, int umax) { return (size_t)umax * 2 * 32 * halo_nb(nb) * sizeof(float2); }
+// staged entries of one tile: planes (float4), MD (float), local indices (uint16 in 4-byte words)
+constexpr size_t HALO_ENTRY_BYTES = (size_t)HALO_EMAX * 16 + (size_t)HALO_EMAX * 4 + ((size_t)HALO_EMAX + 4) * 2;
+size_t halo_smem_bytes(int nb, int umax) {
+  return (size_t)umax * 2 * 32 * halo_nb(nb) * sizeof(float2) + HALO_ENTRY_BYTES;
+}
+int halo_umax(int nb) {
+  return (int)((HALO_SMEM_BUDGET - HALO_ENTRY_BYTES) / ((size_t)2 * 32 * halo_nb(nb) * sizeof(float2)));
+}
 
-__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+  if constexpr (BYTES == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else if constexpr (BYTES == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// tile descriptor: halo rows [u0, u1), owned rows [r0, r1), entries [e0, e1)
+struct TileDesc {
+  int u0, u1, r0, r1, e0, e1;
+};
+__device__ __forceinline__ TileDesc tile_desc(const HaloArgs& h, int tau) {
+  return TileDesc{__ldg(h.u0 + tau), __ldg(h.u0 + tau + 1), __ldg(h.t_r0 + tau),
+                  __ldg(h.t_r0 + tau + 1), __ldg(h.e0 + tau), __ldg(h.e0 + tau + 1)};
 }
 
 template <int NBL, int NB, bool TRANSF, bool CONJ>
@@ -48,13 +65,16 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
                                                       float2* __restrict__ x, float2* __restrict__ q,
                                                       KrylovState ks, RedScratch rs) {
   if (*ks.n_active == 0) return;
-  extern __shared__ float2 sh_[];
-  float2* sz = sh_;                        // [umax][NB][32]: z, then p = z + beta p_prev
-  float2* spv = sh_ + h.umax * NB * 32;    // [umax][NB][32]: p_prev
+  extern __shared__ float4 sh4_[];
+  float2* sz = reinterpret_cast<float2*>(sh4_);     // [umax][NB][32]: z, then p = z + beta p_prev
+  float2* spv = sz + h.umax * NB * 32;               // [umax][NB][32]: p_prev
+  float4* spk = reinterpret_cast<float4*>(spv + h.umax * NB * 32);  // [HALO_EMAX] planes
+  float* smd = reinterpret_cast<float*>(spk + HALO_EMAX);           // [HALO_EMAX] MD
+  uint32_t* sli = reinterpret_cast<uint32_t*>(smd + HALO_EMAX);     // local indices, 2 per word
   constexpr int NSPLIT = NBL / NB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tile = blockIdx.y / NSPLIT, part = blockIdx.y % NSPLIT;
-  const int r0 = (tile * 32 + lane) * NBL + part * NB;  // first system of this lane
+  const int r0 = (tile * 32 + lane) * NBL + part * NB;     // first system of this lane
   const int c0 = tile * 32 * NBL + lane + 32 * part * NB;  // its first column (stride 32)
   const bool on = r0 < op.R;
   const int par = *ks.par;
@@ -95,11 +115,13 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
   int cnt = 0;
   if (__syncthreads_or(any)) {
     const int tb = h.seg_tile0[sg_], te = h.seg_tile0[sg_ + 1];
-    for (int tau = tb + sk_; tau < te; tau += snb_) {
-      // ---- 1. stage z and p_prev of the halo rows (warp w takes rows w, w + 8, ...)
-      const int ub = h.u0[tau], nu = h.u0[tau + 1] - ub;
-      const int myrows = nu > warp ? (nu - warp + 7) / 8 : 0;  // <= 32 since umax <= 256
-      const uint32_t wl = lane < myrows ? __ldg(h.ucol + ub + warp + 8 * lane) : 0u;
+    int tau = tb + sk_;
+    TileDesc cur = tau < te ? tile_desc(h, tau) : TileDesc{0, 0, 0, 0, 0, 0};
+    // halo rows of this warp (w, w + 8, ...): <= 32 since umax <= 256
+    int myrows = cur.u1 - cur.u0 > warp ? (cur.u1 - cur.u0 - warp + 7) / 8 : 0;
+    uint32_t wl = lane < myrows ? __ldg(h.ucol + cur.u0 + warp + 8 * lane) : 0u;
+    for (; tau < te; tau += snb_) {
+      // ---- 1. asynchronous copies: z and p_prev of the halo rows, the tile's entries
       for (int k = 0; k < myrows; ++k) {
         const uint32_t w = __shfl_sync(0xffffffffu, wl, k);
         const int uu = warp + 8 * k;
@@ -107,12 +129,31 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
         const bool own = (w >> 31) != 0;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          if (act[b]) cp_async8(sz + (uu * NB + b) * 32 + lane, z + e + 32 * b);
-          if (usep[b] || (own && pend[b])) cp_async8(spv + (uu * NB + b) * 32 + lane, src + e + 32 * b);
+          if (act[b]) cp_async<8>(sz + (uu * NB + b) * 32 + lane, z + e + 32 * b);
+          if (usep[b] || (own && pend[b])) cp_async<8>(spv + (uu * NB + b) * 32 + lane, src + e + 32 * b);
         }
       }
+      const int ne = cur.e1 - cur.e0;  // <= HALO_EMAX (tile builder)
+      for (int t = threadIdx.x; t < ne; t += blockDim.x) {
+        cp_async<16>(spk + t, h.pkt + cur.e0 + t);
+        if constexpr (TRANSF) cp_async<4>(smd + t, h.mdt + cur.e0 + t);
+      }
+      const int w0 = cur.e0 >> 1, nw = ((cur.e1 + 1) >> 1) - w0;  // the index array is padded
+      for (int t = threadIdx.x; t < nw; t += blockDim.x)
+        cp_async<4>(sli + t, reinterpret_cast<const uint32_t*>(h.lidx) + w0 + t);
+      const int loff = cur.e0 & 1;
+      // owned rows of this warp (lane-parallel metadata; used after the barrier)
+      const int nown = cur.r1 - cur.r0 > warp ? (cur.r1 - cur.r0 - warp + 7) / 8 : 0;  // <= 16
+      const int ko = cur.r0 + warp + 8 * lane;
+      const int m_row = lane < nown ? __ldg(h.rows + ko) : 0;
+      const int m_e0 = lane < nown ? __ldg(h.rowe + ko) - cur.e0 : 0;
+      const int m_e1 = lane < nown ? __ldg(h.rowe + ko + 1) - cur.e0 : 0;
+      const int m_lo = lane < nown ? (int)__ldg(h.rowl + ko) : 0;
+      // next tile's descriptor while the copies are in flight
+      const bool more = tau + snb_ < te;
+      const TileDesc nxt = more ? tile_desc(h, tau + snb_) : cur;
       cp_async_wait_all();
-      // each thread converts exactly the entries it copied: no barrier needed in between
+      // p = z + beta p_prev in place; each thread converts exactly what it copied
       for (int k = 0; k < myrows; ++k) {
         const int uu = warp + 8 * k;
 #pragma unroll
@@ -127,13 +168,16 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
           sz[ix] = pn;
         }
       }
+      // next tile's halo rows (loads in flight during the sums below)
+      const int myrows_n = more ? (nxt.u1 - nxt.u0 > warp ? (nxt.u1 - nxt.u0 - warp + 7) / 8 : 0) : 0;
+      const uint32_t wl_n = lane < myrows_n ? __ldg(h.ucol + nxt.u0 + warp + 8 * lane) : 0u;
       __syncthreads();
-      // ---- 2. q = L p for the owned rows, from shared memory
-      const int ra = h.t_r0[tau], rz = h.t_r0[tau + 1];
-      for (int k = ra + warp; k < rz; k += 8) {
-        const int row = __ldg(h.rows + k);
-        const int e0 = __ldg(h.rowe + k), e1 = __ldg(h.rowe + k + 1);
-        const int lo = __ldg(h.rowl + k);
+      // ---- 2. q = L p for the owned rows, everything from shared memory
+      const uint16_t* sl16 = reinterpret_cast<const uint16_t*>(sli) + loff;
+      for (int kk = 0; kk < nown; ++kk) {
+        const int row = __shfl_sync(0xffffffffu, m_row, kk);
+        const int e0 = __shfl_sync(0xffffffffu, m_e0, kk), e1 = __shfl_sync(0xffffffffu, m_e1, kk);
+        const int lo = __shfl_sync(0xffffffffu, m_lo, kk);
         const size_t erow = (size_t)row * op.Rp + c0;
         float2 xv[NB];
 #pragma unroll
@@ -141,34 +185,24 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
         float2 P[NB], Q[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) P[b] = Q[b] = make_float2(0.f, 0.f);
-        constexpr int KU = 4;
-        for (int e = e0; e < e1; e += KU) {
-          float4 v[KU];
-          int l[KU];
-          float z1[KU];
+#pragma unroll 2
+        for (int e = e0; e < e1; ++e) {
+          const float4 v = spk[e];
+          const int l = sl16[e];
+          const float m = qx * v.y + qy * v.z + qz * v.w;
+          float a0 = ca * v.x;
+          float z1 = 0.f;
+          if constexpr (TRANSF) z1 = smd[e];
+          const float2* xs = sz + l * NB * 32 + lane;
 #pragma unroll
-          for (int u = 0; u < KU; ++u) {
-            const int ee = min(e + u, e1 - 1);
-            v[u] = __ldg(h.pkt + ee);
-            l[u] = __ldg(h.lidx + ee);
-            z1[u] = TRANSF ? __ldg(h.mdt + ee) : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < KU; ++u) {
-            if (e + u >= e1) break;
-            const float m = qx * v[u].y + qy * v[u].z + qz * v[u].w;
-            const float a0 = ca * v[u].x;
-            const float2* xs = sz + l[u] * NB * 32 + lane;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-              const float2 xx = xs[32 * b];
-              float c = a0;
-              if constexpr (TRANSF) c = fmaf(cb[b], z1[u], c);
-              P[b].x = fmaf(c, xx.x, P[b].x);
-              P[b].y = fmaf(c, xx.y, P[b].y);
-              Q[b].x = fmaf(m, xx.x, Q[b].x);
-              Q[b].y = fmaf(m, xx.y, Q[b].y);
-            }
+          for (int b = 0; b < NB; ++b) {
+            const float2 xx = xs[32 * b];
+            float c = a0;
+            if constexpr (TRANSF) c = fmaf(cb[b], z1, c);
+            P[b].x = fmaf(c, xx.x, P[b].x);
+            P[b].y = fmaf(c, xx.y, P[b].y);
+            Q[b].x = fmaf(m, xx.x, Q[b].x);
+            Q[b].y = fmaf(m, xx.y, Q[b].y);
           }
         }
 #pragma unroll
@@ -202,7 +236,10 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
           }
         }
       }
-      __syncthreads();  // the next tile overwrites the staged rows
+      __syncthreads();  // the next tile overwrites the staged rows and entries
+      cur = nxt;
+      myrows = myrows_n;
+      wl = wl_n;
     }
   }
 #pragma unroll

@@ -146,7 +146,8 @@ def test_state_errors(bt):
                                         (lambda: geom.cfg3(n=10, n_dir=1, n_b=1), 192),
                                         (lambda: geom.cfg4(n=12, n_dir=1, bvals=(1000.0,)), 384)])
 def test_halo_tiles_cover_the_pattern(bt, maker, umax):
-    """Every row is owned by exactly one tile; each tile's halo is the sorted,
+    """Every row is owned by exactly one tile (at most 128 rows and 448 entries
+    per tile); each tile's halo is the sorted,
     duplicate-free union of its rows' columns, within umax; the local indices
     of every entry point back to the CSR column; the owned flags mark exactly
     the tile's rows; and the halo is smaller than one gather per nonzero."""
@@ -162,6 +163,7 @@ def test_halo_tiles_cover_the_pattern(bt, maker, umax):
         for k in range(nt):
             rows = t["rows"][t["r0"][k]:t["r0"][k + 1]]
             assert 0 < len(rows) <= 128
+            assert t["rowe"][t["r0"][k + 1]] - t["rowe"][t["r0"][k]] <= 448
             uc = t["ucol"][t["u0"][k]:t["u0"][k + 1]]
             ids = (uc & 0x7FFFFFFF).astype(np.int64)
             own = (uc >> 31).astype(bool)
