@@ -194,15 +194,15 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
           float z1 = 0.f;
           if constexpr (TRANSF) z1 = smd[e];
           const float2* xs = sz + l * NB * 32 + lane;
+          const float2 m2 = make_float2(m, m);
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
             const float2 xx = xs[32 * b];
             float c = a0;
             if constexpr (TRANSF) c = fmaf(cb[b], z1, c);
-            P[b].x = fmaf(c, xx.x, P[b].x);
-            P[b].y = fmaf(c, xx.y, P[b].y);
-            Q[b].x = fmaf(m, xx.x, Q[b].x);
-            Q[b].y = fmaf(m, xx.y, Q[b].y);
+            // packed FP32 pairs (re, im): one FFMA2 per complex update
+            P[b] = __ffma2_rn(make_float2(c, c), xx, P[b]);
+            Q[b] = __ffma2_rn(m2, xx, Q[b]);
           }
         }
 #pragma unroll

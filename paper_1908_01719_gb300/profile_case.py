@@ -38,10 +38,13 @@ def main():
     p.TE = 2 * half * p.dt
     sim = Simulation(p)
     mode = bt.BT_MODE_MIXED if a.mode == "mixed" else bt.BT_MODE_PLAIN_FP64
-    flags = bt.BT_OPT_NO_GRAPH | {"auto": 0, "row": bt.BT_OPT_VARIANT_ROW,
+    flags = bt.BT_OPT_NO_GRAPH | bt.BT_OPT_PROFILE | {"auto": 0, "row": bt.BT_OPT_VARIANT_ROW,
                                   "halo": bt.BT_OPT_VARIANT_HALO}[a.variant]
     S, err, stat, _ = sim.run(mode, flags=flags)
     tuning = bt.bt_get_tuning(sim.ctx) if mode != bt.BT_MODE_PLAIN_FP64 else None
+    st = sim.stats()
+    print(f"per launch: SpMM-class {st['spmm_ms'] / max(1, st['spmm_launches']):.3f} ms, "
+          f"residual {st['resid_ms'] / max(1, st['resid_launches']):.3f} ms")
     print(f"{a.config} grid {a.grid}: n_dof {sim.n_dof}, nnz {sim.nnz}, RHS {sim.R}, stats {sim.stats()}, "
           f"tuning {tuning}")
     sim.close()
