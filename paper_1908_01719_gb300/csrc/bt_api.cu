@@ -522,6 +522,9 @@ bt_status ensure_halo(bt_ctx* ctx, int nb, cudaStream_t st) {
     CK(ensure(ctx->h_mdt, ctx->mesh.nnz));
     launch_gather_tile_planes(ctx->h_slot.p, ctx->mesh.nnz, ctx->d_pk32.p, ctx->d_md32.p, ctx->h_pkt.p,
                               ctx->h_mdt.p, st);
+    CK(ensure(ctx->h_dft, 3 * (size_t)ctx->mesh.nnz));
+    launch_gather_tile_df(ctx->h_slot.p, ctx->mesh.nnz, ctx->d_pkhi.p, ctx->d_pklo.p, ctx->d_kjmd_hi.p,
+                          ctx->d_kjmd_lo.p, ctx->h_dft.p, st);
     CKL();
     ctx->halo_planes_version = ctx->planes_version;
   }
@@ -530,7 +533,8 @@ bt_status ensure_halo(bt_ctx* ctx, int nb, cudaStream_t st) {
 
 HaloArgs halo_args(const bt_ctx* ctx) {
   return HaloArgs{ctx->h_r0.p,   ctx->h_rows.p, ctx->h_rowe.p, ctx->h_rowl.p, ctx->h_u0.p,  ctx->h_e0.p,
-                  ctx->h_ucol.p, ctx->h_lidx.p, ctx->h_pkt.p,  ctx->h_mdt.p,  ctx->h_seg0.p, ctx->halo_umax};
+                  ctx->h_ucol.p, ctx->h_lidx.p, ctx->h_pkt.p,  ctx->h_mdt.p,  ctx->h_dft.p,  ctx->h_seg0.p,
+                  ctx->halo_umax};
 }
 
 // Autotuner: time one Krylov iteration of each variant on the real pattern

@@ -64,6 +64,7 @@ struct bt_ctx {
   bt::DBuf<uint32_t> h_ucol;
   bt::DBuf<float4> h_pkt;
   bt::DBuf<float> h_mdt;
+  bt::DBuf<float4> h_dft;  // double-float planes in tile-entry order (3 per entry)
   std::vector<int64_t> halo_for;
   int halo_umax = 0;
   bool halo_ok = false;             // every row fits a tile of umax halo rows

@@ -142,6 +142,7 @@ struct HaloArgs {
   const uint16_t* lidx;     // [nnz] local column index of each entry
   const float4* pkt;        // [nnz] {A0, d0, d1, d2} in tile-entry order
   const float* mdt;         // [nnz] MD in tile-entry order
+  const float4* dft;        // [3 nnz] double-float planes in tile-entry order
   const int32_t* seg_tile0; // [G + 1]
   int umax;
 };
@@ -207,6 +208,8 @@ void launch_resid_sub_df(const OpArgs& op, const float2* d, float4* u, float4* r
                          RedScratch rs, int nb, int sms, cudaStream_t st);
 // the same over the halo tiles (the halo-staged variant)
 void resid_df_halo_prepare();
+void launch_gather_tile_df(const int32_t* slot, int64_t nnz, const float4* pkhi, const float4* pklo, const float2* kh,
+                           const float2* kl, float4* out, cudaStream_t st);
 bool resid_df_halo_available(int nb, int mode);
 void launch_resid0_df_halo(const OpArgs& op, const HaloArgs& h, const float4* u, float4* r, const RefineState& rf,
                            RedScratch rs, int nb, cudaStream_t st);

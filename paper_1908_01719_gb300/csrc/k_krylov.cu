@@ -145,37 +145,49 @@ __global__ void __launch_bounds__(256) k_krylov_init(OpArgs op, VecArgs va, cons
       const double inv = (scale && act && scale[s] > 0) ? 1.0 / scale[s] : 1.0;
       T2 ar = {0, 0}, an = {0, 0};
       int cnt = 0;
-      for (int64_t i = rb + ro; i < re; i += em.rpp) {
-        const size_t e = (size_t)i * va.Rp + col;
-        T2 rv = {0, 0};
-        if (act) {
-          double2 v = load_res(rres, e);
-          rv.x = (T)(v.x * inv);
-          rv.y = (T)(v.y * inv);
-        }
-        T2 z = {0, 0};
-        if (act) {
-          T2 d;
-          if constexpr (sizeof(T) == 4) {
-            float2 df = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
-            d.x = df.x; d.y = df.y;
-          } else {
-            double2 dd = diag_f64(va, op, i, sc.b, sc.c, sc.qx, sc.qy, sc.qz);
-            d.x = dd.x; d.y = dd.y;
+      // four rows per trip, all loads issued before the arithmetic
+      for (int64_t i0 = rb + ro; i0 < re; i0 += 4 * em.rpp) {
+        double2 v[4];
+        T2 d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + (int64_t)u * em.rpp;
+          v[u] = make_double2(0, 0);
+          d[u] = T2{1, 0};
+          if (i < re && act) {
+            v[u] = load_res(rres, (size_t)i * va.Rp + col);
+            if constexpr (sizeof(T) == 4) {
+              float2 df = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
+              d[u].x = df.x; d[u].y = df.y;
+            } else {
+              double2 dd = diag_f64(va, op, i, sc.b, sc.c, sc.qx, sc.qy, sc.qz);
+              d[u].x = dd.x; d[u].y = dd.y;
+            }
           }
-          T den = (T)1 / (d.x * d.x + d.y * d.y);
-          z.x = (rv.x * d.x + rv.y * d.y) * den;
-          z.y = (rv.y * d.x - rv.x * d.y) * den;
         }
-        r[e] = rv;
-        p[e] = z;
-        x[e] = T2{0, 0};
-        T2 rc = rv;
-        if constexpr (CONJ) rc.y = -rc.y;
-        ar.x += rc.x * z.x - rc.y * z.y;
-        ar.y += rc.x * z.y + rc.y * z.x;
-        an.x += rv.x * rv.x + rv.y * rv.y;
-        if (++cnt == 32) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + (int64_t)u * em.rpp;
+          if (i >= re) break;
+          const size_t e = (size_t)i * va.Rp + col;
+          T2 rv = {0, 0}, z = {0, 0};
+          if (act) {
+            rv.x = (T)(v[u].x * inv);
+            rv.y = (T)(v[u].y * inv);
+            T den = (T)1 / (d[u].x * d[u].x + d[u].y * d[u].y);
+            z.x = (rv.x * d[u].x + rv.y * d[u].y) * den;
+            z.y = (rv.y * d[u].x - rv.x * d[u].y) * den;
+          }
+          r[e] = rv;
+          p[e] = z;
+          x[e] = T2{0, 0};
+          T2 rc = rv;
+          if constexpr (CONJ) rc.y = -rc.y;
+          ar.x += rc.x * z.x - rc.y * z.y;
+          ar.y += rc.x * z.y + rc.y * z.x;
+          an.x += rv.x * rv.x + rv.y * rv.y;
+        }
+        if (++cnt == 8) {
           cnt = 0;
           acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
           ar = T2{0, 0}; an = T2{0, 0};
@@ -585,22 +597,39 @@ __global__ void __launch_bounds__(256) k_krylov_init_z(OpArgs op, VecArgs va, co
       const double inv = (scale && act && scale[s] > 0) ? 1.0 / scale[s] : 1.0;
       float2 ar = {0, 0}, an = {0, 0};
       int cnt = 0;
-      for (int64_t i = rb + ro; i < re; i += em.rpp) {
-        const size_t e = (size_t)i * va.Rp + col;
-        float2 rv = {0, 0}, zv = {0, 0};
-        if (act) {
-          const double2 v = load_res(rres, e);
-          rv = make_float2((float)(v.x * inv), (float)(v.y * inv));
-          zv = cdivf(rv, diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz));
+      // four rows per trip, all loads issued before the arithmetic
+      for (int64_t i0 = rb + ro; i0 < re; i0 += 4 * em.rpp) {
+        double2 v[4];
+        float2 d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + (int64_t)u * em.rpp;
+          v[u] = make_double2(0, 0);
+          d[u] = make_float2(1.f, 0.f);
+          if (i < re && act) {
+            v[u] = load_res(rres, (size_t)i * va.Rp + col);
+            d[u] = diag_f32(va, op, i, (float)sc.b, (float)sc.c, (float)sc.qx, (float)sc.qy, (float)sc.qz);
+          }
         }
-        z[e] = zv;
-        x[e] = make_float2(0.f, 0.f);
-        float2 rc = rv;
-        if constexpr (CONJ) rc.y = -rc.y;
-        ar.x += rc.x * zv.x - rc.y * zv.y;
-        ar.y += rc.x * zv.y + rc.y * zv.x;
-        an.x += rv.x * rv.x + rv.y * rv.y;
-        if (++cnt == 32) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + (int64_t)u * em.rpp;
+          if (i >= re) break;
+          const size_t e = (size_t)i * va.Rp + col;
+          float2 rv = {0, 0}, zv = {0, 0};
+          if (act) {
+            rv = make_float2((float)(v[u].x * inv), (float)(v[u].y * inv));
+            zv = cdivf(rv, d[u]);
+          }
+          z[e] = zv;
+          x[e] = make_float2(0.f, 0.f);
+          float2 rc = rv;
+          if constexpr (CONJ) rc.y = -rc.y;
+          ar.x += rc.x * zv.x - rc.y * zv.y;
+          ar.y += rc.x * zv.y + rc.y * zv.x;
+          an.x += rv.x * rv.x + rv.y * rv.y;
+        }
+        if (++cnt == 8) {
           cnt = 0;
           acc[k][0].x += ar.x; acc[k][0].y += ar.y; acc[k][1].x += an.x;
           ar = float2{0, 0}; an = float2{0, 0};

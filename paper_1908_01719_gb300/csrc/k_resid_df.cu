@@ -30,9 +30,12 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
   s = a + b;
   e = b - (s - a);
 }
+// Products that feed an error-free sum are formed with __fmul_rn, which the
+// compiler never contracts into an FMA with the following addition (a
+// contraction would make fl(a b) differ from the p the error term assumes).
 // (sh, sl) += (ah + al) * (xh + xl)
 __device__ __forceinline__ void dd_acc(float& sh, float& sl, float ah, float al, float xh, float xl) {
-  float p = ah * xh;
+  float p = __fmul_rn(ah, xh);
   float e = fmaf(ah, xh, -p);
   e = fmaf(ah, xl, fmaf(al, xh, e));
   float s, t;
@@ -42,7 +45,7 @@ __device__ __forceinline__ void dd_acc(float& sh, float& sl, float ah, float al,
 }
 // (sh, sl) += (ah + al) * x, x an exact FP32 number
 __device__ __forceinline__ void dd_acc1(float& sh, float& sl, float ah, float al, float x) {
-  float p = ah * x;
+  float p = __fmul_rn(ah, x);
   float e = fmaf(ah, x, -p);
   e = fmaf(al, x, e);
   float s, t;
@@ -65,7 +68,7 @@ __device__ __forceinline__ dd dd_split(double v) {
   return r;
 }
 __device__ __forceinline__ dd dd_mul(dd a, dd b) {
-  float p = a.h * b.h;
+  float p = __fmul_rn(a.h, b.h);
   float e = fmaf(a.h, b.h, -p);
   e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
   return dd_norm(p, e);
@@ -293,20 +296,29 @@ void launch_fill_u_df(const VecArgs& va, float4* u, cudaStream_t st) { k_fill_u_
 }  // namespace bt
 
 // ---------------------------------------------------------------- halo-staged variant
-// The same two residuals over the halo tiles of the Krylov apply: the gathered
-// vector (u in mode 0, d in mode 1) is staged in shared memory for the tile's
-// halo rows, then every owned row forms its double-float sums from shared
-// memory.  Each owned row's entries are its CSR entries in order, so the
-// double-float planes are read at their CSR slots.  Shared memory per halo
-// row: 32 NB sizeof(TX) bytes (NB columns per lane in this block).
+// The same two residuals over the halo tiles of the Krylov apply.  Per tile,
+// asynchronous copies bring into shared memory the gathered vector (u in mode
+// 0, d in mode 1) for the halo rows and the tile's double-float plane values
+// (A0, Pd, K+J, MD as hi/lo pairs, copied into tile-entry order once per
+// assembly) and local column indices; every owned row then forms its
+// double-float sums from shared memory only.  Staged bytes per halo row:
+// 32 NB sizeof(TX) = 512 (NB = 1 in mode 0, up to 2 in mode 1).
 namespace bt {
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async_tx(void* sdst, const void* gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-  if constexpr (BYTES == 16) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+  if constexpr (BYTES == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else if constexpr (BYTES == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
+
+// staged entries: 48 B of planes and a 2-byte local index each; the index
+// block is padded to a multiple of 16 bytes so the staged vector after it
+// stays 16-byte aligned for 16-byte copies
+constexpr int DF_LIDX_WORDS = (HALO_EMAX + 8) / 2;
+constexpr size_t DF_ENTRY_BYTES = (size_t)HALO_EMAX * 48 + (size_t)DF_LIDX_WORDS * 4;
+static_assert(DF_ENTRY_BYTES % 16 == 0, "staged vector must start 16-byte aligned");
 
 template <int NBL, int NB, bool TRANSF, int MODE, class TX>
 __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h, const TX* __restrict__ x,
@@ -314,7 +326,9 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
                                                           RefineState rf, RedScratch rs) {
   if (*rf.n_active == 0) return;
   extern __shared__ float4 sdf_[];
-  TX* xs_ = reinterpret_cast<TX*>(sdf_);  // [umax][NB][32]
+  float4* sent = sdf_;                                                  // [HALO_EMAX][3] planes
+  uint32_t* sli = reinterpret_cast<uint32_t*>(sent + 3 * HALO_EMAX);   // local indices, 2 per word
+  TX* xs_ = reinterpret_cast<TX*>(sli + DF_LIDX_WORDS);                 // [umax][NB][32]
   constexpr int NSPLIT = NBL / NB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tile = blockIdx.y / NSPLIT, part = blockIdx.y % NSPLIT;
@@ -354,9 +368,11 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
   if (__syncthreads_or(any)) {
     const int tb = h.seg_tile0[sg_], te = h.seg_tile0[sg_ + 1];
     for (int tau = tb + sk_; tau < te; tau += snb_) {
-      // ---- stage the gathered vector for the halo rows (asynchronous copies;
-      // entries of inactive lanes are left unset and never used)
-      const int ub = h.u0[tau], nu = h.u0[tau + 1] - ub;
+      const int ub = __ldg(h.u0 + tau), nu = __ldg(h.u0 + tau + 1) - ub;
+      const int ra = __ldg(h.t_r0 + tau), rz = __ldg(h.t_r0 + tau + 1);
+      const int te0 = __ldg(h.e0 + tau), te1 = __ldg(h.e0 + tau + 1);
+      // ---- asynchronous copies: the gathered vector of the halo rows (active
+      // lanes only; the others are never read) and the tile's entries
       const int myrows = nu > warp ? (nu - warp + 7) / 8 : 0;  // <= 32 since umax <= 256
       const uint32_t wl = lane < myrows ? __ldg(h.ucol + ub + warp + 8 * lane) : 0u;
       for (int k = 0; k < myrows; ++k) {
@@ -367,31 +383,39 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
         for (int b = 0; b < NB; ++b)
           if (act[b]) cp_async_tx<sizeof(TX)>(xs_ + (uu * NB + b) * 32 + lane, x + e + 32 * b);
       }
+      const int ne = te1 - te0;  // <= HALO_EMAX (tile builder)
+      for (int t = threadIdx.x; t < 3 * ne; t += blockDim.x) cp_async_tx<16>(sent + t, h.dft + 3 * (size_t)te0 + t);
+      const int w0 = te0 >> 1, nw = ((te1 + 1) >> 1) - w0;  // the index array is padded
+      for (int t = threadIdx.x; t < nw; t += blockDim.x)
+        cp_async_tx<4>(sli + t, reinterpret_cast<const uint32_t*>(h.lidx) + w0 + t);
+      const uint16_t* sl16 = reinterpret_cast<const uint16_t*>(sli) + (te0 & 1);
+      const int nown = rz - ra > warp ? (rz - ra - warp + 7) / 8 : 0;  // <= 16
+      const int ko = ra + warp + 8 * lane;
+      const int m_row = lane < nown ? __ldg(h.rows + ko) : 0;
+      const int m_e0 = lane < nown ? __ldg(h.rowe + ko) - te0 : 0;
+      const int m_e1 = lane < nown ? __ldg(h.rowe + ko + 1) - te0 : 0;
+      const int m_lo = lane < nown ? (int)__ldg(h.rowl + ko) : 0;
       asm volatile("cp.async.commit_group;\n" ::: "memory");
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       __syncthreads();
-      // ---- double-float sums of the owned rows
-      const int ra = h.t_r0[tau], rz = h.t_r0[tau + 1];
-      for (int kk = ra + warp; kk < rz; kk += 8) {
-        const int row = __ldg(h.rows + kk);
-        const int e0 = __ldg(h.rowe + kk), e1 = __ldg(h.rowe + kk + 1);
-        const int k0 = op.rp[row];  // CSR slot of the row's first entry
+      // ---- double-float sums of the owned rows, from shared memory
+      for (int kk = 0; kk < nown; ++kk) {
+        const int row = __shfl_sync(0xffffffffu, m_row, kk);
+        const int e0 = __shfl_sync(0xffffffffu, m_e0, kk), e1 = __shfl_sync(0xffffffffu, m_e1, kk);
+        const int lo = __shfl_sync(0xffffffffu, m_lo, kk);
         float Ph[NB][2], Pl[NB][2], Qh[NB][2], Ql[NB][2], Zh[NB][2], Zl[NB][2];
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
           for (int c = 0; c < 2; ++c) Ph[b][c] = Pl[b][c] = Qh[b][c] = Ql[b][c] = Zh[b][c] = Zl[b][c] = 0.f;
         for (int e = e0; e < e1; ++e) {
-          const int k = k0 + (e - e0);
-          const int l = __ldg(h.lidx + e);
-          const float4 vh = __ldg(op.pkhi + k), vl = __ldg(op.pklo + k);
-          float p0h, p0l, mdh = 0.f, mdl = 0.f;
-          if (MODE == 0 || TRANSF) {
-            const float2 kh = __ldg(op.kjmd_hi + k), kl = __ldg(op.kjmd_lo + k);
-            mdh = kh.y;
-            mdl = kl.y;
-            p0h = MODE == 0 ? kh.x : vh.x;
-            p0l = MODE == 0 ? kl.x : vl.x;
+          const float4 vh = sent[3 * e], vl = sent[3 * e + 1], kk4 = sent[3 * e + 2];  // {kh.x, kh.y, kl.x, kl.y}
+          const int l = sl16[e];
+          float p0h, p0l;
+          const float mdh = kk4.y, mdl = kk4.w;
+          if (MODE == 0) {
+            p0h = kk4.x;
+            p0l = kk4.z;
           } else {
             p0h = vh.x;
             p0l = vl.x;
@@ -427,7 +451,7 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
             }
           }
         }
-        const TX* xo = xs_ + (int)__ldg(h.rowl + kk) * NB * 32 + lane;
+        const TX* xo = xs_ + lo * NB * 32 + lane;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
           if (!act[b]) continue;
@@ -483,21 +507,18 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
   reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 t) { refine_finish(MODE, rf, s, t); });
 }
 
-// columns per lane one block of the halo residual handles: the staged halo
-// (umax rows of 32 NB sizeof(TX) bytes) must fit the Krylov apply's budget of
-// umax rows of 32 NBL float2
+// columns per lane one block handles: 512 staged bytes per halo row
 template <int NBL, int MODE>
 constexpr int df_halo_nb() {
-  return MODE == 0 ? (NBL < 2 ? 1 : NBL / 2) : (NBL < 2 ? NBL : 2);
+  return MODE == 0 ? 1 : (NBL < 2 ? NBL : 2);
 }
 
 template <int NBL, int MODE, class TX>
 static void resid_df_halo_t(const OpArgs& op, const HaloArgs& h, const TX* x, float4* u, float4* r,
                             const RefineState& rf, RedScratch rs, cudaStream_t st) {
   constexpr int NB = df_halo_nb<NBL, MODE>();
-  static_assert(NB >= 1, "no halo residual for this width");
   dim3 grid(op.sp.nblk, ((op.R + 32 * NBL - 1) / (32 * NBL)) * (NBL / NB));
-  const size_t smem = (size_t)h.umax * 32 * NB * sizeof(TX);
+  const size_t smem = DF_ENTRY_BYTES + (size_t)h.umax * 32 * NB * sizeof(TX);
   if (op.transformed)
     k_resid_df_halo<NBL, NB, true, MODE, TX><<<grid, 256, smem, st>>>(op, h, x, u, r, rf, rs);
   else
@@ -508,30 +529,44 @@ template <int NBL, int MODE, class TX>
 static void df_halo_attr() {
   constexpr int NB = df_halo_nb<NBL, MODE>();
   cudaFuncSetAttribute(k_resid_df_halo<NBL, NB, true, MODE, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       96 * 1024);
+                       HALO_SMEM_BUDGET);
   cudaFuncSetAttribute(k_resid_df_halo<NBL, NB, false, MODE, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       96 * 1024);
+                       HALO_SMEM_BUDGET);
 }
 void resid_df_halo_prepare() {
   df_halo_attr<4, 0, float4>();
   df_halo_attr<2, 0, float4>();
-  df_halo_attr<1, 0, float4>();
   df_halo_attr<4, 1, float2>();
   df_halo_attr<2, 1, float2>();
   df_halo_attr<1, 1, float2>();
 }
 
-bool resid_df_halo_available(int nb, int mode) {
-  (void)nb;
-  (void)mode;
-  return true;
+// the double-float planes in tile-entry order: 3 float4 per entry
+// {pkhi}, {pklo}, {kjmd_hi.x, kjmd_hi.y, kjmd_lo.x, kjmd_lo.y}
+__global__ void k_gather_tile_df(const int32_t* __restrict__ slot, int64_t nnz, const float4* __restrict__ pkhi,
+                                 const float4* __restrict__ pklo, const float2* __restrict__ kh,
+                                 const float2* __restrict__ kl, float4* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t sl = slot[k];
+    out[3 * k] = pkhi[sl];
+    out[3 * k + 1] = pklo[sl];
+    const float2 a = kh[sl], b = kl[sl];
+    out[3 * k + 2] = make_float4(a.x, a.y, b.x, b.y);
+  }
 }
+void launch_gather_tile_df(const int32_t* slot, int64_t nnz, const float4* pkhi, const float4* pklo, const float2* kh,
+                           const float2* kl, float4* out, cudaStream_t st) {
+  k_gather_tile_df<<<1024, 256, 0, st>>>(slot, nnz, pkhi, pklo, kh, kl, out);
+}
+
+// mode 0 at one column per lane would need 2 x 512 staged bytes per halo row
+// at the doubled umax of that layout: it stays on the row kernel
+bool resid_df_halo_available(int nb, int mode) { return !(mode == 0 && nb == 1); }
 
 void launch_resid0_df_halo(const OpArgs& op, const HaloArgs& h, const float4* u, float4* r, const RefineState& rf,
                            RedScratch rs, int nb, cudaStream_t st) {
   if (nb == 4) resid_df_halo_t<4, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
-  else if (nb == 2) resid_df_halo_t<2, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
-  else resid_df_halo_t<1, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
+  else resid_df_halo_t<2, 0, float4>(op, h, u, const_cast<float4*>(u), r, rf, rs, st);
 }
 
 void launch_resid_sub_df_halo(const OpArgs& op, const HaloArgs& h, const float2* d, float4* u, float4* r,
