@@ -188,6 +188,14 @@ def run_reference(args):
 VECTORS_PER_SYSTEM = {"row": 2, "halo": 6}
 
 
+# DRAM bytes (read + write) of one launch of the row SpMM k_spmm_krylov<4>, lab
+# frame, 128 RHS, measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# on the cfg4 geometry at 64^3 (343,793 dofs); see
+# profiles/k_spmm_krylov_cfg4_grid64.md.  The row kernel reads every column
+# whatever the number of active systems, so the figure scales with the dofs.
+ROW_SPMM_TRAFFIC = {"n_dof": 343793, "bytes": 791.9e6 + 329.7e6}
+
+
 def spmm_bytes(n, nnz, transformed, launches, sys_iters, variant):
     """Algorithmic HBM bytes of the dominant kernel summed over its launches:
     per launch the row pointers, column indices and packed FP32 planes (A0 and
@@ -323,7 +331,11 @@ def run_ours(args):
                          + " (fused FP32 complex SpMM of the Krylov iteration, the autotuned variant)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "frac_of_nominal_7900_gbs": achieved / 7900.0,
-                         "traffic": None,
+                         "traffic": (ROW_SPMM_TRAFFIC["bytes"] * n / ROW_SPMM_TRAFFIC["n_dof"]
+                                     if tuning["variant"] == "row" and not p.transformed and p.n_rhs == 128
+                                     else None),
+                         "traffic_note": "ncu DRAM bytes per launch of the 64^3 case scaled by the dof "
+                                         "ratio (the row kernel reads all columns)",
                          "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms,
                          "active_rhs_per_launch": sys_iters / max(1, spmm_launch),
                          "launches": spmm_launch},

@@ -163,8 +163,9 @@ enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
  * BT_OPT_PROFILE CUDA events around every fused SpMM and residual launch
  * (host-driven loop); BT_OPT_NO_GRAPH host-driven loop instead of the
  * captured step graph; BT_OPT_VARIANT_ROW / _HALO bypass the autotuner and
- * use that Krylov variant (bt_get_tuning; _HALO falls back to the tuned
- * choice where the halo tiles are not available). */
+ * use that Krylov variant together with the row / halo double-float residuals
+ * (bt_get_tuning; _HALO falls back to the tuned choice where the halo tiles
+ * are not available). */
 enum {
   BT_OPT_RESID_FP64 = 1u,
   BT_OPT_PROFILE = 2u,
@@ -210,11 +211,14 @@ bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_
  *   0  row SpMM (one warp per row, X gathered per nonzero) + vector updates
  *   1  halo-staged apply (Morton-ordered row tiles, their halo rows of X staged
  *      in shared memory, search-direction and solution updates fused in) +
- *      z update, and halo-staged double-float residuals; offered in
- *      BT_MODE_MIXED only
+ *      z update; offered in BT_MODE_MIXED only
  * ms_iter [2] (may be NULL) receives the measured ms per iteration of each
- * (0 = not timed).  BT_ESTATE before any tuning. */
-bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter);
+ * (0 = not timed).  The double-float correction residual is tuned on its own:
+ * resid_variant 0 = row kernel, 1 = halo-staged kernel (the step-start
+ * residual follows it), ms_resid [2] the measured ms per launch of each.
+ * Any pointer may be NULL.  BT_ESTATE before any tuning. */
+bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter, int32_t* resid_variant,
+                        double* ms_resid);
 /* Counters of the last bt_run (any pointer may be NULL): time steps, total
  * Krylov iterations (summed over solves, not RHS), refinement passes, fused
  * SpMM launches, with BT_OPT_PROFILE the summed device time (ms) of the

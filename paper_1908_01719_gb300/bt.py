@@ -75,7 +75,7 @@ def lib():
             "bt_set_sequence": [P, C.c_int, D, D, D],
             "bt_set_gradients": [P, I32, P, I32, P],
             "bt_set_segments": [P, I32, P, P, P, P],
-            "bt_get_tuning": [P, P, P],
+            "bt_get_tuning": [P, P, P, P, P],
             "bt_default_opts": [C.POINTER(bt_solver_opts)],
             "bt_run": [P, C.c_int, C.POINTER(bt_solver_opts)],
             "bt_get_signals": [P, P, P, P],
@@ -327,5 +327,8 @@ def bt_precond_grad_noalloc(w_ptr, n, feat_ptr, G_ptr, h_ptr, grad_ptr, loss_ptr
 def bt_get_tuning(ctx):
     v = C.c_int32()
     d = (C.c_double * 2)()
-    _check(ctx, lib().bt_get_tuning(ctx, C.byref(v), d))
-    return {"variant": ["row", "halo"][v.value], "ms_iter_row": d[0], "ms_iter_halo": d[1]}
+    rv = C.c_int32()
+    dr = (C.c_double * 2)()
+    _check(ctx, lib().bt_get_tuning(ctx, C.byref(v), d, C.byref(rv), dr))
+    return {"variant": ["row", "halo"][v.value], "ms_iter_row": d[0], "ms_iter_halo": d[1],
+            "resid_variant": ["row", "halo"][rv.value], "ms_resid_row": dr[0], "ms_resid_halo": dr[1]}

@@ -544,13 +544,14 @@ HaloArgs halo_args(const bt_ctx* ctx) {
 //   1: halo-staged apply + z update (when the halo tiles exist and allow_halo)
 // The Krylov state is primed with benign scalars (nothing converges while
 // timing); the Krylov init of the first solve re-initialises all of it.
-bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const KrylovState& ks, RedScratch rs,
-                        RedScratch rs2, int conj, int nb, int SY, int Rs, int G, bool allow_halo, int* variant) {
+bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const KrylovState& ks,
+                        const RefineState& rf, RedScratch rs, RedScratch rs2, int conj, int nb, int SY, int Rs, int G,
+                        bool allow_halo, bool df, int* variant, bool* resid_halo) {
   bt_ctx::Tuned* hit = nullptr;
   for (auto& t : ctx->tuned)
     if (t.R == Rs && t.nb == nb && t.G == G) hit = &t;
   const bool halo = allow_halo && ctx->halo_ok;
-  if (!hit || (halo && hit->ms[1] == 0)) {
+  if (!hit || (halo && hit->ms[1] == 0) || (halo && df && hit->ms_resid[1] == 0)) {
     cudaStream_t st = ctx->stream;
     const size_t NE = (size_t)op.n * op.Rp;
     std::vector<double> one(2 * (size_t)SY), small(2 * (size_t)SY), half(2 * (size_t)SY), big(SY, 1e300);
@@ -590,7 +591,7 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0}};
+    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0}, {0, 0}};
     for (int v = 0; v < (halo ? 2 : 1); ++v) {
       if (bt_status e = prime()) return e;
       iter(v);  // warm-up
@@ -602,6 +603,35 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
       CK(cudaEventElapsedTime(&ms, e0, e1));
       tu.ms[v] = ms / 3;
     }
+    // the correction residual (double-float): row kernel vs halo tiles, one
+    // launch at a time with the refinement state primed before each (a launch
+    // may retire systems)
+    if (halo && df) {
+      std::vector<double> ones(SY, 1.0), huge(SY, 1e300);
+      for (float4* b : {ctx->udf.p, ctx->rdf.p})
+        if (b) CK(cudaMemsetAsync(b, 0x3e, NE * sizeof(float4), st));
+      for (int v = 0; v < 2; ++v) {
+        float tot = 0;
+        for (int k = 0; k < 3; ++k) {
+          launch_set_int(rf.active, 1, SY, st);
+          launch_set_int(rf.n_active, SY, 1, st);
+          CK(cudaMemcpyAsync(rf.scale, ones.data(), SY * sizeof(double), cudaMemcpyHostToDevice, st));
+          CK(cudaMemcpyAsync(rf.r0n2, ones.data(), SY * sizeof(double), cudaMemcpyHostToDevice, st));
+          CK(cudaMemcpyAsync(rf.rk2, huge.data(), SY * sizeof(double), cudaMemcpyHostToDevice, st));
+          CK(cudaEventRecord(e0, st));
+          if (v == 1)
+            launch_resid_sub_df_halo(op, halo_args(ctx), ctx->x32.p, ctx->udf.p, ctx->rdf.p, rf, rs, nb, st);
+          else launch_resid_sub_df(op, ctx->x32.p, ctx->udf.p, ctx->rdf.p, rf, rs, nb, ctx->sms, st);
+          CK(cudaEventRecord(e1, st));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (k > 0) tot += ms;  // the first launch is the warm-up
+        }
+        tu.ms_resid[v] = tot / 2;
+      }
+      CK(cudaMemsetAsync(rf.err, 0, SY * sizeof(double), st));
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CKL();
@@ -611,6 +641,9 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     hit = hit ? hit : &ctx->tuned.back();
   }
   *variant = (halo && hit->ms[1] > 0 && hit->ms[1] < hit->ms[0]) ? 1 : 0;
+  *resid_halo = halo && df && hit->ms_resid[1] > 0 && hit->ms_resid[1] < hit->ms_resid[0];
+  hit->variant = *variant;
+  hit->resid_halo = *resid_halo;
   return BT_OK;
 }
 
@@ -687,6 +720,7 @@ static bt_status collect_samples(bt_ctx* ctx, OpArgs op, const VecArgs& va, cons
 // kernels from the host.
 struct GraphRun {
   int variant;
+  bool resid_halo;
   OpArgs op;
   VecArgs va;
   KrylovState ks;
@@ -750,7 +784,7 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
   };
   if (E(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) {
     launch_graph_step_begin(gc, ctx->rf_active.p, cs);
-    if (g.df && g.variant == 1 && resid_df_halo_available(g.nb, 0))
+    if (g.df && g.resid_halo && resid_df_halo_available(g.nb, 0))
       launch_resid0_df_halo(op0, halo_args(ctx), ctx->udf.p, ctx->rdf.p, g.rf, rs_at(0), g.nb, cs);
     else if (g.df) launch_resid0_df(op0, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(0), g.nb, ctx->sms, cs);
     else launch_resid0(op0, ctx->u64.p, ctx->r64.p, g.rf, rs_at(0), g.nb, ctx->sms, cs);
@@ -792,7 +826,7 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
         }
       }
       if (g.variant == 1) launch_flush_x(g.va, ctx->x32.p, ctx->p32.p, ctx->p32b.p, g.ks, c2);
-      if (g.df && g.variant == 1)
+      if (g.df && g.resid_halo)
         launch_resid_sub_df_halo(opL, halo_args(ctx), ctx->x32.p, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(4), g.nb, c2);
       else if (g.df) launch_resid_sub_df(opL, ctx->x32.p, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(4), g.nb, ctx->sms, c2);
       else launch_resid_sub(opL, ctx->x32.p, ctx->u64.p, ctx->r64.p, g.rf, rs_at(4), g.nb, ctx->sms, c2);
@@ -1002,18 +1036,21 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   rf.floor_c2 = feps * feps;
   auto rs_at = [&](int c) { return RedScratch{ctx->red_part.p, ctx->red_counter.p + c}; };
 
-  // halo tiles and the tuned Krylov variant for the FP32 inner solves
+  // halo tiles, the tuned Krylov variant for the FP32 inner solves and the
+  // tuned double-float residual kernel
   int variant = 0;
+  bool resid_halo = false;
   if (!plain) {
     const bool allow_halo = !learned && !col;
     if (allow_halo)
       if (bt_status e = ensure_halo(ctx, nb, st)) return e;
     OpArgs opt = op;
     opt.coef = ctx->d_coef.p + G;  // step 1, L operator
-    if (bt_status e = autotune_spmm(ctx, opt, va, ks, rs_at(2), rs_at(3), conj, nb, SY, Rs, G, allow_halo, &variant))
+    if (bt_status e = autotune_spmm(ctx, opt, va, ks, rf, rs_at(2), rs_at(3), conj, nb, SY, Rs, G, allow_halo, df,
+                                    &variant, &resid_halo))
       return e;
-    if (o.flags & BT_OPT_VARIANT_ROW) variant = 0;
-    if ((o.flags & BT_OPT_VARIANT_HALO) && allow_halo && ctx->halo_ok) variant = 1;
+    if (o.flags & BT_OPT_VARIANT_ROW) variant = 0, resid_halo = false;
+    if ((o.flags & BT_OPT_VARIANT_HALO) && allow_halo && ctx->halo_ok) variant = 1, resid_halo = df;
   }
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
   ctx->st_spmm_ms = ctx->st_resid_ms = 0;
@@ -1043,7 +1080,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   // production path: the captured time step (mixed mode)
   bool graph_done = false;
   if (!plain && !learned && !col && !prof && !(o.flags & BT_OPT_NO_GRAPH)) {
-    GraphRun gr{variant, op, va, ks, rf, df, conj, nb, N, o.tol_inner};
+    GraphRun gr{variant, resid_halo, op, va, ks, rf, df, conj, nb, N, o.tol_inner};
     int64_t gi = 0, gp = 0;
     if (run_graph(ctx, gr, o, Rs, G, &gi, &gp) == BT_OK) {
       graph_done = true;
@@ -1079,7 +1116,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     L += 3;  // two set kernels and the step-start residual
     op.coef = c_r0;
     timed(1, [&] {
-      if (df && variant == 1 && resid_df_halo_available(nb, 0))
+      if (df && resid_halo && resid_df_halo_available(nb, 0))
         launch_resid0_df_halo(op, halo_args(ctx), ctx->udf.p, ctx->rdf.p, rf, rs_at(0), nb, st);
       else if (df) launch_resid0_df(op, ctx->udf.p, ctx->rdf.p, rf, rs_at(0), nb, ctx->sms, st);
       else if (narrow) launch_resid0_narrow(op, ctx->u64.p, ctx->r64.p, rf, rs_at(0), ctx->sms, st);
@@ -1169,7 +1206,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
           L += 2;
         }
         timed(1, [&] {
-          if (df && variant == 1)
+          if (df && resid_halo)
             launch_resid_sub_df_halo(op, halo_args(ctx), ctx->x32.p, ctx->udf.p, ctx->rdf.p, rf, rs_at(4), nb, st);
           else if (df) launch_resid_sub_df(op, ctx->x32.p, ctx->udf.p, ctx->rdf.p, rf, rs_at(4), nb, ctx->sms, st);
           else launch_resid_sub(op, ctx->x32.p, ctx->u64.p, ctx->r64.p, rf, rs_at(4), nb, ctx->sms, st);
@@ -1283,13 +1320,17 @@ extern "C" bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, 
   return BT_OK;
 }
 
-extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter) {
+extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter, int32_t* resid_variant,
+                                   double* ms_resid) {
   if (!ctx) return BT_EINVAL;
   if (ctx->tuned.empty()) return BT_ESTATE;
   const auto& t = ctx->tuned.back();
   if (variant) *variant = t.variant;
-  if (ms_iter)
-    for (int k = 0; k < 2; ++k) ms_iter[k] = t.ms[k];
+  if (resid_variant) *resid_variant = t.resid_halo ? 1 : 0;
+  for (int k = 0; k < 2; ++k) {
+    if (ms_iter) ms_iter[k] = t.ms[k];
+    if (ms_resid) ms_resid[k] = t.ms_resid[k];
+  }
   return BT_OK;
 }
 

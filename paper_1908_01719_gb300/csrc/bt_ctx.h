@@ -74,6 +74,8 @@ struct bt_ctx {
     int R, nb, G;
     int variant;   // 0 row SpMM iteration, 1 halo iteration
     double ms[2];  // one Krylov iteration of each variant (ms; 0 = not timed)
+    double ms_resid[2];  // one correction residual launch: row, halo (0 = not timed)
+    bool resid_halo = false;
   };
   std::vector<Tuned> tuned;
 
