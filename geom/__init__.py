@@ -245,6 +245,9 @@ class Problem:
     theta: float = 0.5
     transformed: bool = False  # True: gauge-transformed frame (needed when periodic)
     meta: dict = field(default_factory=dict)
+    # temporal profile other than PGSE: {"kind": "cos_ogse" | "sin_ogse" | "double_pgse" |
+    # "trapezoid" | "double_trapezoid", "n_periods": int, "ramp": us}; None = PGSE
+    profile: dict | None = None
 
     @property
     def n_cmpt(self):

@@ -139,9 +139,22 @@ bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta_us, double Delta_u
  * Neumann transformed frame only (no periodic box). */
 bt_status bt_set_segments(bt_ctx* ctx, int32_t G, const int64_t* node_off, const double* delta_us,
                           const double* Delta_us, const double* TE_us);
+/* An arbitrary temporal profile f(t) (Section 4, "General diffusion-encoding
+ * sequence"; the magnetization equation and b of Section 2, Eq. strong_BT and
+ * Eq. b_value), given by its integral on the time grid:
+ *   F [n_steps + 1]  F(t_n) = int_0^{t_n} f(s) ds at t_n = n dt (us), F[0] = 0;
+ *   int_F2           int_0^TE F(s)^2 ds (us^3), TE = n_steps dt, used for
+ *                    b = q^2 int_F2 in bt_set_gradients.
+ * Each step uses the step average f_bar_n = (F_n - F_{n-1}) / dt (lab frame)
+ * or F_n (transformed frame, which needs F(TE) = 0), as for PGSE.  Replaces
+ * bt_set_sequence (one geometry; bt_set_segments stays PGSE); call
+ * bt_set_gradients afterwards.  BT_EINVAL for F[0] != 0, non-finite values,
+ * int_F2 <= 0, or F(TE) != 0 in the transformed frame. */
+bt_status bt_set_profile(bt_ctx* ctx, int32_t n_steps, const double* F, double int_F2);
 /* Directions dirs [3*n_dir] (normalised here) and b-values bvals [n_b]
  * (s/mm^2).  Right-hand side r = d*n_b + j uses dirs[d], bvals[j];
- * q = gamma |g| = sqrt(b / (delta^2 (Delta - delta/3))) (Eq. b_value, PGSE). */
+ * q = gamma |g| = sqrt(b / int_0^TE F^2) (Eq. b_value): delta^2 (Delta - delta/3)
+ * for PGSE, the caller's int_F2 after bt_set_profile. */
 bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32_t n_b,
                            const double* bvals);
 

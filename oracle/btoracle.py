@@ -226,6 +226,20 @@ def pgse_tables(delta, Delta, dt, n_steps):
     return fbar, F
 
 
+def sequence(p):
+    """(f_bar_n, F_n, int_0^TE F^2) of problem p: PGSE in closed form (Section 2,
+    Eq. pgse), or p.profile = {"kind": ..., "n_periods": ..., "ramp": ...}
+    integrated numerically from f (oracle/profiles.py)."""
+    N = p.n_steps
+    prof = getattr(p, "profile", None)
+    if prof:
+        from . import profiles
+        return profiles.tables(prof["kind"], p.delta, p.Delta, p.TE, p.dt, prof.get("n_periods", 1),
+                               prof.get("ramp"))
+    fbar, F = pgse_tables(p.delta, p.Delta, p.dt, N)
+    return fbar, F, p.delta * p.delta * (p.Delta - p.delta / 3.0)
+
+
 def q_from_b(b, delta, Delta):
     """q = gamma |g| from b = q^2 delta^2 (Delta - delta/3) (Eq. b_value with the
     PGSE F(t))."""
@@ -292,14 +306,14 @@ def run_lab(p, asm=None, rhs=None, return_history=False, route=None, return_fiel
     M, KJ = asm["M"], asm["K"] + asm["J"]
     w = signal_weights(asm)
     N = p.n_steps
-    fbar, _ = pgse_tables(p.delta, p.Delta, p.dt, N)
+    fbar, _, intF2 = sequence(p)
     nb = len(p.bvals)
     rhs = range(p.n_rhs) if rhs is None else rhs
     th, dt = p.theta, p.dt
     out, hist, fields = [], [], []
     for r in rhs:
         qh = p.dirs[r // nb]
-        q = float(q_from_b(p.bvals[r % nb], p.delta, p.Delta))
+        q = math.sqrt(float(p.bvals[r % nb]) / intF2)  # b = q^2 int F^2 (Eq. b_value)
         Mq = qh[0] * asm["Mx"] + qh[1] * asm["My"] + qh[2] * asm["Mz"]
         sol = _Solver(asm["n"], route)
         u = np.ones(asm["n"], dtype=np.complex128)
@@ -326,7 +340,7 @@ def run_transformed(p, asm=None, rhs=None, return_history=False, route=None, ret
     M, KJ, MD = asm["M"], asm["K"] + asm["J"], asm["MD"]
     w = signal_weights(asm)
     N = p.n_steps
-    _, F = pgse_tables(p.delta, p.Delta, p.dt, N)
+    _, F, intF2 = sequence(p)
     if abs(F[-1]) > 1e-12 * max(1.0, p.delta):
         raise ValueError("F(TE) != 0: the signal needs the phase factor")
     nb = len(p.bvals)
@@ -335,7 +349,7 @@ def run_transformed(p, asm=None, rhs=None, return_history=False, route=None, ret
     out, hist, fields = [], [], []
     for r in rhs:
         qh = p.dirs[r // nb]
-        q = float(q_from_b(p.bvals[r % nb], p.delta, p.Delta))
+        q = math.sqrt(float(p.bvals[r % nb]) / intF2)  # b = q^2 int F^2 (Eq. b_value)
         Eq = qh[0] * asm["Ex"] + qh[1] * asm["Ey"] + qh[2] * asm["Ez"]
 
         def A(Fv):

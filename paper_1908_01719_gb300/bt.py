@@ -29,7 +29,7 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats",
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
-           "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles"]
+           "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -74,6 +74,7 @@ def lib():
             "bt_get_plane": [P, C.c_int, P],
             "bt_set_sequence": [P, C.c_int, D, D, D],
             "bt_set_gradients": [P, I32, P, I32, P],
+            "bt_set_profile": [P, I32, P, D],
             "bt_set_segments": [P, I32, P, P, P, P],
             "bt_get_tuning": [P, P, P, P, P],
             "bt_default_opts": [C.POINTER(bt_solver_opts)],
@@ -187,6 +188,12 @@ def bt_set_segments(ctx, node_off, delta, Delta, TE):
     D = np.ascontiguousarray(Delta, dtype=np.float64)
     T = np.ascontiguousarray(TE, dtype=np.float64)
     _check(ctx, lib().bt_set_segments(ctx, len(no) - 1, _ptr(no), _ptr(d), _ptr(D), _ptr(T)))
+
+
+def bt_set_profile(ctx, F, int_F2):
+    """Arbitrary temporal profile: F[n] = int_0^{n dt} f (us), int_F2 = int_0^TE F^2 (us^3)."""
+    F = np.ascontiguousarray(F, dtype=np.float64).ravel()
+    _check(ctx, lib().bt_set_profile(ctx, len(F) - 1, _ptr(F), float(int_F2)))
 
 
 def bt_set_gradients(ctx, dirs, bvals):

@@ -340,7 +340,43 @@ bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta, double Delta, dou
   ctx->seg_row0 = {0, ctx->mesh.n_dof};
   ctx->seg_delta = {delta};
   ctx->seg_Delta = {Delta};
+  ctx->seg_intF2 = {delta * delta * (Delta - delta / 3.0)};  // int_0^TE F^2 for PGSE
   ctx->seg_TE = {TE};
+  ctx->seg_N = {N};
+  ctx->seg_fbar = {ctx->fbar};
+  ctx->seg_F = {ctx->F};
+  ctx->have_seq = true;
+  ctx->R = 0;
+  return BT_OK;
+}
+
+bt_status bt_set_profile(bt_ctx* ctx, int32_t n_steps, const double* F, double int_F2) {
+  if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
+  if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_set_profile: assemble first (dt is needed)");
+  if (n_steps < 1 || !F) return fail(ctx, BT_EINVAL, "bt_set_profile: need n_steps >= 1 and F");
+  if (!(int_F2 > 0) || !std::isfinite(int_F2)) return fail(ctx, BT_EINVAL, "bt_set_profile: need int_F2 > 0");
+  double fmax = 0;
+  for (int n = 0; n <= n_steps; ++n) {
+    if (!std::isfinite(F[n])) return fail(ctx, BT_EINVAL, "bt_set_profile: non-finite F");
+    fmax = std::max(fmax, std::fabs(F[n]));
+  }
+  if (F[0] != 0.0) return fail(ctx, BT_EINVAL, "bt_set_profile: F(0) must be 0");
+  if (ctx->transformed && std::fabs(F[n_steps]) > 1e-12 * std::max(fmax, 1e-300))
+    return fail(ctx, BT_EINVAL, "bt_set_profile: F(TE) != 0 in the transformed frame");
+  const int N = n_steps;
+  ctx->n_steps = N;
+  ctx->TE = N * ctx->dt;
+  ctx->delta = ctx->Delta = 0;
+  ctx->F.assign(F, F + N + 1);
+  ctx->fbar.resize(N);
+  for (int n = 1; n <= N; ++n) ctx->fbar[n - 1] = (ctx->F[n] - ctx->F[n - 1]) / ctx->dt;
+  ctx->G = 1;
+  ctx->seg_row0 = {0, ctx->mesh.n_dof};
+  ctx->seg_delta = {0.0};
+  ctx->seg_Delta = {0.0};
+  ctx->seg_TE = {ctx->TE};
+  ctx->seg_intF2 = {int_F2};
   ctx->seg_N = {N};
   ctx->seg_fbar = {ctx->fbar};
   ctx->seg_F = {ctx->F};
@@ -358,8 +394,7 @@ bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32
   const int R = n_dir * n_b, G = ctx->G;
   std::vector<double> qh(3 * (size_t)G * R), qv((size_t)G * R);
   for (int g = 0; g < G; ++g) {
-    const double d = ctx->seg_delta[g], D = ctx->seg_Delta[g];
-    const double intF2 = d * d * (D - d / 3.0);  // int_0^TE F^2 for PGSE
+    const double intF2 = ctx->seg_intF2[g];
     for (int i = 0; i < n_dir; ++i) {
       double nx = dirs[3 * i], ny = dirs[3 * i + 1], nz = dirs[3 * i + 2];
       double nr = std::sqrt(nx * nx + ny * ny + nz * nz);
@@ -438,6 +473,8 @@ bt_status bt_set_segments(bt_ctx* ctx, int32_t G, const int64_t* node_off, const
   ctx->seg_row0 = row0;
   ctx->seg_delta.assign(delta, delta + G);
   ctx->seg_Delta.assign(Delta, Delta + G);
+  ctx->seg_intF2.resize(G);
+  for (int g = 0; g < G; ++g) ctx->seg_intF2[g] = delta[g] * delta[g] * (Delta[g] - delta[g] / 3.0);
   ctx->seg_TE.assign(TE, TE + G);
   ctx->seg_N = N;
   ctx->seg_fbar = fb;

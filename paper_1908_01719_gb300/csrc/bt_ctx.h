@@ -51,6 +51,7 @@ struct bt_ctx {
   int G = 1;
   std::vector<int64_t> seg_row0{0, 0};          // [G+1] dof offsets
   std::vector<double> seg_delta, seg_Delta, seg_TE;
+  std::vector<double> seg_intF2;                 // int_0^TE F^2 per segment (b = q^2 int F^2)
   std::vector<int> seg_N;                        // steps per segment
   std::vector<std::vector<double>> seg_fbar, seg_F;
   bt::DBuf<int> d_blk_seg, d_blk0, d_seg_N, d_ctl;

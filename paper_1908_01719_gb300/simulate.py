@@ -5,13 +5,14 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import bt
+from . import bt, profiles
 
 
 class Simulation:
     """One context holding one geometry.  `geom` is any object with the fields
     xyz, tets, tet_cmpt, D_cmpt, kappa_cmpt, periodic_mask, box_lo, box_hi,
-    dt, theta, delta, Delta, TE, dirs, bvals, transformed."""
+    dt, theta, delta, Delta, TE, dirs, bvals, transformed, and optionally a
+    temporal `profile` (see profiles.py; None = PGSE)."""
 
     def __init__(self, geom, device: int = 0, stream: int | None = None):
         self.g = geom
@@ -26,7 +27,12 @@ class Simulation:
         self.G = 1 if seg is None else len(seg["node_off"]) - 1
         if device >= 0:
             bt.bt_assemble(self.ctx, geom.dt, geom.theta, self.frame)
-            if seg is None:
+            prof = getattr(geom, "profile", None)
+            if seg is None and prof:
+                F, I = profiles.tables(prof["kind"], geom.delta, geom.Delta, geom.TE, geom.dt,
+                                       prof.get("n_periods", 1), prof.get("ramp"))
+                bt.bt_set_profile(self.ctx, F, I)
+            elif seg is None:
                 bt.bt_set_sequence(self.ctx, bt.BT_PGSE, geom.delta, geom.Delta, geom.TE)
             else:
                 bt.bt_set_segments(self.ctx, seg["node_off"], seg["delta"], seg["Delta"], seg["TE"])

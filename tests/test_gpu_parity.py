@@ -257,3 +257,52 @@ def test_golden_signals(sim_cls, bt, name, mode):
         assert rel(S, ref).max() < tol, rel(S, ref)
     finally:
         sim.close()
+
+
+# ---------------------------------------------------------------- arbitrary temporal profiles
+def _profile_case(kind):
+    p = geom.cfg2(n=6, kappa=1e-4, bvals=(800.0, 2500.0))
+    p.dirs = np.array([[1.0, 0.0, 0.0], [0.0, 0.6, 0.8]])
+    p.delta, p.Delta = 1500.0, 2000.0
+    p.TE = {"cos_ogse": 0.5 * (1500.0 + 2000.0) + 1500.0, "sin_ogse": 0.5 * (1500.0 + 2000.0) + 1500.0,
+            "double_pgse": 2 * 3500.0, "trapezoid": 3500.0}[kind]
+    p.profile = {"kind": kind, "n_periods": 2, "ramp": 200.0}
+    return p
+
+
+@pytest.mark.parametrize("kind", ["cos_ogse", "sin_ogse", "double_pgse", "trapezoid"])
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_profiles_match_oracle(sim_cls, bt, kind, mode):
+    """bt_set_profile with the library's tables against the oracle's own
+    quadrature of f, lab frame, signals of every RHS."""
+    p = _profile_case(kind)
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S, err, stat, st = sim.run(m)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()
+
+
+def test_free_periodic_profile_exact_gpu(sim_cls, bt):
+    """Periodic box, cos-OGSE: the exact discrete product with the profile's F."""
+    from paper_1908_01719_gb300 import profiles
+    p = geom.free_periodic_box(n=8, L=8.0, dirs=((0.3, 0.4, math.sqrt(0.75)),), bvals=(600.0, 1500.0))
+    p.delta, p.Delta = 2000.0, 2000.0
+    p.TE = 0.5 * (p.delta + p.Delta) + p.delta
+    p.profile = {"kind": "cos_ogse", "n_periods": 2}
+    F, I = profiles.tables("cos_ogse", p.delta, p.Delta, p.TE, p.dt, n_periods=2)
+    sim = sim_cls(p)
+    try:
+        for mode, tol in [(bt.BT_MODE_PLAIN_FP64, 1e-11), (bt.BT_MODE_MIXED, 1e-8)]:
+            S, err, stat, st = sim.run(mode)
+            for r, b in enumerate(p.bvals):
+                q2 = b / I
+                prod = np.prod((1 - 0.5 * p.dt * 2e-3 * q2 * F[:-1] ** 2) / (1 + 0.5 * p.dt * 2e-3 * q2 * F[1:] ** 2))
+                assert abs(S[r] / 512.0 - prod) < tol
+    finally:
+        sim.close()
