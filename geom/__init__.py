@@ -248,6 +248,9 @@ class Problem:
     # temporal profile other than PGSE: {"kind": "cos_ogse" | "sin_ogse" | "double_pgse" |
     # "trapezoid" | "double_trapezoid", "n_periods": int, "ramp": us}; None = PGSE
     profile: dict | None = None
+    # transverse relaxation 1/T2 (1/us) and initial magnetization per compartment; None = 0 / 1
+    inv_T2: np.ndarray | None = None
+    rho: np.ndarray | None = None
 
     @property
     def n_cmpt(self):

@@ -103,14 +103,27 @@ bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t
                             int32_t* rows, int32_t* rowe, uint16_t* rowl, int32_t* u0, uint32_t* ucol,
                             uint16_t* lidx);
 
+/* Transverse relaxation and initial magnetization per compartment (Section 2:
+ * the T2 term of the Bloch-Torrey equation, which enters the weak form as
+ * (U / T2, v), and the initial condition U(x, 0) = rho; Section 4 "Initial
+ * conditions").  inv_T2 [n_cmpt] 1/T2 in 1/us (0 = no relaxation, the
+ * default); rho [n_cmpt] initial value of u in that compartment (default 1).
+ * Either pointer may be NULL (keeps the default).  The relaxation is
+ * assembled into the operator as the plane MR = sum over elements of 1/T2 x
+ * mass (bt_get_plane BT_PLANE_MR), so this call clears the assembly: call
+ * bt_assemble (and the sequence and gradients) again.  BT_EINVAL for negative
+ * or non-finite 1/T2 or non-finite rho. */
+bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho);
+
 /* ---------------------------------------------------------------- assembly
  * Element-by-element, deterministic assembly on the GPU of every matrix over
  * the shared pattern (Appendix B, Eq. matrix_form; Appendix A weak form):
  *   M mass, K stiffness (D-weighted), J interface (kappa-weighted),
  *   MD D-weighted mass, Mx My Mz first-moment mass (x relative to the box
  *   centre), Ex Ey Ez = C_k - C_k^T with C_k[i,j] = D int phi_i d_k phi_j,
+ *   MR the 1/T2-weighted mass (zero without bt_set_relaxation),
  * then the step planes for time step dt_us and theta (0 < theta <= 1):
- *   A0 = M + theta dt (K + J), in FP64, FP32 and double-float (hi+lo FP32).
+ *   A0 = M + theta dt (K + J + MR), in FP64, FP32 and double-float (hi+lo FP32).
  * flags: BT_FRAME_LAB (Neumann only) or BT_FRAME_TRANSFORMED (required when
  * periodic_mask != 0). */
 enum { BT_FRAME_LAB = 0, BT_FRAME_TRANSFORMED = 1 };
@@ -118,7 +131,7 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags);
 /* Copy one assembled FP64 value plane [nnz] to host memory. */
 enum { BT_PLANE_M = 0, BT_PLANE_K = 1, BT_PLANE_J = 2, BT_PLANE_MD = 3, BT_PLANE_MX = 4,
        BT_PLANE_MY = 5, BT_PLANE_MZ = 6, BT_PLANE_EX = 7, BT_PLANE_EY = 8, BT_PLANE_EZ = 9,
-       BT_PLANE_A0 = 10, BT_N_PLANES = 11 };
+       BT_PLANE_A0 = 10, BT_PLANE_MR = 11, BT_N_PLANES = 12 };
 bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals);
 
 /* ---------------------------------------------------------------- sequence

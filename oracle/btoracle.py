@@ -139,6 +139,7 @@ def assemble(p):
       J   interface jump, kappa-weighted    (Appendix B, matrix I)
       Mx, My, Mz  first-moment mass         (Appendix B, matrix J = sum g_k M_k)
       MD  D-weighted mass                   (transformed frame, Appendix A)
+      MR  1/T2-weighted mass                (relaxation term of Section 2)
       Ex, Ey, Ez  skew transport matrices   (transformed frame, Appendix A)
     """
     master = periodic_master(p.xyz, p.periodic_mask, p.box_lo, p.box_hi)
@@ -161,6 +162,10 @@ def assemble(p):
     out["M"] = _coo(rows, cols, Me, n)
     out["K"] = _coo(rows, cols, Ke, n)
     out["MD"] = _coo(rows, cols, Dt[:, None, None] * Me, n)
+    # relaxation (U/T2, v) of the weak form: mass weighted by 1/T2 per compartment
+    invT2 = getattr(p, "inv_T2", None)
+    rT2 = np.zeros(len(vol)) if invT2 is None else np.asarray(invT2, float)[p.tet_cmpt]
+    out["MR"] = _coo(rows, cols, rT2[:, None, None] * Me, n)
     for k, nm in enumerate("xyz"):
         Mk = vol[:, None, None] * np.einsum("ijl,tl->tij", c3, Xc[:, :, k])
         out["M" + nm] = _coo(rows, cols, Mk, n)
@@ -196,6 +201,14 @@ def assemble(p):
     out["n_iface"] = nf
     out["volume"] = float(vol.sum())
     return out
+
+
+def initial_field(p, asm):
+    """u^0: the initial magnetization rho of each dof's compartment (1 by default)."""
+    rho = getattr(p, "rho", None)
+    if rho is None:
+        return np.ones(asm["n"], dtype=np.complex128)
+    return np.asarray(rho, float)[asm["dof_cmpt"]].astype(np.complex128)
 
 
 def signal_weights(asm):
@@ -296,14 +309,14 @@ class _Solver:
 
 def run_lab(p, asm=None, rhs=None, return_history=False, route=None, return_field=False):
     """Lab frame (Neumann outer boundary):
-        L_n = M + theta dt (K + J + i q f_bar_n Mq)
-        R_n = M - (1 - theta) dt (K + J + i q f_bar_n Mq),  Mq = sum_k qhat_k M_k
-        L_n u^n = R_n u^{n-1},  u^0 = 1,  S = (M 1)^T u^N."""
+        L_n = M + theta dt (K + J + MR + i q f_bar_n Mq)
+        R_n = M - (1 - theta) dt (K + J + MR + i q f_bar_n Mq),  Mq = sum_k qhat_k M_k
+        L_n u^n = R_n u^{n-1},  u^0 = rho (1 by default),  S = (M 1)^T u^N."""
     if asm is None:
         asm = assemble(p)
     if p.periodic_mask:
         raise ValueError("periodic boxes need the transformed frame")
-    M, KJ = asm["M"], asm["K"] + asm["J"]
+    M, KJ = asm["M"], asm["K"] + asm["J"] + asm["MR"]
     w = signal_weights(asm)
     N = p.n_steps
     fbar, _, intF2 = sequence(p)
@@ -316,7 +329,7 @@ def run_lab(p, asm=None, rhs=None, return_history=False, route=None, return_fiel
         q = math.sqrt(float(p.bvals[r % nb]) / intF2)  # b = q^2 int F^2 (Eq. b_value)
         Mq = qh[0] * asm["Mx"] + qh[1] * asm["My"] + qh[2] * asm["Mz"]
         sol = _Solver(asm["n"], route)
-        u = np.ones(asm["n"], dtype=np.complex128)
+        u = initial_field(p, asm)
         h = [w @ u]
         for n in range(1, N + 1):
             fb = fbar[n - 1]
@@ -337,7 +350,7 @@ def run_transformed(p, asm=None, rhs=None, return_history=False, route=None, ret
         S = (M 1)^T u^N  (F(TE) = 0 for PGSE, so U = u at TE)."""
     if asm is None:
         asm = assemble(p)
-    M, KJ, MD = asm["M"], asm["K"] + asm["J"], asm["MD"]
+    M, KJ, MD = asm["M"], asm["K"] + asm["J"] + asm["MR"], asm["MD"]
     w = signal_weights(asm)
     N = p.n_steps
     _, F, intF2 = sequence(p)
@@ -356,7 +369,7 @@ def run_transformed(p, asm=None, rhs=None, return_history=False, route=None, ret
             return KJ + (q * q * Fv * Fv) * MD + (1j * q * Fv) * Eq
 
         sol = _Solver(asm["n"], route, hermitian=True)
-        u = np.ones(asm["n"], dtype=np.complex128)
+        u = initial_field(p, asm)
         h = [w @ u]
         for n in range(1, N + 1):
             Fn, Fp = F[n], F[n - 1]

@@ -21,7 +21,8 @@ BT_PGSE = 0
 BT_MODE_PLAIN_FP64, BT_MODE_MIXED, BT_MODE_LEARNED = 0, 1, 2
 BT_OPT_RESID_FP64, BT_OPT_PROFILE, BT_OPT_NO_GRAPH = 1, 2, 4
 BT_OPT_VARIANT_ROW, BT_OPT_VARIANT_HALO = 8, 16
-PLANES = {"M": 0, "K": 1, "J": 2, "MD": 3, "Mx": 4, "My": 5, "Mz": 6, "Ex": 7, "Ey": 8, "Ez": 9, "A0": 10}
+PLANES = {"M": 0, "K": 1, "J": 2, "MD": 3, "Mx": 4, "My": 5, "Mz": 6, "Ex": 7, "Ey": 8, "Ez": 9, "A0": 10,
+          "MR": 11}
 
 # every symbol include/bt.h declares
 EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_upload_mesh", "bt_get_sizes",
@@ -29,7 +30,7 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats",
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
-           "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile"]
+           "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -75,6 +76,7 @@ def lib():
             "bt_set_sequence": [P, C.c_int, D, D, D],
             "bt_set_gradients": [P, I32, P, I32, P],
             "bt_set_profile": [P, I32, P, D],
+            "bt_set_relaxation": [P, P, P],
             "bt_set_segments": [P, I32, P, P, P, P],
             "bt_get_tuning": [P, P, P, P, P],
             "bt_default_opts": [C.POINTER(bt_solver_opts)],
@@ -188,6 +190,13 @@ def bt_set_segments(ctx, node_off, delta, Delta, TE):
     D = np.ascontiguousarray(Delta, dtype=np.float64)
     T = np.ascontiguousarray(TE, dtype=np.float64)
     _check(ctx, lib().bt_set_segments(ctx, len(no) - 1, _ptr(no), _ptr(d), _ptr(D), _ptr(T)))
+
+
+def bt_set_relaxation(ctx, inv_T2=None, rho=None):
+    """1/T2 (1/us) and initial magnetization per compartment; None keeps the default."""
+    a = None if inv_T2 is None else np.ascontiguousarray(inv_T2, dtype=np.float64)
+    b = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+    _check(ctx, lib().bt_set_relaxation(ctx, None if a is None else _ptr(a), None if b is None else _ptr(b)))
 
 
 def bt_set_profile(ctx, F, int_F2):

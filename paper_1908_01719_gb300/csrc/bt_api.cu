@@ -141,6 +141,9 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
   ctx->have_mesh = true;
   ctx->G = 1;
   ctx->seg_row0 = {0, ctx->mesh.n_dof};
+  ctx->cm_invT2.assign(n_cmpt, 0.0);
+  ctx->cm_rho.assign(n_cmpt, 1.0);
+  ctx->have_rho = false;
   if (ctx->host_only) return BT_OK;
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -208,6 +211,27 @@ bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t
   return BT_OK;
 }
 
+bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho) {
+  if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
+  if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_set_relaxation: no mesh");
+  const int nc = ctx->mesh.n_cmpt;
+  std::vector<double> it(nc, 0.0), rh(nc, 1.0);
+  for (int c = 0; c < nc; ++c) {
+    if (inv_T2) it[c] = inv_T2[c];
+    if (rho) rh[c] = rho[c];
+    if (!(it[c] >= 0) || !std::isfinite(it[c]) || !std::isfinite(rh[c]))
+      return fail(ctx, BT_EINVAL, "bt_set_relaxation: need finite 1/T2 >= 0 and finite rho");
+  }
+  ctx->cm_invT2 = it;
+  ctx->cm_rho = rh;
+  ctx->have_rho = false;
+  for (double v : rh) ctx->have_rho |= v != 1.0;
+  // the relaxation enters the assembled operator: assemble again
+  ctx->assembled = ctx->have_seq = false;
+  return BT_OK;
+}
+
 bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
@@ -221,14 +245,23 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   const HostMesh& m = ctx->mesh;
   const int64_t nnz = m.nnz, n = m.n_dof;
   cudaStream_t st = ctx->stream;
-  CK(ctx->d_geo.alloc(26 * (size_t)m.n_tets));
+  CK(ctx->d_geo.alloc(27 * (size_t)m.n_tets));
   CK(ctx->d_fcoef.alloc(std::max<int64_t>(1, m.n_face)));
-  CK(ctx->d_planes.alloc(10 * (size_t)nnz));
+  CK(ctx->d_planes.alloc(11 * (size_t)nnz));
+  CK(upload(ctx->d_invT2, ctx->cm_invT2, st));
+  if (ctx->have_rho) {
+    std::vector<double> rd(n);
+    for (int64_t i = 0; i < n; ++i) rd[i] = ctx->cm_rho[m.dof_cmpt[i]];
+    CK(upload(ctx->d_rho_dof, rd, st));
+  } else {
+    ctx->d_rho_dof.free();
+  }
   AsmArgs a;
   a.xyz = ctx->d_xyz.p;
   a.tets = ctx->d_tets.p;
   a.cmpt = ctx->d_cmpt.p;
   a.Dc = ctx->d_D.p;
+  a.invT2c = ctx->d_invT2.p;
   for (int k = 0; k < 3; ++k) a.centre[k] = 0.5 * (m.lo[k] + m.hi[k]);
   a.nt = m.n_tets;
   a.nf = m.n_face;
@@ -303,7 +336,8 @@ bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals) {
   if (!need_gpu(ctx)) return fail(ctx, BT_ENODEV, "bt_get_plane: host-only context");
   if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_get_plane: not assembled");
   CK(cudaSetDevice(ctx->device));
-  const double* src = which == BT_PLANE_A0 ? ctx->d_A0.p : ctx->d_planes.p + (size_t)which * ctx->mesh.nnz;
+  const size_t plane = which == BT_PLANE_MR ? 10 : (size_t)which;
+  const double* src = which == BT_PLANE_A0 ? ctx->d_A0.p : ctx->d_planes.p + plane * ctx->mesh.nnz;
   CK(cudaMemcpyAsync(vals, src, ctx->mesh.nnz * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return BT_OK;
@@ -1095,8 +1129,9 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   CK(cudaMemsetAsync(ctx->rf_err.p, 0, SY * sizeof(double), st));
   CK(cudaMemsetAsync(ctx->ks_status.p, 0, SY * sizeof(int), st));
   CK(cudaMemsetAsync(ctx->d_sys_iter.p, 0, sizeof(unsigned long long), st));
-  if (df) launch_fill_u_df(va, ctx->udf.p, st);
-  else launch_fill_u(va, ctx->u64.p, st);
+  const double* rho_dof = ctx->have_rho ? ctx->d_rho_dof.p : nullptr;
+  if (df) launch_fill_u_df(va, ctx->udf.p, rho_dof, st);
+  else launch_fill_u(va, ctx->u64.p, rho_dof, st);
   CKL();
   int64_t& L = ctx->st_launches;
   L = 1;

@@ -29,6 +29,10 @@ struct bt_ctx {
 
   // device copies of the mesh and the contribution lists
   bt::DBuf<double> d_xyz, d_D, d_face_kappa, d_geo, d_fcoef;
+  // relaxation and initial condition per compartment (bt_set_relaxation)
+  std::vector<double> cm_invT2, cm_rho;
+  bool have_rho = false;
+  bt::DBuf<double> d_invT2, d_rho_dof;
   bt::DBuf<int32_t> d_tets, d_cmpt, d_face_ta, d_tc, d_fc, d_rp, d_col;
   bt::DBuf<int8_t> d_face_lv;
   bt::DBuf<int64_t> d_tc_ptr, d_fc_ptr;

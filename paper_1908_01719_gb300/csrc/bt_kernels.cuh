@@ -16,6 +16,7 @@ struct AsmArgs {
   const int32_t* tets;
   const int32_t* cmpt;
   const double* Dc;
+  const double* invT2c;  // [n_cmpt] 1/T2 per compartment (or null: none)
   double centre[3];
   int64_t nt, nf, nnz;
   const int32_t* face_ta;
@@ -25,9 +26,9 @@ struct AsmArgs {
   const int32_t* tc;
   const int64_t* fc_ptr;
   const int32_t* fc;
-  double* geo;     // 26 nt
+  double* geo;     // 27 nt
   double* fcoef;   // nf
-  double* planes;  // 10 nnz
+  double* planes;  // 11 nnz
 };
 void launch_assembly(const AsmArgs& a, cudaStream_t st);
 
@@ -220,7 +221,7 @@ void launch_krylov_init_f32_df(const OpArgs& op, const VecArgs& va, const float4
                                double tol, RedScratch rs, int conj, int sms, cudaStream_t st);
 void launch_signal_df(const VecArgs& va, const double* w, const float4* u, double* S, RedScratch rs, int sms,
                       cudaStream_t st);
-void launch_fill_u_df(const VecArgs& va, float4* u, cudaStream_t st);
+void launch_fill_u_df(const VecArgs& va, float4* u, const double* rho, cudaStream_t st);
 
 void launch_spmm_krylov_f64_narrow(const OpArgs& op, const double2* p, double2* q, const KrylovState& ks,
                                    RedScratch rs, int conj, int sms, cudaStream_t st);
@@ -273,7 +274,7 @@ void launch_krylov_p_f64(const OpArgs& op, const VecArgs& va, const double2* r, 
 
 void launch_axpy_u(const VecArgs& va, const double2* d, double2* u, const KrylovState& ks,
                    const RefineState& rf, int sms, cudaStream_t st);
-void launch_fill_u(const VecArgs& va, double2* u, cudaStream_t st);
+void launch_fill_u(const VecArgs& va, double2* u, const double* rho, cudaStream_t st);
 void launch_extract_state(const void* u, int df, int64_t row0, int64_t rows, int Rp, int col, double2* out,
                           int sms, cudaStream_t st);
 void launch_signal(const VecArgs& va, const double* w, const double2* u, double* S, RedScratch rs, int sms,

@@ -19,12 +19,13 @@
 namespace bt {
 
 // geometry record of one tetrahedron: vol, G[4][3], Xc[4][3] (relative to the
-// box centre), D
-static constexpr int TG = 26;
+// box centre), D, 1/T2
+static constexpr int TG = 27;
 
 __global__ void k_tet_geom(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
                            const int32_t* __restrict__ cmpt, const double* __restrict__ Dc,
-                           double cx, double cy, double cz, int64_t nt, double* __restrict__ out) {
+                           const double* __restrict__ invT2c, double cx, double cy, double cz, int64_t nt,
+                           double* __restrict__ out) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double X[4][3];
@@ -72,6 +73,7 @@ __global__ void k_tet_geom(const double* __restrict__ xyz, const int32_t* __rest
   for (int a = 0; a < 4; ++a)
     for (int k = 0; k < 3; ++k) o[13 + 3 * a + k] = X[a][k] - c[k];
   o[25] = Dc[cmpt[t]];
+  o[26] = invT2c ? invT2c[cmpt[t]] : 0.0;
 }
 
 // kappa |F| / 12 per interface face
@@ -98,27 +100,30 @@ __global__ void k_face_coef(const double* __restrict__ xyz, const int32_t* __res
 }
 
 // One thread per slot of the pattern: sums that slot's tetrahedron and face
-// contributions (in increasing element order) into the ten value planes
-// M, K, J, MD, Mx, My, Mz, Ex, Ey, Ez (plane stride nnz).
+// contributions (in increasing element order) into the eleven value planes
+// M, K, J, MD, Mx, My, Mz, Ex, Ey, Ez, MR (plane stride nnz); MR is the mass
+// weighted by 1/T2 of each element's compartment (the relaxation term
+// (U / T2, v) of the weak form).
 __global__ void k_assemble_slots(const double* __restrict__ geo, const int64_t* __restrict__ tc_ptr,
                                  const int32_t* __restrict__ tc, const int64_t* __restrict__ fc_ptr,
                                  const int32_t* __restrict__ fc, const double* __restrict__ fcoef,
                                  int64_t nnz, double* __restrict__ planes) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= nnz) return;
-  double m = 0, kk = 0, md = 0, mx = 0, my = 0, mz = 0, ex = 0, ey = 0, ez = 0, jj = 0;
+  double m = 0, kk = 0, md = 0, mx = 0, my = 0, mz = 0, ex = 0, ey = 0, ez = 0, jj = 0, mr = 0;
   for (int64_t q = tc_ptr[s]; q < tc_ptr[s + 1]; ++q) {
     int32_t code = tc[q];
     int32_t t = code >> 4;
     int i = (code >> 2) & 3, j = code & 3;
     const double* g = geo + (int64_t)TG * t;
-    double vol = g[0], D = g[25];
+    double vol = g[0], D = g[25], rT2 = g[26];
     const double* Gi = g + 1 + 3 * i;
     const double* Gj = g + 1 + 3 * j;
     const double* Xc = g + 13;
     double mass = vol * (i == j ? 0.1 : 0.05);
     m += mass;
     md += D * mass;
+    mr += rT2 * mass;
     kk += D * vol * (Gi[0] * Gj[0] + Gi[1] * Gj[1] + Gi[2] * Gj[2]);
     double mom[3];
     for (int k = 0; k < 3; ++k) {
@@ -152,10 +157,11 @@ __global__ void k_assemble_slots(const double* __restrict__ geo, const int64_t* 
   planes[7 * nnz + s] = ex;
   planes[8 * nnz + s] = ey;
   planes[9 * nnz + s] = ez;
+  planes[10 * nnz + s] = mr;
 }
 
 // Step planes for theta and dt, per slot:
-//   A0 = M + theta dt (K + J), KJ = K + J
+//   A0 = M + theta dt (K + J + MR), KJ = K + J + MR (MR = 0 without relaxation)
 //   pk64 = {A0, d0, d1, d2} (FP64), pk32 = same in FP32,
 //   direction planes d = (Mx,My,Mz) in the lab frame, (Ex,Ey,Ez) transformed.
 __global__ void k_derive_planes(const double* __restrict__ planes, int64_t nnz, double thdt, int transformed,
@@ -168,7 +174,7 @@ __global__ void k_derive_planes(const double* __restrict__ planes, int64_t nnz, 
   double m = planes[s], k = planes[nnz + s], j = planes[2 * nnz + s], md = planes[3 * nnz + s];
   int o = transformed ? 7 : 4;
   double d0 = planes[(o + 0) * nnz + s], d1 = planes[(o + 1) * nnz + s], d2 = planes[(o + 2) * nnz + s];
-  double kj = k + j;
+  double kj = k + j + planes[10 * nnz + s];
   double a0 = m + thdt * kj;
   A0[s] = a0;
   KJ[s] = kj;
@@ -211,8 +217,9 @@ __global__ void k_row_data(const int32_t* __restrict__ rp, const int32_t* __rest
 
 void launch_assembly(const AsmArgs& a, cudaStream_t st) {
   const int TB = 256;
-  if (a.nt) k_tet_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.centre[0],
-                                                                  a.centre[1], a.centre[2], a.nt, a.geo);
+  if (a.nt) k_tet_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c,
+                                                                  a.centre[0], a.centre[1], a.centre[2], a.nt,
+                                                                  a.geo);
   if (a.nf) k_face_coef<<<(unsigned)((a.nf + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.face_ta, a.face_lv,
                                                                    a.face_kappa, a.nf, a.fcoef);
   k_assemble_slots<<<(unsigned)((a.nnz + TB - 1) / TB), TB, 0, st>>>(a.geo, a.tc_ptr, a.tc, a.fc_ptr, a.fc,

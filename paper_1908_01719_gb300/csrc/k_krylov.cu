@@ -405,11 +405,13 @@ __global__ void k_finish_step(RefineState rf, KrylovState ks, int R) {
   }
 }
 
-__global__ void k_fill_u(VecArgs va, double2* __restrict__ u) {
+// u^0: rho of the dof's compartment (1 without an initial-condition array)
+__global__ void k_fill_u(VecArgs va, double2* __restrict__ u, const double* __restrict__ rho) {
   size_t N = (size_t)va.n * va.Rp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
     int s = sys_of_col((int)(e % va.Rp), va.nb);
-    u[e] = s < va.R ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+    const double v = rho ? rho[e / va.Rp] : 1.0;
+    u[e] = s < va.R ? make_double2(v, 0.0) : make_double2(0.0, 0.0);
   }
 }
 
@@ -502,8 +504,8 @@ void launch_axpy_u(const VecArgs& va, const double2* d, double2* u, const Krylov
 void launch_finish_step(const RefineState& rf, const KrylovState& ks, int R, cudaStream_t st) {
   k_finish_step<<<1, 256, 0, st>>>(rf, ks, R);
 }
-void launch_fill_u(const VecArgs& va, double2* u, cudaStream_t st) {
-  k_fill_u<<<1024, 256, 0, st>>>(va, u);
+void launch_fill_u(const VecArgs& va, double2* u, const double* rho, cudaStream_t st) {
+  k_fill_u<<<1024, 256, 0, st>>>(va, u, rho);
 }
 void launch_set_int(int* p, int v, int n, cudaStream_t st) {
   k_set_int<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, st>>>(p, v, n);

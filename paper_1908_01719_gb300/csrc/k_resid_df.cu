@@ -284,14 +284,19 @@ void launch_resid_sub_df(const OpArgs& op, const float2* d, float4* u, float4* r
   BT_DISPATCH_NB(nb, { resid_df_t<NB_, 1, float2>(op, d, u, r, rf, rs, sms, st); })
 }
 
-__global__ void k_fill_u_df(VecArgs va, float4* __restrict__ u) {
+// u^0 in double-float: rho of the dof's compartment (1 without an initial-condition array)
+__global__ void k_fill_u_df(VecArgs va, float4* __restrict__ u, const double* __restrict__ rho) {
   size_t N = (size_t)va.n * va.Rp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
     int s = sys_of_col((int)(e % va.Rp), va.nb);
-    u[e] = s < va.R ? make_float4(1.f, 0.f, 0.f, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const double v = rho ? rho[e / va.Rp] : 1.0;
+    const float h = (float)v;
+    u[e] = s < va.R ? make_float4(h, 0.f, (float)(v - (double)h), 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
-void launch_fill_u_df(const VecArgs& va, float4* u, cudaStream_t st) { k_fill_u_df<<<1024, 256, 0, st>>>(va, u); }
+void launch_fill_u_df(const VecArgs& va, float4* u, const double* rho, cudaStream_t st) {
+  k_fill_u_df<<<1024, 256, 0, st>>>(va, u, rho);
+}
 
 }  // namespace bt
 

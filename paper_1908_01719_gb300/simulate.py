@@ -12,7 +12,8 @@ class Simulation:
     """One context holding one geometry.  `geom` is any object with the fields
     xyz, tets, tet_cmpt, D_cmpt, kappa_cmpt, periodic_mask, box_lo, box_hi,
     dt, theta, delta, Delta, TE, dirs, bvals, transformed, and optionally a
-    temporal `profile` (see profiles.py; None = PGSE)."""
+    temporal `profile` (see profiles.py; None = PGSE), per-compartment `inv_T2`
+    (1/us) and initial magnetization `rho`."""
 
     def __init__(self, geom, device: int = 0, stream: int | None = None):
         self.g = geom
@@ -25,6 +26,9 @@ class Simulation:
         self.frame = bt.BT_FRAME_TRANSFORMED if (geom.transformed or geom.periodic_mask) else bt.BT_FRAME_LAB
         seg = getattr(geom, "segments", None)
         self.G = 1 if seg is None else len(seg["node_off"]) - 1
+        inv_T2, rho = getattr(geom, "inv_T2", None), getattr(geom, "rho", None)
+        if inv_T2 is not None or rho is not None:
+            bt.bt_set_relaxation(self.ctx, inv_T2, rho)
         if device >= 0:
             bt.bt_assemble(self.ctx, geom.dt, geom.theta, self.frame)
             prof = getattr(geom, "profile", None)
