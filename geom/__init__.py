@@ -251,6 +251,8 @@ class Problem:
     # transverse relaxation 1/T2 (1/us) and initial magnetization per compartment; None = 0 / 1
     inv_T2: np.ndarray | None = None
     rho: np.ndarray | None = None
+    # anisotropic diffusion: [n_cmpt, 6] (xx, yy, zz, xy, yz, zx) in mm^2/s; None = isotropic D_cmpt
+    D_tensor: np.ndarray | None = None
 
     @property
     def n_cmpt(self):

@@ -115,6 +115,17 @@ bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t
  * or non-finite 1/T2 or non-finite rho. */
 bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho);
 
+/* Anisotropic diffusion (the diffusion term div(D grad U) of Section 2 with a
+ * tensor D per compartment; the survey lists per-compartment tensors as an
+ * extension): D6 [n_cmpt][6] = (xx, yy, zz, xy, yz, zx) in mm^2/s, each
+ * symmetric positive semi-definite; NULL returns to the isotropic D_cmpt.
+ * The tensor enters the stiffness K = (D grad phi_j, grad phi_i).  Lab frame
+ * only (bt_assemble with BT_FRAME_TRANSFORMED then fails with BT_EINVAL: the
+ * gauge-transformed operator would need direction-dependent D-weighted
+ * masses).  Clears the assembly like bt_set_relaxation.  BT_EINVAL for
+ * non-finite or indefinite tensors. */
+bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6);
+
 /* ---------------------------------------------------------------- assembly
  * Element-by-element, deterministic assembly on the GPU of every matrix over
  * the shared pattern (Appendix B, Eq. matrix_form; Appendix A weak form):

@@ -135,7 +135,8 @@ def assemble(p):
 
     Returns a dict with the dof map and the CSR matrices
       M   mass                              (Appendix B, matrix M)
-      K   stiffness, D-weighted             (Appendix B, matrix S)
+      K   stiffness, D-weighted             (Appendix B, matrix S; p.D_tensor gives
+                                            one 3x3 tensor per compartment)
       J   interface jump, kappa-weighted    (Appendix B, matrix I)
       Mx, My, Mz  first-moment mass         (Appendix B, matrix J = sum g_k M_k)
       MD  D-weighted mass                   (transformed frame, Appendix A)
@@ -153,7 +154,19 @@ def assemble(p):
 
     eye = np.eye(4)
     Me = vol[:, None, None] / 20.0 * (1.0 + eye)[None]
-    Ke = (Dt * vol)[:, None, None] * np.einsum("tik,tjk->tij", G, G)
+    Dten = getattr(p, "D_tensor", None)
+    if Dten is None:
+        Ke = (Dt * vol)[:, None, None] * np.einsum("tik,tjk->tij", G, G)
+    else:
+        # anisotropic diffusion: (D grad u, grad v) with one symmetric tensor
+        # per compartment, given as (xx, yy, zz, xy, yz, zx)
+        T = np.asarray(Dten, float)
+        Dm = np.empty((len(T), 3, 3))
+        Dm[:, 0, 0], Dm[:, 1, 1], Dm[:, 2, 2] = T[:, 0], T[:, 1], T[:, 2]
+        Dm[:, 0, 1] = Dm[:, 1, 0] = T[:, 3]
+        Dm[:, 1, 2] = Dm[:, 2, 1] = T[:, 4]
+        Dm[:, 2, 0] = Dm[:, 0, 2] = T[:, 5]
+        Ke = vol[:, None, None] * np.einsum("tik,tkl,tjl->tij", G, Dm[p.tet_cmpt], G)
     centre = 0.5 * (np.asarray(p.box_lo, float) + np.asarray(p.box_hi, float))
     Xc = X - centre
     c3 = _cubic_moments()

@@ -143,6 +143,7 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
   ctx->seg_row0 = {0, ctx->mesh.n_dof};
   ctx->cm_invT2.assign(n_cmpt, 0.0);
   ctx->cm_rho.assign(n_cmpt, 1.0);
+  ctx->cm_Dten.clear();
   ctx->have_rho = false;
   if (ctx->host_only) return BT_OK;
   CK(cudaSetDevice(ctx->device));
@@ -232,6 +233,33 @@ bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho
   return BT_OK;
 }
 
+bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6) {
+  if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
+  if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_set_diffusion_tensor: no mesh");
+  const int nc = ctx->mesh.n_cmpt;
+  if (!D6) {
+    ctx->cm_Dten.clear();
+  } else {
+    std::vector<double> t(D6, D6 + 6 * (size_t)nc);
+    for (int c = 0; c < nc; ++c) {
+      const double* d = &t[6 * (size_t)c];
+      for (int k = 0; k < 6; ++k)
+        if (!std::isfinite(d[k])) return fail(ctx, BT_EINVAL, "bt_set_diffusion_tensor: non-finite entry");
+      // positive semi-definite: leading minors of [[xx, xy, zx], [xy, yy, yz], [zx, yz, zz]]
+      const double m1 = d[0], m2 = d[0] * d[1] - d[3] * d[3];
+      const double m3 = d[0] * (d[1] * d[2] - d[4] * d[4]) - d[3] * (d[3] * d[2] - d[4] * d[5]) +
+                        d[5] * (d[3] * d[4] - d[1] * d[5]);
+      const double sc = std::max({std::fabs(d[0]), std::fabs(d[1]), std::fabs(d[2]), 1e-300});
+      if (m1 < 0 || d[1] < 0 || d[2] < 0 || m2 < -1e-12 * sc * sc || m3 < -1e-12 * sc * sc * sc)
+        return fail(ctx, BT_EINVAL, "bt_set_diffusion_tensor: tensor not positive semi-definite");
+    }
+    ctx->cm_Dten = t;
+  }
+  ctx->assembled = ctx->have_seq = false;
+  return BT_OK;
+}
+
 bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
@@ -241,14 +269,18 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
     return fail(ctx, BT_EINVAL, "bt_assemble: need dt > 0, 0 < theta <= 1, flags in {LAB, TRANSFORMED}");
   if (ctx->mesh.pmask && flags != BT_FRAME_TRANSFORMED)
     return fail(ctx, BT_EINVAL, "bt_assemble: periodic boxes need BT_FRAME_TRANSFORMED");
+  if (!ctx->cm_Dten.empty() && flags == BT_FRAME_TRANSFORMED)
+    return fail(ctx, BT_EINVAL, "bt_assemble: diffusion tensors need the lab frame");
   CK(cudaSetDevice(ctx->device));
   const HostMesh& m = ctx->mesh;
   const int64_t nnz = m.nnz, n = m.n_dof;
   cudaStream_t st = ctx->stream;
-  CK(ctx->d_geo.alloc(27 * (size_t)m.n_tets));
+  CK(ctx->d_geo.alloc(33 * (size_t)m.n_tets));
   CK(ctx->d_fcoef.alloc(std::max<int64_t>(1, m.n_face)));
   CK(ctx->d_planes.alloc(11 * (size_t)nnz));
   CK(upload(ctx->d_invT2, ctx->cm_invT2, st));
+  if (!ctx->cm_Dten.empty()) CK(upload(ctx->d_Dten, ctx->cm_Dten, st));
+  else ctx->d_Dten.free();
   if (ctx->have_rho) {
     std::vector<double> rd(n);
     for (int64_t i = 0; i < n; ++i) rd[i] = ctx->cm_rho[m.dof_cmpt[i]];
@@ -262,6 +294,7 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   a.cmpt = ctx->d_cmpt.p;
   a.Dc = ctx->d_D.p;
   a.invT2c = ctx->d_invT2.p;
+  a.Dten = ctx->cm_Dten.empty() ? nullptr : ctx->d_Dten.p;
   for (int k = 0; k < 3; ++k) a.centre[k] = 0.5 * (m.lo[k] + m.hi[k]);
   a.nt = m.n_tets;
   a.nf = m.n_face;

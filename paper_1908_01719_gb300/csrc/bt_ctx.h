@@ -30,9 +30,9 @@ struct bt_ctx {
   // device copies of the mesh and the contribution lists
   bt::DBuf<double> d_xyz, d_D, d_face_kappa, d_geo, d_fcoef;
   // relaxation and initial condition per compartment (bt_set_relaxation)
-  std::vector<double> cm_invT2, cm_rho;
+  std::vector<double> cm_invT2, cm_rho, cm_Dten;  // cm_Dten empty: isotropic
   bool have_rho = false;
-  bt::DBuf<double> d_invT2, d_rho_dof;
+  bt::DBuf<double> d_invT2, d_rho_dof, d_Dten;
   bt::DBuf<int32_t> d_tets, d_cmpt, d_face_ta, d_tc, d_fc, d_rp, d_col;
   bt::DBuf<int8_t> d_face_lv;
   bt::DBuf<int64_t> d_tc_ptr, d_fc_ptr;

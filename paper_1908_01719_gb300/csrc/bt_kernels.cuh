@@ -17,6 +17,7 @@ struct AsmArgs {
   const int32_t* cmpt;
   const double* Dc;
   const double* invT2c;  // [n_cmpt] 1/T2 per compartment (or null: none)
+  const double* Dten;    // [n_cmpt][6] diffusion tensors (or null: isotropic Dc)
   double centre[3];
   int64_t nt, nf, nnz;
   const int32_t* face_ta;
@@ -26,7 +27,7 @@ struct AsmArgs {
   const int32_t* tc;
   const int64_t* fc_ptr;
   const int32_t* fc;
-  double* geo;     // 27 nt
+  double* geo;     // 33 nt
   double* fcoef;   // nf
   double* planes;  // 11 nnz
 };

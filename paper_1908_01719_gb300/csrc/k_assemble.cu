@@ -19,13 +19,13 @@
 namespace bt {
 
 // geometry record of one tetrahedron: vol, G[4][3], Xc[4][3] (relative to the
-// box centre), D, 1/T2
-static constexpr int TG = 27;
+// box centre), D, 1/T2, diffusion tensor (xx, yy, zz, xy, yz, zx)
+static constexpr int TG = 33;
 
 __global__ void k_tet_geom(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
                            const int32_t* __restrict__ cmpt, const double* __restrict__ Dc,
-                           const double* __restrict__ invT2c, double cx, double cy, double cz, int64_t nt,
-                           double* __restrict__ out) {
+                           const double* __restrict__ invT2c, const double* __restrict__ Dten, double cx,
+                           double cy, double cz, int64_t nt, double* __restrict__ out) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double X[4][3];
@@ -72,8 +72,10 @@ __global__ void k_tet_geom(const double* __restrict__ xyz, const int32_t* __rest
   const double c[3] = {cx, cy, cz};
   for (int a = 0; a < 4; ++a)
     for (int k = 0; k < 3; ++k) o[13 + 3 * a + k] = X[a][k] - c[k];
-  o[25] = Dc[cmpt[t]];
-  o[26] = invT2c ? invT2c[cmpt[t]] : 0.0;
+  const int cm = cmpt[t];
+  o[25] = Dc[cm];
+  o[26] = invT2c ? invT2c[cm] : 0.0;
+  for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
 }
 
 // kappa |F| / 12 per interface face
@@ -124,7 +126,12 @@ __global__ void k_assemble_slots(const double* __restrict__ geo, const int64_t* 
     m += mass;
     md += D * mass;
     mr += rT2 * mass;
-    kk += D * vol * (Gi[0] * Gj[0] + Gi[1] * Gj[1] + Gi[2] * Gj[2]);
+    // (D grad phi_j) . grad phi_i with the element's symmetric tensor
+    const double* T = g + 27;
+    const double DG0 = T[0] * Gj[0] + T[3] * Gj[1] + T[5] * Gj[2];
+    const double DG1 = T[3] * Gj[0] + T[1] * Gj[1] + T[4] * Gj[2];
+    const double DG2 = T[5] * Gj[0] + T[4] * Gj[1] + T[2] * Gj[2];
+    kk += vol * (Gi[0] * DG0 + Gi[1] * DG1 + Gi[2] * DG2);
     double mom[3];
     for (int k = 0; k < 3; ++k) {
       double S = Xc[k] + Xc[3 + k] + Xc[6 + k] + Xc[9 + k];
@@ -218,8 +225,8 @@ __global__ void k_row_data(const int32_t* __restrict__ rp, const int32_t* __rest
 void launch_assembly(const AsmArgs& a, cudaStream_t st) {
   const int TB = 256;
   if (a.nt) k_tet_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c,
-                                                                  a.centre[0], a.centre[1], a.centre[2], a.nt,
-                                                                  a.geo);
+                                                                  a.Dten, a.centre[0], a.centre[1], a.centre[2],
+                                                                  a.nt, a.geo);
   if (a.nf) k_face_coef<<<(unsigned)((a.nf + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.face_ta, a.face_lv,
                                                                    a.face_kappa, a.nf, a.fcoef);
   k_assemble_slots<<<(unsigned)((a.nnz + TB - 1) / TB), TB, 0, st>>>(a.geo, a.tc_ptr, a.tc, a.fc_ptr, a.fc,

@@ -13,7 +13,7 @@ class Simulation:
     xyz, tets, tet_cmpt, D_cmpt, kappa_cmpt, periodic_mask, box_lo, box_hi,
     dt, theta, delta, Delta, TE, dirs, bvals, transformed, and optionally a
     temporal `profile` (see profiles.py; None = PGSE), per-compartment `inv_T2`
-    (1/us) and initial magnetization `rho`."""
+    (1/us) and initial magnetization `rho`, and `D_tensor` (lab frame)."""
 
     def __init__(self, geom, device: int = 0, stream: int | None = None):
         self.g = geom
@@ -29,6 +29,8 @@ class Simulation:
         inv_T2, rho = getattr(geom, "inv_T2", None), getattr(geom, "rho", None)
         if inv_T2 is not None or rho is not None:
             bt.bt_set_relaxation(self.ctx, inv_T2, rho)
+        if getattr(geom, "D_tensor", None) is not None:
+            bt.bt_set_diffusion_tensor(self.ctx, geom.D_tensor)
         if device >= 0:
             bt.bt_assemble(self.ctx, geom.dt, geom.theta, self.frame)
             prof = getattr(geom, "profile", None)

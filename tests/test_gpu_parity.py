@@ -341,3 +341,50 @@ def test_relaxation_and_initial_condition_match_oracle(sim_cls, bt, mode):
             assert (np.abs(u - U[r]) / np.abs(U[r]).max()).max() < tol
     finally:
         sim.close()
+
+
+# ---------------------------------------------------------------- anisotropic diffusion
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_diffusion_tensor_matches_oracle(sim_cls, bt, mode):
+    """Per-compartment diffusion tensors (lab frame): the stiffness plane
+    against the oracle's, then the signals."""
+    p = geom.cfg2(n=6, kappa=1e-4, bvals=(1000.0, 2500.0))
+    p.dirs = np.array([[1.0, 0.0, 0.0], [0.0, 0.6, 0.8]])
+    p.D_tensor = np.array([[2.0e-3, 1.1e-3, 0.6e-3, 0.3e-3, -0.2e-3, 0.15e-3],
+                           [1.0e-3, 1.5e-3, 2.5e-3, -0.4e-3, 0.35e-3, 0.1e-3]])
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        a = bo.assemble(p)
+        rp, col = bt.bt_get_pattern(sim.ctx)
+        v = bt.bt_get_plane(sim.ctx, "K")
+        kk = a["K"].tocsr()
+        dense = np.zeros_like(v)
+        for i in range(len(rp) - 1):
+            row = kk.getrow(i)
+            m = dict(zip(row.indices, row.data))
+            dense[rp[i]:rp[i + 1]] = [m.get(c, 0.0) for c in col[rp[i]:rp[i + 1]]]
+        assert np.abs(v - dense).max() <= 1e-13 * np.abs(dense).max()
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S, err, stat, st = sim.run(m)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()
+
+
+def test_diffusion_tensor_refused_in_transformed_frame(bt):
+    p = geom.free_periodic_box(n=3, L=5.0)
+    ctx = bt.bt_create(0)
+    try:
+        bt.bt_upload_mesh(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, 7, p.box_lo, p.box_hi)
+        bt.bt_set_diffusion_tensor(ctx, np.array([[2e-3, 1e-3, 1e-3, 0.0, 0.0, 0.0]]))
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_assemble(ctx, 50.0, 0.5, bt.BT_FRAME_TRANSFORMED)
+        assert e.value.code == bt.BT_EINVAL
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_set_diffusion_tensor(ctx, np.array([[1e-3, 1e-3, 1e-3, 2e-3, 0.0, 0.0]]))  # indefinite
+        assert e.value.code == bt.BT_EINVAL
+    finally:
+        bt.bt_destroy(ctx)
