@@ -126,6 +126,23 @@ bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho
  * non-finite or indefinite tensors. */
 bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6);
 
+/* Weak pseudo-periodic conditions on a box that is not meshed periodically
+ * (Appendix B, "Weak implementation of the pseudo-periodic BCs"): on every
+ * axis k of `axes` (bit mask, disjoint from the mesh's periodic_mask) the
+ * faces x_k = lo_k and x_k = hi_k are coupled through an artificial
+ * permeability kappa_e (um/us; <= 0 selects max D / h, h = (6 x mean
+ * tetrahedron volume)^(1/3)).  Each step treats a face implicitly and its
+ * partner face from the previous step with the phase e^{+-i q qhat_k L_k
+ * F(t_n)}: L_n = M + theta dt (A_n + kappa_e B), r_0 += theta dt kappa_e C_n
+ * u^{n-1}, B the boundary-face mass, C_n the face-mass coupling of partner
+ * faces (Appendix B weighs the partner term by 1 - theta; theta is used for
+ * both here, which is identical at theta = 1/2).  The mesh must match across
+ * the box (the partner of a node is the node at x + L_k e_k).  Lab frame and
+ * one geometry only.  Clears the assembly like bt_set_relaxation; axes = 0
+ * switches the coupling off.  BT_EINVAL for a non-matching mesh or axes that
+ * are periodic in the mesh. */
+bt_status bt_set_weak_periodic(bt_ctx* ctx, uint32_t axes, double kappa_e);
+
 /* ---------------------------------------------------------------- assembly
  * Element-by-element, deterministic assembly on the GPU of every matrix over
  * the shared pattern (Appendix B, Eq. matrix_form; Appendix A weak form):

@@ -332,7 +332,11 @@ def run_lab(p, asm=None, rhs=None, return_history=False, route=None, return_fiel
     M, KJ = asm["M"], asm["K"] + asm["J"] + asm["MR"]
     w = signal_weights(asm)
     N = p.n_steps
-    fbar, _, intF2 = sequence(p)
+    fbar, Fn, intF2 = sequence(p)
+    weak = getattr(p, "weak_periodic", None)
+    if weak:
+        from . import weakper
+        Bw, pairs, ke, Lbox = weakper.operators(p, asm, weak["axes"], weak.get("kappa_e"))
     nb = len(p.bvals)
     rhs = range(p.n_rhs) if rhs is None else rhs
     th, dt = p.theta, p.dt
@@ -347,7 +351,14 @@ def run_lab(p, asm=None, rhs=None, return_history=False, route=None, return_fiel
         for n in range(1, N + 1):
             fb = fbar[n - 1]
             A = KJ + (1j * q * fb) * Mq
-            u = sol.solve(fb, lambda: M + th * dt * A, (M - (1.0 - th) * dt * A) @ u, x0=u)
+            rhs = (M - (1.0 - th) * dt * A) @ u
+            if weak:
+                # artificial permeability on the box faces: implicit own side,
+                # partner side from the previous step with the phase of F(t_n)
+                rhs = rhs + (th * dt * ke) * (weakper.coupling(pairs, asm["n"], q, qh, Lbox, Fn[n]) @ u)
+                u = sol.solve(fb, lambda: M + th * dt * (A + ke * Bw), rhs, x0=u)
+            else:
+                u = sol.solve(fb, lambda: M + th * dt * A, rhs, x0=u)
             h.append(w @ u)
         out.append(w @ u)
         hist.append(h)

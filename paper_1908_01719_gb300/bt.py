@@ -30,7 +30,7 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats",
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
-           "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation", "bt_set_diffusion_tensor"]
+           "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation", "bt_set_diffusion_tensor", "bt_set_weak_periodic"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -78,6 +78,7 @@ def lib():
             "bt_set_profile": [P, I32, P, D],
             "bt_set_relaxation": [P, P, P],
             "bt_set_diffusion_tensor": [P, P],
+            "bt_set_weak_periodic": [P, U32, D],
             "bt_set_segments": [P, I32, P, P, P, P],
             "bt_get_tuning": [P, P, P, P, P],
             "bt_default_opts": [C.POINTER(bt_solver_opts)],
@@ -198,6 +199,11 @@ def bt_set_relaxation(ctx, inv_T2=None, rho=None):
     a = None if inv_T2 is None else np.ascontiguousarray(inv_T2, dtype=np.float64)
     b = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
     _check(ctx, lib().bt_set_relaxation(ctx, None if a is None else _ptr(a), None if b is None else _ptr(b)))
+
+
+def bt_set_weak_periodic(ctx, axes, kappa_e=0.0):
+    """Artificial-permeability coupling of the box faces on the axes of the bit mask."""
+    _check(ctx, lib().bt_set_weak_periodic(ctx, int(axes), float(kappa_e)))
 
 
 def bt_set_diffusion_tensor(ctx, D6=None):

@@ -144,6 +144,7 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
   ctx->cm_invT2.assign(n_cmpt, 0.0);
   ctx->cm_rho.assign(n_cmpt, 1.0);
   ctx->cm_Dten.clear();
+  ctx->weak_axes = 0;
   ctx->have_rho = false;
   if (ctx->host_only) return BT_OK;
   CK(cudaSetDevice(ctx->device));
@@ -233,6 +234,27 @@ bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho
   return BT_OK;
 }
 
+bt_status bt_set_weak_periodic(bt_ctx* ctx, uint32_t axes, double kappa_e) {
+  if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
+  if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_set_weak_periodic: no mesh");
+  if (axes > 7 || (axes & ctx->mesh.pmask) || !std::isfinite(kappa_e))
+    return fail(ctx, BT_EINVAL, "bt_set_weak_periodic: axes must be a mask of non-periodic axes");
+  if (axes) {
+    std::string msg;
+    WeakPeriodic wp;
+    if (int st = build_weak_periodic(ctx->mesh, axes, wp, msg)) return fail(ctx, st, "bt_set_weak_periodic: " + msg);
+    double dmax = 0;
+    for (double d : ctx->mesh.D) dmax = std::max(dmax, d);
+    ctx->weak = std::move(wp);
+    ctx->weak_kappa = kappa_e > 0 ? kappa_e : dmax / ctx->weak.h;  // max D / h by default
+  }
+  ctx->weak_axes = axes;
+  ctx->weak_kappa_in = kappa_e;
+  ctx->assembled = ctx->have_seq = false;
+  return BT_OK;
+}
+
 bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6) {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
@@ -271,6 +293,8 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
     return fail(ctx, BT_EINVAL, "bt_assemble: periodic boxes need BT_FRAME_TRANSFORMED");
   if (!ctx->cm_Dten.empty() && flags == BT_FRAME_TRANSFORMED)
     return fail(ctx, BT_EINVAL, "bt_assemble: diffusion tensors need the lab frame");
+  if (ctx->weak_axes && flags == BT_FRAME_TRANSFORMED)
+    return fail(ctx, BT_EINVAL, "bt_assemble: the weak periodic box needs the lab frame");
   CK(cudaSetDevice(ctx->device));
   const HostMesh& m = ctx->mesh;
   const int64_t nnz = m.nnz, n = m.n_dof;
@@ -279,6 +303,16 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   CK(ctx->d_fcoef.alloc(std::max<int64_t>(1, m.n_face)));
   CK(ctx->d_planes.alloc(11 * (size_t)nnz));
   CK(upload(ctx->d_invT2, ctx->cm_invT2, st));
+  if (ctx->weak_axes) {
+    std::vector<double> mb(ctx->weak.B);
+    for (double& v : mb) v *= ctx->weak_kappa;
+    CK(upload(ctx->d_MB, mb, st));
+    CK(upload(ctx->d_wrows, ctx->weak.rows, st));
+    CK(upload(ctx->d_wptr, ctx->weak.ptr, st));
+    CK(upload(ctx->d_wcol, ctx->weak.col, st));
+    CK(upload(ctx->d_ww, ctx->weak.w, st));
+    CK(upload(ctx->d_wcode, ctx->weak.code, st));
+  }
   if (!ctx->cm_Dten.empty()) CK(upload(ctx->d_Dten, ctx->cm_Dten, st));
   else ctx->d_Dten.free();
   if (ctx->have_rho) {
@@ -347,6 +381,8 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   d.diag_md64 = ctx->d_diag_md64.p;
   d.diag32 = ctx->d_diag32.p;
   d.diag_md32 = ctx->d_diag_md32.p;
+  d.MB = ctx->weak_axes ? ctx->d_MB.p : nullptr;
+  d.theta = theta;
   launch_derive(d, st);
   CKL();
   std::vector<double> w(n);
@@ -825,6 +861,8 @@ static bt_status collect_samples(bt_ctx* ctx, OpArgs op, const VecArgs& va, cons
 struct GraphRun {
   int variant;
   bool resid_halo;
+  bool weak;
+  WeakArgs wa;
   OpArgs op;
   VecArgs va;
   KrylovState ks;
@@ -892,6 +930,14 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
       launch_resid0_df_halo(op0, halo_args(ctx), ctx->udf.p, ctx->rdf.p, g.rf, rs_at(0), g.nb, cs);
     else if (g.df) launch_resid0_df(op0, ctx->udf.p, ctx->rdf.p, g.rf, rs_at(0), g.nb, ctx->sms, cs);
     else launch_resid0(op0, ctx->u64.p, ctx->r64.p, g.rf, rs_at(0), g.nb, ctx->sms, cs);
+    if (g.weak) {
+      WeakArgs wg = g.wa;
+      wg.step_dev = ctx->d_ctl.p;  // ctl[0]: the 1-based step number
+      const void* uu = g.df ? (const void*)ctx->udf.p : (const void*)ctx->u64.p;
+      void* rr = g.df ? (void*)ctx->rdf.p : (void*)ctx->r64.p;
+      launch_weak_coupling(wg, g.va, op0, uu, rr, g.df, cs);
+      launch_resid0_renorm(g.va, uu, rr, g.rf, rs_at(8), g.df, cs);
+    }
     cudaGraphConditionalHandle hR{}, hI{};
     cudaGraph_t bodyR = nullptr, bodyI = nullptr;
     cudaGraph_t top = capg_of(cs);
@@ -988,6 +1034,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   const int G = ctx->G;
   if (G > 1 && (rb != 0 || re != ctx->R)) return fail(ctx, BT_EINVAL, "bt_run: RHS ranges need a single segment");
   if (G > 1 && (learned || col)) return fail(ctx, BT_EINVAL, "bt_run: learned mode and data collection need a single segment");
+  if (G > 1 && ctx->weak_axes) return fail(ctx, BT_EINVAL, "bt_run: the weak periodic box needs a single segment");
   if (o.max_iter < 1 || o.max_refine < 1 || o.check_every < 1 || !(o.tol_fp64 > 0) || !(o.tol_inner > 0) ||
       !(o.tol_ref > 0))
     return fail(ctx, BT_EINVAL, "bt_run: bad solver options");
@@ -1139,6 +1186,15 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   const double feps = 1e-14 * ctx->wmax;
   rf.floor_c2 = feps * feps;
   auto rs_at = [&](int c) { return RedScratch{ctx->red_part.p, ctx->red_counter.p + c}; };
+  // weak pseudo-periodic box: partner-face coupling rows and F(t_n)
+  const bool weak = ctx->weak_axes != 0;
+  WeakArgs wa{};
+  if (weak) {
+    CK(upload(ctx->d_Fstep, ctx->F, st));
+    wa = WeakArgs{ctx->d_wrows.p, ctx->d_wptr.p, ctx->d_wcol.p, ctx->d_ww.p, ctx->d_wcode.p,
+                  (int64_t)ctx->weak.rows.size(), {ctx->weak.L[0], ctx->weak.L[1], ctx->weak.L[2]},
+                  ctx->theta * ctx->dt * ctx->weak_kappa, ctx->d_Fstep.p, nullptr, 0};
+  }
 
   // halo tiles, the tuned Krylov variant for the FP32 inner solves and the
   // tuned double-float residual kernel
@@ -1185,7 +1241,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   // production path: the captured time step (mixed mode)
   bool graph_done = false;
   if (!plain && !learned && !col && !prof && !(o.flags & BT_OPT_NO_GRAPH)) {
-    GraphRun gr{variant, resid_halo, op, va, ks, rf, df, conj, nb, N, o.tol_inner};
+    GraphRun gr{variant, resid_halo, weak, wa, op, va, ks, rf, df, conj, nb, N, o.tol_inner};
     int64_t gi = 0, gp = 0;
     if (run_graph(ctx, gr, o, Rs, G, &gi, &gp) == BT_OK) {
       graph_done = true;
@@ -1194,6 +1250,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       ctx->st_refine = gp;
       ctx->st_resid = N + gp;
       L += variant == 1 ? 5 * (int64_t)N + 6 * gp + 3 * gi : 5 * (int64_t)N + 4 * gp + 4 * gi;
+      if (weak) L += 2 * (int64_t)N;
     }
   }
   double last_fq = NAN;
@@ -1227,6 +1284,14 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       else if (narrow) launch_resid0_narrow(op, ctx->u64.p, ctx->r64.p, rf, rs_at(0), ctx->sms, st);
       else launch_resid0(op, ctx->u64.p, ctx->r64.p, rf, rs_at(0), nb, ctx->sms, st);
     });
+    if (weak) {
+      wa.step_host = step;
+      const void* uu = df ? (const void*)ctx->udf.p : (const void*)ctx->u64.p;
+      void* rr = df ? (void*)ctx->rdf.p : (void*)ctx->r64.p;
+      launch_weak_coupling(wa, va, op, uu, rr, df, st);
+      launch_resid0_renorm(va, uu, rr, rf, rs_at(8), df, st);
+      L += 2;
+    }
     CKL();
     ctx->st_resid++;
     op.coef = c_L;

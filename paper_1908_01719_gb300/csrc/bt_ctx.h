@@ -33,6 +33,13 @@ struct bt_ctx {
   std::vector<double> cm_invT2, cm_rho, cm_Dten;  // cm_Dten empty: isotropic
   bool have_rho = false;
   bt::DBuf<double> d_invT2, d_rho_dof, d_Dten;
+  // weak pseudo-periodic box (bt_set_weak_periodic)
+  uint32_t weak_axes = 0;
+  double weak_kappa_in = 0, weak_kappa = 0;
+  bt::WeakPeriodic weak;
+  bt::DBuf<double> d_MB, d_ww, d_Fstep;
+  bt::DBuf<int32_t> d_wrows, d_wptr, d_wcol;
+  bt::DBuf<int8_t> d_wcode;
   bt::DBuf<int32_t> d_tets, d_cmpt, d_face_ta, d_tc, d_fc, d_rp, d_col;
   bt::DBuf<int8_t> d_face_lv;
   bt::DBuf<int64_t> d_tc_ptr, d_fc_ptr;

@@ -75,6 +75,23 @@ constexpr int HALO_TMAX = 128;
 constexpr int HALO_EMAX = 448;
 constexpr int HALO_SMEM_BUDGET = 96 * 1024;
 
+// Weak pseudo-periodic coupling of the box faces (artificial permeability,
+// Appendix B): the boundary-face mass B on both sides of every selected axis
+// (as values on the CSR slots) and the face-mass coupling of each face with
+// its partner face, as rows of (col, weight, axis | sign << 2) sorted by row.
+// The mesh must match across the box (partner node at x + L_k e_k).
+struct WeakPeriodic {
+  std::vector<double> B;        // [nnz] boundary-face mass per slot
+  std::vector<int32_t> rows;    // [nr] boundary dofs with coupling entries
+  std::vector<int32_t> ptr;     // [nr + 1]
+  std::vector<int32_t> col;     // partner dof
+  std::vector<double> w;        // face-mass weight
+  std::vector<int8_t> code;     // axis (bits 0-1), sign bit 2 (set = -1)
+  double L[3] = {0, 0, 0};      // box lengths
+  double h = 0;                 // (6 x mean tetrahedron volume)^(1/3)
+};
+int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std::string& msg);
+
 // ---------------------------------------------------------------- device helpers
 template <class T>
 struct DBuf {

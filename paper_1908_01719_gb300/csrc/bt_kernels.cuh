@@ -54,6 +54,8 @@ struct DeriveArgs {
   double* diag_md64;
   float4* diag32;
   float* diag_md32;
+  const double* MB;  // [nnz] kappa_e x boundary-face mass (weak periodic box) or null
+  double theta;
 };
 void launch_derive(const DeriveArgs& a, cudaStream_t st);
 
@@ -157,6 +159,21 @@ struct VecArgs {
   const double* diag_md64;
   const float4* diag32;
   const float* diag_md32;
+};
+
+// Weak pseudo-periodic coupling rows on the device (WeakPeriodic).
+struct WeakArgs {
+  const int32_t* rows;
+  const int32_t* ptr;
+  const int32_t* col;
+  const double* w;
+  const int8_t* code;
+  int64_t nr;
+  double L[3];
+  double scale;         // theta dt kappa_e
+  const double* F;      // [N + 1] F(t_n)
+  const int* step_dev;  // captured step counter, or null
+  int step_host;
 };
 
 // partial-sum scratch for the deterministic last-block reductions
@@ -276,6 +293,12 @@ void launch_krylov_p_f64(const OpArgs& op, const VecArgs& va, const double2* r, 
 void launch_axpy_u(const VecArgs& va, const double2* d, double2* u, const KrylovState& ks,
                    const RefineState& rf, int sms, cudaStream_t st);
 void launch_fill_u(const VecArgs& va, double2* u, const double* rho, cudaStream_t st);
+// r_0 += theta dt kappa_e C_n u (partner faces) and the step-start
+// refinement bookkeeping redone on the new r_0 (weak pseudo-periodic box)
+void launch_weak_coupling(const WeakArgs& wa, const VecArgs& va, const OpArgs& op, const void* u, void* r, int df,
+                          cudaStream_t st);
+void launch_resid0_renorm(const VecArgs& va, const void* u, const void* r, const RefineState& rf, RedScratch rs,
+                          int df, cudaStream_t st);
 void launch_extract_state(const void* u, int df, int64_t row0, int64_t rows, int Rp, int col, double2* out,
                           int sms, cudaStream_t st);
 void launch_signal(const VecArgs& va, const double* w, const double2* u, double* S, RedScratch rs, int sms,

@@ -11,7 +11,9 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
+#include <tuple>
 #include <thread>
 
 #include "bt_internal.h"
@@ -444,6 +446,137 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
   t.u0.push_back((int32_t)t.ucol.size());
   t.e0.push_back((int32_t)t.lidx.size());
   t.rowe.push_back((int32_t)t.lidx.size());
+}
+
+int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std::string& msg) {
+  wp = WeakPeriodic();
+  double Lmax = 0, vsum = 0;
+  for (int k = 0; k < 3; ++k) {
+    wp.L[k] = m.hi[k] - m.lo[k];
+    Lmax = std::max(Lmax, wp.L[k]);
+  }
+  const double tol = 1e-9 * Lmax;
+  static const int LOC[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  auto X = [&](int32_t v, int k) { return m.xyz[3 * (size_t)v + k]; };
+  for (int64_t t = 0; t < m.n_tets; ++t) {
+    const int32_t* tv = &m.tets[4 * t];
+    double e[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 3; ++k) e[a][k] = X(tv[a + 1], k) - X(tv[0], k);
+    vsum += std::fabs(e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                      e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                      e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0])) / 6.0;
+  }
+  wp.h = std::cbrt(6.0 * vsum / (double)m.n_tets);
+  wp.B.assign(m.nnz, 0.0);
+  auto slot = [&](int32_t r, int32_t c) -> int64_t {
+    const int32_t* b = &m.col[m.row_ptr[r]];
+    const int32_t* e = &m.col[m.row_ptr[r + 1]];
+    const int32_t* it = std::lower_bound(b, e, c);
+    return (it != e && *it == c) ? m.row_ptr[r] + (it - b) : -1;
+  };
+  struct Face {
+    int64_t t;
+    int lf;
+  };
+  std::vector<std::tuple<int32_t, int32_t, double, int8_t>> ent;  // row, col, w, code
+  for (int k = 0; k < 3; ++k) {
+    if (!((axes >> k) & 1)) continue;
+    std::vector<Face> side[2];
+    for (int64_t t = 0; t < m.n_tets; ++t)
+      for (int f = 0; f < 4; ++f)
+        for (int sd = 0; sd < 2; ++sd) {
+          const double plane = sd ? m.hi[k] : m.lo[k];
+          bool on = true;
+          for (int a = 0; a < 3; ++a) on &= std::fabs(X(m.tets[4 * t + LOC[f][a]], k) - plane) < tol;
+          if (on) side[sd].push_back({t, f});
+        }
+    // slave faces by their sorted node triple; slave nodes by coordinates
+    std::map<std::array<int32_t, 3>, Face> sface;
+    std::map<std::array<int64_t, 3>, int32_t> snode;
+    auto qkey = [&](double x, double y, double z) {
+      return std::array<int64_t, 3>{(int64_t)std::llround(x / tol), (int64_t)std::llround(y / tol),
+                                    (int64_t)std::llround(z / tol)};
+    };
+    for (const Face& f : side[1]) {
+      std::array<int32_t, 3> tri;
+      for (int a = 0; a < 3; ++a) {
+        tri[a] = m.tets[4 * f.t + LOC[f.lf][a]];
+        snode[qkey(X(tri[a], 0), X(tri[a], 1), X(tri[a], 2))] = tri[a];
+      }
+      std::sort(tri.begin(), tri.end());
+      sface[tri] = f;
+    }
+    for (int sd = 0; sd < 2; ++sd)
+      for (const Face& f : side[sd]) {
+        int32_t v[3], dof[3];
+        double P[3][3];
+        for (int a = 0; a < 3; ++a) {
+          v[a] = m.tets[4 * f.t + LOC[f.lf][a]];
+          dof[a] = m.tet_dof[4 * f.t + LOC[f.lf][a]];
+          for (int kk = 0; kk < 3; ++kk) P[a][kk] = X(v[a], kk);
+        }
+        const double u1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+        const double u2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+        const double cx = u1[1] * u2[2] - u1[2] * u2[1], cy = u1[2] * u2[0] - u1[0] * u2[2],
+                     cz = u1[0] * u2[1] - u1[1] * u2[0];
+        const double area = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            const int64_t sl = slot(dof[a], dof[b]);
+            if (sl < 0) {
+              msg = "boundary face entry outside the pattern";
+              return BT_EINVAL;
+            }
+            wp.B[sl] += area / 12.0 * (a == b ? 2.0 : 1.0);
+          }
+        if (sd == 1) continue;
+        // master face: partner nodes at x + L_k e_k and the slave face holding them
+        int32_t pv[3];
+        for (int a = 0; a < 3; ++a) {
+          double y[3] = {P[a][0], P[a][1], P[a][2]};
+          y[k] += wp.L[k];
+          auto it = snode.find(qkey(y[0], y[1], y[2]));
+          if (it == snode.end()) {
+            msg = "the mesh does not match across the box on axis " + std::to_string(k);
+            return BT_EINVAL;
+          }
+          pv[a] = it->second;
+        }
+        std::array<int32_t, 3> tri = {pv[0], pv[1], pv[2]};
+        std::sort(tri.begin(), tri.end());
+        auto fit = sface.find(tri);
+        if (fit == sface.end()) {
+          msg = "the mesh does not match across the box on axis " + std::to_string(k);
+          return BT_EINVAL;
+        }
+        const Face& g = fit->second;
+        int32_t pdof[3];
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c)
+            if (m.tets[4 * g.t + LOC[g.lf][c]] == pv[a]) pdof[a] = m.tet_dof[4 * g.t + LOC[g.lf][c]];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            const double wt = area / 12.0 * (a == b ? 2.0 : 1.0);
+            ent.emplace_back(dof[a], pdof[b], wt, (int8_t)k);           // master row: slave value, +phase
+            ent.emplace_back(pdof[a], dof[b], wt, (int8_t)(k | 4));     // slave row: master value, -phase
+          }
+      }
+  }
+  std::stable_sort(ent.begin(), ent.end(),
+                   [](const auto& x, const auto& y) { return std::get<0>(x) < std::get<0>(y); });
+  for (size_t i = 0; i < ent.size(); ++i) {
+    const int32_t r = std::get<0>(ent[i]);
+    if (wp.rows.empty() || wp.rows.back() != r) {
+      wp.rows.push_back(r);
+      wp.ptr.push_back((int32_t)i);
+    }
+    wp.col.push_back(std::get<1>(ent[i]));
+    wp.w.push_back(std::get<2>(ent[i]));
+    wp.code.push_back(std::get<3>(ent[i]));
+  }
+  wp.ptr.push_back((int32_t)ent.size());
+  return BT_OK;
 }
 
 int build_host_mesh(HostMesh& m, std::string& msg) {

@@ -168,10 +168,12 @@ __global__ void k_assemble_slots(const double* __restrict__ geo, const int64_t* 
 }
 
 // Step planes for theta and dt, per slot:
-//   A0 = M + theta dt (K + J + MR), KJ = K + J + MR (MR = 0 without relaxation)
+//   A0 = M + theta dt (K + J + MR + MB), KJ = K + J + MR + theta MB
+//   (MR = 0 without relaxation, MB = 0 without the weak periodic box)
 //   pk64 = {A0, d0, d1, d2} (FP64), pk32 = same in FP32,
 //   direction planes d = (Mx,My,Mz) in the lab frame, (Ex,Ey,Ez) transformed.
-__global__ void k_derive_planes(const double* __restrict__ planes, int64_t nnz, double thdt, int transformed,
+__global__ void k_derive_planes(const double* __restrict__ planes, const double* __restrict__ MB, double theta,
+                                int64_t nnz, double thdt, int transformed,
                                 double* __restrict__ A0, double* __restrict__ KJ, double4* __restrict__ pk64,
                                 float4* __restrict__ pk32, float* __restrict__ md32,
                                 float4* __restrict__ pkhi, float4* __restrict__ pklo,
@@ -181,8 +183,12 @@ __global__ void k_derive_planes(const double* __restrict__ planes, int64_t nnz, 
   double m = planes[s], k = planes[nnz + s], j = planes[2 * nnz + s], md = planes[3 * nnz + s];
   int o = transformed ? 7 : 4;
   double d0 = planes[(o + 0) * nnz + s], d1 = planes[(o + 1) * nnz + s], d2 = planes[(o + 2) * nnz + s];
-  double kj = k + j + planes[10 * nnz + s];
-  double a0 = m + thdt * kj;
+  // the artificial-permeability boundary mass enters L with theta dt and the
+  // step-start operator (R - L) with theta dt, i.e. P0 = K + J + MR + theta MB
+  const double base = k + j + planes[10 * nnz + s];
+  const double mb = MB ? MB[s] : 0.0;
+  double kj = base + theta * mb;
+  double a0 = m + thdt * (base + mb);
   A0[s] = a0;
   KJ[s] = kj;
   pk64[s] = make_double4(a0, d0, d1, d2);
@@ -236,7 +242,7 @@ void launch_assembly(const AsmArgs& a, cudaStream_t st) {
 void launch_derive(const DeriveArgs& a, cudaStream_t st) {
   const int TB = 256;
   k_derive_planes<<<(unsigned)((a.nnz + TB - 1) / TB), TB, 0, st>>>(
-      a.planes, a.nnz, a.thdt, a.transformed, a.A0, a.KJ, a.pk64, a.pk32, a.md32, a.pkhi, a.pklo, a.kjmd_hi,
+      a.planes, a.MB, a.theta, a.nnz, a.thdt, a.transformed, a.A0, a.KJ, a.pk64, a.pk32, a.md32, a.pkhi, a.pklo, a.kjmd_hi,
       a.kjmd_lo);
   k_row_data<<<(unsigned)((a.n + TB - 1) / TB), TB, 0, st>>>(a.rp, a.col, a.planes, a.pk64, a.nnz, a.n, a.w,
                                                             a.diag64, a.diag_md64, a.diag32, a.diag_md32);

@@ -809,3 +809,94 @@ void launch_flush_x(const VecArgs& va, float2* x, const float2* pA, const float2
   k_clear_pend<<<(n + 255) / 256, 256, 0, st>>>(ks, n);
 }
 }  // namespace bt
+
+// ---------------------------------------------------------------- weak pseudo-periodic coupling
+namespace bt {
+__device__ __forceinline__ void store_res(double2* p, size_t e, double2 v) { p[e] = v; }
+__device__ __forceinline__ void store_res(float4* p, size_t e, double2 v) {
+  const float hr = (float)v.x, hi = (float)v.y;
+  p[e] = make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
+}
+
+// r_i += scale sum_j w_ij e^{i sign q qhat_k L_k F_n} u_j over the partner-face
+// entries of boundary row i (Appendix B, explicit partner side of the
+// artificial-permeability condition), for every system (one geometry).
+template <class T>
+__global__ void __launch_bounds__(256) k_weak_coupling(WeakArgs wa, VecArgs va, OpArgs op, const T* __restrict__ u,
+                                                       T* __restrict__ r) {
+  const double F = wa.F[wa.step_dev ? *wa.step_dev : wa.step_host];
+  for (int64_t k = blockIdx.x; k < wa.nr; k += gridDim.x) {
+    const int row = wa.rows[k];
+    const int e0 = wa.ptr[k], e1 = wa.ptr[k + 1];
+    for (int c = threadIdx.x; c < va.Rp; c += blockDim.x) {
+      const int s = sys_of_col(c, va.nb);
+      if (s >= va.R) continue;
+      const double q = op.q[s];
+      double2 acc = make_double2(0, 0);
+      for (int e = e0; e < e1; ++e) {
+        const int code = wa.code[e];
+        const int ax = code & 3;
+        const double phi = ((code & 4) ? -1.0 : 1.0) * q * op.qhat[3 * s + ax] * wa.L[ax] * F;
+        double sn, cs;
+        sincos(phi, &sn, &cs);
+        const double2 v = load_res(u, (size_t)wa.col[e] * va.Rp + c);
+        acc.x += wa.w[e] * (cs * v.x - sn * v.y);
+        acc.y += wa.w[e] * (cs * v.y + sn * v.x);
+      }
+      const size_t er = (size_t)row * va.Rp + c;
+      double2 rv = load_res(r, er);
+      rv.x += wa.scale * acc.x;
+      rv.y += wa.scale * acc.y;
+      store_res(r, er, rv);
+    }
+  }
+}
+
+// The step-start bookkeeping of the refinement again, after the coupling
+// changed r_0: |r_0|^2 and |u|^2 per system, then refine_finish(0) with every
+// system of the (single) geometry active.
+template <class T>
+__global__ void __launch_bounds__(256) k_resid0_renorm(VecArgs va, const T* __restrict__ u,
+                                                       const T* __restrict__ r, RefineState rf, RedScratch rs) {
+  ElemMap em(va.Rp);
+  const int t = threadIdx.x;
+  const bool live = t < em.rpp * em.RS;
+  const int rr = t % em.RS, ro = t / em.RS;
+  double2 acc[EM_NK][1];
+  for (int k = 0; k < EM_NK; ++k) acc[k][0] = make_double2(0, 0);
+  BT_SEG_ROWS(va);
+  if (live) {
+    for (int k = 0; k < em.NK; ++k) {
+      const int col = rr + 256 * k;
+      if (col >= va.Rp) continue;
+      if (sys_of_col(col, va.nb) >= va.R) continue;
+      for (int64_t i = rb + ro; i < re; i += em.rpp) {
+        const double2 a = load_res(r, (size_t)i * va.Rp + col), b = load_res(u, (size_t)i * va.Rp + col);
+        acc[k][0].x += a.x * a.x + a.y * a.y;
+        acc[k][0].y += b.x * b.x + b.y * b.y;
+      }
+    }
+  }
+  if (!elem_block_reduce<1>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
+  if (threadIdx.x == 0) *rf.n_active = va.sp.G * va.R;
+  __syncthreads();
+  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+    double2 o[1];
+    sum_part<1>(rs.part, va.sp, va.R, va.Rp, s, o);
+    rf.active[s] = 1;
+    refine_finish(0, rf, s, o[0]);
+  }
+}
+
+void launch_weak_coupling(const WeakArgs& wa, const VecArgs& va, const OpArgs& op, const void* u, void* r, int df,
+                          cudaStream_t st) {
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>(wa.nr, 4096));
+  if (df) k_weak_coupling<float4><<<g, 256, 0, st>>>(wa, va, op, (const float4*)u, (float4*)r);
+  else k_weak_coupling<double2><<<g, 256, 0, st>>>(wa, va, op, (const double2*)u, (double2*)r);
+}
+void launch_resid0_renorm(const VecArgs& va, const void* u, const void* r, const RefineState& rf, RedScratch rs,
+                          int df, cudaStream_t st) {
+  if (df) k_resid0_renorm<float4><<<elem_grid(va), 256, 0, st>>>(va, (const float4*)u, (const float4*)r, rf, rs);
+  else k_resid0_renorm<double2><<<elem_grid(va), 256, 0, st>>>(va, (const double2*)u, (const double2*)r, rf, rs);
+}
+}  // namespace bt

@@ -13,7 +13,8 @@ class Simulation:
     xyz, tets, tet_cmpt, D_cmpt, kappa_cmpt, periodic_mask, box_lo, box_hi,
     dt, theta, delta, Delta, TE, dirs, bvals, transformed, and optionally a
     temporal `profile` (see profiles.py; None = PGSE), per-compartment `inv_T2`
-    (1/us) and initial magnetization `rho`, and `D_tensor` (lab frame)."""
+    (1/us) and initial magnetization `rho`, `D_tensor` (lab frame) and
+    `weak_periodic` (lab frame)."""
 
     def __init__(self, geom, device: int = 0, stream: int | None = None):
         self.g = geom
@@ -31,6 +32,9 @@ class Simulation:
             bt.bt_set_relaxation(self.ctx, inv_T2, rho)
         if getattr(geom, "D_tensor", None) is not None:
             bt.bt_set_diffusion_tensor(self.ctx, geom.D_tensor)
+        weak = getattr(geom, "weak_periodic", None)
+        if weak:
+            bt.bt_set_weak_periodic(self.ctx, weak["axes"], weak.get("kappa_e") or 0.0)
         if device >= 0:
             bt.bt_assemble(self.ctx, geom.dt, geom.theta, self.frame)
             prof = getattr(geom, "profile", None)

@@ -388,3 +388,57 @@ def test_diffusion_tensor_refused_in_transformed_frame(bt):
         assert e.value.code == bt.BT_EINVAL
     finally:
         bt.bt_destroy(ctx)
+
+
+# ---------------------------------------------------------------- weak pseudo-periodic box
+def _weak_box(dt=50.0):
+    p = geom.free_periodic_box(n=6, L=8.0, dt=dt, bvals=(800.0, 2000.0),
+                               dirs=((1.0, 0.0, 0.0), (0.3, 0.4, math.sqrt(0.75))))
+    p.periodic_mask = 0
+    p.transformed = False
+    p.weak_periodic = {"axes": 7, "kappa_e": None}
+    return p
+
+
+def _weak_cells():
+    p = geom.cfg2(n=6, kappa=1e-4, bvals=(1000.0, 2500.0))
+    p.dirs = np.array([[1.0, 0.0, 0.0], [0.0, 0.6, 0.8]])
+    p.weak_periodic = {"axes": 5, "kappa_e": 4e-3}
+    return p
+
+
+@pytest.mark.parametrize("case", ["box", "cells"])
+@pytest.mark.parametrize("mode", ["plain", "mixed", "mixed_host"])
+def test_weak_periodic_matches_oracle(sim_cls, bt, case, mode):
+    """Artificial-permeability coupling of the box faces (bt_set_weak_periodic)
+    against the oracle: a free box coupled on all axes, and the sphere case
+    coupled on x and z with a given kappa_e; captured graph and host loop."""
+    p = _weak_box() if case == "box" else _weak_cells()
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        flags = bt.BT_OPT_NO_GRAPH if mode == "mixed_host" else 0
+        S, err, stat, st = sim.run(m, flags=flags)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()
+
+
+def test_weak_periodic_refusals(bt):
+    q = geom.free_periodic_box(n=3, L=5.0)
+    ctx = bt.bt_create(0)
+    try:
+        bt.bt_upload_mesh(ctx, q.xyz, q.tets, q.tet_cmpt, q.D_cmpt, q.kappa_cmpt, 7, q.box_lo, q.box_hi)
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_set_weak_periodic(ctx, 1, 0.0)              # axis already periodic in the mesh
+        assert e.value.code == bt.BT_EINVAL
+        bt.bt_upload_mesh(ctx, q.xyz, q.tets, q.tet_cmpt, q.D_cmpt, q.kappa_cmpt, 0, q.box_lo, q.box_hi)
+        bt.bt_set_weak_periodic(ctx, 7, 0.0)
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_assemble(ctx, 50.0, 0.5, bt.BT_FRAME_TRANSFORMED)
+        assert e.value.code == bt.BT_EINVAL
+    finally:
+        bt.bt_destroy(ctx)
