@@ -374,6 +374,47 @@ def slab_1d(nx: int, L: float = 40.0, w: float = 1.0, dt: float = 50.0, D: float
                    np.array([[1.0, 0.0, 0.0]]), np.array([b]))
 
 
+def kuhn_grid_2d(nx: int, ny: int, lo, hi):
+    """Nodes (z = 0) and counter-clockwise triangles of an nx*ny grid of the
+    rectangle [lo, hi] (x, y): each cell is split along its (0,0)-(1,1)
+    diagonal, identically in every cell.  Node (i, j) has index i + (nx+1) j."""
+    xs = np.linspace(lo[0], hi[0], nx + 1)
+    ys = np.linspace(lo[1], hi[1], ny + 1)
+    Y, X = np.meshgrid(ys, xs, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1)
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    v00 = (i + (nx + 1) * j).ravel()
+    v10, v01 = v00 + 1, v00 + nx + 1
+    v11 = v01 + 1
+    tris = np.stack([np.stack([v00, v10, v11], 1), np.stack([v00, v11, v01], 1)], axis=1).reshape(-1, 3)
+    return xyz, tris.astype(np.int32)
+
+
+def square_disk(n: int = 40, L: float = 10.0, R: float = 3.0, dt: float = 50.0, kappa: float = 1e-5,
+                bvals=(0.0, 1000.0, 3000.0), dirs=((1.0, 0.0, 0.0),)):
+    """2-D: a disk of radius R (compartment 1, centroid rule, permeable membrane)
+    centred in the square [-L/2, L/2]^2 (compartment 0), Neumann outer
+    boundary; the paper's two-dimensional disk experiments at reduced size."""
+    lo2, hi2 = np.full(2, -L / 2), np.full(2, L / 2)
+    xyz, tris = kuhn_grid_2d(n, n, lo2, hi2)
+    cen = xyz[tris].mean(axis=1)
+    lab = (np.hypot(cen[:, 0], cen[:, 1]) < R).astype(np.int32)
+    lo, hi = np.array([lo2[0], lo2[1], -1.0]), np.array([hi2[0], hi2[1], 1.0])
+    return Problem("square_disk", xyz, tris, lab, np.array([2e-3, 2e-3]), np.array([NO_MEMBRANE, kappa]), 0,
+                   lo, hi, dt, 2500.0, 5000.0, 7500.0, np.asarray(dirs, dtype=np.float64),
+                   np.asarray(bvals, dtype=np.float64))
+
+
+def free_periodic_square(n: int = 8, L: float = 10.0, dt: float = 50.0, D: float = 2e-3,
+                         dirs=((1.0, 0.0, 0.0),), bvals=(1000.0,)):
+    """2-D periodic square without compartments (free diffusion)."""
+    xyz, tris = kuhn_grid_2d(n, n, np.zeros(2), np.full(2, L))
+    lo, hi = np.array([0.0, 0.0, -1.0]), np.array([L, L, 1.0])
+    return Problem("free_periodic_square", xyz, tris, np.zeros(len(tris), np.int32), np.array([D]),
+                   np.array([NO_MEMBRANE]), 3, lo, hi, dt, 2500.0, 5000.0, 7500.0,
+                   np.asarray(dirs, dtype=np.float64), np.asarray(bvals, dtype=np.float64), transformed=True)
+
+
 def union(problems, name="batch"):
     """Disjoint union of several geometries as one input mesh (the uneven
     batch): each geometry is translated so that its box centre sits at the

@@ -81,6 +81,18 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
                          const int32_t* tet4, const int32_t* tet_cmpt, int32_t n_cmpt,
                          const double* D_cmpt, const double* kappa_cmpt, uint32_t periodic_mask,
                          const double* box_lo, const double* box_hi);
+/* The same for a 2-D domain (the paper's two-dimensional experiments, P1
+ * triangles; Section 2 holds in any dimension): xy [2 n_nodes] (um), tri3
+ * [3 n_tris] counter-clockwise triangles, tri_cmpt [n_tris]; periodic_mask
+ * bits 0 (x) and 1 (y); box_lo, box_hi [2].  Internally the plane z = 0 of a
+ * box [-1, 1] in z, so gradient directions act through their x and y parts;
+ * interfaces are edges with the jump term kappa <[u], [v]> on them.  Every
+ * later entry point works unchanged, except bt_set_weak_periodic
+ * (tetrahedra only).  Errors as bt_upload_mesh (inverted triangles included). */
+bt_status bt_upload_mesh_2d(bt_ctx* ctx, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri3,
+                            const int32_t* tri_cmpt, int32_t n_cmpt, const double* D_cmpt,
+                            const double* kappa_cmpt, uint32_t periodic_mask, const double* box_lo,
+                            const double* box_hi);
 /* Sizes after bt_upload_mesh.  Any output pointer may be NULL. */
 bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t* n_iface);
 /* dof_node [n_dof] master node of each dof; dof_cmpt [n_dof] its compartment. */

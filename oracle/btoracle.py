@@ -72,23 +72,27 @@ def doubling(master, tets, tet_cmpt, n_cmpt):
     (node, compartment) order."""
     keys = master[tets].astype(np.int64) * n_cmpt + tet_cmpt[:, None].astype(np.int64)
     uniq, inv = np.unique(keys.ravel(), return_inverse=True)
-    tet_dof = inv.reshape(-1, 4)
+    tet_dof = inv.reshape(-1, tets.shape[1])
     return tet_dof, uniq // n_cmpt, uniq % n_cmpt
 
 
 def interface_faces(master, tets, tet_cmpt):
-    """Faces shared by two tetrahedra of different compartments.
+    """Faces (edges in 2-D) shared by two elements of different compartments.
 
-    Returns (tet_a, tet_b, verts [nf,3] master ids, local vertex indices of the
-    face in tet_a [nf,3]).  Face keys use master ids, so faces identified by
+    Returns (elem_a, elem_b, local vertex indices of the face in elem_a
+    [nf, 3] for tetrahedra, [nf, 2] for triangles).  Face keys use master ids, so faces identified by
     periodicity are found too."""
-    loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    if tets.shape[1] == 3:                        # 2-D: edges of triangles
+        loc = np.array([[1, 2], [0, 2], [0, 1]])
+    else:
+        loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    nf_loc, fsz = loc.shape                        # faces per element, nodes per face
     mt = master[tets]
-    fv = mt[:, loc]                                # [nt, 4, 3]
-    fv_sorted = np.sort(fv, axis=2).reshape(-1, 3)
-    owner = np.repeat(np.arange(len(tets)), 4)
-    lface = np.tile(np.arange(4), len(tets))
-    order = np.lexsort((fv_sorted[:, 2], fv_sorted[:, 1], fv_sorted[:, 0]))
+    fv = mt[:, loc]                                # [nt, nf_loc, fsz]
+    fv_sorted = np.sort(fv, axis=2).reshape(-1, fsz)
+    owner = np.repeat(np.arange(len(tets)), nf_loc)
+    lface = np.tile(np.arange(nf_loc), len(tets))
+    order = np.lexsort(fv_sorted.T[::-1])
     fs = fv_sorted[order]
     same = np.all(fs[1:] == fs[:-1], axis=1)
     i0 = np.flatnonzero(same)
@@ -102,17 +106,30 @@ def interface_faces(master, tets, tet_cmpt):
 # --------------------------------------------------------------------------
 # Element matrices (P1 tetrahedra, exact integration)
 # --------------------------------------------------------------------------
-def _cubic_moments():
-    """c[i,j,l] = (1/|T|) * integral over T of lambda_i lambda_j lambda_l, from
-    the barycentric integration formula alpha! 3! / (|alpha| + 3)!."""
-    c = np.empty((4, 4, 4))
-    for i in range(4):
-        for j in range(4):
-            for l in range(4):
-                a = np.bincount([i, j, l], minlength=4)
-                num = np.prod([math.factorial(x) for x in a]) * math.factorial(3)
-                c[i, j, l] = num / math.factorial(3 + 3)
+def _cubic_moments(d=3):
+    """c[i,j,l] = (1/|T|) * integral over a d-simplex T of lambda_i lambda_j
+    lambda_l, from the barycentric integration formula alpha! d! / (|alpha| + d)!."""
+    nv = d + 1
+    c = np.empty((nv, nv, nv))
+    for i in range(nv):
+        for j in range(nv):
+            for l in range(nv):
+                a = np.bincount([i, j, l], minlength=nv)
+                num = np.prod([math.factorial(x) for x in a]) * math.factorial(d)
+                c[i, j, l] = num / math.factorial(3 + d)
     return c
+
+
+def tri_geometry(X):
+    """Areas [nt] and barycentric gradients [nt, 3, 3] (z = 0) of triangles in the
+    xy plane, X [nt, 3, 3]: grad lambda solves E grad = e_a for the edge matrix."""
+    E = X[:, 1:, :2] - X[:, :1, :2]                # [nt, 2, 2] edge vectors
+    area = 0.5 * np.linalg.det(E)
+    Ginv = np.linalg.inv(E)                        # columns: grad lambda_{1,2}
+    G = np.zeros((len(X), 3, 3))
+    G[:, 1:, :2] = np.transpose(Ginv, (0, 2, 1))
+    G[:, 0, :] = -G[:, 1:, :].sum(axis=1)
+    return area, G
 
 
 def tet_geometry(X):
@@ -147,13 +164,15 @@ def assemble(p):
     tet_dof, dof_node, dof_cmpt = doubling(master, p.tets, p.tet_cmpt, p.n_cmpt)
     n = len(dof_node)
     X = p.xyz[p.tets]                              # unwrapped element coordinates
-    vol, G = tet_geometry(X)
+    nv = p.tets.shape[1]                           # 4: tetrahedra, 3: triangles (2-D)
+    d = nv - 1
+    vol, G = tet_geometry(X) if nv == 4 else tri_geometry(X)
     Dt = p.D_cmpt[p.tet_cmpt]
-    rows = np.repeat(tet_dof[:, :, None], 4, axis=2)
-    cols = np.repeat(tet_dof[:, None, :], 4, axis=1)
+    rows = np.repeat(tet_dof[:, :, None], nv, axis=2)
+    cols = np.repeat(tet_dof[:, None, :], nv, axis=1)
 
-    eye = np.eye(4)
-    Me = vol[:, None, None] / 20.0 * (1.0 + eye)[None]
+    # P1 mass: |T| (1 + delta_ij) / ((d + 1)(d + 2))
+    Me = vol[:, None, None] / ((d + 1) * (d + 2)) * (1.0 + np.eye(nv))[None]
     Dten = getattr(p, "D_tensor", None)
     if Dten is None:
         Ke = (Dt * vol)[:, None, None] * np.einsum("tik,tjk->tij", G, G)
@@ -169,7 +188,7 @@ def assemble(p):
         Ke = vol[:, None, None] * np.einsum("tik,tkl,tjl->tij", G, Dm[p.tet_cmpt], G)
     centre = 0.5 * (np.asarray(p.box_lo, float) + np.asarray(p.box_hi, float))
     Xc = X - centre
-    c3 = _cubic_moments()
+    c3 = _cubic_moments(d)
     out = {"n": n, "tet_dof": tet_dof, "dof_node": dof_node, "dof_cmpt": dof_cmpt,
            "master": master}
     out["M"] = _coo(rows, cols, Me, n)
@@ -182,7 +201,7 @@ def assemble(p):
     for k, nm in enumerate("xyz"):
         Mk = vol[:, None, None] * np.einsum("ijl,tl->tij", c3, Xc[:, :, k])
         out["M" + nm] = _coo(rows, cols, Mk, n)
-        Ck = (Dt * vol / 4.0)[:, None, None] * np.broadcast_to(G[:, None, :, k], (len(vol), 4, 4))
+        Ck = (Dt * vol / (d + 1))[:, None, None] * np.broadcast_to(G[:, None, :, k], (len(vol), nv, nv))
         out["E" + nm] = _coo(rows, cols, Ck - np.transpose(Ck, (0, 2, 1)), n)
 
     # interface jump term kappa <[u], [v]> on faces between compartments
@@ -191,7 +210,11 @@ def assemble(p):
     if nf:
         va = p.tets[ta[:, None], lv]                    # global vertices of face (tet a)
         Xa = p.xyz[va]
-        area = 0.5 * np.linalg.norm(np.cross(Xa[:, 1] - Xa[:, 0], Xa[:, 2] - Xa[:, 0]), axis=1)
+        if nv == 4:
+            area = 0.5 * np.linalg.norm(np.cross(Xa[:, 1] - Xa[:, 0], Xa[:, 2] - Xa[:, 0]), axis=1)
+        else:                                           # interface edges: length
+            area = np.linalg.norm(Xa[:, 1] - Xa[:, 0], axis=1)
+        fs = nv - 1
         ka = p.kappa_cmpt[p.tet_cmpt[ta]]
         kb = p.kappa_cmpt[p.tet_cmpt[tb]]
         with np.errstate(divide="ignore"):
@@ -202,12 +225,13 @@ def assemble(p):
         ma = master[va]
         lb = np.argmax(mb[:, None, :] == ma[:, :, None], axis=2)
         dof_b = tet_dof[tb[:, None], lb]
-        Fm = (area * kap)[:, None, None] / 12.0 * (1.0 + np.eye(3))[None]
+        # face mass of a (d-1)-simplex: |F| (1 + delta_ab) / (d (d + 1))
+        Fm = (area * kap)[:, None, None] / (d * (d + 1)) * (1.0 + np.eye(fs))[None]
         d6 = np.concatenate([dof_a, dof_b], axis=1)
-        blk = np.block([[np.ones((3, 3)), -np.ones((3, 3))], [-np.ones((3, 3)), np.ones((3, 3))]])
+        blk = np.block([[np.ones((fs, fs)), -np.ones((fs, fs))], [-np.ones((fs, fs)), np.ones((fs, fs))]])
         F6 = np.tile(Fm, (1, 2, 2)) * blk[None]
-        r6 = np.repeat(d6[:, :, None], 6, axis=2)
-        c6 = np.repeat(d6[:, None, :], 6, axis=1)
+        r6 = np.repeat(d6[:, :, None], 2 * fs, axis=2)
+        c6 = np.repeat(d6[:, None, :], 2 * fs, axis=1)
         out["J"] = _coo(r6, c6, F6, n)
     else:
         out["J"] = sp.csr_matrix((n, n))

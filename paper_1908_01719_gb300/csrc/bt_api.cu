@@ -104,9 +104,10 @@ bt_status bt_set_stream(bt_ctx* ctx, void* s) {
 
 const char* bt_last_error(const bt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_tets, const int32_t* tet4,
-                         const int32_t* tet_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* kappa_cmpt,
-                         uint32_t periodic_mask, const double* box_lo, const double* box_hi) {
+static bt_status upload_mesh_nv(bt_ctx* ctx, int nv, int64_t n_nodes, const double* xyz, int64_t n_tets,
+                                const int32_t* tet4, const int32_t* tet_cmpt, int32_t n_cmpt, const double* D_cmpt,
+                                const double* kappa_cmpt, uint32_t periodic_mask, const double* box_lo,
+                                const double* box_hi) {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!xyz || !tet4 || !tet_cmpt || !D_cmpt || !kappa_cmpt || !box_lo || !box_hi || n_nodes <= 0 || n_tets <= 0 ||
@@ -116,11 +117,12 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
   m = HostMesh();
   ctx->have_mesh = ctx->assembled = ctx->have_seq = false;
   try {
+    m.nv = nv;
     m.n_nodes = n_nodes;
     m.n_tets = n_tets;
     m.n_cmpt = n_cmpt;
     m.xyz.assign(xyz, xyz + 3 * n_nodes);
-    m.tets.assign(tet4, tet4 + 4 * n_tets);
+    m.tets.assign(tet4, tet4 + (size_t)nv * n_tets);
     m.tet_cmpt.assign(tet_cmpt, tet_cmpt + n_tets);
     m.D.assign(D_cmpt, D_cmpt + n_cmpt);
     m.kappa.assign(kappa_cmpt, kappa_cmpt + n_cmpt);
@@ -165,6 +167,30 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
   CK(upload(ctx->d_col, m.col, st));
   CK(cudaStreamSynchronize(st));
   return BT_OK;
+}
+
+bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_tets, const int32_t* tet4,
+                         const int32_t* tet_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* kappa_cmpt,
+                         uint32_t periodic_mask, const double* box_lo, const double* box_hi) {
+  return upload_mesh_nv(ctx, 4, n_nodes, xyz, n_tets, tet4, tet_cmpt, n_cmpt, D_cmpt, kappa_cmpt, periodic_mask,
+                        box_lo, box_hi);
+}
+
+bt_status bt_upload_mesh_2d(bt_ctx* ctx, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri3,
+                            const int32_t* tri_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* kappa_cmpt,
+                            uint32_t periodic_mask, const double* box_lo, const double* box_hi) {
+  if (!ctx) return BT_EINVAL;
+  if (!xy || !box_lo || !box_hi || n_nodes <= 0 || periodic_mask > 3)
+    return fail(ctx, BT_EINVAL, "bt_upload_mesh_2d: invalid argument");
+  // the plane z = 0 inside a box centred on it, so z moments vanish
+  std::vector<double> xyz(3 * (size_t)n_nodes, 0.0);
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    xyz[3 * i] = xy[2 * i];
+    xyz[3 * i + 1] = xy[2 * i + 1];
+  }
+  const double lo[3] = {box_lo[0], box_lo[1], -1.0}, hi[3] = {box_hi[0], box_hi[1], 1.0};
+  return upload_mesh_nv(ctx, 3, n_nodes, xyz.data(), n_tris, tri3, tri_cmpt, n_cmpt, D_cmpt, kappa_cmpt,
+                        periodic_mask, lo, hi);
 }
 
 bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t* n_iface) {
@@ -331,6 +357,7 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   a.Dten = ctx->cm_Dten.empty() ? nullptr : ctx->d_Dten.p;
   for (int k = 0; k < 3; ++k) a.centre[k] = 0.5 * (m.lo[k] + m.hi[k]);
   a.nt = m.n_tets;
+  a.nv = m.nv;
   a.nf = m.n_face;
   a.nnz = nnz;
   a.face_ta = ctx->d_face_ta.p;
@@ -539,10 +566,10 @@ bt_status bt_set_segments(bt_ctx* ctx, int32_t G, const int64_t* node_off, const
     if (node_off[g + 1] <= node_off[g]) return fail(ctx, BT_EINVAL, "bt_set_segments: empty segment");
   // every tetrahedron inside one segment
   for (int64_t t = 0; t < m.n_tets; ++t) {
-    const int32_t v0 = m.tets[4 * t];
+    const int32_t v0 = m.tets[m.nv * t];
     const int g = (int)(std::upper_bound(node_off, node_off + G + 1, (int64_t)v0) - node_off) - 1;
-    for (int a2 = 1; a2 < 4; ++a2)
-      if (m.tets[4 * t + a2] < node_off[g] || m.tets[4 * t + a2] >= node_off[g + 1])
+    for (int a2 = 1; a2 < m.nv; ++a2)
+      if (m.tets[m.nv * t + a2] < node_off[g] || m.tets[m.nv * t + a2] >= node_off[g + 1])
         return fail(ctx, BT_EINVAL, "bt_set_segments: a tetrahedron spans two segments");
   }
   std::vector<int64_t> row0(G + 1);

@@ -14,32 +14,35 @@ namespace bt {
 // ---------------------------------------------------------------- host mesh
 struct HostMesh {
   // input (copied)
-  int64_t n_nodes = 0, n_tets = 0;
+  int64_t n_nodes = 0, n_tets = 0;   // elements: tetrahedra (nv = 4) or triangles (nv = 3)
   int32_t n_cmpt = 0;
+  int nv = 4;                          // nodes per element; faces have nv - 1 nodes
   std::vector<double> xyz;          // 3 n_nodes
-  std::vector<int32_t> tets;        // 4 n_tets
+  std::vector<int32_t> tets;        // nv n_tets
   std::vector<int32_t> tet_cmpt;    // n_tets
   std::vector<double> D, kappa;     // n_cmpt
   uint32_t pmask = 0;
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   // derived on the host
   std::vector<int32_t> master;      // n_nodes -> master node
-  std::vector<int32_t> tet_dof;     // 4 n_tets
+  std::vector<int32_t> tet_dof;     // nv n_tets
   std::vector<int32_t> dof_node, dof_cmpt;
   int64_t n_dof = 0;
-  // interface faces: tet a / tet b, local vertex ids of the face in tet a,
-  // the 6 dofs (3 of side a, then the matching 3 of side b), kappa
+  // interface faces (edges in 2-D): element a / element b, local vertex ids of
+  // the face in element a, the 2 (nv - 1) dofs (side a, then the matching ones
+  // of side b), kappa
   std::vector<int32_t> face_ta, face_tb;
-  std::vector<int8_t> face_lv;      // 3 nf
-  std::vector<int32_t> face_dof;    // 6 nf
+  std::vector<int8_t> face_lv;      // (nv - 1) nf
+  std::vector<int32_t> face_dof;    // 2 (nv - 1) nf
   std::vector<double> face_kappa;
   int64_t n_face = 0;
   // CSR pattern shared by every matrix
   std::vector<int64_t> row_ptr;     // n_dof + 1
   std::vector<int32_t> col;         // nnz
   int64_t nnz = 0;
-  // slot-sorted element contributions: tet entries (t*16 + i*4 + j) and face
-  // entries (f*36 + a*6 + b), each in increasing element order per slot
+  // slot-sorted element contributions: element entries (t nv^2 + i nv + j) and
+  // face entries (f (2 fs)^2 + a 2 fs + b, fs = nv - 1), each in increasing
+  // element order per slot
   std::vector<int64_t> tc_ptr, fc_ptr;  // nnz + 1
   std::vector<int32_t> tc, fc;
 };

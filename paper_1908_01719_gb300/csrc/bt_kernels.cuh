@@ -20,6 +20,7 @@ struct AsmArgs {
   const double* Dten;    // [n_cmpt][6] diffusion tensors (or null: isotropic Dc)
   double centre[3];
   int64_t nt, nf, nnz;
+  int nv;  // 4 tetrahedra, 3 triangles
   const int32_t* face_ta;
   const int8_t* face_lv;
   const double* face_kappa;

@@ -72,6 +72,31 @@ namespace bt {
 void compute_geom_features(bt_ctx* ctx) {
   const HostMesh& m = ctx->mesh;
   double vol = 0, dv = 0;
+  if (m.nv == 3) {
+    // 2-D: areas, interface edge lengths, h = (2 x mean triangle area)^(1/2)
+    for (int64_t t = 0; t < m.n_tets; ++t) {
+      const int32_t* v = &m.tets[3 * t];
+      const double* a = &m.xyz[3 * v[0]];
+      const double* b = &m.xyz[3 * v[1]];
+      const double* c = &m.xyz[3 * v[2]];
+      const double A = 0.5 * ((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]));
+      vol += A;
+      dv += A * m.D[m.tet_cmpt[t]];
+    }
+    double len = 0, kl = 0;
+    for (int64_t f = 0; f < m.n_face; ++f) {
+      const int32_t t = m.face_ta[f];
+      const double* a = &m.xyz[3 * m.tets[3 * t + m.face_lv[2 * f]]];
+      const double* b = &m.xyz[3 * m.tets[3 * t + m.face_lv[2 * f + 1]]];
+      const double l = std::sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]));
+      len += l;
+      kl += l * m.face_kappa[f];
+    }
+    ctx->feat_D = vol > 0 ? dv / vol : 0;
+    ctx->feat_kappa = len > 0 ? kl / len : 0;
+    ctx->feat_h = std::sqrt(2.0 * vol / std::max<int64_t>(1, m.n_tets));
+    return;
+  }
   for (int64_t t = 0; t < m.n_tets; ++t) {
     const int32_t* v = &m.tets[4 * t];
     const double* a = &m.xyz[3 * v[0]];

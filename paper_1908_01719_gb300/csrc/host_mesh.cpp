@@ -57,6 +57,14 @@ int validate(const HostMesh& m, std::string& msg) {
     msg = "empty mesh";
     return BT_EINVAL;
   }
+  if (m.nv != 3 && m.nv != 4) {
+    msg = "elements must be triangles or tetrahedra";
+    return BT_EINVAL;
+  }
+  if (m.nv == 3 && (m.pmask & 4u)) {
+    msg = "a 2-D mesh has no periodic z axis";
+    return BT_EINVAL;
+  }
   if (m.n_nodes >= (int64_t(1) << 31) || m.n_tets * 16 >= (int64_t(1) << 31)) {
     msg = "mesh too large for 32-bit element indexing";
     return BT_EINVAL;
@@ -81,21 +89,29 @@ int validate(const HostMesh& m, std::string& msg) {
       msg = "non-finite node coordinate";
       return BT_EINVAL;
     }
+  const char* what = m.nv == 4 ? "tetrahedron " : "triangle ";
   for (int64_t t = 0; t < m.n_tets; ++t) {
-    const int32_t* v = &m.tets[4 * t];
-    for (int a = 0; a < 4; ++a)
+    const int32_t* v = &m.tets[m.nv * t];
+    for (int a = 0; a < m.nv; ++a)
       if (v[a] < 0 || v[a] >= m.n_nodes) {
-        msg = "tetrahedron " + std::to_string(t) + " has a node id out of range";
+        msg = what + std::to_string(t) + " has a node id out of range";
         return BT_EINVAL;
       }
     if (m.tet_cmpt[t] < 0 || m.tet_cmpt[t] >= m.n_cmpt) {
-      msg = "tetrahedron " + std::to_string(t) + " has a compartment id out of range";
+      msg = what + std::to_string(t) + " has a compartment id out of range";
       return BT_EINVAL;
     }
-    double vol = signed_volume(&m.xyz[3 * v[0]], &m.xyz[3 * v[1]], &m.xyz[3 * v[2]], &m.xyz[3 * v[3]]);
+    double vol;
+    if (m.nv == 4) {
+      vol = signed_volume(&m.xyz[3 * v[0]], &m.xyz[3 * v[1]], &m.xyz[3 * v[2]], &m.xyz[3 * v[3]]);
+    } else {  // signed area in the xy plane (counter-clockwise positive)
+      const double* a = &m.xyz[3 * v[0]];
+      const double* b = &m.xyz[3 * v[1]];
+      const double* c = &m.xyz[3 * v[2]];
+      vol = 0.5 * ((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]));
+    }
     if (!(vol > 0.0)) {
-      msg = "tetrahedron " + std::to_string(t) + " is degenerate or inverted (signed volume " +
-            std::to_string(vol) + ")";
+      msg = what + std::to_string(t) + " is degenerate or inverted (signed measure " + std::to_string(vol) + ")";
       return BT_EINVAL;
     }
   }
@@ -153,10 +169,11 @@ void double_interface_nodes(HostMesh& m) {
   const int64_t n = m.n_nodes;
   std::vector<int32_t> first(n, -1);
   std::vector<std::pair<int32_t, int32_t>> extra;
+  const int nv = m.nv;
   for (int64_t t = 0; t < m.n_tets; ++t) {
     int32_t c = m.tet_cmpt[t];
-    for (int a = 0; a < 4; ++a) {
-      int32_t v = m.master[m.tets[4 * t + a]];
+    for (int a = 0; a < nv; ++a) {
+      int32_t v = m.master[m.tets[nv * t + a]];
       if (first[v] < 0)
         first[v] = c;
       else if (first[v] != c)
@@ -184,15 +201,15 @@ void double_interface_nodes(HostMesh& m) {
     std::sort(cl, cl + k);
     for (int j = 0; j < k; ++j) m.dof_node[base[v] + j] = (int32_t)v;
   }
-  m.tet_dof.resize(4 * m.n_tets);
+  m.tet_dof.resize(nv * m.n_tets);
   parallel_for(m.n_tets, [&](int64_t b, int64_t e) {
     for (int64_t t = b; t < e; ++t) {
       int32_t c = m.tet_cmpt[t];
-      for (int a = 0; a < 4; ++a) {
-        int32_t v = m.master[m.tets[4 * t + a]];
+      for (int a = 0; a < nv; ++a) {
+        int32_t v = m.master[m.tets[nv * t + a]];
         int64_t d = base[v];
         while (m.dof_cmpt[d] != c) ++d;
-        m.tet_dof[4 * t + a] = (int32_t)d;
+        m.tet_dof[nv * t + a] = (int32_t)d;
       }
     }
   });
@@ -204,7 +221,11 @@ void find_interface_faces(HostMesh& m) {
   std::vector<uint8_t> multi(m.n_nodes, 0);
   for (int64_t d = 1; d < m.n_dof; ++d)
     if (m.dof_node[d] == m.dof_node[d - 1]) multi[m.dof_node[d]] = 1;
-  static const int LOC[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  // faces of a tetrahedron (vertex triples) or edges of a triangle (pairs)
+  static const int LOC4[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  static const int LOC3[3][3] = {{1, 2, -1}, {0, 2, -1}, {0, 1, -1}};
+  const int nv = m.nv, fs = nv - 1;
+  auto LOC = [&](int f, int a) { return nv == 4 ? LOC4[f][a] : LOC3[f][a]; };
   struct Cand {
     std::array<int32_t, 3> key;
     int32_t tet;
@@ -212,11 +233,11 @@ void find_interface_faces(HostMesh& m) {
   };
   std::vector<Cand> cand;
   for (int64_t t = 0; t < m.n_tets; ++t) {
-    for (int f = 0; f < 4; ++f) {
-      std::array<int32_t, 3> k;
+    for (int f = 0; f < nv; ++f) {
+      std::array<int32_t, 3> k = {-1, -1, -1};
       bool ok = true;
-      for (int a = 0; a < 3; ++a) {
-        k[a] = m.master[m.tets[4 * t + LOC[f][a]]];
+      for (int a = 0; a < fs; ++a) {
+        k[a] = m.master[m.tets[nv * t + LOC(f, a)]];
         ok = ok && multi[k[a]];
       }
       if (!ok) continue;
@@ -240,16 +261,16 @@ void find_interface_faces(HostMesh& m) {
     m.face_ta.push_back(ta);
     m.face_tb.push_back(tb);
     int32_t dofs[6];
-    for (int a = 0; a < 3; ++a) {
-      int la = LOC[cand[i].lf][a];
+    for (int a = 0; a < fs; ++a) {
+      int la = LOC(cand[i].lf, a);
       m.face_lv.push_back((int8_t)la);
-      dofs[a] = m.tet_dof[4 * ta + la];
-      int32_t v = m.master[m.tets[4 * ta + la]];
+      dofs[a] = m.tet_dof[nv * ta + la];
+      int32_t v = m.master[m.tets[nv * ta + la]];
       int lb = 0;
-      while (m.master[m.tets[4 * tb + lb]] != v) ++lb;
-      dofs[3 + a] = m.tet_dof[4 * tb + lb];
+      while (m.master[m.tets[nv * tb + lb]] != v) ++lb;
+      dofs[fs + a] = m.tet_dof[nv * tb + lb];
     }
-    for (int a = 0; a < 6; ++a) m.face_dof.push_back(dofs[a]);
+    for (int a = 0; a < 2 * fs; ++a) m.face_dof.push_back(dofs[a]);
     double inv = 1.0 / m.kappa[ca] + 1.0 / m.kappa[cb];  // 1/inf = 0
     m.face_kappa.push_back(inv > 0 ? 1.0 / inv : INFINITY);
   }
@@ -258,29 +279,30 @@ void find_interface_faces(HostMesh& m) {
 
 void build_pattern(HostMesh& m) {
   const int64_t nd = m.n_dof, nt = m.n_tets, nf = m.n_face;
-  // dof -> elements incidence (tets, then faces)
+  const int nv = m.nv, nfd = 2 * (nv - 1);
+  // dof -> elements incidence (elements, then faces)
   std::vector<int64_t> tp(nd + 1, 0), fp(nd + 1, 0);
-  for (int64_t i = 0; i < 4 * nt; ++i) tp[m.tet_dof[i] + 1]++;
-  for (int64_t i = 0; i < 6 * nf; ++i) fp[m.face_dof[i] + 1]++;
+  for (int64_t i = 0; i < nv * nt; ++i) tp[m.tet_dof[i] + 1]++;
+  for (int64_t i = 0; i < nfd * nf; ++i) fp[m.face_dof[i] + 1]++;
   for (int64_t d = 0; d < nd; ++d) {
     tp[d + 1] += tp[d];
     fp[d + 1] += fp[d];
   }
-  std::vector<int32_t> ti(4 * nt), fi(6 * nf);
+  std::vector<int32_t> ti(nv * nt), fi(nfd * nf);
   {
     std::vector<int64_t> pos(tp.begin(), tp.end() - 1);
     for (int64_t t = 0; t < nt; ++t)
-      for (int a = 0; a < 4; ++a) ti[pos[m.tet_dof[4 * t + a]]++] = (int32_t)t;
+      for (int a = 0; a < nv; ++a) ti[pos[m.tet_dof[nv * t + a]]++] = (int32_t)t;
     std::vector<int64_t> pf(fp.begin(), fp.end() - 1);
     for (int64_t f = 0; f < nf; ++f)
-      for (int a = 0; a < 6; ++a) fi[pf[m.face_dof[6 * f + a]]++] = (int32_t)f;
+      for (int a = 0; a < nfd; ++a) fi[pf[m.face_dof[nfd * f + a]]++] = (int32_t)f;
   }
   auto row_cols = [&](int64_t d, std::vector<int32_t>& buf) {
     buf.clear();
     for (int64_t k = tp[d]; k < tp[d + 1]; ++k)
-      for (int a = 0; a < 4; ++a) buf.push_back(m.tet_dof[4 * (int64_t)ti[k] + a]);
+      for (int a = 0; a < nv; ++a) buf.push_back(m.tet_dof[nv * (int64_t)ti[k] + a]);
     for (int64_t k = fp[d]; k < fp[d + 1]; ++k)
-      for (int a = 0; a < 6; ++a) buf.push_back(m.face_dof[6 * (int64_t)fi[k] + a]);
+      for (int a = 0; a < nfd; ++a) buf.push_back(m.face_dof[nfd * (int64_t)fi[k] + a]);
     std::sort(buf.begin(), buf.end());
     buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
   };
@@ -315,33 +337,34 @@ inline int64_t slot_of(const HostMesh& m, int32_t r, int32_t c) {
 // increasing element order, so the per-slot sums are deterministic.
 void build_contributions(HostMesh& m) {
   const int64_t nt = m.n_tets, nf = m.n_face, nnz = m.nnz;
-  std::vector<int64_t> tslot(16 * nt);
+  const int nv = m.nv, n2 = nv * nv, nfd = 2 * (nv - 1), nf2 = nfd * nfd;
+  std::vector<int64_t> tslot(n2 * nt);
   parallel_for(nt, [&](int64_t b, int64_t e) {
     for (int64_t t = b; t < e; ++t)
-      for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j)
-          tslot[16 * t + 4 * i + j] = slot_of(m, m.tet_dof[4 * t + i], m.tet_dof[4 * t + j]);
+      for (int i = 0; i < nv; ++i)
+        for (int j = 0; j < nv; ++j)
+          tslot[n2 * t + nv * i + j] = slot_of(m, m.tet_dof[nv * t + i], m.tet_dof[nv * t + j]);
   });
   m.tc_ptr.assign(nnz + 1, 0);
-  for (int64_t k = 0; k < 16 * nt; ++k) m.tc_ptr[tslot[k] + 1]++;
+  for (int64_t k = 0; k < n2 * nt; ++k) m.tc_ptr[tslot[k] + 1]++;
   for (int64_t s = 0; s < nnz; ++s) m.tc_ptr[s + 1] += m.tc_ptr[s];
-  m.tc.resize(16 * nt);
+  m.tc.resize(n2 * nt);
   {
     std::vector<int64_t> pos(m.tc_ptr.begin(), m.tc_ptr.end() - 1);
-    for (int64_t k = 0; k < 16 * nt; ++k) m.tc[pos[tslot[k]]++] = (int32_t)k;
+    for (int64_t k = 0; k < n2 * nt; ++k) m.tc[pos[tslot[k]]++] = (int32_t)k;
   }
   std::vector<int64_t>().swap(tslot);
   m.fc_ptr.assign(nnz + 1, 0);
-  std::vector<int64_t> fslot(36 * nf);
+  std::vector<int64_t> fslot(nf2 * nf);
   for (int64_t f = 0; f < nf; ++f)
-    for (int a = 0; a < 6; ++a)
-      for (int b = 0; b < 6; ++b)
-        fslot[36 * f + 6 * a + b] = slot_of(m, m.face_dof[6 * f + a], m.face_dof[6 * f + b]);
-  for (int64_t k = 0; k < 36 * nf; ++k) m.fc_ptr[fslot[k] + 1]++;
+    for (int a = 0; a < nfd; ++a)
+      for (int b = 0; b < nfd; ++b)
+        fslot[nf2 * f + nfd * a + b] = slot_of(m, m.face_dof[nfd * f + a], m.face_dof[nfd * f + b]);
+  for (int64_t k = 0; k < nf2 * nf; ++k) m.fc_ptr[fslot[k] + 1]++;
   for (int64_t s = 0; s < nnz; ++s) m.fc_ptr[s + 1] += m.fc_ptr[s];
-  m.fc.resize(36 * nf);
+  m.fc.resize(nf2 * nf);
   std::vector<int64_t> pos(m.fc_ptr.begin(), m.fc_ptr.end() - 1);
-  for (int64_t k = 0; k < 36 * nf; ++k) m.fc[pos[fslot[k]]++] = (int32_t)k;
+  for (int64_t k = 0; k < nf2 * nf; ++k) m.fc[pos[fslot[k]]++] = (int32_t)k;
 }
 
 }  // namespace
@@ -450,6 +473,10 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
 
 int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std::string& msg) {
   wp = WeakPeriodic();
+  if (m.nv != 4) {
+    msg = "tetrahedral meshes only";
+    return BT_EINVAL;
+  }
   double Lmax = 0, vsum = 0;
   for (int k = 0; k < 3; ++k) {
     wp.L[k] = m.hi[k] - m.lo[k];

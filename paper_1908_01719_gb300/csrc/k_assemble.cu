@@ -78,12 +78,54 @@ __global__ void k_tet_geom(const double* __restrict__ xyz, const int32_t* __rest
   for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
 }
 
-// kappa |F| / 12 per interface face
+// The same record for a triangle in the xy plane (2-D meshes): area, the
+// gradients of the three barycentric coordinates (z = 0), the vertices
+// relative to the box centre; the fourth vertex slots are zero.
+__global__ void k_tri_geom(const double* __restrict__ xyz, const int32_t* __restrict__ tris,
+                           const int32_t* __restrict__ cmpt, const double* __restrict__ Dc,
+                           const double* __restrict__ invT2c, const double* __restrict__ Dten, double cx,
+                           double cy, double cz, int64_t nt, double* __restrict__ out) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double X[3][3];
+  for (int a = 0; a < 3; ++a) {
+    int64_t v = tris[3 * t + a];
+    for (int k = 0; k < 3; ++k) X[a][k] = xyz[3 * v + k];
+  }
+  const double area2 = (X[1][0] - X[0][0]) * (X[2][1] - X[0][1]) - (X[1][1] - X[0][1]) * (X[2][0] - X[0][0]);
+  const double id = 1.0 / area2;
+  double* o = out + TG * t;
+  for (int k = 0; k < TG; ++k) o[k] = 0.0;
+  o[0] = 0.5 * area2;
+  // grad lambda_a = perp(x_{a+2} - x_{a+1}) / (2 area), indices mod 3
+  for (int a = 0; a < 3; ++a) {
+    const double* p = X[(a + 1) % 3];
+    const double* q = X[(a + 2) % 3];
+    o[1 + 3 * a + 0] = (p[1] - q[1]) * id;
+    o[1 + 3 * a + 1] = (q[0] - p[0]) * id;
+  }
+  const double c[3] = {cx, cy, cz};
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) o[13 + 3 * a + k] = X[a][k] - c[k];
+  const int cm = cmpt[t];
+  o[25] = Dc[cm];
+  o[26] = invT2c ? invT2c[cm] : 0.0;
+  for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
+}
+
+// kappa |F| / 12 per interface face (3-D); kappa |e| / 6 per interface edge (2-D)
 __global__ void k_face_coef(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
                             const int32_t* __restrict__ ta, const int8_t* __restrict__ lv,
-                            const double* __restrict__ kap, int64_t nf, double* __restrict__ out) {
+                            const double* __restrict__ kap, int64_t nf, int nv, double* __restrict__ out) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= nf) return;
+  if (nv == 3) {
+    const int64_t v0 = tets[3 * (int64_t)ta[f] + lv[2 * f]], v1 = tets[3 * (int64_t)ta[f] + lv[2 * f + 1]];
+    double l2 = 0;
+    for (int k = 0; k < 3; ++k) l2 += (xyz[3 * v1 + k] - xyz[3 * v0 + k]) * (xyz[3 * v1 + k] - xyz[3 * v0 + k]);
+    out[f] = kap[f] * sqrt(l2) / 6.0;
+    return;
+  }
   double P[3][3];
   for (int a = 0; a < 3; ++a) {
     int64_t v = tets[4 * (int64_t)ta[f] + lv[3 * f + a]];
@@ -109,20 +151,27 @@ __global__ void k_face_coef(const double* __restrict__ xyz, const int32_t* __res
 __global__ void k_assemble_slots(const double* __restrict__ geo, const int64_t* __restrict__ tc_ptr,
                                  const int32_t* __restrict__ tc, const int64_t* __restrict__ fc_ptr,
                                  const int32_t* __restrict__ fc, const double* __restrict__ fcoef,
-                                 int64_t nnz, double* __restrict__ planes) {
+                                 int64_t nnz, int nv, double* __restrict__ planes) {
+  // element integrals (exact for P1): int l_i l_j = |T| (1 + d_ij) / ((d+1)(d+2)),
+  // int l_i l_j l_l = |T| d! a! b! c! / (d + a + b + c)!, int l_i = |T| / (d + 1)
+  const bool tri = nv == 3;
+  const double m_diag = tri ? 1.0 / 6.0 : 0.1, m_off = tri ? 1.0 / 12.0 : 0.05;
+  const double mom_d = tri ? 30.0 : 60.0, mom_o = tri ? 60.0 : 120.0, c_int = tri ? 1.0 / 3.0 : 0.25;
+  const int n2 = nv * nv, fs = nv - 1, nfd = 2 * fs;
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= nnz) return;
   double m = 0, kk = 0, md = 0, mx = 0, my = 0, mz = 0, ex = 0, ey = 0, ez = 0, jj = 0, mr = 0;
   for (int64_t q = tc_ptr[s]; q < tc_ptr[s + 1]; ++q) {
     int32_t code = tc[q];
-    int32_t t = code >> 4;
-    int i = (code >> 2) & 3, j = code & 3;
+    int32_t t = code / n2;
+    const int rr = code - n2 * t;
+    int i = rr / nv, j = rr - nv * (rr / nv);
     const double* g = geo + (int64_t)TG * t;
     double vol = g[0], D = g[25], rT2 = g[26];
     const double* Gi = g + 1 + 3 * i;
     const double* Gj = g + 1 + 3 * j;
     const double* Xc = g + 13;
-    double mass = vol * (i == j ? 0.1 : 0.05);
+    double mass = vol * (i == j ? m_diag : m_off);
     m += mass;
     md += D * mass;
     mr += rT2 * mass;
@@ -134,25 +183,25 @@ __global__ void k_assemble_slots(const double* __restrict__ geo, const int64_t* 
     kk += vol * (Gi[0] * DG0 + Gi[1] * DG1 + Gi[2] * DG2);
     double mom[3];
     for (int k = 0; k < 3; ++k) {
-      double S = Xc[k] + Xc[3 + k] + Xc[6 + k] + Xc[9 + k];
-      mom[k] = (i == j) ? vol * (2.0 * Xc[3 * i + k] + S) / 60.0
-                        : vol * (S + Xc[3 * i + k] + Xc[3 * j + k]) / 120.0;
+      double S = Xc[k] + Xc[3 + k] + Xc[6 + k] + (tri ? 0.0 : Xc[9 + k]);
+      mom[k] = (i == j) ? vol * (2.0 * Xc[3 * i + k] + S) / mom_d
+                        : vol * (S + Xc[3 * i + k] + Xc[3 * j + k]) / mom_o;
     }
     mx += mom[0];
     my += mom[1];
     mz += mom[2];
-    double c4 = D * vol * 0.25;
+    double c4 = D * vol * c_int;
     ex += c4 * (Gj[0] - Gi[0]);
     ey += c4 * (Gj[1] - Gi[1]);
     ez += c4 * (Gj[2] - Gi[2]);
   }
   for (int64_t q = fc_ptr[s]; q < fc_ptr[s + 1]; ++q) {
     int32_t code = fc[q];
-    int32_t f = code / 36;
-    int r = code - 36 * f;
-    int a = r / 6, b = r - 6 * a;
-    double v = fcoef[f] * ((a % 3) == (b % 3) ? 2.0 : 1.0);
-    jj += ((a < 3) == (b < 3)) ? v : -v;
+    int32_t f = code / (nfd * nfd);
+    int r = code - nfd * nfd * f;
+    int a = r / nfd, b = r - nfd * a;
+    double v = fcoef[f] * ((a % fs) == (b % fs) ? 2.0 : 1.0);
+    jj += ((a < fs) == (b < fs)) ? v : -v;
   }
   planes[0 * nnz + s] = m;
   planes[1 * nnz + s] = kk;
@@ -230,13 +279,16 @@ __global__ void k_row_data(const int32_t* __restrict__ rp, const int32_t* __rest
 
 void launch_assembly(const AsmArgs& a, cudaStream_t st) {
   const int TB = 256;
-  if (a.nt) k_tet_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c,
-                                                                  a.Dten, a.centre[0], a.centre[1], a.centre[2],
-                                                                  a.nt, a.geo);
+  if (a.nt && a.nv == 4)
+    k_tet_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
+                                                              a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
+  if (a.nt && a.nv == 3)
+    k_tri_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
+                                                              a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
   if (a.nf) k_face_coef<<<(unsigned)((a.nf + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.face_ta, a.face_lv,
-                                                                   a.face_kappa, a.nf, a.fcoef);
+                                                                   a.face_kappa, a.nf, a.nv, a.fcoef);
   k_assemble_slots<<<(unsigned)((a.nnz + TB - 1) / TB), TB, 0, st>>>(a.geo, a.tc_ptr, a.tc, a.fc_ptr, a.fc,
-                                                                    a.fcoef, a.nnz, a.planes);
+                                                                    a.fcoef, a.nnz, a.nv, a.planes);
 }
 
 void launch_derive(const DeriveArgs& a, cudaStream_t st) {

@@ -442,3 +442,59 @@ def test_weak_periodic_refusals(bt):
         assert e.value.code == bt.BT_EINVAL
     finally:
         bt.bt_destroy(ctx)
+
+
+# ---------------------------------------------------------------- 2-D triangles
+def test_triangle_planes_match_oracle(sim_cls, bt):
+    p = geom.square_disk(n=12, L=10.0, R=3.0, kappa=1e-4)
+    a = bo.assemble(p)
+    sim = sim_cls(p)
+    try:
+        rp, col = bt.bt_get_pattern(sim.ctx)
+        for nm in ["M", "K", "J", "MD", "Mx", "My", "Mz", "Ex", "Ey", "Ez"]:
+            v = bt.bt_get_plane(sim.ctx, nm)
+            ref = a[nm].tocsr()
+            dense = np.zeros_like(v)
+            for i in range(len(rp) - 1):
+                m = dict(zip(ref.getrow(i).indices, ref.getrow(i).data))
+                dense[rp[i]:rp[i + 1]] = [m.get(c, 0.0) for c in col[rp[i]:rp[i + 1]]]
+            scale = max(np.abs(dense).max(), 1e-300)
+            assert np.abs(v - dense).max() <= 1e-13 * scale, nm
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_triangle_signals_match_oracle(sim_cls, bt, mode):
+    """Disk in a square (lab frame), two directions and three b-values."""
+    p = geom.square_disk(n=16, L=10.0, R=3.0, kappa=1e-4, bvals=(0.0, 1000.0, 3000.0),
+                         dirs=((1.0, 0.0, 0.0), (0.6, 0.8, 0.0)))
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S, err, stat, st = sim.run(m)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()
+
+
+def test_triangle_periodic_square_exact_product_gpu(sim_cls, bt):
+    """Free diffusion in a periodic square (transformed frame): the exact
+    discrete product of the theta-scheme."""
+    p = geom.free_periodic_square(n=8, L=6.0, dt=50.0, dirs=((0.6, 0.8, 0.0), (1.0, 0.0, 0.0)),
+                                  bvals=(900.0, 2000.0))
+    sim = sim_cls(p)
+    try:
+        fbar, F, I = oracle.sequence(p)
+        for mode, tol in [(bt.BT_MODE_PLAIN_FP64, 1e-11), (bt.BT_MODE_MIXED, 1e-8)]:
+            S, err, stat, st = sim.run(mode)
+            assert np.all(stat == 0)
+            for r in range(p.n_rhs):
+                q2 = p.bvals[r % 2] / I
+                prod = np.prod((1 - 0.5 * p.dt * 2e-3 * q2 * F[:-1] ** 2) / (1 + 0.5 * p.dt * 2e-3 * q2 * F[1:] ** 2))
+                assert abs(S[r] / 36.0 - prod) < tol
+    finally:
+        sim.close()

@@ -184,3 +184,49 @@ def test_halo_tiles_cover_the_pattern(bt, maker, umax):
             bt.bt_get_halo_tiles(ctx, 8)
     finally:
         bt.bt_destroy(ctx)
+
+
+def _host2d(bt, p):
+    ctx = bt.bt_create(-1)
+    bt.bt_upload_mesh_2d(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, p.periodic_mask, p.box_lo,
+                         p.box_hi)
+    return ctx
+
+
+@pytest.mark.parametrize("maker", [lambda: geom.square_disk(n=10, L=10.0, R=3.0),
+                                   lambda: geom.free_periodic_square(n=5, L=6.0)])
+def test_triangle_doubling_and_pattern_match_oracle(bt, maker):
+    """2-D: interface edges doubled, dof map and CSR pattern as the oracle's."""
+    p = maker()
+    a = bo.assemble(p)
+    ctx = _host2d(bt, p)
+    try:
+        n, nnz, nf = bt.bt_get_sizes(ctx)
+        assert n == a["n"] and nf == a["n_iface"]
+        dn, dc = bt.bt_get_dofmap(ctx)
+        assert np.array_equal(dn, a["dof_node"]) and np.array_equal(dc, a["dof_cmpt"])
+        rp, col = bt.bt_get_pattern(ctx)
+        orp, ocol = _oracle_pattern(a)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    finally:
+        bt.bt_destroy(ctx)
+
+
+def test_triangle_validation_and_refusals(bt):
+    p = geom.square_disk(n=4, L=10.0, R=3.0)
+    ctx = bt.bt_create(-1)
+    try:
+        tris = p.tets.copy()
+        tris[2, [1, 2]] = tris[2, [2, 1]]                      # clockwise
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_upload_mesh_2d(ctx, p.xyz, tris, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, 0, p.box_lo, p.box_hi)
+        assert e.value.code == bt.BT_EINVAL
+        with pytest.raises(bt.BtError) as e:                    # no z axis to identify in 2-D
+            bt.bt_upload_mesh_2d(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, 4, p.box_lo, p.box_hi)
+        assert e.value.code == bt.BT_EINVAL
+        bt.bt_upload_mesh_2d(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, 0, p.box_lo, p.box_hi)
+        with pytest.raises(bt.BtError) as e:                    # weak coupling is built for tetrahedra only
+            bt.bt_set_weak_periodic(ctx, 1, 0.0)
+        assert e.value.code == bt.BT_EINVAL
+    finally:
+        bt.bt_destroy(ctx)

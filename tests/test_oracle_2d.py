@@ -1,0 +1,92 @@
+"""Pins of the 2-D (P1 triangle) discretisation.  The barycentric moments are
+checked against direct quadrature on the reference triangle; the assembled
+matrices against identities that fix them (areas, linear fields, moments,
+skew-symmetry, the interface length measured independently); the whole
+2-D transformed path against the exact discrete solution of free diffusion
+in a periodic square; the lab path by conservation at g = 0."""
+import math
+
+import numpy as np
+import pytest
+
+import geom
+import oracle
+from oracle import btoracle as bo
+
+
+def test_triangle_cubic_moments_by_quadrature():
+    """int over the reference triangle of l_i l_j l_l / area, by a Duffy map of
+    Gauss-Legendre points (exact for these cubics)."""
+    x, w = np.polynomial.legendre.leggauss(8)
+    u, v = np.meshgrid(0.5 * (x + 1), 0.5 * (x + 1), indexing="ij")
+    W = np.outer(0.25 * w, w)
+    s, t = u * (1 - v), u * v                  # Duffy: Jacobian u
+    lam = [1 - s - t, s, t]
+    c = bo._cubic_moments(2)
+    for i in range(3):
+        for j in range(3):
+            for l in range(3):
+                q = np.sum(W * u * lam[i] * lam[j] * lam[l]) / 0.5
+                assert abs(q - c[i, j, l]) < 1e-14
+
+
+@pytest.fixture(scope="module")
+def disk():
+    p = geom.square_disk(n=12, L=10.0, R=3.0)
+    return p, bo.assemble(p)
+
+
+def test_area_linear_fields_and_moments(disk):
+    p, a = disk
+    n = a["n"]
+    one = np.ones(n)
+    assert abs(one @ a["M"] @ one - 100.0) < 1e-12 * 100.0
+    for nm in ("K", "J"):
+        assert np.abs(a[nm] @ one).max() < 1e-14
+    X = p.xyz[a["dof_node"]]
+    # int x_k over the square is 0 (centred); int x^2 = L^4 / 12 by the linear-field identity
+    for k, nm in enumerate("xy"):
+        assert abs(one @ a["M" + nm] @ one) < 1e-12
+        assert abs(X[:, k] @ a["M"] @ X[:, k] - 10.0 ** 4 / 12.0) < 1e-9
+        # energy of a linear field: D |grad|^2 area
+        assert abs(X[:, k] @ a["K"] @ X[:, k] - 2e-3 * 100.0) < 1e-12
+        E = a["E" + nm]
+        assert abs(E + E.T).max() < 1e-18
+    assert a["Mz"].count_nonzero() == 0 or abs(a["Mz"]).max() < 1e-18
+
+
+def test_interface_length_by_brute_force(disk):
+    """The jump matrix J carries kappa |e| / 6 (1 + delta) per interface edge;
+    1^T J_side 1 over one side equals kappa times the interface length, which is
+    recomputed here from edges shared by triangles of different labels."""
+    p, a = disk
+    edges = {}
+    for t, tri in enumerate(p.tets):
+        for e in ((tri[0], tri[1]), (tri[1], tri[2]), (tri[2], tri[0])):
+            edges.setdefault(tuple(sorted(e)), []).append(p.tet_cmpt[t])
+    length = sum(np.linalg.norm(p.xyz[i] - p.xyz[j]) for (i, j), c in edges.items() if len(c) == 2 and c[0] != c[1])
+    side = (a["dof_cmpt"] == 1).astype(float)
+    assert abs(-(side @ a["J"] @ (1 - side)) - 1e-5 * length) < 1e-15 * max(1.0, length)
+
+
+def test_conservation_at_zero_gradient(disk):
+    p, _ = disk
+    p.bvals = np.array([0.0])
+    S, H = oracle.run(p, return_history=True)
+    assert np.max(np.abs(H[0] - 100.0)) < 1e-10 * 100.0
+
+
+def test_periodic_square_exact_discrete_product():
+    """Free diffusion in a periodic square, transformed frame: u stays constant
+    and S/|Omega| = prod (1 - (1-th) dt D q^2 F_{n-1}^2) / (1 + th dt D q^2 F_n^2),
+    tending to exp(-b D)."""
+    errs = []
+    for dt in (50.0, 25.0):
+        p = geom.free_periodic_square(n=4, L=6.0, dt=dt, dirs=((0.6, 0.8, 0.0),), bvals=(900.0,))
+        S = oracle.run(p)[0] / 36.0
+        fbar, F, I = oracle.sequence(p)
+        q2 = 900.0 / I
+        prod = np.prod((1 - 0.5 * dt * 2e-3 * q2 * F[:-1] ** 2) / (1 + 0.5 * dt * 2e-3 * q2 * F[1:] ** 2))
+        assert abs(S - prod) < 1e-12
+        errs.append(abs(S.real - math.exp(-900.0 * 2e-3)))
+    assert 3.0 < errs[0] / errs[1] < 5.0
