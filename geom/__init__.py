@@ -229,7 +229,7 @@ class Problem:
     RHS r = d * n_b + j uses direction dirs[d] and b-value bvals[j]."""
     name: str
     xyz: np.ndarray            # [n_nodes, 3] float64, um
-    tets: np.ndarray           # [n_tets, 4] int32, positive orientation
+    tets: np.ndarray           # [n_tets, 4] int32, positive orientation ([n, 3] triangles, [n, 2] segments)
     tet_cmpt: np.ndarray       # [n_tets] int32 in [0, n_cmpt)
     D_cmpt: np.ndarray         # [n_cmpt] float64, um^2/us (= mm^2/s)
     kappa_cmpt: np.ndarray     # [n_cmpt] float64, um/us (= m/s); inf = no membrane
@@ -413,6 +413,60 @@ def free_periodic_square(n: int = 8, L: float = 10.0, dt: float = 50.0, D: float
     return Problem("free_periodic_square", xyz, tris, np.zeros(len(tris), np.int32), np.array([D]),
                    np.array([NO_MEMBRANE]), 3, lo, hi, dt, 2500.0, 5000.0, 7500.0,
                    np.asarray(dirs, dtype=np.float64), np.asarray(bvals, dtype=np.float64), transformed=True)
+
+
+def line_segments(n: int, L: float = 40.0, direction=(1.0, 0.0, 0.0), dt: float = 50.0, D: float = 2e-3,
+                  bvals=(1000.0,), dirs=((1.0, 0.0, 0.0),), delta: float = 2500.0, Delta: float = 5000.0):
+    """1-D manifold: a straight fibre of length L along `direction`, centred at
+    the origin, cut into n equal P1 segments (Neumann ends)."""
+    t = np.asarray(direction, float)
+    t = t / np.linalg.norm(t)
+    s = np.linspace(-L / 2, L / 2, n + 1)
+    xyz = s[:, None] * t[None, :]
+    segs = np.stack([np.arange(n), np.arange(1, n + 1)], axis=1).astype(np.int32)
+    lo, hi = np.full(3, -L / 2), np.full(3, L / 2)
+    return Problem("line", xyz, segs, np.zeros(n, np.int32), np.array([D]), np.array([NO_MEMBRANE]), 0, lo, hi,
+                   dt, delta, Delta, Delta + delta, np.asarray(dirs, dtype=np.float64),
+                   np.asarray(bvals, dtype=np.float64))
+
+
+def dendrite_tree(seed: int = 0, n_stems: int = 6, depth: int = 5, h: float = 1.0, length=(15.0, 40.0),
+                  dt: float = 200.0, D: float = 2e-3, bvals=(0.0, 1000.0, 3000.0), n_dir: int = 3):
+    """1-D manifold standing in for a neuron's dendrite tree: n_stems primary
+    branches leave a soma point at the origin in random directions; every
+    branch bends slightly along its length and splits into two children
+    turned 25-60 degrees away from it, down to `depth` levels.  Branch lengths
+    are uniform in `length`, segments about h long; one compartment."""
+    rng = np.random.default_rng(seed)
+    xyz = [np.zeros(3)]
+    segs = []
+
+    def unit(v):
+        return v / np.linalg.norm(v)
+
+    def turn(d, lo_deg, hi_deg):
+        a = math.radians(rng.uniform(lo_deg, hi_deg))
+        w = unit(np.cross(d, rng.normal(size=3)))
+        return unit(math.cos(a) * d + math.sin(a) * w)
+
+    stack = [(0, unit(rng.normal(size=3)), 1) for _ in range(n_stems)]
+    while stack:
+        v0, d, level = stack.pop()
+        n = max(2, int(round(rng.uniform(*length) / h)))
+        v = v0
+        for _ in range(n):
+            d = turn(d, 0.0, 8.0)
+            xyz.append(xyz[v] + h * d)
+            segs.append((v, len(xyz) - 1))
+            v = len(xyz) - 1
+        if level < depth:
+            stack += [(v, turn(d, 25.0, 60.0), level + 1), (v, turn(d, 25.0, 60.0), level + 1)]
+    xyz = np.array(xyz)
+    segs = np.array(segs, dtype=np.int32)
+    lo, hi = xyz.min(axis=0) - h, xyz.max(axis=0) + h
+    return Problem("dendrite_tree", xyz, segs, np.zeros(len(segs), np.int32), np.array([D]),
+                   np.array([NO_MEMBRANE]), 0, lo, hi, dt, 10600.0, 43100.0, 53700.0, fibonacci_dirs(n_dir),
+                   np.asarray(bvals, dtype=np.float64))
 
 
 def union(problems, name="batch"):

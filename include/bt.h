@@ -85,13 +85,30 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
  * triangles; Section 2 holds in any dimension): xy [2 n_nodes] (um), tri3
  * [3 n_tris] counter-clockwise triangles, tri_cmpt [n_tris]; periodic_mask
  * bits 0 (x) and 1 (y); box_lo, box_hi [2].  Internally the plane z = 0 of a
- * box [-1, 1] in z, so gradient directions act through their x and y parts;
- * interfaces are edges with the jump term kappa <[u], [v]> on them.  Every
- * later entry point works unchanged, except bt_set_weak_periodic
- * (tetrahedra only).  Errors as bt_upload_mesh (inverted triangles included). */
+ * box [-1, 1] in z; gradient directions must lie in the xy plane
+ * (bt_set_gradients refuses a z component with BT_EINVAL); interfaces are
+ * edges with the jump term kappa <[u], [v]> on them.  Every later entry
+ * point works unchanged, except bt_set_weak_periodic (tetrahedra only).
+ * Errors as bt_upload_mesh (inverted triangles included). */
 bt_status bt_upload_mesh_2d(bt_ctx* ctx, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri3,
                             const int32_t* tri_cmpt, int32_t n_cmpt, const double* D_cmpt,
                             const double* kappa_cmpt, uint32_t periodic_mask, const double* box_lo,
+                            const double* box_hi);
+/* A 1-D manifold embedded in 3-D (Section 5, "Realistic neurons": simulation
+ * on manifolds, after the thin-media method the paper cites; Section 1 on
+ * the 1-D Bloch-Torrey equation of dendrite trees): the centre lines of thin
+ * tubes as P1 segments, cross-sections taken uniform, so the weak form is
+ * Section 2's with integrals along the curve and gradients tangential.
+ * xyz [3 n_nodes] (um); seg2 [2 n_segs] node ids (any order; zero-length
+ * segments are BT_EINVAL); seg_cmpt [n_segs] in [0, n_cmpt); D_cmpt
+ * [n_cmpt].  Branch points are nodes shared by several segments.  No
+ * membranes and no periodicity: segments of different compartments may not
+ * share a node (BT_EINVAL).  box_lo/box_hi [3] fix the origin of g.x only.
+ * Later calls work as for tetrahedra, in the lab frame only (bt_assemble
+ * refuses BT_FRAME_TRANSFORMED: there |grad (q.x)|^2 would be (q.t)^2 per
+ * segment, not q^2); bt_set_weak_periodic is refused. */
+bt_status bt_upload_mesh_1d(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_segs, const int32_t* seg2,
+                            const int32_t* seg_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* box_lo,
                             const double* box_hi);
 /* Sizes after bt_upload_mesh.  Any output pointer may be NULL. */
 bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t* n_iface);
@@ -117,7 +134,7 @@ bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t
 
 /* Transverse relaxation and initial magnetization per compartment (Section 2:
  * the T2 term of the Bloch-Torrey equation, which enters the weak form as
- * (U / T2, v), and the initial condition U(x, 0) = rho; Section 4 "Initial
+ * (U / T2, v), and the initial condition U(x, 0) = rho; Section 3 "Initial
  * conditions").  inv_T2 [n_cmpt] 1/T2 in 1/us (0 = no relaxation, the
  * default); rho [n_cmpt] initial value of u in that compartment (default 1).
  * Either pointer may be NULL (keeps the default).  The relaxation is
@@ -192,7 +209,7 @@ bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta_us, double Delta_u
  * Neumann transformed frame only (no periodic box). */
 bt_status bt_set_segments(bt_ctx* ctx, int32_t G, const int64_t* node_off, const double* delta_us,
                           const double* Delta_us, const double* TE_us);
-/* An arbitrary temporal profile f(t) (Section 4, "General diffusion-encoding
+/* An arbitrary temporal profile f(t) (Section 3, "General diffusion-encoding
  * sequence"; the magnetization equation and b of Section 2, Eq. strong_BT and
  * Eq. b_value), given by its integral on the time grid:
  *   F [n_steps + 1]  F(t_n) = int_0^{t_n} f(s) ds at t_n = n dt (us), F[0] = 0;

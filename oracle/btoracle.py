@@ -11,7 +11,11 @@ What it follows (section / equation of arXiv 1908.01719):
     Eqs. theta_discretization2, linear_billinear2, matrix_form);
   * strong pseudo-periodic conditions through the gauge transform
     u = U exp(i gamma F(t) g.x) (Appendix A, Eqs. trBlo, Periodic,
-    Binterface2 and the weak form F(u, v, t)).
+    Binterface2 and the weak form F(u, v, t));
+  * elements: P1 tetrahedra, P1 triangles for 2-D domains, and P1 segments
+    for 1-D manifolds embedded in 3-D (Section 5, "Realistic neurons": the
+    centre lines of thin tubes, integrals along the curve, tangential
+    gradients, uniform cross-section).
 
 Readings where the paper leaves a choice (each is also listed in the design
 notes of the repository):
@@ -82,7 +86,9 @@ def interface_faces(master, tets, tet_cmpt):
     Returns (elem_a, elem_b, local vertex indices of the face in elem_a
     [nf, 3] for tetrahedra, [nf, 2] for triangles).  Face keys use master ids, so faces identified by
     periodicity are found too."""
-    if tets.shape[1] == 3:                        # 2-D: edges of triangles
+    if tets.shape[1] == 2:                        # 1-D: end points of segments
+        loc = np.array([[1], [0]])
+    elif tets.shape[1] == 3:                      # 2-D: edges of triangles
         loc = np.array([[1, 2], [0, 2], [0, 1]])
     else:
         loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
@@ -118,6 +124,18 @@ def _cubic_moments(d=3):
                 num = np.prod([math.factorial(x) for x in a]) * math.factorial(d)
                 c[i, j, l] = num / math.factorial(3 + d)
     return c
+
+
+def seg_geometry(X):
+    """Lengths [nt] and tangential barycentric gradients [nt, 2, 3] of segments
+    X [nt, 2, 3] of a curve in 3-D: lambda_1 grows from 0 to 1 along e = x_1 - x_0,
+    so its gradient along the curve is e / |e|^2."""
+    e = X[:, 1] - X[:, 0]
+    l2 = np.einsum("ij,ij->i", e, e)
+    G = np.empty((len(X), 2, 3))
+    G[:, 1] = e / l2[:, None]
+    G[:, 0] = -G[:, 1]
+    return np.sqrt(l2), G
 
 
 def tri_geometry(X):
@@ -160,13 +178,17 @@ def assemble(p):
       MR  1/T2-weighted mass                (relaxation term of Section 2)
       Ex, Ey, Ez  skew transport matrices   (transformed frame, Appendix A)
     """
+    nv = p.tets.shape[1]                           # 4: tetrahedra, 3: triangles, 2: segments
+    d = nv - 1
+    if nv == 2 and (p.periodic_mask or p.transformed):
+        raise ValueError("1-D manifolds are solved in the lab frame, without periodicity")
     master = periodic_master(p.xyz, p.periodic_mask, p.box_lo, p.box_hi)
     tet_dof, dof_node, dof_cmpt = doubling(master, p.tets, p.tet_cmpt, p.n_cmpt)
     n = len(dof_node)
+    if nv == 2 and np.any(dof_node[1:] == dof_node[:-1]):
+        raise ValueError("segments of different compartments share a node")
     X = p.xyz[p.tets]                              # unwrapped element coordinates
-    nv = p.tets.shape[1]                           # 4: tetrahedra, 3: triangles (2-D)
-    d = nv - 1
-    vol, G = tet_geometry(X) if nv == 4 else tri_geometry(X)
+    vol, G = {4: tet_geometry, 3: tri_geometry, 2: seg_geometry}[nv](X)
     Dt = p.D_cmpt[p.tet_cmpt]
     rows = np.repeat(tet_dof[:, :, None], nv, axis=2)
     cols = np.repeat(tet_dof[:, None, :], nv, axis=1)
@@ -441,5 +463,7 @@ def _result(out, hist, fields, return_history, return_field):
 
 
 def run(p, asm=None, rhs=None, return_history=False, route=None, return_field=False):
+    if p.tets.shape[1] == 3 and np.any(np.abs(np.asarray(p.dirs, float)[:, 2]) > 1e-12):
+        raise ValueError("2-D meshes need gradient directions in the xy plane")
     f = run_transformed if (p.transformed or p.periodic_mask) else run_lab
     return f(p, asm, rhs, return_history, route, return_field)

@@ -1,8 +1,8 @@
 """Oracle side of the temporal profiles (TEST INFRASTRUCTURE ONLY).
 
-f(t) is written out piecewise as the paper defines it (Section 4, "General
+f(t) is written out piecewise as the paper defines it (Section 3, "General
 diffusion-encoding sequence", cos-OGSE with w = 2 pi n / delta and
-tau = (delta + Delta)/2; the other profiles of Section 5 built the same way),
+tau = (delta + Delta)/2; the other profiles of Section 4 built the same way),
 and everything else is obtained by adaptive numerical integration (SciPy
 `quad`), a different route from the library's closed forms:
   F_n   = sum over steps of int_{t_{k-1}}^{t_k} f,

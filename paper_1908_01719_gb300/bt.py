@@ -30,7 +30,8 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_set_gradients", "bt_default_opts", "bt_run", "bt_get_signals", "bt_get_stats",
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
-           "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation", "bt_set_diffusion_tensor", "bt_set_weak_periodic", "bt_upload_mesh_2d"]
+           "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation", "bt_set_diffusion_tensor", "bt_set_weak_periodic", "bt_upload_mesh_2d",
+           "bt_upload_mesh_1d"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -69,6 +70,7 @@ def lib():
             "bt_set_stream": [P, P],
             "bt_upload_mesh": [P, I64, P, I64, P, P, I32, P, P, U32, P, P],
             "bt_upload_mesh_2d": [P, I64, P, I64, P, P, I32, P, P, U32, P, P],
+            "bt_upload_mesh_1d": [P, I64, P, I64, P, P, I32, P, P, P],
             "bt_get_sizes": [P, P, P, P],
             "bt_get_dofmap": [P, P, P],
             "bt_get_pattern": [P, P, P],
@@ -160,6 +162,18 @@ def bt_upload_mesh_2d(ctx, xy, tris, tri_cmpt, D_cmpt, kappa_cmpt, periodic_mask
     hi = np.ascontiguousarray(np.asarray(box_hi, dtype=np.float64)[:2])
     _check(ctx, lib().bt_upload_mesh_2d(ctx, len(xy), _ptr(xy), len(tris), _ptr(tris), _ptr(tc), len(D), _ptr(D),
                                         _ptr(K), int(periodic_mask), _ptr(lo), _ptr(hi)))
+
+
+def bt_upload_mesh_1d(ctx, xyz, segs, seg_cmpt, D_cmpt, box_lo, box_hi):
+    """1-D manifold: P1 segments (centre lines of thin tubes) embedded in 3-D."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    segs = np.ascontiguousarray(segs, dtype=np.int32)
+    sc = np.ascontiguousarray(seg_cmpt, dtype=np.int32)
+    D = np.ascontiguousarray(D_cmpt, dtype=np.float64)
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(box_hi, dtype=np.float64)
+    _check(ctx, lib().bt_upload_mesh_1d(ctx, len(xyz), _ptr(xyz), len(segs), _ptr(segs), _ptr(sc), len(D), _ptr(D),
+                                        _ptr(lo), _ptr(hi)))
 
 
 def bt_get_sizes(ctx):

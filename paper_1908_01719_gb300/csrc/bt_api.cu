@@ -193,6 +193,17 @@ bt_status bt_upload_mesh_2d(bt_ctx* ctx, int64_t n_nodes, const double* xy, int6
                         periodic_mask, lo, hi);
 }
 
+bt_status bt_upload_mesh_1d(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_segs, const int32_t* seg2,
+                            const int32_t* seg_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* box_lo,
+                            const double* box_hi) {
+  if (!ctx) return BT_EINVAL;
+  if (n_cmpt <= 0 || n_cmpt > (1 << 20)) return fail(ctx, BT_EINVAL, "bt_upload_mesh_1d: invalid argument");
+  // no membranes on a manifold: the permeabilities are never used
+  const std::vector<double> no_kappa((size_t)n_cmpt, 0.0);
+  return upload_mesh_nv(ctx, 2, n_nodes, xyz, n_segs, seg2, seg_cmpt, n_cmpt, D_cmpt, no_kappa.data(), 0, box_lo,
+                        box_hi);
+}
+
 bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t* n_iface) {
   if (!ctx || !ctx->have_mesh) return BT_ESTATE;
   if (n_dof) *n_dof = ctx->mesh.n_dof;
@@ -317,6 +328,8 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
     return fail(ctx, BT_EINVAL, "bt_assemble: need dt > 0, 0 < theta <= 1, flags in {LAB, TRANSFORMED}");
   if (ctx->mesh.pmask && flags != BT_FRAME_TRANSFORMED)
     return fail(ctx, BT_EINVAL, "bt_assemble: periodic boxes need BT_FRAME_TRANSFORMED");
+  if (ctx->mesh.nv == 2 && flags != BT_FRAME_LAB)
+    return fail(ctx, BT_EINVAL, "bt_assemble: 1-D manifolds need the lab frame");
   if (!ctx->cm_Dten.empty() && flags == BT_FRAME_TRANSFORMED)
     return fail(ctx, BT_EINVAL, "bt_assemble: diffusion tensors need the lab frame");
   if (ctx->weak_axes && flags == BT_FRAME_TRANSFORMED)
@@ -529,6 +542,8 @@ bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32
       double nx = dirs[3 * i], ny = dirs[3 * i + 1], nz = dirs[3 * i + 2];
       double nr = std::sqrt(nx * nx + ny * ny + nz * nz);
       if (!(nr > 0) || !std::isfinite(nr)) return fail(ctx, BT_EINVAL, "bt_set_gradients: zero direction");
+      if (ctx->mesh.nv == 3 && std::fabs(nz) > 1e-12 * nr)
+        return fail(ctx, BT_EINVAL, "bt_set_gradients: 2-D meshes need directions in the xy plane");
       for (int j = 0; j < n_b; ++j) {
         if (!(bvals[j] >= 0) || !std::isfinite(bvals[j])) return fail(ctx, BT_EINVAL, "bt_set_gradients: b < 0");
         const size_t s = (size_t)g * R + i * n_b + j;

@@ -72,6 +72,21 @@ namespace bt {
 void compute_geom_features(bt_ctx* ctx) {
   const HostMesh& m = ctx->mesh;
   double vol = 0, dv = 0;
+  if (m.nv == 2) {
+    // 1-D manifold: lengths, no membranes, h = mean segment length
+    for (int64_t t = 0; t < m.n_tets; ++t) {
+      const double* a = &m.xyz[3 * m.tets[2 * t]];
+      const double* b = &m.xyz[3 * m.tets[2 * t + 1]];
+      const double l =
+          std::sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) + (b[2] - a[2]) * (b[2] - a[2]));
+      vol += l;
+      dv += l * m.D[m.tet_cmpt[t]];
+    }
+    ctx->feat_D = vol > 0 ? dv / vol : 0;
+    ctx->feat_kappa = 0;
+    ctx->feat_h = vol / std::max<int64_t>(1, m.n_tets);
+    return;
+  }
   if (m.nv == 3) {
     // 2-D: areas, interface edge lengths, h = (2 x mean triangle area)^(1/2)
     for (int64_t t = 0; t < m.n_tets; ++t) {

@@ -57,12 +57,16 @@ int validate(const HostMesh& m, std::string& msg) {
     msg = "empty mesh";
     return BT_EINVAL;
   }
-  if (m.nv != 3 && m.nv != 4) {
-    msg = "elements must be triangles or tetrahedra";
+  if (m.nv < 2 || m.nv > 4) {
+    msg = "elements must be segments, triangles or tetrahedra";
     return BT_EINVAL;
   }
   if (m.nv == 3 && (m.pmask & 4u)) {
     msg = "a 2-D mesh has no periodic z axis";
+    return BT_EINVAL;
+  }
+  if (m.nv == 2 && m.pmask) {
+    msg = "a 1-D manifold mesh has no periodic axes";
     return BT_EINVAL;
   }
   if (m.n_nodes >= (int64_t(1) << 31) || m.n_tets * 16 >= (int64_t(1) << 31)) {
@@ -89,7 +93,7 @@ int validate(const HostMesh& m, std::string& msg) {
       msg = "non-finite node coordinate";
       return BT_EINVAL;
     }
-  const char* what = m.nv == 4 ? "tetrahedron " : "triangle ";
+  const char* what = m.nv == 4 ? "tetrahedron " : m.nv == 3 ? "triangle " : "segment ";
   for (int64_t t = 0; t < m.n_tets; ++t) {
     const int32_t* v = &m.tets[m.nv * t];
     for (int a = 0; a < m.nv; ++a)
@@ -104,6 +108,10 @@ int validate(const HostMesh& m, std::string& msg) {
     double vol;
     if (m.nv == 4) {
       vol = signed_volume(&m.xyz[3 * v[0]], &m.xyz[3 * v[1]], &m.xyz[3 * v[2]], &m.xyz[3 * v[3]]);
+    } else if (m.nv == 2) {  // length of a segment (no orientation)
+      const double* a = &m.xyz[3 * v[0]];
+      const double* b = &m.xyz[3 * v[1]];
+      vol = std::sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) + (b[2] - a[2]) * (b[2] - a[2]));
     } else {  // signed area in the xy plane (counter-clockwise positive)
       const double* a = &m.xyz[3 * v[0]];
       const double* b = &m.xyz[3 * v[1]];
@@ -215,7 +223,8 @@ void double_interface_nodes(HostMesh& m) {
   });
 }
 
-// Faces shared by two tetrahedra of different compartments.  Only faces whose
+// Faces (edges in 2-D) shared by two elements of different compartments; a
+// 1-D mesh has none, its nodes carrying one dof each.  Only faces whose
 // three (master) vertices all carry more than one dof can be interface faces.
 void find_interface_faces(HostMesh& m) {
   std::vector<uint8_t> multi(m.n_nodes, 0);
@@ -224,8 +233,9 @@ void find_interface_faces(HostMesh& m) {
   // faces of a tetrahedron (vertex triples) or edges of a triangle (pairs)
   static const int LOC4[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
   static const int LOC3[3][3] = {{1, 2, -1}, {0, 2, -1}, {0, 1, -1}};
+  static const int LOC2[2][3] = {{1, -1, -1}, {0, -1, -1}};
   const int nv = m.nv, fs = nv - 1;
-  auto LOC = [&](int f, int a) { return nv == 4 ? LOC4[f][a] : LOC3[f][a]; };
+  auto LOC = [&](int f, int a) { return nv == 4 ? LOC4[f][a] : nv == 3 ? LOC3[f][a] : LOC2[f][a]; };
   struct Cand {
     std::array<int32_t, 3> key;
     int32_t tet;
@@ -612,6 +622,12 @@ int build_host_mesh(HostMesh& m, std::string& msg) {
   st = periodic_identify(m, msg);
   if (st) return st;
   double_interface_nodes(m);
+  if (m.nv == 2)  // a manifold carries no membranes: one compartment per node
+    for (int64_t d = 1; d < m.n_dof; ++d)
+      if (m.dof_node[d] == m.dof_node[d - 1]) {
+        msg = "segments of different compartments share node " + std::to_string(m.dof_node[d]);
+        return BT_EINVAL;
+      }
   find_interface_faces(m);
   if (m.nnz >= (int64_t(1) << 31)) {
     msg = "pattern too large";

@@ -113,6 +113,41 @@ __global__ void k_tri_geom(const double* __restrict__ xyz, const int32_t* __rest
   for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
 }
 
+// The record for a segment of a 1-D manifold embedded in 3-D: length, the
+// tangential gradients -+ e / |e|^2 of the two barycentric coordinates, the
+// vertices relative to the box centre; the other vertex slots are zero.
+__global__ void k_seg_geom(const double* __restrict__ xyz, const int32_t* __restrict__ segs,
+                           const int32_t* __restrict__ cmpt, const double* __restrict__ Dc,
+                           const double* __restrict__ invT2c, const double* __restrict__ Dten, double cx,
+                           double cy, double cz, int64_t nt, double* __restrict__ out) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double X[2][3];
+  for (int a = 0; a < 2; ++a) {
+    int64_t v = segs[2 * t + a];
+    for (int k = 0; k < 3; ++k) X[a][k] = xyz[3 * v + k];
+  }
+  double e[3], l2 = 0;
+  for (int k = 0; k < 3; ++k) {
+    e[k] = X[1][k] - X[0][k];
+    l2 += e[k] * e[k];
+  }
+  double* o = out + TG * t;
+  for (int k = 0; k < TG; ++k) o[k] = 0.0;
+  o[0] = sqrt(l2);
+  for (int k = 0; k < 3; ++k) {
+    o[1 + k] = -e[k] / l2;
+    o[4 + k] = e[k] / l2;
+  }
+  const double c[3] = {cx, cy, cz};
+  for (int a = 0; a < 2; ++a)
+    for (int k = 0; k < 3; ++k) o[13 + 3 * a + k] = X[a][k] - c[k];
+  const int cm = cmpt[t];
+  o[25] = Dc[cm];
+  o[26] = invT2c ? invT2c[cm] : 0.0;
+  for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
+}
+
 // kappa |F| / 12 per interface face (3-D); kappa |e| / 6 per interface edge (2-D)
 __global__ void k_face_coef(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
                             const int32_t* __restrict__ ta, const int8_t* __restrict__ lv,
@@ -152,11 +187,14 @@ __global__ void k_assemble_slots(const double* __restrict__ geo, const int64_t* 
                                  const int32_t* __restrict__ tc, const int64_t* __restrict__ fc_ptr,
                                  const int32_t* __restrict__ fc, const double* __restrict__ fcoef,
                                  int64_t nnz, int nv, double* __restrict__ planes) {
-  // element integrals (exact for P1): int l_i l_j = |T| (1 + d_ij) / ((d+1)(d+2)),
-  // int l_i l_j l_l = |T| d! a! b! c! / (d + a + b + c)!, int l_i = |T| / (d + 1)
-  const bool tri = nv == 3;
-  const double m_diag = tri ? 1.0 / 6.0 : 0.1, m_off = tri ? 1.0 / 12.0 : 0.05;
-  const double mom_d = tri ? 30.0 : 60.0, mom_o = tri ? 60.0 : 120.0, c_int = tri ? 1.0 / 3.0 : 0.25;
+  // element integrals over a d-simplex (exact for P1):
+  //   int l_i l_j = |T| (1 + d_ij) / ((d+1)(d+2)),   int l_i = |T| / (d + 1),
+  //   int l_i l_j l_l = |T| d! a! b! c! / (d + a + b + c)!, which makes
+  //   int l_i^2 x = 2 |T| (S + 2 x_i) d! / (d+3)!,  int l_i l_j x = |T| (S + x_i + x_j) d! / (d+3)!
+  //   with S the sum of the element's vertices (unused vertex slots hold zero)
+  const int d = nv - 1;
+  const double m_off = 1.0 / ((d + 1) * (d + 2)), m_diag = 2.0 * m_off;
+  const double mom_o = d == 3 ? 120.0 : d == 2 ? 60.0 : 24.0, mom_d = 0.5 * mom_o, c_int = 1.0 / (d + 1);
   const int n2 = nv * nv, fs = nv - 1, nfd = 2 * fs;
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= nnz) return;
@@ -183,7 +221,7 @@ __global__ void k_assemble_slots(const double* __restrict__ geo, const int64_t* 
     kk += vol * (Gi[0] * DG0 + Gi[1] * DG1 + Gi[2] * DG2);
     double mom[3];
     for (int k = 0; k < 3; ++k) {
-      double S = Xc[k] + Xc[3 + k] + Xc[6 + k] + (tri ? 0.0 : Xc[9 + k]);
+      double S = Xc[k] + Xc[3 + k] + Xc[6 + k] + Xc[9 + k];
       mom[k] = (i == j) ? vol * (2.0 * Xc[3 * i + k] + S) / mom_d
                         : vol * (S + Xc[3 * i + k] + Xc[3 * j + k]) / mom_o;
     }
@@ -282,6 +320,9 @@ void launch_assembly(const AsmArgs& a, cudaStream_t st) {
   if (a.nt && a.nv == 4)
     k_tet_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
                                                               a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
+  if (a.nt && a.nv == 2)
+    k_seg_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
+                                                               a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
   if (a.nt && a.nv == 3)
     k_tri_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
                                                               a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);

@@ -2,9 +2,9 @@
 `bt_set_profile` takes: F(t_n) = int_0^{t_n} f on the time grid and
 int_0^TE F^2 (for b = q^2 int F^2, Eq. b_value).
 
-The paper's framework accepts arbitrary profiles (Section 4, "General
+The paper's framework accepts arbitrary profiles (Section 3, "General
 diffusion-encoding sequence") and shows PGSE, double PGSE, cos-OGSE, sin-OGSE,
-trapezoidal and double trapezoidal PGSE (Section 5).  Here F is written in
+trapezoidal and double trapezoidal PGSE (Section 4).  Here F is written in
 closed form per profile and int F^2 is integrated with composite
 Gauss-Legendre quadrature between the profile's breakpoints (F is smooth
 between them).  Times in us.

@@ -21,9 +21,12 @@ class Simulation:
         self.ctx = bt.bt_create(device)
         if stream is not None:
             bt.bt_set_stream(self.ctx, stream)
-        upload = bt.bt_upload_mesh_2d if geom.tets.shape[1] == 3 else bt.bt_upload_mesh
-        upload(self.ctx, geom.xyz, geom.tets, geom.tet_cmpt, geom.D_cmpt, geom.kappa_cmpt,
-               geom.periodic_mask, geom.box_lo, geom.box_hi)
+        if geom.tets.shape[1] == 2:
+            bt.bt_upload_mesh_1d(self.ctx, geom.xyz, geom.tets, geom.tet_cmpt, geom.D_cmpt, geom.box_lo, geom.box_hi)
+        else:
+            upload = bt.bt_upload_mesh_2d if geom.tets.shape[1] == 3 else bt.bt_upload_mesh
+            upload(self.ctx, geom.xyz, geom.tets, geom.tet_cmpt, geom.D_cmpt, geom.kappa_cmpt,
+                   geom.periodic_mask, geom.box_lo, geom.box_hi)
         self.n_dof, self.nnz, self.n_iface = bt.bt_get_sizes(self.ctx)
         self.frame = bt.BT_FRAME_TRANSFORMED if (geom.transformed or geom.periodic_mask) else bt.BT_FRAME_LAB
         seg = getattr(geom, "segments", None)

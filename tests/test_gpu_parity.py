@@ -498,3 +498,63 @@ def test_triangle_periodic_square_exact_product_gpu(sim_cls, bt):
                 assert abs(S[r] / 36.0 - prod) < tol
     finally:
         sim.close()
+
+
+def test_triangle_directions_must_lie_in_plane(sim_cls, bt):
+    p = geom.square_disk(n=4, L=10.0, R=3.0, dirs=((0.6, 0.0, 0.8),))
+    with pytest.raises(bt.BtError) as e:
+        sim_cls(p)
+    assert e.value.code == bt.BT_EINVAL
+
+
+# ---------------------------------------------------------------- 1-D manifolds
+def _tree():
+    return geom.dendrite_tree(seed=4, n_stems=4, depth=4, length=(10.0, 25.0))
+
+
+def test_manifold_planes_match_oracle(sim_cls, bt):
+    p = _tree()
+    a = bo.assemble(p)
+    sim = sim_cls(p)
+    try:
+        rp, col = bt.bt_get_pattern(sim.ctx)
+        for nm in ["M", "K", "J", "MD", "Mx", "My", "Mz", "Ex", "Ey", "Ez"]:
+            v = bt.bt_get_plane(sim.ctx, nm)
+            ref = a[nm].tocsr()
+            dense = np.zeros_like(v)
+            for i in range(len(rp) - 1):
+                m = dict(zip(ref.getrow(i).indices, ref.getrow(i).data))
+                dense[rp[i]:rp[i + 1]] = [m.get(c, 0.0) for c in col[rp[i]:rp[i + 1]]]
+            scale = max(np.abs(dense).max(), 1e-300)
+            assert np.abs(v - dense).max() <= 1e-13 * scale, nm
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_manifold_signals_match_oracle(sim_cls, bt, mode):
+    """Branched dendrite tree, three directions and three b-values."""
+    p = _tree()
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S, err, stat, st = sim.run(m)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()
+
+
+def test_manifold_transformed_frame_refused(bt):
+    p = geom.line_segments(8)
+    ctx = bt.bt_create(0)
+    try:
+        bt.bt_upload_mesh_1d(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.box_lo, p.box_hi)
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_assemble(ctx, 50.0, 0.5, bt.BT_FRAME_TRANSFORMED)
+        assert e.value.code == bt.BT_EINVAL
+        bt.bt_assemble(ctx, 50.0, 0.5, bt.BT_FRAME_LAB)
+    finally:
+        bt.bt_destroy(ctx)

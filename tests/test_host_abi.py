@@ -230,3 +230,48 @@ def test_triangle_validation_and_refusals(bt):
         assert e.value.code == bt.BT_EINVAL
     finally:
         bt.bt_destroy(ctx)
+
+
+def test_manifold_dofmap_and_pattern_match_oracle(bt):
+    """1-D: one dof per node, tridiagonal along branches, wider at branch points."""
+    p = geom.dendrite_tree(seed=2, n_stems=3, depth=3, length=(6.0, 12.0))
+    a = bo.assemble(p)
+    ctx = bt.bt_create(-1)
+    try:
+        bt.bt_upload_mesh_1d(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.box_lo, p.box_hi)
+        n, nnz, nf = bt.bt_get_sizes(ctx)
+        assert n == a["n"] == len(p.xyz) and nf == 0
+        dn, dc = bt.bt_get_dofmap(ctx)
+        assert np.array_equal(dn, a["dof_node"]) and np.array_equal(dc, a["dof_cmpt"])
+        rp, col = bt.bt_get_pattern(ctx)
+        orp, ocol = _oracle_pattern(a)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+        deg = np.bincount(p.tets.ravel(), minlength=len(p.xyz))
+        assert np.array_equal(np.diff(rp), deg + 1)
+    finally:
+        bt.bt_destroy(ctx)
+
+
+@pytest.mark.parametrize("defect", ["zero_length", "touching_cmpts", "node_range"])
+def test_manifold_validation_errors(bt, defect):
+    p = geom.line_segments(8)
+    xyz, segs, sc, D = p.xyz.copy(), p.tets.copy(), p.tet_cmpt.copy(), p.D_cmpt.copy()
+    if defect == "zero_length":
+        xyz[3] = xyz[2]
+    elif defect == "touching_cmpts":
+        sc[4:] = 1
+        D = np.array([2e-3, 1e-3])
+    elif defect == "node_range":
+        segs[2, 1] = len(xyz)
+    ctx = bt.bt_create(-1)
+    try:
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_upload_mesh_1d(ctx, xyz, segs, sc, D, p.box_lo, p.box_hi)
+        assert e.value.code == bt.BT_EINVAL
+        assert len(bt.bt_last_error(ctx)) > 0
+        bt.bt_upload_mesh_1d(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.box_lo, p.box_hi)
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_set_weak_periodic(ctx, 1, 0.0)
+        assert e.value.code == bt.BT_EINVAL
+    finally:
+        bt.bt_destroy(ctx)

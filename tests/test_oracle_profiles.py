@@ -1,5 +1,5 @@
-"""Pins of the arbitrary temporal profiles (Section 4, "General
-diffusion-encoding sequence"; the profiles of Section 5).  The oracle
+"""Pins of the arbitrary temporal profiles (Section 3, "General
+diffusion-encoding sequence"; the profiles of Section 4).  The oracle
 integrates f numerically; these tests fix it against closed forms of
 int_0^TE F^2 derived by hand, against the library's independent closed-form
 tables, and through the exact free-diffusion solution of the periodic box,

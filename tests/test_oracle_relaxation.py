@@ -1,6 +1,6 @@
 """Pins of transverse relaxation and per-compartment initial conditions
 (Section 2, the T2 term of the Bloch-Torrey equation and the initial
-condition; Section 4, "Initial conditions").  At g = 0 and kappa = 0 each
+condition; Section 3, "Initial conditions").  At g = 0 and kappa = 0 each
 compartment keeps a spatially constant field, so the theta-scheme reduces to
 the scalar recursion u^n = u^{n-1} (1 - (1-th) dt/T2) / (1 + th dt/T2):
 S = sum_c rho_c |Omega_c| r_c^N exactly, with |Omega_c| summed from the
