@@ -9,7 +9,13 @@ and finite cylinders with per-cell permeability, 32 directions x 4 b-values,
 PGSE delta 2.5 ms / Delta 5 ms, dt 50 us, 150 steps), mixed precision (FP32
 complex SpMM and COCG inside double-float iterative refinement).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Other workloads (--config): cfg1-cfg3 (the smaller 3-D cases), disk2d (2-D P1
+triangles: a disk of radius 5 um in a 20 um square, 512^2 cells, 32 in-plane
+directions x 4 b-values) and trees1d (1-D manifolds: 64 seeded dendrite trees
+as one uneven batch, PGSE delta 10.6 ms / Delta 43.1 ms, dt 200 us, 3
+directions x 3 b-values per tree).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config NAME]
   torchrun --nproc-per-node N bench.py --gpus N ...     (one replica per rank,
                                                         weak scaling, no collective
                                                         on the data path)
@@ -39,8 +45,22 @@ METRIC = "Bloch-Torrey step-RHS/s and HBM %peak, at <=1e-6 signal err vs FP64"
 UNIT = "step-RHS/s"
 
 
+N_TREES = 64
+
+
+def disk2d(n=512):
+    import geom
+    ang = np.pi * np.arange(32) / 32
+    dirs = np.stack([np.cos(ang), np.sin(ang), np.zeros_like(ang)], axis=1)
+    return geom.square_disk(n=n, L=20.0, R=5.0, kappa=1e-4, bvals=(500.0, 1000.0, 2000.0, 3000.0), dirs=dirs)
+
+
 def workload(name):
     import geom
+    if name == "disk2d":
+        return disk2d()
+    if name == "trees1d":
+        return geom.union([geom.dendrite_tree(seed=s) for s in range(N_TREES)], name="trees1d")
     if name == "cfg4":
         return geom.cfg4()
     if name == "cfg3":
@@ -52,15 +72,23 @@ def workload(name):
     raise ValueError(name)
 
 
+def n_geometries(p):
+    seg = getattr(p, "segments", None)
+    return 1 if seg is None else len(seg["node_off"]) - 1
+
+
 def describe(name, p, n_dof, nnz, n_face):
-    return {"workload": f"{name}: {len(p.xyz)} nodes, {len(p.tets)} Kuhn tets, {p.n_cmpt} compartments, "
+    elem = {4: "Kuhn tets", 3: "triangles (2-D)", 2: "segments (1-D manifold)"}[p.tets.shape[1]]
+    G = n_geometries(p)
+    return {"workload": f"{name}: {len(p.xyz)} nodes, {len(p.tets)} {elem}, {p.n_cmpt} compartments, "
+                        + (f"{G} geometries as one uneven batch, " if G > 1 else "") +
                         f"{n_dof} dofs after interface doubling, {nnz} nonzeros, {n_face} interface faces; "
                         f"{len(p.dirs)} dirs x {len(p.bvals)} b-values = {p.n_rhs} RHS; PGSE delta {p.delta/1e3} ms "
                         f"Delta {p.Delta/1e3} ms, dt {p.dt} us, {p.n_steps} steps; "
                         f"{'transformed (periodic)' if p.transformed else 'lab'} frame",
-            "n_dof": n_dof, "nnz": nnz, "rhs": p.n_rhs, "time_steps": p.n_steps,
+            "n_dof": n_dof, "nnz": nnz, "rhs": p.n_rhs * G, "time_steps": p.n_steps,
             "l2_policy": "inputs larger than L2: Krylov vectors n_dof x RHS x 8 B each "
-                         f"({n_dof * p.n_rhs * 8 / 1e9:.2f} GB) >> 129 MB L2"}
+                         f"({n_dof * p.n_rhs * 8 / 1e9:.2f} GB) vs 129 MB L2"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -117,15 +145,26 @@ def _oracle_task(args):
     name, grid, r = args
     import geom
     import oracle
-    p = {"cfg4": geom.cfg4, "cfg3": geom.cfg3, "cfg2": geom.cfg2, "cfg1": geom.cfg1}[name](n=grid)
     t0 = time.time()
+    if name == "trees1d":                  # one whole tree (all its RHS) per task
+        p = geom.dendrite_tree(seed=r)
+        oracle.run(p)
+        return time.time() - t0, p.n_steps * p.n_rhs
+    p = disk2d(n=grid) if name == "disk2d" else \
+        {"cfg4": geom.cfg4, "cfg3": geom.cfg3, "cfg2": geom.cfg2, "cfg1": geom.cfg1}[name](n=grid)
     oracle.run(p, rhs=[r])
     return time.time() - t0, p.n_steps
 
 
+def oracle_grid(name):
+    return {"disk2d": 192, "trees1d": 0}.get(name, ORACLE_GRID)
+
+
 def oracle_sample(name, n_rhs_sample, grid):
     """The oracle as it stands on `n_rhs_sample` RHS of the same seeded
-    geometry on a `grid`^3 Kuhn grid, one process per RHS (spawn pool)."""
+    geometry on a coarser grid (3-D: `grid`^3 Kuhn cells; 2-D: `grid`^2
+    cells), one process per RHS (spawn pool); for the dendrite trees, the
+    first `n_rhs_sample` trees of the batch with all their RHS."""
     cores = min(n_rhs_sample, os.cpu_count() or 1)
     ctx = mp.get_context("spawn")
     # one BLAS/OpenMP thread per worker: several workers with multi-threaded
@@ -143,10 +182,15 @@ def oracle_sample(name, n_rhs_sample, grid):
             else:
                 os.environ[k] = v
     wall = time.time() - t0
-    steps = res[0][1]
-    return {"value": steps * n_rhs_sample / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{name} seeded geometry on a {grid}^3 Kuhn grid, {n_rhs_sample} RHS x {steps} steps, "
-                      f"one process per RHS, wall {wall:.1f} s including assembly and process start"}
+    units = sum(r[1] for r in res)
+    if name == "trees1d":
+        what = f"trees1d: the first {n_rhs_sample} dendrite trees of the batch, all 9 RHS x {res[0][1] // 9} steps"
+    elif name == "disk2d":
+        what = f"disk2d seeded geometry on a {grid}^2 grid, {n_rhs_sample} RHS x {res[0][1]} steps"
+    else:
+        what = f"{name} seeded geometry on a {grid}^3 Kuhn grid, {n_rhs_sample} RHS x {res[0][1]} steps"
+    return {"value": units / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": what + f", one process per task, wall {wall:.1f} s including assembly and process start"}
 
 
 # ---------------------------------------------------------------- main arms
@@ -163,7 +207,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    sample_rhs, grid = min(8, os.cpu_count() or 1), ORACLE_GRID
+    sample_rhs, grid = min(8, os.cpu_count() or 1), oracle_grid(args.config)
     vals, walls = [], []
     for i in range(args.warmup + args.steps):
         t0 = time.time()
@@ -226,7 +270,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     t_setup = time.time() - t_setup
     mode = bt.BT_MODE_MIXED
-    units = p.n_steps * p.n_rhs
+    G = n_geometries(p)
+    units = p.n_steps * p.n_rhs * G
 
     def barrier():
         if ws > 1:
@@ -271,17 +316,20 @@ def run_ours(args):
     value = units * args.steps * ws / (ms_max / 1e3)
 
     # accuracy and the plain per-direction FP64 GPU solve on a sample of RHS
-    sample = sorted(set([0, p.n_rhs // 3, (2 * p.n_rhs) // 3, p.n_rhs - 1]))
+    # (an uneven batch runs every RHS of every geometry at once)
+    sample = sorted(set([0, p.n_rhs // 3, (2 * p.n_rhs) // 3, p.n_rhs - 1])) if G == 1 else list(range(p.n_rhs))
+    ranges = [(r, r + 1) for r in sample] if G == 1 else [(0, 0)]
     fp64_ms, errs = 0.0, []
-    for r in sample:
+    for rb, re in ranges:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        S64, _, stat64, _ = sim.run(bt.BT_MODE_PLAIN_FP64, rhs_begin=r, rhs_end=r + 1)
+        S64, _, stat64, _ = sim.run(bt.BT_MODE_PLAIN_FP64, rhs_begin=rb, rhs_end=re)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         fp64_ms += e0.elapsed_time(e1)
-        errs.append(abs(S[r] - S64[r]) / abs(S64[r]))
-    fp64_rate = p.n_steps * len(sample) / (fp64_ms / 1e3)
+        idx = [rb] if G == 1 else range(G * p.n_rhs)
+        errs += [abs(S[i] - S64[i]) / abs(S64[i]) for i in idx]
+    fp64_rate = p.n_steps * len(sample) * G / (fp64_ms / 1e3)
 
     # roofline of the dominant kernel (fused FP32 SpMM), from live CUDA events
     n, nnz, nf = sim.n_dof, sim.nnz, sim.n_iface
@@ -313,7 +361,7 @@ def run_ours(args):
 
     if rank != 0:
         return
-    cpu = oracle_sample(args.config, min(8, os.cpu_count() or 1), ORACLE_GRID) if ws == 1 else None
+    cpu = oracle_sample(args.config, min(8, os.cpu_count() or 1), oracle_grid(args.config)) if ws == 1 else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp32 (SpMM/Krylov) + double-float residual",
@@ -332,7 +380,7 @@ def run_ours(args):
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "frac_of_nominal_7900_gbs": achieved / 7900.0,
                          "traffic": (ROW_SPMM_TRAFFIC["bytes"] * n / ROW_SPMM_TRAFFIC["n_dof"]
-                                     if tuning["variant"] == "row" and not p.transformed and p.n_rhs == 128
+                                     if tuning["variant"] == "row" and args.config == "cfg4"
                                      else None),
                          "traffic_note": "ncu DRAM bytes per launch of the 64^3 case scaled by the dof "
                                          "ratio (the row kernel reads all columns)",
@@ -357,7 +405,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--config", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4", "disk2d", "trees1d"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
