@@ -12,7 +12,7 @@ complex SpMM and COCG inside double-float iterative refinement).
 Other workloads (--config): cfg1-cfg3 (the smaller 3-D cases), disk2d (2-D P1
 triangles: a disk of radius 5 um in a 20 um square, 512^2 cells, 32 in-plane
 directions x 4 b-values) and trees1d (1-D manifolds: 64 seeded dendrite trees
-as one uneven batch, PGSE delta 10.6 ms / Delta 43.1 ms, dt 200 us, 3
+as one uneven batch, PGSE delta 10.6 ms / Delta 43.1 ms, dt 100 us, 3
 directions x 3 b-values per tree).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config NAME]

@@ -431,12 +431,14 @@ def line_segments(n: int, L: float = 40.0, direction=(1.0, 0.0, 0.0), dt: float 
 
 
 def dendrite_tree(seed: int = 0, n_stems: int = 6, depth: int = 5, h: float = 1.0, length=(15.0, 40.0),
-                  dt: float = 200.0, D: float = 2e-3, bvals=(0.0, 1000.0, 3000.0), n_dir: int = 3):
+                  dt: float = 100.0, D: float = 2e-3, bvals=(0.0, 1000.0, 3000.0), n_dir: int = 3):
     """1-D manifold standing in for a neuron's dendrite tree: n_stems primary
     branches leave a soma point at the origin in random directions; every
     branch bends slightly along its length and splits into two children
     turned 25-60 degrees away from it, down to `depth` levels.  Branch lengths
-    are uniform in `length`, segments about h long; one compartment."""
+    are uniform in `length`, segments about h long; one compartment.  The
+    sequence is the paper's neuron PGSE (delta 10.6 ms, Delta 43.1 ms), whose
+    TE = 53.7 ms is a multiple of dt = 100 us."""
     rng = np.random.default_rng(seed)
     xyz = [np.zeros(3)]
     segs = []

@@ -301,8 +301,11 @@ def pgse_tables(delta, Delta, dt, n_steps):
 def sequence(p):
     """(f_bar_n, F_n, int_0^TE F^2) of problem p: PGSE in closed form (Section 2,
     Eq. pgse), or p.profile = {"kind": ..., "n_periods": ..., "ramp": ...}
-    integrated numerically from f (oracle/profiles.py)."""
+    integrated numerically from f (oracle/profiles.py).  The time grid
+    t_n = n dt of the theta-scheme must end at TE."""
     N = p.n_steps
+    if N < 1 or abs(N * p.dt - p.TE) > 1e-9 * p.TE:
+        raise ValueError("TE must be a positive integer multiple of dt")
     prof = getattr(p, "profile", None)
     if prof:
         from . import profiles
