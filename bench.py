@@ -240,14 +240,17 @@ VECTORS_PER_SYSTEM = {"row": 2, "halo": 6}
 ROW_SPMM_TRAFFIC = {"n_dof": 343793, "bytes": 791.9e6 + 329.7e6}
 
 
-def spmm_bytes(n, nnz, transformed, launches, sys_iters, variant):
+def spmm_bytes(n, nnz, transformed, launches, sys_iters, variant, G=1):
     """Algorithmic HBM bytes of the dominant kernel summed over its launches:
     per launch the row pointers, column indices and packed FP32 planes (A0 and
     three direction planes, plus MD in the transformed frame), and per active
-    system of each launch its vectors (VECTORS_PER_SYSTEM x n x 8 B)."""
+    system of each launch its vectors (VECTORS_PER_SYSTEM x rows x 8 B).  A
+    system spans its own geometry's rows: n for one geometry, n / G on average
+    in an uneven batch of G (the per-geometry split of the iteration count is
+    not recorded, so the batch figure uses the mean)."""
     planes = 5 if transformed else 4
     matrix = 4 * (n + 1) + nnz * (4 + 4 * planes)
-    return launches * matrix + sys_iters * VECTORS_PER_SYSTEM[variant] * n * 8
+    return launches * matrix + sys_iters * VECTORS_PER_SYSTEM[variant] * (n / G) * 8
 
 
 def run_ours(args):
@@ -333,7 +336,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (fused FP32 SpMM), from live CUDA events
     n, nnz, nf = sim.n_dof, sim.nnz, sim.n_iface
-    bytes_total = spmm_bytes(n, nnz, p.transformed, spmm_launch, sys_iters, tuning["variant"])
+    bytes_total = spmm_bytes(n, nnz, p.transformed, spmm_launch, sys_iters, tuning["variant"], G)
     bytes_launch = bytes_total / max(1, spmm_launch)
     avg_ms = spmm_ms / max(1, spmm_launch)
     achieved = bytes_total / (spmm_ms / 1e3) / 1e9
