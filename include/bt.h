@@ -145,8 +145,8 @@ bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t
 bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho);
 
 /* Anisotropic diffusion (the diffusion term div(D grad U) of Section 2 with a
- * tensor D per compartment; the survey lists per-compartment tensors as an
- * extension): D6 [n_cmpt][6] = (xx, yy, zz, xy, yz, zx) in mm^2/s, each
+ * tensor D per compartment, as Section 3 "Diffusion coefficients and
+ * tensors" allows): D6 [n_cmpt][6] = (xx, yy, zz, xy, yz, zx) in mm^2/s, each
  * symmetric positive semi-definite; NULL returns to the isotropic D_cmpt.
  * The tensor enters the stiffness K = (D grad phi_j, grad phi_i).  Lab frame
  * only (bt_assemble with BT_FRAME_TRANSFORMED then fails with BT_EINVAL: the

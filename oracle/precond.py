@@ -1,8 +1,8 @@
 """FP64 CPU reference of the learned polynomial preconditioner (test
 infrastructure only).
 
-Model (the preconditioner the spec problem statement asks for; the paper
-itself uses an unnamed PETSc solver, Appendix B "linsolver"):
+Model (a learned preconditioner added to the method: the paper itself leaves
+the linear solver to an unnamed PETSc method, Appendix B "linsolver"):
   features  phi = (dt, q |f|, D, kappa, h), each mapped to
             x_k = (log(phi_k + eps_k) - mu_k) / sd_k  (constants FEATURE_NORM)
   network   a1 = relu(W1 x + b1) (64), a2 = relu(W2 a1 + b2) (64),
