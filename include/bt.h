@@ -88,8 +88,8 @@ bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_
  * box [-1, 1] in z; gradient directions must lie in the xy plane
  * (bt_set_gradients refuses a z component with BT_EINVAL); interfaces are
  * edges with the jump term kappa <[u], [v]> on them.  Every later entry
- * point works unchanged, except bt_set_weak_periodic (tetrahedra only).
- * Errors as bt_upload_mesh (inverted triangles included). */
+ * point works unchanged; bt_set_weak_periodic couples boundary edges on the
+ * x and y sides.  Errors as bt_upload_mesh (inverted triangles included). */
 bt_status bt_upload_mesh_2d(bt_ctx* ctx, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri3,
                             const int32_t* tri_cmpt, int32_t n_cmpt, const double* D_cmpt,
                             const double* kappa_cmpt, uint32_t periodic_mask, const double* box_lo,
@@ -160,7 +160,8 @@ bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6);
  * axis k of `axes` (bit mask, disjoint from the mesh's periodic_mask) the
  * faces x_k = lo_k and x_k = hi_k are coupled through an artificial
  * permeability kappa_e (um/us; <= 0 selects max D / h, h = (6 x mean
- * tetrahedron volume)^(1/3)).  Each step treats a face implicitly and its
+ * tetrahedron volume)^(1/3), or (2 x mean triangle area)^(1/2) in 2-D, where
+ * the faces are boundary edges and axis z cannot be coupled).  Each step treats a face implicitly and its
  * partner face from the previous step with the phase e^{+-i q qhat_k L_k
  * F(t_n)}: L_n = M + theta dt (A_n + kappa_e B), r_0 += theta dt kappa_e C_n
  * u^{n-1}, B the boundary-face mass, C_n the face-mass coupling of partner
@@ -168,8 +169,8 @@ bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6);
  * both here, which is identical at theta = 1/2).  The mesh must match across
  * the box (the partner of a node is the node at x + L_k e_k).  Lab frame and
  * one geometry only.  Clears the assembly like bt_set_relaxation; axes = 0
- * switches the coupling off.  BT_EINVAL for a non-matching mesh or axes that
- * are periodic in the mesh. */
+ * switches the coupling off.  BT_EINVAL for a non-matching mesh, axes that
+ * are periodic in the mesh, or a 1-D manifold mesh. */
 bt_status bt_set_weak_periodic(bt_ctx* ctx, uint32_t axes, double kappa_e);
 
 /* ---------------------------------------------------------------- assembly

@@ -483,28 +483,40 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
 
 int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std::string& msg) {
   wp = WeakPeriodic();
-  if (m.nv != 4) {
-    msg = "tetrahedral meshes only";
+  if (m.nv != 4 && m.nv != 3) {
+    msg = "tetrahedral or triangular meshes only";
     return BT_EINVAL;
   }
+  if (m.nv == 3 && (axes & 4u)) {
+    msg = "a 2-D mesh couples the x and y sides only";
+    return BT_EINVAL;
+  }
+  const int nv = m.nv, fs = nv - 1;  // nodes per element, per boundary face
   double Lmax = 0, vsum = 0;
   for (int k = 0; k < 3; ++k) {
     wp.L[k] = m.hi[k] - m.lo[k];
     Lmax = std::max(Lmax, wp.L[k]);
   }
   const double tol = 1e-9 * Lmax;
-  static const int LOC[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  // boundary faces: vertex triples of a tetrahedron, vertex pairs of a triangle
+  static const int LOC4[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  static const int LOC3[3][3] = {{1, 2, -1}, {0, 2, -1}, {0, 1, -1}};
+  auto LOC = [&](int f, int a) { return nv == 4 ? LOC4[f][a] : LOC3[f][a]; };
   auto X = [&](int32_t v, int k) { return m.xyz[3 * (size_t)v + k]; };
   for (int64_t t = 0; t < m.n_tets; ++t) {
-    const int32_t* tv = &m.tets[4 * t];
+    const int32_t* tv = &m.tets[nv * t];
     double e[3][3];
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < fs; ++a)
       for (int k = 0; k < 3; ++k) e[a][k] = X(tv[a + 1], k) - X(tv[0], k);
-    vsum += std::fabs(e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
-                      e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
-                      e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0])) / 6.0;
+    if (nv == 4)
+      vsum += std::fabs(e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                        e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                        e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0])) / 6.0;
+    else
+      vsum += 0.5 * std::fabs(e[0][0] * e[1][1] - e[0][1] * e[1][0]);
   }
-  wp.h = std::cbrt(6.0 * vsum / (double)m.n_tets);
+  // the Kuhn cell edge: (d! x mean element measure)^(1/d)
+  wp.h = nv == 4 ? std::cbrt(6.0 * vsum / (double)m.n_tets) : std::sqrt(2.0 * vsum / (double)m.n_tets);
   wp.B.assign(m.nnz, 0.0);
   auto slot = [&](int32_t r, int32_t c) -> int64_t {
     const int32_t* b = &m.col[m.row_ptr[r]];
@@ -512,6 +524,16 @@ int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std:
     const int32_t* it = std::lower_bound(b, e, c);
     return (it != e && *it == c) ? m.row_ptr[r] + (it - b) : -1;
   };
+  // P1 mass of a face: measure / (fs (fs + 1)) (1 + delta_ab)
+  auto face_measure = [&](const double P[3][3]) {
+    const double u1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+    if (fs == 2) return std::sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    const double u2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+    const double cx = u1[1] * u2[2] - u1[2] * u2[1], cy = u1[2] * u2[0] - u1[0] * u2[2],
+                 cz = u1[0] * u2[1] - u1[1] * u2[0];
+    return 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+  };
+  const double mdiv = (double)(fs * (fs + 1));
   struct Face {
     int64_t t;
     int lf;
@@ -521,14 +543,14 @@ int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std:
     if (!((axes >> k) & 1)) continue;
     std::vector<Face> side[2];
     for (int64_t t = 0; t < m.n_tets; ++t)
-      for (int f = 0; f < 4; ++f)
+      for (int f = 0; f < nv; ++f)
         for (int sd = 0; sd < 2; ++sd) {
           const double plane = sd ? m.hi[k] : m.lo[k];
           bool on = true;
-          for (int a = 0; a < 3; ++a) on &= std::fabs(X(m.tets[4 * t + LOC[f][a]], k) - plane) < tol;
+          for (int a = 0; a < fs; ++a) on &= std::fabs(X(m.tets[nv * t + LOC(f, a)], k) - plane) < tol;
           if (on) side[sd].push_back({t, f});
         }
-    // slave faces by their sorted node triple; slave nodes by coordinates
+    // slave faces by their sorted node ids (-1 pads an edge); slave nodes by coordinates
     std::map<std::array<int32_t, 3>, Face> sface;
     std::map<std::array<int64_t, 3>, int32_t> snode;
     auto qkey = [&](double x, double y, double z) {
@@ -536,41 +558,38 @@ int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std:
                                     (int64_t)std::llround(z / tol)};
     };
     for (const Face& f : side[1]) {
-      std::array<int32_t, 3> tri;
-      for (int a = 0; a < 3; ++a) {
-        tri[a] = m.tets[4 * f.t + LOC[f.lf][a]];
-        snode[qkey(X(tri[a], 0), X(tri[a], 1), X(tri[a], 2))] = tri[a];
+      std::array<int32_t, 3> key = {-1, -1, -1};
+      for (int a = 0; a < fs; ++a) {
+        key[a] = m.tets[nv * f.t + LOC(f.lf, a)];
+        snode[qkey(X(key[a], 0), X(key[a], 1), X(key[a], 2))] = key[a];
       }
-      std::sort(tri.begin(), tri.end());
-      sface[tri] = f;
+      std::sort(key.begin(), key.end());
+      sface[key] = f;
     }
     for (int sd = 0; sd < 2; ++sd)
       for (const Face& f : side[sd]) {
         int32_t v[3], dof[3];
-        double P[3][3];
-        for (int a = 0; a < 3; ++a) {
-          v[a] = m.tets[4 * f.t + LOC[f.lf][a]];
-          dof[a] = m.tet_dof[4 * f.t + LOC[f.lf][a]];
+        double P[3][3] = {};
+        for (int a = 0; a < fs; ++a) {
+          v[a] = m.tets[nv * f.t + LOC(f.lf, a)];
+          dof[a] = m.tet_dof[nv * f.t + LOC(f.lf, a)];
           for (int kk = 0; kk < 3; ++kk) P[a][kk] = X(v[a], kk);
         }
-        const double u1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
-        const double u2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
-        const double cx = u1[1] * u2[2] - u1[2] * u2[1], cy = u1[2] * u2[0] - u1[0] * u2[2],
-                     cz = u1[0] * u2[1] - u1[1] * u2[0];
-        const double area = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) {
+        const double meas = face_measure(P);
+        for (int a = 0; a < fs; ++a)
+          for (int b = 0; b < fs; ++b) {
             const int64_t sl = slot(dof[a], dof[b]);
             if (sl < 0) {
               msg = "boundary face entry outside the pattern";
               return BT_EINVAL;
             }
-            wp.B[sl] += area / 12.0 * (a == b ? 2.0 : 1.0);
+            wp.B[sl] += meas / mdiv * (a == b ? 2.0 : 1.0);
           }
         if (sd == 1) continue;
         // master face: partner nodes at x + L_k e_k and the slave face holding them
         int32_t pv[3];
-        for (int a = 0; a < 3; ++a) {
+        std::array<int32_t, 3> key = {-1, -1, -1};
+        for (int a = 0; a < fs; ++a) {
           double y[3] = {P[a][0], P[a][1], P[a][2]};
           y[k] += wp.L[k];
           auto it = snode.find(qkey(y[0], y[1], y[2]));
@@ -578,23 +597,27 @@ int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std:
             msg = "the mesh does not match across the box on axis " + std::to_string(k);
             return BT_EINVAL;
           }
-          pv[a] = it->second;
+          pv[a] = key[a] = it->second;
         }
-        std::array<int32_t, 3> tri = {pv[0], pv[1], pv[2]};
-        std::sort(tri.begin(), tri.end());
-        auto fit = sface.find(tri);
+        std::sort(key.begin(), key.end());
+        auto fit = sface.find(key);
         if (fit == sface.end()) {
           msg = "the mesh does not match across the box on axis " + std::to_string(k);
           return BT_EINVAL;
         }
         const Face& g = fit->second;
-        int32_t pdof[3];
-        for (int a = 0; a < 3; ++a)
-          for (int c = 0; c < 3; ++c)
-            if (m.tets[4 * g.t + LOC[g.lf][c]] == pv[a]) pdof[a] = m.tet_dof[4 * g.t + LOC[g.lf][c]];
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) {
-            const double wt = area / 12.0 * (a == b ? 2.0 : 1.0);
+        int32_t pdof[3] = {-1, -1, -1};
+        for (int a = 0; a < fs; ++a)
+          for (int c = 0; c < fs; ++c)
+            if (m.tets[nv * g.t + LOC(g.lf, c)] == pv[a]) pdof[a] = m.tet_dof[nv * g.t + LOC(g.lf, c)];
+        for (int a = 0; a < fs; ++a)
+          if (pdof[a] < 0 || pdof[a] >= m.n_dof) {
+            msg = "partner face lookup failed on axis " + std::to_string(k);
+            return BT_EINVAL;
+          }
+        for (int a = 0; a < fs; ++a)
+          for (int b = 0; b < fs; ++b) {
+            const double wt = meas / mdiv * (a == b ? 2.0 : 1.0);
             ent.emplace_back(dof[a], pdof[b], wt, (int8_t)k);           // master row: slave value, +phase
             ent.emplace_back(pdof[a], dof[b], wt, (int8_t)(k | 4));     // slave row: master value, -phase
           }

@@ -407,13 +407,22 @@ def _weak_cells():
     return p
 
 
-@pytest.mark.parametrize("case", ["box", "cells"])
+def _weak_square_disk():
+    d = (1 / math.sqrt(2), 1 / math.sqrt(2), 0.0)
+    p = geom.square_disk(n=12, L=10.0, R=3.0, dt=100.0, kappa=1e-4, bvals=(1000.0, 3000.0), dirs=(d, (1.0, 0, 0)))
+    p.delta, p.Delta, p.TE = 10000.0, 13000.0, 23000.0
+    p.weak_periodic = {"axes": 3, "kappa_e": None}
+    return p
+
+
+@pytest.mark.parametrize("case", ["box", "cells", "square_disk"])
 @pytest.mark.parametrize("mode", ["plain", "mixed", "mixed_host"])
 def test_weak_periodic_matches_oracle(sim_cls, bt, case, mode):
     """Artificial-permeability coupling of the box faces (bt_set_weak_periodic)
-    against the oracle: a free box coupled on all axes, and the sphere case
-    coupled on x and z with a given kappa_e; captured graph and host loop."""
-    p = _weak_box() if case == "box" else _weak_cells()
+    against the oracle: a free box coupled on all axes, the sphere case
+    coupled on x and z with a given kappa_e, and in 2-D a disk in a square
+    coupled through its side edges; captured graph and host loop."""
+    p = {"box": _weak_box, "cells": _weak_cells, "square_disk": _weak_square_disk}[case]()
     ref = oracle.run(p)
     sim = sim_cls(p)
     try:

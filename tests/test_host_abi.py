@@ -231,9 +231,18 @@ def test_triangle_validation_and_refusals(bt):
             bt.bt_upload_mesh_2d(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, 4, p.box_lo, p.box_hi)
         assert e.value.code == bt.BT_EINVAL
         bt.bt_upload_mesh_2d(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, 0, p.box_lo, p.box_hi)
-        with pytest.raises(bt.BtError) as e:                    # weak coupling is built for tetrahedra only
-            bt.bt_set_weak_periodic(ctx, 1, 0.0)
+        bt.bt_set_weak_periodic(ctx, 3, 0.0)                    # boundary edges on the x and y sides
+        with pytest.raises(bt.BtError) as e:                    # no z sides in 2-D
+            bt.bt_set_weak_periodic(ctx, 4, 0.0)
         assert e.value.code == bt.BT_EINVAL
+        xyz = p.xyz.copy()
+        on_hi = np.flatnonzero(np.abs(xyz[:, 0] - p.box_hi[0]) < 1e-9)
+        xyz[on_hi[1], 1] += 0.3 * (xyz[on_hi[2], 1] - xyz[on_hi[1], 1])   # sides no longer match
+        bt.bt_upload_mesh_2d(ctx, xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, 0, p.box_lo, p.box_hi)
+        bt.bt_set_weak_periodic(ctx, 2, 0.0)                    # y sides still match
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_set_weak_periodic(ctx, 1, 0.0)
+        assert e.value.code == bt.BT_EINVAL and "match" in bt.bt_last_error(ctx)
     finally:
         bt.bt_destroy(ctx)
 

@@ -47,3 +47,55 @@ def test_first_order_in_dt():
 def test_approaches_pseudo_periodic_value():
     S = oracle.run(_box(dt=12.5, kappa_e=1.5e-2))[0] / 512.0
     assert abs(S - math.exp(-1000.0 * 2e-3)) < 0.03
+
+
+# ---------------------------------------------------------------- 2-D (boundary edges)
+def _square(dt=50.0, b=1000.0, dirs=((1.0, 0.0, 0.0),), kappa_e=None, n=8):
+    p = geom.free_periodic_square(n=n, L=8.0, dt=dt, bvals=(b,), dirs=dirs)
+    p.periodic_mask = 0
+    p.transformed = False
+    p.weak_periodic = {"axes": 3, "kappa_e": kappa_e}
+    return p
+
+
+def test_square_constant_field_conserved_at_zero_gradient():
+    S, H = oracle.run(_square(b=0.0), return_history=True)
+    assert np.max(np.abs(H[0] - 64.0)) < 1e-11 * 64.0
+
+
+def test_square_reversed_gradient_conjugates_and_first_order():
+    d = (0.6, 0.8, 0.0)
+    a = oracle.run(_square(dirs=(d,), n=4, b=2500.0))[0]
+    b = oracle.run(_square(dirs=(tuple(-x for x in d),), n=4, b=2500.0))[0]
+    assert abs(a - np.conj(b)) < 1e-12 * abs(a)
+    S = [oracle.run(_square(dt=dt, kappa_e=1.5e-2, n=4))[0] for dt in (50.0, 25.0, 12.5)]
+    d1, d2 = abs(S[0] - S[1]), abs(S[1] - S[2])
+    assert 1.6 < d1 / d2 < 2.4
+
+
+def test_square_approaches_pseudo_periodic_value():
+    S = oracle.run(_square(dt=12.5, kappa_e=1.5e-2))[0] / 64.0
+    assert abs(S - math.exp(-1000.0 * 2e-3)) < 0.03
+
+
+def test_square_with_disk_weak_approaches_strong_conditions():
+    """The paper's 2-D comparison of the two routes (Appendix B): a disk in a
+    square, gradient along (1, 1)/sqrt(2), delta 10 ms, Delta 13 ms.  The
+    strong route meshes the square periodically (transformed frame); the weak
+    route couples the sides of the same, non-periodic mesh.  The gap shrinks
+    as dt is halved (the partner term lags one step)."""
+    d = (1 / math.sqrt(2), 1 / math.sqrt(2), 0.0)
+
+    def make(dt, strong):
+        p = geom.square_disk(n=16, L=10.0, R=3.0, dt=dt, kappa=1e-4, bvals=(1000.0,), dirs=(d,))
+        p.delta, p.Delta, p.TE = 10000.0, 13000.0, 23000.0
+        if strong:
+            p.periodic_mask, p.transformed = 3, True
+        else:
+            p.weak_periodic = {"axes": 3, "kappa_e": 1e-2}
+        return p
+    gaps = []
+    for dt in (50.0, 25.0, 12.5):
+        Ss, Sw = oracle.run(make(dt, True))[0], oracle.run(make(dt, False))[0]
+        gaps.append(abs(Sw - Ss) / abs(Ss))
+    assert gaps[0] > gaps[1] > gaps[2] and gaps[2] < 0.08, gaps
