@@ -356,10 +356,16 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_s = time.time() - t0
     sim2.close()
-    h2d = (p.xyz.nbytes + p.tets.nbytes + p.tet_cmpt.nbytes + p.D_cmpt.nbytes + p.kappa_cmpt.nbytes +
-           8 * (nnz + 1) * 2 + 4 * (16 * len(p.tets) + 36 * nf) + 4 * (n + 1) + 4 * nnz +
-           nf * (4 + 3 + 8) + 3 * 8 * p.n_rhs + 8 * p.n_rhs + 48 * p.n_steps)
-    d2h = p.n_rhs * (16 + 8 + 4) + 8 * n
+    # what the library copies to the device: nodes, elements, compartments and
+    # diffusivities; interface faces (element, local vertices, kappa); the
+    # element and face contribution lists with their slot pointers; the
+    # pattern; per run the directions, q and the sequence tables
+    nv = p.tets.shape[1]
+    fs = nv - 1
+    h2d = (p.xyz.nbytes + 4 * nv * len(p.tets) + 4 * len(p.tets) + p.D_cmpt.nbytes + nf * (4 + fs + 8) +
+           8 * (nnz + 1) * 2 + 4 * (nv * nv * len(p.tets) + (2 * fs) ** 2 * nf) + 4 * (n + 1) + 4 * nnz +
+           (3 * 8 + 8) * p.n_rhs * G + 48 * p.n_steps * G)
+    d2h = p.n_rhs * G * (16 + 8 + 4) + 8 * n
     sim.close()
 
     if rank != 0:
