@@ -256,6 +256,8 @@ class Problem:
     # weak pseudo-periodic conditions on a non-periodic box (lab frame):
     # {"axes": bit mask, "kappa_e": um/us or None for max D / h}
     weak_periodic: dict | None = None
+    # triangles of a thin layer embedded in 3-D (a 2-D manifold) instead of a planar 2-D domain
+    surface: bool = False
 
     @property
     def n_cmpt(self):
@@ -469,6 +471,52 @@ def dendrite_tree(seed: int = 0, n_stems: int = 6, depth: int = 5, h: float = 1.
     return Problem("dendrite_tree", xyz, segs, np.zeros(len(segs), np.int32), np.array([D]),
                    np.array([NO_MEMBRANE]), 0, lo, hi, dt, 10600.0, 43100.0, 53700.0, fibonacci_dirs(n_dir),
                    np.asarray(bvals, dtype=np.float64))
+
+
+def icosphere(level: int, R: float = 1.0):
+    """Nodes on the sphere of radius R and triangles of the icosahedron refined
+    `level` times (each triangle cut into four, new nodes pushed to the
+    sphere), outward-oriented."""
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    xyz = [np.array(p, float) / np.linalg.norm(p) for p in v]
+    for _ in range(level):
+        mid = {}
+
+        def midpoint(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                m = xyz[a] + xyz[b]
+                xyz.append(m / np.linalg.norm(m))
+                mid[key] = len(xyz) - 1
+            return mid[key]
+        nf = []
+        for a, b, c in f:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        f = nf
+    return R * np.array(xyz), np.array(f, dtype=np.int32)
+
+
+def spherical_shell(level: int = 4, R: float = 5.0, dt: float = 50.0, D: float = 2e-3, kappa: float | None = None,
+                    cap_z: float = 0.5, bvals=(0.0, 1000.0, 3000.0), dirs=((1.0, 0.0, 0.0), (0.0, 0.0, 1.0))):
+    """Thin layer: the sphere of radius R as a 2-D manifold of triangles.  With
+    kappa given, triangles whose centroid has z > cap_z R form a second
+    compartment, separated from the rest by a permeable membrane along the
+    circle of latitude (a curve on the surface)."""
+    xyz, tris = icosphere(level, R)
+    lab = np.zeros(len(tris), np.int32)
+    D_c, k_c = np.array([D]), np.array([NO_MEMBRANE])
+    if kappa is not None:
+        lab = (xyz[tris].mean(axis=1)[:, 2] > cap_z * R).astype(np.int32)
+        D_c, k_c = np.array([D, D]), np.array([NO_MEMBRANE, kappa])
+    lo, hi = np.full(3, -R), np.full(3, R)
+    return Problem("spherical_shell", xyz, tris, lab, D_c, k_c, 0, lo, hi, dt, 2500.0, 5000.0, 7500.0,
+                   np.asarray(dirs, dtype=np.float64), np.asarray(bvals, dtype=np.float64), surface=True)
 
 
 def union(problems, name="batch"):

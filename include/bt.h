@@ -110,6 +110,21 @@ bt_status bt_upload_mesh_2d(bt_ctx* ctx, int64_t n_nodes, const double* xy, int6
 bt_status bt_upload_mesh_1d(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_segs, const int32_t* seg2,
                             const int32_t* seg_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* box_lo,
                             const double* box_hi);
+/* A thin layer as a 2-D manifold embedded in 3-D (Section 1's "thin-layer
+ * and thin-tube media using a discretization on manifolds"; Section 5): P1
+ * triangles of a surface, thickness taken uniform, so the weak form is
+ * Section 2's with integrals over the surface and tangential gradients.
+ * xyz [3 n_nodes] (um); tri3 [3 n_tris] node ids in any orientation
+ * (zero-area triangles are BT_EINVAL); tri_cmpt [n_tris]; D_cmpt, kappa_cmpt
+ * [n_cmpt] as for bt_upload_mesh: compartments meet along curves on the
+ * surface, membranes there carry the jump term kappa <[u], [v]> per unit
+ * length.  No periodicity; box_lo/box_hi [3] fix the origin of g.x only.
+ * Lab frame only (bt_assemble refuses BT_FRAME_TRANSFORMED: there the
+ * tangential part of q varies over the surface); bt_set_weak_periodic is
+ * refused. */
+bt_status bt_upload_mesh_surface(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_tris,
+                                 const int32_t* tri3, const int32_t* tri_cmpt, int32_t n_cmpt, const double* D_cmpt,
+                                 const double* kappa_cmpt, const double* box_lo, const double* box_hi);
 /* Sizes after bt_upload_mesh.  Any output pointer may be NULL. */
 bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t* n_iface);
 /* dof_node [n_dof] master node of each dof; dof_cmpt [n_dof] its compartment. */

@@ -12,10 +12,11 @@ What it follows (section / equation of arXiv 1908.01719):
   * strong pseudo-periodic conditions through the gauge transform
     u = U exp(i gamma F(t) g.x) (Appendix A, Eqs. trBlo, Periodic,
     Binterface2 and the weak form F(u, v, t));
-  * elements: P1 tetrahedra, P1 triangles for 2-D domains, and P1 segments
-    for 1-D manifolds embedded in 3-D (Section 5, "Realistic neurons": the
-    centre lines of thin tubes, integrals along the curve, tangential
-    gradients, uniform cross-section).
+  * elements: P1 tetrahedra, P1 triangles for 2-D domains, and, for the
+    thin-layer and thin-tube media of the manifold route (Section 1's feature
+    list; Section 5, "Realistic neurons"), P1 triangles of a surface and P1
+    segments of a curve embedded in 3-D: integrals over the manifold,
+    tangential gradients, uniform thickness or cross-section.
 
 Readings where the paper leaves a choice (each is also listed in the design
 notes of the repository):
@@ -138,6 +139,22 @@ def seg_geometry(X):
     return np.sqrt(l2), G
 
 
+def surf_geometry(X):
+    """Areas [nt] and tangential barycentric gradients [nt, 3, 3] of triangles
+    X [nt, 3, 3] anywhere in 3-D (a thin layer as a 2-D manifold).  With the
+    edge matrix E (rows x_1 - x_0, x_2 - x_0), grad lambda_1, grad lambda_2 are
+    the tangent vectors g with E g = e_a, i.e. the columns of the
+    pseudo-inverse E^T (E E^T)^-1; |T| = sqrt(det(E E^T)) / 2."""
+    E = X[:, 1:, :] - X[:, :1, :]                  # [nt, 2, 3]
+    Gram = np.einsum("tak,tbk->tab", E, E)
+    area = 0.5 * np.sqrt(np.linalg.det(Gram))
+    P = np.einsum("tak,tab->tkb", E, np.linalg.inv(Gram))   # [nt, 3, 2] pseudo-inverse
+    G = np.empty((len(X), 3, 3))
+    G[:, 1:, :] = np.transpose(P, (0, 2, 1))
+    G[:, 0, :] = -G[:, 1:, :].sum(axis=1)
+    return area, G
+
+
 def tri_geometry(X):
     """Areas [nt] and barycentric gradients [nt, 3, 3] (z = 0) of triangles in the
     xy plane, X [nt, 3, 3]: grad lambda solves E grad = e_a for the edge matrix."""
@@ -180,15 +197,19 @@ def assemble(p):
     """
     nv = p.tets.shape[1]                           # 4: tetrahedra, 3: triangles, 2: segments
     d = nv - 1
-    if nv == 2 and (p.periodic_mask or p.transformed):
-        raise ValueError("1-D manifolds are solved in the lab frame, without periodicity")
+    manifold = nv == 2 or getattr(p, "surface", False)
+    if manifold and (p.periodic_mask or p.transformed):
+        raise ValueError("manifolds are solved in the lab frame, without periodicity")
     master = periodic_master(p.xyz, p.periodic_mask, p.box_lo, p.box_hi)
     tet_dof, dof_node, dof_cmpt = doubling(master, p.tets, p.tet_cmpt, p.n_cmpt)
     n = len(dof_node)
     if nv == 2 and np.any(dof_node[1:] == dof_node[:-1]):
         raise ValueError("segments of different compartments share a node")
     X = p.xyz[p.tets]                              # unwrapped element coordinates
-    vol, G = {4: tet_geometry, 3: tri_geometry, 2: seg_geometry}[nv](X)
+    if nv == 3 and getattr(p, "surface", False):
+        vol, G = surf_geometry(X)
+    else:
+        vol, G = {4: tet_geometry, 3: tri_geometry, 2: seg_geometry}[nv](X)
     Dt = p.D_cmpt[p.tet_cmpt]
     rows = np.repeat(tet_dof[:, :, None], nv, axis=2)
     cols = np.repeat(tet_dof[:, None, :], nv, axis=1)
@@ -466,7 +487,8 @@ def _result(out, hist, fields, return_history, return_field):
 
 
 def run(p, asm=None, rhs=None, return_history=False, route=None, return_field=False):
-    if p.tets.shape[1] == 3 and np.any(np.abs(np.asarray(p.dirs, float)[:, 2]) > 1e-12):
+    if p.tets.shape[1] == 3 and not getattr(p, "surface", False) and \
+            np.any(np.abs(np.asarray(p.dirs, float)[:, 2]) > 1e-12):
         raise ValueError("2-D meshes need gradient directions in the xy plane")
     f = run_transformed if (p.transformed or p.periodic_mask) else run_lab
     return f(p, asm, rhs, return_history, route, return_field)

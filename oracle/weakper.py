@@ -41,6 +41,8 @@ def box_faces(p, axes):
     vertex indices of the face, axis, side) with side 0 = lo (master), 1 = hi
     (slave)."""
     nv = p.tets.shape[1]
+    if getattr(p, "surface", False):
+        raise ValueError("a surface has no box sides to couple")
     if nv not in _LOC or (nv == 3 and axes & 4):
         raise ValueError("weak periodic faces need tetrahedra, or triangles coupled along x and y")
     loc = _LOC[nv]

@@ -31,7 +31,7 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
            "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation", "bt_set_diffusion_tensor", "bt_set_weak_periodic", "bt_upload_mesh_2d",
-           "bt_upload_mesh_1d"]
+           "bt_upload_mesh_1d", "bt_upload_mesh_surface"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -71,6 +71,7 @@ def lib():
             "bt_upload_mesh": [P, I64, P, I64, P, P, I32, P, P, U32, P, P],
             "bt_upload_mesh_2d": [P, I64, P, I64, P, P, I32, P, P, U32, P, P],
             "bt_upload_mesh_1d": [P, I64, P, I64, P, P, I32, P, P, P],
+            "bt_upload_mesh_surface": [P, I64, P, I64, P, P, I32, P, P, P, P],
             "bt_get_sizes": [P, P, P, P],
             "bt_get_dofmap": [P, P, P],
             "bt_get_pattern": [P, P, P],
@@ -174,6 +175,19 @@ def bt_upload_mesh_1d(ctx, xyz, segs, seg_cmpt, D_cmpt, box_lo, box_hi):
     hi = np.ascontiguousarray(box_hi, dtype=np.float64)
     _check(ctx, lib().bt_upload_mesh_1d(ctx, len(xyz), _ptr(xyz), len(segs), _ptr(segs), _ptr(sc), len(D), _ptr(D),
                                         _ptr(lo), _ptr(hi)))
+
+
+def bt_upload_mesh_surface(ctx, xyz, tris, tri_cmpt, D_cmpt, kappa_cmpt, box_lo, box_hi):
+    """Thin layer: P1 triangles of a surface embedded in 3-D."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    tc = np.ascontiguousarray(tri_cmpt, dtype=np.int32)
+    D = np.ascontiguousarray(D_cmpt, dtype=np.float64)
+    K = np.ascontiguousarray(kappa_cmpt, dtype=np.float64)
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(box_hi, dtype=np.float64)
+    _check(ctx, lib().bt_upload_mesh_surface(ctx, len(xyz), _ptr(xyz), len(tris), _ptr(tris), _ptr(tc), len(D),
+                                             _ptr(D), _ptr(K), _ptr(lo), _ptr(hi)))
 
 
 def bt_get_sizes(ctx):

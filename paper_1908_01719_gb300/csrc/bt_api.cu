@@ -107,7 +107,7 @@ const char* bt_last_error(const bt_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 static bt_status upload_mesh_nv(bt_ctx* ctx, int nv, int64_t n_nodes, const double* xyz, int64_t n_tets,
                                 const int32_t* tet4, const int32_t* tet_cmpt, int32_t n_cmpt, const double* D_cmpt,
                                 const double* kappa_cmpt, uint32_t periodic_mask, const double* box_lo,
-                                const double* box_hi) {
+                                const double* box_hi, bool surface = false) {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!xyz || !tet4 || !tet_cmpt || !D_cmpt || !kappa_cmpt || !box_lo || !box_hi || n_nodes <= 0 || n_tets <= 0 ||
@@ -118,6 +118,7 @@ static bt_status upload_mesh_nv(bt_ctx* ctx, int nv, int64_t n_nodes, const doub
   ctx->have_mesh = ctx->assembled = ctx->have_seq = false;
   try {
     m.nv = nv;
+    m.surface = surface;
     m.n_nodes = n_nodes;
     m.n_tets = n_tets;
     m.n_cmpt = n_cmpt;
@@ -202,6 +203,14 @@ bt_status bt_upload_mesh_1d(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int
   const std::vector<double> no_kappa((size_t)n_cmpt, 0.0);
   return upload_mesh_nv(ctx, 2, n_nodes, xyz, n_segs, seg2, seg_cmpt, n_cmpt, D_cmpt, no_kappa.data(), 0, box_lo,
                         box_hi);
+}
+
+bt_status bt_upload_mesh_surface(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_tris,
+                                 const int32_t* tri3, const int32_t* tri_cmpt, int32_t n_cmpt, const double* D_cmpt,
+                                 const double* kappa_cmpt, const double* box_lo, const double* box_hi) {
+  if (!ctx) return BT_EINVAL;
+  return upload_mesh_nv(ctx, 3, n_nodes, xyz, n_tris, tri3, tri_cmpt, n_cmpt, D_cmpt, kappa_cmpt, 0, box_lo, box_hi,
+                        true);
 }
 
 bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t* n_iface) {
@@ -328,8 +337,8 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
     return fail(ctx, BT_EINVAL, "bt_assemble: need dt > 0, 0 < theta <= 1, flags in {LAB, TRANSFORMED}");
   if (ctx->mesh.pmask && flags != BT_FRAME_TRANSFORMED)
     return fail(ctx, BT_EINVAL, "bt_assemble: periodic boxes need BT_FRAME_TRANSFORMED");
-  if (ctx->mesh.nv == 2 && flags != BT_FRAME_LAB)
-    return fail(ctx, BT_EINVAL, "bt_assemble: 1-D manifolds need the lab frame");
+  if ((ctx->mesh.nv == 2 || ctx->mesh.surface) && flags != BT_FRAME_LAB)
+    return fail(ctx, BT_EINVAL, "bt_assemble: manifold meshes need the lab frame");
   if (!ctx->cm_Dten.empty() && flags == BT_FRAME_TRANSFORMED)
     return fail(ctx, BT_EINVAL, "bt_assemble: diffusion tensors need the lab frame");
   if (ctx->weak_axes && flags == BT_FRAME_TRANSFORMED)
@@ -371,6 +380,7 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   for (int k = 0; k < 3; ++k) a.centre[k] = 0.5 * (m.lo[k] + m.hi[k]);
   a.nt = m.n_tets;
   a.nv = m.nv;
+  a.surface = m.surface ? 1 : 0;
   a.nf = m.n_face;
   a.nnz = nnz;
   a.face_ta = ctx->d_face_ta.p;
@@ -542,7 +552,7 @@ bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32
       double nx = dirs[3 * i], ny = dirs[3 * i + 1], nz = dirs[3 * i + 2];
       double nr = std::sqrt(nx * nx + ny * ny + nz * nz);
       if (!(nr > 0) || !std::isfinite(nr)) return fail(ctx, BT_EINVAL, "bt_set_gradients: zero direction");
-      if (ctx->mesh.nv == 3 && std::fabs(nz) > 1e-12 * nr)
+      if (ctx->mesh.nv == 3 && !ctx->mesh.surface && std::fabs(nz) > 1e-12 * nr)
         return fail(ctx, BT_EINVAL, "bt_set_gradients: 2-D meshes need directions in the xy plane");
       for (int j = 0; j < n_b; ++j) {
         if (!(bvals[j] >= 0) || !std::isfinite(bvals[j])) return fail(ctx, BT_EINVAL, "bt_set_gradients: b < 0");

@@ -14,9 +14,10 @@ namespace bt {
 // ---------------------------------------------------------------- host mesh
 struct HostMesh {
   // input (copied)
-  int64_t n_nodes = 0, n_tets = 0;   // elements: tetrahedra (nv = 4) or triangles (nv = 3)
+  int64_t n_nodes = 0, n_tets = 0;   // elements: tetrahedra (nv = 4), triangles (3) or segments (2)
   int32_t n_cmpt = 0;
   int nv = 4;                          // nodes per element; faces have nv - 1 nodes
+  bool surface = false;                // triangles of a surface in 3-D, not of the xy plane
   std::vector<double> xyz;          // 3 n_nodes
   std::vector<int32_t> tets;        // nv n_tets
   std::vector<int32_t> tet_cmpt;    // n_tets

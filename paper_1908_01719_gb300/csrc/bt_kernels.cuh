@@ -20,7 +20,8 @@ struct AsmArgs {
   const double* Dten;    // [n_cmpt][6] diffusion tensors (or null: isotropic Dc)
   double centre[3];
   int64_t nt, nf, nnz;
-  int nv;  // 4 tetrahedra, 3 triangles
+  int nv;       // 4 tetrahedra, 3 triangles, 2 segments
+  int surface;  // triangles of a surface in 3-D (else in the xy plane)
   const int32_t* face_ta;
   const int8_t* face_lv;
   const double* face_kappa;

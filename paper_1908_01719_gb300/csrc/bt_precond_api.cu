@@ -88,13 +88,18 @@ void compute_geom_features(bt_ctx* ctx) {
     return;
   }
   if (m.nv == 3) {
-    // 2-D: areas, interface edge lengths, h = (2 x mean triangle area)^(1/2)
+    // 2-D or surface: areas, interface edge lengths, h = (2 x mean triangle area)^(1/2)
     for (int64_t t = 0; t < m.n_tets; ++t) {
       const int32_t* v = &m.tets[3 * t];
       const double* a = &m.xyz[3 * v[0]];
       const double* b = &m.xyz[3 * v[1]];
       const double* c = &m.xyz[3 * v[2]];
-      const double A = 0.5 * ((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]));
+      double A = 0.5 * ((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]));
+      if (m.surface) {
+        const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        const double n0 = u[1] * w[2] - u[2] * w[1], n1 = u[2] * w[0] - u[0] * w[2], n2 = u[0] * w[1] - u[1] * w[0];
+        A = 0.5 * std::sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+      }
       vol += A;
       dv += A * m.D[m.tet_cmpt[t]];
     }
@@ -103,7 +108,8 @@ void compute_geom_features(bt_ctx* ctx) {
       const int32_t t = m.face_ta[f];
       const double* a = &m.xyz[3 * m.tets[3 * t + m.face_lv[2 * f]]];
       const double* b = &m.xyz[3 * m.tets[3 * t + m.face_lv[2 * f + 1]]];
-      const double l = std::sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]));
+      const double l =
+          std::sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) + (b[2] - a[2]) * (b[2] - a[2]));
       len += l;
       kl += l * m.face_kappa[f];
     }

@@ -69,6 +69,10 @@ int validate(const HostMesh& m, std::string& msg) {
     msg = "a 1-D manifold mesh has no periodic axes";
     return BT_EINVAL;
   }
+  if (m.surface && (m.nv != 3 || m.pmask)) {
+    msg = "a surface mesh has triangles and no periodic axes";
+    return BT_EINVAL;
+  }
   if (m.n_nodes >= (int64_t(1) << 31) || m.n_tets * 16 >= (int64_t(1) << 31)) {
     msg = "mesh too large for 32-bit element indexing";
     return BT_EINVAL;
@@ -94,6 +98,7 @@ int validate(const HostMesh& m, std::string& msg) {
       return BT_EINVAL;
     }
   const char* what = m.nv == 4 ? "tetrahedron " : m.nv == 3 ? "triangle " : "segment ";
+  if (m.surface) what = "surface triangle ";
   for (int64_t t = 0; t < m.n_tets; ++t) {
     const int32_t* v = &m.tets[m.nv * t];
     for (int a = 0; a < m.nv; ++a)
@@ -108,6 +113,13 @@ int validate(const HostMesh& m, std::string& msg) {
     double vol;
     if (m.nv == 4) {
       vol = signed_volume(&m.xyz[3 * v[0]], &m.xyz[3 * v[1]], &m.xyz[3 * v[2]], &m.xyz[3 * v[3]]);
+    } else if (m.surface) {  // area of a triangle in 3-D (no orientation)
+      const double* a = &m.xyz[3 * v[0]];
+      const double* b = &m.xyz[3 * v[1]];
+      const double* c = &m.xyz[3 * v[2]];
+      const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      const double n0 = u[1] * w[2] - u[2] * w[1], n1 = u[2] * w[0] - u[0] * w[2], n2 = u[0] * w[1] - u[1] * w[0];
+      vol = 0.5 * std::sqrt(n0 * n0 + n1 * n1 + n2 * n2);
     } else if (m.nv == 2) {  // length of a segment (no orientation)
       const double* a = &m.xyz[3 * v[0]];
       const double* b = &m.xyz[3 * v[1]];
@@ -489,6 +501,10 @@ int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std:
   }
   if (m.nv == 3 && (axes & 4u)) {
     msg = "a 2-D mesh couples the x and y sides only";
+    return BT_EINVAL;
+  }
+  if (m.surface) {
+    msg = "a surface has no box sides to couple";
     return BT_EINVAL;
   }
   const int nv = m.nv, fs = nv - 1;  // nodes per element, per boundary face

@@ -113,6 +113,49 @@ __global__ void k_tri_geom(const double* __restrict__ xyz, const int32_t* __rest
   for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
 }
 
+// The record for a triangle of a surface embedded in 3-D (a thin layer): area,
+// the tangential gradients grad lambda_a = n x (x_{a+2} - x_{a+1}) / |n|^2 with
+// n = (x_1 - x_0) x (x_2 - x_0) (indices mod 3; for a counter-clockwise
+// triangle of the xy plane this is the planar formula), the vertices relative
+// to the box centre; the fourth vertex slots are zero.
+__global__ void k_stri_geom(const double* __restrict__ xyz, const int32_t* __restrict__ tris,
+                            const int32_t* __restrict__ cmpt, const double* __restrict__ Dc,
+                            const double* __restrict__ invT2c, const double* __restrict__ Dten, double cx,
+                            double cy, double cz, int64_t nt, double* __restrict__ out) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double X[3][3];
+  for (int a = 0; a < 3; ++a) {
+    int64_t v = tris[3 * t + a];
+    for (int k = 0; k < 3; ++k) X[a][k] = xyz[3 * v + k];
+  }
+  double u[3], w[3];
+  for (int k = 0; k < 3; ++k) {
+    u[k] = X[1][k] - X[0][k];
+    w[k] = X[2][k] - X[0][k];
+  }
+  const double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+  const double n2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  double* o = out + TG * t;
+  for (int k = 0; k < TG; ++k) o[k] = 0.0;
+  o[0] = 0.5 * sqrt(n2);
+  for (int a = 0; a < 3; ++a) {
+    const double* p = X[(a + 1) % 3];
+    const double* q = X[(a + 2) % 3];
+    const double e[3] = {q[0] - p[0], q[1] - p[1], q[2] - p[2]};
+    o[1 + 3 * a + 0] = (n[1] * e[2] - n[2] * e[1]) / n2;
+    o[1 + 3 * a + 1] = (n[2] * e[0] - n[0] * e[2]) / n2;
+    o[1 + 3 * a + 2] = (n[0] * e[1] - n[1] * e[0]) / n2;
+  }
+  const double c[3] = {cx, cy, cz};
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) o[13 + 3 * a + k] = X[a][k] - c[k];
+  const int cm = cmpt[t];
+  o[25] = Dc[cm];
+  o[26] = invT2c ? invT2c[cm] : 0.0;
+  for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
+}
+
 // The record for a segment of a 1-D manifold embedded in 3-D: length, the
 // tangential gradients -+ e / |e|^2 of the two barycentric coordinates, the
 // vertices relative to the box centre; the other vertex slots are zero.
@@ -323,7 +366,10 @@ void launch_assembly(const AsmArgs& a, cudaStream_t st) {
   if (a.nt && a.nv == 2)
     k_seg_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
                                                                a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
-  if (a.nt && a.nv == 3)
+  if (a.nt && a.nv == 3 && a.surface)
+    k_stri_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
+                                                               a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
+  if (a.nt && a.nv == 3 && !a.surface)
     k_tri_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
                                                               a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
   if (a.nf) k_face_coef<<<(unsigned)((a.nf + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.face_ta, a.face_lv,

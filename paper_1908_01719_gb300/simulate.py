@@ -23,6 +23,9 @@ class Simulation:
             bt.bt_set_stream(self.ctx, stream)
         if geom.tets.shape[1] == 2:
             bt.bt_upload_mesh_1d(self.ctx, geom.xyz, geom.tets, geom.tet_cmpt, geom.D_cmpt, geom.box_lo, geom.box_hi)
+        elif getattr(geom, "surface", False):
+            bt.bt_upload_mesh_surface(self.ctx, geom.xyz, geom.tets, geom.tet_cmpt, geom.D_cmpt, geom.kappa_cmpt,
+                                      geom.box_lo, geom.box_hi)
         else:
             upload = bt.bt_upload_mesh_2d if geom.tets.shape[1] == 3 else bt.bt_upload_mesh
             upload(self.ctx, geom.xyz, geom.tets, geom.tet_cmpt, geom.D_cmpt, geom.kappa_cmpt,

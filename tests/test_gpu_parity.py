@@ -567,3 +567,57 @@ def test_manifold_transformed_frame_refused(bt):
         bt.bt_assemble(ctx, 50.0, 0.5, bt.BT_FRAME_LAB)
     finally:
         bt.bt_destroy(ctx)
+
+
+# ---------------------------------------------------------------- thin layers (surfaces in 3-D)
+def _shell():
+    return geom.spherical_shell(level=3, R=5.0, kappa=1e-4, cap_z=0.3, bvals=(0.0, 1000.0, 3000.0),
+                                dirs=((1.0, 0.0, 0.0), (0.3, -0.5, 0.8)))
+
+
+def test_surface_planes_match_oracle(sim_cls, bt):
+    p = _shell()
+    a = bo.assemble(p)
+    sim = sim_cls(p)
+    try:
+        rp, col = bt.bt_get_pattern(sim.ctx)
+        for nm in ["M", "K", "J", "MD", "Mx", "My", "Mz", "Ex", "Ey", "Ez"]:
+            v = bt.bt_get_plane(sim.ctx, nm)
+            ref = a[nm].tocsr()
+            dense = np.zeros_like(v)
+            for i in range(len(rp) - 1):
+                m = dict(zip(ref.getrow(i).indices, ref.getrow(i).data))
+                dense[rp[i]:rp[i + 1]] = [m.get(c, 0.0) for c in col[rp[i]:rp[i + 1]]]
+            scale = max(np.abs(dense).max(), 1e-300)
+            assert np.abs(v - dense).max() <= 1e-13 * scale, nm
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_surface_signals_match_oracle(sim_cls, bt, mode):
+    """Sphere with a permeable cap, two 3-D directions and three b-values."""
+    p = _shell()
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S, err, stat, st = sim.run(m)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()
+
+
+def test_surface_transformed_frame_refused(bt):
+    p = geom.spherical_shell(level=1)
+    ctx = bt.bt_create(0)
+    try:
+        bt.bt_upload_mesh_surface(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, p.box_lo, p.box_hi)
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_assemble(ctx, 50.0, 0.5, bt.BT_FRAME_TRANSFORMED)
+        assert e.value.code == bt.BT_EINVAL
+        bt.bt_assemble(ctx, 50.0, 0.5, bt.BT_FRAME_LAB)
+    finally:
+        bt.bt_destroy(ctx)

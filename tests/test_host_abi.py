@@ -290,3 +290,32 @@ def test_manifold_validation_errors(bt, defect):
         assert e.value.code == bt.BT_EINVAL
     finally:
         bt.bt_destroy(ctx)
+
+
+def test_surface_dofmap_and_pattern_match_oracle(bt):
+    """Thin layer: a sphere with a permeable cap, membrane along a latitude."""
+    p = geom.spherical_shell(level=3, R=5.0, kappa=1e-4, cap_z=0.3)
+    a = bo.assemble(p)
+    ctx = bt.bt_create(-1)
+    try:
+        bt.bt_upload_mesh_surface(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, p.box_lo, p.box_hi)
+        n, nnz, nf = bt.bt_get_sizes(ctx)
+        assert n == a["n"] and nf == a["n_iface"] > 0
+        dn, dc = bt.bt_get_dofmap(ctx)
+        assert np.array_equal(dn, a["dof_node"]) and np.array_equal(dc, a["dof_cmpt"])
+        rp, col = bt.bt_get_pattern(ctx)
+        orp, ocol = _oracle_pattern(a)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_set_weak_periodic(ctx, 1, 0.0)
+        assert e.value.code == bt.BT_EINVAL
+        # any orientation is accepted; a zero-area triangle is not
+        tris = p.tets.copy()
+        tris[::2] = tris[::2, ::-1]
+        bt.bt_upload_mesh_surface(ctx, p.xyz, tris, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, p.box_lo, p.box_hi)
+        tris[5, 2] = tris[5, 1]
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_upload_mesh_surface(ctx, p.xyz, tris, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, p.box_lo, p.box_hi)
+        assert e.value.code == bt.BT_EINVAL
+    finally:
+        bt.bt_destroy(ctx)
