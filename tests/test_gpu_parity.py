@@ -226,6 +226,37 @@ def test_free_periodic_exact_closed_form_gpu(sim_cls, bt):
         sim.close()
 
 
+# ---------------------------------------------------------------- the benchmarked workload at full size
+def test_cfg4_full_size_properties(sim_cls, bt):
+    """cfg4 at full size (96^3 Kuhn grid, 1.07 M dofs, 32 directions x 4
+    b-values), run as bench.py runs it (mixed mode, autotuned variants,
+    captured step graph): sampled RHS against the plain FP64 GPU path (itself
+    parity-tested against the oracle above), and, on the same geometry, the
+    b = 0 signal equal to the box volume at every direction (conservation,
+    exact at any size)."""
+    p = geom.cfg4()
+    sim = sim_cls(p)
+    try:
+        S, err, stat, _ = sim.run(bt.BT_MODE_MIXED)
+        assert np.all(stat == 0)
+        for r in (0, p.n_rhs - 1):
+            S64, _, st64, _ = sim.run(bt.BT_MODE_PLAIN_FP64, rhs_begin=r, rhs_end=r + 1)
+            assert st64[r] == 0
+            assert rel(S[r], S64[r]) < TOL_MIXED, (r, S[r], S64[r])
+    finally:
+        sim.close()
+    q = geom.cfg4(n_dir=2, bvals=(0.0, 3000.0))
+    sim = sim_cls(q)
+    try:
+        S, err, stat, _ = sim.run(bt.BT_MODE_MIXED)
+        assert np.all(stat == 0)
+        vol = float(np.prod(np.asarray(q.box_hi) - np.asarray(q.box_lo)))
+        assert np.max(np.abs(S[::2] - vol)) < 1e-9 * vol, S[::2]
+        assert np.all(np.abs(S[1::2]) < vol)
+    finally:
+        sim.close()
+
+
 # ---------------------------------------------------------------- stored oracle signals (full sizes)
 def _golden(name):
     path = os.path.join(GOLDEN, name + ".json")
