@@ -515,8 +515,9 @@ def spherical_shell(level: int = 4, R: float = 5.0, dt: float = 50.0, D: float =
         lab = (xyz[tris].mean(axis=1)[:, 2] > cap_z * R).astype(np.int32)
         D_c, k_c = np.array([D, D]), np.array([NO_MEMBRANE, kappa])
     lo, hi = np.full(3, -R), np.full(3, R)
+    d = np.asarray(dirs, dtype=np.float64)
     return Problem("spherical_shell", xyz, tris, lab, D_c, k_c, 0, lo, hi, dt, 2500.0, 5000.0, 7500.0,
-                   np.asarray(dirs, dtype=np.float64), np.asarray(bvals, dtype=np.float64), surface=True)
+                   d / np.linalg.norm(d, axis=1, keepdims=True), np.asarray(bvals, dtype=np.float64), surface=True)
 
 
 def union(problems, name="batch"):
