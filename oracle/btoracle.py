@@ -487,6 +487,9 @@ def _result(out, hist, fields, return_history, return_field):
 
 
 def run(p, asm=None, rhs=None, return_history=False, route=None, return_field=False):
+    dn = np.linalg.norm(np.asarray(p.dirs, float), axis=1)
+    if np.any(np.abs(dn - 1.0) > 1e-12):
+        raise ValueError("gradient directions must be unit vectors (q = gamma |g| carries the magnitude)")
     if p.tets.shape[1] == 3 and not getattr(p, "surface", False) and \
             np.any(np.abs(np.asarray(p.dirs, float)[:, 2]) > 1e-12):
         raise ValueError("2-D meshes need gradient directions in the xy plane")
