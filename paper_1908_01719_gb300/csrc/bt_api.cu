@@ -113,6 +113,9 @@ static bt_status upload_mesh_nv(bt_ctx* ctx, int nv, int64_t n_nodes, const doub
   if (!xyz || !tet4 || !tet_cmpt || !D_cmpt || !kappa_cmpt || !box_lo || !box_hi || n_nodes <= 0 || n_tets <= 0 ||
       n_cmpt <= 0 || periodic_mask > 7)
     return fail(ctx, BT_EINVAL, "bt_upload_mesh: invalid argument");
+  // the 32-bit index limits, checked before any caller array is read
+  if (n_nodes >= (int64_t(1) << 31) || n_tets * 16 >= (int64_t(1) << 31))
+    return fail(ctx, BT_EINVAL, "bt_upload_mesh: mesh too large for 32-bit element indexing");
   HostMesh& m = ctx->mesh;
   m = HostMesh();
   ctx->have_mesh = ctx->assembled = ctx->have_seq = false;
@@ -172,16 +175,16 @@ static bt_status upload_mesh_nv(bt_ctx* ctx, int nv, int64_t n_nodes, const doub
 
 bt_status bt_upload_mesh(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_tets, const int32_t* tet4,
                          const int32_t* tet_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* kappa_cmpt,
-                         uint32_t periodic_mask, const double* box_lo, const double* box_hi) {
+                         uint32_t periodic_mask, const double* box_lo, const double* box_hi) try {
   return upload_mesh_nv(ctx, 4, n_nodes, xyz, n_tets, tet4, tet_cmpt, n_cmpt, D_cmpt, kappa_cmpt, periodic_mask,
                         box_lo, box_hi);
-}
+} BT_ABI_CATCH(ctx)
 
 bt_status bt_upload_mesh_2d(bt_ctx* ctx, int64_t n_nodes, const double* xy, int64_t n_tris, const int32_t* tri3,
                             const int32_t* tri_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* kappa_cmpt,
-                            uint32_t periodic_mask, const double* box_lo, const double* box_hi) {
+                            uint32_t periodic_mask, const double* box_lo, const double* box_hi) try {
   if (!ctx) return BT_EINVAL;
-  if (!xy || !box_lo || !box_hi || n_nodes <= 0 || periodic_mask > 3)
+  if (!xy || !box_lo || !box_hi || n_nodes <= 0 || n_nodes >= (int64_t(1) << 31) || periodic_mask > 3)
     return fail(ctx, BT_EINVAL, "bt_upload_mesh_2d: invalid argument");
   // the plane z = 0 inside a box centred on it, so z moments vanish
   std::vector<double> xyz(3 * (size_t)n_nodes, 0.0);
@@ -192,26 +195,26 @@ bt_status bt_upload_mesh_2d(bt_ctx* ctx, int64_t n_nodes, const double* xy, int6
   const double lo[3] = {box_lo[0], box_lo[1], -1.0}, hi[3] = {box_hi[0], box_hi[1], 1.0};
   return upload_mesh_nv(ctx, 3, n_nodes, xyz.data(), n_tris, tri3, tri_cmpt, n_cmpt, D_cmpt, kappa_cmpt,
                         periodic_mask, lo, hi);
-}
+} BT_ABI_CATCH(ctx)
 
 bt_status bt_upload_mesh_1d(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_segs, const int32_t* seg2,
                             const int32_t* seg_cmpt, int32_t n_cmpt, const double* D_cmpt, const double* box_lo,
-                            const double* box_hi) {
+                            const double* box_hi) try {
   if (!ctx) return BT_EINVAL;
   if (n_cmpt <= 0 || n_cmpt > (1 << 20)) return fail(ctx, BT_EINVAL, "bt_upload_mesh_1d: invalid argument");
   // no membranes on a manifold: the permeabilities are never used
   const std::vector<double> no_kappa((size_t)n_cmpt, 0.0);
   return upload_mesh_nv(ctx, 2, n_nodes, xyz, n_segs, seg2, seg_cmpt, n_cmpt, D_cmpt, no_kappa.data(), 0, box_lo,
                         box_hi);
-}
+} BT_ABI_CATCH(ctx)
 
 bt_status bt_upload_mesh_surface(bt_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_tris,
                                  const int32_t* tri3, const int32_t* tri_cmpt, int32_t n_cmpt, const double* D_cmpt,
-                                 const double* kappa_cmpt, const double* box_lo, const double* box_hi) {
+                                 const double* kappa_cmpt, const double* box_lo, const double* box_hi) try {
   if (!ctx) return BT_EINVAL;
   return upload_mesh_nv(ctx, 3, n_nodes, xyz, n_tris, tri3, tri_cmpt, n_cmpt, D_cmpt, kappa_cmpt, 0, box_lo, box_hi,
                         true);
-}
+} BT_ABI_CATCH(ctx)
 
 bt_status bt_get_sizes(const bt_ctx* ctx, int64_t* n_dof, int64_t* nnz, int64_t* n_iface) {
   if (!ctx || !ctx->have_mesh) return BT_ESTATE;
@@ -237,7 +240,7 @@ bt_status bt_get_pattern(const bt_ctx* ctx, int64_t* row_ptr, int32_t* col) {
 
 bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t* n_halo, int32_t* r0,
                             int32_t* rows, int32_t* rowe, uint16_t* rowl, int32_t* u0, uint32_t* ucol,
-                            uint16_t* lidx) {
+                            uint16_t* lidx) try {
   if (!ctx) return BT_EINVAL;
   if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_get_halo_tiles: no mesh");
   if (umax < 16 || umax > 65535) return fail(ctx, BT_EINVAL, "bt_get_halo_tiles: umax outside [16, 65535]");
@@ -257,9 +260,9 @@ bt_status bt_get_halo_tiles(bt_ctx* ctx, int32_t umax, int64_t* n_tiles, int64_t
   put(ucol, t.ucol);
   put(lidx, t.lidx);
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
-bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho) {
+bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_set_relaxation: no mesh");
@@ -278,9 +281,9 @@ bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho
   // the relaxation enters the assembled operator: assemble again
   ctx->assembled = ctx->have_seq = false;
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
-bt_status bt_set_weak_periodic(bt_ctx* ctx, uint32_t axes, double kappa_e) {
+bt_status bt_set_weak_periodic(bt_ctx* ctx, uint32_t axes, double kappa_e) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_set_weak_periodic: no mesh");
@@ -299,9 +302,9 @@ bt_status bt_set_weak_periodic(bt_ctx* ctx, uint32_t axes, double kappa_e) {
   ctx->weak_kappa_in = kappa_e;
   ctx->assembled = ctx->have_seq = false;
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
-bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6) {
+bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_set_diffusion_tensor: no mesh");
@@ -326,9 +329,9 @@ bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6) {
   }
   ctx->assembled = ctx->have_seq = false;
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
-bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
+bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_assemble: no mesh");
@@ -448,9 +451,9 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) {
   ctx->assembled = true;
   ctx->have_seq = false;
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
-bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals) {
+bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals) try {
   if (!ctx || !vals || which < 0 || which >= BT_N_PLANES) return fail(ctx, BT_EINVAL, "bt_get_plane: bad argument");
   if (!need_gpu(ctx)) return fail(ctx, BT_ENODEV, "bt_get_plane: host-only context");
   if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_get_plane: not assembled");
@@ -460,9 +463,9 @@ bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals) {
   CK(cudaMemcpyAsync(vals, src, ctx->mesh.nnz * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
-bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta, double Delta, double TE) {
+bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta, double Delta, double TE) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_set_sequence: assemble first (dt is needed)");
@@ -501,9 +504,9 @@ bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta, double Delta, dou
   ctx->have_seq = true;
   ctx->R = 0;
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
-bt_status bt_set_profile(bt_ctx* ctx, int32_t n_steps, const double* F, double int_F2) {
+bt_status bt_set_profile(bt_ctx* ctx, int32_t n_steps, const double* F, double int_F2) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_set_profile: assemble first (dt is needed)");
@@ -536,9 +539,9 @@ bt_status bt_set_profile(bt_ctx* ctx, int32_t n_steps, const double* F, double i
   ctx->have_seq = true;
   ctx->R = 0;
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
-bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32_t n_b, const double* bvals) {
+bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32_t n_b, const double* bvals) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!ctx->have_seq) return fail(ctx, BT_ESTATE, "bt_set_gradients: set the sequence first");
@@ -573,13 +576,13 @@ bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32
   ctx->err_est.assign((size_t)G * R, 0.0);
   ctx->status.assign((size_t)G * R, BT_OK);
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
 // Several geometries in one context: segment g = nodes [node_off[g],
 // node_off[g+1]) with its own PGSE timing; the time loop runs to the largest
 // TE and freezes each segment after its own last step.
 bt_status bt_set_segments(bt_ctx* ctx, int32_t G, const int64_t* node_off, const double* delta,
-                          const double* Delta, const double* TE) {
+                          const double* Delta, const double* TE) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
   if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_set_segments: assemble first");
@@ -643,7 +646,7 @@ bt_status bt_set_segments(bt_ctx* ctx, int32_t G, const int64_t* node_off, const
   ctx->have_seq = true;
   ctx->R = 0;
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
 bt_status bt_default_opts(bt_solver_opts* o) {
   if (!o) return BT_EINVAL;
@@ -1478,12 +1481,12 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   return ret;
 }
 
-extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts) {
+extern "C" bt_status bt_run(bt_ctx* ctx, int mode, const bt_solver_opts* opts) try {
   return run_impl(ctx, mode, opts, nullptr);
-}
+} BT_ABI_CATCH(ctx)
 
 extern "C" bt_status bt_collect_precond_data(bt_ctx* ctx, const bt_solver_opts* opts, int32_t n_steps,
-                                             const int32_t* steps, float* feat, double* G, double* h) {
+                                             const int32_t* steps, float* feat, double* G, double* h) try {
   if (!ctx || n_steps < 1 || !steps || !feat || !G || !h) return fail(ctx, BT_EINVAL, "bt_collect_precond_data: bad arguments");
   if (!ctx->have_seq) return fail(ctx, BT_ESTATE, "bt_collect_precond_data: set sequence and gradients first");
   CollectSpec c;
@@ -1499,9 +1502,9 @@ extern "C" bt_status bt_collect_precond_data(bt_ctx* ctx, const bt_solver_opts* 
   c.G = G;
   c.h = h;
   return run_impl(ctx, BT_MODE_MIXED, &o, &c);
-}
+} BT_ABI_CATCH(ctx)
 
-extern "C" bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t* status) {
+extern "C" bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t* status) try {
   if (!ctx) return BT_EINVAL;
   if (ctx->R == 0) return fail(ctx, BT_ESTATE, "bt_get_signals: nothing run");
   const size_t SYt = (size_t)ctx->G * ctx->R;
@@ -1510,9 +1513,9 @@ extern "C" bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_es
   if (status)
     for (size_t i = 0; i < SYt; ++i) status[i] = ctx->status[i];
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
-extern "C" bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_rows) {
+extern "C" bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_rows) try {
   if (!ctx) return BT_EINVAL;
   if (!need_gpu(ctx)) return fail(ctx, BT_ENODEV, "bt_get_state: host-only context");
   if (ctx->last_kind == 0) return fail(ctx, BT_ESTATE, "bt_get_state: no state (run first)");
@@ -1540,7 +1543,7 @@ extern "C" bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, 
   CK(cudaMemcpyAsync(u_re_im, ctx->d_state.p, (size_t)rows * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
 extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter, int32_t* resid_variant,
                                    double* ms_resid) {

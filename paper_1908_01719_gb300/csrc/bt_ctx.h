@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -140,12 +142,35 @@ inline bt_status fail(bt_ctx* c, bt_status code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
 }
+// The last line of defence of every entry point: no C++ exception crosses the
+// C ABI.  Setting the message may itself fail under memory exhaustion.
+inline bt_status guard_fail(bt_ctx* c, bt_status code, const char* what) noexcept {
+  if (c) {
+    try {
+      c->err = what;
+    } catch (...) {
+    }
+  }
+  return code;
+}
 template <class T>
 cudaError_t ensure(DBuf<T>& b, size_t n) {
   if (b.n >= n && b.p) return cudaSuccess;
   return b.alloc(n);
 }
 }  // namespace bt
+
+// Closes an entry point written as a function-try-block.
+#define BT_ABI_CATCH(ctx_)                                                                       \
+  catch (const std::bad_alloc&) {                                                                \
+    return bt::guard_fail(ctx_, BT_ENOMEM, "host allocation failed");                           \
+  }                                                                                              \
+  catch (const std::exception& e_) {                                                             \
+    return bt::guard_fail(ctx_, BT_EINVAL, e_.what());                                           \
+  }                                                                                              \
+  catch (...) {                                                                                  \
+    return bt::guard_fail(ctx_, BT_EINVAL, "unexpected exception");                             \
+  }
 
 #define CK(call)                                                                                 \
   do {                                                                                           \

@@ -187,7 +187,7 @@ bt_status bt_save_precond(const bt_ctx* ctx_c, float* w) {
   return BT_OK;
 }
 
-bt_status bt_load_precond(bt_ctx* ctx, const float* w) {
+bt_status bt_load_precond(bt_ctx* ctx, const float* w) try {
   if (!ctx || !w) return BT_EINVAL;
   if (ctx->host_only) return fail(ctx, BT_ENODEV, "bt_load_precond: host-only context");
   for (int i = 0; i < MLP_NPARAM; ++i)
@@ -200,12 +200,12 @@ bt_status bt_load_precond(bt_ctx* ctx, const float* w) {
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->have_precond = true;
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
 // Train the network on n samples (raw features [n][5], G [n][81], h [n][9])
 // with minibatch Adam; loss_hist[epoch] receives the mean training loss.
 bt_status bt_train_precond(bt_ctx* ctx, int64_t n, const float* feat, const double* G, const double* h,
-                           const bt_train_opts* opts, double* loss_hist) {
+                           const bt_train_opts* opts, double* loss_hist) try {
   if (!ctx) return BT_EINVAL;
   if (ctx->host_only) return fail(ctx, BT_ENODEV, "bt_train_precond: host-only context");
   bt_train_opts o;
@@ -308,13 +308,13 @@ bt_status bt_train_precond(bt_ctx* ctx, int64_t n, const float* feat, const doub
   CK(cudaStreamSynchronize(st));
   ctx->have_precond = true;
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
 // For n samples: coefficients [n][9] from the current network, the mean loss
 // and its gradient with respect to the parameters [MLP_NPARAM] (through the
 // bfloat16 weights).  Any output pointer may be NULL.
 bt_status bt_precond_eval(bt_ctx* ctx, int64_t n, const float* feat, const double* G, const double* h,
-                          double* coef, double* loss, double* grad) {
+                          double* coef, double* loss, double* grad) try {
   if (!ctx || n < 1 || !feat) return fail(ctx, BT_EINVAL, "bt_precond_eval: bad arguments");
   if (ctx->host_only) return fail(ctx, BT_ENODEV, "bt_precond_eval: host-only context");
   if (!ctx->have_precond) return fail(ctx, BT_ESTATE, "bt_precond_eval: no network");
@@ -387,6 +387,6 @@ bt_status bt_precond_eval(bt_ctx* ctx, int64_t n, const float* feat, const doubl
     }
   }
   return BT_OK;
-}
+} BT_ABI_CATCH(ctx)
 
 }  // extern "C"

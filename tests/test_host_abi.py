@@ -319,3 +319,28 @@ def test_surface_dofmap_and_pattern_match_oracle(bt):
         assert e.value.code == bt.BT_EINVAL
     finally:
         bt.bt_destroy(ctx)
+
+
+def test_oversize_counts_refused_before_reading(bt):
+    """Element and node counts beyond the 32-bit index limits are refused
+    before any caller array is read (the arrays here are tiny)."""
+    import ctypes as C
+    p = geom.cfg1(n=2)
+    xyz = np.ascontiguousarray(p.xyz)
+    tets = np.ascontiguousarray(p.tets, dtype=np.int32)
+    tc = np.ascontiguousarray(p.tet_cmpt, dtype=np.int32)
+    D, K = np.ascontiguousarray(p.D_cmpt), np.ascontiguousarray(p.kappa_cmpt)
+    lo, hi = np.ascontiguousarray(p.box_lo), np.ascontiguousarray(p.box_hi)
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    L = bt.lib()
+    ctx = bt.bt_create(-1)
+    try:
+        for nn, nt in [(1 << 31, len(tets)), (len(xyz), 1 << 28), (1 << 40, 1 << 40)]:
+            st = L.bt_upload_mesh(ctx, nn, ptr(xyz), nt, ptr(tets), ptr(tc), 1, ptr(D), ptr(K), 0, ptr(lo), ptr(hi))
+            assert st == bt.BT_EINVAL
+            st = L.bt_upload_mesh_2d(ctx, nn, ptr(xyz), nt, ptr(tets), ptr(tc), 1, ptr(D), ptr(K), 0, ptr(lo),
+                                     ptr(hi))
+            assert st == bt.BT_EINVAL
+        assert "32-bit" in bt.bt_last_error(ctx) or "invalid" in bt.bt_last_error(ctx)
+    finally:
+        bt.bt_destroy(ctx)
