@@ -47,7 +47,7 @@ enum {
   BT_ECUDA = 3,     /* CUDA runtime error (message in bt_last_error)          */
   BT_ENOCONV = 4,   /* a Krylov or refinement loop hit its iteration cap      */
   BT_ENAN = 5,      /* NaN/Inf met in a right-hand side or a Krylov scalar    */
-  BT_ETIMEOUT = 6,  /* a bounded device loop gave up                          */
+  BT_ETIMEOUT = 6,  /* reserved: no kernel here waits on another; unused      */
   BT_ESTATE = 7,    /* call out of order (e.g. bt_run before bt_assemble)     */
   BT_ENODEV = 8     /* GPU call on a host-only context                        */
 };
