@@ -339,3 +339,46 @@ def test_direct_and_iterative_routes_agree():
     S1 = oracle.run(p, a, route="lu")
     S2 = oracle.run(p, a, route="iter")
     assert np.abs(S1 - S2).max() < 1e-12 * np.abs(S1).max()
+
+
+def test_step_average_reading_keeps_second_order():
+    """Reading Q1: the theta-scheme with f evaluated at the step ends (the
+    literal form) integrates the PGSE lobes by the trapezoid rule, which gives
+    the first lobe delta + dt/2 and the second -delta: a net phase q dt/2 at TE.
+    On a fibre whose gradient origin is off its centre that phase shows up as
+    a first-order error with a spurious imaginary part, while the step
+    averages (F(TE) = 0 exactly) stay second order with a real signal.  The
+    literal stepping is written out here only to show the defect."""
+    import scipy.sparse.linalg as spla
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+
+    def f_point(t):
+        return 1.0 if 0.0 <= t <= 2500.0 else (-1.0 if 5000.0 < t <= 7500.0 else 0.0)
+
+    def fibre(dt):
+        p = geom.line_segments(96, dt=dt)
+        p.box_lo, p.box_hi = np.array([-20.0, -20.0, -20.0]), np.array([60.0, 20.0, 20.0])
+        return p
+
+    def literal(p):
+        a = bo.assemble(p)
+        M, K, Mx = a["M"].tocsc(), a["K"].tocsc(), a["Mx"].tocsc()
+        u = np.ones(a["n"], complex)
+        for k in range(1, p.n_steps + 1):
+            fn, fo = f_point(k * p.dt), f_point((k - 1) * p.dt)
+            u = spla.spsolve((M + 0.5 * p.dt * (K + 1j * q * fn * Mx)).tocsc(),
+                             (M - 0.5 * p.dt * (K + 1j * q * fo * Mx)) @ u)
+        return (a["M"] @ np.ones(a["n"])) @ u / 40.0
+
+    ref = oracle.run(fibre(3.125))[0] / 40.0
+    lit, avg = [], []
+    for dt in (50.0, 25.0, 12.5):
+        Sl = literal(fibre(dt))
+        Sa = oracle.run(fibre(dt))[0] / 40.0
+        lit.append(abs(Sl - ref))
+        avg.append(abs(Sa - ref))
+        assert abs(Sa.imag) < 1e-12 and abs(Sl.imag) > 2e-4 * dt      # a phase of order dt
+        fbar, F, _ = oracle.sequence(fibre(dt))
+        assert abs(F[-1]) < 1e-9
+    assert 1.7 < lit[0] / lit[1] < 2.3 and 1.7 < lit[1] / lit[2] < 2.3, lit
+    assert 3.5 < avg[0] / avg[1] < 4.7 and 3.5 < avg[1] / avg[2] < 4.7, avg
