@@ -78,3 +78,53 @@ def test_two_gloo_ranks_gather_equals_unsharded():
     ref = oracle.run(p)
     for r in (0, 1):
         assert np.array_equal(res[r], ref)
+
+
+def _forest():
+    import geom
+    return [geom.dendrite_tree(seed=s, n_stems=2, depth=2, length=(6.0, 12.0)) for s in range(5)]
+
+
+def _forest_worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    trees = _forest()
+    R = trees[0].n_rhs
+    mine = shard.geometry_partition([len(t.tets) for t in trees], world)[rank]
+    local = [oracle.run(trees[g]) for g in mine]
+    index = [g * R + r for g in mine for r in range(R)]
+    full = shard.gather_signals(np.concatenate(local) if local else np.zeros(0, complex), index, len(trees) * R)
+    dist.destroy_process_group()
+    q.put((rank, mine, full))
+
+
+def test_two_gloo_ranks_shard_a_forest_by_geometry():
+    """A batch of dendrite trees (1-D manifolds) split across two ranks by
+    geometry (LPT on segment counts), no exchange but the final gather: every
+    rank ends with the unsharded batch's signals, bit for bit."""
+    import multiprocessing as mp
+
+    import oracle
+    ctx = mp.get_context("spawn")
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_forest_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res = {}
+    for _ in procs:
+        rank, mine, full = q.get(timeout=300)
+        res[rank] = (mine, full)
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    assert sorted(res[0][0] + res[1][0]) == list(range(5)) and res[0][0] and res[1][0]
+    ref = np.concatenate([oracle.run(t) for t in _forest()])
+    for r in (0, 1):
+        assert np.array_equal(res[r][1], ref)
