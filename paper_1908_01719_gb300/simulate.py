@@ -3,8 +3,6 @@ sequence and gradients, run, read the signals.  Marshalling only; every step of
 the method runs inside libbtgpu."""
 from __future__ import annotations
 
-import numpy as np
-
 from . import bt, profiles
 
 

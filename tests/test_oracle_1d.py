@@ -4,7 +4,6 @@ fibre against the matrix formalism of the Neumann interval (second order in h
 and dt together); the embedding against rotation (only the projection of the
 gradient on the fibre matters, an exact discrete identity); a branched tree
 against its length, linear fields and conservation at g = 0."""
-import math
 
 import numpy as np
 import pytest

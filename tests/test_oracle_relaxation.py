@@ -6,7 +6,6 @@ the scalar recursion u^n = u^{n-1} (1 - (1-th) dt/T2) / (1 + th dt/T2):
 S = sum_c rho_c |Omega_c| r_c^N exactly, with |Omega_c| summed from the
 tetrahedron volumes (not from the oracle's assembly), tending to
 exp(-TE/T2) at second order in dt."""
-import math
 
 import numpy as np
 
