@@ -298,6 +298,7 @@ template <int NB, bool TRANSF>
 static void resid0_t(const OpArgs& op, const double2* u, double2* r, const RefineState& rf, RedScratch rs, int sms,
                      cudaStream_t st) {
   dim3 grid(op.sp.nblk, (op.R + 32 * NB - 1) / (32 * NB));
+  // MODE 0 only reads u, through both pointers; restrict allows aliasing objects that are not modified
   k_resid64<NB, TRANSF, 0, double2><<<grid, 256, 0, st>>>(op, u, const_cast<double2*>(u), r, rf, rs);
 }
 template <int NB, bool TRANSF>
