@@ -8,11 +8,13 @@
  *   PDE      dU/dt = -i gamma f(t) g.x U + div(D grad U)        (Section 2, Eq. strong_BT)
  *   membrane flux continuity, mean flux = -kappa [U]            (Section 2, Eq. btpde_ic)
  *   outer    homogeneous Neumann, or pseudo-periodic             (Section 2, Eq. btpde_bc)
- *   profile  PGSE f(t)                                           (Section 2, Eq. pgse)
+ *   profile  PGSE f(t), or any profile as F on the time grid     (Section 2, Eq. pgse;
+ *                                                                 Section 3)
  *   signal   S = integral of U(x, TE) dx                         (Section 2, Eq. signal)
  *   b-value  b = gamma^2 |g|^2 int_0^TE F(s)^2 ds                (Section 2, Eq. b_value)
- *   space    P1 tetrahedra, one nodal copy per compartment on interface nodes (PUFEM,
- *            Appendix A, Eq. phase_func)
+ *   space    P1 tetrahedra (or planar triangles, or the segments and surface
+ *            triangles of thin tubes and layers), one nodal copy per compartment on
+ *            interface nodes (PUFEM, Appendix A, Eq. phase_func)
  *   time     theta-method, matrix form A U^n = F                 (Appendix B, Eq. matrix_form)
  *   periodic gauge transform u = U exp(i gamma F(t) g.x)         (Appendix A, Eq. trBlo)
  *

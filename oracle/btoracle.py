@@ -2,7 +2,8 @@
 Bloch-Torrey equation (test infrastructure only; see the package docstring).
 
 What it follows (section / equation of arXiv 1908.01719):
-  * model: Bloch-Torrey PDE (Eq. strong_BT, Section 2) with T2 = infinity, the
+  * model: Bloch-Torrey PDE (Eq. strong_BT, Section 2) with the T2 term
+    (p.inv_T2, default none) and per-compartment initial values (p.rho), the
     permeable interface conditions (Eq. btpde_ic), PGSE profile (Eq. pgse),
     signal S = integral of U at TE (Eq. signal), b-value (Eq. b_value);
   * PUFEM interface treatment (Appendix A): one nodal copy per compartment on
