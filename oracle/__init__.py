@@ -1,7 +1,8 @@
 """CPU FP64 oracle for the finite-element Bloch-Torrey solve.
 
 TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import it: only the
-tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg use it.
+tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg and
+reference arm use it.
 It shares no code with the CUDA library; both read the same seeded inputs from
 ``geom``.
 """

@@ -17,7 +17,13 @@ What it follows (section / equation of arXiv 1908.01719):
     thin-layer and thin-tube media of the manifold route (Section 1's feature
     list; Section 5, "Realistic neurons"), P1 triangles of a surface and P1
     segments of a curve embedded in 3-D: integrals over the manifold,
-    tangential gradients, uniform thickness or cross-section.
+    tangential gradients, uniform thickness or cross-section;
+  * a diffusion tensor per compartment (p.D_tensor, Section 3 "Diffusion
+    coefficients and tensors") in the stiffness, lab frame;
+  * temporal profiles other than PGSE integrated from f (oracle/profiles.py,
+    Section 3 "General diffusion-encoding sequence");
+  * weak pseudo-periodic conditions through an artificial permeability
+    (oracle/weakper.py, Appendix B).
 
 Readings where the paper leaves a choice (each is also listed in the design
 notes of the repository):
