@@ -652,3 +652,47 @@ def test_surface_transformed_frame_refused(bt):
         bt.bt_assemble(ctx, 50.0, 0.5, bt.BT_FRAME_LAB)
     finally:
         bt.bt_destroy(ctx)
+
+
+# ---------------------------------------------------------------- every element family under each variant
+FAMILIES = {
+    "disk2d": lambda: geom.square_disk(n=16, L=10.0, R=3.0, kappa=1e-4, bvals=(0.0, 1000.0, 3000.0),
+                                       dirs=((1.0, 0.0, 0.0), (0.6, 0.8, 0.0))),
+    "tree": lambda: _tree(),
+    "shell": lambda: _shell(),
+}
+
+
+@pytest.fixture(scope="module")
+def family_field():
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            p = FAMILIES[name]()
+            cache[name] = (p,) + oracle.run(p, return_field=True)
+        return cache[name]
+    return get
+
+
+@pytest.mark.parametrize("name", list(FAMILIES))
+@pytest.mark.parametrize("variant", ["row", "halo"])
+@pytest.mark.parametrize("loop", ["graph", "host"])
+def test_element_families_under_each_variant(sim_cls, bt, family_field, name, variant, loop):
+    """Planar triangles, manifold segments and surface triangles through both
+    inner-Krylov variants and both drivers: signals and every dof of the
+    field at TE against the oracle, mixed mode."""
+    p, ref, U = family_field(name)
+    flags = {"row": bt.BT_OPT_VARIANT_ROW, "halo": bt.BT_OPT_VARIANT_HALO}[variant]
+    if loop == "host":
+        flags |= bt.BT_OPT_NO_GRAPH
+    sim = sim_cls(p)
+    try:
+        S, err, stat, st = sim.run(bt.BT_MODE_MIXED, flags=flags)
+        assert np.all(stat == 0)
+        assert rel(S, ref).max() < TOL_MIXED, rel(S, ref)
+        for r in range(p.n_rhs):
+            u = bt.bt_get_state(sim.ctx, r)
+            assert (np.abs(u - U[r]) / np.abs(U[r]).max()).max() < TOL_MIXED, r
+    finally:
+        sim.close()
