@@ -407,6 +407,32 @@ def square_disk(n: int = 40, L: float = 10.0, R: float = 3.0, dt: float = 50.0, 
                    np.asarray(bvals, dtype=np.float64))
 
 
+def layered_disk(n: int = 40, radii=(5.0, 7.5, 10.0), dt: float = 100.0, D: float = 3e-3, kappa: float = 1e-5,
+                 rho=(0.0, 1.0, 0.0), bvals=(0.0, 1000.0, 4000.0), dirs=((1.0, 0.0, 0.0),)):
+    """2-D: concentric layers r < radii[0], ..., r < radii[-1] (one compartment
+    each, permeable membranes between them, Neumann outside) cut from an n x n
+    grid of the square [-R, R]^2, R = radii[-1]: triangles whose centroid lies
+    outside R are dropped and the unused nodes removed.  The paper's
+    three-layer disk with the initial magnetization rho per layer, its PGSE
+    (delta 10.6 ms, Delta 43.1 ms) on a 100 us grid."""
+    R = radii[-1]
+    xyz, tris = kuhn_grid_2d(n, n, np.full(2, -R), np.full(2, R))
+    r = np.hypot(*xyz[tris].mean(axis=1)[:, :2].T)
+    tris = tris[r < R]
+    r = r[r < R]
+    used = np.unique(tris)
+    new_id = np.full(len(xyz), -1, np.int64)
+    new_id[used] = np.arange(len(used))
+    xyz, tris = xyz[used], new_id[tris].astype(np.int32)
+    lab = np.searchsorted(np.asarray(radii[:-1], float), r, side="right").astype(np.int32)
+    nc = len(radii)
+    lo, hi = np.array([-R, -R, -1.0]), np.array([R, R, 1.0])
+    p = Problem("layered_disk", xyz, tris, lab, np.full(nc, D), np.full(nc, kappa), 0, lo, hi, dt, 10600.0,
+                43100.0, 53700.0, np.asarray(dirs, dtype=np.float64), np.asarray(bvals, dtype=np.float64))
+    p.rho = np.asarray(rho, dtype=np.float64)
+    return p
+
+
 def free_periodic_square(n: int = 8, L: float = 10.0, dt: float = 50.0, D: float = 2e-3,
                          dirs=((1.0, 0.0, 0.0),), bvals=(1000.0,)):
     """2-D periodic square without compartments (free diffusion)."""

@@ -696,3 +696,20 @@ def test_element_families_under_each_variant(sim_cls, bt, family_field, name, va
             assert (np.abs(u - U[r]) / np.abs(U[r]).max()).max() < TOL_MIXED, r
     finally:
         sim.close()
+
+
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_layered_disk_discontinuous_initial_condition(sim_cls, bt, mode):
+    """The paper's three-layer disk with initial magnetization [0, 1, 0], its
+    D, kappa and neuron PGSE, against the oracle."""
+    p = geom.layered_disk(n=24, bvals=(0.0, 1000.0, 4000.0), dirs=((1.0, 0.0, 0.0), (0.6, 0.8, 0.0)))
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S, err, stat, st = sim.run(m)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()

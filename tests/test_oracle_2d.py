@@ -90,3 +90,23 @@ def test_periodic_square_exact_discrete_product():
         assert abs(S - prod) < 1e-12
         errs.append(abs(S.real - math.exp(-900.0 * 2e-3)))
     assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_layered_disk_initial_condition_conservation_and_linearity():
+    """The paper's three-layer disk (radii 5, 7.5, 10 um) with initial
+    magnetization [0, 1, 0]: at g = 0 the signal stays the middle layer's area
+    while the membranes exchange magnetization; at any b the scheme is linear
+    in the initial condition, S[0,1,0] + S[1,0,1] = S[1,1,1]."""
+    p = geom.layered_disk(n=20, bvals=(0.0,))
+    X = p.xyz[p.tets]
+    area = 0.5 * np.abs(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0])[:, 2])
+    S, H = oracle.run(p, return_history=True)
+    mid = area[p.tet_cmpt == 1].sum()
+    assert np.max(np.abs(H[0] - mid)) < 1e-10 * mid
+    res = {}
+    for rho in ((0.0, 1.0, 0.0), (1.0, 0.0, 1.0), (1.0, 1.0, 1.0)):
+        q = geom.layered_disk(n=20, rho=rho, bvals=(1000.0, 4000.0), dirs=((0.6, 0.8, 0.0),))
+        res[rho] = oracle.run(q)
+    lhs = res[(0.0, 1.0, 0.0)] + res[(1.0, 0.0, 1.0)]
+    assert np.max(np.abs(lhs - res[(1.0, 1.0, 1.0)])) < 1e-11 * np.max(np.abs(res[(1.0, 1.0, 1.0)]))
+    assert abs(res[(0.0, 1.0, 0.0)][0]) < 0.9 * mid          # the gradient attenuates it
