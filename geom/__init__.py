@@ -253,6 +253,8 @@ class Problem:
     rho: np.ndarray | None = None
     # anisotropic diffusion: [n_cmpt, 6] (xx, yy, zz, xy, yz, zx) in mm^2/s; None = isotropic D_cmpt
     D_tensor: np.ndarray | None = None
+    # cell-based tensors: [n_tets, 6], one per element (overrides D_tensor); None = per compartment
+    D_tensor_elem: np.ndarray | None = None
     # weak pseudo-periodic conditions on a non-periodic box (lab frame):
     # {"axes": bit mask, "kappa_e": um/us or None for max D / h}
     weak_periodic: dict | None = None

@@ -171,6 +171,14 @@ bt_status bt_set_relaxation(bt_ctx* ctx, const double* inv_T2, const double* rho
  * masses).  Clears the assembly like bt_set_relaxation.  BT_EINVAL for
  * non-finite or indefinite tensors. */
 bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6);
+/* Cell-based diffusion tensors (Section 3, "Diffusion coefficients and
+ * tensors": d_jk cell-wise, set per cell from its midpoint or its marker):
+ * D6 [n_elem][6] = (xx, yy, zz, xy, yz, zx) in mm^2/s for every element in
+ * upload order, each finite and symmetric positive semi-definite; they
+ * override the per-compartment tensors.  NULL removes them.  Lab frame only,
+ * as bt_set_diffusion_tensor; clears the assembly.  BT_EINVAL names the first
+ * non-finite or indefinite element. */
+bt_status bt_set_element_tensors(bt_ctx* ctx, const double* D6);
 
 /* Weak pseudo-periodic conditions on a box that is not meshed periodically
  * (Appendix B, "Weak implementation of the pseudo-periodic BCs"): on every

@@ -18,8 +18,9 @@ What it follows (section / equation of arXiv 1908.01719):
     list; Section 5, "Realistic neurons"), P1 triangles of a surface and P1
     segments of a curve embedded in 3-D: integrals over the manifold,
     tangential gradients, uniform thickness or cross-section;
-  * a diffusion tensor per compartment (p.D_tensor, Section 3 "Diffusion
-    coefficients and tensors") in the stiffness, lab frame;
+  * a diffusion tensor per compartment (p.D_tensor) or per cell
+    (p.D_tensor_elem), Section 3 "Diffusion coefficients and tensors", in the
+    stiffness, lab frame;
   * temporal profiles other than PGSE integrated from f (oracle/profiles.py,
     Section 3 "General diffusion-encoding sequence");
   * weak pseudo-periodic conditions through an artificial permeability
@@ -224,18 +225,21 @@ def assemble(p):
     # P1 mass: |T| (1 + delta_ij) / ((d + 1)(d + 2))
     Me = vol[:, None, None] / ((d + 1) * (d + 2)) * (1.0 + np.eye(nv))[None]
     Dten = getattr(p, "D_tensor", None)
-    if Dten is None:
+    Dten_e = getattr(p, "D_tensor_elem", None)
+    if Dten is None and Dten_e is None:
         Ke = (Dt * vol)[:, None, None] * np.einsum("tik,tjk->tij", G, G)
     else:
         # anisotropic diffusion: (D grad u, grad v) with one symmetric tensor
-        # per compartment, given as (xx, yy, zz, xy, yz, zx)
-        T = np.asarray(Dten, float)
+        # per compartment, or per cell (Section 3: cell-based piecewise
+        # continuous d_jk), given as (xx, yy, zz, xy, yz, zx)
+        T = np.asarray(Dten_e if Dten_e is not None else Dten, float)
         Dm = np.empty((len(T), 3, 3))
         Dm[:, 0, 0], Dm[:, 1, 1], Dm[:, 2, 2] = T[:, 0], T[:, 1], T[:, 2]
         Dm[:, 0, 1] = Dm[:, 1, 0] = T[:, 3]
         Dm[:, 1, 2] = Dm[:, 2, 1] = T[:, 4]
         Dm[:, 2, 0] = Dm[:, 0, 2] = T[:, 5]
-        Ke = vol[:, None, None] * np.einsum("tik,tkl,tjl->tij", G, Dm[p.tet_cmpt], G)
+        De = Dm if Dten_e is not None else Dm[p.tet_cmpt]
+        Ke = vol[:, None, None] * np.einsum("tik,tkl,tjl->tij", G, De, G)
     centre = 0.5 * (np.asarray(p.box_lo, float) + np.asarray(p.box_hi, float))
     Xc = X - centre
     c3 = _cubic_moments(d)
@@ -448,7 +452,10 @@ def run_transformed(p, asm=None, rhs=None, return_history=False, route=None, ret
     for periodic and Neumann outer boundaries:
         A(F) = K + J + q^2 F^2 MD + i q F Eq,  Eq = sum_k qhat_k E_k
         L_n = M + theta dt A(F_n),  R_n = M - (1 - theta) dt A(F_{n-1})
-        S = (M 1)^T u^N  (F(TE) = 0 for PGSE, so U = u at TE)."""
+        S = (M 1)^T u^N  (F(TE) = 0 for PGSE, so U = u at TE).
+    Diffusion tensors are refused: the q^2 F^2 term would need q^T D q."""
+    if getattr(p, "D_tensor", None) is not None or getattr(p, "D_tensor_elem", None) is not None:
+        raise ValueError("diffusion tensors need the lab frame")
     if asm is None:
         asm = assemble(p)
     M, KJ, MD = asm["M"], asm["K"] + asm["J"] + asm["MR"], asm["MD"]

@@ -31,7 +31,7 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
            "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation", "bt_set_diffusion_tensor", "bt_set_weak_periodic", "bt_upload_mesh_2d",
-           "bt_upload_mesh_1d", "bt_upload_mesh_surface"]
+           "bt_upload_mesh_1d", "bt_upload_mesh_surface", "bt_set_element_tensors"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -72,6 +72,7 @@ def lib():
             "bt_upload_mesh_2d": [P, I64, P, I64, P, P, I32, P, P, U32, P, P],
             "bt_upload_mesh_1d": [P, I64, P, I64, P, P, I32, P, P, P],
             "bt_upload_mesh_surface": [P, I64, P, I64, P, P, I32, P, P, P, P],
+            "bt_set_element_tensors": [P, P],
             "bt_get_sizes": [P, P, P, P],
             "bt_get_dofmap": [P, P, P],
             "bt_get_pattern": [P, P, P],
@@ -255,6 +256,16 @@ def bt_set_diffusion_tensor(ctx, D6=None):
         return
     a = np.ascontiguousarray(D6, dtype=np.float64).reshape(-1, 6)
     _check(ctx, lib().bt_set_diffusion_tensor(ctx, _ptr(a)))
+
+
+def bt_set_element_tensors(ctx, D6=None):
+    """Cell-based diffusion tensors [n_elem, 6] (xx, yy, zz, xy, yz, zx), one row
+    per element in upload order; None removes them."""
+    if D6 is None:
+        _check(ctx, lib().bt_set_element_tensors(ctx, None))
+        return
+    a = np.ascontiguousarray(D6, dtype=np.float64).reshape(-1, 6)
+    _check(ctx, lib().bt_set_element_tensors(ctx, _ptr(a)))
 
 
 def bt_set_profile(ctx, F, int_F2):

@@ -150,6 +150,7 @@ static bt_status upload_mesh_nv(bt_ctx* ctx, int nv, int64_t n_nodes, const doub
   ctx->cm_invT2.assign(n_cmpt, 0.0);
   ctx->cm_rho.assign(n_cmpt, 1.0);
   ctx->cm_Dten.clear();
+  ctx->el_Dten.clear();
   ctx->weak_axes = 0;
   ctx->have_rho = false;
   if (ctx->host_only) return BT_OK;
@@ -304,6 +305,19 @@ bt_status bt_set_weak_periodic(bt_ctx* ctx, uint32_t axes, double kappa_e) try {
   return BT_OK;
 } BT_ABI_CATCH(ctx)
 
+// A symmetric tensor (xx, yy, zz, xy, yz, zx) that is finite and positive
+// semi-definite: the leading minors of [[xx, xy, zx], [xy, yy, yz], [zx, yz, zz]]
+// and the diagonal are non-negative (to rounding).
+static bool tensor_ok(const double* d) {
+  for (int k = 0; k < 6; ++k)
+    if (!std::isfinite(d[k])) return false;
+  const double m1 = d[0], m2 = d[0] * d[1] - d[3] * d[3];
+  const double m3 = d[0] * (d[1] * d[2] - d[4] * d[4]) - d[3] * (d[3] * d[2] - d[4] * d[5]) +
+                    d[5] * (d[3] * d[4] - d[1] * d[5]);
+  const double sc = std::max({std::fabs(d[0]), std::fabs(d[1]), std::fabs(d[2]), 1e-300});
+  return !(m1 < 0 || d[1] < 0 || d[2] < 0 || m2 < -1e-12 * sc * sc || m3 < -1e-12 * sc * sc * sc);
+}
+
 bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;
@@ -313,19 +327,29 @@ bt_status bt_set_diffusion_tensor(bt_ctx* ctx, const double* D6) try {
     ctx->cm_Dten.clear();
   } else {
     std::vector<double> t(D6, D6 + 6 * (size_t)nc);
-    for (int c = 0; c < nc; ++c) {
-      const double* d = &t[6 * (size_t)c];
-      for (int k = 0; k < 6; ++k)
-        if (!std::isfinite(d[k])) return fail(ctx, BT_EINVAL, "bt_set_diffusion_tensor: non-finite entry");
-      // positive semi-definite: leading minors of [[xx, xy, zx], [xy, yy, yz], [zx, yz, zz]]
-      const double m1 = d[0], m2 = d[0] * d[1] - d[3] * d[3];
-      const double m3 = d[0] * (d[1] * d[2] - d[4] * d[4]) - d[3] * (d[3] * d[2] - d[4] * d[5]) +
-                        d[5] * (d[3] * d[4] - d[1] * d[5]);
-      const double sc = std::max({std::fabs(d[0]), std::fabs(d[1]), std::fabs(d[2]), 1e-300});
-      if (m1 < 0 || d[1] < 0 || d[2] < 0 || m2 < -1e-12 * sc * sc || m3 < -1e-12 * sc * sc * sc)
-        return fail(ctx, BT_EINVAL, "bt_set_diffusion_tensor: tensor not positive semi-definite");
-    }
+    for (int c = 0; c < nc; ++c)
+      if (!tensor_ok(&t[6 * (size_t)c]))
+        return fail(ctx, BT_EINVAL, "bt_set_diffusion_tensor: non-finite or indefinite tensor");
     ctx->cm_Dten = t;
+  }
+  ctx->assembled = ctx->have_seq = false;
+  return BT_OK;
+} BT_ABI_CATCH(ctx)
+
+bt_status bt_set_element_tensors(bt_ctx* ctx, const double* D6) try {
+  if (!ctx) return BT_EINVAL;
+  ctx->last_kind = 0;
+  if (!ctx->have_mesh) return fail(ctx, BT_ESTATE, "bt_set_element_tensors: no mesh");
+  const int64_t ne = ctx->mesh.n_tets;
+  if (!D6) {
+    ctx->el_Dten.clear();
+  } else {
+    std::vector<double> t(D6, D6 + 6 * (size_t)ne);
+    for (int64_t e = 0; e < ne; ++e)
+      if (!tensor_ok(&t[6 * (size_t)e]))
+        return fail(ctx, BT_EINVAL, "bt_set_element_tensors: non-finite or indefinite tensor at element " +
+                                        std::to_string(e));
+    ctx->el_Dten = std::move(t);
   }
   ctx->assembled = ctx->have_seq = false;
   return BT_OK;
@@ -342,7 +366,7 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) t
     return fail(ctx, BT_EINVAL, "bt_assemble: periodic boxes need BT_FRAME_TRANSFORMED");
   if ((ctx->mesh.nv == 2 || ctx->mesh.surface) && flags != BT_FRAME_LAB)
     return fail(ctx, BT_EINVAL, "bt_assemble: manifold meshes need the lab frame");
-  if (!ctx->cm_Dten.empty() && flags == BT_FRAME_TRANSFORMED)
+  if ((!ctx->cm_Dten.empty() || !ctx->el_Dten.empty()) && flags == BT_FRAME_TRANSFORMED)
     return fail(ctx, BT_EINVAL, "bt_assemble: diffusion tensors need the lab frame");
   if (ctx->weak_axes && flags == BT_FRAME_TRANSFORMED)
     return fail(ctx, BT_EINVAL, "bt_assemble: the weak periodic box needs the lab frame");
@@ -366,6 +390,8 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) t
   }
   if (!ctx->cm_Dten.empty()) CK(upload(ctx->d_Dten, ctx->cm_Dten, st));
   else ctx->d_Dten.free();
+  if (!ctx->el_Dten.empty()) CK(upload(ctx->d_Dten_el, ctx->el_Dten, st));
+  else ctx->d_Dten_el.free();
   if (ctx->have_rho) {
     std::vector<double> rd(n);
     for (int64_t i = 0; i < n; ++i) rd[i] = ctx->cm_rho[m.dof_cmpt[i]];
@@ -373,13 +399,14 @@ bt_status bt_assemble(bt_ctx* ctx, double dt_us, double theta, uint32_t flags) t
   } else {
     ctx->d_rho_dof.free();
   }
-  AsmArgs a;
+  AsmArgs a{};
   a.xyz = ctx->d_xyz.p;
   a.tets = ctx->d_tets.p;
   a.cmpt = ctx->d_cmpt.p;
   a.Dc = ctx->d_D.p;
   a.invT2c = ctx->d_invT2.p;
   a.Dten = ctx->cm_Dten.empty() ? nullptr : ctx->d_Dten.p;
+  a.DtenE = ctx->el_Dten.empty() ? nullptr : ctx->d_Dten_el.p;
   for (int k = 0; k < 3; ++k) a.centre[k] = 0.5 * (m.lo[k] + m.hi[k]);
   a.nt = m.n_tets;
   a.nv = m.nv;

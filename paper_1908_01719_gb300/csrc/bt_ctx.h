@@ -33,8 +33,9 @@ struct bt_ctx {
   bt::DBuf<double> d_xyz, d_D, d_face_kappa, d_geo, d_fcoef;
   // relaxation and initial condition per compartment (bt_set_relaxation)
   std::vector<double> cm_invT2, cm_rho, cm_Dten;  // cm_Dten empty: isotropic
+  std::vector<double> el_Dten;                     // [n_elem][6] cell-based tensors (empty: none)
   bool have_rho = false;
-  bt::DBuf<double> d_invT2, d_rho_dof, d_Dten;
+  bt::DBuf<double> d_invT2, d_rho_dof, d_Dten, d_Dten_el;
   // weak pseudo-periodic box (bt_set_weak_periodic)
   uint32_t weak_axes = 0;
   double weak_kappa_in = 0, weak_kappa = 0;

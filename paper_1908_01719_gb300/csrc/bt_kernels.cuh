@@ -18,6 +18,7 @@ struct AsmArgs {
   const double* Dc;
   const double* invT2c;  // [n_cmpt] 1/T2 per compartment (or null: none)
   const double* Dten;    // [n_cmpt][6] diffusion tensors (or null: isotropic Dc)
+  const double* DtenE;   // [n_elem][6] per-element tensors, overriding Dten (or null)
   double centre[3];
   int64_t nt, nf, nnz;
   int nv;       // 4 tetrahedra, 3 triangles, 2 segments

@@ -19,13 +19,15 @@
 namespace bt {
 
 // geometry record of one tetrahedron: vol, G[4][3], Xc[4][3] (relative to the
-// box centre), D, 1/T2, diffusion tensor (xx, yy, zz, xy, yz, zx)
+// box centre), D, 1/T2, diffusion tensor (xx, yy, zz, xy, yz, zx): the
+// element's own (DtenE, cell-based), else its compartment's (Dten), else D I
 static constexpr int TG = 33;
 
 __global__ void k_tet_geom(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
                            const int32_t* __restrict__ cmpt, const double* __restrict__ Dc,
                            const double* __restrict__ invT2c, const double* __restrict__ Dten, double cx,
-                           double cy, double cz, int64_t nt, double* __restrict__ out) {
+                           double cy, double cz, int64_t nt, double* __restrict__ out,
+                           const double* __restrict__ DtenE) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double X[4][3];
@@ -75,7 +77,8 @@ __global__ void k_tet_geom(const double* __restrict__ xyz, const int32_t* __rest
   const int cm = cmpt[t];
   o[25] = Dc[cm];
   o[26] = invT2c ? invT2c[cm] : 0.0;
-  for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
+  for (int k = 0; k < 6; ++k)
+    o[27 + k] = DtenE ? DtenE[6 * t + k] : Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
 }
 
 // The same record for a triangle in the xy plane (2-D meshes): area, the
@@ -84,7 +87,8 @@ __global__ void k_tet_geom(const double* __restrict__ xyz, const int32_t* __rest
 __global__ void k_tri_geom(const double* __restrict__ xyz, const int32_t* __restrict__ tris,
                            const int32_t* __restrict__ cmpt, const double* __restrict__ Dc,
                            const double* __restrict__ invT2c, const double* __restrict__ Dten, double cx,
-                           double cy, double cz, int64_t nt, double* __restrict__ out) {
+                           double cy, double cz, int64_t nt, double* __restrict__ out,
+                           const double* __restrict__ DtenE) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double X[3][3];
@@ -110,7 +114,8 @@ __global__ void k_tri_geom(const double* __restrict__ xyz, const int32_t* __rest
   const int cm = cmpt[t];
   o[25] = Dc[cm];
   o[26] = invT2c ? invT2c[cm] : 0.0;
-  for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
+  for (int k = 0; k < 6; ++k)
+    o[27 + k] = DtenE ? DtenE[6 * t + k] : Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
 }
 
 // The record for a triangle of a surface embedded in 3-D (a thin layer): area,
@@ -121,7 +126,8 @@ __global__ void k_tri_geom(const double* __restrict__ xyz, const int32_t* __rest
 __global__ void k_stri_geom(const double* __restrict__ xyz, const int32_t* __restrict__ tris,
                             const int32_t* __restrict__ cmpt, const double* __restrict__ Dc,
                             const double* __restrict__ invT2c, const double* __restrict__ Dten, double cx,
-                            double cy, double cz, int64_t nt, double* __restrict__ out) {
+                            double cy, double cz, int64_t nt, double* __restrict__ out,
+                           const double* __restrict__ DtenE) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double X[3][3];
@@ -153,7 +159,8 @@ __global__ void k_stri_geom(const double* __restrict__ xyz, const int32_t* __res
   const int cm = cmpt[t];
   o[25] = Dc[cm];
   o[26] = invT2c ? invT2c[cm] : 0.0;
-  for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
+  for (int k = 0; k < 6; ++k)
+    o[27 + k] = DtenE ? DtenE[6 * t + k] : Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
 }
 
 // The record for a segment of a 1-D manifold embedded in 3-D: length, the
@@ -162,7 +169,8 @@ __global__ void k_stri_geom(const double* __restrict__ xyz, const int32_t* __res
 __global__ void k_seg_geom(const double* __restrict__ xyz, const int32_t* __restrict__ segs,
                            const int32_t* __restrict__ cmpt, const double* __restrict__ Dc,
                            const double* __restrict__ invT2c, const double* __restrict__ Dten, double cx,
-                           double cy, double cz, int64_t nt, double* __restrict__ out) {
+                           double cy, double cz, int64_t nt, double* __restrict__ out,
+                           const double* __restrict__ DtenE) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double X[2][3];
@@ -188,7 +196,8 @@ __global__ void k_seg_geom(const double* __restrict__ xyz, const int32_t* __rest
   const int cm = cmpt[t];
   o[25] = Dc[cm];
   o[26] = invT2c ? invT2c[cm] : 0.0;
-  for (int k = 0; k < 6; ++k) o[27 + k] = Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
+  for (int k = 0; k < 6; ++k)
+    o[27 + k] = DtenE ? DtenE[6 * t + k] : Dten ? Dten[6 * cm + k] : (k < 3 ? Dc[cm] : 0.0);
 }
 
 // kappa |F| / 12 per interface face (3-D); kappa |e| / 6 per interface edge (2-D)
@@ -362,16 +371,20 @@ void launch_assembly(const AsmArgs& a, cudaStream_t st) {
   const int TB = 256;
   if (a.nt && a.nv == 4)
     k_tet_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
-                                                              a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
+                                                              a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo,
+                                                              a.DtenE);
   if (a.nt && a.nv == 2)
     k_seg_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
-                                                               a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
+                                                               a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo,
+                                                              a.DtenE);
   if (a.nt && a.nv == 3 && a.surface)
     k_stri_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
-                                                               a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
+                                                               a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo,
+                                                              a.DtenE);
   if (a.nt && a.nv == 3 && !a.surface)
     k_tri_geom<<<(unsigned)((a.nt + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.cmpt, a.Dc, a.invT2c, a.Dten,
-                                                              a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo);
+                                                              a.centre[0], a.centre[1], a.centre[2], a.nt, a.geo,
+                                                              a.DtenE);
   if (a.nf) k_face_coef<<<(unsigned)((a.nf + TB - 1) / TB), TB, 0, st>>>(a.xyz, a.tets, a.face_ta, a.face_lv,
                                                                    a.face_kappa, a.nf, a.nv, a.fcoef);
   k_assemble_slots<<<(unsigned)((a.nnz + TB - 1) / TB), TB, 0, st>>>(a.geo, a.tc_ptr, a.tc, a.fc_ptr, a.fc,

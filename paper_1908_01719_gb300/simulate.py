@@ -11,7 +11,8 @@ class Simulation:
     xyz, tets, tet_cmpt, D_cmpt, kappa_cmpt, periodic_mask, box_lo, box_hi,
     dt, theta, delta, Delta, TE, dirs, bvals, transformed, and optionally a
     temporal `profile` (see profiles.py; None = PGSE), per-compartment `inv_T2`
-    (1/us) and initial magnetization `rho`, `D_tensor` (lab frame) and
+    (1/us) and initial magnetization `rho`, per-compartment `D_tensor` or
+    per-element `D_tensor_elem` (lab frame) and
     `weak_periodic` (lab frame)."""
 
     def __init__(self, geom, device: int = 0, stream: int | None = None):
@@ -37,6 +38,11 @@ class Simulation:
             bt.bt_set_relaxation(self.ctx, inv_T2, rho)
         if getattr(geom, "D_tensor", None) is not None:
             bt.bt_set_diffusion_tensor(self.ctx, geom.D_tensor)
+        De = getattr(geom, "D_tensor_elem", None)
+        if De is not None:
+            if len(De) != len(geom.tets):
+                raise ValueError("D_tensor_elem needs one row per element")
+            bt.bt_set_element_tensors(self.ctx, De)
         weak = getattr(geom, "weak_periodic", None)
         if weak:
             bt.bt_set_weak_periodic(self.ctx, weak["axes"], weak.get("kappa_e") or 0.0)

@@ -344,3 +344,21 @@ def test_oversize_counts_refused_before_reading(bt):
         assert "32-bit" in bt.bt_last_error(ctx) or "invalid" in bt.bt_last_error(ctx)
     finally:
         bt.bt_destroy(ctx)
+
+
+def test_element_tensor_validation(bt):
+    p = geom.cfg2(n=3, kappa=1e-4)
+    ctx = _host(bt, p)
+    try:
+        D = np.tile([2e-3, 1e-3, 1.5e-3, 1e-4, 0.0, -2e-4], (len(p.tets), 1))
+        bt.bt_set_element_tensors(ctx, D)
+        bt.bt_set_element_tensors(ctx, None)
+        D[17] = [1e-3, 1e-3, 1e-3, 2e-3, 0.0, 0.0]              # |xy| > sqrt(xx yy): indefinite
+        with pytest.raises(bt.BtError) as e:
+            bt.bt_set_element_tensors(ctx, D)
+        assert e.value.code == bt.BT_EINVAL and "17" in bt.bt_last_error(ctx)
+        D[17, 3] = np.nan
+        with pytest.raises(bt.BtError):
+            bt.bt_set_element_tensors(ctx, D)
+    finally:
+        bt.bt_destroy(ctx)
