@@ -226,6 +226,7 @@ def assemble(p):
     Me = vol[:, None, None] / ((d + 1) * (d + 2)) * (1.0 + np.eye(nv))[None]
     Dten = getattr(p, "D_tensor", None)
     Dten_e = getattr(p, "D_tensor_elem", None)
+    De = None
     if Dten is None and Dten_e is None:
         Ke = (Dt * vol)[:, None, None] * np.einsum("tik,tjk->tij", G, G)
     else:
@@ -240,6 +241,7 @@ def assemble(p):
         Dm[:, 2, 0] = Dm[:, 0, 2] = T[:, 5]
         De = Dm if Dten_e is not None else Dm[p.tet_cmpt]
         Ke = vol[:, None, None] * np.einsum("tik,tkl,tjl->tij", G, De, G)
+    # De: [nt, 3, 3] per-element tensors, or None (isotropic D per compartment)
     centre = 0.5 * (np.asarray(p.box_lo, float) + np.asarray(p.box_hi, float))
     Xc = X - centre
     c3 = _cubic_moments(d)
@@ -252,11 +254,19 @@ def assemble(p):
     invT2 = getattr(p, "inv_T2", None)
     rT2 = np.zeros(len(vol)) if invT2 is None else np.asarray(invT2, float)[p.tet_cmpt]
     out["MR"] = _coo(rows, cols, rT2[:, None, None] * Me, n)
+    # the flux of the transformed weak form is D (grad u - i q F qhat u): with a
+    # tensor, C_k[i, j] = int phi_i (D grad phi_j)_k and the q^2 F^2 mass is
+    # weighted by qhat^T D qhat, kept as six planes MD_ab = sum_e D_e,ab M_e
+    DG = G if De is None else np.einsum("tkl,tjl->tjk", De, G)          # [nt, nv, 3]
+    Dw = Dt if De is None else np.ones(len(vol))
     for k, nm in enumerate("xyz"):
         Mk = vol[:, None, None] * np.einsum("ijl,tl->tij", c3, Xc[:, :, k])
         out["M" + nm] = _coo(rows, cols, Mk, n)
-        Ck = (Dt * vol / (d + 1))[:, None, None] * np.broadcast_to(G[:, None, :, k], (len(vol), nv, nv))
+        Ck = (Dw * vol / (d + 1))[:, None, None] * np.broadcast_to(DG[:, None, :, k], (len(vol), nv, nv))
         out["E" + nm] = _coo(rows, cols, Ck - np.transpose(Ck, (0, 2, 1)), n)
+    if De is not None:
+        ab = ((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (2, 0))
+        out["MDt"] = [_coo(rows, cols, De[:, a, b][:, None, None] * Me, n) for a, b in ab]
 
     # interface jump term kappa <[u], [v]> on faces between compartments
     ta, tb, lv = interface_faces(master, p.tets, p.tet_cmpt)
@@ -453,9 +463,8 @@ def run_transformed(p, asm=None, rhs=None, return_history=False, route=None, ret
         A(F) = K + J + q^2 F^2 MD + i q F Eq,  Eq = sum_k qhat_k E_k
         L_n = M + theta dt A(F_n),  R_n = M - (1 - theta) dt A(F_{n-1})
         S = (M 1)^T u^N  (F(TE) = 0 for PGSE, so U = u at TE).
-    Diffusion tensors are refused: the q^2 F^2 term would need q^T D q."""
-    if getattr(p, "D_tensor", None) is not None or getattr(p, "D_tensor_elem", None) is not None:
-        raise ValueError("diffusion tensors need the lab frame")
+    With diffusion tensors, MD is replaced per direction by
+    sum_ab qhat_a qhat_b MD_ab and E_k carries D grad phi (see assemble)."""
     if asm is None:
         asm = assemble(p)
     M, KJ, MD = asm["M"], asm["K"] + asm["J"] + asm["MR"], asm["MD"]
@@ -472,9 +481,14 @@ def run_transformed(p, asm=None, rhs=None, return_history=False, route=None, ret
         qh = p.dirs[r // nb]
         q = math.sqrt(float(p.bvals[r % nb]) / intF2)  # b = q^2 int F^2 (Eq. b_value)
         Eq = qh[0] * asm["Ex"] + qh[1] * asm["Ey"] + qh[2] * asm["Ez"]
+        MDq = MD
+        if "MDt" in asm:
+            xx, yy, zz, xy, yz, zx = asm["MDt"]
+            MDq = (qh[0] ** 2 * xx + qh[1] ** 2 * yy + qh[2] ** 2 * zz +
+                   2 * (qh[0] * qh[1] * xy + qh[1] * qh[2] * yz + qh[2] * qh[0] * zx))
 
         def A(Fv):
-            return KJ + (q * q * Fv * Fv) * MD + (1j * q * Fv) * Eq
+            return KJ + (q * q * Fv * Fv) * MDq + (1j * q * Fv) * Eq
 
         sol = _Solver(asm["n"], route, hermitian=True)
         u = initial_field(p, asm)
