@@ -53,6 +53,8 @@ def _host(bt, p):
     ctx = bt.bt_create(-1)
     if p.tets.shape[1] == 2:
         bt.bt_upload_mesh_1d(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.box_lo, p.box_hi)
+    elif p.surface:
+        bt.bt_upload_mesh_surface(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, p.box_lo, p.box_hi)
     else:
         up = bt.bt_upload_mesh_2d if p.tets.shape[1] == 3 else bt.bt_upload_mesh
         up(ctx, p.xyz, p.tets, p.tet_cmpt, p.D_cmpt, p.kappa_cmpt, p.periodic_mask, p.box_lo, p.box_hi)
@@ -150,7 +152,8 @@ def test_state_errors(bt):
                                         (lambda: geom.cfg3(n=10, n_dir=1, n_b=1), 192),
                                         (lambda: geom.cfg4(n=12, n_dir=1, bvals=(1000.0,)), 384),
                                         (lambda: geom.square_disk(n=24, L=10.0, R=3.0), 96),
-                                        (lambda: geom.dendrite_tree(seed=3, n_stems=3, depth=3), 96)])
+                                        (lambda: geom.dendrite_tree(seed=3, n_stems=3, depth=3), 96),
+                                        (lambda: geom.spherical_shell(level=3, R=5.0, kappa=1e-4), 96)])
 def test_halo_tiles_cover_the_pattern(bt, maker, umax):
     """Every row is owned by exactly one tile (at most 128 rows and 448 entries
     per tile); each tile's halo is the sorted,
