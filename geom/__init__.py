@@ -409,6 +409,47 @@ def square_disk(n: int = 40, L: float = 10.0, R: float = 3.0, dt: float = 50.0, 
                    np.asarray(bvals, dtype=np.float64))
 
 
+def polar_disk(m: int, R: float = 5.0, dt: float = 50.0, D: float = 2e-3, bvals=(1000.0,),
+               dirs=((1.0, 0.0, 0.0),), delta: float = 2500.0, Delta: float = 5000.0):
+    """2-D: the disk of radius R meshed in m rings (ring i holds 6 i nodes on
+    the circle of radius R i / m, plus the centre), neighbouring rings joined
+    by walking both in angle; the boundary nodes lie on the circle, so the
+    polygon approaches the disk at second order.  One compartment, Neumann."""
+    xyz = [np.zeros(3)]
+    rings = [[0]]
+    for i in range(1, m + 1):
+        ang = 2.0 * np.pi * np.arange(6 * i) / (6 * i)
+        ids = list(range(len(xyz), len(xyz) + 6 * i))
+        xyz += [np.array([R * i / m * math.cos(a), R * i / m * math.sin(a), 0.0]) for a in ang]
+        rings.append(ids)
+    xyz = np.array(xyz)
+    tris = []
+    for i in range(1, m + 1):
+        inner, outer = rings[i - 1], rings[i]
+        if i == 1:
+            tris += [(0, outer[j], outer[(j + 1) % 6]) for j in range(6)]
+            continue
+        ni, no = len(inner), len(outer)
+        a = b = 0
+        while a < ni or b < no:
+            ta = 2.0 * np.pi * (a + 1) / ni            # angle of the next inner node
+            tb = 2.0 * np.pi * (b + 1) / no            # angle of the next outer node
+            if b < no and (a >= ni or tb <= ta):
+                tris.append((inner[a % ni], outer[b % no], outer[(b + 1) % no]))
+                b += 1
+            else:
+                tris.append((inner[a % ni], outer[b % no], inner[(a + 1) % ni]))
+                a += 1
+    tris = np.array(tris, dtype=np.int32)
+    X = xyz[tris]
+    area2 = (X[:, 1, 0] - X[:, 0, 0]) * (X[:, 2, 1] - X[:, 0, 1]) - (X[:, 1, 1] - X[:, 0, 1]) * (X[:, 2, 0] - X[:, 0, 0])
+    tris[area2 < 0] = tris[area2 < 0][:, [0, 2, 1]]            # counter-clockwise
+    lo, hi = np.array([-R, -R, -1.0]), np.array([R, R, 1.0])
+    return Problem("polar_disk", xyz, tris, np.zeros(len(tris), np.int32), np.array([D]), np.array([NO_MEMBRANE]),
+                   0, lo, hi, dt, delta, Delta, Delta + delta, np.asarray(dirs, dtype=np.float64),
+                   np.asarray(bvals, dtype=np.float64))
+
+
 def layered_disk(n: int = 40, radii=(5.0, 7.5, 10.0), dt: float = 100.0, D: float = 3e-3, kappa: float = 1e-5,
                  rho=(0.0, 1.0, 0.0), bvals=(0.0, 1000.0, 4000.0), dirs=((1.0, 0.0, 0.0),)):
     """2-D: concentric layers r < radii[0], ..., r < radii[-1] (one compartment

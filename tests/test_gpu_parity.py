@@ -760,3 +760,24 @@ def test_element_tensors_match_oracle(sim_cls, bt, case, mode):
         assert rel(S, ref).max() < tol, rel(S, ref)
     finally:
         sim.close()
+
+
+def test_polar_disk_against_oracle_and_matrix_formalism(sim_cls, bt):
+    """A disk meshed with its boundary on the circle: mixed-mode signals against
+    the oracle, and within the discretisation error (measured on the CPU) of the
+    disk's matrix-formalism value."""
+    from oracle import mfdisk
+    p = geom.polar_disk(32, dt=12.5)
+    ref = oracle.run(p)
+    X = p.xyz[p.tets]
+    area = 0.5 * np.abs(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0])[:, 2]).sum()
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+    mf = mfdisk.mf_disk_signal(5.0, 2e-3, q, 2500.0, 5000.0).real
+    sim = sim_cls(p)
+    try:
+        S, err, stat, st = sim.run(bt.BT_MODE_MIXED)
+        assert np.all(stat == 0)
+        assert rel(S, ref).max() < TOL_MIXED
+        assert abs(S[0].real / area - mf) < 2e-5
+    finally:
+        sim.close()

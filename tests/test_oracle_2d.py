@@ -110,3 +110,39 @@ def test_layered_disk_initial_condition_conservation_and_linearity():
     lhs = res[(0.0, 1.0, 0.0)] + res[(1.0, 0.0, 1.0)]
     assert np.max(np.abs(lhs - res[(1.0, 1.0, 1.0)])) < 1e-11 * np.max(np.abs(res[(1.0, 1.0, 1.0)]))
     assert abs(res[(0.0, 1.0, 0.0)][0]) < 0.9 * mid          # the gradient attenuates it
+
+
+# ---------------------------------------------------------------- the disk against the matrix formalism
+def test_disk_matrix_formalism_limits():
+    """The disk's matrix formalism: the narrow-pulse long-time limit is the
+    closed form [2 J1(k R) / (k R)]^2, k = q delta; no diffusion or no
+    gradient leaves the signal at 1; truncation converges."""
+    import scipy.special as sps
+    from oracle import mfdisk
+    R = 5.0
+    for k in (0.3, 0.8):
+        s = mfdisk.mf_disk_signal(R, 2e-3, k / 1.0, 1.0, 2e6)
+        want = (2 * sps.j1(k * R) / (k * R)) ** 2
+        assert abs(s - want) < 2e-3 * want, (k, s, want)
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+    assert abs(mfdisk.mf_disk_signal(R, 0.0, q, 2500.0, 5000.0) - 1.0) < 1e-10
+    assert abs(mfdisk.mf_disk_signal(R, 2e-3, 0.0, 2500.0, 5000.0) - 1.0) < 1e-12
+    a = mfdisk.mf_disk_signal(R, 2e-3, q, 2500.0, 5000.0, 16, 16)
+    b = mfdisk.mf_disk_signal(R, 2e-3, q, 2500.0, 5000.0, 28, 28)
+    assert abs(a - b) < 1e-7
+
+
+def test_polar_disk_converges_to_matrix_formalism_second_order():
+    """P1 triangles on a polar mesh of the disk (boundary nodes on the circle),
+    h and dt halved together: the signal approaches the matrix-formalism value
+    at second order (error ratios about 4)."""
+    from oracle import mfdisk
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+    ref = mfdisk.mf_disk_signal(5.0, 2e-3, q, 2500.0, 5000.0).real
+    errs = []
+    for m, dt in ((8, 50.0), (16, 25.0), (32, 12.5)):
+        p = geom.polar_disk(m, dt=dt)
+        X = p.xyz[p.tets]
+        area = 0.5 * np.abs(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0])[:, 2]).sum()
+        errs.append(abs(oracle.run(p)[0].real / area - ref))
+    assert 3.3 < errs[0] / errs[1] < 4.7 and 3.3 < errs[1] / errs[2] < 4.7, errs
