@@ -781,3 +781,24 @@ def test_polar_disk_against_oracle_and_matrix_formalism(sim_cls, bt):
         assert abs(S[0].real / area - mf) < 2e-5
     finally:
         sim.close()
+
+
+def test_icosphere_against_oracle_and_matrix_formalism(sim_cls, bt):
+    """A thin spherical layer (level-4 icosphere): mixed-mode signals against
+    the oracle, and within the discretisation error (measured on the CPU) of
+    the shell's matrix-formalism value."""
+    from oracle import mfshell
+    p = geom.spherical_shell(level=4, R=5.0, dt=12.5, bvals=(1000.0,), dirs=((0.0, 0.0, 1.0),))
+    ref = oracle.run(p)
+    X = p.xyz[p.tets]
+    area = 0.5 * np.linalg.norm(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]), axis=1).sum()
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+    mf = mfshell.mf_shell_signal(5.0, 2e-3, q, 2500.0, 5000.0).real
+    sim = sim_cls(p)
+    try:
+        S, err, stat, st = sim.run(bt.BT_MODE_MIXED)
+        assert np.all(stat == 0)
+        assert rel(S, ref).max() < TOL_MIXED
+        assert abs(S[0].real / area - mf) < 2e-4
+    finally:
+        sim.close()

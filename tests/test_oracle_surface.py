@@ -108,3 +108,35 @@ def test_surface_refusals():
     p.transformed = True
     with pytest.raises(ValueError):
         bo.assemble(p)
+
+
+def test_shell_matrix_formalism_limits():
+    """Diffusion on a spherical shell: the narrow-pulse long-time limit of the
+    matrix formalism is [sin(kR) / (kR)]^2, the squared mean of e^{ikz} over the
+    sphere; no gradient leaves 1; truncation converges."""
+    from oracle import mfshell
+    R = 5.0
+    for k in (0.3, 0.8):
+        s = mfshell.mf_shell_signal(R, 2e-3, k, 1.0, 2e6)
+        want = (math.sin(k * R) / (k * R)) ** 2
+        assert abs(s - want) < 2e-3 * want, (k, s, want)
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+    assert abs(mfshell.mf_shell_signal(R, 2e-3, 0.0, 2500.0, 5000.0) - 1.0) < 1e-12
+    assert abs(mfshell.mf_shell_signal(R, 2e-3, q, 2500.0, 5000.0, 30) -
+               mfshell.mf_shell_signal(R, 2e-3, q, 2500.0, 5000.0, 60)) < 1e-12
+
+
+def test_icosphere_converges_to_shell_matrix_formalism_second_order():
+    """Surface triangles on refined icospheres with dt halved together: the
+    signal per area approaches the shell's matrix-formalism value at second
+    order (error ratios about 4)."""
+    from oracle import mfshell
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+    ref = mfshell.mf_shell_signal(5.0, 2e-3, q, 2500.0, 5000.0).real
+    errs = []
+    for level, dt in ((2, 50.0), (3, 25.0), (4, 12.5)):
+        p = geom.spherical_shell(level=level, R=5.0, dt=dt, bvals=(1000.0,), dirs=((0.0, 0.0, 1.0),))
+        X = p.xyz[p.tets]
+        area = 0.5 * np.linalg.norm(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]), axis=1).sum()
+        errs.append(abs(oracle.run(p)[0].real / area - ref))
+    assert 3.3 < errs[0] / errs[1] < 4.7 and 3.3 < errs[1] / errs[2] < 4.7, errs
