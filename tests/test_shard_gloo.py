@@ -81,7 +81,8 @@ def test_two_gloo_ranks_gather_equals_unsharded():
 
 def _forest():
     import geom
-    return [geom.dendrite_tree(seed=s, n_stems=2, depth=2, length=(6.0, 12.0)) for s in range(5)]
+    return [geom.dendrite_tree(seed=s, n_stems=2, depth=2, length=(6.0, 12.0), bvals=(1000.0,), n_dir=2)
+            for s in range(5)]
 
 
 def _forest_worker(rank, world, port, q):
