@@ -450,6 +450,34 @@ def polar_disk(m: int, R: float = 5.0, dt: float = 50.0, D: float = 2e-3, bvals=
                    np.asarray(bvals, dtype=np.float64))
 
 
+def periodic_cylinder(m: int, nz: int = 2, R: float = 5.0, H: float = 2.0, dt: float = 50.0, D: float = 2e-3,
+                      bvals=(1000.0,), dirs=((1.0, 0.0, 0.0),)):
+    """3-D: the polar disk of `polar_disk` extruded into nz layers over a height
+    H that is periodic in z (transformed frame), each prism cut into three
+    tetrahedra by the order of its triangle's global vertex ids (so shared
+    quadrilateral faces are cut the same way from both sides).  For gradients
+    across the axis the signal is the disk's."""
+    d = polar_disk(m, R=R)
+    nn = len(d.xyz)
+    z = np.linspace(0.0, H, nz + 1)
+    xyz = np.concatenate([np.column_stack([d.xyz[:, :2], np.full(nn, zk)]) for zk in z])
+    tets = []
+    for tri in np.sort(d.tets, axis=1):
+        a, b, c = tri
+        for k in range(nz):
+            lo, up = k * nn, (k + 1) * nn
+            tets += [(a + lo, b + lo, c + lo, a + up), (b + lo, c + lo, a + up, b + up),
+                     (c + lo, a + up, b + up, c + up)]
+    tets = np.array(tets, dtype=np.int32)
+    X = xyz[tets]
+    vol = np.einsum("ij,ij->i", X[:, 1] - X[:, 0], np.cross(X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]))
+    tets[vol < 0] = tets[vol < 0][:, [0, 1, 3, 2]]
+    lo, hi = np.array([-R, -R, 0.0]), np.array([R, R, H])
+    return Problem("periodic_cylinder", xyz, tets, np.zeros(len(tets), np.int32), np.array([D]),
+                   np.array([NO_MEMBRANE]), 4, lo, hi, dt, 2500.0, 5000.0, 7500.0,
+                   np.asarray(dirs, dtype=np.float64), np.asarray(bvals, dtype=np.float64), transformed=True)
+
+
 def layered_disk(n: int = 40, radii=(5.0, 7.5, 10.0), dt: float = 100.0, D: float = 3e-3, kappa: float = 1e-5,
                  rho=(0.0, 1.0, 0.0), bvals=(0.0, 1000.0, 4000.0), dirs=((1.0, 0.0, 0.0),)):
     """2-D: concentric layers r < radii[0], ..., r < radii[-1] (one compartment

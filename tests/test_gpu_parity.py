@@ -802,3 +802,20 @@ def test_icosphere_against_oracle_and_matrix_formalism(sim_cls, bt):
         assert abs(S[0].real / area - mf) < 2e-4
     finally:
         sim.close()
+
+
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_periodic_cylinder_against_oracle(sim_cls, bt, mode):
+    """Tetrahedra of a disk extruded along a periodic z axis (transformed frame,
+    curved Neumann wall): signals against the oracle."""
+    p = geom.periodic_cylinder(12, dt=25.0, dirs=((0.6, 0.8, 0.0), (0.0, 0.0, 1.0)), bvals=(1000.0, 3000.0))
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S, err, stat, st = sim.run(m)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()

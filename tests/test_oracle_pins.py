@@ -382,3 +382,20 @@ def test_step_average_reading_keeps_second_order():
         assert abs(F[-1]) < 1e-9
     assert 1.7 < lit[0] / lit[1] < 2.3 and 1.7 < lit[1] / lit[2] < 2.3, lit
     assert 3.5 < avg[0] / avg[1] < 4.7 and 3.5 < avg[1] / avg[2] < 4.7, avg
+
+
+def test_periodic_cylinder_transformed_converges_to_disk_matrix_formalism():
+    """3-D tetrahedra of a disk extruded along a periodic z axis (transformed
+    frame), gradient across the axis: the signal per volume approaches the
+    disk's matrix-formalism value at second order as h and dt halve together
+    (a curved boundary, unlike the box pins)."""
+    from oracle import mfdisk
+    q = float(oracle.q_from_b(1000.0, 2500.0, 5000.0))
+    ref = mfdisk.mf_disk_signal(5.0, 2e-3, q, 2500.0, 5000.0).real
+    errs = []
+    for m, dt in ((6, 50.0), (12, 25.0), (24, 12.5)):
+        p = geom.periodic_cylinder(m, dt=dt, dirs=((0.6, 0.8, 0.0),))
+        X = p.xyz[p.tets]
+        vol = np.einsum("ij,ij->i", X[:, 1] - X[:, 0], np.cross(X[:, 2] - X[:, 0], X[:, 3] - X[:, 0])).sum() / 6.0
+        errs.append(abs(oracle.run(p)[0].real / vol - ref))
+    assert 3.3 < errs[0] / errs[1] < 4.7 and 3.3 < errs[1] / errs[2] < 4.7, errs
