@@ -819,3 +819,22 @@ def test_periodic_cylinder_against_oracle(sim_cls, bt, mode):
         assert rel(S, ref).max() < tol, rel(S, ref)
     finally:
         sim.close()
+
+
+@pytest.mark.parametrize("kind", ["pgse", "double_pgse", "cos_ogse", "sin_ogse", "trapezoid", "double_trapezoid"])
+def test_six_profiles_in_a_disk(sim_cls, bt, kind):
+    """Section 4's six temporal profiles in a disk of radius 5 um with
+    delta = Delta = 10 ms, mixed mode, against the oracle."""
+    TE = {"pgse": 20000.0, "double_pgse": 40000.0, "cos_ogse": 20000.0, "sin_ogse": 20000.0,
+          "trapezoid": 20000.0, "double_trapezoid": 40000.0}
+    p = geom.polar_disk(12, dt=100.0, bvals=(1000.0, 3000.0), dirs=((1.0, 0.0, 0.0), (0.6, 0.8, 0.0)))
+    p.delta, p.Delta, p.TE = 10000.0, 10000.0, TE[kind]
+    p.profile = {"kind": kind, "n_periods": 1, "ramp": 1000.0}
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        S, err, stat, st = sim.run(bt.BT_MODE_MIXED)
+        assert np.all(stat == 0)
+        assert rel(S, ref).max() < TOL_MIXED, rel(S, ref)
+    finally:
+        sim.close()

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import geom
+import oracle
 from oracle import btoracle as bo
 from oracle import profiles as op
 from paper_1908_01719_gb300 import profiles as lp
@@ -84,3 +85,21 @@ def test_free_periodic_box_exact_and_limit(kind):
         assert abs(S - prod) < 1e-12
         errs.append(abs(S.real - math.exp(-b * D)))
     assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_ogse_decays_faster_in_a_disk():
+    """Section 4's comparison of six profiles in a disk of radius 5 um with
+    delta = Delta = 10 ms: at equal b the OGSE signals decay faster than the
+    PGSE, double PGSE and trapezoidal ones (shorter effective diffusion time,
+    less restriction)."""
+    TE = {"pgse": 20000.0, "double_pgse": 40000.0, "cos_ogse": 20000.0, "sin_ogse": 20000.0,
+          "trapezoid": 20000.0, "double_trapezoid": 40000.0}
+    S = {}
+    for kind, te in TE.items():
+        p = geom.polar_disk(8, dt=100.0, bvals=(1000.0, 3000.0))
+        p.delta, p.Delta, p.TE = 10000.0, 10000.0, te
+        p.profile = {"kind": kind, "n_periods": 1, "ramp": 1000.0}
+        S[kind] = oracle.run(p).real
+    for og in ("cos_ogse", "sin_ogse"):
+        for other in ("pgse", "double_pgse", "trapezoid", "double_trapezoid"):
+            assert np.all(S[og] < S[other]), (og, other, S[og], S[other])
