@@ -838,3 +838,23 @@ def test_six_profiles_in_a_disk(sim_cls, bt, kind):
         assert rel(S, ref).max() < TOL_MIXED, rel(S, ref)
     finally:
         sim.close()
+
+
+@pytest.mark.parametrize("t2", ["none", "inner", "outer"])
+def test_three_layer_t2_cross_section(sim_cls, bt, t2):
+    """Section 4's T2 study of a three-layer cylinder with the gradient across
+    its axis, as its cross-section (the three-layer disk): T2 = 40 ms in no
+    layer, in the inner one, or in the two outer ones; delta = Delta = 10 ms;
+    mixed mode against the oracle."""
+    inv = {"none": (0.0, 0.0, 0.0), "inner": (1 / 40000.0, 0.0, 0.0), "outer": (0.0, 1 / 40000.0, 1 / 40000.0)}[t2]
+    p = geom.layered_disk(n=24, rho=(1.0, 1.0, 1.0), bvals=(0.0, 2000.0, 4000.0), dirs=((0.0, 1.0, 0.0),))
+    p.delta, p.Delta, p.TE = 10000.0, 10000.0, 20000.0
+    p.inv_T2 = np.array(inv)
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        S, err, stat, st = sim.run(bt.BT_MODE_MIXED)
+        assert np.all(stat == 0)
+        assert rel(S, ref).max() < TOL_MIXED, rel(S, ref)
+    finally:
+        sim.close()
