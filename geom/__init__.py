@@ -504,6 +504,56 @@ def layered_disk(n: int = 40, radii=(5.0, 7.5, 10.0), dt: float = 100.0, D: floa
     return p
 
 
+def _keep_elements(xyz, tets, keep):
+    """The elements `keep` and the nodes they use, renumbered."""
+    tets = tets[keep]
+    used = np.unique(tets)
+    new_id = np.full(len(xyz), -1, np.int64)
+    new_id[used] = np.arange(len(used))
+    return xyz[used], new_id[tets].astype(np.int32)
+
+
+def layered_sphere(n: int = 16, radii=(5.0, 7.5, 10.0), dt: float = 100.0, D=(3e-3, 1e-3, 3e-3),
+                   kappa: float = 1e-5, bvals=(1000.0, 4000.0), dirs=((1.0, 0.0, 0.0),)):
+    """3-D: concentric shells r < radii[0] < ... < radii[-1] (one compartment
+    each, permeable membranes, Neumann outside) cut from an n^3 Kuhn grid of
+    the cube [-R, R]^3 by tetrahedron centroids; the paper's three-layer
+    sphere with its per-layer diffusivities and neuron PGSE (100 us grid)."""
+    R = radii[-1]
+    xyz, tets = kuhn_grid(n, n, n, np.full(3, -R), np.full(3, R))
+    r = np.linalg.norm(xyz[tets].mean(axis=1), axis=1)
+    xyz, tets = _keep_elements(xyz, tets, r < R)
+    r = np.linalg.norm(xyz[tets].mean(axis=1), axis=1)
+    lab = np.searchsorted(np.asarray(radii[:-1], float), r, side="right").astype(np.int32)
+    nc = len(radii)
+    return Problem("layered_sphere", xyz, tets, lab, np.asarray(D, float), np.full(nc, kappa), 0, np.full(3, -R),
+                   np.full(3, R), dt, 10600.0, 43100.0, 53700.0, np.asarray(dirs, dtype=np.float64),
+                   np.asarray(bvals, dtype=np.float64))
+
+
+def layered_torus(h: float = 2.0, R_ring: float = 20.0, radii=(5.0, 7.5, 10.0), dt: float = 100.0,
+                  D=(3e-3, 1e-3, 3e-3), kappa: float = 1e-5, bvals=(1000.0, 4000.0), dirs=((1.0, 0.0, 0.0),)):
+    """3-D: a torus whose tube (distance rho to the circle of radius R_ring in
+    the xy plane) is layered rho < radii[0] < ... < radii[-1], cut from a
+    Kuhn grid of spacing about h; the paper's three-layer torus."""
+    a = radii[-1]
+    lo = np.array([-(R_ring + a), -(R_ring + a), -a])
+    hi = -lo
+    nx = int(round((hi[0] - lo[0]) / h))
+    nz = int(round((hi[2] - lo[2]) / h))
+    xyz, tets = kuhn_grid(nx, nx, nz, lo, hi)
+
+    def tube_dist(c):
+        return np.hypot(np.hypot(c[:, 0], c[:, 1]) - R_ring, c[:, 2])
+    rho = tube_dist(xyz[tets].mean(axis=1))
+    xyz, tets = _keep_elements(xyz, tets, rho < a)
+    rho = tube_dist(xyz[tets].mean(axis=1))
+    lab = np.searchsorted(np.asarray(radii[:-1], float), rho, side="right").astype(np.int32)
+    nc = len(radii)
+    return Problem("layered_torus", xyz, tets, lab, np.asarray(D, float), np.full(nc, kappa), 0, lo, hi, dt,
+                   10600.0, 43100.0, 53700.0, np.asarray(dirs, dtype=np.float64), np.asarray(bvals, dtype=np.float64))
+
+
 def free_periodic_square(n: int = 8, L: float = 10.0, dt: float = 50.0, D: float = 2e-3,
                          dirs=((1.0, 0.0, 0.0),), bvals=(1000.0,)):
     """2-D periodic square without compartments (free diffusion)."""

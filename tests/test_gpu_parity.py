@@ -858,3 +858,32 @@ def test_three_layer_t2_cross_section(sim_cls, bt, t2):
         assert rel(S, ref).max() < TOL_MIXED, rel(S, ref)
     finally:
         sim.close()
+
+
+def _three_layer(kind):
+    """Section 4's three-layer structures (radii 5, 7.5, 10 um; torus ring
+    radius 20 um) with per-layer diffusivities 3e-3, 1e-3, 3e-3 and permeable
+    membranes; a short PGSE keeps the oracle quick."""
+    if kind == "disk":
+        p = geom.layered_disk(n=24, D=3e-3, rho=(1.0, 1.0, 1.0), bvals=(1000.0, 4000.0))
+        p.D_cmpt = np.array([3e-3, 1e-3, 3e-3])
+    elif kind == "sphere":
+        p = geom.layered_sphere(n=12)
+    else:
+        p = geom.layered_torus(h=3.0)
+    p.dt, p.delta, p.Delta, p.TE = 50.0, 2500.0, 5000.0, 7500.0
+    p.dirs = np.array([[1.0, 0.0, 0.0], [0.0, 0.6, 0.8]]) if kind != "disk" else np.array([[1.0, 0.0, 0.0]])
+    return p
+
+
+@pytest.mark.parametrize("kind", ["disk", "sphere", "torus"])
+def test_three_layer_structures(sim_cls, bt, kind):
+    p = _three_layer(kind)
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        S, err, stat, st = sim.run(bt.BT_MODE_MIXED)
+        assert np.all(stat == 0)
+        assert rel(S, ref).max() < TOL_MIXED, rel(S, ref)
+    finally:
+        sim.close()

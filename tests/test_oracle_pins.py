@@ -399,3 +399,16 @@ def test_periodic_cylinder_transformed_converges_to_disk_matrix_formalism():
         vol = np.einsum("ij,ij->i", X[:, 1] - X[:, 0], np.cross(X[:, 2] - X[:, 0], X[:, 3] - X[:, 0])).sum() / 6.0
         errs.append(abs(oracle.run(p)[0].real / vol - ref))
     assert 3.3 < errs[0] / errs[1] < 4.7 and 3.3 < errs[1] / errs[2] < 4.7, errs
+
+
+@pytest.mark.parametrize("maker", [lambda: geom.layered_sphere(n=8, bvals=(0.0,)),
+                                   lambda: geom.layered_torus(h=4.0, bvals=(0.0,))])
+def test_three_layer_structures_conserve_at_zero_gradient(maker):
+    """Section 4's three-layer sphere and torus, layers of different D with
+    permeable membranes: at g = 0 the signal stays the volume at every step."""
+    p = maker()
+    p.dt, p.delta, p.Delta, p.TE = 50.0, 1000.0, 2000.0, 3000.0
+    X = p.xyz[p.tets]
+    vol = np.abs(np.einsum("ij,ij->i", X[:, 1] - X[:, 0], np.cross(X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]))).sum() / 6
+    S, H = oracle.run(p, return_history=True)
+    assert np.max(np.abs(H[0] - vol)) < 1e-10 * vol
