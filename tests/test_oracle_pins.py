@@ -412,3 +412,17 @@ def test_three_layer_structures_conserve_at_zero_gradient(maker):
     vol = np.abs(np.einsum("ij,ij->i", X[:, 1] - X[:, 0], np.cross(X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]))).sum() / 6
     S, H = oracle.run(p, return_history=True)
     assert np.max(np.abs(H[0] - vol)) < 1e-10 * vol
+
+
+def test_stored_signals_still_match_the_oracle():
+    """The stored oracle signals the GPU tests read must still be what the
+    oracle computes (cheapest stored case, every RHS, with its fingerprint)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cfg2_n12_dt100.json")
+    g = json.load(open(path))
+    p = geom.cfg2(**g["kwargs"])
+    assert len(p.xyz) == g["fingerprint"]["n_nodes"] and len(p.tets) == g["fingerprint"]["n_tets"]
+    S = oracle.run(p, rhs=g["rhs"])
+    ref = np.array(g["S_re"]) + 1j * np.array(g["S_im"])
+    assert np.max(np.abs(S - ref) / np.abs(ref)) < 1e-12
