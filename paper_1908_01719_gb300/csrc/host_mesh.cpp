@@ -299,32 +299,45 @@ void find_interface_faces(HostMesh& m) {
   m.n_face = (int64_t)m.face_ta.size();
 }
 
-void build_pattern(HostMesh& m) {
+// Element and face incidence of every dof: the elements (faces) holding it,
+// one entry per (element, local vertex) occurrence, in increasing element order.
+struct Incidence {
+  std::vector<int64_t> tp, fp;  // [n_dof + 1] offsets
+  std::vector<int32_t> ti, fi;  // element (face) ids
+};
+
+Incidence build_incidence(const HostMesh& m) {
   const int64_t nd = m.n_dof, nt = m.n_tets, nf = m.n_face;
   const int nv = m.nv, nfd = 2 * (nv - 1);
-  // dof -> elements incidence (elements, then faces)
-  std::vector<int64_t> tp(nd + 1, 0), fp(nd + 1, 0);
-  for (int64_t i = 0; i < nv * nt; ++i) tp[m.tet_dof[i] + 1]++;
-  for (int64_t i = 0; i < nfd * nf; ++i) fp[m.face_dof[i] + 1]++;
+  Incidence inc;
+  inc.tp.assign(nd + 1, 0);
+  inc.fp.assign(nd + 1, 0);
+  for (int64_t i = 0; i < nv * nt; ++i) inc.tp[m.tet_dof[i] + 1]++;
+  for (int64_t i = 0; i < nfd * nf; ++i) inc.fp[m.face_dof[i] + 1]++;
   for (int64_t d = 0; d < nd; ++d) {
-    tp[d + 1] += tp[d];
-    fp[d + 1] += fp[d];
+    inc.tp[d + 1] += inc.tp[d];
+    inc.fp[d + 1] += inc.fp[d];
   }
-  std::vector<int32_t> ti(nv * nt), fi(nfd * nf);
-  {
-    std::vector<int64_t> pos(tp.begin(), tp.end() - 1);
-    for (int64_t t = 0; t < nt; ++t)
-      for (int a = 0; a < nv; ++a) ti[pos[m.tet_dof[nv * t + a]]++] = (int32_t)t;
-    std::vector<int64_t> pf(fp.begin(), fp.end() - 1);
-    for (int64_t f = 0; f < nf; ++f)
-      for (int a = 0; a < nfd; ++a) fi[pf[m.face_dof[nfd * f + a]]++] = (int32_t)f;
-  }
+  inc.ti.resize(nv * nt);
+  inc.fi.resize(nfd * nf);
+  std::vector<int64_t> pos(inc.tp.begin(), inc.tp.end() - 1);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int a = 0; a < nv; ++a) inc.ti[pos[m.tet_dof[nv * t + a]]++] = (int32_t)t;
+  std::vector<int64_t> pf(inc.fp.begin(), inc.fp.end() - 1);
+  for (int64_t f = 0; f < nf; ++f)
+    for (int a = 0; a < nfd; ++a) inc.fi[pf[m.face_dof[nfd * f + a]]++] = (int32_t)f;
+  return inc;
+}
+
+void build_pattern(HostMesh& m, const Incidence& inc) {
+  const int64_t nd = m.n_dof;
+  const int nv = m.nv, nfd = 2 * (nv - 1);
   auto row_cols = [&](int64_t d, std::vector<int32_t>& buf) {
     buf.clear();
-    for (int64_t k = tp[d]; k < tp[d + 1]; ++k)
-      for (int a = 0; a < nv; ++a) buf.push_back(m.tet_dof[nv * (int64_t)ti[k] + a]);
-    for (int64_t k = fp[d]; k < fp[d + 1]; ++k)
-      for (int a = 0; a < nfd; ++a) buf.push_back(m.face_dof[nfd * (int64_t)fi[k] + a]);
+    for (int64_t k = inc.tp[d]; k < inc.tp[d + 1]; ++k)
+      for (int a = 0; a < nv; ++a) buf.push_back(m.tet_dof[nv * (int64_t)inc.ti[k] + a]);
+    for (int64_t k = inc.fp[d]; k < inc.fp[d + 1]; ++k)
+      for (int a = 0; a < nfd; ++a) buf.push_back(m.face_dof[nfd * (int64_t)inc.fi[k] + a]);
     std::sort(buf.begin(), buf.end());
     buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
   };
@@ -349,44 +362,53 @@ void build_pattern(HostMesh& m) {
   });
 }
 
-inline int64_t slot_of(const HostMesh& m, int32_t r, int32_t c) {
-  const int32_t* b = m.col.data() + m.row_ptr[r];
-  const int32_t* e = m.col.data() + m.row_ptr[r + 1];
-  return m.row_ptr[r] + (std::lower_bound(b, e, c) - b);
+// Slot-sorted contribution lists for one kind of entity (elements with w
+// nodes, or interface faces with w dofs), built row by row in parallel: the
+// slots of row d receive entries only from entities holding dof d.  Walking
+// those in increasing entity order, and each entity's local rows and columns
+// in increasing order, lists every slot's entries by increasing code
+// w^2 entity + w a + b, so each slot sums its entries in a fixed order and the
+// assembly is deterministic.  Row d's entries start at (occurrences before d) x w.
+void slot_lists(const HostMesh& m, const std::vector<int64_t>& ip, const std::vector<int32_t>& ids,
+                const std::vector<int32_t>& edof, int w, std::vector<int64_t>& cptr, std::vector<int32_t>& codes) {
+  const int64_t nd = m.n_dof;
+  cptr.assign(m.nnz + 1, 0);
+  codes.resize(ip[nd] * w);
+  cptr[m.nnz] = ip[nd] * w;
+  parallel_for(nd, [&](int64_t b, int64_t e) {
+    std::vector<int32_t> cnt, lslot, lcode;
+    for (int64_t d = b; d < e; ++d) {
+      const int64_t r0 = m.row_ptr[d], rl = m.row_ptr[d + 1] - r0;
+      const int32_t* cols = m.col.data() + r0;
+      cnt.assign(rl + 1, 0);
+      lslot.clear();
+      lcode.clear();
+      for (int64_t k = ip[d]; k < ip[d + 1];) {
+        const int32_t t = ids[k];
+        while (k < ip[d + 1] && ids[k] == t) ++k;  // an entity holding d at several local vertices
+        const int32_t* ed = &edof[(int64_t)w * t];
+        for (int a = 0; a < w; ++a) {
+          if (ed[a] != d) continue;
+          for (int c = 0; c < w; ++c) {
+            const int32_t s = (int32_t)(std::lower_bound(cols, cols + rl, ed[c]) - cols);
+            lslot.push_back(s);
+            lcode.push_back(w * w * t + w * a + c);
+            cnt[s + 1]++;
+          }
+        }
+      }
+      for (int64_t s = 0; s < rl; ++s) cnt[s + 1] += cnt[s];
+      const int64_t base = ip[d] * w;
+      for (int64_t s = 0; s < rl; ++s) cptr[r0 + s] = base + cnt[s];
+      for (size_t q = 0; q < lslot.size(); ++q) codes[base + cnt[lslot[q]]++] = lcode[q];
+    }
+  });
 }
 
-// Counting sort of element entries by slot; within a slot the entries keep
-// increasing element order, so the per-slot sums are deterministic.
-void build_contributions(HostMesh& m) {
-  const int64_t nt = m.n_tets, nf = m.n_face, nnz = m.nnz;
-  const int nv = m.nv, n2 = nv * nv, nfd = 2 * (nv - 1), nf2 = nfd * nfd;
-  std::vector<int64_t> tslot(n2 * nt);
-  parallel_for(nt, [&](int64_t b, int64_t e) {
-    for (int64_t t = b; t < e; ++t)
-      for (int i = 0; i < nv; ++i)
-        for (int j = 0; j < nv; ++j)
-          tslot[n2 * t + nv * i + j] = slot_of(m, m.tet_dof[nv * t + i], m.tet_dof[nv * t + j]);
-  });
-  m.tc_ptr.assign(nnz + 1, 0);
-  for (int64_t k = 0; k < n2 * nt; ++k) m.tc_ptr[tslot[k] + 1]++;
-  for (int64_t s = 0; s < nnz; ++s) m.tc_ptr[s + 1] += m.tc_ptr[s];
-  m.tc.resize(n2 * nt);
-  {
-    std::vector<int64_t> pos(m.tc_ptr.begin(), m.tc_ptr.end() - 1);
-    for (int64_t k = 0; k < n2 * nt; ++k) m.tc[pos[tslot[k]]++] = (int32_t)k;
-  }
-  std::vector<int64_t>().swap(tslot);
-  m.fc_ptr.assign(nnz + 1, 0);
-  std::vector<int64_t> fslot(nf2 * nf);
-  for (int64_t f = 0; f < nf; ++f)
-    for (int a = 0; a < nfd; ++a)
-      for (int b = 0; b < nfd; ++b)
-        fslot[nf2 * f + nfd * a + b] = slot_of(m, m.face_dof[nfd * f + a], m.face_dof[nfd * f + b]);
-  for (int64_t k = 0; k < nf2 * nf; ++k) m.fc_ptr[fslot[k] + 1]++;
-  for (int64_t s = 0; s < nnz; ++s) m.fc_ptr[s + 1] += m.fc_ptr[s];
-  m.fc.resize(nf2 * nf);
-  std::vector<int64_t> pos(m.fc_ptr.begin(), m.fc_ptr.end() - 1);
-  for (int64_t k = 0; k < nf2 * nf; ++k) m.fc[pos[fslot[k]]++] = (int32_t)k;
+void build_contributions(HostMesh& m, const Incidence& inc) {
+  const int nv = m.nv, nfd = 2 * (nv - 1);
+  slot_lists(m, inc.tp, inc.ti, m.tet_dof, nv, m.tc_ptr, m.tc);
+  slot_lists(m, inc.fp, inc.fi, m.face_dof, nfd, m.fc_ptr, m.fc);
 }
 
 }  // namespace
@@ -672,12 +694,13 @@ int build_host_mesh(HostMesh& m, std::string& msg) {
     msg = "pattern too large";
     return BT_EINVAL;
   }
-  build_pattern(m);
+  const Incidence inc = build_incidence(m);
+  build_pattern(m, inc);
   if (m.nnz >= (int64_t(1) << 31) || 36 * m.n_face >= (int64_t(1) << 31)) {
     msg = "pattern too large for 32-bit indexing";
     return BT_EINVAL;
   }
-  build_contributions(m);
+  build_contributions(m, inc);
   return BT_OK;
 }
 
