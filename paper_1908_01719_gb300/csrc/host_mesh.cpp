@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <tuple>
 #include <thread>
@@ -253,20 +254,31 @@ void find_interface_faces(HostMesh& m) {
     int32_t tet;
     int8_t lf;
   };
-  std::vector<Cand> cand;
-  for (int64_t t = 0; t < m.n_tets; ++t) {
-    for (int f = 0; f < nv; ++f) {
-      std::array<int32_t, 3> k = {-1, -1, -1};
-      bool ok = true;
-      for (int a = 0; a < fs; ++a) {
-        k[a] = m.master[m.tets[nv * t + LOC(f, a)]];
-        ok = ok && multi[k[a]];
+  // candidates gathered by element chunks in parallel; the sort below orders
+  // them by (key, element), which no gathering order can change
+  std::mutex mu;
+  std::vector<std::pair<int64_t, std::vector<Cand>>> parts;
+  parallel_for(m.n_tets, [&](int64_t b, int64_t e) {
+    std::vector<Cand> local;
+    for (int64_t t = b; t < e; ++t) {
+      for (int f = 0; f < nv; ++f) {
+        std::array<int32_t, 3> k = {-1, -1, -1};
+        bool ok = true;
+        for (int a = 0; a < fs; ++a) {
+          k[a] = m.master[m.tets[nv * t + LOC(f, a)]];
+          ok = ok && multi[k[a]];
+        }
+        if (!ok) continue;
+        std::sort(k.begin(), k.end());
+        local.push_back({k, (int32_t)t, (int8_t)f});
       }
-      if (!ok) continue;
-      std::sort(k.begin(), k.end());
-      cand.push_back({k, (int32_t)t, (int8_t)f});
     }
-  }
+    std::lock_guard<std::mutex> lk(mu);
+    parts.emplace_back(b, std::move(local));
+  });
+  std::sort(parts.begin(), parts.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  std::vector<Cand> cand;
+  for (auto& pt : parts) cand.insert(cand.end(), pt.second.begin(), pt.second.end());
   std::sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
     return a.key != b.key ? a.key < b.key : a.tet < b.tet;
   });
