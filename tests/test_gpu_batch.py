@@ -74,27 +74,3 @@ def test_seeded_packings_batch_equals_separate_runs(sim_cls, bt):
             s1.close()
         assert np.all(st == 0)
         assert np.max(np.abs(S[g * R:(g + 1) * R] - Sg) / np.abs(Sg)) < 1e-6, g
-
-
-def test_dendrite_forest_full_size_sampled_against_oracle(sim_cls, bt):
-    """The 1-D workload at full size (64 seeded dendrite trees as one uneven
-    batch, 537 steps, 9 RHS each), mixed mode as benchmarked: sampled trees
-    against the oracle, and every tree's b = 0 signals equal its length
-    (conservation, any size)."""
-    trees = [geom.dendrite_tree(seed=s) for s in range(64)]
-    u = geom.union(trees, name="trees1d")
-    sim = sim_cls(u)
-    try:
-        S, err, stat, _ = sim.run(bt.BT_MODE_MIXED)
-    finally:
-        sim.close()
-    assert np.all(stat == 0)
-    R = trees[0].n_rhs
-    for g in (0, 21, 42, 63):
-        ref = oracle.run(trees[g])
-        assert np.max(np.abs(S[g * R:(g + 1) * R] - ref) / np.abs(ref)) < 1e-6, g
-    nb = len(trees[0].bvals)
-    for g, t in enumerate(trees):
-        length = np.linalg.norm(t.xyz[t.tets[:, 1]] - t.xyz[t.tets[:, 0]], axis=1).sum()
-        s0 = S[g * R:(g + 1) * R][::nb]                    # b = 0 of each direction
-        assert np.max(np.abs(s0 - length)) < 1e-6 * length, g
