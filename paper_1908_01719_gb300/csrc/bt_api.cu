@@ -114,7 +114,7 @@ static bt_status upload_mesh_nv(bt_ctx* ctx, int nv, int64_t n_nodes, const doub
       n_cmpt <= 0 || periodic_mask > 7)
     return fail(ctx, BT_EINVAL, "bt_upload_mesh: invalid argument");
   // the 32-bit index limits, checked before any caller array is read
-  if (n_nodes >= (int64_t(1) << 31) || n_tets * 16 >= (int64_t(1) << 31))
+  if (n_nodes >= (int64_t(1) << 31) || n_tets >= (int64_t(1) << 27))
     return fail(ctx, BT_EINVAL, "bt_upload_mesh: mesh too large for 32-bit element indexing");
   HostMesh& m = ctx->mesh;
   m = HostMesh();

@@ -74,7 +74,7 @@ int validate(const HostMesh& m, std::string& msg) {
     msg = "a surface mesh has triangles and no periodic axes";
     return BT_EINVAL;
   }
-  if (m.n_nodes >= (int64_t(1) << 31) || m.n_tets * 16 >= (int64_t(1) << 31)) {
+  if (m.n_nodes >= (int64_t(1) << 31) || m.n_tets >= (int64_t(1) << 27)) {
     msg = "mesh too large for 32-bit element indexing";
     return BT_EINVAL;
   }

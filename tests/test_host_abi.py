@@ -338,7 +338,7 @@ def test_oversize_counts_refused_before_reading(bt):
     L = bt.lib()
     ctx = bt.bt_create(-1)
     try:
-        for nn, nt in [(1 << 31, len(tets)), (len(xyz), 1 << 28), (1 << 40, 1 << 40)]:
+        for nn, nt in [(1 << 31, len(tets)), (len(xyz), 1 << 28), (1 << 40, 1 << 40), (len(xyz), 1 << 60)]:
             st = L.bt_upload_mesh(ctx, nn, ptr(xyz), nt, ptr(tets), ptr(tc), 1, ptr(D), ptr(K), 0, ptr(lo), ptr(hi))
             assert st == bt.BT_EINVAL
             st = L.bt_upload_mesh_2d(ctx, nn, ptr(xyz), nt, ptr(tets), ptr(tc), 1, ptr(D), ptr(K), 0, ptr(lo),
