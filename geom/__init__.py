@@ -564,6 +564,23 @@ def free_periodic_square(n: int = 8, L: float = 10.0, dt: float = 50.0, D: float
                    np.asarray(dirs, dtype=np.float64), np.asarray(bvals, dtype=np.float64), transformed=True)
 
 
+def sheared_box(n: int = 6, L: float = 8.0, eps: float = 0.3, dt: float = 50.0, D: float = 2e-3,
+                dirs=((1.0, 0.0, 0.0),), bvals=(1000.0,)):
+    """A free box [0, L]^3 meshed without periodicity whose x sides do not
+    match: every node moves along y by eps sin(pi y / L) x / L, so nodes stay
+    on their box planes, the x = 0 side is untouched and the x = L side's
+    nodes slide along y (a shear smaller than half a cell keeps every
+    tetrahedron positive)."""
+    p = free_periodic_box(n=n, L=L, dt=dt, D=D, dirs=dirs, bvals=bvals)
+    x, y = p.xyz[:, 0], p.xyz[:, 1]
+    p.xyz = p.xyz.copy()
+    p.xyz[:, 1] = y + eps * np.sin(np.pi * y / L) * x / L
+    p.periodic_mask = 0
+    p.transformed = False
+    p.name = "sheared_box"
+    return p
+
+
 def line_segments(n: int, L: float = 40.0, direction=(1.0, 0.0, 0.0), dt: float = 50.0, D: float = 2e-3,
                   bvals=(1000.0,), dirs=((1.0, 0.0, 0.0),), delta: float = 2500.0, Delta: float = 5000.0):
     """1-D manifold: a straight fibre of length L along `direction`, centred at

@@ -12,8 +12,8 @@ face-mass coupling of each face with its partner face times e^{+-i theta^n}:
   L_n = M + th dt (A_n + kappa_e B),  rhs = R_n u^{n-1} + th dt kappa_e C_n u^{n-1}.
 Appendix B weighs the implicit part by theta and the explicit part by
 (1 - theta); both are weighted by theta here (equal at theta = 1/2, and
-consistent for every theta).  The partner face is found by shifting the
-master face by L_k along axis k: the mesh must match across the box.
+consistent for every theta).  The partner value is the P1 field of the opposite side at the node shifted by
++-L_k along axis k (the master/slave projection), so the sides need not match.
 kappa_e defaults to max_c D_c / h (the paper's Nitsche-consistent choice) with
 h = (d! x mean element measure)^(1/d), the Kuhn cell edge in d = 3 or 2.
 In 2-D (triangles in the xy plane) the faces are boundary edges and only the
@@ -72,9 +72,44 @@ def face_mass(Xf):
     return meas / (fs * (fs + 1)) * (np.ones((fs, fs)) + np.eye(fs))
 
 
+def _tangential(p, k):
+    """The coordinates along a side of axis k: the other two axes in 3-D, the
+    other in-plane axis for a 2-D mesh."""
+    if p.tets.shape[1] == 3:
+        return [1] if k == 0 else [0]
+    return [a for a in range(3) if a != k]
+
+
+def _locate(side_faces, y, tang):
+    """(dofs, barycentric weights) of the face of `side_faces` containing the
+    point y, by its tangential coordinates; the face with the largest smallest
+    weight wins, so points on shared edges and vertices are found."""
+    best = None
+    for Xf, dofs, _ in side_faces:
+        P = Xf[:, tang]
+        z = y[tang]
+        if len(tang) == 2:
+            T = np.column_stack([P[1] - P[0], P[2] - P[0]])
+            l12 = np.linalg.solve(T, z - P[0])
+            lam = np.array([1.0 - l12.sum(), l12[0], l12[1]])
+        else:
+            s = (z[0] - P[0, 0]) / (P[1, 0] - P[0, 0])
+            lam = np.array([1.0 - s, s])
+        if best is None or lam.min() > best[0]:
+            best = (lam.min(), dofs, lam)
+    if best is None or best[0] < -1e-9:
+        raise ValueError("a node's partner point lies outside the opposite side of the box")
+    return best[1], best[2]
+
+
 def operators(p, asm, axes, kappa_e=None):
     """(B, pairs, kappa_e, L): B [n, n] boundary mass, pairs = list of
-    (row dof, col dof, weight, axis, sign) for the coupling C."""
+    (row dof, col dof, weight, axis, sign) for the coupling C.
+
+    The partner value on the opposite side is the P1 field there, taken at
+    the shifted node positions (the master/slave projection of Appendix B):
+    with P the interpolation matrix of those points, C = B_side P.  Rows of P
+    sum to 1, so C 1 = B 1; on matching sides P is a permutation."""
     X = p.xyz[p.tets]
     if p.tets.shape[1] == 4:
         vol = np.abs(np.einsum("ij,ij->i", X[:, 1] - X[:, 0], np.cross(X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]))) / 6.0
@@ -82,13 +117,11 @@ def operators(p, asm, axes, kappa_e=None):
         vol = 0.5 * np.abs(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0])[:, 2])
     ke = default_kappa_e(p, vol) if kappa_e is None else float(kappa_e)
     L = np.asarray(p.box_hi, float) - np.asarray(p.box_lo, float)
-    tol = 1e-9 * float(np.max(L))
     n = asm["n"]
     tet_dof = asm["tet_dof"]
     faces = box_faces(p, axes)
     rows, cols, vals = [], [], []
-    # slave faces by axis: key = sorted quantized coordinates of the nodes moved to the lo side
-    index = {}
+    sides = {}
     for (t, lf, k, side) in faces:
         Xf = p.xyz[p.tets[t, lf]]
         dofs = tet_dof[t, lf]
@@ -97,36 +130,27 @@ def operators(p, asm, axes, kappa_e=None):
         for a in range(fs):
             for b in range(fs):
                 rows.append(dofs[a]), cols.append(dofs[b]), vals.append(Mf[a, b])
-        if side == 1:
-            Xm = Xf.copy()
-            Xm[:, k] -= L[k]
-            key = (k, tuple(sorted(tuple(np.round(x / tol).astype(np.int64)) for x in Xm)))
-            index[key] = (t, lf)
+        sides.setdefault((k, side), []).append((Xf, dofs, Mf))
     B = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
     pairs = []
-    for (t, lf, k, side) in faces:
-        if side != 0:
+    for k in range(3):
+        if not (axes >> k) & 1:
             continue
-        Xf = p.xyz[p.tets[t, lf]]
-        key = (k, tuple(sorted(tuple(np.round(x / tol).astype(np.int64)) for x in Xf)))
-        if key not in index:
-            raise ValueError(f"mesh does not match across the box on axis {k}")
-        ts, lfs = index[key]
-        Xs = p.xyz[p.tets[ts, lfs]]
-        # partner of master vertex a: the slave vertex at x_a + L_k e_k
-        fs = len(lf)
-        perm = []
-        for a in range(fs):
-            target = Xf[a].copy()
-            target[k] += L[k]
-            perm.append(int(np.argmin(np.linalg.norm(Xs - target, axis=1))))
-        dm = tet_dof[t, lf]
-        ds = tet_dof[ts, lfs][perm]
-        Mf = face_mass(Xf)
-        for a in range(fs):
-            for b in range(fs):
-                pairs.append((int(dm[a]), int(ds[b]), Mf[a, b], k, +1))   # master row, slave value
-                pairs.append((int(ds[a]), int(dm[b]), Mf[a, b], k, -1))   # slave row, master value
+        tang = _tangential(p, k)
+        for side, other, shift, sign in ((0, 1, +L[k], +1), (1, 0, -L[k], -1)):
+            partner = {}
+            for Xf, dofs, Mf in sides.get((k, side), []):
+                for b in range(len(dofs)):
+                    if dofs[b] not in partner:
+                        y = Xf[b].copy()
+                        y[k] += shift
+                        partner[dofs[b]] = _locate(sides.get((k, other), []), y, tang)
+                for a in range(len(dofs)):
+                    for b in range(len(dofs)):
+                        pd, pw = partner[dofs[b]]
+                        for d, wgt in zip(pd, pw):
+                            if wgt != 0.0:
+                                pairs.append((int(dofs[a]), int(d), Mf[a, b] * wgt, k, sign))
     return B, pairs, ke, L
 
 

@@ -99,3 +99,41 @@ def test_square_with_disk_weak_approaches_strong_conditions():
         Ss, Sw = oracle.run(make(dt, True))[0], oracle.run(make(dt, False))[0]
         gaps.append(abs(Sw - Ss) / abs(Ss))
     assert gaps[0] > gaps[1] > gaps[2] and gaps[2] < 0.08, gaps
+
+
+# ---------------------------------------------------------------- non-matching sides (projection)
+def _sheared(eps, dt=50.0, b=1000.0, dirs=((1.0, 0.0, 0.0),), kappa_e=None, n=4):
+    p = geom.sheared_box(n=n, L=8.0, eps=eps, dt=dt, bvals=(b,), dirs=dirs)
+    p.weak_periodic = {"axes": 7, "kappa_e": kappa_e}
+    return p
+
+
+def test_projection_reproduces_constants_on_non_matching_sides():
+    """With the x sides sheared against each other, the projected coupling
+    still satisfies C 1 = B 1 (interpolation reproduces constants), so the
+    signal stays |Omega| at g = 0."""
+    from oracle import btoracle as bo
+    from oracle import weakper
+    p = _sheared(0.3, b=0.0, n=6)
+    a = bo.assemble(p)
+    B, pairs, ke, L = weakper.operators(p, a, 7)
+    C = weakper.coupling(pairs, a["n"], 0.0, (1.0, 0.0, 0.0), L, 0.0)
+    one = np.ones(a["n"])
+    assert np.max(np.abs(C @ one - B @ one)) < 1e-13 * np.max(np.abs(B @ one))
+    S, H = oracle.run(p, return_history=True)
+    assert np.max(np.abs(H[0] - 512.0)) < 1e-11 * 512.0
+
+
+def test_projection_conjugates_and_tends_to_the_matching_solution():
+    d = (0.3, 0.4, math.sqrt(0.75))
+    a = oracle.run(_sheared(0.3, dirs=(d,)))[0]
+    b = oracle.run(_sheared(0.3, dirs=(tuple(-x for x in d),)))[0]
+    assert abs(a - np.conj(b)) < 1e-12 * abs(a)
+    S0 = oracle.run(_sheared(0.0))[0]
+    gaps = [abs(oracle.run(_sheared(e))[0] - S0) for e in (0.4, 0.2, 0.1)]
+    assert gaps[0] > gaps[1] > gaps[2] and gaps[2] < 0.01 * abs(S0), gaps
+
+
+def test_projection_approaches_pseudo_periodic_value():
+    S = oracle.run(_sheared(0.3, dt=12.5, kappa_e=1.5e-2, n=6))[0] / 512.0
+    assert abs(S - math.exp(-1000.0 * 2e-3)) < 0.03
