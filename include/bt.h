@@ -191,11 +191,14 @@ bt_status bt_set_element_tensors(bt_ctx* ctx, const double* D6);
  * F(t_n)}: L_n = M + theta dt (A_n + kappa_e B), r_0 += theta dt kappa_e C_n
  * u^{n-1}, B the boundary-face mass, C_n the face-mass coupling of partner
  * faces (Appendix B weighs the partner term by 1 - theta; theta is used for
- * both here, which is identical at theta = 1/2).  The mesh must match across
- * the box (the partner of a node is the node at x + L_k e_k).  Lab frame and
- * one geometry only.  Clears the assembly like bt_set_relaxation; axes = 0
- * switches the coupling off.  BT_EINVAL for a non-matching mesh, axes that
- * are periodic in the mesh, or a 1-D manifold mesh. */
+ * both here, which is identical at theta = 1/2).  The two sides may be meshed
+ * differently: a node's partner value is the opposite side's P1 field at the
+ * node shifted by +-L_k e_k, interpolated in the face that contains that point
+ * (the master/slave projection); on matching sides this is the node at the
+ * shifted position.  BT_EINVAL if a shifted node falls outside the opposite
+ * side.  Lab frame and one geometry only.  Clears the assembly like bt_set_relaxation; axes = 0
+ * switches the coupling off.  BT_EINVAL for axes that are periodic in the
+ * mesh, a 1-D manifold or a surface mesh. */
 bt_status bt_set_weak_periodic(bt_ctx* ctx, uint32_t axes, double kappa_e);
 
 /* ---------------------------------------------------------------- assembly

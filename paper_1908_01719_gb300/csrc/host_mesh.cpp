@@ -588,7 +588,155 @@ int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std:
     int64_t t;
     int lf;
   };
-  std::vector<std::tuple<int32_t, int32_t, double, int8_t>> ent;  // row, col, w, code
+  using Entry = std::tuple<int32_t, int32_t, double, int8_t>;  // row, col, w, code
+  std::vector<Entry> ent;
+  // The projection for sides that do not match: a node's partner value is the
+  // opposite side's P1 field at the node shifted by +-L_k, read from the face
+  // that contains the shifted point with its barycentric weights.  A uniform
+  // grid over the side's tangential coordinates finds the candidate faces.
+  auto project_axis = [&](int k, const std::vector<Face>* sides, std::vector<Entry>& out,
+                          std::string& err) -> int {
+    int ta[2] = {0, 0}, ntan = 0;  // tangential axes
+    if (nv == 3) {
+      ta[ntan++] = k == 0 ? 1 : 0;
+    } else {
+      for (int a = 0; a < 3; ++a)
+        if (a != k) ta[ntan++] = a;
+    }
+    struct Rec {
+      int32_t node[3], dof[3];
+      double meas;
+    };
+    std::vector<Rec> rec[2];
+    for (int sd = 0; sd < 2; ++sd)
+      for (const Face& f : sides[sd]) {
+        Rec r{};
+        double P[3][3] = {};
+        for (int a = 0; a < fs; ++a) {
+          r.node[a] = m.tets[nv * f.t + LOC(f.lf, a)];
+          r.dof[a] = m.tet_dof[nv * f.t + LOC(f.lf, a)];
+          for (int kk = 0; kk < 3; ++kk) P[a][kk] = X(r.node[a], kk);
+        }
+        r.meas = face_measure(P);
+        rec[sd].push_back(r);
+      }
+    // grids over each side's tangential box
+    struct Grid {
+      double lo[2] = {0, 0}, cell[2] = {1, 1};
+      int n[2] = {1, 1};
+      std::vector<std::vector<int32_t>> bins;
+    } grid[2];
+    for (int sd = 0; sd < 2; ++sd) {
+      Grid& g = grid[sd];
+      double hi[2] = {-1e300, -1e300};
+      g.lo[0] = g.lo[1] = 1e300;
+      for (const Rec& r : rec[sd])
+        for (int a = 0; a < fs; ++a)
+          for (int j = 0; j < ntan; ++j) {
+            g.lo[j] = std::min(g.lo[j], X(r.node[a], ta[j]));
+            hi[j] = std::max(hi[j], X(r.node[a], ta[j]));
+          }
+      const double per = ntan == 2 ? std::sqrt((double)rec[sd].size()) : (double)rec[sd].size();
+      for (int j = 0; j < ntan; ++j) {
+        g.n[j] = std::max(1, (int)std::min(4096.0, per));
+        g.cell[j] = std::max((hi[j] - g.lo[j]) / g.n[j], 1e-300);
+      }
+      g.bins.assign((size_t)g.n[0] * g.n[1], {});
+      for (size_t i = 0; i < rec[sd].size(); ++i) {
+        int c0[2] = {0, 0}, c1[2] = {0, 0};
+        for (int j = 0; j < ntan; ++j) {
+          double a0 = 1e300, a1 = -1e300;
+          for (int a = 0; a < fs; ++a) {
+            a0 = std::min(a0, X(rec[sd][i].node[a], ta[j]));
+            a1 = std::max(a1, X(rec[sd][i].node[a], ta[j]));
+          }
+          c0[j] = std::max(0, std::min(g.n[j] - 1, (int)std::floor((a0 - g.lo[j]) / g.cell[j])));
+          c1[j] = std::max(0, std::min(g.n[j] - 1, (int)std::floor((a1 - g.lo[j]) / g.cell[j])));
+        }
+        for (int u = c0[0]; u <= c1[0]; ++u)
+          for (int v = c0[1]; v <= c1[1]; ++v) g.bins[(size_t)u * g.n[1] + v].push_back((int32_t)i);
+      }
+    }
+    // barycentric weights of the point y in face i of side sd (tangential coordinates)
+    auto weights = [&](int sd, int32_t i, const double* y, double* lam) {
+      const Rec& r = rec[sd][i];
+      if (ntan == 1) {
+        const double p0 = X(r.node[0], ta[0]), p1 = X(r.node[1], ta[0]);
+        const double t = (y[ta[0]] - p0) / (p1 - p0);
+        lam[0] = 1.0 - t;
+        lam[1] = t;
+        return;
+      }
+      const double u0 = X(r.node[0], ta[0]), v0 = X(r.node[0], ta[1]);
+      const double e1u = X(r.node[1], ta[0]) - u0, e1v = X(r.node[1], ta[1]) - v0;
+      const double e2u = X(r.node[2], ta[0]) - u0, e2v = X(r.node[2], ta[1]) - v0;
+      const double du = y[ta[0]] - u0, dv = y[ta[1]] - v0;
+      const double det = e1u * e2v - e1v * e2u;
+      lam[1] = (du * e2v - dv * e2u) / det;
+      lam[2] = (e1u * dv - e1v * du) / det;
+      lam[0] = 1.0 - lam[1] - lam[2];
+    };
+    auto locate = [&](int sd, const double* y, int32_t* pd, double* pw) -> bool {
+      const Grid& g = grid[sd];
+      int c[2] = {0, 0};
+      for (int j = 0; j < ntan; ++j)
+        c[j] = std::max(0, std::min(g.n[j] - 1, (int)std::floor((y[ta[j]] - g.lo[j]) / g.cell[j])));
+      double best = -1e300, lam[3];
+      int32_t bi = -1;
+      auto consider = [&](int32_t i) {
+        weights(sd, i, y, lam);
+        double mn = lam[0];
+        for (int a = 1; a < fs; ++a) mn = std::min(mn, lam[a]);
+        if (mn > best) {
+          best = mn;
+          bi = i;
+        }
+      };
+      for (int32_t i : g.bins[(size_t)c[0] * g.n[1] + c[1]]) consider(i);
+      if (best < -1e-9)  // not in its cell's candidates: search the whole side
+        for (int32_t i = 0; i < (int32_t)rec[sd].size(); ++i) consider(i);
+      if (bi < 0 || best < -1e-9) return false;
+      weights(sd, bi, y, lam);
+      for (int a = 0; a < fs; ++a) {
+        pd[a] = rec[sd][bi].dof[a];
+        pw[a] = lam[a];
+      }
+      return true;
+    };
+    for (int sd = 0; sd < 2; ++sd) {
+      const int other = 1 - sd;
+      const double shift = sd == 0 ? wp.L[k] : -wp.L[k];
+      std::map<int32_t, std::pair<std::array<int32_t, 3>, std::array<double, 3>>> partner;
+      for (const Rec& r : rec[sd]) {
+        for (int b = 0; b < fs; ++b) {
+          if (partner.count(r.node[b])) continue;
+          double y[3] = {X(r.node[b], 0), X(r.node[b], 1), X(r.node[b], 2)};
+          y[k] += shift;
+          std::array<int32_t, 3> pd = {-1, -1, -1};
+          std::array<double, 3> pw = {0, 0, 0};
+          if (!locate(other, y, pd.data(), pw.data())) {
+            err = "a node's partner point lies outside the opposite side on axis " + std::to_string(k);
+            return BT_EINVAL;
+          }
+          for (int a = 0; a < fs; ++a)
+            if (pd[a] < 0 || pd[a] >= m.n_dof) {
+              err = "partner face lookup failed on axis " + std::to_string(k);
+              return BT_EINVAL;
+            }
+          partner[r.node[b]] = {pd, pw};
+        }
+        for (int a = 0; a < fs; ++a)
+          for (int b = 0; b < fs; ++b) {
+            const double wt = r.meas / mdiv * (a == b ? 2.0 : 1.0);
+            const auto& pr = partner[r.node[b]];
+            for (int c = 0; c < fs; ++c)
+              if (pr.second[c] != 0.0)
+                out.emplace_back(r.dof[a], pr.first[c], wt * pr.second[c], (int8_t)(sd ? (k | 4) : k));
+          }
+      }
+    }
+    return BT_OK;
+  };
   for (int k = 0; k < 3; ++k) {
     if (!((axes >> k) & 1)) continue;
     std::vector<Face> side[2];
@@ -616,6 +764,10 @@ int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std:
       std::sort(key.begin(), key.end());
       sface[key] = f;
     }
+    // matching sides: each master node's partner is the slave node at x + L_k e_k;
+    // otherwise the projection below couples the sides
+    bool matched = true;
+    std::vector<std::tuple<int32_t, int32_t, double, int8_t>> axis_ent;
     for (int sd = 0; sd < 2; ++sd)
       for (const Face& f : side[sd]) {
         int32_t v[3], dof[3];
@@ -635,25 +787,26 @@ int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std:
             }
             wp.B[sl] += meas / mdiv * (a == b ? 2.0 : 1.0);
           }
-        if (sd == 1) continue;
+        if (sd == 1 || !matched) continue;
         // master face: partner nodes at x + L_k e_k and the slave face holding them
         int32_t pv[3];
         std::array<int32_t, 3> key = {-1, -1, -1};
-        for (int a = 0; a < fs; ++a) {
+        bool all = true;
+        for (int a = 0; a < fs && all; ++a) {
           double y[3] = {P[a][0], P[a][1], P[a][2]};
           y[k] += wp.L[k];
           auto it = snode.find(qkey(y[0], y[1], y[2]));
           if (it == snode.end()) {
-            msg = "the mesh does not match across the box on axis " + std::to_string(k);
-            return BT_EINVAL;
+            all = false;
+          } else {
+            pv[a] = key[a] = it->second;
           }
-          pv[a] = key[a] = it->second;
         }
         std::sort(key.begin(), key.end());
-        auto fit = sface.find(key);
+        auto fit = all ? sface.find(key) : sface.end();
         if (fit == sface.end()) {
-          msg = "the mesh does not match across the box on axis " + std::to_string(k);
-          return BT_EINVAL;
+          matched = false;
+          continue;
         }
         const Face& g = fit->second;
         int32_t pdof[3] = {-1, -1, -1};
@@ -668,10 +821,15 @@ int build_weak_periodic(const HostMesh& m, uint32_t axes, WeakPeriodic& wp, std:
         for (int a = 0; a < fs; ++a)
           for (int b = 0; b < fs; ++b) {
             const double wt = meas / mdiv * (a == b ? 2.0 : 1.0);
-            ent.emplace_back(dof[a], pdof[b], wt, (int8_t)k);           // master row: slave value, +phase
-            ent.emplace_back(pdof[a], dof[b], wt, (int8_t)(k | 4));     // slave row: master value, -phase
+            axis_ent.emplace_back(dof[a], pdof[b], wt, (int8_t)k);        // master row: slave value, +phase
+            axis_ent.emplace_back(pdof[a], dof[b], wt, (int8_t)(k | 4));  // slave row: master value, -phase
           }
       }
+    if (matched) {
+      ent.insert(ent.end(), axis_ent.begin(), axis_ent.end());
+    } else if (int st = project_axis(k, side, ent, msg)) {
+      return st;
+    }
   }
   std::stable_sort(ent.begin(), ent.end(),
                    [](const auto& x, const auto& y) { return std::get<0>(x) < std::get<0>(y); });

@@ -332,3 +332,23 @@ def test_three_layer_structures(sim_cls, bt, kind):
         assert rel(S, ref).max() < TOL_MIXED, rel(S, ref)
     finally:
         sim.close()
+
+
+@pytest.mark.parametrize("mode", ["plain", "mixed"])
+def test_weak_periodic_projection_on_non_matching_sides(sim_cls, bt, mode):
+    """A box whose x sides are sheared against each other: the weak coupling
+    reads the opposite side's field at the shifted nodes (projection), against
+    the oracle."""
+    p = geom.sheared_box(n=5, L=8.0, eps=0.3, bvals=(1000.0, 2500.0),
+                         dirs=((1.0, 0.0, 0.0), (0.0, 0.6, 0.8)))
+    p.weak_periodic = {"axes": 7, "kappa_e": None}
+    ref = oracle.run(p)
+    sim = sim_cls(p)
+    try:
+        m = bt.BT_MODE_PLAIN_FP64 if mode == "plain" else bt.BT_MODE_MIXED
+        S, err, stat, st = sim.run(m)
+        assert np.all(stat == 0)
+        tol = TOL_FP64 if mode == "plain" else TOL_MIXED
+        assert rel(S, ref).max() < tol, rel(S, ref)
+    finally:
+        sim.close()
