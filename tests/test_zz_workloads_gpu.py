@@ -63,7 +63,8 @@ def test_cfg4_full_size_properties(sim_cls, bt):
             assert rel(S[r], S64[r]) < TOL_MIXED, (r, S[r], S64[r])
     finally:
         sim.close()
-    q = geom.cfg4(n_dir=2, bvals=(0.0, 3000.0))
+    import dataclasses
+    q = dataclasses.replace(p, dirs=p.dirs[:2].copy(), bvals=np.array([0.0, 3000.0]))
     sim = sim_cls(q)
     try:
         S, err, stat, _ = sim.run(bt.BT_MODE_MIXED)
