@@ -13,7 +13,8 @@ Other workloads (--config): cfg1-cfg3 (the smaller 3-D cases), disk2d (2-D P1
 triangles: a disk of radius 5 um in a 20 um square, 512^2 cells, 32 in-plane
 directions x 4 b-values) and trees1d (1-D manifolds: 64 seeded dendrite trees
 as one uneven batch, PGSE delta 10.6 ms / Delta 43.1 ms, dt 100 us, 3
-directions x 3 b-values per tree).
+directions x 3 b-values per tree) and shells (thin layers: 32 capped spheres of
+seeded radii as level-5 icospheres, 3 directions x 3 b-values each).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config NAME]
   torchrun --nproc-per-node N bench.py --gpus N ...     (one replica per rank,
@@ -45,6 +46,17 @@ UNIT = "step-RHS/s"
 
 
 N_TREES = 64
+N_SHELLS = 32
+
+
+def shells(n=N_SHELLS):
+    """Thin layers: n spheres of seeded radii U(3, 8) um, level-5 icospheres,
+    each with a permeable cap above z = 0.3 R; 3 axis directions x 3 b-values."""
+    import geom
+    rng = np.random.default_rng(0)
+    return [geom.spherical_shell(level=5, R=float(r), kappa=1e-4, cap_z=0.3, bvals=(0.0, 1000.0, 3000.0),
+                                 dirs=((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)))
+            for r in rng.uniform(3.0, 8.0, n)]
 
 
 def disk2d(n=512):
@@ -60,6 +72,8 @@ def workload(name):
         return disk2d()
     if name == "trees1d":
         return geom.union([geom.dendrite_tree(seed=s) for s in range(N_TREES)], name="trees1d")
+    if name == "shells":
+        return geom.union(shells(), name="shells")
     if name == "cfg4":
         return geom.cfg4()
     if name == "cfg3":
@@ -78,6 +92,8 @@ def n_geometries(p):
 
 def describe(name, p, n_dof, nnz, n_face):
     elem = {4: "Kuhn tets", 3: "triangles (2-D)", 2: "segments (1-D manifold)"}[p.tets.shape[1]]
+    if getattr(p, "surface", False):
+        elem = "surface triangles (thin layers)"
     G = n_geometries(p)
     return {"workload": f"{name}: {len(p.xyz)} nodes, {len(p.tets)} {elem}, {p.n_cmpt} compartments, "
                         + (f"{G} geometries as one uneven batch, " if G > 1 else "") +
@@ -145,8 +161,8 @@ def _oracle_task(args):
     import geom
     import oracle
     t0 = time.time()
-    if name == "trees1d":                  # one whole tree (all its RHS) per task
-        p = geom.dendrite_tree(seed=r)
+    if name in ("trees1d", "shells"):      # one whole geometry (all its RHS) per task
+        p = geom.dendrite_tree(seed=r) if name == "trees1d" else shells(r + 1)[r]
         oracle.run(p)
         return time.time() - t0, p.n_steps * p.n_rhs
     p = disk2d(n=grid) if name == "disk2d" else \
@@ -156,7 +172,7 @@ def _oracle_task(args):
 
 
 def oracle_grid(name):
-    return {"disk2d": 192, "trees1d": 0}.get(name, ORACLE_GRID)
+    return {"disk2d": 192, "trees1d": 0, "shells": 0}.get(name, ORACLE_GRID)
 
 
 def oracle_sample(name, n_rhs_sample, grid):
@@ -182,8 +198,8 @@ def oracle_sample(name, n_rhs_sample, grid):
                 os.environ[k] = v
     wall = time.time() - t0
     units = sum(r[1] for r in res)
-    if name == "trees1d":
-        what = f"trees1d: the first {n_rhs_sample} dendrite trees of the batch, all 9 RHS x {res[0][1] // 9} steps"
+    if name in ("trees1d", "shells"):
+        what = f"{name}: the first {n_rhs_sample} geometries of the batch, all 9 RHS x {res[0][1] // 9} steps"
     elif name == "disk2d":
         what = f"disk2d seeded geometry on a {grid}^2 grid, {n_rhs_sample} RHS x {res[0][1]} steps"
     else:
@@ -413,7 +429,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4", "disk2d", "trees1d"])
+    ap.add_argument("--config", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4", "disk2d", "trees1d", "shells"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

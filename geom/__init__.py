@@ -705,9 +705,12 @@ def union(problems, name="batch"):
         c_off += p.n_cmpt
         half = max(half, float(np.max(np.asarray(p.box_hi) - c)))
     p0 = problems[0]
+    if len({p.tets.shape[1] for p in problems}) != 1 or len({p.surface for p in problems}) != 1:
+        raise ValueError("a batch holds one element family")
     out = Problem(name, np.concatenate(xyz), np.concatenate(tets).astype(np.int32),
                   np.concatenate(cmpt).astype(np.int32), np.concatenate(D), np.concatenate(kap), 0,
-                  np.full(3, -half), np.full(3, half), p0.dt, p0.delta, p0.Delta, p0.TE, p0.dirs, p0.bvals)
+                  np.full(3, -half), np.full(3, half), p0.dt, p0.delta, p0.Delta, p0.TE, p0.dirs, p0.bvals,
+                  surface=p0.surface)
     out.segments = {"node_off": np.array(node_off, dtype=np.int64),
                     "delta": np.array([p.delta for p in problems]),
                     "Delta": np.array([p.Delta for p in problems]),
