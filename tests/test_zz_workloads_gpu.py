@@ -353,3 +353,19 @@ def test_weak_periodic_projection_on_non_matching_sides(sim_cls, bt, mode):
         assert rel(S, ref).max() < tol, rel(S, ref)
     finally:
         sim.close()
+
+
+def test_batch_of_thin_layers_per_geometry(sim_cls, bt):
+    """Three capped spheres of different radii as one uneven batch (surface
+    triangles): each geometry's signals against its own oracle run."""
+    parts = [geom.spherical_shell(level=2, R=r, kappa=1e-4, cap_z=0.3, bvals=(0.0, 2000.0),
+                                  dirs=((1.0, 0.0, 0.0), (0.0, 0.0, 1.0))) for r in (3.0, 4.5, 6.0)]
+    u = geom.union(parts)
+    ref = np.concatenate([oracle.run(p) for p in parts])
+    sim = sim_cls(u)
+    try:
+        S, err, stat, _ = sim.run(bt.BT_MODE_MIXED)
+        assert np.all(stat == 0)
+        assert rel(S, ref).max() < TOL_MIXED, rel(S, ref)
+    finally:
+        sim.close()
