@@ -446,9 +446,8 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
   t.rowl.reserve(n);
   t.lidx.reserve(m.nnz);
   t.slot.reserve(m.nnz);
-  std::vector<int32_t> mark(n, -1), lpos(n, 0);
+  std::vector<int32_t> mark(n, -1);
   std::vector<std::pair<uint64_t, int32_t>> order;
-  std::vector<int32_t> cur, uc;
   int32_t tid = 0;
   for (int g = 0; g < G; ++g) {
     t.seg_tile0.push_back((int32_t)t.r0.size());
@@ -474,51 +473,86 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
     }
     std::sort(order.begin(), order.end());
     // greedy tiles along the curve: at most tmax rows, umax distinct columns
-    // and emax entries
+    // and emax entries.  The boundaries need one pass in order (a tile's
+    // distinct columns depend on the rows before it); the tiles' halos, local
+    // indices and entries are then written in parallel at their offsets.
+    struct Span {
+      size_t i0, i1;   // rows order[i0, i1)
+      int32_t nu;      // distinct columns
+      int64_t ne;      // entries
+    };
+    std::vector<Span> spans;
     size_t i = 0;
     while (i < order.size()) {
-      cur.clear();
-      uc.clear();
-      int64_t ne = 0;
-      for (; i < order.size() && (int)cur.size() < tmax; ++i) {
+      Span sp{i, i, 0, 0};
+      for (; i < order.size() && (int)(i - sp.i0) < tmax; ++i) {
         const int32_t r = order[i].second;
         const int64_t rn = m.row_ptr[r + 1] - m.row_ptr[r];
         int fresh = 0;
         for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k) fresh += mark[m.col[k]] != tid;
-        if ((int)uc.size() + fresh > umax || ne + rn > emax) {
-          if (cur.empty()) {
+        if (sp.nu + fresh > umax || sp.ne + rn > emax) {
+          if (i == sp.i0) {
             // a single row wider than umax (or emax) cannot be staged
             t.too_wide = true;
             return;
           }
           break;
         }
-        ne += rn;
-        for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k)
-          if (mark[m.col[k]] != tid) {
-            mark[m.col[k]] = tid;
-            uc.push_back(m.col[k]);
-          }
-        cur.push_back(r);
+        sp.ne += rn;
+        sp.nu += fresh;
+        for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k) mark[m.col[k]] = tid;
       }
-      std::sort(uc.begin(), uc.end());
-      for (size_t u = 0; u < uc.size(); ++u) lpos[uc[u]] = (int32_t)u;
-      t.r0.push_back((int32_t)t.rows.size());
-      t.u0.push_back((int32_t)t.ucol.size());
-      t.e0.push_back((int32_t)t.lidx.size());
-      for (int32_t c : uc) t.ucol.push_back((uint32_t)c);
-      for (int32_t r : cur) {
-        t.ucol[t.u0.back() + lpos[r]] |= 0x80000000u;  // owned by this tile
-        t.rows.push_back(r);
-        t.rowe.push_back((int32_t)t.lidx.size());
-        t.rowl.push_back((uint16_t)lpos[r]);
-        for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k) {
-          t.lidx.push_back((uint16_t)lpos[m.col[k]]);
-          t.slot.push_back((int32_t)k);
-        }
-      }
+      sp.i1 = i;
+      spans.push_back(sp);
       ++tid;
     }
+    const size_t T0 = t.r0.size(), nrow0 = t.rows.size(), nu0 = t.ucol.size(), ne0 = t.lidx.size();
+    std::vector<int64_t> ro(spans.size() + 1, 0), uo(spans.size() + 1, 0), eo(spans.size() + 1, 0);
+    for (size_t s2 = 0; s2 < spans.size(); ++s2) {
+      ro[s2 + 1] = ro[s2] + (int64_t)(spans[s2].i1 - spans[s2].i0);
+      uo[s2 + 1] = uo[s2] + spans[s2].nu;
+      eo[s2 + 1] = eo[s2] + spans[s2].ne;
+    }
+    t.r0.resize(T0 + spans.size());
+    t.u0.resize(T0 + spans.size());
+    t.e0.resize(T0 + spans.size());
+    t.rows.resize(nrow0 + ro.back());
+    t.rowe.resize(nrow0 + ro.back());
+    t.rowl.resize(nrow0 + ro.back());
+    t.ucol.resize(nu0 + uo.back());
+    t.lidx.resize(ne0 + eo.back());
+    t.slot.resize(ne0 + eo.back());
+    parallel_for((int64_t)spans.size(), [&](int64_t b0, int64_t b1) {
+      std::vector<int32_t> uc;
+      for (int64_t s2 = b0; s2 < b1; ++s2) {
+        const Span& sp = spans[s2];
+        uc.clear();
+        for (size_t q = sp.i0; q < sp.i1; ++q) {
+          const int32_t r = order[q].second;
+          uc.insert(uc.end(), m.col.begin() + m.row_ptr[r], m.col.begin() + m.row_ptr[r + 1]);
+        }
+        std::sort(uc.begin(), uc.end());
+        uc.erase(std::unique(uc.begin(), uc.end()), uc.end());
+        auto lp = [&](int32_t c) { return (int32_t)(std::lower_bound(uc.begin(), uc.end(), c) - uc.begin()); };
+        t.r0[T0 + s2] = (int32_t)(nrow0 + ro[s2]);
+        t.u0[T0 + s2] = (int32_t)(nu0 + uo[s2]);
+        t.e0[T0 + s2] = (int32_t)(ne0 + eo[s2]);
+        for (size_t u = 0; u < uc.size(); ++u) t.ucol[nu0 + uo[s2] + u] = (uint32_t)uc[u];
+        int64_t e = ne0 + eo[s2];
+        for (size_t q = sp.i0; q < sp.i1; ++q) {
+          const int32_t r = order[q].second;
+          const size_t j = nrow0 + ro[s2] + (q - sp.i0);
+          t.ucol[nu0 + uo[s2] + lp(r)] |= 0x80000000u;  // owned by this tile
+          t.rows[j] = r;
+          t.rowe[j] = (int32_t)e;
+          t.rowl[j] = (uint16_t)lp(r);
+          for (int64_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k, ++e) {
+            t.lidx[e] = (uint16_t)lp(m.col[k]);
+            t.slot[e] = (int32_t)k;
+          }
+        }
+      }
+    });
   }
   t.seg_tile0.push_back((int32_t)t.r0.size());
   t.r0.push_back((int32_t)t.rows.size());
