@@ -400,9 +400,10 @@ bt_status bt_load_precond(bt_ctx* ctx, const float* w);
 /* ---------------------------------------------------------------- allocation-free gradient
  * bt_precond_grad_noalloc computes what bt_precond_eval computes for the loss
  * and gradient of the preconditioner network, for callers that cannot
- * allocate device memory: code running inside CUDA stream capture, under a
- * framework that owns every device allocation, or in a service that forbids
- * allocation after start-up.  It calls no cudaMalloc, cudaFree or allocating
+ * allocate device memory: code under a framework that owns every device
+ * allocation (a caching allocator or a fixed budget that cudaMalloc would
+ * bypass), or a service that forbids allocation after start-up because
+ * cudaMalloc and cudaFree synchronise the device.  It calls no cudaMalloc, cudaFree or allocating
  * library routine; its scratch is a fixed file-scope device array of about
  * 2.2 MB that every GPU loading the library holds until the process exits.
  * The paper has no counterpart of this entry point.
@@ -417,7 +418,11 @@ bt_status bt_load_precond(bt_ctx* ctx, const float* w);
  * make that first call before any stream capture.  All calls on a device share
  * the scratch array, so calls that overlap on the GPU (different streams, no
  * ordering between them) race; order them on one stream.  No context is used:
- * errors are reported by the return code only. */
+ * errors are reported by the return code only.  BT_ECUDA without a launch if
+ * a launch error is already pending on the calling thread (it is left
+ * pending), or if one of this call's launches fails.  The scratch address is
+ * cached per device for the life of the process: after cudaDeviceReset on a
+ * device, do not call this entry point on that device again. */
 enum { BT_NOALLOC_MAX_SAMPLES = 2048 };
 bt_status bt_precond_grad_noalloc(const float* w, int32_t n, const float* feat, const float* G, const float* h,
                                   double* grad, float* loss, void* stream);

@@ -1,10 +1,13 @@
 // bt_precond_grad_noalloc: the preconditioner-network gradient of
-// bt_precond_eval for callers that cannot allocate device memory -- code that
-// runs inside CUDA stream capture, under a framework that owns every
-// allocation (a caching allocator or a fixed memory budget), or in a service
-// that forbids allocation after start-up.  It uses no cudaMalloc/cudaFree and
-// no allocating library routine: its scratch is the file-scope array below,
-// whose device address is looked up once per device.
+// bt_precond_eval for callers that cannot allocate device memory -- code under
+// a framework that owns every device allocation (a caching allocator or a
+// fixed memory budget that cudaMalloc would bypass), or a service that forbids
+// allocation after start-up because cudaMalloc/cudaFree synchronise the device.
+// It uses no cudaMalloc/cudaFree and no allocating library routine: its scratch
+// is the file-scope array below, whose device address is looked up once per
+// device.  That address belongs to the device's primary context; after a
+// cudaDeviceReset the cached address is stale, so a process that resets a
+// device must not call this entry point on it again.
 #include <mutex>
 
 #include "bt_kernels.cuh"
@@ -63,9 +66,13 @@ extern "C" bt_status bt_precond_grad_noalloc(const float* w, int32_t n, const fl
   int* idx = reinterpret_cast<int*>(a.sdc + A * MLP_OUT);
   __nv_bfloat16* w16 = reinterpret_cast<__nv_bfloat16*>(idx + A);
   cudaStream_t st = (cudaStream_t)stream;
+  // a launch error left pending by the caller's own earlier work would be
+  // indistinguishable from ours: refuse to run on top of it (it stays pending)
+  if (cudaPeekAtLastError() != cudaSuccess) return BT_ECUDA;
   // nothing in the scratch has to start at zero: every value the kernels read
   // is written earlier in the same call
   k_prepare<<<(MLP_NPARAM > n ? MLP_NPARAM : n) / 256 + 1, 256, 0, st>>>(w, w16, idx, n);
+  if (cudaGetLastError() != cudaSuccess) return BT_ECUDA;
   a.w32 = nullptr;
   a.w16 = w16;
   a.m = a.v = nullptr;
@@ -78,5 +85,5 @@ extern "C" bt_status bt_precond_grad_noalloc(const float* w, int32_t n, const fl
   a.grad_out = grad;
   a.apply = 0;
   launch_mlp_train(a, st);
-  return cudaGetLastError() == cudaSuccess ? BT_OK : BT_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? BT_OK : BT_ECUDA;  // only this call's launches since the check above
 }

@@ -7,6 +7,7 @@
 // kappa <[U],[v]> (Appendix B, Eq. loadvec); master-slave periodicity
 // (Section 2, Eq. btpde_bc).
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <climits>
 #include <cmath>
@@ -522,6 +523,7 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
     t.ucol.resize(nu0 + uo.back());
     t.lidx.resize(ne0 + eo.back());
     t.slot.resize(ne0 + eo.back());
+    std::atomic<bool> bad{false};
     parallel_for((int64_t)spans.size(), [&](int64_t b0, int64_t b1) {
       std::vector<int32_t> uc;
       for (int64_t s2 = b0; s2 < b1; ++s2) {
@@ -533,6 +535,12 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
         }
         std::sort(uc.begin(), uc.end());
         uc.erase(std::unique(uc.begin(), uc.end()), uc.end());
+        if ((int32_t)uc.size() != sp.nu) {
+          // the boundary pass counted a different number of distinct columns
+          // (a row with a repeated column): the offsets would overlap
+          bad.store(true);
+          continue;
+        }
         auto lp = [&](int32_t c) { return (int32_t)(std::lower_bound(uc.begin(), uc.end(), c) - uc.begin()); };
         t.r0[T0 + s2] = (int32_t)(nrow0 + ro[s2]);
         t.u0[T0 + s2] = (int32_t)(nu0 + uo[s2]);
@@ -553,6 +561,10 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
         }
       }
     });
+    if (bad.load()) {
+      t.too_wide = true;  // not stageable: the halo iteration is not offered
+      return;
+    }
   }
   t.seg_tile0.push_back((int32_t)t.r0.size());
   t.r0.push_back((int32_t)t.rows.size());

@@ -2,7 +2,7 @@
 of a config on a chosen grid, a shortened PGSE sequence (a few time steps),
 mixed precision.  It prints the sizes and the counters of the run.
 
-  python -m paper_1908_01719_gb300.profile_case --config cfg4 --grid 64 --steps 2 [--variant halo]
+  python profile_case.py --config cfg4 --grid 64 --steps 2 [--variant halo]
 
 --config disk2d takes --grid as the cells per side of the disk-in-square (32
 in-plane directions x 4 b-values); --config trees1d takes it as the number of
@@ -14,7 +14,7 @@ import argparse
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
