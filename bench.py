@@ -222,7 +222,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    sample_rhs, grid = min(8, os.cpu_count() or 1), oracle_grid(args.config)
+    sample_rhs, grid = min(16, os.cpu_count() or 1), oracle_grid(args.config)
     vals, walls = [], []
     for i in range(args.warmup + args.steps):
         t0 = time.time()
@@ -243,8 +243,14 @@ def run_reference(args):
 
 # vectors of n complex FP32 values (8 B) each active right-hand side moves per
 # launch of the dominant kernel: the row SpMM reads X and writes Y; the
-# halo-staged apply reads z, p_prev and x and writes x, p and q
-VECTORS_PER_SYSTEM = {"row": 2, "halo": 6}
+# halo-staged apply reads z, p_prev and x and writes x, p and q; the
+# slice-tiled SpMM reads p and writes q
+VECTORS_PER_SYSTEM = {"row": 2, "halo": 6, "slice": 2}
+# ... and per Krylov iteration (all launches of one iteration): row 2 + 6 + 3,
+# halo 6 + 3 (z update: reads z, q, writes z), slice 2 + 3 (r, q read, r
+# written) + 5 (x, p, r read, x, p written)
+VECTORS_PER_ITER = {"row": 11, "halo": 9, "slice": 10}
+KERNEL = {"row": "k_spmm_krylov", "halo": "k_spmm_halo", "slice": "k_spmm_slice"}
 
 
 # DRAM bytes (read + write) of one launch of the row SpMM k_spmm_krylov<4>, lab
@@ -319,14 +325,16 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     clocks = clk.summary()
     tuning = bt.bt_get_tuning(sim.ctx)
-    # the same runs as one captured CUDA graph per time step (no per-launch events)
+    # the same runs as one captured CUDA graph per time step (no per-launch
+    # events), on at most two simulations to bound the bench's wall time
+    n_graph = min(args.steps, 2)
     eg0, eg1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     eg0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(n_graph):
         sim.run(mode)
     eg1.record(stream)
     torch.cuda.synchronize(dev)
-    ms_graph = eg0.elapsed_time(eg1)
+    ms_graph = eg0.elapsed_time(eg1) * args.steps / n_graph
     ms_t = torch.tensor([ms], device=dev)
     if ws > 1:
         torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
@@ -355,6 +363,12 @@ def run_ours(args):
     bytes_launch = bytes_total / max(1, spmm_launch)
     avg_ms = spmm_ms / max(1, spmm_launch)
     achieved = bytes_total / (spmm_ms / 1e3) / 1e9
+    # the whole Krylov iteration of the chosen variant (autotuner timing: one
+    # iteration with every system active, CUDA events inside the library)
+    v = tuning["variant"]
+    planes = 5 if p.transformed else 4
+    it_bytes = 4 * (n + 1) + nnz * (4 + 4 * planes) + VECTORS_PER_ITER[v] * n * p.n_rhs * 8
+    ms_it = tuning["ms_iter_" + v]
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -385,7 +399,7 @@ def run_ours(args):
 
     if rank != 0:
         return
-    cpu = oracle_sample(args.config, min(8, os.cpu_count() or 1), oracle_grid(args.config)) if ws == 1 else None
+    cpu = oracle_sample(args.config, min(16, os.cpu_count() or 1), oracle_grid(args.config)) if ws == 1 else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp32 (SpMM/Krylov) + double-float residual",
@@ -399,7 +413,7 @@ def run_ours(args):
                                              "speedup_of_value": value / ws / fp64_rate},
             "spmm_autotune": tuning,
             "roofline": {"bound": "hbm",
-                         "kernel": {"row": "k_spmm_krylov", "halo": "k_spmm_halo"}[tuning["variant"]]
+                         "kernel": KERNEL[tuning["variant"]]
                          + " (fused FP32 complex SpMM of the Krylov iteration, the autotuned variant)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "frac_of_nominal_7900_gbs": achieved / 7900.0,
@@ -411,6 +425,12 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms,
                          "active_rhs_per_launch": sys_iters / max(1, spmm_launch),
                          "launches": spmm_launch},
+            "iteration_roofline": {"variant": v, "ms_per_iteration": ms_it, "bytes_per_iteration": it_bytes,
+                                   "vectors_per_system": VECTORS_PER_ITER[v],
+                                   "achieved": it_bytes / (ms_it / 1e3) / 1e9 if ms_it > 0 else None,
+                                   "frac": it_bytes / (ms_it / 1e3) / 1e9 / peak if ms_it > 0 else None,
+                                   "unit": "GB/s", "note": "one inner iteration with all systems active, "
+                                   "timed by the autotuner with CUDA events"},
             "cpu_baseline": cpu,
             "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "seconds": e2e_s,

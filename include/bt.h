@@ -277,13 +277,17 @@ enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
  * captured step graph; BT_OPT_VARIANT_ROW / _HALO bypass the autotuner and
  * use that Krylov variant together with the row / halo double-float residuals
  * (bt_get_tuning; _HALO falls back to the tuned choice where the halo tiles
- * are not available). */
+ * are not available); BT_OPT_VARIANT_SLICE bypasses the autotuner's Krylov
+ * choice for the slice-tiled iteration (residual kernel still tuned; falls
+ * back to the tuned choice when the padded RHS width is not a multiple of 32
+ * or a row does not fit a slice tile). */
 enum {
   BT_OPT_RESID_FP64 = 1u,
   BT_OPT_PROFILE = 2u,
   BT_OPT_NO_GRAPH = 4u,
   BT_OPT_VARIANT_ROW = 8u,
-  BT_OPT_VARIANT_HALO = 16u
+  BT_OPT_VARIANT_HALO = 16u,
+  BT_OPT_VARIANT_SLICE = 32u
 };
 typedef struct bt_solver_opts {
   double tol_fp64;      /* plain FP64 stopping tolerance (default 1e-12)          */
@@ -324,7 +328,12 @@ bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_
  *   1  halo-staged apply (Morton-ordered row tiles, their halo rows of X staged
  *      in shared memory, search-direction and solution updates fused in) +
  *      z update; offered in BT_MODE_MIXED only
- * ms_iter [2] (may be NULL) receives the measured ms per iteration of each
+ *   2  slice-tiled apply (Morton tiles, one 32-system slice of the halo rows
+ *      of p staged in shared memory in two pipelined stages, <p, q> and the
+ *      two inner products that give the next rho fused in) + one fused
+ *      x, r, p update; offered in BT_MODE_MIXED when the padded RHS width is
+ *      a multiple of 32
+ * ms_iter [3] (may be NULL) receives the measured ms per iteration of each
  * (0 = not timed).  The double-float correction residual is tuned on its own:
  * resid_variant 0 = row kernel, 1 = halo-staged kernel (the step-start
  * residual follows it), ms_resid [2] the measured ms per launch of each.

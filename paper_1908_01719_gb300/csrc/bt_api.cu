@@ -759,6 +759,85 @@ HaloArgs halo_args(const bt_ctx* ctx) {
                   ctx->halo_umax};
 }
 
+// Slice tiles (owned rows longest first, FP32 planes in tile-entry order) and
+// the plan of tile blocks for S slices of 32 systems: about one block per SM
+// in all (the blocks hold two stages of ~97 KB), split over the segments in
+// proportion to their tiles, at least one each.  Sets ctx->slice_ok = false
+// when a row does not fit a tile (the slice iteration is then not offered).
+bt_status ensure_slice(bt_ctx* ctx, int S, cudaStream_t st) {
+  if (!ctx->slice_attr) {
+    slice_prepare();
+    CKL();
+    ctx->slice_attr = true;
+  }
+  if (ctx->slice_for != ctx->seg_row0) {
+    HaloTiles t;
+    build_halo_tiles(ctx->mesh, ctx->seg_row0, SL_UMAX, SL_TMAX, SL_EMAX, t, true);
+    ctx->slice_for = ctx->seg_row0;
+    ctx->slice_ok = !t.too_wide;
+    ctx->slice_planes_version = -1;
+    ctx->slice_S = 0;
+    if (!ctx->slice_ok) return BT_OK;
+    CK(upload(ctx->s_r0, t.r0, st));
+    CK(upload(ctx->s_rows, t.rows, st));
+    CK(upload(ctx->s_rowe, t.rowe, st));
+    t.rowl.push_back(0);  // padding: the kernel copies local row indices in 4-byte words
+    t.rowl.push_back(0);
+    CK(upload(ctx->s_rowl, t.rowl, st));
+    CK(upload(ctx->s_u0, t.u0, st));
+    CK(upload(ctx->s_e0, t.e0, st));
+    CK(upload(ctx->s_ucol, t.ucol, st));
+    t.lidx.push_back(0);  // padding: the kernel copies local indices in 4-byte words
+    t.lidx.push_back(0);
+    CK(upload(ctx->s_lidx, t.lidx, st));
+    CK(upload(ctx->s_slot, t.slot, st));
+    CK(upload(ctx->s_seg0, t.seg_tile0, st));
+    ctx->slice_seg_tile0 = t.seg_tile0;
+    CK(cudaStreamSynchronize(st));
+  }
+  if (!ctx->slice_ok) return BT_OK;
+  if (ctx->slice_planes_version != ctx->planes_version) {
+    CK(ensure(ctx->s_pkt, ctx->mesh.nnz));
+    CK(ensure(ctx->s_mdt, ctx->mesh.nnz));
+    launch_gather_tile_planes(ctx->s_slot.p, ctx->mesh.nnz, ctx->d_pk32.p, ctx->d_md32.p, ctx->s_pkt.p,
+                              ctx->s_mdt.p, st);
+    CKL();
+    ctx->slice_planes_version = ctx->planes_version;
+  }
+  if (ctx->slice_S != S) {
+    const int G = ctx->G;
+    const auto& t0 = ctx->slice_seg_tile0;
+    const int64_t T = std::max<int64_t>(1, t0[G] - t0[0]);
+    const int target = std::max(1, ctx->sms / S);
+    std::vector<int> blk_seg, blk0(G + 1, 0);
+    for (int g = 0; g < G; ++g) {
+      const int64_t Tg = t0[g + 1] - t0[g];
+      int64_t nbg = (int64_t)std::llround((double)target * Tg / (double)T);
+      nbg = std::max<int64_t>(1, std::min<int64_t>(nbg, std::max<int64_t>(1, Tg)));
+      blk0[g + 1] = blk0[g] + (int)nbg;
+      for (int64_t k = 0; k < nbg; ++k) blk_seg.push_back(g);
+    }
+    CK(upload(ctx->s_blk_seg, blk_seg, st));
+    CK(upload(ctx->s_blk0, blk0, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->slice_nblk = blk0[G];
+    ctx->slice_S = S;
+  }
+  return BT_OK;
+}
+
+HaloArgs slice_args(const bt_ctx* ctx) {
+  return HaloArgs{ctx->s_r0.p,   ctx->s_rows.p, ctx->s_rowe.p, ctx->s_rowl.p, ctx->s_u0.p,  ctx->s_e0.p,
+                  ctx->s_ucol.p, ctx->s_lidx.p, ctx->s_pkt.p,  ctx->s_mdt.p,  nullptr,      ctx->s_seg0.p,
+                  SL_UMAX};
+}
+// the x/p update of the slice iteration keeps a counter of its own (it only
+// uses the last-block ticket)
+RedScratch rs_xp(const bt_ctx* ctx) { return RedScratch{ctx->red_part.p, ctx->red_counter.p + 10}; }
+SegPlan slice_plan(const bt_ctx* ctx) {
+  return SegPlan{ctx->s_blk_seg.p, ctx->s_blk0.p, ctx->d_row0.p, ctx->G, ctx->slice_nblk};
+}
+
 // Autotuner: time one Krylov iteration of each variant on the real pattern
 // and RHS count (CUDA events, 3 iterations after a warm-up) and keep the
 // faster, cached per (RHS, RHS per lane, segments):
@@ -768,12 +847,13 @@ HaloArgs halo_args(const bt_ctx* ctx) {
 // timing); the Krylov init of the first solve re-initialises all of it.
 bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const KrylovState& ks,
                         const RefineState& rf, RedScratch rs, RedScratch rs2, int conj, int nb, int SY, int Rs, int G,
-                        bool allow_halo, bool df, int* variant, bool* resid_halo) {
+                        bool allow_halo, bool allow_slice, bool df, int* variant, bool* resid_halo) {
   bt_ctx::Tuned* hit = nullptr;
   for (auto& t : ctx->tuned)
     if (t.R == Rs && t.nb == nb && t.G == G) hit = &t;
   const bool halo = allow_halo && ctx->halo_ok;
-  if (!hit || (halo && hit->ms[1] == 0) || (halo && df && hit->ms_resid[1] == 0)) {
+  const bool slice = allow_slice && ctx->slice_ok;
+  if (!hit || (halo && hit->ms[1] == 0) || (slice && hit->ms[2] == 0) || (halo && df && hit->ms_resid[1] == 0)) {
     cudaStream_t st = ctx->stream;
     const size_t NE = (size_t)op.n * op.Rp;
     std::vector<double> one(2 * (size_t)SY), small(2 * (size_t)SY), half(2 * (size_t)SY), big(SY, 1e300);
@@ -799,7 +879,11 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     for (float2* b : {ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ctx->p32b.p})
       if (b) CK(cudaMemsetAsync(b, 0x3e, NE * sizeof(float2), st));
     auto iter = [&](int v) {
-      if (v == 1) {
+      if (v == 2) {
+        launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx), ctx->p32.p, ctx->q32.p, ks, rs, conj, nb, st);
+        launch_slice_r(op, va, ctx->r32.p, ctx->q32.p, ks, rs2, conj, st);
+        launch_slice_xp(op, va, ctx->x32.p, ctx->p32.p, ctx->r32.p, ks, rs_xp(ctx), st);
+      } else if (v == 1) {
         launch_spmm_halo(op, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, ks, rs,
                          conj, nb, st);
         launch_krylov_update_z(op, va, ctx->r32.p, ctx->q32.p, ks, rs2, conj, st);
@@ -813,8 +897,9 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0}, {0, 0}};
-    for (int v = 0; v < (halo ? 2 : 1); ++v) {
+    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0, 0}, {0, 0}};
+    for (int v = 0; v < 3; ++v) {
+      if ((v == 1 && !halo) || (v == 2 && !slice)) continue;
       if (bt_status e = prime()) return e;
       iter(v);  // warm-up
       CK(cudaEventRecord(e0, st));
@@ -862,7 +947,12 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     else ctx->tuned.push_back(tu);
     hit = hit ? hit : &ctx->tuned.back();
   }
-  *variant = (halo && hit->ms[1] > 0 && hit->ms[1] < hit->ms[0]) ? 1 : 0;
+  int best = 0;
+  for (int v = 1; v < 3; ++v) {
+    const bool avail = v == 1 ? halo : slice;
+    if (avail && hit->ms[v] > 0 && hit->ms[v] < hit->ms[best]) best = v;
+  }
+  *variant = best;
   *resid_halo = halo && df && hit->ms_resid[1] > 0 && hit->ms_resid[1] < hit->ms_resid[0];
   hit->variant = *variant;
   hit->resid_halo = *resid_halo;
@@ -1045,6 +1135,11 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
             launch_spmm_halo(opL, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, g.ks,
                              rs_at(2), g.conj, g.nb, c3);
             launch_krylov_update_z(opL, g.va, ctx->r32.p, ctx->q32.p, g.ks, rs_at(3), g.conj, c3);
+          } else if (g.variant == 2) {
+            launch_spmm_slice(opL, slice_args(ctx), slice_plan(ctx), ctx->p32.p, ctx->q32.p, g.ks, rs_at(2), g.conj,
+                              g.nb, c3);
+            launch_slice_r(opL, g.va, ctx->r32.p, ctx->q32.p, g.ks, rs_at(3), g.conj, c3);
+            launch_slice_xp(opL, g.va, ctx->x32.p, ctx->p32.p, ctx->r32.p, g.ks, rs_xp(ctx), c3);
           } else {
             launch_spmm_krylov_f32(opL, ctx->p32.p, ctx->q32.p, g.ks, rs_at(2), g.conj, g.nb, ctx->sms, c3);
             launch_krylov_update_f32(opL, g.va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, g.ks, rs_at(3),
@@ -1215,7 +1310,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     CK(ensure(ctx->gram_out, (size_t)Rs * 55));
   }
   const size_t max_blocks = (size_t)std::max(ctx->sms * REDUCE_BLOCKS_PER_SM, ctx->nblk) + 64;
-  CK(ensure(ctx->red_part, max_blocks * Rp * 4));  // up to two complex partials per (block, RHS)
+  CK(ensure(ctx->red_part, max_blocks * Rp * 6));  // up to three complex partials per (block, RHS)
   // coefficient table: per step, [0] = r_0 operator (R_n - L_n), [1] = L_n
   // coefficient table [step][0 = r_0 operator (R_n - L_n), 1 = L_n][segment]
   const int N = ctx->n_steps;
@@ -1284,15 +1379,19 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   bool resid_halo = false;
   if (!plain) {
     const bool allow_halo = !learned && !col;
+    const bool allow_slice = !learned && !col && Rp % 32 == 0;
     if (allow_halo)
       if (bt_status e = ensure_halo(ctx, nb, st)) return e;
+    if (allow_slice)
+      if (bt_status e = ensure_slice(ctx, Rp / 32, st)) return e;
     OpArgs opt = op;
     opt.coef = ctx->d_coef.p + G;  // step 1, L operator
-    if (bt_status e = autotune_spmm(ctx, opt, va, ks, rf, rs_at(2), rs_at(3), conj, nb, SY, Rs, G, allow_halo, df,
-                                    &variant, &resid_halo))
+    if (bt_status e = autotune_spmm(ctx, opt, va, ks, rf, rs_at(2), rs_at(3), conj, nb, SY, Rs, G, allow_halo,
+                                    allow_slice, df, &variant, &resid_halo))
       return e;
     if (o.flags & BT_OPT_VARIANT_ROW) variant = 0, resid_halo = false;
     if ((o.flags & BT_OPT_VARIANT_HALO) && allow_halo && ctx->halo_ok) variant = 1, resid_halo = df;
+    if ((o.flags & BT_OPT_VARIANT_SLICE) && allow_slice && ctx->slice_ok) variant = 2;
   }
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
   ctx->st_spmm_ms = ctx->st_resid_ms = 0;
@@ -1425,6 +1524,13 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
           });
           launch_krylov_update_z(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
           L -= 1;  // two launches per iteration
+        } else if (variant == 2) {
+          timed(0, [&] {
+            launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx), ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb,
+                              st);
+          });
+          launch_slice_r(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
+          launch_slice_xp(op, va, ctx->x32.p, ctx->p32.p, ctx->r32.p, ks, rs_xp(ctx), st);
         } else {
           timed(0, [&] { launch_spmm_krylov_f32(op, ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb, ctx->sms, st); });
           launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs_at(3), conj,
@@ -1579,10 +1685,10 @@ extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* 
   const auto& t = ctx->tuned.back();
   if (variant) *variant = t.variant;
   if (resid_variant) *resid_variant = t.resid_halo ? 1 : 0;
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 3; ++k)
     if (ms_iter) ms_iter[k] = t.ms[k];
+  for (int k = 0; k < 2; ++k)
     if (ms_resid) ms_resid[k] = t.ms_resid[k];
-  }
   return BT_OK;
 }
 

@@ -71,13 +71,18 @@ struct HaloTiles {
   std::vector<int32_t> seg_tile0; // [G + 1]
 };
 void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, int umax, int tmax, int emax,
-                      HaloTiles& t);
+                      HaloTiles& t, bool sort_by_len = false);
 // tile limits of the halo kernels: rows and entries per tile, and the shared
 // memory (bytes) one block of the halo apply may use for its staged rows and
 // entries
 constexpr int HALO_TMAX = 128;
 constexpr int HALO_EMAX = 448;
 constexpr int HALO_SMEM_BUDGET = 96 * 1024;
+// tile limits of the slice-tiled apply: halo rows (one 256-byte slice each in
+// shared memory), owned rows and entries per tile
+constexpr int SL_UMAX = 256;
+constexpr int SL_TMAX = 128;
+constexpr int SL_EMAX = 1536;
 
 // Weak pseudo-periodic coupling of the box faces (artificial permeability,
 // Appendix B): the boundary-face mass B on both sides of every selected axis

@@ -437,7 +437,7 @@ static uint64_t spread3(uint64_t v) {
 }
 
 void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, int umax, int tmax, int emax,
-                      HaloTiles& t) {
+                      HaloTiles& t, bool sort_by_len) {
   t = HaloTiles();
   t.umax = umax;
   const int G = (int)seg_row0.size() - 1;
@@ -525,7 +525,7 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
     t.slot.resize(ne0 + eo.back());
     std::atomic<bool> bad{false};
     parallel_for((int64_t)spans.size(), [&](int64_t b0, int64_t b1) {
-      std::vector<int32_t> uc;
+      std::vector<int32_t> uc, span_rows;
       for (int64_t s2 = b0; s2 < b1; ++s2) {
         const Span& sp = spans[s2];
         uc.clear();
@@ -547,9 +547,17 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
         t.e0[T0 + s2] = (int32_t)(ne0 + eo[s2]);
         for (size_t u = 0; u < uc.size(); ++u) t.ucol[nu0 + uo[s2] + u] = (uint32_t)uc[u];
         int64_t e = ne0 + eo[s2];
-        for (size_t q = sp.i0; q < sp.i1; ++q) {
-          const int32_t r = order[q].second;
-          const size_t j = nrow0 + ro[s2] + (q - sp.i0);
+        // owned rows in curve order, or longest first (rows of similar length
+        // then share a warp in the slice-tiled apply)
+        span_rows.clear();
+        for (size_t q = sp.i0; q < sp.i1; ++q) span_rows.push_back(order[q].second);
+        if (sort_by_len)
+          std::stable_sort(span_rows.begin(), span_rows.end(), [&](int32_t x, int32_t y) {
+            return m.row_ptr[x + 1] - m.row_ptr[x] > m.row_ptr[y + 1] - m.row_ptr[y];
+          });
+        for (size_t qq = 0; qq < span_rows.size(); ++qq) {
+          const int32_t r = span_rows[qq];
+          const size_t j = nrow0 + ro[s2] + qq;
           t.ucol[nu0 + uo[s2] + lp(r)] |= 0x80000000u;  // owned by this tile
           t.rows[j] = r;
           t.rowe[j] = (int32_t)e;

@@ -1,0 +1,613 @@
+// Slice-tiled Jacobi COCG/CG iteration: three launches and ten vector passes
+// per Krylov iteration, every inner product computed directly from the
+// vectors it is defined by (the textbook recurrences).
+//
+// Notation: L = the step operator of Appendix B (lab frame) or Appendix A
+// (transformed frame), D = diag(L) (complex per system; real for CG), and
+// (a, b) the unconjugated bilinear form (COCG, lab frame) or a^H b (CG,
+// transformed frame).  Iteration k:
+//   spmm:   q = L p,  alpha = rho / (p, q)                 p gathered, q written
+//   update: r -= alpha q,  z = D^-1 r,  rho' = (r, z),  |r|^2,  beta = rho'/rho
+//                                                          r, q read, r written
+//   xp:     x += alpha p,  p = D^-1 r + beta p             x, p, r read, x, p written
+// The x update rides on the p update (both read p), which is where the ten
+// passes come from (the row variant's eleven read p twice).  One-reduction
+// rearrangements (the rho' expansion, Chronopoulos-Gear) were tried and lose
+// too much accuracy for the complex symmetric COCG of the lab frame, whose
+// bilinear forms cancel strongly.
+//
+// SpMM layout.  Rows are grouped into Morton tiles (HaloTiles, owned rows
+// sorted longest first).  A block handles one slice of 32 systems of every
+// tile assigned to it: lanes per row LPR = 32 / NB, NB systems per lane (the NB
+// b-values of one direction, sharing the direction operator), NB rows per
+// warp.  For every tile the block stages, with cp.async into one of two
+// shared-memory stages (the next tile's copies overlap this tile's sums):
+//   - the slice of p at every halo row of the tile (32 complex = 256 B),
+//   - the tile's entries: FP32 planes {A0, d0, d1, d2}, MD, 16-bit local
+//     column indices, and the owned rows' ids, entry offsets and local indices.
+// Each staged value is read from shared memory once per nonzero that needs
+// it, instead of once per nonzero from L2, and the own-row p of (p, q) comes
+// from the same stage.  Within a warp the NB row groups read their NB chunks
+// in rotated order (group g reads chunk (k + g) mod NB at step k), which keeps
+// the reads free of bank conflicts.
+#include "bt_kernels.cuh"
+
+namespace bt {
+
+namespace {
+
+constexpr int SL_THREADS = 256;
+// shared memory of one stage: halo rows (32 float2 each), then the entries
+constexpr size_t SL_HALO_BYTES = (size_t)SL_UMAX * 32 * sizeof(float2);
+constexpr size_t SL_PK_BYTES = (size_t)SL_EMAX * sizeof(float4);
+constexpr size_t SL_MD_BYTES = (size_t)SL_EMAX * sizeof(float);
+constexpr size_t SL_LI_BYTES = (((size_t)SL_EMAX + 8) * sizeof(uint16_t) + 15) / 16 * 16;
+// owned rows: ids, entry offsets (one more), local indices (16-bit, copied in 4-byte words)
+constexpr size_t SL_ROW_BYTES = (((size_t)SL_TMAX * 4 + ((size_t)SL_TMAX + 1) * 4 + ((size_t)SL_TMAX + 4) * 2) + 15) /
+                                16 * 16;
+constexpr size_t SL_STAGE_BYTES = SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES + SL_LI_BYTES + SL_ROW_BYTES;
+static_assert(SL_STAGE_BYTES % 16 == 0, "stage alignment");
+
+__device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa4(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// 1 / d for a complex diagonal d = (re, im); the same arithmetic in both
+// launches, so z = D^-1 r agrees bit for bit between them
+__device__ __forceinline__ float2 diag_inv(float re, float im) {
+  const float s = __frcp_rn(fmaf(re, re, im * im));
+  return make_float2(re * s, -im * s);
+}
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// acc += a b
+__device__ __forceinline__ void cmacf(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// Per-lane FP32 partials (slot k of group g holds system (k + g) mod NB) are
+// un-rotated into system order, summed over the NB row groups of the warp and
+// added in FP64 to the partials kept by the lanes of group 0.
+template <int NB, int LPR>
+__device__ __forceinline__ void slice_flush(float2 (&a32)[NB][1], double2 (&a64)[NB][1], int g) {
+  // exact selection by bit masks (a data-dependent register index would be
+  // placed in local memory)
+  float2 sys[NB][1];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int c = 0; c < 1; ++c) {
+      unsigned vx = 0u, vy = 0u;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        const unsigned msk = (((b - g + NB) % NB) == k) ? 0xFFFFFFFFu : 0u;
+        vx |= __float_as_uint(a32[k][c].x) & msk;
+        vy |= __float_as_uint(a32[k][c].y) & msk;
+      }
+      sys[b][c] = make_float2(__uint_as_float(vx), __uint_as_float(vy));
+    }
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int c = 0; c < 1; ++c) {
+      float2 v = sys[b][c];
+#pragma unroll
+      for (int o = LPR; o < 32; o <<= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (g == 0) {
+        a64[b][c].x += (double)v.x;
+        a64[b][c].y += (double)v.y;
+      }
+      a32[b][c] = make_float2(0.f, 0.f);
+    }
+}
+
+}  // namespace
+
+size_t slice_smem_bytes() { return 2 * SL_STAGE_BYTES; }
+
+// ---------------------------------------------------------------- SpMM + (p, q)
+template <int NB, bool TRANSF, bool CONJ>
+__global__ void __launch_bounds__(SL_THREADS, 1)
+    k_spmm_slice(OpArgs op, HaloArgs h, SegPlan spt, int S, const float2* __restrict__ p, float2* __restrict__ q,
+                 KrylovState ks, RedScratch rs) {
+  if (*ks.n_active == 0) return;
+  constexpr int LPR = 32 / NB;   // lanes per row
+  constexpr int PPC = 16 / NB;   // 16-byte pieces per chunk of LPR complex values
+  constexpr int SLOTS = 8 * NB;  // rows in flight per block
+  constexpr int HPT = SL_UMAX * 16 / SL_THREADS;  // halo pieces per thread at most
+  extern __shared__ float4 sl_smem_[];
+  char* smem = reinterpret_cast<char*>(sl_smem_);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int slice = blockIdx.x % S, tb = blockIdx.x / S;
+  const int tt = slice / NB, jc = slice % NB;
+  const int g = lane / LPR, lp = lane % LPR;
+  const int L = LPR * jc + lp;
+  const int r0 = (tt * 32 + L) * NB;       // first system of this lane (in its segment)
+  const int c0 = tt * 32 * NB + L;         // its first column
+  const int cs = tt * 32 * NB + LPR * jc;  // first column of chunk 0 of the slice
+  const bool on = r0 < op.R;
+  const int sg = spt.blk_seg[tb], sk = tb - spt.blk0[sg], snb = spt.blk0[sg + 1] - spt.blk0[sg];
+  const OpCoef cf = op_coef(op, sg);
+  const int base = sg * op.R;
+  const int dsys = base + (on ? r0 : 0);
+  const float qx = (float)op.qhat[3 * dsys], qy = (float)op.qhat[3 * dsys + 1], qz = (float)op.qhat[3 * dsys + 2];
+  const float ca = (float)cf.a;
+  // slot k holds system b = (k + g) mod NB
+  float cb[NB], cc[NB];
+  int off[NB], colk[NB];
+  bool act[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int b = (k + g) % NB, rr = r0 + b;
+    const double qq = (on && rr < op.R) ? op.q[base + rr] : 0.0;
+    cb[k] = (float)(cf.bq2 * qq * qq);
+    cc[k] = (float)(cf.cq * qq);
+    act[k] = on && rr < op.R && ks.active[base + rr] != 0;
+    off[k] = b * LPR;
+    colk[k] = c0 + 32 * b;
+  }
+  // (p, q) per slot: FP32 over a few tiles, then warp-reduced into FP64
+  float2 a32[NB][1];
+  double2 a64[NB][1];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    a32[k][0] = make_float2(0.f, 0.f);
+    a64[k][0] = make_double2(0.0, 0.0);
+  }
+
+  const int T0 = h.seg_tile0[sg], T1 = h.seg_tile0[sg + 1];
+  auto stage_ptr = [&](int st) { return smem + (size_t)st * SL_STAGE_BYTES; };
+  auto issue = [&](int tau, int st) {
+    char* b0 = stage_ptr(st);
+    float2* sh = reinterpret_cast<float2*>(b0);
+    float4* spk = reinterpret_cast<float4*>(b0 + SL_HALO_BYTES);
+    float* smd = reinterpret_cast<float*>(b0 + SL_HALO_BYTES + SL_PK_BYTES);
+    uint32_t* sli = reinterpret_cast<uint32_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES);
+    int32_t* srow = reinterpret_cast<int32_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES + SL_LI_BYTES);
+    int32_t* srowe = srow + SL_TMAX;
+    uint32_t* srowl = reinterpret_cast<uint32_t*>(srowe + SL_TMAX + 1);
+    const int u0 = __ldg(h.u0 + tau), nu = __ldg(h.u0 + tau + 1) - u0;  // <= SL_UMAX (tile builder)
+    const int e0 = __ldg(h.e0 + tau), ne = __ldg(h.e0 + tau + 1) - e0;  // <= SL_EMAX
+    const int R0 = __ldg(h.t_r0 + tau), nown = __ldg(h.t_r0 + tau + 1) - R0;  // <= SL_TMAX
+    // halo rows: all row ids of this thread's pieces are loaded before any copy
+    uint32_t rid[HPT];
+#pragma unroll
+    for (int j = 0; j < HPT; ++j) {
+      const int u = (tid >> 4) + 16 * j;
+      rid[j] = u < nu ? (__ldg(h.ucol + u0 + u) & 0x7FFFFFFFu) : 0u;
+    }
+    const int pc = tid & 15, b = pc / PPC, pp = pc - b * PPC;
+#pragma unroll
+    for (int j = 0; j < HPT; ++j) {
+      const int u = (tid >> 4) + 16 * j;
+      if (u < nu) cpa16(sh + u * 32 + b * LPR + 2 * pp, p + (size_t)rid[j] * op.Rp + cs + 32 * b + 2 * pp);
+    }
+    for (int e = tid; e < ne; e += SL_THREADS) {
+      cpa16(spk + e, h.pkt + e0 + e);
+      if constexpr (TRANSF) cpa4(smd + e, h.mdt + e0 + e);
+    }
+    const int w0 = e0 >> 1, nw = ((e0 + ne + 1) >> 1) - w0;  // the index array is padded
+    for (int w = tid; w < nw; w += SL_THREADS) cpa4(sli + w, reinterpret_cast<const uint32_t*>(h.lidx) + w0 + w);
+    // owned rows: ids, entry offsets, local indices
+    for (int k = tid; k <= nown; k += SL_THREADS) {
+      if (k < nown) cpa4(srow + k, h.rows + R0 + k);
+      cpa4(srowe + k, h.rowe + R0 + k);
+    }
+    const int l0 = R0 >> 1, nl = ((R0 + nown + 1) >> 1) - l0;  // the local-index array is padded
+    for (int k = tid; k < nl; k += SL_THREADS) cpa4(srowl + k, reinterpret_cast<const uint32_t*>(h.rowl) + l0 + k);
+  };
+
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) any |= act[k];
+  int ntile = 0;
+  if (__syncthreads_or(any)) {
+    int tau = T0 + sk;
+    if (tau < T1) issue(tau, 0);
+    cpa_commit();
+    for (int it = 0; tau < T1; tau += snb, ++it) {
+      const int st = it & 1;
+      if (tau + snb < T1) issue(tau + snb, st ^ 1);
+      cpa_commit();
+      cpa_wait<1>();  // this thread's copies of tile tau have landed
+      __syncthreads();
+      const char* b0 = stage_ptr(st);
+      const float2* sh = reinterpret_cast<const float2*>(b0);
+      const float4* spk = reinterpret_cast<const float4*>(b0 + SL_HALO_BYTES);
+      const float* smd = reinterpret_cast<const float*>(b0 + SL_HALO_BYTES + SL_PK_BYTES);
+      const int e0 = __ldg(h.e0 + tau);
+      const uint16_t* sli =
+          reinterpret_cast<const uint16_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES) + (e0 & 1);
+      const int32_t* srow =
+          reinterpret_cast<const int32_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES + SL_LI_BYTES);
+      const int32_t* srowe = srow + SL_TMAX;
+      const int R0 = __ldg(h.t_r0 + tau), nown = __ldg(h.t_r0 + tau + 1) - R0;
+      const uint16_t* srowl = reinterpret_cast<const uint16_t*>(srowe + SL_TMAX + 1) + (R0 & 1);
+      const float2* xs = sh + lp;
+      for (int k = warp * NB + g; k < nown; k += SLOTS) {
+        const int row = srow[k];
+        const int ea = srowe[k] - e0, eb = srowe[k + 1] - e0;
+        const int lo = srowl[k];
+        float2 P[NB], Q[NB];
+#pragma unroll
+        for (int kk = 0; kk < NB; ++kk) P[kk] = Q[kk] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int e = ea; e < eb; ++e) {
+          const float4 v = spk[e];
+          const int l = sli[e];
+          const float m = fmaf(qx, v.y, fmaf(qy, v.z, qz * v.w));
+          const float a0 = ca * v.x;
+          float z1 = 0.f;
+          if constexpr (TRANSF) z1 = smd[e];
+          const float2* xr = xs + l * 32;
+          const float2 m2 = make_float2(m, m);
+#pragma unroll
+          for (int kk = 0; kk < NB; ++kk) {
+            const float2 xx = xr[off[kk]];
+            float c = a0;
+            if constexpr (TRANSF) c = fmaf(cb[kk], z1, c);
+            P[kk] = __ffma2_rn(make_float2(c, c), xx, P[kk]);
+            Q[kk] = __ffma2_rn(m2, xx, Q[kk]);
+          }
+        }
+        const size_t erow = (size_t)row * op.Rp;
+        const float2* pown = xs + lo * 32;
+#pragma unroll
+        for (int kk = 0; kk < NB; ++kk) {
+          const float2 y = make_float2(fmaf(-cc[kk], Q[kk].y, P[kk].x), fmaf(cc[kk], Q[kk].x, P[kk].y));
+          if (act[kk]) __stcs(q + erow + colk[kk], y);
+          float2 pv = pown[off[kk]];
+          if constexpr (CONJ) pv = conjf2(pv);
+          const float wgt = act[kk] ? 1.f : 0.f;  // inactive systems add zeros
+          cmacf(a32[kk][0], make_float2(wgt * pv.x, wgt * pv.y), y);
+        }
+      }
+      if ((++ntile & 3) == 0) slice_flush<NB, LPR>(a32, a64, g);
+      __syncthreads();  // the stage is refilled two tiles from now
+    }
+    cpa_wait<0>();
+  }
+  slice_flush<NB, LPR>(a32, a64, g);
+  // block reduction: group-0 lanes of each warp hold FP64 partials of the
+  // slice's 32 systems (lane lp: systems L*NB .. L*NB+NB-1)
+  __syncthreads();
+  double2* red = reinterpret_cast<double2*>(smem);  // [8 warps][32 systems]
+  if (g == 0) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) red[(size_t)warp * 32 + lp * NB + b] = a64[b][0];
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double2 sum = make_double2(0.0, 0.0);
+    for (int wp = 0; wp < 8; ++wp) {
+      const double2 v = red[(size_t)wp * 32 + tid];
+      sum.x += v.x;
+      sum.y += v.y;
+    }
+    // slice system tid = lp * NB + b belongs to lane L = LPR jc + lp
+    const int rloc = (tt * 32 + LPR * jc + tid / NB) * NB + tid % NB;
+    if (rloc < op.R) reinterpret_cast<double2*>(rs.part)[(size_t)tb * op.Rp + rloc] = sum;
+  }
+  if (!last_block(rs.counter, gridDim.x)) return;
+  if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
+  __syncthreads();
+  for (int s = threadIdx.x; s < spt.G * op.R; s += blockDim.x) {
+    const int gg = s / op.R, rl = s - gg * op.R;
+    double2 t = make_double2(0, 0);
+    for (int b = spt.blk0[gg]; b < spt.blk0[gg + 1]; ++b) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(rs.part) + (size_t)b * op.Rp + rl);
+      t.x += v.x;
+      t.y += v.y;
+    }
+    krylov_alpha(ks, s, t);
+    ks.pend[s] = ks.active[s];  // the x update of this iteration is still to do
+  }
+}
+
+// ---------------------------------------------------------------- vector updates
+// Column map of the two elementwise launches: each thread owns two adjacent
+// columns (16-byte accesses) and, inside the block's contiguous share of its
+// segment's rows, every rpp-th row.
+struct PairMap {
+  int TPR, rpp, cp, ro, nch;
+  bool live;
+  __device__ PairMap(int Rp) {
+    const int half = Rp / 2;  // column pairs per row
+    TPR = half < 256 ? half : 256;
+    rpp = 256 / TPR;
+    cp = threadIdx.x % TPR;
+    ro = threadIdx.x / TPR;
+    nch = (half + 255) / 256;
+    live = (int)threadIdx.x < rpp * TPR;
+  }
+};
+
+// per-system constants of the Jacobi diagonal d = A0_ii + b MD_ii + i c (qhat . Pd_ii)
+struct DiagCoef {
+  float cb, cc, qx, qy, qz;
+};
+__device__ __forceinline__ DiagCoef diag_coef(const OpArgs& op, const OpCoef& cf, int s, bool valid) {
+  const double qq = valid ? op.q[s] : 0.0;
+  DiagCoef d;
+  d.cb = (float)(cf.bq2 * qq * qq);
+  d.cc = (float)(cf.cq * qq);
+  d.qx = valid ? (float)op.qhat[3 * s] : 0.f;
+  d.qy = valid ? (float)op.qhat[3 * s + 1] : 0.f;
+  d.qz = valid ? (float)op.qhat[3 * s + 2] : 0.f;
+  return d;
+}
+__device__ __forceinline__ float2 diag_of(const DiagCoef& c, float4 dg, float dm) {
+  return make_float2(fmaf(c.cb, dm, dg.x), c.cc * fmaf(c.qx, dg.y, fmaf(c.qy, dg.z, c.qz * dg.w)));
+}
+
+// r -= alpha q; z = D^-1 r; rho' = (r, z), |r|^2 (FP32 over at most 32 rows,
+// then FP64); the last block applies the convergence tests and forms beta.
+template <bool CONJ>
+__global__ void __launch_bounds__(256, 2) k_slice_r(OpArgs op, VecArgs va, float2* __restrict__ r,
+                                                    const float2* __restrict__ q, KrylovState ks, RedScratch rs) {
+  if (*ks.n_active == 0) return;
+  constexpr int U = 4;  // rows in flight per thread
+  const int Rp = va.Rp;
+  const PairMap pm(Rp);
+  BT_SEG_BEGIN(va.sp);
+  const int64_t per = (sr1_ - sr0_ + snb_ - 1) / snb_;
+  const int64_t rb = sr0_ + (int64_t)sk_ * per, re = min(sr1_, rb + per);
+  const OpCoef cf = op_coef(op, sg_);
+  const int base = sg_ * va.R;
+  __shared__ double2 sred[256][2][2];
+  for (int ch = 0; ch < pm.nch; ++ch) {
+    const int col = 2 * (pm.cp + 256 * ch);
+    double2 acc[2][2] = {{make_double2(0, 0), make_double2(0, 0)}, {make_double2(0, 0), make_double2(0, 0)}};
+    bool ac[2] = {false, false};
+    float2 al[2];
+    DiagCoef dc[2];
+    if (pm.live && col < Rp) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int rl = sys_of_col(col + u, va.nb), s = base + rl;
+        ac[u] = rl < va.R && ks.active[s] != 0;
+        al[u] = ac[u] ? make_float2((float)ks.alpha[2 * s], (float)ks.alpha[2 * s + 1]) : make_float2(0.f, 0.f);
+        dc[u] = diag_coef(op, cf, s, rl < va.R);
+      }
+    }
+    if (ac[0] || ac[1]) {
+      float2 fr[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      float fn[2] = {0.f, 0.f};
+      int cnt = 0;
+      for (int64_t i0 = rb + pm.ro; i0 < re; i0 += U * pm.rpp) {
+        float4 rv[U], qv[U], dg[U];
+        float dm[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t i = i0 + (int64_t)k * pm.rpp;
+          if (i < re) {
+            const size_t e = (size_t)i * Rp + col;
+            rv[k] = *reinterpret_cast<const float4*>(r + e);
+            qv[k] = __ldcs(reinterpret_cast<const float4*>(q + e));
+            dg[k] = __ldg(va.diag32 + i);
+            dm[k] = op.transformed ? __ldg(va.diag_md32 + i) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t i = i0 + (int64_t)k * pm.rpp;
+          if (i >= re) break;
+          float2 rs2[2] = {make_float2(rv[k].x, rv[k].y), make_float2(rv[k].z, rv[k].w)};
+          const float2 qs[2] = {make_float2(qv[k].x, qv[k].y), make_float2(qv[k].z, qv[k].w)};
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (!ac[u]) continue;
+            cmacf(rs2[u], make_float2(-al[u].x, -al[u].y), qs[u]);
+            const float2 d = diag_of(dc[u], dg[k], dm[k]);
+            const float2 z = cmulf(rs2[u], diag_inv(d.x, d.y));
+            cmacf(fr[u], CONJ ? conjf2(rs2[u]) : rs2[u], z);
+            fn[u] = fmaf(rs2[u].x, rs2[u].x, fmaf(rs2[u].y, rs2[u].y, fn[u]));
+          }
+          *reinterpret_cast<float4*>(r + (size_t)i * Rp + col) = make_float4(rs2[0].x, rs2[0].y, rs2[1].x, rs2[1].y);
+        }
+        if (++cnt == 8) {  // FP32 over at most 32 rows, then FP64
+          cnt = 0;
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            acc[u][0].x += fr[u].x;
+            acc[u][0].y += fr[u].y;
+            acc[u][1].x += fn[u];
+            fr[u] = make_float2(0.f, 0.f);
+            fn[u] = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        acc[u][0].x += fr[u].x;
+        acc[u][0].y += fr[u].y;
+        acc[u][1].x += fn[u];
+      }
+    }
+    // block reduction over the rows-per-pass groups; partials [block][system][2]
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      sred[threadIdx.x][u][0] = acc[u][0];
+      sred[threadIdx.x][u][1] = acc[u][1];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < pm.TPR && col < Rp) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
+        for (int o = 0; o < pm.rpp; ++o) {
+          const double2 a0 = sred[o * pm.TPR + threadIdx.x][u][0], a1 = sred[o * pm.TPR + threadIdx.x][u][1];
+          s0.x += a0.x;
+          s0.y += a0.y;
+          s1.x += a1.x;
+        }
+        const int rl = sys_of_col(col + u, va.nb);
+        if (rl < va.R) {
+          double2* o2 = reinterpret_cast<double2*>(rs.part) + ((size_t)blockIdx.x * Rp + rl) * 2;
+          o2[0] = s0;
+          o2[1] = s1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!last_block(rs.counter, gridDim.x)) return;
+  __shared__ int s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+    if (!ks.active[s]) continue;
+    const int gg = s / va.R, rl = s - gg * va.R;
+    double2 o[2] = {make_double2(0, 0), make_double2(0, 0)};
+    for (int b = va.sp.blk0[gg]; b < va.sp.blk0[gg + 1]; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(rs.part) + ((size_t)b * Rp + rl) * 2 + c);
+        o[c].x += v.x;
+        o[c].y += v.y;
+      }
+    if (krylov_step_finish(ks, s, o, nullptr)) atomicAdd(&s_cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ks.n_active = s_cnt;
+}
+
+// x += alpha p for the systems of the last SpMM (pend), and p = D^-1 r + beta p
+// for those still active; the last block clears pend, so a launch after the
+// loop has ended changes nothing.
+__global__ void __launch_bounds__(256, 2) k_slice_xp(OpArgs op, VecArgs va, float2* __restrict__ x,
+                                                     float2* __restrict__ p, const float2* __restrict__ r,
+                                                     KrylovState ks, RedScratch rs) {
+  constexpr int U = 4;  // rows in flight per thread
+  const int Rp = va.Rp;
+  const PairMap pm(Rp);
+  BT_SEG_BEGIN(va.sp);
+  const int64_t per = (sr1_ - sr0_ + snb_ - 1) / snb_;
+  const int64_t rb = sr0_ + (int64_t)sk_ * per, re = min(sr1_, rb + per);
+  const OpCoef cf = op_coef(op, sg_);
+  const int base = sg_ * va.R;
+  if (pm.live) {
+    for (int ch = 0; ch < pm.nch; ++ch) {
+      const int col = 2 * (pm.cp + 256 * ch);
+      if (col >= Rp) continue;
+      bool pd[2], ac[2];
+      float2 al[2], be[2];
+      DiagCoef dc[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int rl = sys_of_col(col + u, va.nb), s = base + rl;
+        pd[u] = rl < va.R && ks.pend[s] != 0;
+        ac[u] = pd[u] && ks.active[s] != 0;
+        al[u] = pd[u] ? make_float2((float)ks.alpha[2 * s], (float)ks.alpha[2 * s + 1]) : make_float2(0.f, 0.f);
+        be[u] = ac[u] ? make_float2((float)ks.beta[2 * s], (float)ks.beta[2 * s + 1]) : make_float2(0.f, 0.f);
+        dc[u] = diag_coef(op, cf, s, rl < va.R);
+      }
+      if (!pd[0] && !pd[1]) continue;
+      const bool anyp = ac[0] || ac[1];
+      for (int64_t i0 = rb + pm.ro; i0 < re; i0 += U * pm.rpp) {
+        float4 xv[U], pv[U], rv[U], dg[U];
+        float dm[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t i = i0 + (int64_t)k * pm.rpp;
+          if (i < re) {
+            const size_t e = (size_t)i * Rp + col;
+            xv[k] = *reinterpret_cast<const float4*>(x + e);
+            pv[k] = *reinterpret_cast<const float4*>(p + e);
+            if (anyp) {
+              rv[k] = __ldcs(reinterpret_cast<const float4*>(r + e));
+              dg[k] = __ldg(va.diag32 + i);
+              dm[k] = op.transformed ? __ldg(va.diag_md32 + i) : 0.f;
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t i = i0 + (int64_t)k * pm.rpp;
+          if (i >= re) break;
+          float2 xs[2] = {make_float2(xv[k].x, xv[k].y), make_float2(xv[k].z, xv[k].w)};
+          float2 ps[2] = {make_float2(pv[k].x, pv[k].y), make_float2(pv[k].z, pv[k].w)};
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (!pd[u]) continue;
+            cmacf(xs[u], al[u], ps[u]);
+            if (ac[u]) {
+              const float2 rr = u == 0 ? make_float2(rv[k].x, rv[k].y) : make_float2(rv[k].z, rv[k].w);
+              const float2 d = diag_of(dc[u], dg[k], dm[k]);
+              float2 np = cmulf(rr, diag_inv(d.x, d.y));
+              cmacf(np, be[u], ps[u]);
+              ps[u] = np;
+            }
+          }
+          const size_t e = (size_t)i * Rp + col;
+          *reinterpret_cast<float4*>(x + e) = make_float4(xs[0].x, xs[0].y, xs[1].x, xs[1].y);
+          if (anyp) *reinterpret_cast<float4*>(p + e) = make_float4(ps[0].x, ps[0].y, ps[1].x, ps[1].y);
+        }
+      }
+    }
+  }
+  if (!last_block(rs.counter, gridDim.x)) return;
+  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) ks.pend[s] = 0;
+}
+
+// ---------------------------------------------------------------- launchers
+template <int NB, bool TRANSF, bool CONJ>
+static void slice_attr() {
+  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)slice_smem_bytes());
+}
+void slice_prepare() {
+  slice_attr<4, false, false>(); slice_attr<4, false, true>(); slice_attr<4, true, false>(); slice_attr<4, true, true>();
+  slice_attr<2, false, false>(); slice_attr<2, false, true>(); slice_attr<2, true, false>(); slice_attr<2, true, true>();
+  slice_attr<1, false, false>(); slice_attr<1, false, true>(); slice_attr<1, true, false>(); slice_attr<1, true, true>();
+}
+
+void launch_spmm_slice(const OpArgs& op, const HaloArgs& h, const SegPlan& spt, const float2* p, float2* q,
+                       const KrylovState& ks, RedScratch rs, int conj, int nb, cudaStream_t st) {
+  const int S = op.Rp / 32;
+  const dim3 grid(spt.nblk * S);
+  const size_t sm = slice_smem_bytes();
+#define BT_SL_CASE(NBV)                                                                                  \
+  if (op.transformed) {                                                                                  \
+    if (conj) k_spmm_slice<NBV, true, true><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);   \
+    else k_spmm_slice<NBV, true, false><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);       \
+  } else {                                                                                               \
+    if (conj) k_spmm_slice<NBV, false, true><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);  \
+    else k_spmm_slice<NBV, false, false><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);      \
+  }
+  switch (nb) {
+    case 4: BT_SL_CASE(4) break;
+    case 2: BT_SL_CASE(2) break;
+    default: BT_SL_CASE(1) break;
+  }
+#undef BT_SL_CASE
+}
+
+void launch_slice_r(const OpArgs& op, const VecArgs& va, float2* r, const float2* q, const KrylovState& ks,
+                    RedScratch rs, int conj, cudaStream_t st) {
+  if (conj) k_slice_r<true><<<va.sp.nblk, 256, 0, st>>>(op, va, r, q, ks, rs);
+  else k_slice_r<false><<<va.sp.nblk, 256, 0, st>>>(op, va, r, q, ks, rs);
+}
+
+void launch_slice_xp(const OpArgs& op, const VecArgs& va, float2* x, float2* p, const float2* r,
+                     const KrylovState& ks, RedScratch rs, cudaStream_t st) {
+  k_slice_xp<<<va.sp.nblk, 256, 0, st>>>(op, va, x, p, r, ks, rs);
+}
+
+}  // namespace bt

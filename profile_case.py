@@ -30,7 +30,7 @@ def main():
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--steps", type=int, default=2, help="time steps (pulse on throughout)")
     ap.add_argument("--mode", default="mixed", choices=["mixed", "plain"])
-    ap.add_argument("--variant", default="auto", choices=["auto", "row", "halo"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "row", "halo", "slice"],
                     help="inner Krylov variant (auto: the autotuner's choice)")
     a = ap.parse_args()
     build()
@@ -54,7 +54,8 @@ def main():
     sim = Simulation(p)
     mode = bt.BT_MODE_MIXED if a.mode == "mixed" else bt.BT_MODE_PLAIN_FP64
     flags = bt.BT_OPT_NO_GRAPH | bt.BT_OPT_PROFILE | {"auto": 0, "row": bt.BT_OPT_VARIANT_ROW,
-                                  "halo": bt.BT_OPT_VARIANT_HALO}[a.variant]
+                                                      "halo": bt.BT_OPT_VARIANT_HALO,
+                                                      "slice": bt.BT_OPT_VARIANT_SLICE}[a.variant]
     S, err, stat, _ = sim.run(mode, flags=flags)
     tuning = bt.bt_get_tuning(sim.ctx) if mode != bt.BT_MODE_PLAIN_FP64 else None
     st = sim.stats()
