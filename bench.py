@@ -245,12 +245,13 @@ def run_reference(args):
 # launch of the dominant kernel: the row SpMM reads X and writes Y; the
 # halo-staged apply reads z, p_prev and x and writes x, p and q; the
 # slice-tiled SpMM reads p and writes q
-VECTORS_PER_SYSTEM = {"row": 2, "halo": 6, "slice": 2}
+VECTORS_PER_SYSTEM = {"row": 2, "halo": 6, "slice": 2, "slice1": 2}
 # ... and per Krylov iteration (all launches of one iteration): row 2 + 6 + 3,
 # halo 6 + 3 (z update: reads z, q, writes z), slice 2 + 3 (r, q read, r
 # written) + 5 (x, p, r read, x, p written)
-VECTORS_PER_ITER = {"row": 11, "halo": 9, "slice": 10}
-KERNEL = {"row": "k_spmm_krylov", "halo": "k_spmm_halo", "slice": "k_spmm_slice"}
+VECTORS_PER_ITER = {"row": 11, "halo": 9, "slice": 10, "slice1": 10}
+KERNEL = {"row": "k_spmm_krylov", "halo": "k_spmm_halo", "slice": "k_spmm_slice (two stages)",
+          "slice1": "k_spmm_slice (one stage, two blocks per SM)"}
 
 
 # DRAM bytes (read + write) of one launch of the row SpMM k_spmm_krylov<4>, lab

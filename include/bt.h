@@ -278,16 +278,18 @@ enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
  * use that Krylov variant together with the row / halo double-float residuals
  * (bt_get_tuning; _HALO falls back to the tuned choice where the halo tiles
  * are not available); BT_OPT_VARIANT_SLICE bypasses the autotuner's Krylov
- * choice for the slice-tiled iteration (residual kernel still tuned; falls
- * back to the tuned choice when the padded RHS width is not a multiple of 32
- * or a row does not fit a slice tile). */
+ * choice for the slice-tiled iteration, the faster of its two configurations,
+ * or with BT_OPT_SLICE_ONE_STAGE the one-stage configuration (residual kernel
+ * still tuned; falls back to the tuned choice when the padded RHS width is
+ * not a multiple of 32 or a row does not fit a slice tile). */
 enum {
   BT_OPT_RESID_FP64 = 1u,
   BT_OPT_PROFILE = 2u,
   BT_OPT_NO_GRAPH = 4u,
   BT_OPT_VARIANT_ROW = 8u,
   BT_OPT_VARIANT_HALO = 16u,
-  BT_OPT_VARIANT_SLICE = 32u
+  BT_OPT_VARIANT_SLICE = 32u,
+  BT_OPT_SLICE_ONE_STAGE = 64u
 };
 typedef struct bt_solver_opts {
   double tol_fp64;      /* plain FP64 stopping tolerance (default 1e-12)          */
@@ -329,11 +331,11 @@ bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_
  *      in shared memory, search-direction and solution updates fused in) +
  *      z update; offered in BT_MODE_MIXED only
  *   2  slice-tiled apply (Morton tiles, one 32-system slice of the halo rows
- *      of p staged in shared memory in two pipelined stages, <p, q> and the
- *      two inner products that give the next rho fused in) + one fused
- *      x, r, p update; offered in BT_MODE_MIXED when the padded RHS width is
- *      a multiple of 32
- * ms_iter [3] (may be NULL) receives the measured ms per iteration of each
+ *      of p staged in shared memory, two pipelined stages, one block per SM)
+ *      + r update (rho', |r|^2) + x and p update; offered in BT_MODE_MIXED
+ *      when the padded RHS width is a multiple of 32
+ *   3  the same with one stage and two blocks per SM
+ * ms_iter [4] (may be NULL) receives the measured ms per iteration of each
  * (0 = not timed).  The double-float correction residual is tuned on its own:
  * resid_variant 0 = row kernel, 1 = halo-staged kernel (the step-start
  * residual follows it), ms_resid [2] the measured ms per launch of each.

@@ -20,7 +20,7 @@ BT_FRAME_LAB, BT_FRAME_TRANSFORMED = 0, 1
 BT_PGSE = 0
 BT_MODE_PLAIN_FP64, BT_MODE_MIXED, BT_MODE_LEARNED = 0, 1, 2
 BT_OPT_RESID_FP64, BT_OPT_PROFILE, BT_OPT_NO_GRAPH = 1, 2, 4
-BT_OPT_VARIANT_ROW, BT_OPT_VARIANT_HALO, BT_OPT_VARIANT_SLICE = 8, 16, 32
+BT_OPT_VARIANT_ROW, BT_OPT_VARIANT_HALO, BT_OPT_VARIANT_SLICE, BT_OPT_SLICE_ONE_STAGE = 8, 16, 32, 64
 PLANES = {"M": 0, "K": 1, "J": 2, "MD": 3, "Mx": 4, "My": 5, "Mz": 6, "Ex": 7, "Ey": 8, "Ez": 9, "A0": 10,
           "MR": 11}
 
@@ -411,10 +411,10 @@ def bt_precond_grad_noalloc(w_ptr, n, feat_ptr, G_ptr, h_ptr, grad_ptr, loss_ptr
 
 def bt_get_tuning(ctx):
     v = C.c_int32()
-    d = (C.c_double * 3)()
+    d = (C.c_double * 4)()
     rv = C.c_int32()
     dr = (C.c_double * 2)()
     _check(ctx, lib().bt_get_tuning(ctx, C.byref(v), d, C.byref(rv), dr))
-    return {"variant": ["row", "halo", "slice"][v.value], "ms_iter_row": d[0], "ms_iter_halo": d[1],
-            "ms_iter_slice": d[2], "resid_variant": ["row", "halo"][rv.value], "ms_resid_row": dr[0],
-            "ms_resid_halo": dr[1]}
+    return {"variant": ["row", "halo", "slice", "slice1"][v.value], "ms_iter_row": d[0], "ms_iter_halo": d[1],
+            "ms_iter_slice": d[2], "ms_iter_slice1": d[3], "resid_variant": ["row", "halo"][rv.value],
+            "ms_resid_row": dr[0], "ms_resid_halo": dr[1]}

@@ -772,11 +772,11 @@ bt_status ensure_slice(bt_ctx* ctx, int S, cudaStream_t st) {
   }
   if (ctx->slice_for != ctx->seg_row0) {
     HaloTiles t;
+    ctx->slice_plan[0].S = ctx->slice_plan[1].S = 0;
     build_halo_tiles(ctx->mesh, ctx->seg_row0, SL_UMAX, SL_TMAX, SL_EMAX, t, true);
     ctx->slice_for = ctx->seg_row0;
     ctx->slice_ok = !t.too_wide;
     ctx->slice_planes_version = -1;
-    ctx->slice_S = 0;
     if (!ctx->slice_ok) return BT_OK;
     CK(upload(ctx->s_r0, t.r0, st));
     CK(upload(ctx->s_rows, t.rows, st));
@@ -804,11 +804,13 @@ bt_status ensure_slice(bt_ctx* ctx, int S, cudaStream_t st) {
     CKL();
     ctx->slice_planes_version = ctx->planes_version;
   }
-  if (ctx->slice_S != S) {
+  for (int stages = 1; stages <= 2; ++stages) {
+    auto& pl = ctx->slice_plan[stages - 1];
+    if (pl.S == S) continue;
     const int G = ctx->G;
     const auto& t0 = ctx->slice_seg_tile0;
     const int64_t T = std::max<int64_t>(1, t0[G] - t0[0]);
-    const int target = std::max(1, ctx->sms / S);
+    const int target = std::max(1, ctx->sms * (3 - stages) / S);  // resident blocks: 3 - stages per SM
     std::vector<int> blk_seg, blk0(G + 1, 0);
     for (int g = 0; g < G; ++g) {
       const int64_t Tg = t0[g + 1] - t0[g];
@@ -817,11 +819,11 @@ bt_status ensure_slice(bt_ctx* ctx, int S, cudaStream_t st) {
       blk0[g + 1] = blk0[g] + (int)nbg;
       for (int64_t k = 0; k < nbg; ++k) blk_seg.push_back(g);
     }
-    CK(upload(ctx->s_blk_seg, blk_seg, st));
-    CK(upload(ctx->s_blk0, blk0, st));
+    CK(upload(pl.blk_seg, blk_seg, st));
+    CK(upload(pl.blk0, blk0, st));
     CK(cudaStreamSynchronize(st));
-    ctx->slice_nblk = blk0[G];
-    ctx->slice_S = S;
+    pl.nblk = blk0[G];
+    pl.S = S;
   }
   return BT_OK;
 }
@@ -834,9 +836,12 @@ HaloArgs slice_args(const bt_ctx* ctx) {
 // the x/p update of the slice iteration keeps a counter of its own (it only
 // uses the last-block ticket)
 RedScratch rs_xp(const bt_ctx* ctx) { return RedScratch{ctx->red_part.p, ctx->red_counter.p + 10}; }
-SegPlan slice_plan(const bt_ctx* ctx) {
-  return SegPlan{ctx->s_blk_seg.p, ctx->s_blk0.p, ctx->d_row0.p, ctx->G, ctx->slice_nblk};
+SegPlan slice_plan(const bt_ctx* ctx, int stages) {
+  const auto& pl = ctx->slice_plan[stages - 1];
+  return SegPlan{pl.blk_seg.p, pl.blk0.p, ctx->d_row0.p, ctx->G, pl.nblk};
 }
+// Krylov variants 2 and 3 are the slice-tiled iteration with two and one stages
+int slice_stages(int variant) { return variant == 2 ? 2 : 1; }
 
 // Autotuner: time one Krylov iteration of each variant on the real pattern
 // and RHS count (CUDA events, 3 iterations after a warm-up) and keep the
@@ -853,7 +858,8 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     if (t.R == Rs && t.nb == nb && t.G == G) hit = &t;
   const bool halo = allow_halo && ctx->halo_ok;
   const bool slice = allow_slice && ctx->slice_ok;
-  if (!hit || (halo && hit->ms[1] == 0) || (slice && hit->ms[2] == 0) || (halo && df && hit->ms_resid[1] == 0)) {
+  if (!hit || (halo && hit->ms[1] == 0) || (slice && (hit->ms[2] == 0 || hit->ms[3] == 0)) ||
+      (halo && df && hit->ms_resid[1] == 0)) {
     cudaStream_t st = ctx->stream;
     const size_t NE = (size_t)op.n * op.Rp;
     std::vector<double> one(2 * (size_t)SY), small(2 * (size_t)SY), half(2 * (size_t)SY), big(SY, 1e300);
@@ -879,8 +885,9 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     for (float2* b : {ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ctx->p32b.p})
       if (b) CK(cudaMemsetAsync(b, 0x3e, NE * sizeof(float2), st));
     auto iter = [&](int v) {
-      if (v == 2) {
-        launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx), ctx->p32.p, ctx->q32.p, ks, rs, conj, nb, st);
+      if (v >= 2) {
+        launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx, slice_stages(v)), ctx->p32.p, ctx->q32.p, ks, rs, conj,
+                          nb, slice_stages(v), st);
         launch_slice_r(op, va, ctx->r32.p, ctx->q32.p, ks, rs2, conj, st);
         launch_slice_xp(op, va, ctx->x32.p, ctx->p32.p, ctx->r32.p, ks, rs_xp(ctx), st);
       } else if (v == 1) {
@@ -897,9 +904,9 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0, 0}, {0, 0}};
-    for (int v = 0; v < 3; ++v) {
-      if ((v == 1 && !halo) || (v == 2 && !slice)) continue;
+    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0, 0, 0}, {0, 0}};
+    for (int v = 0; v < 4; ++v) {
+      if ((v == 1 && !halo) || (v >= 2 && !slice)) continue;
       if (bt_status e = prime()) return e;
       iter(v);  // warm-up
       CK(cudaEventRecord(e0, st));
@@ -948,7 +955,7 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     hit = hit ? hit : &ctx->tuned.back();
   }
   int best = 0;
-  for (int v = 1; v < 3; ++v) {
+  for (int v = 1; v < 4; ++v) {
     const bool avail = v == 1 ? halo : slice;
     if (avail && hit->ms[v] > 0 && hit->ms[v] < hit->ms[best]) best = v;
   }
@@ -1135,9 +1142,9 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
             launch_spmm_halo(opL, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, g.ks,
                              rs_at(2), g.conj, g.nb, c3);
             launch_krylov_update_z(opL, g.va, ctx->r32.p, ctx->q32.p, g.ks, rs_at(3), g.conj, c3);
-          } else if (g.variant == 2) {
-            launch_spmm_slice(opL, slice_args(ctx), slice_plan(ctx), ctx->p32.p, ctx->q32.p, g.ks, rs_at(2), g.conj,
-                              g.nb, c3);
+          } else if (g.variant >= 2) {
+            launch_spmm_slice(opL, slice_args(ctx), slice_plan(ctx, slice_stages(g.variant)), ctx->p32.p, ctx->q32.p,
+                              g.ks, rs_at(2), g.conj, g.nb, slice_stages(g.variant), c3);
             launch_slice_r(opL, g.va, ctx->r32.p, ctx->q32.p, g.ks, rs_at(3), g.conj, c3);
             launch_slice_xp(opL, g.va, ctx->x32.p, ctx->p32.p, ctx->r32.p, g.ks, rs_xp(ctx), c3);
           } else {
@@ -1391,7 +1398,11 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       return e;
     if (o.flags & BT_OPT_VARIANT_ROW) variant = 0, resid_halo = false;
     if ((o.flags & BT_OPT_VARIANT_HALO) && allow_halo && ctx->halo_ok) variant = 1, resid_halo = df;
-    if ((o.flags & BT_OPT_VARIANT_SLICE) && allow_slice && ctx->slice_ok) variant = 2;
+    if ((o.flags & BT_OPT_VARIANT_SLICE) && allow_slice && ctx->slice_ok && variant < 2) {
+      // the faster of the two slice configurations
+      const auto& tu = ctx->tuned.back();
+      variant = ((o.flags & BT_OPT_SLICE_ONE_STAGE) || (tu.ms[3] > 0 && tu.ms[3] < tu.ms[2])) ? 3 : 2;
+    }
   }
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
   ctx->st_spmm_ms = ctx->st_resid_ms = 0;
@@ -1524,10 +1535,10 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
           });
           launch_krylov_update_z(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
           L -= 1;  // two launches per iteration
-        } else if (variant == 2) {
+        } else if (variant >= 2) {
           timed(0, [&] {
-            launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx), ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb,
-                              st);
+            launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx, slice_stages(variant)), ctx->p32.p, ctx->q32.p, ks,
+                              rs_at(2), conj, nb, slice_stages(variant), st);
           });
           launch_slice_r(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
           launch_slice_xp(op, va, ctx->x32.p, ctx->p32.p, ctx->r32.p, ks, rs_xp(ctx), st);
@@ -1685,7 +1696,7 @@ extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* 
   const auto& t = ctx->tuned.back();
   if (variant) *variant = t.variant;
   if (resid_variant) *resid_variant = t.resid_halo ? 1 : 0;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 4; ++k)
     if (ms_iter) ms_iter[k] = t.ms[k];
   for (int k = 0; k < 2; ++k)
     if (ms_resid) ms_resid[k] = t.ms_resid[k];

@@ -87,7 +87,7 @@ struct bt_ctx {
   bool halo_attr = false;
   // slice tiles of the slice-tiled iteration (owned rows longest first) and
   // the plan of tile blocks (per segment, in proportion to its tiles)
-  bt::DBuf<int32_t> s_r0, s_rows, s_rowe, s_u0, s_e0, s_seg0, s_slot, s_blk_seg, s_blk0;
+  bt::DBuf<int32_t> s_r0, s_rows, s_rowe, s_u0, s_e0, s_seg0, s_slot;
   bt::DBuf<uint16_t> s_rowl, s_lidx;
   bt::DBuf<uint32_t> s_ucol;
   bt::DBuf<float4> s_pkt;
@@ -97,11 +97,15 @@ struct bt_ctx {
   bool slice_ok = false;
   int64_t slice_planes_version = -1;
   bool slice_attr = false;
-  int slice_nblk = 0, slice_S = 0;  // tile blocks of the uploaded plan, slices it was made for
+  // plans of tile blocks for the two slice configurations (index stages - 1)
+  struct SlicePlan {
+    bt::DBuf<int32_t> blk_seg, blk0;
+    int nblk = 0, S = 0;  // tile blocks of the uploaded plan, slices it was made for
+  } slice_plan[2];
   struct Tuned {
     int R, nb, G;
-    int variant;   // 0 row SpMM iteration, 1 halo iteration, 2 slice-tiled iteration
-    double ms[3];  // one Krylov iteration of each variant (ms; 0 = not timed)
+    int variant;   // 0 row SpMM, 1 halo, 2 slice-tiled (two stages), 3 slice-tiled (one stage)
+    double ms[4];  // one Krylov iteration of each variant (ms; 0 = not timed)
     double ms_resid[2];  // one correction residual launch: row, halo (0 = not timed)
     bool resid_halo = false;
   };

@@ -295,10 +295,12 @@ void launch_flush_x(const VecArgs& va, float2* x, const float2* pA, const float2
 // spt is the plan of tile blocks (each block of the SpMM launch is one tile
 // block times one slice of 32 systems); the vector width Rp must be a
 // multiple of 32 (and of 32 NB).
+// stages = 2: one block per SM with two pipelined shared-memory stages;
+// stages = 1: two blocks per SM with one stage each.
 void slice_prepare();
-size_t slice_smem_bytes();
+size_t slice_smem_bytes(int stages);
 void launch_spmm_slice(const OpArgs& op, const HaloArgs& h, const SegPlan& spt, const float2* p, float2* q,
-                       const KrylovState& ks, RedScratch rs, int conj, int nb, cudaStream_t st);
+                       const KrylovState& ks, RedScratch rs, int conj, int nb, int stages, cudaStream_t st);
 void launch_slice_r(const OpArgs& op, const VecArgs& va, float2* r, const float2* q, const KrylovState& ks,
                     RedScratch rs, int conj, cudaStream_t st);
 void launch_slice_xp(const OpArgs& op, const VecArgs& va, float2* x, float2* p, const float2* r,

@@ -119,11 +119,14 @@ __device__ __forceinline__ void slice_flush(float2 (&a32)[NB][1], double2 (&a64)
 
 }  // namespace
 
-size_t slice_smem_bytes() { return 2 * SL_STAGE_BYTES; }
+size_t slice_smem_bytes(int stages) { return (size_t)stages * SL_STAGE_BYTES; }
 
 // ---------------------------------------------------------------- SpMM + (p, q)
-template <int NB, bool TRANSF, bool CONJ>
-__global__ void __launch_bounds__(SL_THREADS, 1)
+// STAGES = 2: one block per SM, the next tile's copies overlap this tile's
+// sums; STAGES = 1: two blocks per SM, each copying then summing (the two
+// blocks overlap each other).
+template <int NB, bool TRANSF, bool CONJ, int STAGES>
+__global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
     k_spmm_slice(OpArgs op, HaloArgs h, SegPlan spt, int S, const float2* __restrict__ p, float2* __restrict__ q,
                  KrylovState ks, RedScratch rs) {
   if (*ks.n_active == 0) return;
@@ -173,6 +176,17 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
 
   const int T0 = h.seg_tile0[sg], T1 = h.seg_tile0[sg + 1];
   auto stage_ptr = [&](int st) { return smem + (size_t)st * SL_STAGE_BYTES; };
+  // halo row ids of the pieces this thread copies for tile tau (loaded one
+  // tile ahead of their copies, so their latency overlaps the sums)
+  uint32_t rid[HPT];
+  auto load_rid = [&](int tau) {
+    const int u0 = __ldg(h.u0 + tau), nu = __ldg(h.u0 + tau + 1) - u0;
+#pragma unroll
+    for (int j = 0; j < HPT; ++j) {
+      const int u = (tid >> 4) + 16 * j;
+      rid[j] = u < nu ? (__ldg(h.ucol + u0 + u) & 0x7FFFFFFFu) : 0xFFFFFFFFu;
+    }
+  };
   auto issue = [&](int tau, int st) {
     char* b0 = stage_ptr(st);
     float2* sh = reinterpret_cast<float2*>(b0);
@@ -182,16 +196,10 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
     int32_t* srow = reinterpret_cast<int32_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES + SL_LI_BYTES);
     int32_t* srowe = srow + SL_TMAX;
     uint32_t* srowl = reinterpret_cast<uint32_t*>(srowe + SL_TMAX + 1);
-    const int u0 = __ldg(h.u0 + tau), nu = __ldg(h.u0 + tau + 1) - u0;  // <= SL_UMAX (tile builder)
+    const int nu = __ldg(h.u0 + tau + 1) - __ldg(h.u0 + tau);            // <= SL_UMAX (tile builder)
     const int e0 = __ldg(h.e0 + tau), ne = __ldg(h.e0 + tau + 1) - e0;  // <= SL_EMAX
     const int R0 = __ldg(h.t_r0 + tau), nown = __ldg(h.t_r0 + tau + 1) - R0;  // <= SL_TMAX
-    // halo rows: all row ids of this thread's pieces are loaded before any copy
-    uint32_t rid[HPT];
-#pragma unroll
-    for (int j = 0; j < HPT; ++j) {
-      const int u = (tid >> 4) + 16 * j;
-      rid[j] = u < nu ? (__ldg(h.ucol + u0 + u) & 0x7FFFFFFFu) : 0u;
-    }
+    // halo rows (rid: loaded by load_rid(tau))
     const int pc = tid & 15, b = pc / PPC, pp = pc - b * PPC;
 #pragma unroll
     for (int j = 0; j < HPT; ++j) {
@@ -219,13 +227,25 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
   int ntile = 0;
   if (__syncthreads_or(any)) {
     int tau = T0 + sk;
-    if (tau < T1) issue(tau, 0);
-    cpa_commit();
-    for (int it = 0; tau < T1; tau += snb, ++it) {
-      const int st = it & 1;
-      if (tau + snb < T1) issue(tau + snb, st ^ 1);
+    if (tau < T1) load_rid(tau);
+    if constexpr (STAGES == 2) {
+      if (tau < T1) issue(tau, 0);
       cpa_commit();
-      cpa_wait<1>();  // this thread's copies of tile tau have landed
+      if (tau + snb < T1) load_rid(tau + snb);
+    }
+    for (int it = 0; tau < T1; tau += snb, ++it) {
+      const int st = STAGES == 2 ? (it & 1) : 0;
+      if constexpr (STAGES == 2) {
+        if (tau + snb < T1) issue(tau + snb, st ^ 1);
+        cpa_commit();
+        if (tau + 2 * snb < T1) load_rid(tau + 2 * snb);
+        cpa_wait<1>();  // this thread's copies of tile tau have landed
+      } else {
+        issue(tau, 0);
+        cpa_commit();
+        if (tau + snb < T1) load_rid(tau + snb);
+        cpa_wait<0>();
+      }
       __syncthreads();
       const char* b0 = stage_ptr(st);
       const float2* sh = reinterpret_cast<const float2*>(b0);
@@ -279,7 +299,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
         }
       }
       if ((++ntile & 3) == 0) slice_flush<NB, LPR>(a32, a64, g);
-      __syncthreads();  // the stage is refilled two tiles from now
+      __syncthreads();  // the stage is refilled before it is read again
     }
     cpa_wait<0>();
   }
@@ -569,8 +589,10 @@ __global__ void __launch_bounds__(256, 2) k_slice_xp(OpArgs op, VecArgs va, floa
 // ---------------------------------------------------------------- launchers
 template <int NB, bool TRANSF, bool CONJ>
 static void slice_attr() {
-  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)slice_smem_bytes());
+  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, CONJ, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)slice_smem_bytes(2));
+  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, CONJ, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)slice_smem_bytes(1));
 }
 void slice_prepare() {
   slice_attr<4, false, false>(); slice_attr<4, false, true>(); slice_attr<4, true, false>(); slice_attr<4, true, true>();
@@ -579,22 +601,30 @@ void slice_prepare() {
 }
 
 void launch_spmm_slice(const OpArgs& op, const HaloArgs& h, const SegPlan& spt, const float2* p, float2* q,
-                       const KrylovState& ks, RedScratch rs, int conj, int nb, cudaStream_t st) {
+                       const KrylovState& ks, RedScratch rs, int conj, int nb, int stages, cudaStream_t st) {
   const int S = op.Rp / 32;
   const dim3 grid(spt.nblk * S);
-  const size_t sm = slice_smem_bytes();
-#define BT_SL_CASE(NBV)                                                                                  \
-  if (op.transformed) {                                                                                  \
-    if (conj) k_spmm_slice<NBV, true, true><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);   \
-    else k_spmm_slice<NBV, true, false><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);       \
-  } else {                                                                                               \
-    if (conj) k_spmm_slice<NBV, false, true><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);  \
-    else k_spmm_slice<NBV, false, false><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);      \
+  const size_t sm = slice_smem_bytes(stages);
+#define BT_SL_CASE(NBV, STG)                                                                                  \
+  if (op.transformed) {                                                                                       \
+    if (conj) k_spmm_slice<NBV, true, true, STG><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);   \
+    else k_spmm_slice<NBV, true, false, STG><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);       \
+  } else {                                                                                                    \
+    if (conj) k_spmm_slice<NBV, false, true, STG><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);  \
+    else k_spmm_slice<NBV, false, false, STG><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);      \
   }
-  switch (nb) {
-    case 4: BT_SL_CASE(4) break;
-    case 2: BT_SL_CASE(2) break;
-    default: BT_SL_CASE(1) break;
+  if (stages == 2) {
+    switch (nb) {
+      case 4: BT_SL_CASE(4, 2) break;
+      case 2: BT_SL_CASE(2, 2) break;
+      default: BT_SL_CASE(1, 2) break;
+    }
+  } else {
+    switch (nb) {
+      case 4: BT_SL_CASE(4, 1) break;
+      case 2: BT_SL_CASE(2, 1) break;
+      default: BT_SL_CASE(1, 1) break;
+    }
   }
 #undef BT_SL_CASE
 }
