@@ -345,15 +345,16 @@ bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter, in
 /* Counters of the last bt_run (any pointer may be NULL): time steps, total
  * Krylov iterations (summed over solves, not RHS), refinement passes, fused
  * SpMM launches, with BT_OPT_PROFILE the summed device time (ms) of the
- * FP32/FP64 fused SpMM launches (for variant 2 the halo-staged apply) and of
- * the refinement-residual launches, the number of refinement-residual
- * launches and of all kernel launches, and the number of active systems
- * summed over the fused SpMM launches (the right-hand sides each launch
- * actually processed). */
+ * FP32/FP64 fused SpMM launches (for Krylov variant 1 the halo-staged apply)
+ * and of the refinement-residual launches, the number of refinement-residual
+ * launches and of all kernel launches, the number of active systems summed
+ * over the fused SpMM launches (the right-hand sides each launch actually
+ * processed), and with BT_OPT_PROFILE the summed device time (ms) of the
+ * other kernels of the Krylov iterations (vector updates, inner products). */
 bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters,
                        int64_t* refine_passes, int64_t* spmm_launches, double* spmm_ms,
                        double* resid_ms, int64_t* resid_launches, int64_t* kernel_launches,
-                       int64_t* sys_iters);
+                       int64_t* sys_iters, double* vec_ms);
 
 /* ---------------------------------------------------------------- learned preconditioner
  * A small network (5 -> 64 -> 64 -> 9, ReLU, bfloat16 weights, FP32

@@ -91,7 +91,7 @@ def lib():
             "bt_get_signals": [P, P, P, P],
             "bt_get_state": [P, I32, P, P],
             "bt_get_halo_tiles": [P, I32, P, P, P, P, P, P, P, P, P],
-            "bt_get_stats": [P, P, P, P, P, P, P, P, P, P],
+            "bt_get_stats": [P, P, P, P, P, P, P, P, P, P, P],
             "bt_train_default_opts": [C.POINTER(bt_train_opts)],
             "bt_precond_features": [P, P, P, P],
             "bt_collect_precond_data": [P, C.POINTER(bt_solver_opts), I32, P, P, P, P],
@@ -330,12 +330,13 @@ def bt_get_halo_tiles(ctx, umax):
 
 def bt_get_stats(ctx):
     i = (C.c_int64 * 7)()
-    d = (C.c_double * 2)()
+    d = (C.c_double * 3)()
     _check(ctx, lib().bt_get_stats(ctx, C.byref(i, 0), C.byref(i, 8), C.byref(i, 16), C.byref(i, 24),
-                                   C.byref(d, 0), C.byref(d, 8), C.byref(i, 32), C.byref(i, 40), C.byref(i, 48)))
+                                   C.byref(d, 0), C.byref(d, 8), C.byref(i, 32), C.byref(i, 40), C.byref(i, 48),
+                                   C.byref(d, 16)))
     return {"steps": i[0], "krylov_iters": i[1], "refine_passes": i[2], "spmm_launches": i[3],
             "spmm_ms": d[0], "resid_ms": d[1], "resid_launches": i[4], "kernel_launches": i[5],
-            "sys_iters": i[6]}
+            "sys_iters": i[6], "vec_ms": d[2]}
 
 
 def bt_train_default_opts(**kw):

@@ -47,6 +47,7 @@ void ev_harvest(bt_ctx* ctx) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, ctx->ev_pool[i].a, ctx->ev_pool[i].b) == cudaSuccess) {
       if (ctx->ev_pool[i].kind == 0) ctx->st_spmm_ms += ms;
+      else if (ctx->ev_pool[i].kind == 2) ctx->st_vec_ms += ms;
       else ctx->st_resid_ms += ms;
     }
   }
@@ -882,8 +883,13 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
       CK(cudaMemcpyAsync(ks.rr_best, big.data(), big.size() * sizeof(double), cudaMemcpyHostToDevice, st));
       return BT_OK;
     };
-    for (float2* b : {ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ctx->p32b.p})
-      if (b) CK(cudaMemsetAsync(b, 0x3e, NE * sizeof(float2), st));
+    // every variant starts from the same vectors (a variant timed after
+    // another must not inherit iterates that may have converged or overflowed)
+    auto reset_vectors = [&]() -> bt_status {
+      for (float2* b : {ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ctx->p32b.p})
+        if (b) CK(cudaMemsetAsync(b, 0x3e, NE * sizeof(float2), st));
+      return BT_OK;
+    };
     auto iter = [&](int v) {
       if (v >= 2) {
         launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx, slice_stages(v)), ctx->p32.p, ctx->q32.p, ks, rs, conj,
@@ -907,6 +913,7 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0, 0, 0}, {0, 0}};
     for (int v = 0; v < 4; ++v) {
       if ((v == 1 && !halo) || (v >= 2 && !slice)) continue;
+      if (bt_status e = reset_vectors()) return e;
       if (bt_status e = prime()) return e;
       iter(v);  // warm-up
       CK(cudaEventRecord(e0, st));
@@ -1128,6 +1135,10 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
         launch_krylov_init_z(opL, g.va, g.df ? (const void*)ctx->rdf.p : (const void*)ctx->r64.p, g.df,
                              ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p, g.ks, g.tol_inner, rs_at(1),
                              g.conj, c2);
+      else if (g.variant >= 2)
+        launch_slice_init(opL, g.va, g.df ? (const void*)ctx->rdf.p : (const void*)ctx->r64.p, g.df,
+                          ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p, ctx->p32.p, g.ks, g.tol_inner,
+                          rs_at(1), g.conj, c2);
       else if (g.df)
         launch_krylov_init_f32_df(opL, g.va, ctx->rdf.p, ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p,
                                   ctx->p32.p, g.ks, g.tol_inner, rs_at(1), g.conj, ctx->sms, c2);
@@ -1405,7 +1416,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     }
   }
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
-  ctx->st_spmm_ms = ctx->st_resid_ms = 0;
+  ctx->st_spmm_ms = ctx->st_resid_ms = ctx->st_vec_ms = 0;
   ctx->ev_used = 0;
   CK(cudaMemsetAsync(ctx->rf_err.p, 0, SY * sizeof(double), st));
   CK(cudaMemsetAsync(ctx->ks_status.p, 0, SY * sizeof(int), st));
@@ -1499,6 +1510,9 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       } else if (variant == 1) {
         launch_krylov_init_z(op, va, df ? (const void*)ctx->rdf.p : (const void*)ctx->r64.p, df, ctx->rf_scale.p,
                              ctx->rf_active.p, ctx->x32.p, ctx->r32.p, ks, o.tol_inner, rs_at(1), conj, st);
+      } else if (variant >= 2) {
+        launch_slice_init(op, va, df ? (const void*)ctx->rdf.p : (const void*)ctx->r64.p, df, ctx->rf_scale.p,
+                          ctx->rf_active.p, ctx->x32.p, ctx->r32.p, ctx->p32.p, ks, o.tol_inner, rs_at(1), conj, st);
       } else if (df) {
         launch_krylov_init_f32_df(op, va, ctx->rdf.p, ctx->rf_scale.p, ctx->rf_active.p, ctx->x32.p, ctx->r32.p,
                                   ctx->p32.p, ks, o.tol_inner, rs_at(1), conj, ctx->sms, st);
@@ -1525,34 +1539,39 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
             if (narrow) launch_spmm_krylov_f64_narrow(op, ctx->p64.p, ctx->q64.p, ks, rs_at(2), conj, ctx->sms, st);
             else launch_spmm_krylov_f64(op, ctx->p64.p, ctx->q64.p, ks, rs_at(2), conj, nb, ctx->sms, st);
           });
-          launch_krylov_update_f64(op, va, ctx->x64.p, ctx->rk64.p, ctx->p64.p, ctx->q64.p, ks, rs_at(3), conj,
-                                   ctx->sms, st);
-          launch_krylov_p_f64(op, va, ctx->rk64.p, ctx->p64.p, ks, ctx->sms, st);
+          timed(2, [&] {
+            launch_krylov_update_f64(op, va, ctx->x64.p, ctx->rk64.p, ctx->p64.p, ctx->q64.p, ks, rs_at(3), conj,
+                                     ctx->sms, st);
+            launch_krylov_p_f64(op, va, ctx->rk64.p, ctx->p64.p, ks, ctx->sms, st);
+          });
         } else if (variant == 1) {
           timed(0, [&] {
             launch_spmm_halo(op, halo_args(ctx), ctx->r32.p, ctx->p32.p, ctx->p32b.p, ctx->x32.p, ctx->q32.p, ks,
                              rs_at(2), conj, nb, st);
           });
-          launch_krylov_update_z(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
+          timed(2, [&] { launch_krylov_update_z(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st); });
           L -= 1;  // two launches per iteration
         } else if (variant >= 2) {
           timed(0, [&] {
             launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx, slice_stages(variant)), ctx->p32.p, ctx->q32.p, ks,
                               rs_at(2), conj, nb, slice_stages(variant), st);
           });
-          launch_slice_r(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
-          launch_slice_xp(op, va, ctx->x32.p, ctx->p32.p, ctx->r32.p, ks, rs_xp(ctx), st);
+          timed(2, [&] {
+            launch_slice_r(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
+            launch_slice_xp(op, va, ctx->x32.p, ctx->p32.p, ctx->r32.p, ks, rs_xp(ctx), st);
+          });
         } else {
           timed(0, [&] { launch_spmm_krylov_f32(op, ctx->p32.p, ctx->q32.p, ks, rs_at(2), conj, nb, ctx->sms, st); });
-          launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs_at(3), conj,
-                                   ctx->sms, st, learned ? ctx->pmode.p : nullptr);
+          timed(2, [&] {
+            launch_krylov_update_f32(op, va, ctx->x32.p, ctx->r32.p, ctx->p32.p, ctx->q32.p, ks, rs_at(3), conj,
+                                     ctx->sms, st, learned ? ctx->pmode.p : nullptr);
+            if (!learned) launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st);
+          });
           if (learned) {
             if (bt_status e = apply_poly(ctx, op, va, ks, st)) return e;
             launch_precond_dot(va, ctx->r32.p, ctx->zA.p, ks, rs_at(6), ctx->pmode.p, conj, 0, ctx->sms, st);
             launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st, ctx->zA.p, ctx->pmode.p);
             L += 10;
-          } else {
-            launch_krylov_p_f32(op, va, ctx->r32.p, ctx->p32.p, ks, ctx->sms, st);
           }
         }
         CKL();
@@ -1705,7 +1724,8 @@ extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* 
 
 extern "C" bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters, int64_t* refine_passes,
                                   int64_t* spmm_launches, double* spmm_ms, double* resid_ms,
-                                  int64_t* resid_launches, int64_t* kernel_launches, int64_t* sys_iters) {
+                                  int64_t* resid_launches, int64_t* kernel_launches, int64_t* sys_iters,
+                                  double* vec_ms) {
   if (!ctx) return BT_EINVAL;
   if (steps) *steps = ctx->st_steps;
   if (krylov_iters) *krylov_iters = ctx->st_iters;
@@ -1716,5 +1736,6 @@ extern "C" bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* kr
   if (resid_launches) *resid_launches = ctx->st_resid;
   if (kernel_launches) *kernel_launches = ctx->st_launches;
   if (sys_iters) *sys_iters = ctx->st_sys_iters;
+  if (vec_ms) *vec_ms = ctx->st_vec_ms;
   return BT_OK;
 }

@@ -15,7 +15,7 @@ namespace bt {
 constexpr int N_COUNTERS = 16;
 struct EventPair {
   cudaEvent_t a, b;
-  int kind;  // 0 fused Krylov SpMM, 1 refinement residual
+  int kind;  // 0 fused Krylov SpMM, 1 refinement residual, 2 vector kernels of a Krylov iteration
 };
 }  // namespace bt
 
@@ -140,7 +140,7 @@ struct bt_ctx {
   std::vector<double> S, err_est;
   std::vector<int> status;
   int64_t st_steps = 0, st_iters = 0, st_refine = 0, st_spmm = 0, st_resid = 0, st_launches = 0, st_sys_iters = 0;
-  double st_spmm_ms = 0, st_resid_ms = 0;
+  double st_spmm_ms = 0, st_resid_ms = 0, st_vec_ms = 0;
   std::vector<bt::EventPair> ev_pool;
   size_t ev_used = 0;
 

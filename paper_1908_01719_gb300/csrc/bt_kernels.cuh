@@ -305,6 +305,12 @@ void launch_slice_r(const OpArgs& op, const VecArgs& va, float2* r, const float2
                     RedScratch rs, int conj, cudaStream_t st);
 void launch_slice_xp(const OpArgs& op, const VecArgs& va, float2* x, float2* p, const float2* r,
                      const KrylovState& ks, RedScratch rs, cudaStream_t st);
+// start of an inner solve for the slice iteration (vectorised form of the row
+// variant's initialisation): rres = the refinement residual (FP64 or, with df,
+// double-float), r = rres / scale, p = D^-1 r, x = 0, rho, |r|^2
+void launch_slice_init(const OpArgs& op, const VecArgs& va, const void* rres, int df, const double* scale,
+                       const int* ref_active, float2* x, float2* r, float2* p, const KrylovState& ks, double tol,
+                       RedScratch rs, int conj, cudaStream_t st);
 
 void launch_krylov_init_f64(const OpArgs& op, const VecArgs& va, const double2* r64, const int* ref_active,
                             double2* x, double2* r, double2* p, const KrylovState& ks, double tol, RedScratch rs,

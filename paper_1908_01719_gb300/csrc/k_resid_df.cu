@@ -53,6 +53,43 @@ __device__ __forceinline__ void dd_acc1(float& sh, float& sl, float ah, float al
   sh = s;
   sl += t + e;
 }
+// The same accumulations on a pair (re, im) at once, with the FP32x2
+// instructions of sm_100+ (__fmul2_rn, __fadd2_rn, __ffma2_rn: each component
+// rounded once, never contracted): every step is the scalar error-free
+// transformation above, component by component, so the packed sums equal the
+// scalar ones bit for bit.  Differences a - b are formed as fma(b, -1, a),
+// which rounds exactly like the subtraction.  The coefficient enters as the
+// pairs ah2 = (ah, ah), nah2 = (-ah, -ah), al2 = (al, al).
+// (sh, sl) += p + e with the product -p = pn given (two_sum of sh and p)
+__device__ __forceinline__ void dd2_two_sum_into(float2& sh, float2& sl, float2 pn, float2 e) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 s = __ffma2_rn(pn, m1, sh);   // sh + p
+  const float2 bb = __ffma2_rn(sh, m1, s);   // s - sh
+  const float2 u1 = __ffma2_rn(bb, m1, s);   // s - bb
+  const float2 u2 = __ffma2_rn(u1, m1, sh);  // sh - (s - bb)
+  const float2 v = __fadd2_rn(pn, bb);       // -(p - bb)
+  const float2 t = __ffma2_rn(v, m1, u2);    // u2 + (p - bb)
+  sh = s;
+  sl = __fadd2_rn(sl, __fadd2_rn(t, e));
+}
+// (sh, sl) += (ah + al) * x, x a pair of exact FP32 numbers
+__device__ __forceinline__ void dd2_acc1(float2& sh, float2& sl, float2 ah2, float2 nah2, float2 al2, float2 x) {
+  const float2 pn = __fmul2_rn(nah2, x);  // -p, p = fl(ah x)
+  float2 e = __ffma2_rn(ah2, x, pn);      // ah x - p, exact
+  e = __ffma2_rn(al2, x, e);              // + al x
+  dd2_two_sum_into(sh, sl, pn, e);
+}
+// (sh, sl) += (ah + al) * (xh + xl), x a pair of double-float numbers
+__device__ __forceinline__ void dd2_acc(float2& sh, float2& sl, float2 ah2, float2 nah2, float2 al2, float2 xh,
+                                        float2 xl) {
+  const float2 pn = __fmul2_rn(nah2, xh);
+  float2 e = __ffma2_rn(ah2, xh, pn);
+  e = __ffma2_rn(al2, xh, e);
+  e = __ffma2_rn(ah2, xl, e);
+  dd2_two_sum_into(sh, sl, pn, e);
+}
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+
 struct dd {
   float h, l;
 };
@@ -122,12 +159,10 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
   if (warp_any) {
     BT_FOR_SEG_CHUNKED_ROWS(row, warp, W) {
       const int k0 = op.rp[row], k1 = op.rp[row + 1];
-      // accumulators: P (P0 x), Q (m x), Z (MD x); re/im, hi/lo
-      float Ph[NB][2], Pl[NB][2], Qh[NB][2], Ql[NB][2], Zh[NB][2], Zl[NB][2];
+      // accumulators: P (P0 x), Q (m x), Z (MD x); packed (re, im), hi/lo
+      float2 Ph[NB], Pl[NB], Qh[NB], Ql[NB], Zh[NB], Zl[NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) Ph[b][c] = Pl[b][c] = Qh[b][c] = Ql[b][c] = Zh[b][c] = Zl[b][c] = 0.f;
+      for (int b = 0; b < NB; ++b) Ph[b] = Pl[b] = Qh[b] = Ql[b] = Zh[b] = Zl[b] = make_float2(0.f, 0.f);
       // column indices fetched lane-parallel, then DU gathers in flight
       constexpr int DU = 2;
       for (int kb = k0; kb < k1; kb += 32) {
@@ -172,29 +207,22 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
             dd_acc(mh, ml, qy.h, qy.l, vh.z, vl.z);
             dd_acc(mh, ml, qz.h, qz.l, vh.w, vl.w);
             const dd m = dd_norm(mh, ml);
+            const float2 p0h2 = bc(p0h), np0h2 = bc(-p0h), p0l2 = bc(p0l);
+            const float2 mh2 = bc(m.h), nmh2 = bc(-m.h), ml2 = bc(m.l);
             if (!on) continue;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
               if constexpr (MODE == 0) {
                 const float4 xv = xs[u][b];
-                dd_acc(Ph[b][0], Pl[b][0], p0h, p0l, xv.x, xv.z);
-                dd_acc(Ph[b][1], Pl[b][1], p0h, p0l, xv.y, xv.w);
-                dd_acc(Qh[b][0], Ql[b][0], m.h, m.l, xv.x, xv.z);
-                dd_acc(Qh[b][1], Ql[b][1], m.h, m.l, xv.y, xv.w);
-                if constexpr (TRANSF) {
-                  dd_acc(Zh[b][0], Zl[b][0], mdh, mdl, xv.x, xv.z);
-                  dd_acc(Zh[b][1], Zl[b][1], mdh, mdl, xv.y, xv.w);
-                }
+                const float2 xh = make_float2(xv.x, xv.y), xl = make_float2(xv.z, xv.w);
+                dd2_acc(Ph[b], Pl[b], p0h2, np0h2, p0l2, xh, xl);
+                dd2_acc(Qh[b], Ql[b], mh2, nmh2, ml2, xh, xl);
+                if constexpr (TRANSF) dd2_acc(Zh[b], Zl[b], bc(mdh), bc(-mdh), bc(mdl), xh, xl);
               } else {
                 const float2 xv = xs[u][b];
-                dd_acc1(Ph[b][0], Pl[b][0], p0h, p0l, xv.x);
-                dd_acc1(Ph[b][1], Pl[b][1], p0h, p0l, xv.y);
-                dd_acc1(Qh[b][0], Ql[b][0], m.h, m.l, xv.x);
-                dd_acc1(Qh[b][1], Ql[b][1], m.h, m.l, xv.y);
-                if constexpr (TRANSF) {
-                  dd_acc1(Zh[b][0], Zl[b][0], mdh, mdl, xv.x);
-                  dd_acc1(Zh[b][1], Zl[b][1], mdh, mdl, xv.y);
-                }
+                dd2_acc1(Ph[b], Pl[b], p0h2, np0h2, p0l2, xv);
+                dd2_acc1(Qh[b], Ql[b], mh2, nmh2, ml2, xv);
+                if constexpr (TRANSF) dd2_acc1(Zh[b], Zl[b], bc(mdh), bc(-mdh), bc(mdl), xv);
               }
             }
           }
@@ -206,12 +234,12 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
           if (!lc.act[b]) continue;
           const size_t e = (size_t)row * op.Rp + c0 + 32 * b;
           // y = a P + b Z + i c Q
-          dd Pr = dd_norm(Ph[b][0], Pl[b][0]), Pi = dd_norm(Ph[b][1], Pl[b][1]);
-          dd Qr = dd_norm(Qh[b][0], Ql[b][0]), Qi = dd_norm(Qh[b][1], Ql[b][1]);
+          dd Pr = dd_norm(Ph[b].x, Pl[b].x), Pi = dd_norm(Ph[b].y, Pl[b].y);
+          dd Qr = dd_norm(Qh[b].x, Ql[b].x), Qi = dd_norm(Qh[b].y, Ql[b].y);
           dd yr = dd_add(dd_mul(ca, Pr), dd_neg(dd_mul(cc[b], Qi)));
           dd yi = dd_add(dd_mul(ca, Pi), dd_mul(cc[b], Qr));
           if constexpr (TRANSF) {
-            dd Zr = dd_norm(Zh[b][0], Zl[b][0]), Zi = dd_norm(Zh[b][1], Zl[b][1]);
+            dd Zr = dd_norm(Zh[b].x, Zl[b].x), Zi = dd_norm(Zh[b].y, Zl[b].y);
             yr = dd_add(yr, dd_mul(cb[b], Zr));
             yi = dd_add(yi, dd_mul(cb[b], Zi));
           }
@@ -408,11 +436,9 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
         const int row = __shfl_sync(0xffffffffu, m_row, kk);
         const int e0 = __shfl_sync(0xffffffffu, m_e0, kk), e1 = __shfl_sync(0xffffffffu, m_e1, kk);
         const int lo = __shfl_sync(0xffffffffu, m_lo, kk);
-        float Ph[NB][2], Pl[NB][2], Qh[NB][2], Ql[NB][2], Zh[NB][2], Zl[NB][2];
+        float2 Ph[NB], Pl[NB], Qh[NB], Ql[NB], Zh[NB], Zl[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-          for (int c = 0; c < 2; ++c) Ph[b][c] = Pl[b][c] = Qh[b][c] = Ql[b][c] = Zh[b][c] = Zl[b][c] = 0.f;
+        for (int b = 0; b < NB; ++b) Ph[b] = Pl[b] = Qh[b] = Ql[b] = Zh[b] = Zl[b] = make_float2(0.f, 0.f);
         for (int e = e0; e < e1; ++e) {
           const float4 vh = sent[3 * e], vl = sent[3 * e + 1], kk4 = sent[3 * e + 2];  // {kh.x, kh.y, kl.x, kl.y}
           const int l = sl16[e];
@@ -430,29 +456,22 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
           dd_acc(mh, ml, qy.h, qy.l, vh.z, vl.z);
           dd_acc(mh, ml, qz.h, qz.l, vh.w, vl.w);
           const dd m = dd_norm(mh, ml);
+          const float2 p0h2 = bc(p0h), np0h2 = bc(-p0h), p0l2 = bc(p0l);
+          const float2 mh2 = bc(m.h), nmh2 = bc(-m.h), ml2 = bc(m.l);
           const TX* xp = xs_ + l * NB * 32 + lane;
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
             if constexpr (MODE == 0) {
               const float4 xv = xp[32 * b];
-              dd_acc(Ph[b][0], Pl[b][0], p0h, p0l, xv.x, xv.z);
-              dd_acc(Ph[b][1], Pl[b][1], p0h, p0l, xv.y, xv.w);
-              dd_acc(Qh[b][0], Ql[b][0], m.h, m.l, xv.x, xv.z);
-              dd_acc(Qh[b][1], Ql[b][1], m.h, m.l, xv.y, xv.w);
-              if constexpr (TRANSF) {
-                dd_acc(Zh[b][0], Zl[b][0], mdh, mdl, xv.x, xv.z);
-                dd_acc(Zh[b][1], Zl[b][1], mdh, mdl, xv.y, xv.w);
-              }
+              const float2 xh = make_float2(xv.x, xv.y), xl = make_float2(xv.z, xv.w);
+              dd2_acc(Ph[b], Pl[b], p0h2, np0h2, p0l2, xh, xl);
+              dd2_acc(Qh[b], Ql[b], mh2, nmh2, ml2, xh, xl);
+              if constexpr (TRANSF) dd2_acc(Zh[b], Zl[b], bc(mdh), bc(-mdh), bc(mdl), xh, xl);
             } else {
               const float2 xv = xp[32 * b];
-              dd_acc1(Ph[b][0], Pl[b][0], p0h, p0l, xv.x);
-              dd_acc1(Ph[b][1], Pl[b][1], p0h, p0l, xv.y);
-              dd_acc1(Qh[b][0], Ql[b][0], m.h, m.l, xv.x);
-              dd_acc1(Qh[b][1], Ql[b][1], m.h, m.l, xv.y);
-              if constexpr (TRANSF) {
-                dd_acc1(Zh[b][0], Zl[b][0], mdh, mdl, xv.x);
-                dd_acc1(Zh[b][1], Zl[b][1], mdh, mdl, xv.y);
-              }
+              dd2_acc1(Ph[b], Pl[b], p0h2, np0h2, p0l2, xv);
+              dd2_acc1(Qh[b], Ql[b], mh2, nmh2, ml2, xv);
+              if constexpr (TRANSF) dd2_acc1(Zh[b], Zl[b], bc(mdh), bc(-mdh), bc(mdl), xv);
             }
           }
         }
@@ -461,12 +480,12 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
         for (int b = 0; b < NB; ++b) {
           if (!act[b]) continue;
           const size_t e = (size_t)row * op.Rp + c0 + 32 * b;
-          dd Pr = dd_norm(Ph[b][0], Pl[b][0]), Pi = dd_norm(Ph[b][1], Pl[b][1]);
-          dd Qr = dd_norm(Qh[b][0], Ql[b][0]), Qi = dd_norm(Qh[b][1], Ql[b][1]);
+          dd Pr = dd_norm(Ph[b].x, Pl[b].x), Pi = dd_norm(Ph[b].y, Pl[b].y);
+          dd Qr = dd_norm(Qh[b].x, Ql[b].x), Qi = dd_norm(Qh[b].y, Ql[b].y);
           dd yr = dd_add(dd_mul(ca, Pr), dd_neg(dd_mul(cc[b], Qi)));
           dd yi = dd_add(dd_mul(ca, Pi), dd_mul(cc[b], Qr));
           if constexpr (TRANSF) {
-            dd Zr = dd_norm(Zh[b][0], Zl[b][0]), Zi = dd_norm(Zh[b][1], Zl[b][1]);
+            dd Zr = dd_norm(Zh[b].x, Zl[b].x), Zi = dd_norm(Zh[b].y, Zl[b].y);
             yr = dd_add(yr, dd_mul(cb[b], Zr));
             yi = dd_add(yi, dd_mul(cb[b], Zi));
           }

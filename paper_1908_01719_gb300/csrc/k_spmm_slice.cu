@@ -62,6 +62,43 @@ __device__ __forceinline__ void cpa_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Bulk (TMA) copies into shared memory, completed on an mbarrier that counts
+// the bytes in flight.  A wait is bounded: past about two seconds the caller
+// records a timeout instead of spinning on.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(sdst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// generic-proxy accesses of this thread before async-proxy writes to the same shared memory
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true when the phase of `parity` completed; false after the time limit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 255u && clock64() - t0 > 4000000000LL) return false;
+  }
+}
+
 // 1 / d for a complex diagonal d = (re, im); the same arithmetic in both
 // launches, so z = D^-1 r agrees bit for bit between them
 __device__ __forceinline__ float2 diag_inv(float re, float im) {
@@ -119,7 +156,8 @@ __device__ __forceinline__ void slice_flush(float2 (&a32)[NB][1], double2 (&a64)
 
 }  // namespace
 
-size_t slice_smem_bytes(int stages) { return (size_t)stages * SL_STAGE_BYTES; }
+// the stages, then one mbarrier per stage
+size_t slice_smem_bytes(int stages) { return (size_t)stages * SL_STAGE_BYTES + 16; }
 
 // ---------------------------------------------------------------- SpMM + (p, q)
 // STAGES = 2: one block per SM, the next tile's copies overlap this tile's
@@ -131,8 +169,8 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
                  KrylovState ks, RedScratch rs) {
   if (*ks.n_active == 0) return;
   constexpr int LPR = 32 / NB;   // lanes per row
-  constexpr int PPC = 16 / NB;   // 16-byte pieces per chunk of LPR complex values
   constexpr int SLOTS = 8 * NB;  // rows in flight per block
+  constexpr int PPC = 16 / NB;                     // 16-byte pieces per chunk of LPR complex values
   constexpr int HPT = SL_UMAX * 16 / SL_THREADS;  // halo pieces per thread at most
   extern __shared__ float4 sl_smem_[];
   char* smem = reinterpret_cast<char*>(sl_smem_);
@@ -176,8 +214,12 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
 
   const int T0 = h.seg_tile0[sg], T1 = h.seg_tile0[sg + 1];
   auto stage_ptr = [&](int st) { return smem + (size_t)st * SL_STAGE_BYTES; };
-  // halo row ids of the pieces this thread copies for tile tau (loaded one
-  // tile ahead of their copies, so their latency overlaps the sums)
+  // one mbarrier per stage (after the stages), its phase parity in bit st
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)STAGES * SL_STAGE_BYTES);
+  unsigned phase = 0u;
+  // halo row ids of the 16-byte pieces this thread copies for tile tau
+  // (loaded one tile ahead of their copies, so their latency overlaps the
+  // sums); piece tid & 15 of halo rows (tid >> 4) + 16 j
   uint32_t rid[HPT];
   auto load_rid = [&](int tau) {
     const int u0 = __ldg(h.u0 + tau), nu = __ldg(h.u0 + tau + 1) - u0;
@@ -199,17 +241,24 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
     const int nu = __ldg(h.u0 + tau + 1) - __ldg(h.u0 + tau);            // <= SL_UMAX (tile builder)
     const int e0 = __ldg(h.e0 + tau), ne = __ldg(h.e0 + tau + 1) - e0;  // <= SL_EMAX
     const int R0 = __ldg(h.t_r0 + tau), nown = __ldg(h.t_r0 + tau + 1) - R0;  // <= SL_TMAX
-    // halo rows (rid: loaded by load_rid(tau))
+    // the tile's planes: one bulk (TMA) copy of 16 ne contiguous bytes,
+    // counted on the stage's mbarrier (issued by the thread that arms it)
+    uint64_t* bar = bars + st;
+    if (tid == 0) {
+      fence_async_smem();
+      mbar_expect(bar, (unsigned)ne * 16u);
+      if (ne > 0) bulk_g2s(spk, h.pkt + e0, (unsigned)ne * 16u, bar);
+    }
+    // halo rows (rid: loaded by load_rid(tau)): 16-byte asynchronous copies,
+    // many in flight per thread
     const int pc = tid & 15, b = pc / PPC, pp = pc - b * PPC;
 #pragma unroll
     for (int j = 0; j < HPT; ++j) {
       const int u = (tid >> 4) + 16 * j;
       if (u < nu) cpa16(sh + u * 32 + b * LPR + 2 * pp, p + (size_t)rid[j] * op.Rp + cs + 32 * b + 2 * pp);
     }
-    for (int e = tid; e < ne; e += SL_THREADS) {
-      cpa16(spk + e, h.pkt + e0 + e);
-      if constexpr (TRANSF) cpa4(smd + e, h.mdt + e0 + e);
-    }
+    if constexpr (TRANSF)
+      for (int e = tid; e < ne; e += SL_THREADS) cpa4(smd + e, h.mdt + e0 + e);
     const int w0 = e0 >> 1, nw = ((e0 + ne + 1) >> 1) - w0;  // the index array is padded
     for (int w = tid; w < nw; w += SL_THREADS) cpa4(sli + w, reinterpret_cast<const uint32_t*>(h.lidx) + w0 + w);
     // owned rows: ids, entry offsets, local indices
@@ -225,6 +274,11 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
 #pragma unroll
   for (int k = 0; k < NB; ++k) any |= act[k];
   int ntile = 0;
+  if (tid == 0) {
+    for (int st = 0; st < STAGES; ++st) mbar_init(bars + st, 1u);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
   if (__syncthreads_or(any)) {
     int tau = T0 + sk;
     if (tau < T1) load_rid(tau);
@@ -246,7 +300,18 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
         if (tau + snb < T1) load_rid(tau + snb);
         cpa_wait<0>();
       }
-      __syncthreads();
+      // the stage's bulk copies (bounded wait; a timeout ends the block's work)
+      const bool arrived = mbar_wait(bars + st, (phase >> st) & 1u);
+      phase ^= 1u << st;
+      if (__syncthreads_or(!arrived)) {
+#pragma unroll
+        for (int kk = 0; kk < NB; ++kk)
+          if (act[kk]) ks.status[base + r0 + (kk + g) % NB] = BT_ETIMEOUT;
+        // let copies still in flight land before the block's shared memory is released
+        mbar_wait(bars + st, (phase >> st) & 1u ^ 1u);
+        if constexpr (STAGES == 2) mbar_wait(bars + (st ^ 1), (phase >> (st ^ 1)) & 1u);
+        break;
+      }
       const char* b0 = stage_ptr(st);
       const float2* sh = reinterpret_cast<const float2*>(b0);
       const float4* spk = reinterpret_cast<const float4*>(b0 + SL_HALO_BYTES);
@@ -586,6 +651,160 @@ __global__ void __launch_bounds__(256, 2) k_slice_xp(OpArgs op, VecArgs va, floa
   for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) ks.pend[s] = 0;
 }
 
+// ---------------------------------------------------------------- start of an inner solve
+// r = r_res / scale_s, z = D^-1 r, p = z, x = 0; rho = (r, z), |r|^2 (FP32 over
+// at most 32 rows, then FP64).  The last block initialises the per-system
+// Krylov state exactly as the row variant's initialisation does.
+__device__ __forceinline__ double2 load_res_d(const double2* p, size_t e) { return p[e]; }
+__device__ __forceinline__ double2 load_res_d(const float4* p, size_t e) {
+  const float4 v = __ldcs(p + e);
+  return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+template <class TR, bool CONJ>
+__global__ void __launch_bounds__(256, 2) k_slice_init(OpArgs op, VecArgs va, const TR* __restrict__ rres,
+                                                       const double* __restrict__ scale,
+                                                       const int* __restrict__ ref_active, float2* __restrict__ x,
+                                                       float2* __restrict__ r, float2* __restrict__ p, KrylovState ks,
+                                                       double tol, RedScratch rs) {
+  constexpr int U = 4;  // rows in flight per thread
+  const int Rp = va.Rp;
+  const PairMap pm(Rp);
+  BT_SEG_BEGIN(va.sp);
+  const int64_t per = (sr1_ - sr0_ + snb_ - 1) / snb_;
+  const int64_t rb = sr0_ + (int64_t)sk_ * per, re = min(sr1_, rb + per);
+  const OpCoef cf = op_coef(op, sg_);
+  const int base = sg_ * va.R;
+  __shared__ double2 sred[256][2][2];
+  for (int ch = 0; ch < pm.nch; ++ch) {
+    const int col = 2 * (pm.cp + 256 * ch);
+    double2 acc[2][2] = {{make_double2(0, 0), make_double2(0, 0)}, {make_double2(0, 0), make_double2(0, 0)}};
+    if (pm.live && col < Rp) {
+      bool ac[2];
+      double inv[2];
+      DiagCoef dc[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int rl = sys_of_col(col + u, va.nb), s = base + rl;
+        ac[u] = rl < va.R && ref_active[s] != 0;
+        inv[u] = (scale && ac[u] && scale[s] > 0) ? 1.0 / scale[s] : 1.0;
+        dc[u] = diag_coef(op, cf, s, rl < va.R);
+      }
+      float2 fr[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      float fn[2] = {0.f, 0.f};
+      int cnt = 0;
+      for (int64_t i0 = rb + pm.ro; i0 < re; i0 += U * pm.rpp) {
+        double2 v[U][2];
+        float4 dg[U];
+        float dm[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t i = i0 + (int64_t)k * pm.rpp;
+          if (i < re) {
+            const size_t e = (size_t)i * Rp + col;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) v[k][u] = ac[u] ? load_res_d(rres, e + u) : make_double2(0, 0);
+            dg[k] = __ldg(va.diag32 + i);
+            dm[k] = op.transformed ? __ldg(va.diag_md32 + i) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t i = i0 + (int64_t)k * pm.rpp;
+          if (i >= re) break;
+          float2 rv[2], zv[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            rv[u] = make_float2((float)(v[k][u].x * inv[u]), (float)(v[k][u].y * inv[u]));
+            const float2 d = diag_of(dc[u], dg[k], dm[k]);
+            zv[u] = cmulf(rv[u], diag_inv(d.x, d.y));
+            cmacf(fr[u], CONJ ? conjf2(rv[u]) : rv[u], zv[u]);
+            fn[u] = fmaf(rv[u].x, rv[u].x, fmaf(rv[u].y, rv[u].y, fn[u]));
+          }
+          const size_t e = (size_t)i * Rp + col;
+          *reinterpret_cast<float4*>(r + e) = make_float4(rv[0].x, rv[0].y, rv[1].x, rv[1].y);
+          *reinterpret_cast<float4*>(p + e) = make_float4(zv[0].x, zv[0].y, zv[1].x, zv[1].y);
+          *reinterpret_cast<float4*>(x + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (++cnt == 8) {  // FP32 over at most 32 rows, then FP64
+          cnt = 0;
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            acc[u][0].x += fr[u].x;
+            acc[u][0].y += fr[u].y;
+            acc[u][1].x += fn[u];
+            fr[u] = make_float2(0.f, 0.f);
+            fn[u] = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        acc[u][0].x += fr[u].x;
+        acc[u][0].y += fr[u].y;
+        acc[u][1].x += fn[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      sred[threadIdx.x][u][0] = acc[u][0];
+      sred[threadIdx.x][u][1] = acc[u][1];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < pm.TPR && col < Rp) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
+        for (int o = 0; o < pm.rpp; ++o) {
+          const double2 a0 = sred[o * pm.TPR + threadIdx.x][u][0], a1 = sred[o * pm.TPR + threadIdx.x][u][1];
+          s0.x += a0.x;
+          s0.y += a0.y;
+          s1.x += a1.x;
+        }
+        const int rl = sys_of_col(col + u, va.nb);
+        if (rl < va.R) {
+          double2* o2 = reinterpret_cast<double2*>(rs.part) + ((size_t)blockIdx.x * Rp + rl) * 2;
+          o2[0] = s0;
+          o2[1] = s1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!last_block(rs.counter, gridDim.x)) return;
+  __shared__ int s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+    const int gg = s / va.R, rl = s - gg * va.R;
+    double2 o[2] = {make_double2(0, 0), make_double2(0, 0)};
+    for (int b = va.sp.blk0[gg]; b < va.sp.blk0[gg + 1]; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(rs.part) + ((size_t)b * Rp + rl) * 2 + c);
+        o[c].x += v.x;
+        o[c].y += v.y;
+      }
+    ks.rho[2 * s] = o[0].x;
+    ks.rho[2 * s + 1] = o[0].y;
+    ks.rr0[s] = o[1].x;
+    ks.rr[s] = o[1].x;
+    ks.tol2[s] = tol * tol * o[1].x;
+    ks.iter[s] = 0;
+    ks.rr_best[s] = o[1].x;
+    ks.it_best[s] = 0;
+    ks.pend[s] = 0;
+    int a = ref_active[s] && o[1].x > 0;
+    if (ref_active[s] && !isfinite(o[1].x)) {
+      a = 0;
+      ks.status[s] = BT_ENAN;
+    }
+    ks.active[s] = a;
+    if (a) atomicAdd(&s_cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ks.n_active = s_cnt;
+}
+
 // ---------------------------------------------------------------- launchers
 template <int NB, bool TRANSF, bool CONJ>
 static void slice_attr() {
@@ -638,6 +857,21 @@ void launch_slice_r(const OpArgs& op, const VecArgs& va, float2* r, const float2
 void launch_slice_xp(const OpArgs& op, const VecArgs& va, float2* x, float2* p, const float2* r,
                      const KrylovState& ks, RedScratch rs, cudaStream_t st) {
   k_slice_xp<<<va.sp.nblk, 256, 0, st>>>(op, va, x, p, r, ks, rs);
+}
+
+void launch_slice_init(const OpArgs& op, const VecArgs& va, const void* rres, int df, const double* scale,
+                       const int* ref_active, float2* x, float2* r, float2* p, const KrylovState& ks, double tol,
+                       RedScratch rs, int conj, cudaStream_t st) {
+  const int g = va.sp.nblk;
+  if (df) {
+    const float4* rr = static_cast<const float4*>(rres);
+    if (conj) k_slice_init<float4, true><<<g, 256, 0, st>>>(op, va, rr, scale, ref_active, x, r, p, ks, tol, rs);
+    else k_slice_init<float4, false><<<g, 256, 0, st>>>(op, va, rr, scale, ref_active, x, r, p, ks, tol, rs);
+  } else {
+    const double2* rr = static_cast<const double2*>(rres);
+    if (conj) k_slice_init<double2, true><<<g, 256, 0, st>>>(op, va, rr, scale, ref_active, x, r, p, ks, tol, rs);
+    else k_slice_init<double2, false><<<g, 256, 0, st>>>(op, va, rr, scale, ref_active, x, r, p, ks, tol, rs);
+  }
 }
 
 }  // namespace bt
