@@ -225,8 +225,42 @@ bt_status bt_get_plane(bt_ctx* ctx, int which, double* vals);
  * otherwise; TE >= Delta + delta, TE/dt must be an integer (to 1e-9).  Each
  * theta step uses the step average of f on both sides (design reading of the
  * paper's f(t^n), f(t^{n-1})); F(t_n) is exact.  Needs bt_assemble first. */
-enum { BT_PGSE = 0 };
+enum {
+  BT_PGSE = 0,
+  BT_DOUBLE_PGSE = 1,      /* bt_set_waveform / bt_waveform_tables only (also below) */
+  BT_COS_OGSE = 2,
+  BT_SIN_OGSE = 3,
+  BT_TRAPEZOID = 4,
+  BT_DOUBLE_TRAPEZOID = 5
+};
 bt_status bt_set_sequence(bt_ctx* ctx, int kind, double delta_us, double Delta_us, double TE_us);
+/* The tables of one of the paper's six temporal profiles (Section 3, "General
+ * diffusion-encoding sequence"; the profiles compared in Section 4), with no
+ * context: F [n_steps + 1] = F(t_n) = int_0^{t_n} f at t_n = n dt in closed
+ * form (F[0] = 0) and int_F2 = int_0^TE F^2 (us^3, for b = q^2 int_F2,
+ * Section 2 Eq. b_value) by composite Gauss-Legendre quadrature between the
+ * profile's breakpoints.  Profiles (times in us):
+ *   BT_PGSE              f = +1 on [0, delta], -1 on [Delta, Delta + delta]
+ *   BT_DOUBLE_PGSE       two PGSE blocks, the second starting at Delta + delta
+ *   BT_COS_OGSE          f = cos(w s) on [0, delta], -cos(w (s - tau)) on
+ *                        (tau, tau + delta], w = 2 pi n_periods / delta,
+ *                        tau = (delta + Delta) / 2
+ *   BT_SIN_OGSE          the same with sin
+ *   BT_TRAPEZOID         PGSE lobes with linear ramps of length ramp_us at both
+ *                        ends (ramp_us <= 0: delta / 10)
+ *   BT_DOUBLE_TRAPEZOID  two trapezoid blocks, the second at Delta + delta
+ * n_steps (out, may be NULL) = TE / dt; F (may be NULL; n_steps + 1 doubles,
+ * caller-owned) and int_F2 (may be NULL) are written when given.  BT_EINVAL
+ * for an unknown kind, delta <= 0, Delta < delta, dt <= 0, TE not an integer
+ * multiple of dt (to 1e-9), TE before the end of the profile, n_periods < 1
+ * (OGSE) or a ramp longer than delta / 2. */
+bt_status bt_waveform_tables(int kind, double delta_us, double Delta_us, double TE_us, double dt_us,
+                             int32_t n_periods, double ramp_us, int32_t* n_steps, double* F, double* int_F2);
+/* bt_set_profile with the tables of bt_waveform_tables for the context's dt
+ * (BT_PGSE is bt_set_sequence).  Needs bt_assemble first; the same errors as
+ * bt_waveform_tables and bt_set_profile. */
+bt_status bt_set_waveform(bt_ctx* ctx, int kind, double delta_us, double Delta_us, double TE_us,
+                          int32_t n_periods, double ramp_us);
 /* Several geometries of uneven size in one context (the uneven batch): after
  * uploading their disjoint union as one mesh (nodes of geometry g =
  * [node_off[g], node_off[g+1]), every tetrahedron inside one geometry, each

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libbtgpu.so")
 BT_OK, BT_EINVAL, BT_ENOMEM, BT_ECUDA, BT_ENOCONV, BT_ENAN, BT_ETIMEOUT, BT_ESTATE, BT_ENODEV = range(9)
 BT_FRAME_LAB, BT_FRAME_TRANSFORMED = 0, 1
 BT_PGSE = 0
+# temporal profiles of bt_set_waveform / bt_waveform_tables
+WAVEFORMS = {"pgse": 0, "double_pgse": 1, "cos_ogse": 2, "sin_ogse": 3, "trapezoid": 4, "double_trapezoid": 5}
 BT_MODE_PLAIN_FP64, BT_MODE_MIXED, BT_MODE_LEARNED = 0, 1, 2
 BT_OPT_RESID_FP64, BT_OPT_PROFILE, BT_OPT_NO_GRAPH = 1, 2, 4
 BT_OPT_VARIANT_ROW, BT_OPT_VARIANT_HALO, BT_OPT_VARIANT_SLICE, BT_OPT_SLICE_ONE_STAGE = 8, 16, 32, 64
@@ -31,7 +33,8 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_train_default_opts", "bt_precond_features", "bt_collect_precond_data", "bt_train_precond",
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
            "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation", "bt_set_diffusion_tensor", "bt_set_weak_periodic", "bt_upload_mesh_2d",
-           "bt_upload_mesh_1d", "bt_upload_mesh_surface", "bt_set_element_tensors"]
+           "bt_upload_mesh_1d", "bt_upload_mesh_surface", "bt_set_element_tensors", "bt_waveform_tables",
+           "bt_set_waveform"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -81,6 +84,8 @@ def lib():
             "bt_set_sequence": [P, C.c_int, D, D, D],
             "bt_set_gradients": [P, I32, P, I32, P],
             "bt_set_profile": [P, I32, P, D],
+            "bt_waveform_tables": [C.c_int, D, D, D, D, I32, D, P, P, P],
+            "bt_set_waveform": [P, C.c_int, D, D, D, I32, D],
             "bt_set_relaxation": [P, P, P],
             "bt_set_diffusion_tensor": [P, P],
             "bt_set_weak_periodic": [P, U32, D],
@@ -272,6 +277,28 @@ def bt_set_profile(ctx, F, int_F2):
     """Arbitrary temporal profile: F[n] = int_0^{n dt} f (us), int_F2 = int_0^TE F^2 (us^3)."""
     F = np.ascontiguousarray(F, dtype=np.float64).ravel()
     _check(ctx, lib().bt_set_profile(ctx, len(F) - 1, _ptr(F), float(int_F2)))
+
+
+def bt_waveform_tables(kind, delta, Delta, TE, dt, n_periods=1, ramp=0.0):
+    """(F[n_steps + 1], int_0^TE F^2) of a named profile (WAVEFORMS), from the
+    library; no context or GPU needed."""
+    k = WAVEFORMS[kind] if isinstance(kind, str) else int(kind)
+    n = C.c_int32()
+    st = lib().bt_waveform_tables(k, float(delta), float(Delta), float(TE), float(dt), int(n_periods),
+                                  float(ramp or 0.0), C.byref(n), None, None)
+    if st != BT_OK:
+        raise BtError(st, "bt_waveform_tables: invalid profile parameters")
+    F = np.zeros(n.value + 1)
+    I = C.c_double()
+    lib().bt_waveform_tables(k, float(delta), float(Delta), float(TE), float(dt), int(n_periods),
+                             float(ramp or 0.0), C.byref(n), _ptr(F), C.byref(I))
+    return F, I.value
+
+
+def bt_set_waveform(ctx, kind, delta, Delta, TE, n_periods=1, ramp=0.0):
+    k = WAVEFORMS[kind] if isinstance(kind, str) else int(kind)
+    _check(ctx, lib().bt_set_waveform(ctx, k, float(delta), float(Delta), float(TE), int(n_periods),
+                                      float(ramp or 0.0)))
 
 
 def bt_set_gradients(ctx, dirs, bvals):

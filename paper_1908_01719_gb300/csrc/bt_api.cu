@@ -569,6 +569,20 @@ bt_status bt_set_profile(bt_ctx* ctx, int32_t n_steps, const double* F, double i
   return BT_OK;
 } BT_ABI_CATCH(ctx)
 
+bt_status bt_set_waveform(bt_ctx* ctx, int kind, double delta, double Delta, double TE, int32_t n_periods,
+                          double ramp) try {
+  if (!ctx) return BT_EINVAL;
+  if (!ctx->assembled) return fail(ctx, BT_ESTATE, "bt_set_waveform: assemble first (dt is needed)");
+  if (kind == BT_PGSE) return bt_set_sequence(ctx, kind, delta, Delta, TE);
+  int32_t N = 0;
+  if (bt_waveform_tables(kind, delta, Delta, TE, ctx->dt, n_periods, ramp, &N, nullptr, nullptr) != BT_OK)
+    return fail(ctx, BT_EINVAL, "bt_set_waveform: invalid profile parameters (see bt_waveform_tables)");
+  std::vector<double> F((size_t)N + 1);
+  double I = 0;
+  bt_waveform_tables(kind, delta, Delta, TE, ctx->dt, n_periods, ramp, &N, F.data(), &I);
+  return bt_set_profile(ctx, N, F.data(), I);
+} BT_ABI_CATCH(ctx)
+
 bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32_t n_b, const double* bvals) try {
   if (!ctx) return BT_EINVAL;
   ctx->last_kind = 0;

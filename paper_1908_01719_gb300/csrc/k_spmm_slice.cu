@@ -163,15 +163,19 @@ size_t slice_smem_bytes(int stages) { return (size_t)stages * SL_STAGE_BYTES + 1
 // STAGES = 2: one block per SM, the next tile's copies overlap this tile's
 // sums; STAGES = 1: two blocks per SM, each copying then summing (the two
 // blocks overlap each other).
+// threads per block of the two configurations
+__host__ __device__ constexpr int slice_threads(int stages) { return stages == 2 ? 2 * SL_THREADS : SL_THREADS; }
+
 template <int NB, bool TRANSF, bool CONJ, int STAGES>
-__global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
+__global__ void __launch_bounds__(slice_threads(STAGES), 3 - STAGES)
     k_spmm_slice(OpArgs op, HaloArgs h, SegPlan spt, int S, const float2* __restrict__ p, float2* __restrict__ q,
                  KrylovState ks, RedScratch rs) {
   if (*ks.n_active == 0) return;
   constexpr int LPR = 32 / NB;   // lanes per row
-  constexpr int SLOTS = 8 * NB;  // rows in flight per block
+  constexpr int NT = slice_threads(STAGES), NW = NT / 32;
+  constexpr int SLOTS = NW * NB;  // rows in flight per block
   constexpr int PPC = 16 / NB;                     // 16-byte pieces per chunk of LPR complex values
-  constexpr int HPT = SL_UMAX * 16 / SL_THREADS;  // halo pieces per thread at most
+  constexpr int HPT = SL_UMAX * 16 / NT;          // halo pieces per thread at most
   extern __shared__ float4 sl_smem_[];
   char* smem = reinterpret_cast<char*>(sl_smem_);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -219,13 +223,13 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
   unsigned phase = 0u;
   // halo row ids of the 16-byte pieces this thread copies for tile tau
   // (loaded one tile ahead of their copies, so their latency overlaps the
-  // sums); piece tid & 15 of halo rows (tid >> 4) + 16 j
+  // sums); piece tid & 15 of halo rows (tid >> 4) + (NT / 16) j
   uint32_t rid[HPT];
   auto load_rid = [&](int tau) {
     const int u0 = __ldg(h.u0 + tau), nu = __ldg(h.u0 + tau + 1) - u0;
 #pragma unroll
     for (int j = 0; j < HPT; ++j) {
-      const int u = (tid >> 4) + 16 * j;
+      const int u = (tid >> 4) + (NT / 16) * j;
       rid[j] = u < nu ? (__ldg(h.ucol + u0 + u) & 0x7FFFFFFFu) : 0xFFFFFFFFu;
     }
   };
@@ -254,20 +258,20 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
     const int pc = tid & 15, b = pc / PPC, pp = pc - b * PPC;
 #pragma unroll
     for (int j = 0; j < HPT; ++j) {
-      const int u = (tid >> 4) + 16 * j;
+      const int u = (tid >> 4) + (NT / 16) * j;
       if (u < nu) cpa16(sh + u * 32 + b * LPR + 2 * pp, p + (size_t)rid[j] * op.Rp + cs + 32 * b + 2 * pp);
     }
     if constexpr (TRANSF)
-      for (int e = tid; e < ne; e += SL_THREADS) cpa4(smd + e, h.mdt + e0 + e);
+      for (int e = tid; e < ne; e += NT) cpa4(smd + e, h.mdt + e0 + e);
     const int w0 = e0 >> 1, nw = ((e0 + ne + 1) >> 1) - w0;  // the index array is padded
-    for (int w = tid; w < nw; w += SL_THREADS) cpa4(sli + w, reinterpret_cast<const uint32_t*>(h.lidx) + w0 + w);
+    for (int w = tid; w < nw; w += NT) cpa4(sli + w, reinterpret_cast<const uint32_t*>(h.lidx) + w0 + w);
     // owned rows: ids, entry offsets, local indices
-    for (int k = tid; k <= nown; k += SL_THREADS) {
+    for (int k = tid; k <= nown; k += NT) {
       if (k < nown) cpa4(srow + k, h.rows + R0 + k);
       cpa4(srowe + k, h.rowe + R0 + k);
     }
     const int l0 = R0 >> 1, nl = ((R0 + nown + 1) >> 1) - l0;  // the local-index array is padded
-    for (int k = tid; k < nl; k += SL_THREADS) cpa4(srowl + k, reinterpret_cast<const uint32_t*>(h.rowl) + l0 + k);
+    for (int k = tid; k < nl; k += NT) cpa4(srowl + k, reinterpret_cast<const uint32_t*>(h.rowl) + l0 + k);
   };
 
   bool any = false;
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
   // block reduction: group-0 lanes of each warp hold FP64 partials of the
   // slice's 32 systems (lane lp: systems L*NB .. L*NB+NB-1)
   __syncthreads();
-  double2* red = reinterpret_cast<double2*>(smem);  // [8 warps][32 systems]
+  double2* red = reinterpret_cast<double2*>(smem);  // [NW warps][32 systems]
   if (g == 0) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) red[(size_t)warp * 32 + lp * NB + b] = a64[b][0];
@@ -380,7 +384,7 @@ __global__ void __launch_bounds__(SL_THREADS, 3 - STAGES)
   __syncthreads();
   if (tid < 32) {
     double2 sum = make_double2(0.0, 0.0);
-    for (int wp = 0; wp < 8; ++wp) {
+    for (int wp = 0; wp < NW; ++wp) {
       const double2 v = red[(size_t)wp * 32 + tid];
       sum.x += v.x;
       sum.y += v.y;
@@ -824,13 +828,16 @@ void launch_spmm_slice(const OpArgs& op, const HaloArgs& h, const SegPlan& spt, 
   const int S = op.Rp / 32;
   const dim3 grid(spt.nblk * S);
   const size_t sm = slice_smem_bytes(stages);
-#define BT_SL_CASE(NBV, STG)                                                                                  \
-  if (op.transformed) {                                                                                       \
-    if (conj) k_spmm_slice<NBV, true, true, STG><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);   \
-    else k_spmm_slice<NBV, true, false, STG><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);       \
-  } else {                                                                                                    \
-    if (conj) k_spmm_slice<NBV, false, true, STG><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);  \
-    else k_spmm_slice<NBV, false, false, STG><<<grid, SL_THREADS, sm, st>>>(op, h, spt, S, p, q, ks, rs);      \
+#define BT_SL_CASE(NBV, STG)                                                                               \
+  {                                                                                                        \
+    constexpr int NT_ = slice_threads(STG);                                                                \
+    if (op.transformed) {                                                                                  \
+      if (conj) k_spmm_slice<NBV, true, true, STG><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);     \
+      else k_spmm_slice<NBV, true, false, STG><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);         \
+    } else {                                                                                               \
+      if (conj) k_spmm_slice<NBV, false, true, STG><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);    \
+      else k_spmm_slice<NBV, false, false, STG><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);        \
+    }                                                                                                      \
   }
   if (stages == 2) {
     switch (nb) {

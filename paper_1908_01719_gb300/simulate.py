@@ -3,14 +3,15 @@ sequence and gradients, run, read the signals.  Marshalling only; every step of
 the method runs inside libbtgpu."""
 from __future__ import annotations
 
-from . import bt, profiles
+from . import bt
 
 
 class Simulation:
     """One context holding one geometry.  `geom` is any object with the fields
     xyz, tets, tet_cmpt, D_cmpt, kappa_cmpt, periodic_mask, box_lo, box_hi,
     dt, theta, delta, Delta, TE, dirs, bvals, transformed, and optionally a
-    temporal `profile` (see profiles.py; None = PGSE), per-compartment `inv_T2`
+    temporal `profile` ({"kind": one of bt.WAVEFORMS, "n_periods", "ramp"}; None =
+    PGSE), per-compartment `inv_T2`
     (1/us) and initial magnetization `rho`, per-compartment `D_tensor` or
     per-element `D_tensor_elem` (lab frame) and
     `weak_periodic` (lab frame)."""
@@ -50,9 +51,8 @@ class Simulation:
             bt.bt_assemble(self.ctx, geom.dt, geom.theta, self.frame)
             prof = getattr(geom, "profile", None)
             if seg is None and prof:
-                F, I = profiles.tables(prof["kind"], geom.delta, geom.Delta, geom.TE, geom.dt,
-                                       prof.get("n_periods", 1), prof.get("ramp"))
-                bt.bt_set_profile(self.ctx, F, I)
+                bt.bt_set_waveform(self.ctx, prof["kind"], geom.delta, geom.Delta, geom.TE,
+                                   prof.get("n_periods", 1), prof.get("ramp") or 0.0)
             elif seg is None:
                 bt.bt_set_sequence(self.ctx, bt.BT_PGSE, geom.delta, geom.Delta, geom.TE)
             else:

@@ -315,7 +315,7 @@ def _profile_case(kind):
 @pytest.mark.parametrize("kind", ["cos_ogse", "sin_ogse", "double_pgse", "trapezoid"])
 @pytest.mark.parametrize("mode", ["plain", "mixed"])
 def test_profiles_match_oracle(sim_cls, bt, kind, mode):
-    """bt_set_profile with the library's tables against the oracle's own
+    """bt_set_waveform (the library's own tables) against the oracle's own
     quadrature of f, lab frame, signals of every RHS."""
     p = _profile_case(kind)
     ref = oracle.run(p)
@@ -332,12 +332,11 @@ def test_profiles_match_oracle(sim_cls, bt, kind, mode):
 
 def test_free_periodic_profile_exact_gpu(sim_cls, bt):
     """Periodic box, cos-OGSE: the exact discrete product with the profile's F."""
-    from paper_1908_01719_gb300 import profiles
     p = geom.free_periodic_box(n=8, L=8.0, dirs=((0.3, 0.4, math.sqrt(0.75)),), bvals=(600.0, 1500.0))
     p.delta, p.Delta = 2000.0, 2000.0
     p.TE = 0.5 * (p.delta + p.Delta) + p.delta
     p.profile = {"kind": "cos_ogse", "n_periods": 2}
-    F, I = profiles.tables("cos_ogse", p.delta, p.Delta, p.TE, p.dt, n_periods=2)
+    F, I = bt.bt_waveform_tables("cos_ogse", p.delta, p.Delta, p.TE, p.dt, n_periods=2)
     sim = sim_cls(p)
     try:
         for mode, tol in [(bt.BT_MODE_PLAIN_FP64, 1e-11), (bt.BT_MODE_MIXED, 1e-8)]:

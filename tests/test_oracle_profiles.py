@@ -2,8 +2,9 @@
 diffusion-encoding sequence"; the profiles of Section 4).  The oracle
 integrates f numerically; these tests fix it against closed forms of
 int_0^TE F^2 derived by hand, against the library's independent closed-form
-tables, and through the exact free-diffusion solution of the periodic box,
-whose continuum limit is exp(-b D) with b = q^2 int F^2 (Eq. b_value)."""
+tables (bt_waveform_tables through the C ABI, host code, no GPU), and through
+the exact free-diffusion solution of the periodic box, whose continuum limit
+is exp(-b D) with b = q^2 int F^2 (Eq. b_value)."""
 import math
 
 import numpy as np
@@ -13,7 +14,7 @@ import geom
 import oracle
 from oracle import btoracle as bo
 from oracle import profiles as op
-from paper_1908_01719_gb300 import profiles as lp
+from paper_1908_01719_gb300 import bt
 
 DELTA, BIG_DELTA, DT = 2000.0, 3000.0, 50.0
 
@@ -51,9 +52,22 @@ def test_library_tables_match_oracle(kind):
     quadrature of f (oracle): two independent routes."""
     TE = _te(kind)
     _, Fo, Io = op.tables(kind, DELTA, BIG_DELTA, TE, DT, n_periods=2, ramp=150.0)
-    Fl, Il = lp.tables(kind, DELTA, BIG_DELTA, TE, DT, n_periods=2, ramp=150.0)
+    Fl, Il = bt.bt_waveform_tables(kind, DELTA, BIG_DELTA, TE, DT, n_periods=2, ramp=150.0)
     assert np.max(np.abs(Fl - Fo)) < 1e-9 * DELTA
     assert abs(Il - Io) < 1e-10 * Io
+
+
+def test_library_refuses_invalid_profiles():
+    """The library's profile parameters are checked before any table is made."""
+    TE = _te("pgse")
+    for args in [("pgse", 0.0, BIG_DELTA, TE, DT), ("pgse", DELTA, DELTA / 2, TE, DT),
+                 ("pgse", DELTA, BIG_DELTA, TE + 1.0, DT), ("pgse", DELTA, BIG_DELTA, DELTA, DT),
+                 ("cos_ogse", DELTA, BIG_DELTA, _te("cos_ogse"), DT, 0),
+                 ("trapezoid", DELTA, BIG_DELTA, TE, DT, 1, 0.6 * DELTA)]:
+        with pytest.raises(bt.BtError):
+            bt.bt_waveform_tables(*args)
+    F, I = bt.bt_waveform_tables("pgse", DELTA, BIG_DELTA, TE, DT)
+    assert len(F) == int(round(TE / DT)) + 1 and F[0] == 0.0
 
 
 def test_trapezoid_tends_to_pgse():
