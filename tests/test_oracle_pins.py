@@ -341,6 +341,22 @@ def test_direct_and_iterative_routes_agree():
     assert np.abs(S1 - S2).max() < 1e-12 * np.abs(S1).max()
 
 
+def test_direct_and_iterative_routes_agree_at_full_cfg1_size():
+    """The stored full-size oracle signals are produced by the iterative route
+    (above a few thousand unknowns).  At cfg1's full 15,625 unknowns the sparse
+    LU is still affordable: both routes give the same signal to rounding, and
+    the stored value with it."""
+    import json
+    import os
+    p = geom.cfg1()
+    S_lu = oracle.run(p, route="lu")
+    S_it = oracle.run(p, route="iter")
+    assert abs(S_lu[0] - S_it[0]) <= 1e-12 * abs(S_lu[0])
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cfg1_full.json")) as f:
+        g = json.load(f)
+    assert abs(S_lu[0] - complex(g["S_re"][0], g["S_im"][0])) <= 1e-12 * abs(S_lu[0])
+
+
 def test_step_average_reading_keeps_second_order():
     """Reading Q1: the theta-scheme with f evaluated at the step ends (the
     literal form) integrates the PGSE lobes by the trapezoid rule, which gives
