@@ -47,6 +47,10 @@ UNIT = "step-RHS/s"
 
 N_TREES = 64
 N_SHELLS = 32
+# the uneven batch of 32 seeded packings (16 directions x 4 b-values each,
+# mixed PGSE timings), at full size or with every grid halved per axis
+CFG5_SCALE = {"cfg5": 1.0, "cfg5_half_grid": 0.5}
+CFG5_ORACLE_CELLS, CFG5_ORACLE_RHS = 8, 2
 
 
 def shells(n=N_SHELLS):
@@ -76,6 +80,8 @@ def workload(name):
         return geom.union(shells(), name="shells")
     if name == "cfg4":
         return geom.cfg4()
+    if name in CFG5_SCALE:
+        return geom.cfg5(scale=CFG5_SCALE[name])
     if name == "cfg3":
         return geom.cfg3()
     if name == "cfg2":
@@ -83,6 +89,21 @@ def workload(name):
     if name == "cfg1":
         return geom.cfg1()
     raise ValueError(name)
+
+
+def step_units(p, n_rhs=None):
+    """Time steps x right-hand sides of one simulation: in an uneven batch each
+    geometry runs its own number of steps (TE_g / dt) for its right-hand sides."""
+    r = p.n_rhs if n_rhs is None else n_rhs
+    seg = getattr(p, "segments", None)
+    if seg is None:
+        return p.n_steps * r
+    return r * int(sum(int(round(te / p.dt)) for te in seg["TE"]))
+
+
+def geom_mod():
+    import geom
+    return geom
 
 
 def n_geometries(p):
@@ -95,13 +116,18 @@ def describe(name, p, n_dof, nnz, n_face):
     if getattr(p, "surface", False):
         elem = "surface triangles (thin layers)"
     G = n_geometries(p)
+    seg = getattr(p, "segments", None)
+    steps = (f"{p.n_steps} steps" if seg is None else
+             f"{min(int(round(t / p.dt)) for t in seg['TE'])}-{max(int(round(t / p.dt)) for t in seg['TE'])} "
+             f"steps per geometry (own PGSE timing each)")
     return {"workload": f"{name}: {len(p.xyz)} nodes, {len(p.tets)} {elem}, {p.n_cmpt} compartments, "
                         + (f"{G} geometries as one uneven batch, " if G > 1 else "") +
                         f"{n_dof} dofs after interface doubling, {nnz} nonzeros, {n_face} interface faces; "
                         f"{len(p.dirs)} dirs x {len(p.bvals)} b-values = {p.n_rhs} RHS; PGSE delta {p.delta/1e3} ms "
-                        f"Delta {p.Delta/1e3} ms, dt {p.dt} us, {p.n_steps} steps; "
+                        f"Delta {p.Delta/1e3} ms, dt {p.dt} us, {steps}; "
                         f"{'transformed (periodic)' if p.transformed else 'lab'} frame",
-            "n_dof": n_dof, "nnz": nnz, "rhs": p.n_rhs * G, "time_steps": p.n_steps,
+            "n_dof": n_dof, "nnz": nnz, "rhs": p.n_rhs * G, "time_steps": p.n_steps if seg is None else None,
+            "step_rhs_per_simulation": step_units(p),
             "l2_policy": "inputs larger than L2: Krylov vectors n_dof x RHS x 8 B each "
                          f"({n_dof * p.n_rhs * 8 / 1e9:.2f} GB) vs 129 MB L2"}
 
@@ -161,6 +187,11 @@ def _oracle_task(args):
     import geom
     import oracle
     t0 = time.time()
+    if name in CFG5_SCALE:                 # geometry r of the batch on a coarse grid, a few RHS
+        p = geom.cfg5_geometry(r, scale=1.0)
+        p = geom.cfg5_geometry(r, scale=CFG5_ORACLE_CELLS / p.meta["N"])
+        oracle.run(p, rhs=list(range(CFG5_ORACLE_RHS)))
+        return time.time() - t0, p.n_steps * CFG5_ORACLE_RHS
     if name in ("trees1d", "shells"):      # one whole geometry (all its RHS) per task
         p = geom.dendrite_tree(seed=r) if name == "trees1d" else shells(r + 1)[r]
         oracle.run(p)
@@ -198,7 +229,10 @@ def oracle_sample(name, n_rhs_sample, grid):
                 os.environ[k] = v
     wall = time.time() - t0
     units = sum(r[1] for r in res)
-    if name in ("trees1d", "shells"):
+    if name in CFG5_SCALE:
+        what = (f"{name}: geometries 0..{n_rhs_sample - 1} of the batch, each on a {CFG5_ORACLE_CELLS}^3 Kuhn grid of "
+                f"its own box, {CFG5_ORACLE_RHS} RHS each over their own full PGSE sequences")
+    elif name in ("trees1d", "shells"):
         what = f"{name}: the first {n_rhs_sample} geometries of the batch, all 9 RHS x {res[0][1] // 9} steps"
     elif name == "disk2d":
         what = f"disk2d seeded geometry on a {grid}^2 grid, {n_rhs_sample} RHS x {res[0][1]} steps"
@@ -262,17 +296,27 @@ KERNEL = {"row": "k_spmm_krylov", "halo": "k_spmm_halo", "slice": "k_spmm_slice 
 ROW_SPMM_TRAFFIC = {"n_dof": 343793, "bytes": 791.9e6 + 329.7e6}
 
 
-def spmm_bytes(n, nnz, transformed, launches, sys_iters, variant, G=1):
-    """Algorithmic HBM bytes of the dominant kernel summed over its launches:
-    per launch the row pointers, column indices and packed FP32 planes (A0 and
-    three direction planes, plus MD in the transformed frame), and per active
-    system of each launch its vectors (VECTORS_PER_SYSTEM x rows x 8 B).  A
-    system spans its own geometry's rows: n for one geometry, n / G on average
-    in an uneven batch of G (the per-geometry split of the iteration count is
-    not recorded, so the batch figure uses the mean)."""
+def spmm_bytes(n, nnz, transformed, launches, seg_iters, seg_rows, vectors):
+    """Algorithmic HBM bytes of a kernel summed over its launches: per launch
+    the row pointers, column indices and packed FP32 planes (A0 and three
+    direction planes, plus MD in the transformed frame), and per active system
+    of each launch its vectors (`vectors` x rows x 8 B).  A system spans its
+    own geometry's rows: seg_iters[g] (active systems of segment g summed over
+    the launches) times seg_rows[g]."""
     planes = 5 if transformed else 4
     matrix = 4 * (n + 1) + nnz * (4 + 4 * planes)
-    return launches * matrix + sys_iters * VECTORS_PER_SYSTEM[variant] * (n / G) * 8
+    return launches * matrix + vectors * 8 * float(np.dot(np.asarray(seg_iters, float), np.asarray(seg_rows, float)))
+
+
+def segment_rows(sim, p):
+    """Rows (dofs) of each geometry of the context."""
+    seg = getattr(p, "segments", None)
+    if seg is None:
+        return np.array([sim.n_dof])
+    from paper_1908_01719_gb300 import bt
+    node, _ = bt.bt_get_dofmap(sim.ctx)
+    g_of = np.searchsorted(np.asarray(seg["node_off"]), node, side="right") - 1
+    return np.bincount(g_of, minlength=len(seg["node_off"]) - 1)
 
 
 def run_ours(args):
@@ -296,7 +340,7 @@ def run_ours(args):
     t_setup = time.time() - t_setup
     mode = bt.BT_MODE_MIXED
     G = n_geometries(p)
-    units = p.n_steps * p.n_rhs * G
+    units = step_units(p)
 
     def barrier():
         if ws > 1:
@@ -307,6 +351,7 @@ def run_ours(args):
     # timed region
     flags = bt.BT_OPT_PROFILE
     spmm_ms, vec_ms, spmm_launch, launches, iters, sys_iters = 0.0, 0.0, 0, 0, 0, 0
+    seg_iters = np.zeros(G, dtype=np.int64)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         barrier()
@@ -321,6 +366,7 @@ def run_ours(args):
             launches += st["kernel_launches"]
             iters += st["krylov_iters"]
             sys_iters += st["sys_iters"]
+            seg_iters += bt.bt_get_segment_stats(sim.ctx, G)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
@@ -343,25 +389,49 @@ def run_ours(args):
     ms_max = float(ms_t.item())
     value = units * args.steps * ws / (ms_max / 1e3)
 
-    # accuracy and the plain per-direction FP64 GPU solve on a sample of RHS
-    # (an uneven batch runs every RHS of every geometry at once)
-    sample = sorted(set([0, p.n_rhs // 3, (2 * p.n_rhs) // 3, p.n_rhs - 1])) if G == 1 else list(range(p.n_rhs))
-    ranges = [(r, r + 1) for r in sample] if G == 1 else [(0, 0)]
-    fp64_ms, errs = 0.0, []
-    for rb, re in ranges:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        S64, _, stat64, _ = sim.run(bt.BT_MODE_PLAIN_FP64, rhs_begin=rb, rhs_end=re)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        fp64_ms += e0.elapsed_time(e1)
-        idx = [rb] if G == 1 else range(G * p.n_rhs)
-        errs += [abs(S[i] - S64[i]) / abs(S64[i]) for i in idx]
-    fp64_rate = p.n_steps * len(sample) * G / (fp64_ms / 1e3)
+    # accuracy and the plain per-direction FP64 GPU solve on a sample of RHS;
+    # a small uneven batch runs every RHS of every geometry at once, the large
+    # one (cfg5) runs single geometries of the batch one RHS at a time
+    fp64_ms, fp64_units, errs, fp64_what = 0.0, 0, [], None
+    if args.config in CFG5_SCALE:
+        sample = []
+        for g in (0, 1):  # two seeded geometries of the batch, three RHS each
+            pg = geom_mod().cfg5_geometry(g, scale=CFG5_SCALE[args.config])
+            sg = Simulation(pg, device=local, stream=stream.cuda_stream)
+            try:
+                for r in (0, pg.n_rhs // 2, pg.n_rhs - 1):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    S64, _, _, _ = sg.run(bt.BT_MODE_PLAIN_FP64, rhs_begin=r, rhs_end=r + 1)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    fp64_ms += e0.elapsed_time(e1)
+                    fp64_units += pg.n_steps
+                    errs.append(abs(S[g * p.n_rhs + r] - S64[r]) / abs(S64[r]))
+                    sample.append([g, r])
+            finally:
+                sg.close()
+        fp64_what = "geometries 0 and 1 of the batch run alone, three RHS each, one RHS per run"
+    else:
+        sample = sorted(set([0, p.n_rhs // 3, (2 * p.n_rhs) // 3, p.n_rhs - 1])) if G == 1 else list(range(p.n_rhs))
+        ranges = [(r, r + 1) for r in sample] if G == 1 else [(0, 0)]
+        for rb, re in ranges:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S64, _, stat64, _ = sim.run(bt.BT_MODE_PLAIN_FP64, rhs_begin=rb, rhs_end=re)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            fp64_ms += e0.elapsed_time(e1)
+            idx = [rb] if G == 1 else range(G * p.n_rhs)
+            errs += [abs(S[i] - S64[i]) / abs(S64[i]) for i in idx]
+        fp64_units = step_units(p, len(sample))
+    fp64_rate = fp64_units / (fp64_ms / 1e3)
 
     # roofline of the dominant kernel (fused FP32 SpMM), from live CUDA events
     n, nnz, nf = sim.n_dof, sim.nnz, sim.n_iface
-    bytes_total = spmm_bytes(n, nnz, p.transformed, spmm_launch, sys_iters, tuning["variant"], G)
+    seg_rows = segment_rows(sim, p)
+    bytes_total = spmm_bytes(n, nnz, p.transformed, spmm_launch, seg_iters, seg_rows,
+                             VECTORS_PER_SYSTEM[tuning["variant"]])
     bytes_launch = bytes_total / max(1, spmm_launch)
     avg_ms = spmm_ms / max(1, spmm_launch)
     achieved = bytes_total / (spmm_ms / 1e3) / 1e9
@@ -371,8 +441,7 @@ def run_ours(args):
     # of all launches of an iteration
     v = tuning["variant"]
     planes = 5 if p.transformed else 4
-    it_bytes = spmm_launch * (4 * (n + 1) + nnz * (4 + 4 * planes)) + \
-        sys_iters * VECTORS_PER_ITER[v] * (n / G) * 8
+    it_bytes = spmm_bytes(n, nnz, p.transformed, spmm_launch, seg_iters, seg_rows, VECTORS_PER_ITER[v])
     it_ms = spmm_ms + vec_ms
     peaks = {}
     try:
@@ -415,7 +484,8 @@ def run_ours(args):
             "accuracy": {"max_rel_err_vs_gpu_fp64": float(max(errs)), "rhs_checked": sample,
                          "err_est_max": float(np.max(err))},
             "fp64_plain_per_direction_gpu": {"value": fp64_rate, "unit": UNIT, "rhs_sample": sample,
-                                             "speedup_of_value": value / ws / fp64_rate},
+                                             "speedup_of_value": value / ws / fp64_rate,
+                                             **({"sample_note": fp64_what} if fp64_what else {})},
             "spmm_autotune": tuning,
             "roofline": {"bound": "hbm",
                          "kernel": KERNEL[tuning["variant"]]
@@ -455,7 +525,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4", "disk2d", "trees1d", "shells"])
+    ap.add_argument("--config", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4", "disk2d", "trees1d", "shells"]
+                    + list(CFG5_SCALE))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

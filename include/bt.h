@@ -385,6 +385,12 @@ bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* ms_iter, in
  * over the fused SpMM launches (the right-hand sides each launch actually
  * processed), and with BT_OPT_PROFILE the summed device time (ms) of the
  * other kernels of the Krylov iterations (vector updates, inner products). */
+/* The active systems of the last bt_run summed over its fused SpMM launches,
+ * per segment (geometry): sys_iters [G], G = the context's segment count (1
+ * without bt_set_segments).  With each segment's row count n_g this gives the
+ * exact vector traffic of an uneven batch.  BT_EINVAL for another G or before
+ * any run. */
+bt_status bt_get_segment_stats(const bt_ctx* ctx, int32_t G, int64_t* sys_iters);
 bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters,
                        int64_t* refine_passes, int64_t* spmm_launches, double* spmm_ms,
                        double* resid_ms, int64_t* resid_launches, int64_t* kernel_launches,

@@ -34,7 +34,7 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
            "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation", "bt_set_diffusion_tensor", "bt_set_weak_periodic", "bt_upload_mesh_2d",
            "bt_upload_mesh_1d", "bt_upload_mesh_surface", "bt_set_element_tensors", "bt_waveform_tables",
-           "bt_set_waveform"]
+           "bt_set_waveform", "bt_get_segment_stats"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -85,6 +85,7 @@ def lib():
             "bt_set_gradients": [P, I32, P, I32, P],
             "bt_set_profile": [P, I32, P, D],
             "bt_waveform_tables": [C.c_int, D, D, D, D, I32, D, P, P, P],
+            "bt_get_segment_stats": [P, I32, P],
             "bt_set_waveform": [P, C.c_int, D, D, D, I32, D],
             "bt_set_relaxation": [P, P, P],
             "bt_set_diffusion_tensor": [P, P],
@@ -352,6 +353,13 @@ def bt_get_halo_tiles(ctx, umax):
     _check(ctx, lib().bt_get_halo_tiles(ctx, int(umax), C.byref(nt), C.byref(nh),
                                         *[_ptr(out[k]) for k in ("r0", "rows", "rowe", "rowl", "u0", "ucol",
                                                                  "lidx")]))
+    return out
+
+
+def bt_get_segment_stats(ctx, G):
+    """Active systems summed over the last run's SpMM launches, per segment."""
+    out = np.zeros(G, dtype=np.int64)
+    _check(ctx, lib().bt_get_segment_stats(ctx, int(G), _ptr(out)))
     return out
 
 

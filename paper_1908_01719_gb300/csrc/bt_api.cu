@@ -1310,7 +1310,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   }
   CK(ensure(ctx->ks_pend, SY));
   CK(ensure(ctx->ks_par, 1));
-  CK(ensure(ctx->d_sys_iter, 1));
+  CK(ensure(ctx->d_sys_iter, 1 + (size_t)G));
   CK(ensure(ctx->ks_rho, 2 * (size_t)SY));
   CK(ensure(ctx->ks_alpha, 2 * (size_t)SY));
   CK(ensure(ctx->ks_beta, 2 * (size_t)SY));
@@ -1434,7 +1434,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   ctx->ev_used = 0;
   CK(cudaMemsetAsync(ctx->rf_err.p, 0, SY * sizeof(double), st));
   CK(cudaMemsetAsync(ctx->ks_status.p, 0, SY * sizeof(int), st));
-  CK(cudaMemsetAsync(ctx->d_sys_iter.p, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(ctx->d_sys_iter.p, 0, (1 + (size_t)G) * sizeof(unsigned long long), st));
   const double* rho_dof = ctx->have_rho ? ctx->d_rho_dof.p : nullptr;
   if (df) launch_fill_u_df(va, ctx->udf.p, rho_dof, st);
   else launch_fill_u(va, ctx->u64.p, rho_dof, st);
@@ -1634,11 +1634,13 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   CK(cudaMemcpyAsync(err.data(), ctx->rf_err.p, SY * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(stat.data(), ctx->ks_status.p, SY * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ref_left.data(), ctx->rf_active.p, SY * sizeof(int), cudaMemcpyDeviceToHost, st));
-  unsigned long long sys_iter = 0;
-  CK(cudaMemcpyAsync(&sys_iter, ctx->d_sys_iter.p, sizeof(sys_iter), cudaMemcpyDeviceToHost, st));
+  std::vector<unsigned long long> sys_iter(1 + (size_t)G, 0ULL);
+  CK(cudaMemcpyAsync(sys_iter.data(), ctx->d_sys_iter.p, sys_iter.size() * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (prof) ev_harvest(ctx);
-  ctx->st_sys_iters = (int64_t)sys_iter;
+  ctx->st_sys_iters = (int64_t)sys_iter[0];
+  ctx->st_seg_sys_iters.assign(sys_iter.begin() + 1, sys_iter.end());
   bt_status ret = BT_OK;
   for (int s = 0; s < SY; ++s) {
     ctx->S[2 * (rb + s)] = S[2 * s];
@@ -1733,6 +1735,13 @@ extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* 
     if (ms_iter) ms_iter[k] = t.ms[k];
   for (int k = 0; k < 2; ++k)
     if (ms_resid) ms_resid[k] = t.ms_resid[k];
+  return BT_OK;
+}
+
+extern "C" bt_status bt_get_segment_stats(const bt_ctx* ctx, int32_t G, int64_t* sys_iters) {
+  if (!ctx || !sys_iters || G < 1) return BT_EINVAL;
+  if ((size_t)G != ctx->st_seg_sys_iters.size()) return BT_EINVAL;
+  for (int32_t g = 0; g < G; ++g) sys_iters[g] = (int64_t)ctx->st_seg_sys_iters[g];
   return BT_OK;
 }
 

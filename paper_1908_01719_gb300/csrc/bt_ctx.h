@@ -141,6 +141,7 @@ struct bt_ctx {
   std::vector<int> status;
   int64_t st_steps = 0, st_iters = 0, st_refine = 0, st_spmm = 0, st_resid = 0, st_launches = 0, st_sys_iters = 0;
   double st_spmm_ms = 0, st_resid_ms = 0, st_vec_ms = 0;
+  std::vector<unsigned long long> st_seg_sys_iters;  // active systems summed over SpMM launches, per segment
   std::vector<bt::EventPair> ev_pool;
   size_t ev_used = 0;
 

@@ -82,7 +82,8 @@ struct KrylovState {
   // halo-tile iteration only (null otherwise)
   int* par;          // device: which of the two p buffers holds the current p
   int* pend;         // per system: x += alpha p of the last apply still to do
-  unsigned long long* sys_iter;  // device: active systems summed over SpMM launches (or null)
+  unsigned long long* sys_iter;  // device [1 + G]: active systems summed over SpMM launches, in all
+                                 // and per segment (or null)
 };
 
 // Per-system refinement scalars.
@@ -521,6 +522,11 @@ __device__ __forceinline__ void reduce_partials(const double* part, const SegPla
   }
 }
 
+
+// one more SpMM for system s of segment s / R, if it is active (last block)
+__device__ __forceinline__ void count_segment_iter(const KrylovState& ks, int s, int R) {
+  if (ks.sys_iter && ks.active[s]) atomicAdd(ks.sys_iter + 1 + s / R, 1ULL);
+}
 
 // alpha = rho / <p, q> for system s (last block of a Krylov SpMM); a zero or
 // non-finite <p, q> is a breakdown and freezes the system.

@@ -142,7 +142,10 @@ __global__ void __launch_bounds__(256) k_spmm_krylov(OpArgs op, const T2* __rest
   if (!last_block(rs.counter, gridDim.x * gridDim.y)) return;
   if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
   __syncthreads();
-  reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 pq) { krylov_alpha(ks, s, pq); });
+  reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 pq) {
+    count_segment_iter(ks, s, op.R);
+    krylov_alpha(ks, s, pq);
+  });
 }
 
 // ---------------------------------------------------------------- plane gather

@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(256, 2) k_spmm_halo(OpArgs op, HaloArgs h, con
   if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
   __syncthreads();
   reduce_partials(rs.part, op.sp, op.Rp, op.R, [&](int s, double2 pq) {
+    count_segment_iter(ks, s, op.R);
     krylov_alpha(ks, s, pq);
     ks.pend[s] = ks.active[s];
   });

@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(slice_threads(STAGES), 3 - STAGES)
       t.x += v.x;
       t.y += v.y;
     }
+    count_segment_iter(ks, s, op.R);
     krylov_alpha(ks, s, t);
     ks.pend[s] = ks.active[s];  // the x update of this iteration is still to do
   }

@@ -74,3 +74,21 @@ def test_seeded_packings_batch_equals_separate_runs(sim_cls, bt):
             s1.close()
         assert np.all(st == 0)
         assert np.max(np.abs(S[g * R:(g + 1) * R] - Sg) / np.abs(Sg)) < 1e-6, g
+
+
+def test_segment_stats_add_up(sim_cls, bt):
+    """Per-geometry SpMM counts (bt_get_segment_stats) sum to the run's total
+    and are larger for a geometry with a longer sequence (more time steps)."""
+    parts = _small_union()
+    u = geom.union(parts)
+    sim = sim_cls(u)
+    try:
+        sim.run(bt.BT_MODE_MIXED)
+        seg = bt.bt_get_segment_stats(sim.ctx, 3)
+        st = sim.stats()
+        assert seg.sum() == st["sys_iters"] and np.all(seg > 0)
+        assert seg[1] > seg[0]          # 150 steps against 60
+        with pytest.raises(bt.BtError):
+            bt.bt_get_segment_stats(sim.ctx, 2)
+    finally:
+        sim.close()
