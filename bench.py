@@ -279,13 +279,16 @@ def run_reference(args):
 # launch of the dominant kernel: the row SpMM reads X and writes Y; the
 # halo-staged apply reads z, p_prev and x and writes x, p and q; the
 # slice-tiled SpMM reads p and writes q
-VECTORS_PER_SYSTEM = {"row": 2, "halo": 6, "slice": 2, "slice1": 2}
+VECTORS_PER_SYSTEM = {"row": 2, "halo": 6, "slice": 2, "slice1": 2, "slice_small": 2, "slice_small1": 2}
 # ... and per Krylov iteration (all launches of one iteration): row 2 + 6 + 3,
 # halo 6 + 3 (z update: reads z, q, writes z), slice 2 + 3 (r, q read, r
 # written) + 5 (x, p, r read, x, p written)
-VECTORS_PER_ITER = {"row": 11, "halo": 9, "slice": 10, "slice1": 10}
-KERNEL = {"row": "k_spmm_krylov", "halo": "k_spmm_halo", "slice": "k_spmm_slice (two stages)",
-          "slice1": "k_spmm_slice (one stage, two blocks per SM)"}
+VECTORS_PER_ITER = {"row": 11, "halo": 9, "slice": 10, "slice1": 10, "slice_small": 10, "slice_small1": 10}
+KERNEL = {"row": "k_spmm_krylov", "halo": "k_spmm_halo",
+          "slice": "k_spmm_slice (256-halo-row tiles, two stages, one block per SM)",
+          "slice1": "k_spmm_slice (256-halo-row tiles, one stage, two blocks per SM)",
+          "slice_small": "k_spmm_slice (128-halo-row tiles, two stages, two blocks per SM)",
+          "slice_small1": "k_spmm_slice (128-halo-row tiles, one stage, three blocks per SM)"}
 
 
 # DRAM bytes (read + write) of one launch of the row SpMM k_spmm_krylov<4>, lab
@@ -451,6 +454,29 @@ def run_ours(args):
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
 
+    # the polynomial preconditioners on the same workload: the network trained
+    # by precond_study.py (96^3, dt 20/50/100 us) and its fitted fixed
+    # Chebyshev polynomial, against Jacobi on the same row-SpMM host loop and
+    # against the tuned Jacobi path; one whole simulation each, wall clock
+    learned = None
+    if args.config == "cfg4" and ws == 1 and not args.no_learned:
+        import precond_study as ps
+        if os.path.exists(ps.WEIGHTS):
+            w, cheb, meta = ps.load_weights()
+            modes, _ = ps.run_modes(sim, bt, w, cheb, ref=S)
+            for m in modes.values():
+                m["step_rhs_per_s"] = units / m["seconds"]
+            learned = {"unit": UNIT, "modes": modes, "chebyshev_interval": [meta["chebyshev"]["lo"],
+                                                                            meta["chebyshev"]["hi"]],
+                       "trained_on": meta["trained_on"],
+                       "gain_vs_jacobi_tuned": modes["jacobi_tuned"]["seconds"] / modes["learned"]["seconds"],
+                       "gain_vs_chebyshev": modes["chebyshev"]["seconds"] / modes["learned"]["seconds"],
+                       "note": "BT_MODE_LEARNED timed as a whole simulation (wall clock, signals on the host); "
+                               "spmm_total = Krylov SpMM launches + Horner SpMM launches; gains are time ratios "
+                               "(> 1: the learned polynomial is faster)"}
+        else:
+            learned = {"unavailable": "no trained weights in the package (precond_study.py --out)"}
+
     # end to end through the public API from host buffers
     torch.cuda.synchronize(dev)
     t0 = time.time()
@@ -512,6 +538,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(d2h), "seconds": e2e_s,
                     "includes": "host mesh pipeline, upload, assembly, full run, signal read-back"},
             "gpu_launches": int(launches), "clocks": clocks,
+            **({"learned_preconditioner": learned} if learned is not None else {}),
             "graph_path": {"value": units * args.steps * ws / (ms_graph / 1e3), "unit": UNIT,
                            "note": "same runs, each time step one captured CUDA graph with conditional "
                                    "WHILE nodes; the headline value uses host-driven launches so that every "
@@ -525,6 +552,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned / Chebyshev / Jacobi preconditioner comparison (cfg4)")
     ap.add_argument("--config", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4", "disk2d", "trees1d", "shells"]
                     + list(CFG5_SCALE))
     args = ap.parse_args()

@@ -49,7 +49,8 @@ enum {
   BT_ECUDA = 3,     /* CUDA runtime error (message in bt_last_error)          */
   BT_ENOCONV = 4,   /* a Krylov or refinement loop hit its iteration cap      */
   BT_ENAN = 5,      /* NaN/Inf met in a right-hand side or a Krylov scalar    */
-  BT_ETIMEOUT = 6,  /* reserved: no kernel here waits on another; unused      */
+  BT_ETIMEOUT = 6,  /* a slice SpMM block's wait for its tile copy ran past its
+                       clock limit (about 2 s); the system's status records it */
   BT_ESTATE = 7,    /* call out of order (e.g. bt_run before bt_assemble)     */
   BT_ENODEV = 8     /* GPU call on a host-only context                        */
 };
@@ -301,7 +302,9 @@ bt_status bt_set_gradients(bt_ctx* ctx, int32_t n_dir, const double* dirs, int32
  *                       double-float (or native FP64 with BT_OPT_RESID_FP64);
  *                       stop at |r| <= tol_ref * |r_0|.
  *   BT_MODE_LEARNED     as MIXED, with the learned polynomial preconditioner
- *                       (bt_load_precond) in the inner Krylov; Jacobi fallback.
+ *                       (bt_load_precond / bt_train_precond) or a fixed one
+ *                       (bt_set_precond_poly) in the inner Krylov; Jacobi
+ *                       fallback.
  * Each step solves L_n d = r_0 = (R_n - L_n) u^{n-1}, u^n = u^{n-1} + d, with
  * L_n = M + theta dt A_n, R_n = M - (1-theta) dt A_{n-1} (Appendix B). */
 enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
@@ -312,10 +315,13 @@ enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
  * use that Krylov variant together with the row / halo double-float residuals
  * (bt_get_tuning; _HALO falls back to the tuned choice where the halo tiles
  * are not available); BT_OPT_VARIANT_SLICE bypasses the autotuner's Krylov
- * choice for the slice-tiled iteration, the faster of its two configurations,
- * or with BT_OPT_SLICE_ONE_STAGE the one-stage configuration (residual kernel
- * still tuned; falls back to the tuned choice when the padded RHS width is
- * not a multiple of 32 or a row does not fit a slice tile). */
+ * choice for the slice-tiled iteration, the fastest of its configurations
+ * (bt_get_tuning variants 2..5); BT_OPT_SLICE_ONE_STAGE forces configuration
+ * 1 (variant 3), and (c + 1) << BT_OPT_SLICE_CONFIG_SHIFT forces
+ * configuration c in 0..3 (variant 2 + c).  The residual kernel is still
+ * tuned, and the slice flags fall back to the tuned choice when the padded
+ * RHS width is not a multiple of 32 or a row does not fit the
+ * configuration's tiles. */
 enum {
   BT_OPT_RESID_FP64 = 1u,
   BT_OPT_PROFILE = 2u,
@@ -323,7 +329,8 @@ enum {
   BT_OPT_VARIANT_ROW = 8u,
   BT_OPT_VARIANT_HALO = 16u,
   BT_OPT_VARIANT_SLICE = 32u,
-  BT_OPT_SLICE_ONE_STAGE = 64u
+  BT_OPT_SLICE_ONE_STAGE = 64u,
+  BT_OPT_SLICE_CONFIG_SHIFT = 8  /* bits 8..10: slice configuration + 1 (0 = none) */
 };
 typedef struct bt_solver_opts {
   double tol_fp64;      /* plain FP64 stopping tolerance (default 1e-12)          */
@@ -365,12 +372,17 @@ bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_
  *      in shared memory, search-direction and solution updates fused in) +
  *      z update; offered in BT_MODE_MIXED only
  *   2  slice-tiled apply (Morton tiles, one 32-system slice of the halo rows
- *      of p staged in shared memory, two pipelined stages, one block per SM)
+ *      of p staged in shared memory, the tile's planes by TMA bulk copy)
  *      + r update (rho', |r|^2) + x and p update; offered in BT_MODE_MIXED
- *      when the padded RHS width is a multiple of 32
- *   3  the same with one stage and two blocks per SM
- * ms_iter [4] (may be NULL) receives the measured ms per iteration of each
- * (0 = not timed).  The double-float correction residual is tuned on its own:
+ *      when the padded RHS width is a multiple of 32.  Configuration 0:
+ *      tiles of at most 256 halo rows, 128 owned rows and 1,536 entries, two
+ *      pipelined stages, one block of 512 threads per SM
+ *   3  configuration 1: the same tiles, one stage, two blocks of 256 per SM
+ *   4  configuration 2: tiles of at most 128 halo rows, 64 owned rows and
+ *      1,024 entries, two stages, two blocks of 256 per SM
+ *   5  configuration 3: the small tiles, one stage, three blocks of 256 per SM
+ * ms_iter [6] (may be NULL) receives the measured ms per iteration of each
+ * (0 = not timed or not offered).  The double-float correction residual is tuned on its own:
  * resid_variant 0 = row kernel, 1 = halo-staged kernel (the step-start
  * residual follows it), ms_resid [2] the measured ms per launch of each.
  * Any pointer may be NULL.  BT_ESTATE before any tuning. */
@@ -407,7 +419,8 @@ bt_status bt_get_stats(const bt_ctx* ctx, int64_t* steps, int64_t* krylov_iters,
  * applied by Horner (8 fused SpMMs) inside the inner Krylov solve.  A system
  * falls back to Jacobi when the polynomial breaks down (rho = 0, or a
  * non-positive <r, z> for the Hermitian transformed systems), stagnates, or
- * has not converged within max_iter / 2; the refinement tolerance judges the
+ * has not converged within 32 iterations (max_iter / 2 if fewer); the
+ * refinement tolerance judges the
  * result, so signals match the Jacobi path to that tolerance.  (The paper's
  * solver is unnamed, Appendix B; this preconditioner has no counterpart
  * there.)  Parameters: BT_PRECOND_NPARAM floats in the order W1 (64x5,
@@ -427,7 +440,8 @@ bt_status bt_train_default_opts(bt_train_opts* o);
  * h = (6 * mean tetrahedron volume)^(1/3). */
 bt_status bt_precond_features(const bt_ctx* ctx, double* D, double* kappa, double* h);
 /* Training samples from the method's own step solves: runs the mixed-mode time
- * loop (opts as bt_run) and, at each listed step (1-based), takes every RHS's
+ * loop (opts as bt_run) up to the last listed step (the context's signals are
+ * then those of that step's state) and, at each listed step (1-based), takes every RHS's
  * normalised step residual r and the Krylov basis y_j = L (D^-1 L)^j D^-1 r,
  * j = 0..8, returning per sample (sample = step-major, then RHS):
  * feat [5], G = Re(Y^H Y)/|r|^2 [81], h = Re(Y^H r)/|r|^2 [9].
@@ -448,6 +462,47 @@ bt_status bt_precond_eval(bt_ctx* ctx, int64_t n, const float* feat, const doubl
 /* Copy the FP32 master weights out / in (BT_PRECOND_NPARAM floats). */
 bt_status bt_save_precond(const bt_ctx* ctx, float* w);
 bt_status bt_load_precond(bt_ctx* ctx, const float* w);
+
+/* ---------------------------------------------------------------- fixed polynomial baseline
+ * The comparison the learned polynomial has to win: one fixed polynomial
+ * P = sum_j c_j (D^-1 L)^j D^-1 for every system and step, applied by the
+ * same Horner kernels.  (No counterpart in the paper, whose solver is
+ * unnamed, Appendix B.)
+ *
+ * bt_set_precond_poly: c9 [9] host array, copied; BT_MODE_LEARNED then uses
+ * these coefficients instead of the network (no network needed).  c9 = NULL
+ * returns BT_MODE_LEARNED to the network.  BT_EINVAL for a non-finite
+ * coefficient.
+ *
+ * bt_chebyshev_poly: the degree-8 p whose residual polynomial 1 - l p(l) is
+ * T_9((hi + lo - 2 l)/(hi - lo)) / T_9((hi + lo)/(hi - lo)), T_9 the Chebyshev
+ * polynomial of the first kind: the least maximum residual over [lo, hi]
+ * among residual polynomials of degree 9 with value 1 at 0.  c9 [9] (out),
+ * monomial coefficients in l.  BT_EINVAL unless 0 < lo < hi < inf.  Host
+ * code; needs no context.
+ *
+ * bt_fit_chebyshev: the interval whose Chebyshev polynomial minimises the
+ * mean of the per-sample loss 1 - 2 c.h + c.G c over n samples of
+ * bt_collect_precond_data (G [n][81], h [n][9], host arrays), plus the
+ * loss's uncertainty rel_err (2 |c|.|h| + |c|.|G| |c|) (means of the entry
+ * moduli) for data known to relative accuracy rel_err (about 1e-6 for the
+ * collected samples, whose Krylov vectors are FP32; the Krylov basis is close
+ * to linearly dependent, so without it large coefficients can show a small
+ * or negative loss).  hi is kept at or above 1.05 lam, lam = the largest
+ * |y_8| / |y_7| over the samples (a power-iteration estimate of the largest
+ * eigenvalue modulus of D^-1 L).  Search: a log-spaced grid over hi in
+ * [max(1/4, 1.05 lam), max(16, 4.2 lam)] and lo/hi in [1e-4, 0.95], refined
+ * three times around the best point.  Outputs (each may be NULL): lo, hi,
+ * c9 [9], loss = the mean loss at the optimum (without the uncertainty term).
+ * BT_EINVAL for n < 1, rel_err outside [0, 1) or non-finite data.
+ *
+ * bt_get_precond_stats: Horner launches of the last bt_run (each is one
+ * fused SpMM over the polynomial systems). */
+bt_status bt_set_precond_poly(bt_ctx* ctx, const double* c9);
+bt_status bt_chebyshev_poly(double lo, double hi, double* c9);
+bt_status bt_fit_chebyshev(int64_t n, const double* G, const double* h, double rel_err, double* lo, double* hi,
+                           double* c9, double* loss);
+bt_status bt_get_precond_stats(const bt_ctx* ctx, int64_t* horner_launches);
 
 /* ---------------------------------------------------------------- allocation-free gradient
  * bt_precond_grad_noalloc computes what bt_precond_eval computes for the loss

@@ -23,6 +23,14 @@ WAVEFORMS = {"pgse": 0, "double_pgse": 1, "cos_ogse": 2, "sin_ogse": 3, "trapezo
 BT_MODE_PLAIN_FP64, BT_MODE_MIXED, BT_MODE_LEARNED = 0, 1, 2
 BT_OPT_RESID_FP64, BT_OPT_PROFILE, BT_OPT_NO_GRAPH = 1, 2, 4
 BT_OPT_VARIANT_ROW, BT_OPT_VARIANT_HALO, BT_OPT_VARIANT_SLICE, BT_OPT_SLICE_ONE_STAGE = 8, 16, 32, 64
+BT_OPT_SLICE_CONFIG_SHIFT = 8
+# Krylov variants of bt_get_tuning: row, halo, then the four slice configurations
+VARIANTS = ["row", "halo", "slice", "slice1", "slice_small", "slice_small1"]
+
+
+def slice_config_flag(c):
+    """Option flags forcing slice configuration c (0..3)."""
+    return (c + 1) << BT_OPT_SLICE_CONFIG_SHIFT
 PLANES = {"M": 0, "K": 1, "J": 2, "MD": 3, "Mx": 4, "My": 5, "Mz": 6, "Ex": 7, "Ey": 8, "Ez": 9, "A0": 10,
           "MR": 11}
 
@@ -34,7 +42,8 @@ EXPORTS = ["bt_create", "bt_destroy", "bt_set_stream", "bt_last_error", "bt_uplo
            "bt_precond_eval", "bt_save_precond", "bt_load_precond", "bt_precond_grad_noalloc",
            "bt_set_segments", "bt_get_tuning", "bt_get_state", "bt_get_halo_tiles", "bt_set_profile", "bt_set_relaxation", "bt_set_diffusion_tensor", "bt_set_weak_periodic", "bt_upload_mesh_2d",
            "bt_upload_mesh_1d", "bt_upload_mesh_surface", "bt_set_element_tensors", "bt_waveform_tables",
-           "bt_set_waveform", "bt_get_segment_stats"]
+           "bt_set_waveform", "bt_get_segment_stats", "bt_set_precond_poly", "bt_chebyshev_poly",
+           "bt_fit_chebyshev", "bt_get_precond_stats"]
 BT_NOALLOC_MAX_SAMPLES = 2048
 BT_PRECOND_NPARAM = 5 * 64 + 64 + 64 * 64 + 64 + 9 * 64 + 9
 BT_TRAIN_CONTINUE = 1
@@ -106,6 +115,10 @@ def lib():
             "bt_save_precond": [P, P],
             "bt_load_precond": [P, P],
             "bt_precond_grad_noalloc": [P, I32, P, P, P, P, P, P],
+            "bt_set_precond_poly": [P, P],
+            "bt_chebyshev_poly": [D, D, P],
+            "bt_fit_chebyshev": [I64, P, P, D, P, P, P, P],
+            "bt_get_precond_stats": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -437,6 +450,47 @@ def bt_load_precond(ctx, w):
     _check(ctx, lib().bt_load_precond(ctx, _ptr(w)))
 
 
+def bt_set_precond_poly(ctx, c9):
+    """Fixed polynomial coefficients for BT_MODE_LEARNED (None: back to the network)."""
+    if c9 is None:
+        _check(ctx, lib().bt_set_precond_poly(ctx, None))
+        return
+    c = np.ascontiguousarray(c9, dtype=np.float64)
+    assert c.shape == (9,)
+    _check(ctx, lib().bt_set_precond_poly(ctx, _ptr(c)))
+
+
+def bt_chebyshev_poly(lo, hi):
+    """Monomial coefficients c_0..c_8 of the degree-8 Chebyshev polynomial
+    preconditioner on [lo, hi] (library host code, no context)."""
+    c = np.zeros(9)
+    st = lib().bt_chebyshev_poly(float(lo), float(hi), _ptr(c))
+    if st != BT_OK:
+        raise BtError(st, "bt_chebyshev_poly: need 0 < lo < hi")
+    return c
+
+
+def bt_fit_chebyshev(G, h, rel_err=1e-6):
+    """(lo, hi, c9, mean loss) of the Chebyshev interval fitted to samples
+    whose G and h are known to relative accuracy rel_err."""
+    n = len(h)
+    Gc = np.ascontiguousarray(G, dtype=np.float64).reshape(n, 81)
+    hc = np.ascontiguousarray(h, dtype=np.float64).reshape(n, 9)
+    lo, hi, loss = C.c_double(), C.c_double(), C.c_double()
+    c = np.zeros(9)
+    st = lib().bt_fit_chebyshev(n, _ptr(Gc), _ptr(hc), float(rel_err), C.byref(lo), C.byref(hi), _ptr(c),
+                                C.byref(loss))
+    if st != BT_OK:
+        raise BtError(st, "bt_fit_chebyshev: bad samples")
+    return lo.value, hi.value, c, loss.value
+
+
+def bt_get_precond_stats(ctx):
+    n = C.c_int64()
+    _check(ctx, lib().bt_get_precond_stats(ctx, C.byref(n)))
+    return {"horner_launches": n.value}
+
+
 def bt_precond_grad_noalloc(w_ptr, n, feat_ptr, G_ptr, h_ptr, grad_ptr, loss_ptr, stream=0):
     """Device-pointer call of the allocation-free gradient (see include/bt.h);
     returns the status code."""
@@ -447,10 +501,11 @@ def bt_precond_grad_noalloc(w_ptr, n, feat_ptr, G_ptr, h_ptr, grad_ptr, loss_ptr
 
 def bt_get_tuning(ctx):
     v = C.c_int32()
-    d = (C.c_double * 4)()
+    d = (C.c_double * len(VARIANTS))()
     rv = C.c_int32()
     dr = (C.c_double * 2)()
     _check(ctx, lib().bt_get_tuning(ctx, C.byref(v), d, C.byref(rv), dr))
-    return {"variant": ["row", "halo", "slice", "slice1"][v.value], "ms_iter_row": d[0], "ms_iter_halo": d[1],
-            "ms_iter_slice": d[2], "ms_iter_slice1": d[3], "resid_variant": ["row", "halo"][rv.value],
-            "ms_resid_row": dr[0], "ms_resid_halo": dr[1]}
+    out = {"variant": VARIANTS[v.value]}
+    out.update({f"ms_iter_{name}": d[k] for k, name in enumerate(VARIANTS)})
+    out.update({"resid_variant": ["row", "halo"][rv.value], "ms_resid_row": dr[0], "ms_resid_halo": dr[1]})
+    return out

@@ -774,62 +774,70 @@ HaloArgs halo_args(const bt_ctx* ctx) {
                   ctx->halo_umax};
 }
 
-// Slice tiles (owned rows longest first, FP32 planes in tile-entry order) and
-// the plan of tile blocks for S slices of 32 systems: about one block per SM
-// in all (the blocks hold two stages of ~97 KB), split over the segments in
-// proportion to their tiles, at least one each.  Sets ctx->slice_ok = false
-// when a row does not fit a tile (the slice iteration is then not offered).
+// Slice tiles of each class (owned rows longest first, FP32 planes in
+// tile-entry order) and the plan of tile blocks of each configuration for S
+// slices of 32 systems: the configuration's resident blocks per SM times the
+// SMs in all, split over the segments in proportion to their tiles, at least
+// one each.  A class whose tiles a row does not fit (ok = false) is not
+// offered.
 bt_status ensure_slice(bt_ctx* ctx, int S, cudaStream_t st) {
   if (!ctx->slice_attr) {
     slice_prepare();
     CKL();
     ctx->slice_attr = true;
   }
-  if (ctx->slice_for != ctx->seg_row0) {
-    HaloTiles t;
-    ctx->slice_plan[0].S = ctx->slice_plan[1].S = 0;
-    build_halo_tiles(ctx->mesh, ctx->seg_row0, SL_UMAX, SL_TMAX, SL_EMAX, t, true);
-    ctx->slice_for = ctx->seg_row0;
-    ctx->slice_ok = !t.too_wide;
-    ctx->slice_planes_version = -1;
-    if (!ctx->slice_ok) return BT_OK;
-    CK(upload(ctx->s_r0, t.r0, st));
-    CK(upload(ctx->s_rows, t.rows, st));
-    CK(upload(ctx->s_rowe, t.rowe, st));
-    t.rowl.push_back(0);  // padding: the kernel copies local row indices in 4-byte words
-    t.rowl.push_back(0);
-    CK(upload(ctx->s_rowl, t.rowl, st));
-    CK(upload(ctx->s_u0, t.u0, st));
-    CK(upload(ctx->s_e0, t.e0, st));
-    CK(upload(ctx->s_ucol, t.ucol, st));
-    t.lidx.push_back(0);  // padding: the kernel copies local indices in 4-byte words
-    t.lidx.push_back(0);
-    CK(upload(ctx->s_lidx, t.lidx, st));
-    CK(upload(ctx->s_slot, t.slot, st));
-    CK(upload(ctx->s_seg0, t.seg_tile0, st));
-    ctx->slice_seg_tile0 = t.seg_tile0;
-    CK(cudaStreamSynchronize(st));
+  for (int cls = 0; cls < SLICE_NCLS; ++cls) {
+    auto& T = ctx->slice_t[cls];
+    int c0 = 0;
+    while (SLICE_CONF[c0].cls != cls) ++c0;
+    const SliceConf& sc = SLICE_CONF[c0];
+    if (T.made_for != ctx->seg_row0) {
+      HaloTiles t;
+      for (int c = 0; c < SLICE_NCONF; ++c)
+        if (SLICE_CONF[c].cls == cls) ctx->slice_plan[c].S = 0;
+      build_halo_tiles(ctx->mesh, ctx->seg_row0, sc.umax, sc.tmax, sc.emax, t, true);
+      T.made_for = ctx->seg_row0;
+      T.ok = !t.too_wide;
+      T.planes_version = -1;
+      if (!T.ok) continue;
+      CK(upload(T.r0, t.r0, st));
+      CK(upload(T.rows, t.rows, st));
+      CK(upload(T.rowe, t.rowe, st));
+      t.rowl.push_back(0);  // padding: the kernel copies local row indices in 4-byte words
+      t.rowl.push_back(0);
+      CK(upload(T.rowl, t.rowl, st));
+      CK(upload(T.u0, t.u0, st));
+      CK(upload(T.e0, t.e0, st));
+      CK(upload(T.ucol, t.ucol, st));
+      t.lidx.push_back(0);  // padding: the kernel copies local indices in 4-byte words
+      t.lidx.push_back(0);
+      CK(upload(T.lidx, t.lidx, st));
+      CK(upload(T.slot, t.slot, st));
+      CK(upload(T.seg0, t.seg_tile0, st));
+      T.seg_tile0 = t.seg_tile0;
+      CK(cudaStreamSynchronize(st));
+    }
+    if (!T.ok) continue;
+    if (T.planes_version != ctx->planes_version) {
+      CK(ensure(T.pkt, ctx->mesh.nnz));
+      CK(ensure(T.mdt, ctx->mesh.nnz));
+      launch_gather_tile_planes(T.slot.p, ctx->mesh.nnz, ctx->d_pk32.p, ctx->d_md32.p, T.pkt.p, T.mdt.p, st);
+      CKL();
+      T.planes_version = ctx->planes_version;
+    }
   }
-  if (!ctx->slice_ok) return BT_OK;
-  if (ctx->slice_planes_version != ctx->planes_version) {
-    CK(ensure(ctx->s_pkt, ctx->mesh.nnz));
-    CK(ensure(ctx->s_mdt, ctx->mesh.nnz));
-    launch_gather_tile_planes(ctx->s_slot.p, ctx->mesh.nnz, ctx->d_pk32.p, ctx->d_md32.p, ctx->s_pkt.p,
-                              ctx->s_mdt.p, st);
-    CKL();
-    ctx->slice_planes_version = ctx->planes_version;
-  }
-  for (int stages = 1; stages <= 2; ++stages) {
-    auto& pl = ctx->slice_plan[stages - 1];
-    if (pl.S == S) continue;
+  for (int c = 0; c < SLICE_NCONF; ++c) {
+    const auto& T = ctx->slice_t[SLICE_CONF[c].cls];
+    auto& pl = ctx->slice_plan[c];
+    if (!T.ok || pl.S == S) continue;
     const int G = ctx->G;
-    const auto& t0 = ctx->slice_seg_tile0;
-    const int64_t T = std::max<int64_t>(1, t0[G] - t0[0]);
-    const int target = std::max(1, ctx->sms * (3 - stages) / S);  // resident blocks: 3 - stages per SM
+    const auto& t0 = T.seg_tile0;
+    const int64_t nT = std::max<int64_t>(1, t0[G] - t0[0]);
+    const int target = std::max(1, ctx->sms * SLICE_CONF[c].blocks / S);  // resident blocks
     std::vector<int> blk_seg, blk0(G + 1, 0);
     for (int g = 0; g < G; ++g) {
       const int64_t Tg = t0[g + 1] - t0[g];
-      int64_t nbg = (int64_t)std::llround((double)target * Tg / (double)T);
+      int64_t nbg = (int64_t)std::llround((double)target * Tg / (double)nT);
       nbg = std::max<int64_t>(1, std::min<int64_t>(nbg, std::max<int64_t>(1, Tg)));
       blk0[g + 1] = blk0[g] + (int)nbg;
       for (int64_t k = 0; k < nbg; ++k) blk_seg.push_back(g);
@@ -843,20 +851,23 @@ bt_status ensure_slice(bt_ctx* ctx, int S, cudaStream_t st) {
   return BT_OK;
 }
 
-HaloArgs slice_args(const bt_ctx* ctx) {
-  return HaloArgs{ctx->s_r0.p,   ctx->s_rows.p, ctx->s_rowe.p, ctx->s_rowl.p, ctx->s_u0.p,  ctx->s_e0.p,
-                  ctx->s_ucol.p, ctx->s_lidx.p, ctx->s_pkt.p,  ctx->s_mdt.p,  nullptr,      ctx->s_seg0.p,
-                  SL_UMAX};
+// Krylov variants 2..5 are the slice-tiled iteration in configuration
+// variant - 2; whether that configuration's tiles exist
+int slice_cfg(int variant) { return variant - 2; }
+bool slice_cfg_ok(const bt_ctx* ctx, int cfg) { return ctx->slice_t[SLICE_CONF[cfg].cls].ok; }
+
+HaloArgs slice_args(const bt_ctx* ctx, int cfg) {
+  const auto& T = ctx->slice_t[SLICE_CONF[cfg].cls];
+  return HaloArgs{T.r0.p,   T.rows.p, T.rowe.p, T.rowl.p, T.u0.p,   T.e0.p,  T.ucol.p,
+                  T.lidx.p, T.pkt.p,  T.mdt.p,  nullptr,  T.seg0.p, SLICE_CONF[cfg].umax};
 }
 // the x/p update of the slice iteration keeps a counter of its own (it only
 // uses the last-block ticket)
 RedScratch rs_xp(const bt_ctx* ctx) { return RedScratch{ctx->red_part.p, ctx->red_counter.p + 10}; }
-SegPlan slice_plan(const bt_ctx* ctx, int stages) {
-  const auto& pl = ctx->slice_plan[stages - 1];
+SegPlan slice_plan(const bt_ctx* ctx, int cfg) {
+  const auto& pl = ctx->slice_plan[cfg];
   return SegPlan{pl.blk_seg.p, pl.blk0.p, ctx->d_row0.p, ctx->G, pl.nblk};
 }
-// Krylov variants 2 and 3 are the slice-tiled iteration with two and one stages
-int slice_stages(int variant) { return variant == 2 ? 2 : 1; }
 
 // Autotuner: time one Krylov iteration of each variant on the real pattern
 // and RHS count (CUDA events, 3 iterations after a warm-up) and keep the
@@ -872,9 +883,12 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
   for (auto& t : ctx->tuned)
     if (t.R == Rs && t.nb == nb && t.G == G) hit = &t;
   const bool halo = allow_halo && ctx->halo_ok;
-  const bool slice = allow_slice && ctx->slice_ok;
-  if (!hit || (halo && hit->ms[1] == 0) || (slice && (hit->ms[2] == 0 || hit->ms[3] == 0)) ||
-      (halo && df && hit->ms_resid[1] == 0)) {
+  bool slice_ok[SLICE_NCONF], slice_untimed = false;
+  for (int c = 0; c < SLICE_NCONF; ++c) {
+    slice_ok[c] = allow_slice && slice_cfg_ok(ctx, c);
+    if (slice_ok[c] && hit && hit->ms[2 + c] == 0) slice_untimed = true;
+  }
+  if (!hit || (halo && hit->ms[1] == 0) || slice_untimed || (halo && df && hit->ms_resid[1] == 0)) {
     cudaStream_t st = ctx->stream;
     const size_t NE = (size_t)op.n * op.Rp;
     std::vector<double> one(2 * (size_t)SY), small(2 * (size_t)SY), half(2 * (size_t)SY), big(SY, 1e300);
@@ -906,8 +920,8 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     };
     auto iter = [&](int v) {
       if (v >= 2) {
-        launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx, slice_stages(v)), ctx->p32.p, ctx->q32.p, ks, rs, conj,
-                          nb, slice_stages(v), st);
+        launch_spmm_slice(op, slice_args(ctx, slice_cfg(v)), slice_plan(ctx, slice_cfg(v)), ctx->p32.p, ctx->q32.p,
+                          ks, rs, conj, nb, slice_cfg(v), st);
         launch_slice_r(op, va, ctx->r32.p, ctx->q32.p, ks, rs2, conj, st);
         launch_slice_xp(op, va, ctx->x32.p, ctx->p32.p, ctx->r32.p, ks, rs_xp(ctx), st);
       } else if (v == 1) {
@@ -924,9 +938,9 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0, 0, 0}, {0, 0}};
-    for (int v = 0; v < 4; ++v) {
-      if ((v == 1 && !halo) || (v >= 2 && !slice)) continue;
+    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0, 0, 0, 0, 0}, {0, 0}};
+    for (int v = 0; v < 2 + SLICE_NCONF; ++v) {
+      if ((v == 1 && !halo) || (v >= 2 && !slice_ok[slice_cfg(v)])) continue;
       if (bt_status e = reset_vectors()) return e;
       if (bt_status e = prime()) return e;
       iter(v);  // warm-up
@@ -976,8 +990,8 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     hit = hit ? hit : &ctx->tuned.back();
   }
   int best = 0;
-  for (int v = 1; v < 4; ++v) {
-    const bool avail = v == 1 ? halo : slice;
+  for (int v = 1; v < 2 + SLICE_NCONF; ++v) {
+    const bool avail = v == 1 ? halo : slice_ok[slice_cfg(v)];
     if (avail && hit->ms[v] > 0 && hit->ms[v] < hit->ms[best]) best = v;
   }
   *variant = best;
@@ -995,6 +1009,7 @@ bt_status apply_poly(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const Kry
     launch_horner(op, va, bufs[w ^ 1], ctx->r32.p, bufs[w], ctx->d_coef9.p, j, ks.active, ctx->pmode.p,
                   ks.n_active, ctx->sms, st);
   }
+  ctx->st_horner += MLP_OUT;
   CKL();
   return BT_OK;
 }
@@ -1168,8 +1183,8 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
                              rs_at(2), g.conj, g.nb, c3);
             launch_krylov_update_z(opL, g.va, ctx->r32.p, ctx->q32.p, g.ks, rs_at(3), g.conj, c3);
           } else if (g.variant >= 2) {
-            launch_spmm_slice(opL, slice_args(ctx), slice_plan(ctx, slice_stages(g.variant)), ctx->p32.p, ctx->q32.p,
-                              g.ks, rs_at(2), g.conj, g.nb, slice_stages(g.variant), c3);
+            launch_spmm_slice(opL, slice_args(ctx, slice_cfg(g.variant)), slice_plan(ctx, slice_cfg(g.variant)),
+                              ctx->p32.p, ctx->q32.p, g.ks, rs_at(2), g.conj, g.nb, slice_cfg(g.variant), c3);
             launch_slice_r(opL, g.va, ctx->r32.p, ctx->q32.p, g.ks, rs_at(3), g.conj, c3);
             launch_slice_xp(opL, g.va, ctx->x32.p, ctx->p32.p, ctx->r32.p, g.ks, rs_xp(ctx), c3);
           } else {
@@ -1231,8 +1246,8 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     return fail(ctx, BT_ESTATE, "bt_run: need mesh, assembly, sequence and gradients");
   if (mode != BT_MODE_PLAIN_FP64 && mode != BT_MODE_MIXED && mode != BT_MODE_LEARNED)
     return fail(ctx, BT_EINVAL, "bt_run: unknown mode");
-  if (mode == BT_MODE_LEARNED && !ctx->have_precond)
-    return fail(ctx, BT_ESTATE, "bt_run: BT_MODE_LEARNED needs a trained or loaded preconditioner");
+  if (mode == BT_MODE_LEARNED && !ctx->have_precond && !ctx->have_fixed_poly)
+    return fail(ctx, BT_ESTATE, "bt_run: BT_MODE_LEARNED needs a trained, loaded or fixed preconditioner");
   const bool learned = mode == BT_MODE_LEARNED;
   bt_solver_opts o;
   bt_default_opts(&o);
@@ -1423,13 +1438,18 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       return e;
     if (o.flags & BT_OPT_VARIANT_ROW) variant = 0, resid_halo = false;
     if ((o.flags & BT_OPT_VARIANT_HALO) && allow_halo && ctx->halo_ok) variant = 1, resid_halo = df;
-    if ((o.flags & BT_OPT_VARIANT_SLICE) && allow_slice && ctx->slice_ok && variant < 2) {
-      // the faster of the two slice configurations
+    const int forced = (int)((o.flags >> BT_OPT_SLICE_CONFIG_SHIFT) & 7u) - 1;  // -1: none
+    if (allow_slice && (o.flags & BT_OPT_VARIANT_SLICE) && variant < 2) {
+      // the fastest slice configuration that was timed
       const auto& tu = ctx->tuned.back();
-      variant = ((o.flags & BT_OPT_SLICE_ONE_STAGE) || (tu.ms[3] > 0 && tu.ms[3] < tu.ms[2])) ? 3 : 2;
+      for (int c = 0; c < SLICE_NCONF; ++c)
+        if (slice_cfg_ok(ctx, c) && tu.ms[2 + c] > 0 && (variant < 2 || tu.ms[2 + c] < tu.ms[variant])) variant = 2 + c;
     }
+    if (allow_slice && (o.flags & BT_OPT_SLICE_ONE_STAGE) && slice_cfg_ok(ctx, 1)) variant = 3;
+    if (allow_slice && forced >= 0 && forced < SLICE_NCONF && slice_cfg_ok(ctx, forced)) variant = 2 + forced;
   }
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
+  ctx->st_horner = 0;
   ctx->st_spmm_ms = ctx->st_resid_ms = ctx->st_vec_ms = 0;
   ctx->ev_used = 0;
   CK(cudaMemsetAsync(ctx->rf_err.p, 0, SY * sizeof(double), st));
@@ -1472,13 +1492,26 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
   }
   double last_fq = NAN;
   size_t col_next = 0;
+  std::vector<double> fixed_coef;  // host copy of the fixed polynomial per system (alive during the run)
+  if (learned && ctx->have_fixed_poly) {
+    fixed_coef.resize(9 * (size_t)Rs);
+    for (int s = 0; s < Rs; ++s)
+      for (int j = 0; j < 9; ++j) fixed_coef[9 * (size_t)s + j] = ctx->fixed_poly[j];
+  }
   for (int step = 1; step <= N && !graph_done; ++step) {
     const OpCoef* c_r0 = ctx->d_coef.p + 2 * (size_t)(step - 1) * G;
     const OpCoef* c_L = c_r0 + G;
     // f_bar_n (lab) or F_n (transformed) of this step: the preconditioner feature
     const double fq = ctx->transformed ? ctx->F[step] : ctx->fbar[step - 1];
     const bool collect_now = col && col_next < col->steps.size() && col->steps[col_next] == step;
-    if (learned) {
+    if (learned && ctx->have_fixed_poly) {
+      if (step == 1) {  // one polynomial for every system, uploaded once per run
+        CK(cudaMemcpyAsync(ctx->d_coef9.p, fixed_coef.data(), fixed_coef.size() * sizeof(double),
+                           cudaMemcpyHostToDevice, st));
+      }
+      launch_set_int(ctx->pmode.p, 1, Rs, st);
+      L += 1;
+    } else if (learned) {
       if (!(fq == last_fq)) {
         launch_features(ctx->d_q.p, Rs, ctx->dt, fq, ctx->feat_D, ctx->feat_kappa, ctx->feat_h, ctx->d_feat.p, st);
         launch_mlp_forward(ctx->pw16.p, ctx->d_feat.p, Rs, ctx->d_coef9.p, st);
@@ -1567,8 +1600,8 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
           L -= 1;  // two launches per iteration
         } else if (variant >= 2) {
           timed(0, [&] {
-            launch_spmm_slice(op, slice_args(ctx), slice_plan(ctx, slice_stages(variant)), ctx->p32.p, ctx->q32.p, ks,
-                              rs_at(2), conj, nb, slice_stages(variant), st);
+            launch_spmm_slice(op, slice_args(ctx, slice_cfg(variant)), slice_plan(ctx, slice_cfg(variant)), ctx->p32.p,
+                              ctx->q32.p, ks, rs_at(2), conj, nb, slice_cfg(variant), st);
           });
           timed(2, [&] {
             launch_slice_r(op, va, ctx->r32.p, ctx->q32.p, ks, rs_at(3), conj, st);
@@ -1622,6 +1655,7 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
       L += 1;
     }
     ctx->st_steps++;
+    if (col && col_next == col->steps.size()) break;  // data collection ends after its last listed step
   }
   op.coef = ctx->d_coef.p;
   if (df) launch_signal_df(va, ctx->d_w.p, ctx->udf.p, ctx->d_S.p, rs_at(5), ctx->sms, st);
@@ -1731,7 +1765,7 @@ extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* 
   const auto& t = ctx->tuned.back();
   if (variant) *variant = t.variant;
   if (resid_variant) *resid_variant = t.resid_halo ? 1 : 0;
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 2 + SLICE_NCONF; ++k)
     if (ms_iter) ms_iter[k] = t.ms[k];
   for (int k = 0; k < 2; ++k)
     if (ms_resid) ms_resid[k] = t.ms_resid[k];

@@ -85,27 +85,29 @@ struct bt_ctx {
   bool halo_ok = false;             // every row fits a tile of umax halo rows
   int64_t halo_planes_version = -1;
   bool halo_attr = false;
-  // slice tiles of the slice-tiled iteration (owned rows longest first) and
-  // the plan of tile blocks (per segment, in proportion to its tiles)
-  bt::DBuf<int32_t> s_r0, s_rows, s_rowe, s_u0, s_e0, s_seg0, s_slot;
-  bt::DBuf<uint16_t> s_rowl, s_lidx;
-  bt::DBuf<uint32_t> s_ucol;
-  bt::DBuf<float4> s_pkt;
-  bt::DBuf<float> s_mdt;
-  std::vector<int64_t> slice_for;
-  std::vector<int32_t> slice_seg_tile0;
-  bool slice_ok = false;
-  int64_t slice_planes_version = -1;
+  // slice tiles of the slice-tiled iteration (owned rows longest first), one
+  // set per tile class (SLICE_CONF), and the plan of tile blocks per
+  // configuration (per segment, in proportion to its tiles)
+  struct SliceTiles {
+    bt::DBuf<int32_t> r0, rows, rowe, u0, e0, seg0, slot;
+    bt::DBuf<uint16_t> rowl, lidx;
+    bt::DBuf<uint32_t> ucol;
+    bt::DBuf<float4> pkt;
+    bt::DBuf<float> mdt;
+    std::vector<int64_t> made_for;  // segment row starts the tiles were built for
+    std::vector<int32_t> seg_tile0;
+    bool ok = false;                // every row fits a tile of this class
+    int64_t planes_version = -1;
+  } slice_t[2];
   bool slice_attr = false;
-  // plans of tile blocks for the two slice configurations (index stages - 1)
   struct SlicePlan {
     bt::DBuf<int32_t> blk_seg, blk0;
     int nblk = 0, S = 0;  // tile blocks of the uploaded plan, slices it was made for
-  } slice_plan[2];
+  } slice_plan[4];
   struct Tuned {
     int R, nb, G;
-    int variant;   // 0 row SpMM, 1 halo, 2 slice-tiled (two stages), 3 slice-tiled (one stage)
-    double ms[4];  // one Krylov iteration of each variant (ms; 0 = not timed)
+    int variant;   // 0 row SpMM, 1 halo, 2 + c the slice-tiled iteration in configuration c
+    double ms[6];  // one Krylov iteration of each variant (ms; 0 = not timed)
     double ms_resid[2];  // one correction residual launch: row, halo (0 = not timed)
     bool resid_halo = false;
   };
@@ -147,6 +149,9 @@ struct bt_ctx {
 
   // learned polynomial preconditioner
   bool have_precond = false;
+  bool have_fixed_poly = false;  // bt_set_precond_poly: one polynomial for every system and step
+  double fixed_poly[9] = {0};
+  int64_t st_horner = 0;  // Horner launches of the last run (the polynomial's SpMMs)
   bt::DBuf<float> pw32, pm, pv, d_feat;
   bt::DBuf<__nv_bfloat16> pw16;
   bt::DBuf<double> d_coef9;

@@ -78,11 +78,19 @@ void build_halo_tiles(const HostMesh& m, const std::vector<int64_t>& seg_row0, i
 constexpr int HALO_TMAX = 128;
 constexpr int HALO_EMAX = 448;
 constexpr int HALO_SMEM_BUDGET = 96 * 1024;
-// tile limits of the slice-tiled apply: halo rows (one 256-byte slice each in
-// shared memory), owned rows and entries per tile
-constexpr int SL_UMAX = 256;
-constexpr int SL_TMAX = 128;
-constexpr int SL_EMAX = 1536;
+// Configurations of the slice-tiled apply: the tile class (tile limits: halo
+// rows, one 256-byte slice each in shared memory; owned rows; entries), the
+// shared-memory stages of a block, its threads and the resident blocks per SM.
+// Configurations 0 and 1 use the large tiles (class 0), 2 and 3 the small
+// ones (class 1); the autotuner times all four.
+struct SliceConf {
+  int cls, umax, tmax, emax, stages, threads, blocks;
+};
+constexpr int SLICE_NCONF = 4, SLICE_NCLS = 2;
+constexpr SliceConf SLICE_CONF[SLICE_NCONF] = {{0, 256, 128, 1536, 2, 512, 1},
+                                               {0, 256, 128, 1536, 1, 256, 2},
+                                               {1, 128, 64, 1024, 2, 256, 2},
+                                               {1, 128, 64, 1024, 1, 256, 3}};
 
 // Weak pseudo-periodic coupling of the box faces (artificial permeability,
 // Appendix B): the boundary-face mass B on both sides of every selected axis

@@ -296,12 +296,12 @@ void launch_flush_x(const VecArgs& va, float2* x, const float2* pA, const float2
 // spt is the plan of tile blocks (each block of the SpMM launch is one tile
 // block times one slice of 32 systems); the vector width Rp must be a
 // multiple of 32 (and of 32 NB).
-// stages = 2: one block per SM with two pipelined shared-memory stages;
-// stages = 1: two blocks per SM with one stage each.
+// cfg: the configuration (SLICE_CONF: tile class, stages, threads, blocks per
+// SM); h must hold the tiles of that configuration's class.
 void slice_prepare();
-size_t slice_smem_bytes(int stages);
+size_t slice_smem_bytes(int cfg);
 void launch_spmm_slice(const OpArgs& op, const HaloArgs& h, const SegPlan& spt, const float2* p, float2* q,
-                       const KrylovState& ks, RedScratch rs, int conj, int nb, int stages, cudaStream_t st);
+                       const KrylovState& ks, RedScratch rs, int conj, int nb, int cfg, cudaStream_t st);
 void launch_slice_r(const OpArgs& op, const VecArgs& va, float2* r, const float2* q, const KrylovState& ks,
                     RedScratch rs, int conj, cudaStream_t st);
 void launch_slice_xp(const OpArgs& op, const VecArgs& va, float2* x, float2* p, const float2* r,
@@ -582,9 +582,10 @@ __device__ __forceinline__ bool krylov_step_finish(const KrylovState& ks, int s,
   }
   if (pmode && pmode[s]) {
     // polynomial-preconditioned system: rho and beta come from z = P_c r
-    // (k_precond_dot); fall back to Jacobi when it is not converged by
-    // max_iter / 2
-    if (it >= ks.max_iter / 2) {
+    // (k_precond_dot); fall back to Jacobi when it is not converged within
+    // 32 iterations (each costs nine SpMM-class launches; a useful
+    // polynomial needs a few) or max_iter / 2 if that is fewer
+    if (it >= min(ks.max_iter / 2, 32)) {
       ks.active[s] = 0;
       pmode[s] = 0;
       return false;

@@ -202,6 +202,25 @@ bt_status bt_load_precond(bt_ctx* ctx, const float* w) try {
   return BT_OK;
 } BT_ABI_CATCH(ctx)
 
+bt_status bt_set_precond_poly(bt_ctx* ctx, const double* c9) {
+  if (!ctx) return BT_EINVAL;
+  if (!c9) {
+    ctx->have_fixed_poly = false;
+    return BT_OK;
+  }
+  for (int j = 0; j < 9; ++j)
+    if (!std::isfinite(c9[j])) return fail(ctx, BT_EINVAL, "bt_set_precond_poly: non-finite coefficient");
+  std::copy(c9, c9 + 9, ctx->fixed_poly);
+  ctx->have_fixed_poly = true;
+  return BT_OK;
+}
+
+bt_status bt_get_precond_stats(const bt_ctx* ctx, int64_t* horner_launches) {
+  if (!ctx) return BT_EINVAL;
+  if (horner_launches) *horner_launches = ctx->st_horner;
+  return BT_OK;
+}
+
 // Train the network on n samples (raw features [n][5], G [n][81], h [n][9])
 // with minibatch Adam; loss_hist[epoch] receives the mean training loss.
 bt_status bt_train_precond(bt_ctx* ctx, int64_t n, const float* feat, const double* G, const double* h,

@@ -20,12 +20,15 @@
 // sorted longest first).  A block handles one slice of 32 systems of every
 // tile assigned to it: lanes per row LPR = 32 / NB, NB systems per lane (the NB
 // b-values of one direction, sharing the direction operator), NB rows per
-// warp.  For every tile the block stages, with cp.async into one of two
-// shared-memory stages (the next tile's copies overlap this tile's sums):
-//   - the slice of p at every halo row of the tile (32 complex = 256 B),
-//   - the tile's entries: FP32 planes {A0, d0, d1, d2}, MD, 16-bit local
-//     column indices, and the owned rows' ids, entry offsets and local indices.
-// Each staged value is read from shared memory once per nonzero that needs
+// warp.  For every tile the block stages into a shared-memory stage:
+//   - the tile's FP32 planes {A0, d0, d1, d2} (16 B per entry, contiguous per
+//     tile) by one TMA bulk copy counted on the stage's mbarrier,
+//   - with cp.async: the slice of p at every halo row of the tile (32 complex
+//     = 256 B), MD (transformed frame), the 16-bit local column indices, and
+//     the owned rows' ids, entry offsets and local indices.
+// Two configurations: two stages and 512 threads, one block per SM (the next
+// tile's copies overlap this tile's sums), or one stage and 256 threads, two
+// blocks per SM (the blocks overlap each other).  Each staged value is read from shared memory once per nonzero that needs
 // it, instead of once per nonzero from L2, and the own-row p of (p, q) comes
 // from the same stage.  Within a warp the NB row groups read their NB chunks
 // in rotated order (group g reads chunk (k + g) mod NB at step k), which keeps
@@ -36,17 +39,27 @@ namespace bt {
 
 namespace {
 
-constexpr int SL_THREADS = 256;
-// shared memory of one stage: halo rows (32 float2 each), then the entries
-constexpr size_t SL_HALO_BYTES = (size_t)SL_UMAX * 32 * sizeof(float2);
-constexpr size_t SL_PK_BYTES = (size_t)SL_EMAX * sizeof(float4);
-constexpr size_t SL_MD_BYTES = (size_t)SL_EMAX * sizeof(float);
-constexpr size_t SL_LI_BYTES = (((size_t)SL_EMAX + 8) * sizeof(uint16_t) + 15) / 16 * 16;
-// owned rows: ids, entry offsets (one more), local indices (16-bit, copied in 4-byte words)
-constexpr size_t SL_ROW_BYTES = (((size_t)SL_TMAX * 4 + ((size_t)SL_TMAX + 1) * 4 + ((size_t)SL_TMAX + 4) * 2) + 15) /
-                                16 * 16;
-constexpr size_t SL_STAGE_BYTES = SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES + SL_LI_BYTES + SL_ROW_BYTES;
-static_assert(SL_STAGE_BYTES % 16 == 0, "stage alignment");
+// shared memory of one stage of configuration c: halo rows (32 float2 each),
+// then the entries' planes, MD, local indices, and the owned rows' ids, entry
+// offsets (one more) and local indices (16-bit, copied in 4-byte words)
+struct StageLayout {
+  size_t halo, pk, md, li, row, total;
+};
+constexpr StageLayout stage_layout(int c) {
+  const size_t U = (size_t)SLICE_CONF[c].umax, T = (size_t)SLICE_CONF[c].tmax, E = (size_t)SLICE_CONF[c].emax;
+  const size_t halo = U * 32 * sizeof(float2), pk = E * sizeof(float4), md = E * sizeof(float),
+               li = ((E + 8) * sizeof(uint16_t) + 15) / 16 * 16, row = ((T * 4 + (T + 1) * 4 + (T + 4) * 2) + 15) / 16 * 16;
+  return StageLayout{halo, pk, md, li, row, halo + pk + md + li + row};
+}
+static_assert(stage_layout(0).total % 16 == 0 && stage_layout(2).total % 16 == 0, "stage alignment");
+// a configuration's blocks must fit one SM's shared memory (228 KB, 1 KB
+// reserved per block)
+constexpr bool fits_sm(int c) {
+  return (size_t)SLICE_CONF[c].blocks * ((size_t)SLICE_CONF[c].stages * stage_layout(c).total + 16 + 1024) <=
+             228 * 1024 &&
+         (size_t)SLICE_CONF[c].stages * stage_layout(c).total + 16 <= 227 * 1024;
+}
+static_assert(fits_sm(0) && fits_sm(1) && fits_sm(2) && fits_sm(3), "slice configuration exceeds shared memory");
 
 __device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
@@ -157,25 +170,30 @@ __device__ __forceinline__ void slice_flush(float2 (&a32)[NB][1], double2 (&a64)
 }  // namespace
 
 // the stages, then one mbarrier per stage
-size_t slice_smem_bytes(int stages) { return (size_t)stages * SL_STAGE_BYTES + 16; }
+size_t slice_smem_bytes(int c) { return (size_t)SLICE_CONF[c].stages * stage_layout(c).total + 16; }
 
 // ---------------------------------------------------------------- SpMM + (p, q)
-// STAGES = 2: one block per SM, the next tile's copies overlap this tile's
-// sums; STAGES = 1: two blocks per SM, each copying then summing (the two
-// blocks overlap each other).
-// threads per block of the two configurations
-__host__ __device__ constexpr int slice_threads(int stages) { return stages == 2 ? 2 * SL_THREADS : SL_THREADS; }
-
-template <int NB, bool TRANSF, bool CONJ, int STAGES>
-__global__ void __launch_bounds__(slice_threads(STAGES), 3 - STAGES)
+// Two stages: the next tile's copies overlap this tile's sums; one stage:
+// each block copies then sums, and the blocks resident on an SM overlap each
+// other.  CONJ = TRANSF: CG (conjugated forms) in the transformed frame,
+// COCG in the lab frame.
+template <int NB, bool TRANSF, int CFG>
+__global__ void __launch_bounds__(SLICE_CONF[CFG].threads, SLICE_CONF[CFG].blocks)
     k_spmm_slice(OpArgs op, HaloArgs h, SegPlan spt, int S, const float2* __restrict__ p, float2* __restrict__ q,
                  KrylovState ks, RedScratch rs) {
   if (*ks.n_active == 0) return;
+  constexpr bool CONJ = TRANSF;
+  constexpr int STAGES = SLICE_CONF[CFG].stages;
+  constexpr int SL_UMAX = SLICE_CONF[CFG].umax, SL_TMAX = SLICE_CONF[CFG].tmax;
+  constexpr StageLayout LY = stage_layout(CFG);
+  constexpr size_t SL_HALO_BYTES = LY.halo, SL_PK_BYTES = LY.pk, SL_MD_BYTES = LY.md, SL_LI_BYTES = LY.li,
+                   SL_STAGE_BYTES = LY.total;
   constexpr int LPR = 32 / NB;   // lanes per row
-  constexpr int NT = slice_threads(STAGES), NW = NT / 32;
+  constexpr int NT = SLICE_CONF[CFG].threads, NW = NT / 32;
   constexpr int SLOTS = NW * NB;  // rows in flight per block
   constexpr int PPC = 16 / NB;                     // 16-byte pieces per chunk of LPR complex values
   constexpr int HPT = SL_UMAX * 16 / NT;          // halo pieces per thread at most
+  static_assert(SL_UMAX * 16 % NT == 0, "halo pieces per thread");
   extern __shared__ float4 sl_smem_[];
   char* smem = reinterpret_cast<char*>(sl_smem_);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -243,7 +261,7 @@ __global__ void __launch_bounds__(slice_threads(STAGES), 3 - STAGES)
     int32_t* srowe = srow + SL_TMAX;
     uint32_t* srowl = reinterpret_cast<uint32_t*>(srowe + SL_TMAX + 1);
     const int nu = __ldg(h.u0 + tau + 1) - __ldg(h.u0 + tau);            // <= SL_UMAX (tile builder)
-    const int e0 = __ldg(h.e0 + tau), ne = __ldg(h.e0 + tau + 1) - e0;  // <= SL_EMAX
+    const int e0 = __ldg(h.e0 + tau), ne = __ldg(h.e0 + tau + 1) - e0;  // <= the emax of CFG
     const int R0 = __ldg(h.t_r0 + tau), nown = __ldg(h.t_r0 + tau + 1) - R0;  // <= SL_TMAX
     // the tile's planes: one bulk (TMA) copy of 16 ne contiguous bytes,
     // counted on the stage's mbarrier (issued by the thread that arms it)
@@ -811,48 +829,53 @@ __global__ void __launch_bounds__(256, 2) k_slice_init(OpArgs op, VecArgs va, co
 }
 
 // ---------------------------------------------------------------- launchers
-template <int NB, bool TRANSF, bool CONJ>
+template <int NB, bool TRANSF>
 static void slice_attr() {
-  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, CONJ, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)slice_smem_bytes(2));
-  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, CONJ, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)slice_smem_bytes(0));
+  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)slice_smem_bytes(1));
+  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)slice_smem_bytes(2));
+  cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)slice_smem_bytes(3));
 }
 void slice_prepare() {
-  slice_attr<4, false, false>(); slice_attr<4, false, true>(); slice_attr<4, true, false>(); slice_attr<4, true, true>();
-  slice_attr<2, false, false>(); slice_attr<2, false, true>(); slice_attr<2, true, false>(); slice_attr<2, true, true>();
-  slice_attr<1, false, false>(); slice_attr<1, false, true>(); slice_attr<1, true, false>(); slice_attr<1, true, true>();
+  slice_attr<4, false>();
+  slice_attr<4, true>();
+  slice_attr<2, false>();
+  slice_attr<2, true>();
+  slice_attr<1, false>();
+  slice_attr<1, true>();
 }
 
+// conj must equal op.transformed (CG in the transformed frame, COCG in the
+// lab frame), as everywhere in the library
 void launch_spmm_slice(const OpArgs& op, const HaloArgs& h, const SegPlan& spt, const float2* p, float2* q,
-                       const KrylovState& ks, RedScratch rs, int conj, int nb, int stages, cudaStream_t st) {
+                       const KrylovState& ks, RedScratch rs, int conj, int nb, int cfg, cudaStream_t st) {
+  (void)conj;
   const int S = op.Rp / 32;
   const dim3 grid(spt.nblk * S);
-  const size_t sm = slice_smem_bytes(stages);
-#define BT_SL_CASE(NBV, STG)                                                                               \
-  {                                                                                                        \
-    constexpr int NT_ = slice_threads(STG);                                                                \
-    if (op.transformed) {                                                                                  \
-      if (conj) k_spmm_slice<NBV, true, true, STG><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);     \
-      else k_spmm_slice<NBV, true, false, STG><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);         \
-    } else {                                                                                               \
-      if (conj) k_spmm_slice<NBV, false, true, STG><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);    \
-      else k_spmm_slice<NBV, false, false, STG><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);        \
-    }                                                                                                      \
+  const size_t sm = slice_smem_bytes(cfg);
+#define BT_SL_CASE(NBV, CFGV)                                                                          \
+  {                                                                                                    \
+    constexpr int NT_ = SLICE_CONF[CFGV].threads;                                                      \
+    if (op.transformed) k_spmm_slice<NBV, true, CFGV><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs); \
+    else k_spmm_slice<NBV, false, CFGV><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);            \
   }
-  if (stages == 2) {
-    switch (nb) {
-      case 4: BT_SL_CASE(4, 2) break;
-      case 2: BT_SL_CASE(2, 2) break;
-      default: BT_SL_CASE(1, 2) break;
-    }
-  } else {
-    switch (nb) {
-      case 4: BT_SL_CASE(4, 1) break;
-      case 2: BT_SL_CASE(2, 1) break;
-      default: BT_SL_CASE(1, 1) break;
-    }
+#define BT_SL_NB(CFGV)                  \
+  switch (nb) {                         \
+    case 4: BT_SL_CASE(4, CFGV) break;  \
+    case 2: BT_SL_CASE(2, CFGV) break;  \
+    default: BT_SL_CASE(1, CFGV) break; \
   }
+  switch (cfg) {
+    case 0: BT_SL_NB(0) break;
+    case 1: BT_SL_NB(1) break;
+    case 2: BT_SL_NB(2) break;
+    default: BT_SL_NB(3) break;
+  }
+#undef BT_SL_NB
 #undef BT_SL_CASE
 }
 

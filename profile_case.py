@@ -30,7 +30,7 @@ def main():
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--steps", type=int, default=2, help="time steps (pulse on throughout)")
     ap.add_argument("--mode", default="mixed", choices=["mixed", "plain"])
-    ap.add_argument("--variant", default="auto", choices=["auto", "row", "halo", "slice", "slice1"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "row", "halo", "slice", "slice1", "slice_small", "slice_small1"],
                     help="inner Krylov variant (auto: the autotuner's choice)")
     a = ap.parse_args()
     build()
@@ -53,11 +53,10 @@ def main():
         seg["delta"][:], seg["Delta"][:], seg["TE"][:] = p.delta, p.Delta, p.TE
     sim = Simulation(p)
     mode = bt.BT_MODE_MIXED if a.mode == "mixed" else bt.BT_MODE_PLAIN_FP64
-    flags = bt.BT_OPT_NO_GRAPH | bt.BT_OPT_PROFILE | {"auto": 0, "row": bt.BT_OPT_VARIANT_ROW,
-                                                      "halo": bt.BT_OPT_VARIANT_HALO,
-                                                      "slice": bt.BT_OPT_VARIANT_SLICE,
-                                                      "slice1": bt.BT_OPT_VARIANT_SLICE | bt.BT_OPT_SLICE_ONE_STAGE
-                                                      }[a.variant]
+    forced = {"auto": 0, "row": bt.BT_OPT_VARIANT_ROW, "halo": bt.BT_OPT_VARIANT_HALO}
+    for c, name in enumerate(bt.VARIANTS[2:]):  # the slice configurations
+        forced[name] = bt.slice_config_flag(c)
+    flags = bt.BT_OPT_NO_GRAPH | bt.BT_OPT_PROFILE | forced[a.variant]
     S, err, stat, _ = sim.run(mode, flags=flags)
     tuning = bt.bt_get_tuning(sim.ctx) if mode != bt.BT_MODE_PLAIN_FP64 else None
     st = sim.stats()

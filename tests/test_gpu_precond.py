@@ -134,6 +134,58 @@ def test_learned_mode_matches_oracle(trained, bt):
     assert it_l < it_j   # the trained polynomial needs fewer (but costlier) iterations
 
 
+def test_fixed_chebyshev_matches_oracle(trained, bt):
+    """The fixed Chebyshev polynomial, its interval fitted to the same samples,
+    runs through the same Horner kernels: fewer Krylov iterations than Jacobi,
+    8 + 1 Horner launches per polynomial application, signals within 1e-6 of
+    the FP64 oracle; with the fixed polynomial cleared the network runs again."""
+    p, sim, feat, G, h, _ = trained
+    lo, hi, c, loss = bt.bt_fit_chebyshev(G, h)
+    e0 = np.eye(9)[0]
+    Ljac = np.mean(1 - 2 * h @ e0 + np.einsum("i,sij,j->s", e0, G, e0))
+    assert 0 < lo < hi and loss < Ljac
+    sim.run(bt.BT_MODE_MIXED)
+    it_j = sim.stats()["krylov_iters"]
+    bt.bt_set_precond_poly(sim.ctx, c)
+    try:
+        S_c, _, st_c, _ = sim.run(bt.BT_MODE_LEARNED)
+        it_c = sim.stats()["krylov_iters"]
+        hor = bt.bt_get_precond_stats(sim.ctx)["horner_launches"]
+    finally:
+        bt.bt_set_precond_poly(sim.ctx, None)
+    assert np.all(st_c == 0) and it_c < it_j
+    assert hor > 0 and hor % 9 == 0
+    rhs = [0, 7, 13, 22, 31]
+    ref = np.asarray(oracle.run(p, rhs=rhs))
+    e = np.abs(S_c[rhs] - ref) / np.abs(ref)
+    print(f"Chebyshev on [{lo:.3g}, {hi:.3g}], mean loss {loss:.3g} (Jacobi {Ljac:.3g}); "
+          f"Krylov iterations {it_c} vs Jacobi {it_j}; max rel err vs oracle {e.max():.2e}")
+    assert e.max() < 1e-6, e
+    sim.run(bt.BT_MODE_LEARNED)
+    assert bt.bt_get_precond_stats(sim.ctx)["horner_launches"] > 0
+
+
+def test_fixed_polynomial_needs_no_network(sim_cls, bt):
+    """A context without a network runs BT_MODE_LEARNED on a fixed polynomial
+    and matches the oracle; NULL coefficients bring back the refusal."""
+    p = geom.cfg1(n=4)
+    sim = sim_cls(p)
+    try:
+        bt.bt_set_precond_poly(sim.ctx, bt.bt_chebyshev_poly(0.05, 2.5))
+        S, _, st, _ = sim.run(bt.BT_MODE_LEARNED)
+        assert np.all(st == 0)
+        ref = np.asarray(oracle.run(p))
+        assert np.max(np.abs(S - ref) / np.abs(ref)) < 1e-6
+        with pytest.raises(bt.BtError):
+            bt.bt_set_precond_poly(sim.ctx, np.full(9, np.nan))
+        bt.bt_set_precond_poly(sim.ctx, None)
+        with pytest.raises(bt.BtError) as e:
+            sim.run(bt.BT_MODE_LEARNED)
+        assert e.value.code == bt.BT_ESTATE
+    finally:
+        sim.close()
+
+
 def test_learned_mode_golden_signals(trained, sim_cls, bt):
     """The trained network, loaded into a context of the 24^3 packing, runs the
     stored oracle case of that geometry in LEARNED mode (per signal 1e-6)."""

@@ -3,9 +3,9 @@ slice of p staged in shared memory, then an r update with the inner products
 and an x/p update) against the FP64 oracle, for
 every vector layout it serves (1, 2 and 4 right-hand sides per lane), both
 frames (COCG in the lab frame, CG in the transformed frame), both drivers
-(captured step graph, host loop), both configurations (two pipelined
-shared-memory stages with one block per SM; one stage with two blocks per SM)
-and an uneven batch.  Bound: mixed mode,
+(captured step graph, host loop), all four configurations (tiles of 256 or
+128 halo rows; two pipelined shared-memory stages or one; one, two or three
+blocks per SM) and an uneven batch.  Bound: mixed mode,
 1e-6 relative per signal, and every dof of every field at 1e-6 of its
 largest value."""
 import numpy as np
@@ -67,12 +67,10 @@ def field():
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("loop", ["graph", "host"])
-@pytest.mark.parametrize("stages", [2, 1])
-def test_slice_variant_matches_oracle(sim_cls, bt, field, name, loop, stages):
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+def test_slice_variant_matches_oracle(sim_cls, bt, field, name, loop, cfg):
     p, ref, U = field(name)
-    flags = bt.BT_OPT_VARIANT_SLICE | (bt.BT_OPT_NO_GRAPH if loop == "host" else 0)
-    if stages == 1:
-        flags |= bt.BT_OPT_SLICE_ONE_STAGE
+    flags = bt.slice_config_flag(cfg) | (bt.BT_OPT_NO_GRAPH if loop == "host" else 0)
     sim = sim_cls(p)
     try:
         S, err, stat, _ = sim.run(bt.BT_MODE_MIXED, flags=flags)
@@ -85,7 +83,8 @@ def test_slice_variant_matches_oracle(sim_cls, bt, field, name, loop, stages):
         st = sim.stats()
         assert st["krylov_iters"] > 0 and 0 < st["sys_iters"] <= st["spmm_launches"] * p.n_rhs
         tu = bt.bt_get_tuning(sim.ctx)
-        assert tu["ms_iter_slice"] > 0
+        assert tu["variant"] == bt.VARIANTS[2 + cfg]
+        assert all(tu[f"ms_iter_{v}"] > 0 for v in bt.VARIANTS[2:])
     finally:
         sim.close()
 
@@ -134,7 +133,8 @@ def test_slice_flag_falls_back_when_the_width_does_not_fit(sim_cls, bt):
         S, err, stat, _ = sim.run(bt.BT_MODE_MIXED, flags=bt.BT_OPT_VARIANT_SLICE)
         assert np.all(stat == 0)
         assert np.abs(S - ref).max() / np.abs(ref).max() < TOL_MIXED
-        assert bt.bt_get_tuning(sim.ctx)["variant"] not in ("slice", "slice1")
-        assert bt.bt_get_tuning(sim.ctx)["ms_iter_slice"] == 0
+        tu = bt.bt_get_tuning(sim.ctx)
+        assert tu["variant"] not in bt.VARIANTS[2:]
+        assert all(tu[f"ms_iter_{v}"] == 0 for v in bt.VARIANTS[2:])
     finally:
         sim.close()
