@@ -364,9 +364,11 @@ bt_status bt_get_signals(bt_ctx* ctx, double* S_re_im, double* err_est, int32_t*
  * call that changes the mesh, assembly, sequence, segments or gradients
  * discards it), BT_EINVAL for a system outside the last run. */
 bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_rows);
-/* The Krylov autotuner's last choice, made at the first FP32 run of a given
- * RHS count, RHS-per-lane and segmentation by timing one inner iteration of
- * each variant on the real pattern:
+/* The Krylov variant and residual kernel of the last FP32 run (the
+ * autotuner's choice unless an option flag forced another) and the
+ * autotuner's timings, made at the first FP32 run of a given RHS count,
+ * RHS-per-lane and segmentation by timing one inner iteration of each
+ * variant on the real pattern:
  *   0  row SpMM (one warp per row, X gathered per nonzero) + vector updates
  *   1  halo-staged apply (Morton-ordered row tiles, their halo rows of X staged
  *      in shared memory, search-direction and solution updates fused in) +
@@ -433,6 +435,13 @@ typedef struct bt_train_opts {
   double lr;        /* Adam step (default 2e-3; betas 0.9, 0.999)       */
   uint64_t seed;    /* initialisation and shuffling (default 1)         */
   uint32_t flags;   /* BT_TRAIN_CONTINUE: start from the current weights */
+  double rel_err;   /* relative accuracy of G and h (default 1e-6, the FP32
+                       Krylov vectors of bt_collect_precond_data): the
+                       objective adds the loss's spread
+                       rel_err (2 |c|.|h| + |c|.|G| |c|) per sample; 0 = the
+                       plain loss.  The Krylov basis is nearly dependent, so
+                       without it the network can fit the data's rounding
+                       (a small training loss that no solve sees). */
 } bt_train_opts;
 bt_status bt_train_default_opts(bt_train_opts* o);
 /* Geometry features of the assembled mesh: volume-weighted mean D,
@@ -449,16 +458,18 @@ bt_status bt_precond_features(const bt_ctx* ctx, double* D, double* kappa, doubl
 bt_status bt_collect_precond_data(bt_ctx* ctx, const bt_solver_opts* opts, int32_t n_steps, const int32_t* steps,
                                   float* feat, double* G, double* h);
 /* Train on n samples (feat [n][5], G [n][81], h [n][9]) with minibatch Adam on
- * the mean loss |r - L P_c r|^2/|r|^2 = 1 - 2 c.h + c.G c; loss_hist[epoch]
- * (may be NULL) receives the mean training loss of each epoch.  The network
+ * the mean loss |r - L P_c r|^2/|r|^2 = 1 - 2 c.h + c.G c plus rel_err times
+ * its spread (bt_train_opts); loss_hist[epoch] (may be NULL) receives the
+ * mean training objective of each epoch.  The network
  * stays in the context for BT_MODE_LEARNED. */
 bt_status bt_train_precond(bt_ctx* ctx, int64_t n, const float* feat, const double* G, const double* h,
                            const bt_train_opts* opts, double* loss_hist);
-/* Coefficients [n][9], mean loss and its gradient [BT_PRECOND_NPARAM] of the
- * current network on n samples (any output may be NULL; G, h needed for loss
- * and gradient). */
+/* Coefficients [n][9], mean objective and its gradient [BT_PRECOND_NPARAM]
+ * of the current network on n samples (any output may be NULL; G, h needed
+ * for loss and gradient): the mean loss plus rel_err times its spread, as in
+ * training (rel_err = 0: the plain loss; BT_EINVAL outside [0, 1)). */
 bt_status bt_precond_eval(bt_ctx* ctx, int64_t n, const float* feat, const double* G, const double* h,
-                          double* coef, double* loss, double* grad);
+                          double rel_err, double* coef, double* loss, double* grad);
 /* Copy the FP32 master weights out / in (BT_PRECOND_NPARAM floats). */
 bt_status bt_save_precond(const bt_ctx* ctx, float* w);
 bt_status bt_load_precond(bt_ctx* ctx, const float* w);
@@ -505,8 +516,9 @@ bt_status bt_fit_chebyshev(int64_t n, const double* G, const double* h, double r
 bt_status bt_get_precond_stats(const bt_ctx* ctx, int64_t* horner_launches);
 
 /* ---------------------------------------------------------------- allocation-free gradient
- * bt_precond_grad_noalloc computes what bt_precond_eval computes for the loss
- * and gradient of the preconditioner network, for callers that cannot
+ * bt_precond_grad_noalloc computes what bt_precond_eval computes, with
+ * rel_err = 0, for the loss and gradient of the preconditioner network, for
+ * callers that cannot
  * allocate device memory: code under a framework that owns every device
  * allocation (a caching allocator or a fixed budget that cudaMalloc would
  * bypass), or a service that forbids allocation after start-up because

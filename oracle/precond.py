@@ -65,15 +65,23 @@ def forward(w, x, bf16=True):
     return c, (x, z1, a1, z2, a2)
 
 
-def loss_and_grad(w, x, G, h, bf16=True):
+def loss_and_grad(w, x, G, h, bf16=True, rel_err=0.0):
     """Mean loss over samples and its gradient with respect to the flat
-    parameters (through the bf16-rounded weights, straight-through)."""
+    parameters (through the bf16-rounded weights, straight-through).  With
+    rel_err > 0 each sample's loss carries its spread for data known to that
+    relative accuracy, rel_err (2 |c|.|h| + |c|.|G| |c|): G and h come from
+    nearly dependent FP32 Krylov vectors, and a coefficient vector whose loss
+    is below that spread is not resolved by the data."""
     W1, b1, W2, b2, W3, b3 = unpack(bf16_round(w) if bf16 else w)
     c, (x, z1, a1, z2, a2) = forward(w, x, bf16)
     n = len(x)
     Gc = np.einsum("sij,sj->si", G, c)
     L = 1.0 - 2.0 * np.sum(c * h, axis=1) + np.sum(c * Gc, axis=1)
     dc = 2.0 * (Gc - h) / n
+    if rel_err > 0:
+        ac, aGc = np.abs(c), np.einsum("sij,sj->si", np.abs(G), np.abs(c))
+        L = L + rel_err * (2.0 * np.sum(ac * np.abs(h), axis=1) + np.sum(ac * aGc, axis=1))
+        dc = dc + 2.0 * rel_err * np.sign(c) * (np.abs(h) + aGc) / n
     gW3 = dc.T @ a2
     gb3 = dc.sum(0)
     d2 = (dc @ W3) * (z2 > 0)

@@ -63,7 +63,7 @@ class bt_solver_opts(C.Structure):
 
 class bt_train_opts(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
-                ("flags", C.c_uint32)]
+                ("flags", C.c_uint32), ("rel_err", C.c_double)]
 
 
 _lib = None
@@ -111,7 +111,7 @@ def lib():
             "bt_precond_features": [P, P, P, P],
             "bt_collect_precond_data": [P, C.POINTER(bt_solver_opts), I32, P, P, P, P],
             "bt_train_precond": [P, I64, P, P, P, C.POINTER(bt_train_opts), P],
-            "bt_precond_eval": [P, I64, P, P, P, P, P, P],
+            "bt_precond_eval": [P, I64, P, P, P, D, P, P, P],
             "bt_save_precond": [P, P],
             "bt_load_precond": [P, P],
             "bt_precond_grad_noalloc": [P, I32, P, P, P, P, P, P],
@@ -423,18 +423,19 @@ def bt_train_precond(ctx, feat, G, h, opts=None):
     return hist
 
 
-def bt_precond_eval(ctx, feat, G=None, h=None):
+def bt_precond_eval(ctx, feat, G=None, h=None, rel_err=0.0):
     feat = np.ascontiguousarray(feat, dtype=np.float32)
     n = len(feat)
     coef = np.zeros((n, 9), np.float64)
     loss = np.zeros(1, np.float64)
     grad = np.zeros(BT_PRECOND_NPARAM, np.float64)
     if G is None:
-        _check(ctx, lib().bt_precond_eval(ctx, n, _ptr(feat), None, None, _ptr(coef), None, None))
+        _check(ctx, lib().bt_precond_eval(ctx, n, _ptr(feat), None, None, 0.0, _ptr(coef), None, None))
         return coef, None, None
     Gc = np.ascontiguousarray(G, dtype=np.float64).reshape(n, 81)
     hc = np.ascontiguousarray(h, dtype=np.float64).reshape(n, 9)
-    _check(ctx, lib().bt_precond_eval(ctx, n, _ptr(feat), _ptr(Gc), _ptr(hc), _ptr(coef), _ptr(loss), _ptr(grad)))
+    _check(ctx, lib().bt_precond_eval(ctx, n, _ptr(feat), _ptr(Gc), _ptr(hc), float(rel_err), _ptr(coef),
+                                      _ptr(loss), _ptr(grad)))
     return coef, float(loss[0]), grad
 
 

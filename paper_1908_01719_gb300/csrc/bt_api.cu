@@ -1447,6 +1447,8 @@ static bt_status run_impl(bt_ctx* ctx, int mode, const bt_solver_opts* opts_in, 
     }
     if (allow_slice && (o.flags & BT_OPT_SLICE_ONE_STAGE) && slice_cfg_ok(ctx, 1)) variant = 3;
     if (allow_slice && forced >= 0 && forced < SLICE_NCONF && slice_cfg_ok(ctx, forced)) variant = 2 + forced;
+    ctx->last_variant = variant;
+    ctx->last_resid_halo = resid_halo ? 1 : 0;
   }
   ctx->st_steps = ctx->st_iters = ctx->st_refine = ctx->st_spmm = ctx->st_resid = ctx->st_launches = 0;
   ctx->st_horner = 0;
@@ -1763,8 +1765,8 @@ extern "C" bt_status bt_get_tuning(const bt_ctx* ctx, int32_t* variant, double* 
   if (!ctx) return BT_EINVAL;
   if (ctx->tuned.empty()) return BT_ESTATE;
   const auto& t = ctx->tuned.back();
-  if (variant) *variant = t.variant;
-  if (resid_variant) *resid_variant = t.resid_halo ? 1 : 0;
+  if (variant) *variant = ctx->last_variant >= 0 ? ctx->last_variant : t.variant;
+  if (resid_variant) *resid_variant = ctx->last_variant >= 0 ? ctx->last_resid_halo : (t.resid_halo ? 1 : 0);
   for (int k = 0; k < 2 + SLICE_NCONF; ++k)
     if (ms_iter) ms_iter[k] = t.ms[k];
   for (int k = 0; k < 2; ++k)

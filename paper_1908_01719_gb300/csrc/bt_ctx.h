@@ -112,6 +112,7 @@ struct bt_ctx {
     bool resid_halo = false;
   };
   std::vector<Tuned> tuned;
+  int last_variant = -1, last_resid_halo = 0;  // what the last FP32 run used (flags may override the tuning)
 
   // gradients
   int n_dir = 0, n_b = 0, R = 0;

@@ -200,6 +200,9 @@ struct MlpTrainArgs {
   double* grad_out;
   int apply, t;
   float lr, beta1, beta2, eps;
+  // > 0: the objective adds the loss's spread for data known to this
+  // relative accuracy, rel_err (2 |c|.|h| + |c|.|G| |c|) per sample
+  float rel_err;
 };
 void launch_mlp_forward(const __nv_bfloat16* w, const float* feat, int S, double* coef, cudaStream_t st);
 void launch_mlp_train(const MlpTrainArgs& a, cudaStream_t st);

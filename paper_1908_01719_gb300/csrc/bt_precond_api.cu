@@ -174,6 +174,7 @@ bt_status bt_train_default_opts(bt_train_opts* o) {
   o->lr = 2e-3;
   o->seed = 1;
   o->flags = 0;
+  o->rel_err = 1e-6;
   return BT_OK;
 }
 
@@ -230,7 +231,8 @@ bt_status bt_train_precond(bt_ctx* ctx, int64_t n, const float* feat, const doub
   bt_train_opts o;
   bt_train_default_opts(&o);
   if (opts) o = *opts;
-  if (n < 1 || !feat || !G || !h || o.epochs < 1 || o.batch < 1 || !(o.lr > 0))
+  if (n < 1 || !feat || !G || !h || o.epochs < 1 || o.batch < 1 || !(o.lr > 0) || !(o.rel_err >= 0) ||
+      !(o.rel_err < 1))
     return fail(ctx, BT_EINVAL, "bt_train_precond: bad arguments");
   const int B = (int)std::min<int64_t>(o.batch, n);
   CK(cudaSetDevice(ctx->device));
@@ -315,6 +317,7 @@ bt_status bt_train_precond(bt_ctx* ctx, int64_t n, const float* feat, const doub
       a.beta1 = 0.9f;
       a.beta2 = 0.999f;
       a.eps = 1e-8f;
+      a.rel_err = (float)o.rel_err;
       launch_mlp_train(a, st);
       CKL();
     }
@@ -333,8 +336,9 @@ bt_status bt_train_precond(bt_ctx* ctx, int64_t n, const float* feat, const doub
 // and its gradient with respect to the parameters [MLP_NPARAM] (through the
 // bfloat16 weights).  Any output pointer may be NULL.
 bt_status bt_precond_eval(bt_ctx* ctx, int64_t n, const float* feat, const double* G, const double* h,
-                          double* coef, double* loss, double* grad) try {
-  if (!ctx || n < 1 || !feat) return fail(ctx, BT_EINVAL, "bt_precond_eval: bad arguments");
+                          double rel_err, double* coef, double* loss, double* grad) try {
+  if (!ctx || n < 1 || !feat || !(rel_err >= 0) || !(rel_err < 1))
+    return fail(ctx, BT_EINVAL, "bt_precond_eval: bad arguments");
   if (ctx->host_only) return fail(ctx, BT_ENODEV, "bt_precond_eval: host-only context");
   if (!ctx->have_precond) return fail(ctx, BT_ESTATE, "bt_precond_eval: no network");
   if ((loss || grad) && (!G || !h)) return fail(ctx, BT_EINVAL, "bt_precond_eval: loss needs G and h");
@@ -393,6 +397,7 @@ bt_status bt_precond_eval(bt_ctx* ctx, int64_t n, const float* feat, const doubl
     a.loss = dl.p;
     a.grad_out = dg.p;
     a.apply = 0;
+    a.rel_err = (float)rel_err;
     launch_mlp_train(a, st);
     CKL();
     std::vector<float> lv(n);

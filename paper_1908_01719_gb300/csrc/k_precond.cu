@@ -10,7 +10,10 @@
 // applied by Horner: z_8 = c_8 D^-1 r, z_j = D^-1 (c_j r + L z_{j+1}).
 // Training data of one RHS r: v_0 = D^-1 r, v_{j+1} = D^-1 L v_j,
 // y_j = L v_j = D v_{j+1}; G = Re(Y^H Y)/|r|^2, h = Re(Y^H r)/|r|^2, and the
-// per-sample loss |r - L P_c r|^2/|r|^2 = 1 - 2 c.h + c.G c.
+// per-sample loss |r - L P_c r|^2/|r|^2 = 1 - 2 c.h + c.G c; training adds
+// its spread e (2 |c|.|h| + |c|.|G| |c|) for data known to relative accuracy
+// e (the Krylov basis is nearly dependent and G, h come from FP32 vectors, so
+// without it the network can fit rounding instead of the operator).
 #include <cuda_bf16.h>
 
 #include "bt_kernels.cuh"
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(256) k_mlp_train_fwd(const __nv_bfloat16* __re
                                                        float* __restrict__ sx, float* __restrict__ sa1,
                                                        float* __restrict__ sa2, float* __restrict__ sd1,
                                                        float* __restrict__ sd2, float* __restrict__ sdc,
-                                                       float* __restrict__ loss) {
+                                                       float* __restrict__ loss, float rel_err) {
   __shared__ float sa[8][4][MLP_H];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = blockIdx.x * 8 + warp;
@@ -105,18 +108,29 @@ __global__ void __launch_bounds__(256) k_mlp_train_fwd(const __nv_bfloat16* __re
   float* a2 = sa[warp][1];
   float* d2s = sa[warp][2];
   MlpAct a = mlp_warp(w, x, a1, a2);
-  // dL/dc = 2 (G c - h) / B, L = 1 - 2 c.h + c.G c
+  // dL/dc = 2 (G c - h) / B, L = 1 - 2 c.h + c.G c; with rel_err > 0 the
+  // objective adds e (2 |c|.|h| + |c|.|G| |c|) (G symmetric), whose
+  // derivative is 2 e sgn(c) (|h| + |G| |c|)
   const float* Gs = G + (size_t)81 * s;
   const float* hs = h + (size_t)9 * s;
-  float gc = 0.f, dc = 0.f, lterm = 0.f;
+  float gc = 0.f, agc = 0.f, dc = 0.f, lterm = 0.f;
 #pragma unroll
   for (int p = 0; p < MLP_OUT; ++p) {
     const float cp = __shfl_sync(0xffffffffu, a.c, p);
-    if (lane < MLP_OUT) gc = fmaf(Gs[lane * 9 + p], cp, gc);
+    if (lane < MLP_OUT) {
+      gc = fmaf(Gs[lane * 9 + p], cp, gc);
+      agc = fmaf(fabsf(Gs[lane * 9 + p]), fabsf(cp), agc);
+    }
   }
   if (lane < MLP_OUT) {
     dc = 2.f * (gc - hs[lane]) / (float)B;
     lterm = a.c * gc - 2.f * a.c * hs[lane];
+    if (rel_err > 0.f) {
+      const float ac = fabsf(a.c), ah = fabsf(hs[lane]);
+      const float sg = (float)((a.c > 0.f) - (a.c < 0.f));
+      lterm = fmaf(rel_err, fmaf(2.f * ac, ah, ac * agc), lterm);
+      dc = fmaf(2.f * rel_err * sg, (ah + agc) / (float)B, dc);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) lterm += __shfl_xor_sync(0xffffffffu, lterm, o);
@@ -200,7 +214,7 @@ void launch_mlp_forward(const __nv_bfloat16* w, const float* feat, int S, double
 }
 void launch_mlp_train(const MlpTrainArgs& a, cudaStream_t st) {
   k_mlp_train_fwd<<<(a.B + 7) / 8, 256, 0, st>>>(a.w16, a.feat, a.G, a.h, a.idx, a.B, a.sx, a.sa1, a.sa2, a.sd1,
-                                                 a.sd2, a.sdc, a.loss);
+                                                 a.sd2, a.sdc, a.loss, a.rel_err);
   k_mlp_train_grad<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(a.w32, a.w16, a.m, a.v, a.B, a.sx, a.sa1, a.sa2,
                                                              a.sd1, a.sd2, a.sdc, a.grad_out, a.apply, a.t, a.lr,
                                                              a.beta1, a.beta2, a.eps);

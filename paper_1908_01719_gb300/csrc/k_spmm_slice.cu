@@ -40,16 +40,17 @@ namespace bt {
 namespace {
 
 // shared memory of one stage of configuration c: halo rows (32 float2 each),
-// then the entries' planes, MD, local indices, and the owned rows' ids, entry
-// offsets (one more) and local indices (16-bit, copied in 4-byte words)
+// then the entries' planes, MD, local indices, the owned rows' ids, entry
+// offsets (one more), local indices (16-bit, copied in 4-byte words), and a
+// 16-byte header with the tile's first entry, first owned row and owned rows
 struct StageLayout {
-  size_t halo, pk, md, li, row, total;
+  size_t halo, pk, md, li, row, hdr, total;
 };
 constexpr StageLayout stage_layout(int c) {
   const size_t U = (size_t)SLICE_CONF[c].umax, T = (size_t)SLICE_CONF[c].tmax, E = (size_t)SLICE_CONF[c].emax;
   const size_t halo = U * 32 * sizeof(float2), pk = E * sizeof(float4), md = E * sizeof(float),
                li = ((E + 8) * sizeof(uint16_t) + 15) / 16 * 16, row = ((T * 4 + (T + 1) * 4 + (T + 4) * 2) + 15) / 16 * 16;
-  return StageLayout{halo, pk, md, li, row, halo + pk + md + li + row};
+  return StageLayout{halo, pk, md, li, row, 16, halo + pk + md + li + row + 16};
 }
 static_assert(stage_layout(0).total % 16 == 0 && stage_layout(2).total % 16 == 0, "stage alignment");
 // a configuration's blocks must fit one SM's shared memory (228 KB, 1 KB
@@ -241,14 +242,30 @@ __global__ void __launch_bounds__(SLICE_CONF[CFG].threads, SLICE_CONF[CFG].block
   unsigned phase = 0u;
   // halo row ids of the 16-byte pieces this thread copies for tile tau
   // (loaded one tile ahead of their copies, so their latency overlaps the
-  // sums); piece tid & 15 of halo rows (tid >> 4) + (NT / 16) j
+  // sums); piece tid & 15 of halo rows (tid >> 4) + (NT / 16) j.  The tile's
+  // extents come with them (m_*), and the halo range of the tile after it is
+  // fetched at the same time (pre_*), so no load here waits on another.
   uint32_t rid[HPT];
-  auto load_rid = [&](int tau) {
-    const int u0 = __ldg(h.u0 + tau), nu = __ldg(h.u0 + tau + 1) - u0;
+  int pre_u0 = 0, pre_nu = 0, m_nu = 0, m_e0 = 0, m_ne = 0, m_R0 = 0, m_nown = 0;
+  auto load_rid = [&](int tau, bool first) {
+    if (first) {
+      pre_u0 = __ldg(h.u0 + tau);
+      pre_nu = __ldg(h.u0 + tau + 1) - pre_u0;
+    }
+    const int u0 = pre_u0, nu = pre_nu;
 #pragma unroll
     for (int j = 0; j < HPT; ++j) {
       const int u = (tid >> 4) + (NT / 16) * j;
       rid[j] = u < nu ? (__ldg(h.ucol + u0 + u) & 0x7FFFFFFFu) : 0xFFFFFFFFu;
+    }
+    m_nu = nu;
+    m_e0 = __ldg(h.e0 + tau);
+    m_ne = __ldg(h.e0 + tau + 1) - m_e0;
+    m_R0 = __ldg(h.t_r0 + tau);
+    m_nown = __ldg(h.t_r0 + tau + 1) - m_R0;
+    if (tau + snb < T1) {
+      pre_u0 = __ldg(h.u0 + tau + snb);
+      pre_nu = __ldg(h.u0 + tau + snb + 1) - pre_u0;
     }
   };
   auto issue = [&](int tau, int st) {
@@ -260,9 +277,10 @@ __global__ void __launch_bounds__(SLICE_CONF[CFG].threads, SLICE_CONF[CFG].block
     int32_t* srow = reinterpret_cast<int32_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES + SL_LI_BYTES);
     int32_t* srowe = srow + SL_TMAX;
     uint32_t* srowl = reinterpret_cast<uint32_t*>(srowe + SL_TMAX + 1);
-    const int nu = __ldg(h.u0 + tau + 1) - __ldg(h.u0 + tau);            // <= SL_UMAX (tile builder)
-    const int e0 = __ldg(h.e0 + tau), ne = __ldg(h.e0 + tau + 1) - e0;  // <= the emax of CFG
-    const int R0 = __ldg(h.t_r0 + tau), nown = __ldg(h.t_r0 + tau + 1) - R0;  // <= SL_TMAX
+    // extents of tile tau, from load_rid(tau): nu <= SL_UMAX, ne <= the emax
+    // of CFG, nown <= SL_TMAX (tile builder)
+    const int nu = m_nu, e0 = m_e0, ne = m_ne, R0 = m_R0, nown = m_nown;
+    if (tid == 0) *reinterpret_cast<int4*>(b0 + SL_STAGE_BYTES - 16) = make_int4(e0, R0, nown, ne);
     // the tile's planes: one bulk (TMA) copy of 16 ne contiguous bytes,
     // counted on the stage's mbarrier (issued by the thread that arms it)
     uint64_t* bar = bars + st;
@@ -303,23 +321,23 @@ __global__ void __launch_bounds__(SLICE_CONF[CFG].threads, SLICE_CONF[CFG].block
   __syncthreads();
   if (__syncthreads_or(any)) {
     int tau = T0 + sk;
-    if (tau < T1) load_rid(tau);
+    if (tau < T1) load_rid(tau, true);
     if constexpr (STAGES == 2) {
       if (tau < T1) issue(tau, 0);
       cpa_commit();
-      if (tau + snb < T1) load_rid(tau + snb);
+      if (tau + snb < T1) load_rid(tau + snb, false);
     }
     for (int it = 0; tau < T1; tau += snb, ++it) {
       const int st = STAGES == 2 ? (it & 1) : 0;
       if constexpr (STAGES == 2) {
         if (tau + snb < T1) issue(tau + snb, st ^ 1);
         cpa_commit();
-        if (tau + 2 * snb < T1) load_rid(tau + 2 * snb);
+        if (tau + 2 * snb < T1) load_rid(tau + 2 * snb, false);
         cpa_wait<1>();  // this thread's copies of tile tau have landed
       } else {
         issue(tau, 0);
         cpa_commit();
-        if (tau + snb < T1) load_rid(tau + snb);
+        if (tau + snb < T1) load_rid(tau + snb, false);
         cpa_wait<0>();
       }
       // the stage's bulk copies (bounded wait; a timeout ends the block's work)
@@ -338,13 +356,14 @@ __global__ void __launch_bounds__(SLICE_CONF[CFG].threads, SLICE_CONF[CFG].block
       const float2* sh = reinterpret_cast<const float2*>(b0);
       const float4* spk = reinterpret_cast<const float4*>(b0 + SL_HALO_BYTES);
       const float* smd = reinterpret_cast<const float*>(b0 + SL_HALO_BYTES + SL_PK_BYTES);
-      const int e0 = __ldg(h.e0 + tau);
+      const int4 hdr = *reinterpret_cast<const int4*>(b0 + SL_STAGE_BYTES - 16);  // written by issue()
+      const int e0 = hdr.x;
       const uint16_t* sli =
           reinterpret_cast<const uint16_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES) + (e0 & 1);
       const int32_t* srow =
           reinterpret_cast<const int32_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES + SL_LI_BYTES);
       const int32_t* srowe = srow + SL_TMAX;
-      const int R0 = __ldg(h.t_r0 + tau), nown = __ldg(h.t_r0 + tau + 1) - R0;
+      const int R0 = hdr.y, nown = hdr.z;
       const uint16_t* srowl = reinterpret_cast<const uint16_t*>(srowe + SL_TMAX + 1) + (R0 & 1);
       const float2* xs = sh + lp;
       for (int k = warp * NB + g; k < nown; k += SLOTS) {

@@ -110,7 +110,7 @@ def run_modes(sim, bt, weights, cheb, modes=("jacobi_row", "jacobi_tuned", "lear
                   "spmm_total": st["spmm_launches"] + hor, "sys_iters": st["sys_iters"],
                   "kernel_launches": st["kernel_launches"], "status_ok": bool(np.all(stat == 0)),
                   "err_est_max": float(np.max(err))}
-        sig[m] = S
+        sig[m] = np.array(S, copy=True)
         if m == "chebyshev":
             bt.bt_set_precond_poly(sim.ctx, None)
     if ref is None:
@@ -170,7 +170,8 @@ def main():
     s0 = Simulation(p0)
     t0 = time.perf_counter()
     hist = bt.bt_train_precond(s0.ctx, feat[train], G[train], h[train],
-                               bt.bt_train_default_opts(epochs=a.epochs, batch=a.batch, seed=a.seed))
+                               bt.bt_train_default_opts(epochs=a.epochs, batch=a.batch, seed=a.seed,
+                                                        rel_err=REL_ERR))
     t_train = time.perf_counter() - t0
     w = bt.bt_save_precond(s0.ctx)
     coef_tr, loss_tr, _ = bt.bt_precond_eval(s0.ctx, feat[train], G[train], h[train])

@@ -53,13 +53,14 @@ def test_forward_and_gradient_match_cpu_reference(sim_cls, bt):
         bt.bt_load_precond(sim.ctx, w)
         assert np.array_equal(bt.bt_save_precond(sim.ctx), w)
         feat, G, h = _samples(64, 4)
-        coef, loss, grad = bt.bt_precond_eval(sim.ctx, feat, G, h)
         x = pc.normalise(feat.astype(np.float64))
         c_ref, _ = pc.forward(w.astype(np.float64), x, bf16=True)
-        L_ref, g_ref, _ = pc.loss_and_grad(w.astype(np.float64), x, G, h, bf16=True)
-        assert np.abs(coef - c_ref).max() <= 1e-4 * np.abs(c_ref).max()
-        assert abs(loss - L_ref) <= 1e-4 * abs(L_ref)
-        assert np.linalg.norm(grad - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
+        for rel_err in (0.0, 1e-3):  # the plain loss, and the loss with its data spread
+            coef, loss, grad = bt.bt_precond_eval(sim.ctx, feat, G, h, rel_err=rel_err)
+            L_ref, g_ref, _ = pc.loss_and_grad(w.astype(np.float64), x, G, h, bf16=True, rel_err=rel_err)
+            assert np.abs(coef - c_ref).max() <= 1e-4 * np.abs(c_ref).max()
+            assert abs(loss - L_ref) <= 1e-4 * abs(L_ref)
+            assert np.linalg.norm(grad - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
     finally:
         sim.close()
 

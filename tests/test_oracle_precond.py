@@ -38,7 +38,10 @@ def test_loss_identity_brute_force():
     assert abs(jac - (1 - 2 * e0 @ h + e0 @ G @ e0)) < 1e-12
 
 
-def test_gradient_matches_finite_differences():
+@pytest.mark.parametrize("rel_err", [0.0, 1e-3])
+def test_gradient_matches_finite_differences(rel_err):
+    """The objective's gradient (the plain loss, and the loss with its spread
+    for data of relative accuracy rel_err) against central differences."""
     rng = np.random.default_rng(2)
     w = rng.normal(size=pc.N_PARAM) * 0.2
     ns = 7
@@ -50,15 +53,27 @@ def test_gradient_matches_finite_differences():
         G.append(g_)
         h.append(h_)
     G, h = np.array(G), np.array(h)
-    L, g, _ = pc.loss_and_grad(w, x, G, h, bf16=False)
+    L, g, _ = pc.loss_and_grad(w, x, G, h, bf16=False, rel_err=rel_err)
     idx = rng.choice(pc.N_PARAM, 60, replace=False)
     eps = 1e-6
     for i in idx:
         wp, wm = w.copy(), w.copy()
         wp[i] += eps
         wm[i] -= eps
-        fd = (pc.loss_and_grad(wp, x, G, h, bf16=False)[0] - pc.loss_and_grad(wm, x, G, h, bf16=False)[0]) / (2 * eps)
+        fd = (pc.loss_and_grad(wp, x, G, h, bf16=False, rel_err=rel_err)[0] -
+              pc.loss_and_grad(wm, x, G, h, bf16=False, rel_err=rel_err)[0]) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+    if rel_err:
+        # the added term, summed element by element
+        c = pc.forward(w, x, bf16=False)[0]
+        extra = 0.0
+        for s_ in range(ns):
+            for i in range(9):
+                extra += 2 * abs(c[s_, i]) * abs(h[s_, i])
+                for j in range(9):
+                    extra += abs(c[s_, i]) * abs(G[s_, i, j]) * abs(c[s_, j])
+        L0 = pc.loss_and_grad(w, x, G, h, bf16=False)[0]
+        assert abs(L - L0 - rel_err * extra / ns) <= 1e-12 * max(1.0, abs(L))
 
 
 def test_optimal_coefficients_minimise_loss():
