@@ -297,6 +297,9 @@ KERNEL = {"row": "k_spmm_krylov", "halo": "k_spmm_halo",
 # profiles/k_spmm_krylov_cfg4_grid64.md.  The row kernel reads every column
 # whatever the number of active systems, so the figure scales with the dofs.
 ROW_SPMM_TRAFFIC = {"n_dof": 343793, "bytes": 791.9e6 + 329.7e6}
+# the same for the slice SpMM (large tiles, one stage, two blocks per SM),
+# captured on a launch with all 128 systems active
+SLICE1_SPMM_TRAFFIC = {"n_dof": 343793, "bytes": 482.844672e6 + 314.620416e6, "active": 128}
 
 
 def spmm_bytes(n, nnz, transformed, launches, seg_iters, seg_rows, vectors):
@@ -477,6 +480,20 @@ def run_ours(args):
         else:
             learned = {"unavailable": "no trained weights in the package (precond_study.py --out)"}
 
+    # DRAM traffic per launch from one ncu capture of the 64^3 case of the same
+    # geometry, scaled to this grid by the dof ratio; for the slice kernel the
+    # capture had every system active, so it is set beside the algorithmic
+    # bytes at that activity
+    traffic, traffic_note = None, "no capture of this kernel on this workload"
+    if args.config == "cfg4" and tuning["variant"] == "row":
+        traffic = ROW_SPMM_TRAFFIC["bytes"] * n / ROW_SPMM_TRAFFIC["n_dof"]
+        traffic_note = "ncu DRAM bytes per launch of the 64^3 case scaled by the dof ratio"
+    elif args.config == "cfg4" and tuning["variant"] == "slice1":
+        traffic = SLICE1_SPMM_TRAFFIC["bytes"] * n / SLICE1_SPMM_TRAFFIC["n_dof"]
+        full = spmm_bytes(n, nnz, p.transformed, 1, [SLICE1_SPMM_TRAFFIC["active"]], [n], 2)
+        traffic_note = (f"ncu DRAM bytes of one 64^3 launch with all {SLICE1_SPMM_TRAFFIC['active']} systems "
+                        f"active, scaled by the dof ratio; algorithmic bytes at that activity {full:.4g}")
+
     # end to end through the public API from host buffers
     torch.cuda.synchronize(dev)
     t0 = time.time()
@@ -518,11 +535,8 @@ def run_ours(args):
                          + " (fused FP32 complex SpMM of the Krylov iteration, the autotuned variant)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src, "frac_of_nominal_7900_gbs": achieved / 7900.0,
-                         "traffic": (ROW_SPMM_TRAFFIC["bytes"] * n / ROW_SPMM_TRAFFIC["n_dof"]
-                                     if tuning["variant"] == "row" and args.config == "cfg4"
-                                     else None),
-                         "traffic_note": "ncu DRAM bytes per launch of the 64^3 case scaled by the dof "
-                                         "ratio (the row kernel reads all columns)",
+                         "traffic": traffic,
+                         "traffic_note": traffic_note,
                          "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms,
                          "active_rhs_per_launch": sys_iters / max(1, spmm_launch),
                          "launches": spmm_launch},
