@@ -279,16 +279,18 @@ def run_reference(args):
 # launch of the dominant kernel: the row SpMM reads X and writes Y; the
 # halo-staged apply reads z, p_prev and x and writes x, p and q; the
 # slice-tiled SpMM reads p and writes q
-VECTORS_PER_SYSTEM = {"row": 2, "halo": 6, "slice": 2, "slice1": 2, "slice_small": 2, "slice_small1": 2}
+VECTORS_PER_SYSTEM = {"row": 2, "halo": 6, "slice": 2, "slice1": 2, "slice_small": 2, "slice_small1": 2, "slice_ws": 2}
 # ... and per Krylov iteration (all launches of one iteration): row 2 + 6 + 3,
 # halo 6 + 3 (z update: reads z, q, writes z), slice 2 + 3 (r, q read, r
 # written) + 5 (x, p, r read, x, p written)
-VECTORS_PER_ITER = {"row": 11, "halo": 9, "slice": 10, "slice1": 10, "slice_small": 10, "slice_small1": 10}
+VECTORS_PER_ITER = {"row": 11, "halo": 9, "slice": 10, "slice1": 10, "slice_small": 10, "slice_small1": 10,
+                    "slice_ws": 10}
 KERNEL = {"row": "k_spmm_krylov", "halo": "k_spmm_halo",
           "slice": "k_spmm_slice (256-halo-row tiles, two stages, one block per SM)",
           "slice1": "k_spmm_slice (256-halo-row tiles, one stage, two blocks per SM)",
           "slice_small": "k_spmm_slice (128-halo-row tiles, two stages, two blocks per SM)",
-          "slice_small1": "k_spmm_slice (128-halo-row tiles, one stage, three blocks per SM)"}
+          "slice_small1": "k_spmm_slice (128-halo-row tiles, one stage, three blocks per SM)",
+          "slice_ws": "k_spmm_slice_ws (256-halo-row tiles, two stages filled by a copy warp, 15 summing warps)"}
 
 
 # DRAM bytes (read + write) of one launch of the row SpMM k_spmm_krylov<4>, lab

@@ -316,9 +316,9 @@ enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
  * (bt_get_tuning; _HALO falls back to the tuned choice where the halo tiles
  * are not available); BT_OPT_VARIANT_SLICE bypasses the autotuner's Krylov
  * choice for the slice-tiled iteration, the fastest of its configurations
- * (bt_get_tuning variants 2..5); BT_OPT_SLICE_ONE_STAGE forces configuration
+ * (bt_get_tuning variants 2..6); BT_OPT_SLICE_ONE_STAGE forces configuration
  * 1 (variant 3), and (c + 1) << BT_OPT_SLICE_CONFIG_SHIFT forces
- * configuration c in 0..3 (variant 2 + c).  The residual kernel is still
+ * configuration c in 0..4 (variant 2 + c).  The residual kernel is still
  * tuned, and the slice flags fall back to the tuned choice when the padded
  * RHS width is not a multiple of 32 or a row does not fit the
  * configuration's tiles. */
@@ -383,7 +383,11 @@ bt_status bt_get_state(bt_ctx* ctx, int32_t system, double* u_re_im, int64_t* n_
  *   4  configuration 2: tiles of at most 128 halo rows, 64 owned rows and
  *      1,024 entries, two stages, two blocks of 256 per SM
  *   5  configuration 3: the small tiles, one stage, three blocks of 256 per SM
- * ms_iter [6] (may be NULL) receives the measured ms per iteration of each
+ *   6  configuration 4: the large tiles, two stages filled by one copy warp
+ *      (cp.async halo rows, TMA planes, per-stage full/empty mbarriers), 15
+ *      summing warps that take rows of a filled stage as they come; one
+ *      block of 512 per SM
+ * ms_iter [7] (may be NULL) receives the measured ms per iteration of each
  * (0 = not timed or not offered).  The double-float correction residual is tuned on its own:
  * resid_variant 0 = row kernel, 1 = halo-staged kernel (the step-start
  * residual follows it), ms_resid [2] the measured ms per launch of each.

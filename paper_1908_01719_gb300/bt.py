@@ -25,11 +25,11 @@ BT_OPT_RESID_FP64, BT_OPT_PROFILE, BT_OPT_NO_GRAPH = 1, 2, 4
 BT_OPT_VARIANT_ROW, BT_OPT_VARIANT_HALO, BT_OPT_VARIANT_SLICE, BT_OPT_SLICE_ONE_STAGE = 8, 16, 32, 64
 BT_OPT_SLICE_CONFIG_SHIFT = 8
 # Krylov variants of bt_get_tuning: row, halo, then the four slice configurations
-VARIANTS = ["row", "halo", "slice", "slice1", "slice_small", "slice_small1"]
+VARIANTS = ["row", "halo", "slice", "slice1", "slice_small", "slice_small1", "slice_ws"]
 
 
 def slice_config_flag(c):
-    """Option flags forcing slice configuration c (0..3)."""
+    """Option flags forcing slice configuration c (0..4)."""
     return (c + 1) << BT_OPT_SLICE_CONFIG_SHIFT
 PLANES = {"M": 0, "K": 1, "J": 2, "MD": 3, "Mx": 4, "My": 5, "Mz": 6, "Ex": 7, "Ey": 8, "Ez": 9, "A0": 10,
           "MR": 11}

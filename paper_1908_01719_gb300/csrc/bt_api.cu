@@ -938,7 +938,7 @@ bt_status autotune_spmm(bt_ctx* ctx, const OpArgs& op, const VecArgs& va, const 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    bt_ctx::Tuned tu{Rs, nb, G, 0, {0, 0, 0, 0, 0, 0}, {0, 0}};
+    bt_ctx::Tuned tu{Rs, nb, G, 0, {}, {0, 0}};
     for (int v = 0; v < 2 + SLICE_NCONF; ++v) {
       if ((v == 1 && !halo) || (v >= 2 && !slice_ok[slice_cfg(v)])) continue;
       if (bt_status e = reset_vectors()) return e;

@@ -103,11 +103,11 @@ struct bt_ctx {
   struct SlicePlan {
     bt::DBuf<int32_t> blk_seg, blk0;
     int nblk = 0, S = 0;  // tile blocks of the uploaded plan, slices it was made for
-  } slice_plan[4];
+  } slice_plan[bt::SLICE_NCONF];
   struct Tuned {
     int R, nb, G;
     int variant;   // 0 row SpMM, 1 halo, 2 + c the slice-tiled iteration in configuration c
-    double ms[6];  // one Krylov iteration of each variant (ms; 0 = not timed)
+    double ms[2 + bt::SLICE_NCONF];  // one Krylov iteration of each variant (ms; 0 = not timed)
     double ms_resid[2];  // one correction residual launch: row, halo (0 = not timed)
     bool resid_halo = false;
   };

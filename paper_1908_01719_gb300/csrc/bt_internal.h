@@ -80,17 +80,21 @@ constexpr int HALO_EMAX = 448;
 constexpr int HALO_SMEM_BUDGET = 96 * 1024;
 // Configurations of the slice-tiled apply: the tile class (tile limits: halo
 // rows, one 256-byte slice each in shared memory; owned rows; entries), the
-// shared-memory stages of a block, its threads and the resident blocks per SM.
-// Configurations 0 and 1 use the large tiles (class 0), 2 and 3 the small
-// ones (class 1); the autotuner times all four.
+// shared-memory stages of a block, its threads, the resident blocks per SM,
+// and whether one warp of the block only copies (ws = 1: a producer warp fills
+// the stages, the other warps take rows of the filled stages as they come,
+// with per-stage mbarriers instead of block-wide barriers).  Configurations
+// 0, 1 and 4 use the large tiles (class 0), 2 and 3 the small ones (class 1);
+// the autotuner times all five.
 struct SliceConf {
-  int cls, umax, tmax, emax, stages, threads, blocks;
+  int cls, umax, tmax, emax, stages, threads, blocks, ws;
 };
-constexpr int SLICE_NCONF = 4, SLICE_NCLS = 2;
-constexpr SliceConf SLICE_CONF[SLICE_NCONF] = {{0, 256, 128, 1536, 2, 512, 1},
-                                               {0, 256, 128, 1536, 1, 256, 2},
-                                               {1, 128, 64, 1024, 2, 256, 2},
-                                               {1, 128, 64, 1024, 1, 256, 3}};
+constexpr int SLICE_NCONF = 5, SLICE_NCLS = 2;
+constexpr SliceConf SLICE_CONF[SLICE_NCONF] = {{0, 256, 128, 1536, 2, 512, 1, 0},
+                                               {0, 256, 128, 1536, 1, 256, 2, 0},
+                                               {1, 128, 64, 1024, 2, 256, 2, 0},
+                                               {1, 128, 64, 1024, 1, 256, 3, 0},
+                                               {0, 256, 128, 1536, 2, 512, 1, 1}};
 
 // Weak pseudo-periodic coupling of the box faces (artificial permeability,
 // Appendix B): the boundary-face mass B on both sides of every selected axis

@@ -55,12 +55,14 @@ constexpr StageLayout stage_layout(int c) {
 static_assert(stage_layout(0).total % 16 == 0 && stage_layout(2).total % 16 == 0, "stage alignment");
 // a configuration's blocks must fit one SM's shared memory (228 KB, 1 KB
 // reserved per block)
+// (the stages are followed by 64 bytes of mbarriers and counters)
 constexpr bool fits_sm(int c) {
-  return (size_t)SLICE_CONF[c].blocks * ((size_t)SLICE_CONF[c].stages * stage_layout(c).total + 16 + 1024) <=
+  return (size_t)SLICE_CONF[c].blocks * ((size_t)SLICE_CONF[c].stages * stage_layout(c).total + 64 + 1024) <=
              228 * 1024 &&
-         (size_t)SLICE_CONF[c].stages * stage_layout(c).total + 16 <= 227 * 1024;
+         (size_t)SLICE_CONF[c].stages * stage_layout(c).total + 64 <= 227 * 1024;
 }
-static_assert(fits_sm(0) && fits_sm(1) && fits_sm(2) && fits_sm(3), "slice configuration exceeds shared memory");
+static_assert(fits_sm(0) && fits_sm(1) && fits_sm(2) && fits_sm(3) && fits_sm(4),
+              "slice configuration exceeds shared memory");
 
 __device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
@@ -92,6 +94,15 @@ __device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, unsigned 
                    smem_u32(sdst)),
                "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+// one arrival on an mbarrier (release semantics at CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// an arrival on the mbarrier made when every cp.async this thread issued so far
+// has landed (the arrival is counted in the barrier's initial count)
+__device__ __forceinline__ void cpa_mbar_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 // generic-proxy accesses of this thread before async-proxy writes to the same shared memory
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -170,8 +181,97 @@ __device__ __forceinline__ void slice_flush(float2 (&a32)[NB][1], double2 (&a64)
 
 }  // namespace
 
-// the stages, then one mbarrier per stage
-size_t slice_smem_bytes(int c) { return (size_t)SLICE_CONF[c].stages * stage_layout(c).total + 16; }
+// One owned row of a staged tile: q_row = L_row p for the lane's NB systems
+// (entries ea..eb of the stage, p from the staged halo rows xs), stored for the
+// active systems, and (p_row, q_row) added to the lane's FP32 partials.
+template <int NB, bool TRANSF>
+__device__ __forceinline__ void slice_row(const float4* spk, const uint16_t* sli, const float* smd, const float2* xs,
+                                          int row, int ea, int eb, int lo, const OpArgs& op, float2* __restrict__ q,
+                                          float qx, float qy, float qz, float ca, const float (&cb)[NB],
+                                          const float (&cc)[NB], const int (&off)[NB], const int (&colk)[NB],
+                                          const bool (&act)[NB], float2 (&a32)[NB][1]) {
+  constexpr bool CONJ = TRANSF;
+  float2 P[NB], Q[NB];
+#pragma unroll
+  for (int kk = 0; kk < NB; ++kk) P[kk] = Q[kk] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int e = ea; e < eb; ++e) {
+    const float4 v = spk[e];
+    const int l = sli[e];
+    const float m = fmaf(qx, v.y, fmaf(qy, v.z, qz * v.w));
+    const float a0 = ca * v.x;
+    float z1 = 0.f;
+    if constexpr (TRANSF) z1 = smd[e];
+    const float2* xr = xs + l * 32;
+    const float2 m2 = make_float2(m, m);
+#pragma unroll
+    for (int kk = 0; kk < NB; ++kk) {
+      const float2 xx = xr[off[kk]];
+      float c = a0;
+      if constexpr (TRANSF) c = fmaf(cb[kk], z1, c);
+      P[kk] = __ffma2_rn(make_float2(c, c), xx, P[kk]);
+      Q[kk] = __ffma2_rn(m2, xx, Q[kk]);
+    }
+  }
+  const size_t erow = (size_t)row * op.Rp;
+  const float2* pown = xs + lo * 32;
+#pragma unroll
+  for (int kk = 0; kk < NB; ++kk) {
+    const float2 y = make_float2(fmaf(-cc[kk], Q[kk].y, P[kk].x), fmaf(cc[kk], Q[kk].x, P[kk].y));
+    if (act[kk]) __stcs(q + erow + colk[kk], y);
+    float2 pv = pown[off[kk]];
+    if constexpr (CONJ) pv = conjf2(pv);
+    const float wgt = act[kk] ? 1.f : 0.f;  // inactive systems add zeros
+    cmacf(a32[kk][0], make_float2(wgt * pv.x, wgt * pv.y), y);
+  }
+}
+
+// End of a slice SpMM block: the FP64 partials of (p, q) of its NW warps
+// (kept by the group-0 lanes) summed per system into the block's slot of
+// rs.part; the last block to arrive forms alpha for every system.
+template <int NB, int NW>
+__device__ __forceinline__ void slice_epilogue(char* smem, int tid, int warp, int g, int lp, int tt, int jc, int tb,
+                                               const OpArgs& op, const SegPlan& spt, const KrylovState& ks,
+                                               RedScratch rs, const double2 (&a64)[NB][1]) {
+  constexpr int LPR = 32 / NB;
+  // block reduction: group-0 lanes of each warp hold FP64 partials of the
+  // slice's 32 systems (lane lp: systems L*NB .. L*NB+NB-1)
+  double2* red = reinterpret_cast<double2*>(smem);  // [NW warps][32 systems]
+  if (g == 0 && warp < NW) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) red[(size_t)warp * 32 + lp * NB + b] = a64[b][0];
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double2 sum = make_double2(0.0, 0.0);
+    for (int wp = 0; wp < NW; ++wp) {
+      const double2 v = red[(size_t)wp * 32 + tid];
+      sum.x += v.x;
+      sum.y += v.y;
+    }
+    // slice system tid = lp * NB + b belongs to lane L = LPR jc + lp
+    const int rloc = (tt * 32 + LPR * jc + tid / NB) * NB + tid % NB;
+    if (rloc < op.R) reinterpret_cast<double2*>(rs.part)[(size_t)tb * op.Rp + rloc] = sum;
+  }
+  if (!last_block(rs.counter, gridDim.x)) return;
+  if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
+  __syncthreads();
+  for (int s = threadIdx.x; s < spt.G * op.R; s += blockDim.x) {
+    const int gg = s / op.R, rl = s - gg * op.R;
+    double2 t = make_double2(0, 0);
+    for (int b = spt.blk0[gg]; b < spt.blk0[gg + 1]; ++b) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(rs.part) + (size_t)b * op.Rp + rl);
+      t.x += v.x;
+      t.y += v.y;
+    }
+    count_segment_iter(ks, s, op.R);
+    krylov_alpha(ks, s, t);
+    ks.pend[s] = ks.active[s];  // the x update of this iteration is still to do
+  }
+}
+
+// the stages, then the mbarriers and counters (64 bytes)
+size_t slice_smem_bytes(int c) { return (size_t)SLICE_CONF[c].stages * stage_layout(c).total + 64; }
 
 // ---------------------------------------------------------------- SpMM + (p, q)
 // Two stages: the next tile's copies overlap this tile's sums; one stage:
@@ -370,39 +470,8 @@ __global__ void __launch_bounds__(SLICE_CONF[CFG].threads, SLICE_CONF[CFG].block
         const int row = srow[k];
         const int ea = srowe[k] - e0, eb = srowe[k + 1] - e0;
         const int lo = srowl[k];
-        float2 P[NB], Q[NB];
-#pragma unroll
-        for (int kk = 0; kk < NB; ++kk) P[kk] = Q[kk] = make_float2(0.f, 0.f);
-#pragma unroll 2
-        for (int e = ea; e < eb; ++e) {
-          const float4 v = spk[e];
-          const int l = sli[e];
-          const float m = fmaf(qx, v.y, fmaf(qy, v.z, qz * v.w));
-          const float a0 = ca * v.x;
-          float z1 = 0.f;
-          if constexpr (TRANSF) z1 = smd[e];
-          const float2* xr = xs + l * 32;
-          const float2 m2 = make_float2(m, m);
-#pragma unroll
-          for (int kk = 0; kk < NB; ++kk) {
-            const float2 xx = xr[off[kk]];
-            float c = a0;
-            if constexpr (TRANSF) c = fmaf(cb[kk], z1, c);
-            P[kk] = __ffma2_rn(make_float2(c, c), xx, P[kk]);
-            Q[kk] = __ffma2_rn(m2, xx, Q[kk]);
-          }
-        }
-        const size_t erow = (size_t)row * op.Rp;
-        const float2* pown = xs + lo * 32;
-#pragma unroll
-        for (int kk = 0; kk < NB; ++kk) {
-          const float2 y = make_float2(fmaf(-cc[kk], Q[kk].y, P[kk].x), fmaf(cc[kk], Q[kk].x, P[kk].y));
-          if (act[kk]) __stcs(q + erow + colk[kk], y);
-          float2 pv = pown[off[kk]];
-          if constexpr (CONJ) pv = conjf2(pv);
-          const float wgt = act[kk] ? 1.f : 0.f;  // inactive systems add zeros
-          cmacf(a32[kk][0], make_float2(wgt * pv.x, wgt * pv.y), y);
-        }
+        slice_row<NB, TRANSF>(spk, sli, smd, xs, row, ea, eb, lo, op, q, qx, qy, qz, ca, cb, cc, off, colk, act,
+                              a32);
       }
       if ((++ntile & 3) == 0) slice_flush<NB, LPR>(a32, a64, g);
       __syncthreads();  // the stage is refilled before it is read again
@@ -410,41 +479,202 @@ __global__ void __launch_bounds__(SLICE_CONF[CFG].threads, SLICE_CONF[CFG].block
     cpa_wait<0>();
   }
   slice_flush<NB, LPR>(a32, a64, g);
-  // block reduction: group-0 lanes of each warp hold FP64 partials of the
-  // slice's 32 systems (lane lp: systems L*NB .. L*NB+NB-1)
   __syncthreads();
-  double2* red = reinterpret_cast<double2*>(smem);  // [NW warps][32 systems]
-  if (g == 0) {
+  slice_epilogue<NB, NW>(smem, tid, warp, g, lp, tt, jc, tb, op, spt, ks, rs, a64);
+}
+
+// ---------------------------------------------------------------- warp-specialized SpMM
+// A configuration with ws = 1: warps 0..CW-1 sum, warp CW only copies.  Each
+// of the two stages has a full mbarrier (the 32 producer lanes arrive when
+// their cp.async pieces have landed, and lane 0's arrival arms the planes' bulk
+// copy) and an empty mbarrier (one arrival per consumer warp once the stage's
+// tile has no rows left for it).  Consumer warps take NB rows at a time from
+// the stage's row counter, so a warp that finishes a tile early goes on to the
+// next one instead of waiting at a block barrier.  Every wait is bounded: a
+// consumer that times out records BT_ETIMEOUT for its systems and raises the
+// block's abort flag; the producer then stops, and before the block ends it
+// waits (bounded) for every stage it filled, so no copy lands in released
+// shared memory.
+template <int NB, bool TRANSF, int CFG>
+__global__ void __launch_bounds__(SLICE_CONF[CFG].threads, 1)
+    k_spmm_slice_ws(OpArgs op, HaloArgs h, SegPlan spt, int S, const float2* __restrict__ p, float2* __restrict__ q,
+                    KrylovState ks, RedScratch rs) {
+  if (*ks.n_active == 0) return;
+  static_assert(SLICE_CONF[CFG].ws == 1 && SLICE_CONF[CFG].stages == 2 && SLICE_CONF[CFG].umax % 32 == 0,
+                "warp-specialized configuration");
+  constexpr int SL_UMAX = SLICE_CONF[CFG].umax, SL_TMAX = SLICE_CONF[CFG].tmax;
+  constexpr StageLayout LY = stage_layout(CFG);
+  constexpr size_t SL_HALO_BYTES = LY.halo, SL_PK_BYTES = LY.pk, SL_MD_BYTES = LY.md, SL_LI_BYTES = LY.li,
+                   SL_STAGE_BYTES = LY.total;
+  constexpr int LPR = 32 / NB, PPC = 16 / NB;
+  constexpr int CW = SLICE_CONF[CFG].threads / 32 - 1;  // consumer warps; warp CW copies
+  extern __shared__ float4 sl_smem_[];
+  char* smem = reinterpret_cast<char*>(sl_smem_);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int slice = blockIdx.x % S, tb = blockIdx.x / S;
+  const int tt = slice / NB, jc = slice % NB;
+  const int g = lane / LPR, lp = lane % LPR;
+  const int L = LPR * jc + lp;
+  const int r0 = (tt * 32 + L) * NB;       // first system of this lane (in its segment)
+  const int c0 = tt * 32 * NB + L;         // its first column
+  const int cs = tt * 32 * NB + LPR * jc;  // first column of chunk 0 of the slice
+  const bool on = r0 < op.R;
+  const int sg = spt.blk_seg[tb], sk = tb - spt.blk0[sg], snb = spt.blk0[sg + 1] - spt.blk0[sg];
+  const OpCoef cf = op_coef(op, sg);
+  const int base = sg * op.R;
+  const int dsys = base + (on ? r0 : 0);
+  const float qx = (float)op.qhat[3 * dsys], qy = (float)op.qhat[3 * dsys + 1], qz = (float)op.qhat[3 * dsys + 2];
+  const float ca = (float)cf.a;
+  float cb[NB], cc[NB];
+  int off[NB], colk[NB];
+  bool act[NB];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) red[(size_t)warp * 32 + lp * NB + b] = a64[b][0];
+  for (int k = 0; k < NB; ++k) {
+    const int b = (k + g) % NB, rr = r0 + b;
+    const double qq = (on && rr < op.R) ? op.q[base + rr] : 0.0;
+    cb[k] = (float)(cf.bq2 * qq * qq);
+    cc[k] = (float)(cf.cq * qq);
+    act[k] = on && rr < op.R && ks.active[base + rr] != 0;
+    off[k] = b * LPR;
+    colk[k] = c0 + 32 * b;
+  }
+  float2 a32[NB][1];
+  double2 a64[NB][1];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    a32[k][0] = make_float2(0.f, 0.f);
+    a64[k][0] = make_double2(0.0, 0.0);
+  }
+  const int T0 = h.seg_tile0[sg], T1 = h.seg_tile0[sg + 1];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * SL_STAGE_BYTES);
+  uint64_t* empty = full + 2;
+  int* cnt = reinterpret_cast<int*>(empty + 2);  // row counters of the two stages
+  volatile int* abort_flag = cnt + 2;
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) any |= act[k];
+  if (tid == 0) {
+    mbar_init(full, 33u);
+    mbar_init(full + 1, 33u);
+    mbar_init(empty, (unsigned)CW);
+    mbar_init(empty + 1, (unsigned)CW);
+    cnt[0] = cnt[1] = 0;
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
-  if (tid < 32) {
-    double2 sum = make_double2(0.0, 0.0);
-    for (int wp = 0; wp < NW; ++wp) {
-      const double2 v = red[(size_t)wp * 32 + tid];
-      sum.x += v.x;
-      sum.y += v.y;
+  if (__syncthreads_or(any)) {
+    if (warp == CW) {
+      // ---- producer: fill stage it & 1 with tile tau once its previous tile is consumed
+      int last0 = -1, last1 = -1;  // last use of each stage
+      int it = 0;
+      for (int tau = T0 + sk; tau < T1; tau += snb, ++it) {
+        const int st = it & 1, use = it >> 1;
+        if (use > 0 && !mbar_wait(empty + st, (unsigned)(use - 1) & 1u)) break;
+        if (*abort_flag) break;
+        char* b0 = smem + (size_t)st * SL_STAGE_BYTES;
+        float2* sh = reinterpret_cast<float2*>(b0);
+        float4* spk = reinterpret_cast<float4*>(b0 + SL_HALO_BYTES);
+        float* smd = reinterpret_cast<float*>(b0 + SL_HALO_BYTES + SL_PK_BYTES);
+        uint32_t* sli = reinterpret_cast<uint32_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES);
+        int32_t* srow = reinterpret_cast<int32_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES + SL_LI_BYTES);
+        int32_t* srowe = srow + SL_TMAX;
+        uint32_t* srowl = reinterpret_cast<uint32_t*>(srowe + SL_TMAX + 1);
+        // extents (tile builder: nu <= SL_UMAX, ne <= emax, nown <= SL_TMAX)
+        const int u0 = __ldg(h.u0 + tau), nu = __ldg(h.u0 + tau + 1) - u0;
+        const int e0 = __ldg(h.e0 + tau), ne = __ldg(h.e0 + tau + 1) - e0;
+        const int R0 = __ldg(h.t_r0 + tau), nown = __ldg(h.t_r0 + tau + 1) - R0;
+        // halo row ids, 32 rows per load: lane i holds row 32 j + i
+        uint32_t rid[SL_UMAX / 32];
+#pragma unroll
+        for (int j = 0; j < SL_UMAX / 32; ++j) {
+          const int u = 32 * j + lane;
+          rid[j] = u < nu ? (__ldg(h.ucol + u0 + u) & 0x7FFFFFFFu) : 0u;
+        }
+        if (lane == 0) {
+          *reinterpret_cast<int4*>(b0 + SL_STAGE_BYTES - 16) = make_int4(e0, R0, nown, ne);
+          cnt[st] = 0;
+          fence_async_smem();
+          mbar_expect(full + st, (unsigned)ne * 16u);  // arrival 33: arms the planes' bulk copy
+          if (ne > 0) bulk_g2s(spk, h.pkt + e0, (unsigned)ne * 16u, full + st);
+        }
+        // halo rows: 16 lanes per row (piece lane & 15), two rows per instruction
+        const int pc = lane & 15, b = pc / PPC, pp = pc - b * PPC;
+#pragma unroll
+        for (int j = 0; j < SL_UMAX / 32; ++j) {
+#pragma unroll
+          for (int v = 0; v < 16; ++v) {
+            const int u = 32 * j + 2 * v + (lane >> 4);
+            const uint32_t r = __shfl_sync(0xffffffffu, rid[j], 2 * v + (lane >> 4));
+            if (u < nu) cpa16(sh + u * 32 + b * LPR + 2 * pp, p + (size_t)r * op.Rp + cs + 32 * b + 2 * pp);
+          }
+        }
+        if constexpr (TRANSF)
+          for (int e = lane; e < ne; e += 32) cpa4(smd + e, h.mdt + e0 + e);
+        const int w0 = e0 >> 1, nw = ((e0 + ne + 1) >> 1) - w0;  // the index array is padded
+        for (int w = lane; w < nw; w += 32) cpa4(sli + w, reinterpret_cast<const uint32_t*>(h.lidx) + w0 + w);
+        for (int k = lane; k <= nown; k += 32) {
+          if (k < nown) cpa4(srow + k, h.rows + R0 + k);
+          cpa4(srowe + k, h.rowe + R0 + k);
+        }
+        const int l0 = R0 >> 1, nl = ((R0 + nown + 1) >> 1) - l0;  // the local-index array is padded
+        for (int k = lane; k < nl; k += 32) cpa4(srowl + k, reinterpret_cast<const uint32_t*>(h.rowl) + l0 + k);
+        cpa_mbar_arrive(full + st);  // arrivals 1..32: each lane's pieces have landed
+        if (st == 0) last0 = use;
+        else last1 = use;
+      }
+      // the stages this warp filled land before the block's shared memory is released
+      if (last0 >= 0) mbar_wait(full, (unsigned)last0 & 1u);
+      if (last1 >= 0) mbar_wait(full + 1, (unsigned)last1 & 1u);
+    } else {
+      // ---- consumers: rows of stage it & 1, NB at a time, until the tile has none left
+      int it = 0, ntile = 0;
+      for (int tau = T0 + sk; tau < T1; tau += snb, ++it) {
+        const int st = it & 1, use = it >> 1;
+        const bool arrived = mbar_wait(full + st, (unsigned)use & 1u);
+        if (!arrived) {
+#pragma unroll
+          for (int kk = 0; kk < NB; ++kk)
+            if (act[kk]) ks.status[base + r0 + (kk + g) % NB] = BT_ETIMEOUT;
+          *abort_flag = 1;
+        }
+        if (!arrived || *abort_flag) break;
+        const char* b0 = smem + (size_t)st * SL_STAGE_BYTES;
+        const float2* sh = reinterpret_cast<const float2*>(b0);
+        const float4* spk = reinterpret_cast<const float4*>(b0 + SL_HALO_BYTES);
+        const float* smd = reinterpret_cast<const float*>(b0 + SL_HALO_BYTES + SL_PK_BYTES);
+        const int4 hdr = *reinterpret_cast<const int4*>(b0 + SL_STAGE_BYTES - 16);  // written by the producer
+        const int e0 = hdr.x, R0 = hdr.y, nown = hdr.z;
+        const uint16_t* sli =
+            reinterpret_cast<const uint16_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES) + (e0 & 1);
+        const int32_t* srow =
+            reinterpret_cast<const int32_t*>(b0 + SL_HALO_BYTES + SL_PK_BYTES + SL_MD_BYTES + SL_LI_BYTES);
+        const int32_t* srowe = srow + SL_TMAX;
+        const uint16_t* srowl = reinterpret_cast<const uint16_t*>(srowe + SL_TMAX + 1) + (R0 & 1);
+        const float2* xs = sh + lp;
+        for (;;) {
+          int k0 = 0;
+          if (lane == 0) k0 = atomicAdd(cnt + st, NB);
+          k0 = __shfl_sync(0xffffffffu, k0, 0);
+          if (k0 >= nown) break;
+          const int k = k0 + g;  // one row per row group of the warp
+          if (k < nown) {
+            const int row = srow[k];
+            const int ea = srowe[k] - e0, eb = srowe[k + 1] - e0;
+            const int lo = srowl[k];
+            slice_row<NB, TRANSF>(spk, sli, smd, xs, row, ea, eb, lo, op, q, qx, qy, qz, ca, cb, cc, off, colk, act,
+                                  a32);
+          }
+        }
+        if ((++ntile & 3) == 0) slice_flush<NB, LPR>(a32, a64, g);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + st);  // this warp is done with the stage
+      }
     }
-    // slice system tid = lp * NB + b belongs to lane L = LPR jc + lp
-    const int rloc = (tt * 32 + LPR * jc + tid / NB) * NB + tid % NB;
-    if (rloc < op.R) reinterpret_cast<double2*>(rs.part)[(size_t)tb * op.Rp + rloc] = sum;
   }
-  if (!last_block(rs.counter, gridDim.x)) return;
-  if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
+  slice_flush<NB, LPR>(a32, a64, g);
   __syncthreads();
-  for (int s = threadIdx.x; s < spt.G * op.R; s += blockDim.x) {
-    const int gg = s / op.R, rl = s - gg * op.R;
-    double2 t = make_double2(0, 0);
-    for (int b = spt.blk0[gg]; b < spt.blk0[gg + 1]; ++b) {
-      const double2 v = __ldcg(reinterpret_cast<const double2*>(rs.part) + (size_t)b * op.Rp + rl);
-      t.x += v.x;
-      t.y += v.y;
-    }
-    count_segment_iter(ks, s, op.R);
-    krylov_alpha(ks, s, t);
-    ks.pend[s] = ks.active[s];  // the x update of this iteration is still to do
-  }
+  slice_epilogue<NB, CW>(smem, tid, warp, g, lp, tt, jc, tb, op, spt, ks, rs, a64);
 }
 
 // ---------------------------------------------------------------- vector updates
@@ -858,6 +1088,8 @@ static void slice_attr() {
                        (int)slice_smem_bytes(2));
   cudaFuncSetAttribute(k_spmm_slice<NB, TRANSF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)slice_smem_bytes(3));
+  cudaFuncSetAttribute(k_spmm_slice_ws<NB, TRANSF, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)slice_smem_bytes(4));
 }
 void slice_prepare() {
   slice_attr<4, false>();
@@ -888,12 +1120,26 @@ void launch_spmm_slice(const OpArgs& op, const HaloArgs& h, const SegPlan& spt, 
     case 2: BT_SL_CASE(2, CFGV) break;  \
     default: BT_SL_CASE(1, CFGV) break; \
   }
+#define BT_SL_WS_CASE(NBV, CFGV)                                                                        \
+  {                                                                                                    \
+    constexpr int NT_ = SLICE_CONF[CFGV].threads;                                                      \
+    if (op.transformed) k_spmm_slice_ws<NBV, true, CFGV><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs); \
+    else k_spmm_slice_ws<NBV, false, CFGV><<<grid, NT_, sm, st>>>(op, h, spt, S, p, q, ks, rs);            \
+  }
   switch (cfg) {
     case 0: BT_SL_NB(0) break;
     case 1: BT_SL_NB(1) break;
     case 2: BT_SL_NB(2) break;
-    default: BT_SL_NB(3) break;
+    case 3: BT_SL_NB(3) break;
+    default:
+      switch (nb) {
+        case 4: BT_SL_WS_CASE(4, 4) break;
+        case 2: BT_SL_WS_CASE(2, 4) break;
+        default: BT_SL_WS_CASE(1, 4) break;
+      }
+      break;
   }
+#undef BT_SL_WS_CASE
 #undef BT_SL_NB
 #undef BT_SL_CASE
 }

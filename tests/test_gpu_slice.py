@@ -67,7 +67,7 @@ def field():
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("loop", ["graph", "host"])
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4])
 def test_slice_variant_matches_oracle(sim_cls, bt, field, name, loop, cfg):
     p, ref, U = field(name)
     flags = bt.slice_config_flag(cfg) | (bt.BT_OPT_NO_GRAPH if loop == "host" else 0)
