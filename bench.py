@@ -381,7 +381,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     clocks = clk.summary()
     tuning = bt.bt_get_tuning(sim.ctx)
-    # the same runs as one captured CUDA graph per time step (no per-launch
+    # the same runs as one captured CUDA graph per simulation (no per-launch
     # events), on at most two simulations to bound the bench's wall time
     n_graph = min(args.steps, 2)
     eg0, eg1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -556,7 +556,7 @@ def run_ours(args):
             "gpu_launches": int(launches), "clocks": clocks,
             **({"learned_preconditioner": learned} if learned is not None else {}),
             "graph_path": {"value": units * args.steps * ws / (ms_graph / 1e3), "unit": UNIT,
-                           "note": "same runs, each time step one captured CUDA graph with conditional "
+                           "note": "same runs, each simulation one captured CUDA graph with nested conditional "
                                    "WHILE nodes; the headline value uses host-driven launches so that every "
                                    "fused SpMM launch is bracketed by CUDA events for the roofline"}}
     print(json.dumps(line), flush=True)

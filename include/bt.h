@@ -311,7 +311,8 @@ enum { BT_MODE_PLAIN_FP64 = 0, BT_MODE_MIXED = 1, BT_MODE_LEARNED = 2 };
 /* Option flags: BT_OPT_RESID_FP64 native-FP64 refinement residuals;
  * BT_OPT_PROFILE CUDA events around every fused SpMM and residual launch
  * (host-driven loop); BT_OPT_NO_GRAPH host-driven loop instead of the
- * captured step graph; BT_OPT_VARIANT_ROW / _HALO bypass the autotuner and
+ * captured run graph (one launch per simulation: WHILE nodes over the time
+ * steps, the refinement passes and the inner iterations); BT_OPT_VARIANT_ROW / _HALO bypass the autotuner and
  * use that Krylov variant together with the row / halo double-float residuals
  * (bt_get_tuning; _HALO falls back to the tuned choice where the halo tiles
  * are not available); BT_OPT_VARIANT_SLICE bypasses the autotuner's Krylov

@@ -1094,12 +1094,12 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
   cudaStream_t run_st = ctx->stream;
   for (auto& s : ctx->cap_stream)
     if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return BT_ECUDA;
-  cudaStream_t cs = ctx->cap_stream[2], c2 = ctx->cap_stream[0], c3 = ctx->cap_stream[1];
+  cudaStream_t c0 = ctx->cap_stream[3], cs = ctx->cap_stream[2], c2 = ctx->cap_stream[0], c3 = ctx->cap_stream[1];
   if (ensure(ctx->d_ctl, 8) != cudaSuccess) return BT_ECUDA;
   const int h0[8] = {1, 0, 0, 0, 0, 0, 0, 0};
   if (cudaMemcpyAsync(ctx->d_ctl.p, h0, sizeof(h0), cudaMemcpyHostToDevice, run_st) != cudaSuccess) return BT_ECUDA;
   if (cudaStreamSynchronize(run_st) != cudaSuccess) return BT_ECUDA;
-  GraphCtl gc{ctx->d_ctl.p, g.ks.n_active, ctx->d_seg_N.p, Rs, G, o.max_iter, o.max_refine};
+  GraphCtl gc{ctx->d_ctl.p, g.ks.n_active, ctx->d_seg_N.p, Rs, G, o.max_iter, o.max_refine, g.N};
   OpArgs op0 = g.op, opL = g.op;
   op0.coef = opL.coef = ctx->d_coef.p;
   op0.step = opL.step = ctx->d_ctl.p;
@@ -1139,7 +1139,16 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
     E(cudaStreamGetCaptureInfo(s, &cst, nullptr, &capg, nullptr, nullptr, nullptr));
     return capg;
   };
-  if (E(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) {
+  // top level: WHILE (steps left) { one time step }
+  cudaGraphConditionalHandle hS{};
+  cudaGraph_t bodyS = nullptr;
+  if (E(cudaStreamBeginCapture(c0, cudaStreamCaptureModeThreadLocal))) {
+    if (E(cudaGraphConditionalHandleCreate(&hS, capg_of(c0), 0, 0))) {
+      launch_graph_cond(gc, 4, hS, c0);
+      while_node(c0, hS, &bodyS);
+    }
+  }
+  if (ok && E(cudaStreamBeginCaptureToGraph(cs, bodyS, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal))) {
     launch_graph_step_begin(gc, ctx->rf_active.p, cs);
     if (g.df && g.resid_halo && resid_df_halo_available(g.nb, 0))
       launch_resid0_df_halo(op0, halo_args(ctx), ctx->udf.p, ctx->rdf.p, g.rf, rs_at(0), g.nb, cs);
@@ -1211,23 +1220,32 @@ static bt_status run_graph(bt_ctx* ctx, const GraphRun& g, const bt_solver_opts&
     }
     launch_mark_ref_left(g.rf, g.ks, Rs * G, cs);
     launch_graph_step_end(gc, cs);
+    launch_graph_cond(gc, 4, hS, cs);
     E(cudaGetLastError());
     cudaGraph_t tmp = nullptr;
-    const bool was_ok = ok;
-    const cudaError_t ee = cudaStreamEndCapture(cs, &tmp);
-    if (ee != cudaSuccess && was_ok) why = std::string("end capture: ") + cudaGetErrorString(ee);
-    if (ee != cudaSuccess) ok = false;
-    graph = tmp;
+    E(cudaStreamEndCapture(cs, &tmp));
+  }
+  {
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c0, &cst);
+    if (cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t tmp = nullptr;
+      const bool was_ok = ok;
+      const cudaError_t ee = cudaStreamEndCapture(c0, &tmp);
+      if (ee != cudaSuccess && was_ok) why = std::string("end capture: ") + cudaGetErrorString(ee);
+      if (ee != cudaSuccess) ok = false;
+      graph = tmp;
+    }
   }
   if (ok && graph) E(cudaGraphInstantiate(&exec, graph, 0));
   if (!ok || !graph) {
     cudaGetLastError();
     if (graph) cudaGraphDestroy(graph);
     // not an error of the run: the caller drives the same kernels from the host
-    ctx->err = "step graph unavailable (" + why + "); host-driven launches used";
+    ctx->err = "run graph unavailable (" + why + "); host-driven launches used";
     return BT_ECUDA;
   }
-  for (int s = 0; s < g.N && ok; ++s) ok = cudaGraphLaunch(exec, run_st) == cudaSuccess;
+  ok = cudaGraphLaunch(exec, run_st) == cudaSuccess;  // the whole simulation
   int hc[8] = {0};
   if (ok) ok = cudaMemcpyAsync(hc, ctx->d_ctl.p, sizeof(hc), cudaMemcpyDeviceToHost, run_st) == cudaSuccess;
   if (ok) ok = cudaStreamSynchronize(run_st) == cudaSuccess;

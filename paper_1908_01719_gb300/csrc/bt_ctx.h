@@ -69,7 +69,7 @@ struct bt_ctx {
   std::vector<int> seg_N;                        // steps per segment
   std::vector<std::vector<double>> seg_fbar, seg_F;
   bt::DBuf<int> d_blk_seg, d_blk0, d_seg_N, d_ctl;
-  cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};  // captures of the step graph
+  cudaStream_t cap_stream[4] = {nullptr, nullptr, nullptr, nullptr};  // captures of the run graph
   bt::DBuf<int64_t> d_row0;
   int nblk = 0;
   int64_t planes_version = 0;  // bumped by every assembly

@@ -348,6 +348,7 @@ struct GraphCtl {
   int* n_active;   // [0] Krylov, [1] refinement
   const int* segN;
   int R, G, max_iter, max_refine;
+  int n_steps;     // time steps of the run (the outer WHILE node's bound)
 };
 void launch_graph_step_begin(const GraphCtl& c, int* rf_active, cudaStream_t st);
 void launch_graph_cond(const GraphCtl& c, int which, cudaGraphConditionalHandle h, cudaStream_t st);

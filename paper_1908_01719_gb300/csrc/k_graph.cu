@@ -1,7 +1,7 @@
-// Device-side control of the captured time step: the step counter, the
-// refinement and inner-Krylov loop counters and the conditions of the two
-// nested WHILE nodes, so that a whole time step runs as one graph launch
-// without any host round trip.
+// Device-side control of the captured run: the step counter, the refinement
+// and inner-Krylov loop counters and the conditions of the three nested WHILE
+// nodes (time steps, refinement passes, inner iterations), so that a whole
+// simulation runs as one graph launch without any host round trip.
 #include "bt_kernels.cuh"
 
 namespace bt {
@@ -29,9 +29,12 @@ __global__ void k_graph_step_begin(GraphCtl c, int* rf_active) {
 //         1: end of a refinement pass (live systems and passes left)
 //         2: before the inner loop (condition: active systems)
 //         3: end of an inner iteration (active systems and iterations left)
+//         4: before the first and after every time step (steps left)
 __global__ void k_graph_cond(GraphCtl c, int which, cudaGraphConditionalHandle h) {
   unsigned int v = 0;
-  if (which == 0) {
+  if (which == 4) {
+    v = c.ctl[0] <= c.n_steps;
+  } else if (which == 0) {
     v = c.n_active[1] > 0;
   } else if (which == 1) {
     const int p = ++c.ctl[1];

@@ -30,7 +30,7 @@ def main():
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--steps", type=int, default=2, help="time steps (pulse on throughout)")
     ap.add_argument("--mode", default="mixed", choices=["mixed", "plain"])
-    ap.add_argument("--variant", default="auto", choices=["auto", "row", "halo", "slice", "slice1", "slice_small", "slice_small1"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "row", "halo", "slice", "slice1", "slice_small", "slice_small1", "slice_ws"],
                     help="inner Krylov variant (auto: the autotuner's choice)")
     a = ap.parse_args()
     build()

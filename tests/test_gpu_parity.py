@@ -169,7 +169,7 @@ def test_field_matches_oracle_elementwise(sim_cls, bt, live_field, name, mode):
 def test_krylov_variants_match_oracle(sim_cls, bt, live_field, name, variant, loop):
     """Each inner-Krylov variant (row SpMM; halo-staged apply with the fused
     direction and solution updates and halo-staged residuals), driven by
-    the captured step graph or by the host loop: signals and fields against
+    the captured run graph or by the host loop: signals and fields against
     the oracle at the mixed-mode bound."""
     p, ref, U = live_field(name)
     flags = {"row": bt.BT_OPT_VARIANT_ROW, "halo": bt.BT_OPT_VARIANT_HALO}[variant]

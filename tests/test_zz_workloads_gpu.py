@@ -48,7 +48,7 @@ def _shell():
 def test_cfg4_full_size_properties(sim_cls, bt):
     """cfg4 at full size (96^3 Kuhn grid, 1.07 M dofs, 32 directions x 4
     b-values), run as bench.py runs it (mixed mode, autotuned variants,
-    captured step graph): sampled RHS against the plain FP64 GPU path (itself
+    captured run graph): sampled RHS against the plain FP64 GPU path (itself
     parity-tested against the oracle above), and, on the same geometry, the
     b = 0 signal equal to the box volume at every direction (conservation,
     exact at any size)."""
