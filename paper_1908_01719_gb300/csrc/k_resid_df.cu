@@ -398,6 +398,23 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
     accf[b] = make_float2(0, 0);
   }
   int cnt = 0;
+  // A correction whose systems are all past the first pass of their step
+  // (|r_prev| <= 1e-4 |r_0|) forms L d with FP32 products and sums: the
+  // correction is then at most 1e-4 |r_0|, so FP32 rounding of L d (about
+  // 1e-7 of sum |L_ij| |d_j|) stays near 1e-10 |r_0|, two orders below the
+  // refinement tolerance; the updates of u and r stay double-float.  Every
+  // warp of a block covers the same systems, so the choice is block-uniform.
+  bool late = false;
+  if constexpr (MODE == 1) {
+    bool l = true;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (act[b]) {
+        const int s = sg_ * op.R + r0 + b;
+        l = l && rf.rk2[s] <= 1e-8 * rf.r0n2[s];
+      }
+    late = __all_sync(0xffffffffu, l);
+  }
   if (__syncthreads_or(any)) {
     const int tb = h.seg_tile0[sg_], te = h.seg_tile0[sg_ + 1];
     for (int tau = tb + sk_; tau < te; tau += snb_) {
@@ -439,6 +456,27 @@ __global__ void __launch_bounds__(256, 2) k_resid_df_halo(OpArgs op, HaloArgs h,
         float2 Ph[NB], Pl[NB], Qh[NB], Ql[NB], Zh[NB], Zl[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) Ph[b] = Pl[b] = Qh[b] = Ql[b] = Zh[b] = Zl[b] = make_float2(0.f, 0.f);
+        if (MODE == 1 && late) {
+          // FP32 products and sums into the high words (the low words stay 0)
+          for (int e = e0; e < e1; ++e) {
+            const float4 vh = sent[3 * e];
+            const int l = sl16[e];
+            const float m = fmaf(qx.h, vh.y, fmaf(qy.h, vh.z, qz.h * vh.w));
+            const float2 p2 = bc(vh.x), m2 = bc(m);
+            float2 md2 = make_float2(0.f, 0.f);
+            if constexpr (TRANSF) md2 = bc(sent[3 * e + 2].y);
+            const TX* xp = xs_ + l * NB * 32 + lane;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              if constexpr (MODE == 1) {
+                const float2 xv = xp[32 * b];
+                Ph[b] = __ffma2_rn(p2, xv, Ph[b]);
+                Qh[b] = __ffma2_rn(m2, xv, Qh[b]);
+                if constexpr (TRANSF) Zh[b] = __ffma2_rn(md2, xv, Zh[b]);
+              }
+            }
+          }
+        } else
         for (int e = e0; e < e1; ++e) {
           const float4 vh = sent[3 * e], vl = sent[3 * e + 1], kk4 = sent[3 * e + 2];  // {kh.x, kh.y, kl.x, kl.y}
           const int l = sl16[e];
