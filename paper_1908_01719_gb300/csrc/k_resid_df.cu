@@ -156,6 +156,19 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
     accf[b] = make_float2(0, 0);
   }
   int cnt = 0;
+  // the FP32 form of L d once every system of the warp is past its step's
+  // first pass (as in k_resid_df_halo below)
+  bool late = false;
+  if constexpr (MODE == 1) {
+    bool l = true;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (on && lc.act[b]) {
+        const int s = sg_ * op.R + r0 + b;
+        l = l && rf.rk2[s] <= 1e-8 * rf.r0n2[s];
+      }
+    late = __all_sync(0xffffffffu, l);
+  }
   if (warp_any) {
     BT_FOR_SEG_CHUNKED_ROWS(row, warp, W) {
       const int k0 = op.rp[row], k1 = op.rp[row + 1];
@@ -183,6 +196,24 @@ __global__ void __launch_bounds__(256) k_resid_df(OpArgs op, const TX* __restric
           for (int u = 0; u < DU; ++u) {
             const int k = kb + t + u;
             if (t + u >= n_in) break;
+            if (MODE == 1 && late) {
+              const float4 vh = __ldg(op.pkhi + k);
+              const float m = fmaf(qx.h, vh.y, fmaf(qy.h, vh.z, qz.h * vh.w));
+              const float2 p2 = bc(vh.x), m2 = bc(m);
+              float2 md2 = make_float2(0.f, 0.f);
+              if constexpr (TRANSF) md2 = bc(__ldg(op.kjmd_hi + k).y);
+              if (!on) continue;
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                if constexpr (MODE == 1) {
+                  const float2 xv = xs[u][b];
+                  Ph[b] = __ffma2_rn(p2, xv, Ph[b]);
+                  Qh[b] = __ffma2_rn(m2, xv, Qh[b]);
+                  if constexpr (TRANSF) Zh[b] = __ffma2_rn(md2, xv, Zh[b]);
+                }
+              }
+              continue;
+            }
             const float4 vh = __ldg(op.pkhi + k), vl = __ldg(op.pklo + k);
             float p0h, p0l;
             float mdh = 0.f, mdl = 0.f;
