@@ -3,9 +3,9 @@ slice of p staged in shared memory, then an r update with the inner products
 and an x/p update) against the FP64 oracle, for
 every vector layout it serves (1, 2 and 4 right-hand sides per lane), both
 frames (COCG in the lab frame, CG in the transformed frame), both drivers
-(captured run graph, host loop), all four configurations (tiles of 256 or
+(captured run graph, host loop), all five configurations (tiles of 256 or
 128 halo rows; two pipelined shared-memory stages or one; one, two or three
-blocks per SM) and an uneven batch.  Bound: mixed mode,
+blocks per SM; a copy warp feeding fifteen summing warps) and an uneven batch.  Bound: mixed mode,
 1e-6 relative per signal, and every dof of every field at 1e-6 of its
 largest value."""
 import numpy as np
