@@ -510,19 +510,44 @@ __device__ __forceinline__ void reduce_partials_flat(const double* part, int nbx
   }
 }
 
+// Sum over blocks b0..b1-1 of the NC complex partials part[(b Rp + r) NC + c]
+// by one warp: lane l adds blocks b0 + l, b0 + l + 32, ... in order, then a
+// fixed xor tree combines the lanes (the same order on every run); every lane
+// gets the sums.  A block-sized last-block reduction done by one thread per
+// system serialises hundreds of L2 round trips; this spreads them over 32.
+template <int NC>
+__device__ __forceinline__ void warp_sum_part(const double* part, int b0, int b1, int Rp, int r,
+                                              double2 (&out)[NC]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c] = make_double2(0, 0);
+  for (int b = b0 + lane; b < b1; b += 32)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(part) + ((size_t)b * Rp + r) * NC + c);
+      out[c].x += v.x;
+      out[c].y += v.y;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      out[c].x += __shfl_xor_sync(0xffffffffu, out[c].x, o);
+      out[c].y += __shfl_xor_sync(0xffffffffu, out[c].y, o);
+    }
+}
+
 // For every global system s = g R + r: sum part[b][r] over the blocks b of
-// segment g in a fixed order; callback fn(s, sum).
+// segment g (one warp per system, warp_sum_part); callback fn(s, sum) on
+// lane 0.  blockDim.x must be a multiple of 32.
 template <class F>
 __device__ __forceinline__ void reduce_partials(const double* part, const SegPlan& sp, int Rp, int R, F&& fn) {
-  for (int s = threadIdx.x; s < sp.G * R; s += blockDim.x) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int s = warp; s < sp.G * R; s += nw) {
     const int g = s / R, r = s - g * R;
-    double2 t = make_double2(0, 0);
-    for (int b = sp.blk0[g]; b < sp.blk0[g + 1]; ++b) {
-      double2 v = __ldcg(reinterpret_cast<const double2*>(part) + (size_t)b * Rp + r);
-      t.x += v.x;
-      t.y += v.y;
-    }
-    fn(s, t);
+    double2 t[1];
+    warp_sum_part<1>(part, sp.blk0[g], sp.blk0[g + 1], Rp, r, t);
+    if ((threadIdx.x & 31) == 0) fn(s, t[0]);
   }
 }
 

@@ -87,23 +87,6 @@ __device__ bool elem_block_reduce(double2 (&acc)[EM_NK][NC], const ElemMap& em, 
   return last_block(counter, gridDim.x);
 }
 
-// sum of the partials of global system s = g R + r over the blocks of segment g
-template <int NC>
-__device__ __forceinline__ void sum_part(const double* part, const SegPlan& sp, int R, int Rp, int s,
-                                         double2 (&out)[NC]) {
-#pragma unroll
-  for (int c = 0; c < NC; ++c) out[c] = make_double2(0, 0);
-  const int g = s / R, r = s - g * R;
-  s = r;
-  for (int b = sp.blk0[g]; b < sp.blk0[g + 1]; ++b)
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      double2 v = __ldcg(reinterpret_cast<const double2*>(part) + ((size_t)b * Rp + s) * NC + c);
-      out[c].x += v.x;
-      out[c].y += v.y;
-    }
-}
-
 static int elem_grid(const VecArgs& va) { return va.sp.nblk; }
 
 // rows of this block: a contiguous share of its segment
@@ -200,9 +183,10 @@ __global__ void __launch_bounds__(256) k_krylov_init(OpArgs op, VecArgs va, cons
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
     double2 o[2];
-    sum_part<2>(rs.part, va.sp, va.R, va.Rp, s, o);
+    warp_sum_part<2>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
+    if ((threadIdx.x & 31) != 0) continue;
     ks.rho[2 * s] = o[0].x;
     ks.rho[2 * s + 1] = o[0].y;
     ks.rr0[s] = o[1].x;
@@ -303,10 +287,11 @@ __global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
     if (!ks.active[s]) continue;
     double2 o[2];
-    sum_part<2>(rs.part, va.sp, va.R, va.Rp, s, o);
+    warp_sum_part<2>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
+    if ((threadIdx.x & 31) != 0) continue;
     if (krylov_step_finish(ks, s, o, pmode)) atomicAdd(&s_cnt, 1);
   }
   __syncthreads();
@@ -445,9 +430,10 @@ __global__ void __launch_bounds__(256) k_signal(VecArgs va, const double* __rest
     }
   }
   if (!elem_block_reduce<1>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
-  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
     double2 o[1];
-    sum_part<1>(rs.part, va.sp, va.R, va.Rp, s, o);
+    warp_sum_part<1>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
+    if ((threadIdx.x & 31) != 0) continue;
     S[2 * s] = o[0].x;
     S[2 * s + 1] = o[0].y;
   }
@@ -647,9 +633,10 @@ __global__ void __launch_bounds__(256) k_krylov_init_z(OpArgs op, VecArgs va, co
     *ks.par = 0;
   }
   __syncthreads();
-  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
     double2 o[2];
-    sum_part<2>(rs.part, va.sp, va.R, va.Rp, s, o);
+    warp_sum_part<2>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
+    if ((threadIdx.x & 31) != 0) continue;
     ks.rho[2 * s] = o[0].x;
     ks.rho[2 * s + 1] = o[0].y;
     ks.beta[2 * s] = 0;
@@ -741,10 +728,11 @@ __global__ void __launch_bounds__(256) k_krylov_update_z(OpArgs op, VecArgs va, 
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
     if (!ks.active[s]) continue;
     double2 o[2];
-    sum_part<2>(rs.part, va.sp, va.R, va.Rp, s, o);
+    warp_sum_part<2>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
+    if ((threadIdx.x & 31) != 0) continue;
     if (krylov_step_finish(ks, s, o, nullptr)) atomicAdd(&s_cnt, 1);
   }
   __syncthreads();
@@ -880,9 +868,10 @@ __global__ void __launch_bounds__(256) k_resid0_renorm(VecArgs va, const T* __re
   if (!elem_block_reduce<1>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
   if (threadIdx.x == 0) *rf.n_active = va.sp.G * va.R;
   __syncthreads();
-  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
     double2 o[1];
-    sum_part<1>(rs.part, va.sp, va.R, va.Rp, s, o);
+    warp_sum_part<1>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
+    if ((threadIdx.x & 31) != 0) continue;
     rf.active[s] = 1;
     refine_finish(0, rf, s, o[0]);
   }

@@ -256,17 +256,15 @@ __device__ __forceinline__ void slice_epilogue(char* smem, int tid, int warp, in
   if (!last_block(rs.counter, gridDim.x)) return;
   if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
   __syncthreads();
-  for (int s = threadIdx.x; s < spt.G * op.R; s += blockDim.x) {
+  for (int s = warp; s < spt.G * op.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
     const int gg = s / op.R, rl = s - gg * op.R;
-    double2 t = make_double2(0, 0);
-    for (int b = spt.blk0[gg]; b < spt.blk0[gg + 1]; ++b) {
-      const double2 v = __ldcg(reinterpret_cast<const double2*>(rs.part) + (size_t)b * op.Rp + rl);
-      t.x += v.x;
-      t.y += v.y;
+    double2 t[1];
+    warp_sum_part<1>(rs.part, spt.blk0[gg], spt.blk0[gg + 1], op.Rp, rl, t);
+    if ((tid & 31) == 0) {
+      count_segment_iter(ks, s, op.R);
+      krylov_alpha(ks, s, t[0]);
+      ks.pend[s] = ks.active[s];  // the x update of this iteration is still to do
     }
-    count_segment_iter(ks, s, op.R);
-    krylov_alpha(ks, s, t);
-    ks.pend[s] = ks.active[s];  // the x update of this iteration is still to do
   }
 }
 
@@ -828,18 +826,12 @@ __global__ void __launch_bounds__(256, 2) k_slice_r(OpArgs op, VecArgs va, float
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
     if (!ks.active[s]) continue;
     const int gg = s / va.R, rl = s - gg * va.R;
-    double2 o[2] = {make_double2(0, 0), make_double2(0, 0)};
-    for (int b = va.sp.blk0[gg]; b < va.sp.blk0[gg + 1]; ++b)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const double2 v = __ldcg(reinterpret_cast<const double2*>(rs.part) + ((size_t)b * Rp + rl) * 2 + c);
-        o[c].x += v.x;
-        o[c].y += v.y;
-      }
-    if (krylov_step_finish(ks, s, o, nullptr)) atomicAdd(&s_cnt, 1);
+    double2 o[2];
+    warp_sum_part<2>(rs.part, va.sp.blk0[gg], va.sp.blk0[gg + 1], Rp, rl, o);
+    if ((threadIdx.x & 31) == 0 && krylov_step_finish(ks, s, o, nullptr)) atomicAdd(&s_cnt, 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) *ks.n_active = s_cnt;
@@ -1046,16 +1038,11 @@ __global__ void __launch_bounds__(256, 2) k_slice_init(OpArgs op, VecArgs va, co
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < va.sp.G * va.R; s += blockDim.x) {
+  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
     const int gg = s / va.R, rl = s - gg * va.R;
-    double2 o[2] = {make_double2(0, 0), make_double2(0, 0)};
-    for (int b = va.sp.blk0[gg]; b < va.sp.blk0[gg + 1]; ++b)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const double2 v = __ldcg(reinterpret_cast<const double2*>(rs.part) + ((size_t)b * Rp + rl) * 2 + c);
-        o[c].x += v.x;
-        o[c].y += v.y;
-      }
+    double2 o[2];
+    warp_sum_part<2>(rs.part, va.sp.blk0[gg], va.sp.blk0[gg + 1], Rp, rl, o);
+    if ((threadIdx.x & 31) != 0) continue;
     ks.rho[2 * s] = o[0].x;
     ks.rho[2 * s + 1] = o[0].y;
     ks.rr0[s] = o[1].x;
