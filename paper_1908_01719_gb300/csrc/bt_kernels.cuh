@@ -537,18 +537,54 @@ __device__ __forceinline__ void warp_sum_part(const double* part, int b0, int b1
     }
 }
 
+// The NC complex block partials part[(b Rp + r) NC + c] of every system
+// s = g R + r of a launch's segments, summed over the segment's blocks b in a
+// fixed order and handed to fn(s, sums) by one thread; skip(s) leaves a system
+// out.  A system is summed by one thread when the segments have few blocks and
+// by one warp (warp_sum_part) when they have many: whichever costs fewer
+// dependent L2 round trips per thread (many systems with few blocks each, as
+// in a batch of small geometries, favour threads; few systems with hundreds of
+// blocks favour warps).  The choice is the same in the whole block, whose size
+// must be a multiple of 32.
+template <int NC, class Skip, class F>
+__device__ __forceinline__ void reduce_systems(const double* part, const SegPlan& sp, int R, int Rp, Skip&& skip,
+                                               F&& fn) {
+  const int GR = sp.G * R, nb = (sp.nblk + sp.G - 1) / sp.G;  // blocks per segment, on average
+  const int nt = (int)blockDim.x, nw = nt >> 5;
+  const bool by_warp =
+      (int64_t)((GR + nt - 1) / nt) * nb > (int64_t)((GR + nw - 1) / nw) * ((nb + 31) / 32 + 5);
+  if (by_warp) {
+    for (int s = (int)(threadIdx.x >> 5); s < GR; s += nw) {
+      if (skip(s)) continue;
+      const int g = s / R;
+      double2 o[NC];
+      warp_sum_part<NC>(part, sp.blk0[g], sp.blk0[g + 1], Rp, s - g * R, o);
+      if ((threadIdx.x & 31) == 0) fn(s, o);
+    }
+  } else {
+    for (int s = (int)threadIdx.x; s < GR; s += nt) {
+      if (skip(s)) continue;
+      const int g = s / R, r = s - g * R;
+      double2 o[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) o[c] = make_double2(0, 0);
+      for (int b = sp.blk0[g]; b < sp.blk0[g + 1]; ++b)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const double2 v = __ldcg(reinterpret_cast<const double2*>(part) + ((size_t)b * Rp + r) * NC + c);
+          o[c].x += v.x;
+          o[c].y += v.y;
+        }
+      fn(s, o);
+    }
+  }
+}
+
 // For every global system s = g R + r: sum part[b][r] over the blocks b of
-// segment g (one warp per system, warp_sum_part); callback fn(s, sum) on
-// lane 0.  blockDim.x must be a multiple of 32.
+// segment g (reduce_systems); callback fn(s, sum).
 template <class F>
 __device__ __forceinline__ void reduce_partials(const double* part, const SegPlan& sp, int Rp, int R, F&& fn) {
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int s = warp; s < sp.G * R; s += nw) {
-    const int g = s / R, r = s - g * R;
-    double2 t[1];
-    warp_sum_part<1>(part, sp.blk0[g], sp.blk0[g + 1], Rp, r, t);
-    if ((threadIdx.x & 31) == 0) fn(s, t[0]);
-  }
+  reduce_systems<1>(part, sp, R, Rp, [](int) { return false; }, [&](int s, const double2 (&o)[1]) { fn(s, o[0]); });
 }
 
 

@@ -183,10 +183,8 @@ __global__ void __launch_bounds__(256) k_krylov_init(OpArgs op, VecArgs va, cons
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
-    double2 o[2];
-    warp_sum_part<2>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
-    if ((threadIdx.x & 31) != 0) continue;
+  reduce_systems<2>(rs.part, va.sp, va.R, va.Rp, [](int) { return false; },
+                     [&](int s, const double2 (&o)[2]) {
     ks.rho[2 * s] = o[0].x;
     ks.rho[2 * s + 1] = o[0].y;
     ks.rr0[s] = o[1].x;
@@ -202,7 +200,7 @@ __global__ void __launch_bounds__(256) k_krylov_init(OpArgs op, VecArgs va, cons
     }
     ks.active[s] = a;
     if (a) atomicAdd(&s_cnt, 1);
-  }
+  });
   __syncthreads();
   if (threadIdx.x == 0) *ks.n_active = s_cnt;
 }
@@ -287,13 +285,10 @@ __global__ void __launch_bounds__(256) k_krylov_update(OpArgs op, VecArgs va, T2
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
-    if (!ks.active[s]) continue;
-    double2 o[2];
-    warp_sum_part<2>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
-    if ((threadIdx.x & 31) != 0) continue;
+  reduce_systems<2>(rs.part, va.sp, va.R, va.Rp, [&](int s) { return !ks.active[s]; },
+                     [&](int s, const double2 (&o)[2]) {
     if (krylov_step_finish(ks, s, o, pmode)) atomicAdd(&s_cnt, 1);
-  }
+  });
   __syncthreads();
   if (threadIdx.x == 0) *ks.n_active = s_cnt;
 }
@@ -430,13 +425,11 @@ __global__ void __launch_bounds__(256) k_signal(VecArgs va, const double* __rest
     }
   }
   if (!elem_block_reduce<1>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
-  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
-    double2 o[1];
-    warp_sum_part<1>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
-    if ((threadIdx.x & 31) != 0) continue;
+  reduce_systems<1>(rs.part, va.sp, va.R, va.Rp, [](int) { return false; },
+                     [&](int s, const double2 (&o)[1]) {
     S[2 * s] = o[0].x;
     S[2 * s + 1] = o[0].y;
-  }
+  });
 }
 
 // ---------------------------------------------------------------- launchers
@@ -633,10 +626,8 @@ __global__ void __launch_bounds__(256) k_krylov_init_z(OpArgs op, VecArgs va, co
     *ks.par = 0;
   }
   __syncthreads();
-  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
-    double2 o[2];
-    warp_sum_part<2>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
-    if ((threadIdx.x & 31) != 0) continue;
+  reduce_systems<2>(rs.part, va.sp, va.R, va.Rp, [](int) { return false; },
+                     [&](int s, const double2 (&o)[2]) {
     ks.rho[2 * s] = o[0].x;
     ks.rho[2 * s + 1] = o[0].y;
     ks.beta[2 * s] = 0;
@@ -655,7 +646,7 @@ __global__ void __launch_bounds__(256) k_krylov_init_z(OpArgs op, VecArgs va, co
     }
     ks.active[s] = a;
     if (a) atomicAdd(&s_cnt, 1);
-  }
+  });
   __syncthreads();
   if (threadIdx.x == 0) *ks.n_active = s_cnt;
 }
@@ -728,13 +719,10 @@ __global__ void __launch_bounds__(256) k_krylov_update_z(OpArgs op, VecArgs va, 
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
-    if (!ks.active[s]) continue;
-    double2 o[2];
-    warp_sum_part<2>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
-    if ((threadIdx.x & 31) != 0) continue;
+  reduce_systems<2>(rs.part, va.sp, va.R, va.Rp, [&](int s) { return !ks.active[s]; },
+                     [&](int s, const double2 (&o)[2]) {
     if (krylov_step_finish(ks, s, o, nullptr)) atomicAdd(&s_cnt, 1);
-  }
+  });
   __syncthreads();
   if (threadIdx.x == 0) *ks.n_active = s_cnt;
 }
@@ -868,13 +856,11 @@ __global__ void __launch_bounds__(256) k_resid0_renorm(VecArgs va, const T* __re
   if (!elem_block_reduce<1>(acc, em, va.Rp, va.nb, rs.part, rs.counter)) return;
   if (threadIdx.x == 0) *rf.n_active = va.sp.G * va.R;
   __syncthreads();
-  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
-    double2 o[1];
-    warp_sum_part<1>(rs.part, va.sp.blk0[s / va.R], va.sp.blk0[s / va.R + 1], va.Rp, s % va.R, o);
-    if ((threadIdx.x & 31) != 0) continue;
+  reduce_systems<1>(rs.part, va.sp, va.R, va.Rp, [](int) { return false; },
+                     [&](int s, const double2 (&o)[1]) {
     rf.active[s] = 1;
     refine_finish(0, rf, s, o[0]);
-  }
+  });
 }
 
 void launch_weak_coupling(const WeakArgs& wa, const VecArgs& va, const OpArgs& op, const void* u, void* r, int df,

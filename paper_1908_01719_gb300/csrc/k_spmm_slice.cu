@@ -256,16 +256,11 @@ __device__ __forceinline__ void slice_epilogue(char* smem, int tid, int warp, in
   if (!last_block(rs.counter, gridDim.x)) return;
   if (threadIdx.x == 0 && ks.sys_iter) atomicAdd(ks.sys_iter, (unsigned long long)*ks.n_active);
   __syncthreads();
-  for (int s = warp; s < spt.G * op.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
-    const int gg = s / op.R, rl = s - gg * op.R;
-    double2 t[1];
-    warp_sum_part<1>(rs.part, spt.blk0[gg], spt.blk0[gg + 1], op.Rp, rl, t);
-    if ((tid & 31) == 0) {
-      count_segment_iter(ks, s, op.R);
-      krylov_alpha(ks, s, t[0]);
-      ks.pend[s] = ks.active[s];  // the x update of this iteration is still to do
-    }
-  }
+  reduce_systems<1>(rs.part, spt, op.R, op.Rp, [](int) { return false; }, [&](int s, const double2 (&t)[1]) {
+    count_segment_iter(ks, s, op.R);
+    krylov_alpha(ks, s, t[0]);
+    ks.pend[s] = ks.active[s];  // the x update of this iteration is still to do
+  });
 }
 
 // the stages, then the mbarriers and counters (64 bytes)
@@ -826,13 +821,10 @@ __global__ void __launch_bounds__(256, 2) k_slice_r(OpArgs op, VecArgs va, float
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
-    if (!ks.active[s]) continue;
-    const int gg = s / va.R, rl = s - gg * va.R;
-    double2 o[2];
-    warp_sum_part<2>(rs.part, va.sp.blk0[gg], va.sp.blk0[gg + 1], Rp, rl, o);
-    if ((threadIdx.x & 31) == 0 && krylov_step_finish(ks, s, o, nullptr)) atomicAdd(&s_cnt, 1);
-  }
+  reduce_systems<2>(rs.part, va.sp, va.R, Rp, [&](int s) { return !ks.active[s]; },
+                    [&](int s, const double2 (&o)[2]) {
+                      if (krylov_step_finish(ks, s, o, nullptr)) atomicAdd(&s_cnt, 1);
+                    });
   __syncthreads();
   if (threadIdx.x == 0) *ks.n_active = s_cnt;
 }
@@ -1038,11 +1030,7 @@ __global__ void __launch_bounds__(256, 2) k_slice_init(OpArgs op, VecArgs va, co
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int s = (int)(threadIdx.x >> 5); s < va.sp.G * va.R; s += (int)(blockDim.x >> 5)) {  // one warp per system
-    const int gg = s / va.R, rl = s - gg * va.R;
-    double2 o[2];
-    warp_sum_part<2>(rs.part, va.sp.blk0[gg], va.sp.blk0[gg + 1], Rp, rl, o);
-    if ((threadIdx.x & 31) != 0) continue;
+  reduce_systems<2>(rs.part, va.sp, va.R, Rp, [](int) { return false; }, [&](int s, const double2 (&o)[2]) {
     ks.rho[2 * s] = o[0].x;
     ks.rho[2 * s + 1] = o[0].y;
     ks.rr0[s] = o[1].x;
@@ -1059,7 +1047,7 @@ __global__ void __launch_bounds__(256, 2) k_slice_init(OpArgs op, VecArgs va, co
     }
     ks.active[s] = a;
     if (a) atomicAdd(&s_cnt, 1);
-  }
+  });
   __syncthreads();
   if (threadIdx.x == 0) *ks.n_active = s_cnt;
 }
