@@ -66,3 +66,13 @@ def test_workloads_and_oracle_samples():
     assert p.tets.shape[1] == 3 and p.n_rhs == 128
     assert np.allclose(p.dirs[:, 2], 0.0) and np.allclose(np.linalg.norm(p.dirs, axis=1), 1.0)
     assert bench.oracle_grid("cfg4") == bench.ORACLE_GRID and bench.oracle_grid("disk2d") == 192
+
+
+def test_every_krylov_variant_has_a_byte_model():
+    """The bench reports the roofline of whichever variant the library used:
+    every name bt_get_tuning can return needs its vector counts and kernel."""
+    from paper_1908_01719_gb300 import bt
+    for v in bt.VARIANTS:
+        assert v in bench.VECTORS_PER_SYSTEM and v in bench.VECTORS_PER_ITER and v in bench.KERNEL, v
+    assert bt.slice_config_flag(0) == 1 << bt.BT_OPT_SLICE_CONFIG_SHIFT
+    assert len(bt.VARIANTS) == 2 + 5
